@@ -1,0 +1,144 @@
+"""Seeded synthetic inputs: wave-speed fields and point-like sources.
+
+This module holds input generation only (no step of the solver's arithmetic); both the GPU
+path's tests/benchmarks and the CPU oracle's tests draw their inputs from it.
+
+Grid convention: n_a cell-centred interior nodes per axis, x_p = (p + 1/2) h on [0, n_a h];
+fields are numpy arrays of shape n[::-1] (x1 fastest).  Every generator is deterministic in
+its seed (numpy.random.default_rng).
+"""
+
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+def node_coords(n_a: int, h: float):
+    return (np.arange(n_a) + 0.5) * h
+
+
+def gaussian_source(n, h, centre, width, cutoff: float = 6.0):
+    """Unit-mass Gaussian exp(-|x-x0|^2 / (2 w^2)) / (2 pi w^2)^(d/2), set to 0 beyond cutoff*w.
+
+    The truncation makes the support compact, so subdomains away from the source see an exactly
+    zero local source.
+    """
+    d = len(n)
+    coords = [node_coords(n[a], h) for a in range(d)]
+    grids = np.meshgrid(*coords[::-1], indexing="ij")       # grids[k] varies along x_{d-k}
+    r2 = np.zeros(tuple(n[::-1]))
+    for a in range(d):
+        r2 = r2 + (grids[d - 1 - a] - centre[a]) ** 2
+    f = np.exp(-r2 / (2.0 * width * width)) / (2.0 * math.pi * width * width) ** (d / 2.0)
+    f[r2 > (cutoff * width) ** 2] = 0.0
+    return f
+
+
+def uniform_centres(rng, count: int, dim: int, lo: float, hi: float):
+    return rng.uniform(lo, hi, size=(count, dim))
+
+
+def gaussian_sources(n, h, centres, width):
+    """One Gaussian per right-hand side: array of shape (R, *n[::-1]), complex128."""
+    return np.stack([gaussian_source(n, h, c, width) for c in centres]).astype(np.complex128)
+
+
+def medium_constant(n, c0: float = 1.0):
+    return np.full(tuple(n[::-1]), c0, dtype=np.float64)
+
+
+def medium_two_layer(n, h, interface: float = 0.37, c_below: float = 1.0,
+                     c_above: float = 1.5, axis: int = 1):
+    """Sharp two-layer medium (Eq. 3.11): c_below where x_{axis+1} < interface, else c_above."""
+    d = len(n)
+    x = node_coords(n[axis], h)
+    shp = [1] * d
+    shp[d - 1 - axis] = n[axis]
+    layer = np.where(x < interface, c_below, c_above).reshape(shp)
+    return np.broadcast_to(layer, tuple(n[::-1])).astype(np.float64).copy()
+
+
+def medium_random(n, h, seed: int, corr_len: float = 0.1, c_min: float = 1.0,
+                  c_max: float = 2.0):
+    """Smooth random medium: c = c_min + (c_max - c_min) Phi(g), g a unit-variance Gaussian
+    random field with Gaussian covariance of length corr_len (spectral filtering of seeded white
+    noise with numpy's FFT), Phi the standard normal CDF."""
+    rng = np.random.default_rng(seed)
+    shape = tuple(n[::-1])
+    noise = rng.standard_normal(shape)
+    freqs = np.meshgrid(*[np.fft.fftfreq(s, d=h) for s in shape], indexing="ij")
+    k2 = sum((2 * math.pi * f) ** 2 for f in freqs)
+    filt = np.exp(-k2 * corr_len ** 2 / 4.0)
+    g = np.real(np.fft.ifftn(np.fft.fftn(noise) * filt))
+    g = (g - g.mean()) / g.std()
+    phi = 0.5 * (1.0 + np.vectorize(math.erf)(g / math.sqrt(2.0)))
+    return c_min + (c_max - c_min) * phi
+
+
+@dataclass
+class Workload:
+    """A named synthetic workload: problem parameters plus its seeded right-hand sides."""
+    name: str
+    n: tuple
+    parts: tuple
+    omega: float
+    pml_cells: int
+    pml_strength: float
+    c: np.ndarray
+    f: np.ndarray                      # (R, *n[::-1]) complex sources on interior nodes
+    precision: str = "fp64"
+    rounds: int = 1
+    tol: float = 1e-6
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def h(self):
+        return 1.0 / self.n[0]
+
+
+def workload(name: str, nrhs: int | None = None) -> Workload:
+    """The synthetic workloads (sizes, media and source recipes) used by tests and benchmarks.
+
+    const2d_128   2D, 128^2 interior, h = 1/128, kappa = 2 pi 8, 2x2 subdomains, 16-cell PML,
+                  one Gaussian (w = 2h) at (0.5, 0.5), direct FP64 DDM, one round.
+    const2d_640   2D, 640^2, kappa = 2 pi 40, 8x8 subdomains of 80^2, 12-cell PML, 16 Gaussians
+                  at seeded uniform centres, mixed precision + FGMRES to 1e-6.
+    layer2d_1024  2D two-layer (c = 1 below y = 0.37, 1.5 above), omega = 2 pi 50, 1024^2,
+                  16x16 subdomains, 12-cell PML, 64 seeded Gaussians, FGMRES to 1e-6.
+    const3d_128   3D, 128^3, kappa = 2 pi 10, 4x4x4 subdomains of 32^3, 8-cell PML, 8 Gaussians.
+    """
+    if name == "const2d_128":
+        n = (128, 128)
+        h = 1.0 / 128
+        f = gaussian_sources(n, h, [(0.5, 0.5)], 2 * h)
+        return Workload(name, n, (2, 2), 2 * math.pi * 8, 16, 30.0, medium_constant(n), f,
+                        "fp64", 1, 1e-6)
+    if name == "const2d_640":
+        n = (640, 640)
+        h = 1.0 / 640
+        R = 16 if nrhs is None else nrhs
+        w = 2 * h
+        cen = uniform_centres(np.random.default_rng(2), R, 2, 6 * w, 1 - 6 * w)
+        return Workload(name, n, (8, 8), 2 * math.pi * 40, 12, 30.0, medium_constant(n),
+                        gaussian_sources(n, h, cen, w), "mixed", 1, 1e-6)
+    if name == "layer2d_1024":
+        n = (1024, 1024)
+        h = 1.0 / 1024
+        R = 64 if nrhs is None else nrhs
+        w = 2 * h
+        cen = uniform_centres(np.random.default_rng(3), R, 2, 6 * w, 1 - 6 * w)
+        return Workload(name, n, (16, 16), 2 * math.pi * 50, 12, 30.0,
+                        medium_two_layer(n, h), gaussian_sources(n, h, cen, w), "mixed", 1,
+                        1e-6)
+    if name == "const3d_128":
+        n = (128, 128, 128)
+        h = 1.0 / 128
+        R = 8 if nrhs is None else nrhs
+        w = 2 * h
+        cen = uniform_centres(np.random.default_rng(4), R, 3, 6 * w, 1 - 6 * w)
+        return Workload(name, n, (4, 4, 4), 2 * math.pi * 10, 8, 30.0, medium_constant(n),
+                        gaussian_sources(n, h, cen, w), "mixed", 1, 1e-6)
+    raise KeyError(name)
