@@ -1,0 +1,381 @@
+"""Benchmark: RHS solves per second of the mixed-precision DDM-preconditioned solver.
+
+Workload (default): 2D constant medium c = 1, kappa = 2 pi 40, 640^2 interior grid (h = 1/640),
+8x8 subdomains of 80^2 with a 12-cell PML (quadratic, strength 30), 16 right-hand sides, each a
+unit-mass Gaussian (width 2h) at a seeded uniform position; complex64 sweeps + FP64 FGMRES.
+One step = one dds_solve of the whole 16-RHS batch to relative residual `tol` (every RHS must
+also reach relative L2 error <= 1e-6 against the plain FP64 GPU solve, checked after timing).
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+N > 1 runs one independent replica per GPU (RHS sharding, no collective on the data path);
+value is the whole-job RHS/s over all ranks.  Rank 0 prints one JSON line.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "RHS solves/sec at rel. L2 1e-6 vs plain FP64 GPU sweep; p50/p99 latency"
+WORKLOAD = "const2d_640"
+WORKLOAD_DESC = ("2D constant medium c=1, k=2*pi*40, 640x640 interior grid, 8x8 subdomains "
+                 "(80x80 + 12-cell PML), 16 Gaussian point sources (width 2h) at seeded uniform "
+                 "positions, complex64 sweeps + FP64 FGMRES")
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.path is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _reduce_max(value: float, world: int):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle (the "reference" arm and the cpu_baseline)
+# ------------------------------------------------------------------------------------------
+def oracle_solve_sample(wl, rhs_index: int, workers: int, tol: float):
+    """One FGMRES solve of one right-hand side of the workload by the CPU oracle."""
+    from oracle.discretize import Problem, assemble_global, extend_interior, rhs_from_source
+    from oracle.fgmres import fgmres
+    from oracle.sweep import LocalProblems, ddm_solve
+    prob = Problem(wl.n, wl.h, wl.omega, wl.c, wl.parts, wl.pml_cells, wl.pml_strength)
+    A, _ = assemble_global(prob)
+    loc = LocalProblems(prob)
+    b = rhs_from_source(prob, extend_interior(prob, wl.f[rhs_index]))
+    shape = b.shape
+    t0 = time.perf_counter()
+    x, it, hist = fgmres(lambda v: A @ v,
+                         lambda v: ddm_solve(prob, v.reshape(shape), wl.rounds, loc,
+                                             workers=workers).ravel(),
+                         b.ravel(), tol=tol, maxit=60)
+    return time.perf_counter() - t0, it, hist[-1]
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    from paper_2003_02585_gb300 import synth
+    wl = synth.workload(args.workload)
+    workers = os.cpu_count() or 1
+    for w in range(args.warmup):
+        oracle_solve_sample(wl, w % wl.f.shape[0], workers, args.tol)
+    times = []
+    iters = []
+    for k in range(args.steps):
+        dt, it, _ = oracle_solve_sample(wl, k % wl.f.shape[0], workers, args.tol)
+        times.append(dt)
+        iters.append(it)
+    total = sum(times)
+    value = args.steps / total
+    sample = (f"one FGMRES solve (tol {args.tol:g}) of one of the {wl.f.shape[0]} right-hand "
+              f"sides per step, oracle subdomain solves of each sweep step on a thread pool")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "RHS/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "name": args.workload, "rhs_per_step": 1},
+        "cpu_baseline": {"value": value, "unit": "RHS/s", "cores": workers, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "RHS/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "fgmres_iterations": iters,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------
+def run_gpu(args):
+    import torch
+
+    from paper_2003_02585_gb300 import build as lbuild
+    from paper_2003_02585_gb300 import dds, synth
+
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    lbuild.build()
+    wl = synth.workload(args.workload)
+    R = wl.f.shape[0]
+
+    ctx = dds.Context(wl.n, wl.h, wl.omega, wl.c, wl.parts, wl.pml_cells, wl.pml_strength,
+                      precision="mixed", plan=args.plan)
+    info = ctx.info()
+    f_host = ctx.extend(wl.f)
+    f_dev = torch.from_numpy(f_host).to(dev)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # 256 MB > 129 MB L2
+
+    iters_seen = []
+    for _ in range(args.warmup):
+        u, it, rel = ctx.solve(f_dev, tol=args.tol, maxit=args.maxit, rounds=wl.rounds)
+        iters_seen.append(it)
+    torch.cuda.synchronize()
+
+    launches0 = ctx.launches()
+    step_ms = []
+    with ClockSampler(local) as clk:
+        _barrier(world)
+        torch.cuda.synchronize()
+        for _ in range(args.steps):
+            flush.fill_(1)                                    # L2 flush between timed steps
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            u, it, rel = ctx.solve(f_dev, tol=args.tol, maxit=args.maxit, rounds=wl.rounds)
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            iters_seen.append(it)
+        torch.cuda.synchronize()
+        _barrier(world)
+    clocks = clk.summary()
+    launches = ctx.launches() - launches0
+    total_ms = _reduce_max(sum(step_ms), world)
+    value = world * R * args.steps / (total_ms / 1e3)
+    u_mixed = u
+
+    # accuracy against the plain FP64 GPU solve, and that solve's own throughput
+    ctx64 = dds.Context(wl.n, wl.h, wl.omega, wl.c, wl.parts, wl.pml_cells, wl.pml_strength,
+                        precision="fp64", plan=args.plan)
+    u64, it64, rel64 = ctx64.solve(f_dev, tol=1e-10, maxit=args.maxit, rounds=wl.rounds)
+    torch.cuda.synchronize()
+    err = [float(torch.linalg.vector_norm(u_mixed[r] - u64[r]) / torch.linalg.vector_norm(u64[r]))
+           for r in range(R)]
+    fp64_ms = []
+    for _ in range(args.fp64_steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, it_c, rel_c = ctx64.solve(f_dev, tol=args.tol, maxit=args.maxit, rounds=wl.rounds)
+        e1.record(stream)
+        e1.synchronize()
+        fp64_ms.append(e0.elapsed_time(e1))
+    fp64_value = R * len(fp64_ms) / (sum(fp64_ms) / 1e3) if fp64_ms else None
+    ctx64.close()
+    del ctx64, u64
+
+    # end to end through the C ABI with host (pinned) buffers
+    f_pin = torch.from_numpy(f_host).pin_memory()
+    u_pin = torch.empty_like(f_pin).pin_memory()
+    fn = f_pin.numpy()
+    un = u_pin.numpy()
+    e2e_s = []
+    for _ in range(args.e2e_steps):
+        t0 = time.perf_counter()
+        st = ctx._lib.dds_solve(ctx._h, ctx._ptr(fn), R, ctx._ptr(un), args.tol, args.maxit,
+                                wl.rounds, None, None)
+        e2e_s.append(time.perf_counter() - t0)
+        if st not in (0, 4):
+            raise RuntimeError(f"dds_solve from host buffers failed: {st}")
+    e2e_total = _reduce_max(sum(e2e_s), world)
+    e2e_value = world * R * len(e2e_s) / e2e_total
+
+    # roofline of the dominant kernel family, timed with CUDA events on the library's stream
+    ctx.profile(True)
+    for _ in range(args.profile_steps):
+        ctx.solve(f_dev, tol=args.tol, maxit=args.maxit, rounds=wl.rounds)
+    stats = ctx.kernel_stats()
+    ctx.profile(False)
+    roofline = roofline_entry(stats, info, wl, R, args)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        workers = os.cpu_count() or 1
+        dt, it_o, _ = oracle_solve_sample(wl, 0, workers, args.tol)
+        cpu = {"value": 1.0 / dt, "unit": "RHS/s", "cores": workers, "kind": "oracle",
+               "sample": f"one FGMRES solve (tol {args.tol:g}, {it_o} iterations) of right-hand "
+                         f"side 0 of the same workload, {dt:.1f} s"}
+
+    lat = sorted(step_ms)
+
+    def pct(p):
+        return lat[min(len(lat) - 1, int(math.ceil(p / 100.0 * len(lat))) - 1)]
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c64 sweeps + c128 FGMRES", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "name": args.workload, "global_batch": R * world,
+                   "grid": list(wl.n), "parts": list(wl.parts), "pml_cells": wl.pml_cells,
+                   "tol": args.tol, "rounds": wl.rounds, "plan": args.plan,
+                   "parallelism": f"replicas x{world} (RHS sharding)",
+                   "l2_flush": "256 MB buffer written between timed steps"},
+        "latency_ms": {"p50": pct(50), "p99": pct(99)},
+        "accuracy": {"max_rel_l2_vs_fp64_gpu": max(err), "fp64_reference_tol": 1e-10,
+                     "fgmres_iterations": sorted(set(iters_seen))},
+        "fp64_comparator": {"value": fp64_value, "unit": "RHS/s",
+                            "what": "same plan and step structure in FP64 (plain FP64 GPU sweep"
+                                    " + FP64 FGMRES)", "steps": len(fp64_ms)},
+        "e2e": {"value": e2e_value, "unit": "RHS/s",
+                "h2d_bytes_per_step": int(f_host.nbytes), "d2h_bytes_per_step": int(f_host.nbytes)},
+        "gpu_launches": launches,
+        "setup_seconds": info["setup_seconds"],
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def roofline_entry(stats, info, wl, R, args):
+    """Roofline of the substitution kernel family (algorithmic FLOPs per launch / event time).
+
+    Algorithmic work of one block-tridiagonal solve: forward + back substitution touch every
+    block inverse once each, 2 * Ml * Mb^2 complex multiply-adds = 16 * Ml * Mb^2 real flops.
+    """
+    peaks, src = _peaks()
+    n_sub = info["n_sub"]
+    M = info["M"][0]
+    Ml, Mb = M, M                                  # 2D: lines of M nodes
+    flops_per_solve = 16.0 * Ml * Mb * Mb
+    n_launch, ms = stats["subst"]
+    if n_launch == 0 or ms <= 0:
+        return None
+    # each DDM application runs two substitution launches over all (subdomain, RHS) columns
+    solves_per_launch = n_sub * R
+    achieved = flops_per_solve * solves_per_launch / (ms / n_launch / 1e3) / 1e12
+    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12       # FP32 FMA lanes x 2 flop x max SM clock
+    return {"kernel": "k_subst<float> (block forward+back substitution)", "bound": "alu",
+            "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+            "frac": achieved / fp32_peak, "traffic": None,
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+            "launches": n_launch, "avg_launch_ms": ms / n_launch,
+            "family_share": {k: v[1] for k, v in stats.items()}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--tol", type=float, default=1e-7)
+    ap.add_argument("--maxit", type=int, default=40)
+    ap.add_argument("--plan", default="auto", choices=["auto", "direct", "trace"])
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--profile-steps", type=int, default=2)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

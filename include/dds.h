@@ -1,0 +1,160 @@
+/*
+ * dds.h -- C ABI of libdds: trace-transfer diagonal sweeping domain decomposition for the
+ * Helmholtz equation on one GB300 GPU (Leng & Ju, arXiv 2003.02585).
+ *
+ * Problem (Section 1, Eq. 1.1-1.2):  Delta u + kappa^2 u = f,  kappa(x) = omega / c(x),
+ * truncated by the uniaxial PML of Eq. 2.1-2.3 (2D) / Eq. 4.1 (3D) and discretised with the
+ * 5-point (2D) / 7-point (3D) second-order finite-difference stencil (Section 5).  The domain
+ * is cut into an N1 x N2 [x N3] checkerboard (Section 2.3); every subdomain problem is extended
+ * by its own PML (Lemma 2.3) with the wave number extended by Eq. 2.8, factored once, and the
+ * 2^n diagonal sweeps of Algorithm 2.1 / Algorithm 4.1 are run with the trace routing of
+ * Rules 2.4/2.5 (2D) and 4.1/4.2 (3D).
+ *
+ * Grid.  Cell-centred nodes x_p = (p + 1/2) h, p = 0..n_a-1 on the physical box [0, n_a h]
+ * per axis, extended on every side by E = halo + pml_cells nodes (halo un-stretched lines, then
+ * the PML), homogeneous Dirichlet just outside.  The "global extended grid" has
+ * G_a = n_a + 2E nodes per axis.  Field arrays (f, u) are laid out [rhs][x3][x2][x1] over the
+ * global extended grid, x1 fastest, as interleaved complex double (re, im) -- 16 bytes per node.
+ *
+ * PML profile (Eq. 2.1, profile left open by the paper): sigma(t) = S ((t - H h)/(P h))^power
+ * for a distance t beyond the box edge larger than H h, alpha = 1 + i sigma.  The discrete
+ * system is the J-scaled, complex-symmetric form A u = J f of Eq. 2.3 / 4.1, J = prod alpha.
+ *
+ * Pointers.  f, u, Au may be device pointers or host pointers (pageable or pinned); host
+ * buffers are staged through device memory owned by the context.  The caller owns them; the
+ * library never frees or retains a caller pointer after a call returns.
+ *
+ * Errors.  Every call returns a dds_status; nothing is thrown across the ABI.  On failure
+ * dds_last_error(ctx) returns a message (valid until the next call on that context).  A context
+ * may be used by one host thread at a time; a concurrent call returns DDS_EBUSY.
+ */
+#ifndef DDS_H
+#define DDS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dds_ctx dds_ctx;
+
+typedef enum {
+  DDS_OK = 0,
+  DDS_EINVAL = 1,    /* invalid argument (sizes, divisibility, null pointers)                */
+  DDS_ENOMEM = 2,    /* device allocation failed or the memory budget would be exceeded       */
+  DDS_ECUDA = 3,     /* a CUDA call failed (message holds the CUDA error string)              */
+  DDS_ENOCONV = 4,   /* dds_solve reached maxit; u holds the best iterate                     */
+  DDS_ETIMEOUT = 5,  /* a bounded device-side wait gave up                                    */
+  DDS_EBUSY = 6      /* the context is in use by another thread                              */
+} dds_status;
+
+typedef enum {
+  DDS_FP64 = 0,      /* every step in complex double                                          */
+  DDS_MIXED = 1      /* factors in FP64; sweeps (substitutions, trace transfer) in complex    */
+                     /* single; FGMRES residual / orthogonalisation in FP64                   */
+} dds_precision;
+
+typedef enum {
+  DDS_PLAN_AUTO = 0,   /* trace-operator plan in 2D, direct plan in 3D                        */
+  DDS_PLAN_DIRECT = 1, /* one batched local solve per (subdomain, RHS) per sweep step         */
+  DDS_PLAN_TRACE = 2   /* local solves of the own sources and of the summed traces, sweep     */
+                       /* steps through the precomputed trace-to-trace map (needs 16 T bytes  */
+                       /* <= 200 KB, T = trace_len)                                           */
+} dds_plan;
+
+typedef struct {
+  int dim;              /* 2 or 3                                                              */
+  int n[3];             /* interior nodes per axis (n[2] ignored in 2D)                        */
+  double h;             /* mesh width                                                          */
+  double omega;         /* angular frequency; kappa = omega / c                                */
+  const double *c;      /* wave speed at the n[0]*n[1]*(n[2]) interior nodes, x1 fastest;      */
+                        /* HOST pointer, copied during dds_setup                               */
+  int parts[3];         /* N1, N2 (, N3); n[a] % parts[a] == 0                                 */
+  int pml_cells;        /* P >= 1                                                              */
+  double pml_strength;  /* S (30 in the experiments of this library)                           */
+  int pml_power;        /* profile exponent, 2 = quadratic                                     */
+  int halo;             /* H >= 0 un-stretched lines between a box edge and its PML            */
+  int precision;        /* dds_precision                                                       */
+  int plan;             /* dds_plan                                                            */
+} dds_problem;
+
+typedef struct {
+  int G[3];               /* global extended grid per axis                                    */
+  int M[3];               /* extended subdomain grid per axis                                 */
+  int n_sub;              /* number of subdomains                                             */
+  int n_factors;          /* distinct extended-subdomain operators after deduplication        */
+  int trace_len;          /* T: complex entries of all 2n two-line traces of one subdomain    */
+  int plan;               /* plan in use                                                      */
+  long long factor_bytes; /* device bytes held by factors (+ trace maps)                      */
+  double setup_seconds;   /* wall time of dds_setup                                           */
+} dds_info_t;
+
+/* dds_setup -- discretise, deduplicate and factor every extended subdomain (Section 2.3,
+ * Eq. 2.8; block-tridiagonal LU over x_last lines/planes with partial pivoting inside each
+ * Schur block, FP64 on the GPU) and allocate the sweep state.  *out receives a new context on
+ * success and is left untouched on failure. */
+dds_status dds_setup(const dds_problem *prob, dds_ctx **out);
+
+/* dds_sweep -- the DDM as a direct solver: `rounds` rounds of the 2^n diagonal sweeps of
+ * Algorithm 2.1 / 4.1 on the sources f (nrhs fields on the global extended grid), writing
+ * u_DDM (Algorithm 2.1, last line) to u.  rounds >= 1 (Theorem 3.10 needs 2 in two-layer
+ * media). */
+dds_status dds_sweep(dds_ctx *ctx, const void *f, int nrhs, void *u, int rounds);
+
+/* dds_solve -- solve the discrete PML problem for nrhs sources with right-preconditioned
+ * flexible GMRES, one DDM application (`rounds` rounds) per iteration as the preconditioner
+ * (Section 5.2), FP64 residuals and orthogonalisation.  Stops when every RHS has relative
+ * residual ||J f - A u|| / ||J f|| < tol or after maxit iterations (then DDS_ENOCONV).
+ * iters (may be NULL) receives the iteration count; relres (may be NULL, else nrhs doubles,
+ * host memory) the final true relative residual of each RHS. */
+dds_status dds_solve(dds_ctx *ctx, const void *f, int nrhs, void *u, double tol, int maxit,
+                     int rounds, int *iters, double *relres);
+
+/* dds_apply -- Au = J^{-1} A u: the PML operator L of Eq. 2.3 / 4.1 applied to nrhs fields
+ * (so that dds_apply(dds_solve(f)) ~= f). */
+dds_status dds_apply(dds_ctx *ctx, const void *u, int nrhs, void *Au);
+
+/* dds_local_solve -- one block-tridiagonal subdomain solve A_R x = b (the local problem
+ * P_{Omega_ij, kappa_ij} of Algorithm 2.1), for nrhs right-hand sides b laid out
+ * [rhs][x3][x2][x1] over the extended subdomain grid (M per axis), interleaved complex double.
+ * sub is the subdomain's linear index (x1 fastest).  Runs in the context's precision. */
+dds_status dds_local_solve(dds_ctx *ctx, int sub, const void *b, int nrhs, void *x);
+
+/* dds_set_stream -- run all later work of ctx on the given cudaStream_t (NULL = the context's
+ * own stream).  Calls still return only after their work has completed. */
+dds_status dds_set_stream(dds_ctx *ctx, void *cuda_stream);
+
+/* dds_get_info -- sizes and counts of a set-up context. */
+dds_status dds_get_info(const dds_ctx *ctx, dds_info_t *info);
+
+/* dds_kernel_launches -- number of kernels this context has launched so far. */
+long long dds_kernel_launches(const dds_ctx *ctx);
+
+/* Kernel families timed by the profiler (dds_profile_read). */
+typedef enum {
+  DDS_K_ASSEMBLE = 0,   /* own-source + trace-potential right-hand sides                    */
+  DDS_K_SUBST = 1,      /* block-tridiagonal forward + back substitution                    */
+  DDS_K_EXTRACT = 2,    /* own-node accumulation, trace extraction and routing              */
+  DDS_K_TRACE_STEP = 3, /* trace-operator sweep step (trace plan)                            */
+  DDS_K_KRYLOV = 4,     /* FP64 operator apply, reductions and vector updates               */
+  DDS_K_OTHER = 5,      /* set-up, conversions                                              */
+  DDS_K_COUNT = 6
+} dds_kernel_kind;
+
+/* dds_profile -- enable (1) / disable (0) per-launch CUDA-event timing on the context's
+ * stream.  Enabling clears the accumulated statistics. */
+dds_status dds_profile(dds_ctx *ctx, int enable);
+
+/* dds_profile_read -- launches and summed device milliseconds of one kernel family since
+ * profiling was enabled (synchronises the context's stream). */
+dds_status dds_profile_read(dds_ctx *ctx, int kind, long long *launches, double *ms);
+
+/* dds_last_error -- message of the last failed call on ctx (empty string if none). */
+const char *dds_last_error(const dds_ctx *ctx);
+
+/* dds_destroy -- free every device and host resource of ctx (NULL is ignored). */
+void dds_destroy(dds_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DDS_H */

@@ -1,0 +1,1090 @@
+// libdds C ABI (include/dds.h): set-up, sweeps, FGMRES and helpers.
+//
+// Host code only; every arithmetic step of set-up and solve runs in the kernels of
+// k_factor.cu, k_sweep.cu and k_krylov.cu.  The host builds the small tables (PML stretching,
+// line-block coefficients, routing, step schedules) and drives the launches.
+#include <algorithm>
+#include <array>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/dds.h"
+#include "dds_internal.cuh"
+
+using namespace dds;
+using cd = std::complex<double>;
+
+namespace {
+
+struct DBuf {
+  void *p = nullptr;
+  size_t n = 0;
+  DBuf() = default;
+  DBuf(const DBuf &) = delete;
+  DBuf &operator=(const DBuf &) = delete;
+  ~DBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  cudaError_t ensure(size_t bytes) {
+    if (bytes <= n && p) return cudaSuccess;
+    release();
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e == cudaSuccess) n = bytes;
+    else p = nullptr;
+    return e;
+  }
+  template <class T> T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+struct StepPlan {            // launch lists of one (direction, step) or one phase
+  int col_off = 0, ncols = 0;
+  int pan_off = 0, npanels = 0, pc = 1;
+};
+
+struct CallPlan {            // all launch lists for one nrhs
+  int nrhs = 0;
+  std::vector<StepPlan> steps;   // [dir][step] for the direct plan (substitution panels)
+  std::vector<StepPlan> tsteps;  // [dir][step] for the trace plan (trace-step panels)
+  StepPlan all;                  // every (sub, rhs) column (trace plan phases, local solves)
+  DBuf cols, panels;
+};
+
+}  // namespace
+
+struct dds_ctx {
+  std::mutex mu;
+  std::string err;
+  Geom g{};
+  int precision = 0, plan = 0;
+  double h = 0, omega = 0, S = 0;
+  int P = 0, power = 2, H = 0;
+  cudaStream_t stream = nullptr;
+  long long launches = 0;
+  double setup_seconds = 0;
+  int nfac = 0;
+  std::vector<int> fac_of_sub;
+  std::vector<std::vector<std::vector<int>>> step_subs;  // [dir][step] -> subs (by factor)
+  int nsteps = 0, ndirs = 0;
+  // device tables
+  DBuf sinv64, sinv32, cpl64, cpl32, coef64, coef32, k2glob, gmap64, gmap32, status;
+  DBuf an_glob[3], iah_glob[3];
+  Tables tb{};
+  // per-call workspaces
+  std::map<int, std::unique_ptr<CallPlan>> plans;
+  std::map<int, std::vector<int>> routes;  // rounds -> route[L][6]
+  DBuf route_dev;
+  int route_rounds = -1;
+  DBuf work, gtr, acc, rawf, bbuf, stage_in, stage_out, dots_part, dots_out, coefbuf, scalebuf;
+  std::vector<std::unique_ptr<DBuf>> Vb, Zb;
+  // profiler: event pairs around launches, folded into per-kind totals on read
+  bool profiling = false;
+  std::vector<std::array<cudaEvent_t, 2>> ev_pool;
+  std::vector<int> ev_kind;
+  size_t ev_used = 0;
+  long long prof_count[DDS_K_COUNT] = {0};
+  double prof_ms[DDS_K_COUNT] = {0};
+  ~dds_ctx() {
+    for (auto &e : ev_pool) {
+      cudaEventDestroy(e[0]);
+      cudaEventDestroy(e[1]);
+    }
+  }
+};
+
+namespace {
+
+#define CK(call)                                                                 \
+  do {                                                                           \
+    cudaError_t e_ = (call);                                                     \
+    if (e_ != cudaSuccess) {                                                     \
+      ctx->err = std::string(#call) + ": " + cudaGetErrorString(e_);             \
+      return DDS_ECUDA;                                                          \
+    }                                                                            \
+  } while (0)
+
+// launch of kernel family `kind`, timed with an event pair when profiling is on
+#define LAUNCHK(kind, call)                                                      \
+  do {                                                                           \
+    ++ctx->launches;                                                             \
+    cudaEvent_t *ev_ = prof_begin(ctx, kind);                                    \
+    CK(call);                                                                    \
+    if (ev_) CK(cudaEventRecord(ev_[1], ctx->stream));                           \
+  } while (0)
+#define LAUNCH(call) LAUNCHK(DDS_K_OTHER, call)
+
+cudaEvent_t *prof_begin(dds_ctx *ctx, int kind) {
+  if (!ctx->profiling) return nullptr;
+  if (ctx->ev_used == ctx->ev_pool.size()) {
+    std::array<cudaEvent_t, 2> e;
+    if (cudaEventCreate(&e[0]) != cudaSuccess) return nullptr;
+    if (cudaEventCreate(&e[1]) != cudaSuccess) { cudaEventDestroy(e[0]); return nullptr; }
+    ctx->ev_pool.push_back(e);
+    ctx->ev_kind.push_back(kind);
+  }
+  ctx->ev_kind[ctx->ev_used] = kind;
+  cudaEvent_t *e = ctx->ev_pool[ctx->ev_used].data();
+  if (cudaEventRecord(e[0], ctx->stream) != cudaSuccess) return nullptr;
+  ++ctx->ev_used;
+  return e;
+}
+
+// fold recorded event pairs into the per-kind totals (synchronises the stream)
+cudaError_t prof_fold(dds_ctx *ctx) {
+  if (ctx->ev_used == 0) return cudaSuccess;
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return e;
+  for (size_t i = 0; i < ctx->ev_used; ++i) {
+    float ms = 0.f;
+    e = cudaEventElapsedTime(&ms, ctx->ev_pool[i][0], ctx->ev_pool[i][1]);
+    if (e != cudaSuccess) return e;
+    ctx->prof_count[ctx->ev_kind[i]] += 1;
+    ctx->prof_ms[ctx->ev_kind[i]] += ms;
+  }
+  ctx->ev_used = 0;
+  return cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------- PML tables ----
+// sigma(t) = S ((t/h - H) / P)^power beyond the halo, alpha = 1 + i sigma  (Eq. 2.1-2.2)
+cd alpha_at(double t_over_h, int H, int P, double S, int power) {
+  double s = 0.0;
+  if (t_over_h > H) s = S * std::pow((t_over_h - H) / P, power);
+  return cd(1.0, s);
+}
+
+// alphas on an axis of `count` nodes whose node p sits at (p + first) h, box [0, len] (in h)
+void axis_alphas(int count, double first, double len, int H, int P, double S, int power,
+                 std::vector<cd> &an, std::vector<cd> &ah) {
+  an.resize(count);
+  ah.resize(count + 1);
+  auto dist = [&](double x) { return std::max(std::max(-x, x - len), 0.0); };
+  for (int p = 0; p < count; ++p) an[p] = alpha_at(dist(p + first), H, P, S, power);
+  for (int q = 0; q <= count; ++q) ah[q] = alpha_at(dist(q - 0.5 + first), H, P, S, power);
+}
+
+std::vector<std::array<int, 3>> sweep_dirs(int dim) {
+  // Eq. 2.9 / Eq. 4.2: x1 flips fastest, then x2, then x3
+  std::vector<std::array<int, 3>> d;
+  for (int i = 0; i < (1 << dim); ++i) {
+    std::array<int, 3> v{0, 0, 0};
+    for (int a = 0; a < dim; ++a) v[a] = ((i >> a) & 1) ? -1 : 1;
+    d.push_back(v);
+  }
+  return d;
+}
+
+bool similar(const int *v1, const int *v2, int dim) {
+  // Section 2.3 (2D): v1 . v2 > 0; Section 4 (3D): also v1(k) v2(k) >= 0 for every k
+  int dot = 0;
+  bool comp = true;
+  for (int a = 0; a < dim; ++a) {
+    dot += v1[a] * v2[a];
+    if (v1[a] * v2[a] < 0) comp = false;
+  }
+  return dim == 2 ? dot > 0 : (dot > 0 && comp);
+}
+
+bool barred(const int *D, const int *dgen, const int *duse, int dim) {
+  if (dim == 2) {  // Rule 2.5: opposite sweep directions
+    return dgen[0] == -duse[0] && dgen[1] == -duse[1];
+  }
+  // Rule 4.2: a plane projection where D has exactly one zero and the sweeps are opposite
+  const int pl[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+  for (auto &pq : pl) {
+    const int zeros = (D[pq[0]] == 0) + (D[pq[1]] == 0);
+    if (zeros != 1) continue;
+    if (dgen[pq[0]] == -duse[pq[0]] && dgen[pq[1]] == -duse[pq[1]]) return true;
+  }
+  return false;
+}
+
+std::vector<int> build_route(int dim, int rounds) {
+  const auto dirs = sweep_dirs(dim);
+  const int nd = (int)dirs.size(), L = nd * rounds;
+  std::vector<int> route(L * 6, -1);
+  for (int l = 0; l < L; ++l) {
+    for (int d = 0; d < 2 * dim; ++d) {
+      int D[3] = {0, 0, 0};
+      D[d >> 1] = (d & 1) ? -1 : 1;
+      for (int lp = l; lp < L; ++lp) {
+        // Rule 2.4 / 4.1 and Rule 2.5 / 4.2: smallest usable sweep
+        if (!similar(D, dirs[lp % nd].data(), dim)) continue;
+        if (lp > l && barred(D, dirs[l % nd].data(), dirs[lp % nd].data(), dim)) continue;
+        route[l * 6 + d] = lp;
+        break;
+      }
+    }
+  }
+  return route;
+}
+
+bool is_device_ptr(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <class T> cudaError_t upload(DBuf &b, const std::vector<T> &v, cudaStream_t st) {
+  cudaError_t e = b.ensure(v.size() * sizeof(T));
+  if (e != cudaSuccess) return e;
+  if (v.empty()) return cudaSuccess;
+  e = cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(st);
+}
+
+int pick_pc(int ncols, int max_pc) {
+  // widest panel that still leaves about two CTAs per SM of independent panels
+  int pc = 1;
+  while (pc * 2 <= max_pc && ncols / (pc * 2) >= 2 * 152) pc *= 2;
+  return pc;
+}
+
+void add_panels(const std::vector<Col> &cols, int c0, int c1, const std::vector<int> &fac, int pc,
+                std::vector<Panel> &panels) {
+  int i = c0;
+  while (i < c1) {
+    const int f = fac[cols[i].sub];
+    int j = i;
+    while (j < c1 && j - i < pc && fac[cols[j].sub] == f) ++j;
+    panels.push_back(Panel{i, j - i, f, 0});
+    i = j;
+  }
+}
+
+int max_pc_for(const dds_ctx *ctx, size_t elem) {
+  // shared memory of the substitution panel: Mb * pc * elem bytes (<= 96 KB)
+  int pc = 8;
+  while (pc > 1 && (size_t)ctx->g.Mb * pc * elem > 96 * 1024) pc /= 2;
+  return pc;
+}
+
+CallPlan *get_plan(dds_ctx *ctx, int nrhs) {
+  auto it = ctx->plans.find(nrhs);
+  if (it != ctx->plans.end()) return it->second.get();
+  auto cp = std::make_unique<CallPlan>();
+  cp->nrhs = nrhs;
+  const Geom &g = ctx->g;
+  const size_t elem = ctx->precision == DDS_MIXED ? sizeof(float2) : sizeof(double2);
+  const int maxpc = max_pc_for(ctx, elem);
+  std::vector<Col> cols;
+  std::vector<Panel> panels;
+  // every (sub, rhs), subs grouped by factor
+  std::vector<int> order(g.nsub);
+  for (int s = 0; s < g.nsub; ++s) order[s] = s;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return ctx->fac_of_sub[a] < ctx->fac_of_sub[b]; });
+  auto emit = [&](const std::vector<int> &subs, int pc_cap, bool trace) {
+    StepPlan sp;
+    sp.col_off = (int)cols.size();
+    for (size_t i = 0; i < subs.size(); ++i)
+      for (int r = 0; r < nrhs; ++r)
+        cols.push_back(Col{subs[i], r, (int)(cols.size() - sp.col_off), 0});
+    sp.ncols = (int)cols.size() - sp.col_off;
+    if (trace) {  // trace-step panels: rows are split over CTAs too, so narrower panels suffice
+      int pc = 1;
+      while (pc * 2 <= pc_cap && sp.ncols / (pc * 2) >= 16) pc *= 2;
+      sp.pc = pc;
+    } else {
+      sp.pc = pick_pc(sp.ncols, pc_cap);
+    }
+    sp.pan_off = (int)panels.size();
+    add_panels(cols, sp.col_off, sp.col_off + sp.ncols, ctx->fac_of_sub, sp.pc, panels);
+    sp.npanels = (int)panels.size() - sp.pan_off;
+    return sp;
+  };
+  cp->all = emit(order, maxpc, false);
+  for (int dir = 0; dir < ctx->ndirs; ++dir)
+    for (int s = 0; s < ctx->nsteps; ++s) cp->steps.push_back(emit(ctx->step_subs[dir][s], maxpc, false));
+  const int tmax = (ctx->g.T * 4 * (int)elem <= 96 * 1024) ? 4 : 2;
+  for (int dir = 0; dir < ctx->ndirs; ++dir)
+    for (int s = 0; s < ctx->nsteps; ++s) cp->tsteps.push_back(emit(ctx->step_subs[dir][s], tmax, true));
+  if (upload(cp->cols, cols, ctx->stream) != cudaSuccess) return nullptr;
+  if (upload(cp->panels, panels, ctx->stream) != cudaSuccess) return nullptr;
+  CallPlan *raw = cp.get();
+  ctx->plans[nrhs] = std::move(cp);
+  return raw;
+}
+
+dds_status set_route(dds_ctx *ctx, int rounds) {
+  if (ctx->route_rounds == rounds) return DDS_OK;
+  const std::vector<int> r = build_route(ctx->g.dim, rounds);
+  CK(upload(ctx->route_dev, r, ctx->stream));
+  ctx->route_rounds = rounds;
+  return DDS_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// one DDM application (Algorithm 2.1 / 4.1): b (J-scaled, device, nrhs fields) -> u (device)
+// ------------------------------------------------------------------------------------------
+template <typename R>
+dds_status run_ddm(dds_ctx *ctx, const double2 *b, int nrhs, double2 *u, int rounds) {
+  using C = typename Cx<R>::T;
+  const Geom &g = ctx->g;
+  cudaStream_t st = ctx->stream;
+  dds_status rs = set_route(ctx, rounds);
+  if (rs != DDS_OK) return rs;
+  CallPlan *cp = get_plan(ctx, nrhs);
+  if (!cp) { ctx->err = "failed to upload launch lists"; return DDS_ENOMEM; }
+  const C *sinv = ctx->precision == DDS_MIXED ? (const C *)ctx->sinv32.p : (const C *)ctx->sinv64.p;
+  const C *cpl = ctx->precision == DDS_MIXED ? (const C *)ctx->cpl32.p : (const C *)ctx->cpl64.p;
+  const C *gmap = ctx->precision == DDS_MIXED ? (const C *)ctx->gmap32.p : (const C *)ctx->gmap64.p;
+  const int L = ctx->ndirs * rounds;
+  const long long slot = (long long)nrhs * g.nsub * g.T;
+  const bool trace_plan = ctx->plan == DDS_PLAN_TRACE;
+  const long long work_cols = trace_plan ? (long long)g.nsub * nrhs : [&] {
+    long long mx = 0;
+    for (auto &sp : cp->steps) mx = std::max<long long>(mx, sp.ncols);
+    return mx;
+  }();
+  CK(ctx->work.ensure(work_cols * g.Nloc * sizeof(C)));
+  CK(ctx->gtr.ensure(L * slot * sizeof(C)));
+  CK(cudaMemsetAsync(ctx->gtr.p, 0, L * slot * sizeof(C), st));
+  C *work = ctx->work.as<C>();
+  C *gtr = ctx->gtr.as<C>();
+  const Col *cols = cp->cols.as<Col>();
+  const Panel *pans = cp->panels.as<Panel>();
+  const int *route = ctx->route_dev.as<int>();
+  if (!trace_plan) {
+    CK(cudaMemsetAsync(u, 0, (size_t)nrhs * g.Nglob * sizeof(double2), st));
+    for (int l = 0; l < L; ++l) {
+      const int dir = l % ctx->ndirs;
+      for (int s = 0; s < ctx->nsteps; ++s) {
+        const StepPlan &sp = cp->steps[dir * ctx->nsteps + s];
+        if (sp.ncols == 0) continue;
+        LAUNCHK(DDS_K_ASSEMBLE, launch_assemble<R>(st, g, ctx->tb, sp.ncols, cols + sp.col_off, work, b, nullptr,
+                                  l == 0, gtr + l * slot, (long long)g.nsub * g.T, g.T));
+        LAUNCHK(DDS_K_SUBST, launch_subst<R>(st, g, sp.npanels, pans + sp.pan_off, cols, sinv, cpl, work, sp.pc));
+        LAUNCHK(DDS_K_EXTRACT, launch_extract<R>(st, g, sp.ncols, cols + sp.col_off, work, u, 1, nullptr, gtr,
+                                 route, l, nrhs));
+      }
+    }
+  } else {
+    CK(ctx->acc.ensure(slot * sizeof(C)));
+    CK(ctx->rawf.ensure(slot * sizeof(C)));
+    CK(cudaMemsetAsync(ctx->acc.p, 0, slot * sizeof(C), st));
+    C *acc = ctx->acc.as<C>();
+    C *rawf = ctx->rawf.as<C>();
+    const StepPlan &all = cp->all;
+    // own sources: x_f = A_R^{-1} b_own; keep its raw trace lines
+    LAUNCHK(DDS_K_ASSEMBLE, launch_assemble<R>(st, g, ctx->tb, all.ncols, cols + all.col_off, work, b, nullptr, 1,
+                              (const C *)nullptr, 0, 0));
+    LAUNCHK(DDS_K_SUBST, launch_subst<R>(st, g, all.npanels, pans + all.pan_off, cols, sinv, cpl, work, all.pc));
+    LAUNCHK(DDS_K_EXTRACT, launch_extract<R>(st, g, all.ncols, cols + all.col_off, work, u, 0, rawf,
+                             (C *)nullptr, route, 0, nrhs));
+    // sweeps: per step, traces of the whole step set through the trace map
+    for (int l = 0; l < L; ++l) {
+      const int dir = l % ctx->ndirs;
+      for (int s = 0; s < ctx->nsteps; ++s) {
+        const StepPlan &sp = cp->tsteps[dir * ctx->nsteps + s];
+        if (sp.ncols == 0) continue;
+        LAUNCHK(DDS_K_TRACE_STEP, launch_trace_step<R>(st, g, sp.npanels, pans + sp.pan_off, cols, gmap, gtr, acc,
+                                    l == 0 ? rawf : nullptr, route, l, nrhs, sp.pc));
+      }
+    }
+    // own nodes: u = A_R^{-1}(b_own + potentials of all traces received in every sweep)
+    LAUNCHK(DDS_K_ASSEMBLE, launch_assemble<R>(st, g, ctx->tb, all.ncols, cols + all.col_off, work, b, nullptr, 1,
+                              acc, (long long)g.nsub * g.T, g.T));
+    LAUNCHK(DDS_K_SUBST, launch_subst<R>(st, g, all.npanels, pans + all.pan_off, cols, sinv, cpl, work, all.pc));
+    LAUNCHK(DDS_K_EXTRACT, launch_extract<R>(st, g, all.ncols, cols + all.col_off, work, u, 2, (C *)nullptr,
+                             (C *)nullptr, route, 0, nrhs));
+  }
+  return DDS_OK;
+}
+
+dds_status ddm(dds_ctx *ctx, const double2 *b, int nrhs, double2 *u, int rounds) {
+  dds_status r = ctx->precision == DDS_MIXED ? run_ddm<float>(ctx, b, nrhs, u, rounds)
+                                             : run_ddm<double>(ctx, b, nrhs, u, rounds);
+  if (r == DDS_OK && ctx->ev_used > 4096) CK(prof_fold(ctx));
+  return r;
+}
+
+// ------------------------------------------------------------------------------------------
+// set-up
+// ------------------------------------------------------------------------------------------
+dds_status validate(const dds_problem *p, std::string &err) {
+  if (!p) { err = "null problem"; return DDS_EINVAL; }
+  if (p->dim != 2 && p->dim != 3) { err = "dim must be 2 or 3"; return DDS_EINVAL; }
+  for (int a = 0; a < p->dim; ++a) {
+    if (p->n[a] <= 0 || p->parts[a] <= 0 || p->n[a] % p->parts[a]) {
+      err = "n[a] must be a positive multiple of parts[a]";
+      return DDS_EINVAL;
+    }
+  }
+  if (!p->c) { err = "null wave speed"; return DDS_EINVAL; }
+  if (p->pml_cells < 1 || p->halo < 0 || p->h <= 0 || p->omega <= 0 || p->pml_power < 1) {
+    err = "invalid PML / grid parameters";
+    return DDS_EINVAL;
+  }
+  if (p->precision != DDS_FP64 && p->precision != DDS_MIXED) { err = "bad precision"; return DDS_EINVAL; }
+  if (p->plan < 0 || p->plan > 2) { err = "bad plan"; return DDS_EINVAL; }
+  return DDS_OK;
+}
+
+template <typename R>
+dds_status build_trace_map(dds_ctx *ctx) {
+  // column k of the map = raw trace lines of A_R^{-1} (commutator source of unit trace k),
+  // computed in FP64 for every distinct factor; then the back-trace correction is folded in.
+  const Geom &g = ctx->g;
+  cudaStream_t st = ctx->stream;
+  const long long TT = (long long)g.T * g.T;
+  CK(ctx->gmap64.ensure(ctx->nfac * TT * sizeof(double2)));
+  const int chunk = std::min(g.T, 1024);
+  CK(ctx->work.ensure((long long)chunk * g.Nloc * sizeof(double2)));
+  std::vector<Col> cols(chunk);
+  for (int q = 0; q < chunk; ++q) cols[q] = Col{0, 0, q, 0};
+  DBuf dcols, dpans;
+  for (int f = 0; f < ctx->nfac; ++f) {
+    int sub0 = 0;
+    while (ctx->fac_of_sub[sub0] != f) ++sub0;
+    for (int q = 0; q < chunk; ++q) cols[q].sub = sub0;
+    CK(upload(dcols, cols, st));
+    for (int k0 = 0; k0 < g.T; k0 += chunk) {
+      const int nk = std::min(chunk, g.T - k0);
+      std::vector<Panel> pans;
+      const int pc = 4;
+      for (int i = 0; i < nk; i += pc) pans.push_back(Panel{i, std::min(pc, nk - i), f, 0});
+      CK(upload(dpans, pans, st));
+      double2 *work = ctx->work.as<double2>();
+      LAUNCH(launch_unit_traces<double>(st, g, ctx->tb, k0, nk, work));
+      LAUNCHK(DDS_K_SUBST, launch_subst<double>(st, g, (int)pans.size(), dpans.as<Panel>(), dcols.as<Col>(),
+                                  ctx->sinv64.as<double2>(), ctx->cpl64.as<double2>(), work, pc));
+      LAUNCH(launch_raw_lines<double>(st, g, nk, work, ctx->gmap64.as<double2>() + f * TT, k0));
+      CK(cudaStreamSynchronize(st));
+    }
+    LAUNCH(launch_gmap_backtrace(st, g, ctx->gmap64.as<double2>() + f * TT));
+  }
+  if (ctx->precision == DDS_MIXED) {
+    CK(ctx->gmap32.ensure(ctx->nfac * TT * sizeof(float2)));
+    LAUNCH(launch_convert_c64_c32(st, ctx->gmap64.as<double2>(), ctx->gmap32.as<float2>(),
+                                  ctx->nfac * TT));
+  }
+  CK(cudaStreamSynchronize(st));
+  return DDS_OK;
+}
+
+dds_status setup_impl(dds_ctx *ctx, const dds_problem *p) {
+  const auto t0 = std::chrono::steady_clock::now();
+  Geom &g = ctx->g;
+  g.dim = p->dim;
+  ctx->precision = p->precision;
+  ctx->plan = p->plan == DDS_PLAN_AUTO ? (p->dim == 2 ? DDS_PLAN_TRACE : DDS_PLAN_DIRECT) : p->plan;
+  ctx->h = p->h;
+  ctx->omega = p->omega;
+  ctx->S = p->pml_strength;
+  ctx->P = p->pml_cells;
+  ctx->power = p->pml_power;
+  ctx->H = p->halo;
+  g.E = p->halo + p->pml_cells;
+  for (int a = 0; a < 3; ++a) {
+    const bool on = a < p->dim;
+    g.n[a] = on ? p->n[a] : 1;
+    g.parts[a] = on ? p->parts[a] : 1;
+    g.m[a] = g.n[a] / g.parts[a];
+    g.M[a] = on ? g.m[a] + 2 * g.E : 1;
+    g.G[a] = on ? g.n[a] + 2 * g.E : 1;
+  }
+  g.nsub = g.parts[0] * g.parts[1] * g.parts[2];
+  g.Nloc = (long long)g.M[0] * g.M[1] * g.M[2];
+  g.Nglob = (long long)g.G[0] * g.G[1] * g.G[2];
+  g.Ml = g.M[p->dim - 1];
+  g.Mb = (int)(g.Nloc / g.Ml);
+  g.nsides = 2 * p->dim;
+  g.T = 0;
+  for (int d = 0; d < 6; ++d) {
+    g.Lt[d] = 0;
+    g.toff[d] = g.T;
+    if (d >= g.nsides) continue;
+    int lt = 1;
+    for (int b = 0; b < p->dim; ++b)
+      if (b != (d >> 1)) lt *= g.M[b];
+    g.Lt[d] = lt;
+    g.T += 2 * lt;
+  }
+  if (ctx->plan == DDS_PLAN_TRACE && (size_t)g.T * sizeof(double2) > 200 * 1024) {
+    ctx->err = "trace vectors too long for the trace-operator plan (T = " + std::to_string(g.T) + ")";
+    return DDS_EINVAL;
+  }
+  const size_t smem_need = (size_t)g.Mb * g.Mb * 16 + g.Mb * 20;
+  if (smem_need > 227 * 1024) {
+    ctx->err = "line block too large for the in-shared-memory Schur factorisation (Mb = " +
+               std::to_string(g.Mb) + ")";
+    return DDS_EINVAL;
+  }
+  const int dim = p->dim;
+  const double h = p->h;
+  const double ih2 = 1.0 / (h * h);
+  // ---- PML stretching: local (translation invariant) and global alphas
+  std::vector<cd> lan[3], lah[3], gan[3], gah[3];
+  for (int a = 0; a < 3; ++a) {
+    if (a < dim) {
+      axis_alphas(g.M[a], -g.E + 0.5, g.m[a], p->halo, p->pml_cells, p->pml_strength,
+                  p->pml_power, lan[a], lah[a]);
+      axis_alphas(g.G[a], -g.E + 0.5, g.n[a], p->halo, p->pml_cells, p->pml_strength,
+                  p->pml_power, gan[a], gah[a]);
+    } else {
+      lan[a].assign(1, cd(1, 0));
+      lah[a].assign(2, cd(1, 0));
+      gan[a].assign(1, cd(1, 0));
+      gah[a].assign(2, cd(1, 0));
+    }
+  }
+  // ---- wave numbers: global (nearest interior node) and per subdomain (Eq. 2.8)
+  const long long nint = (long long)g.n[0] * g.n[1] * g.n[2];
+  std::vector<double> cint(p->c, p->c + nint);
+  for (double v : cint)
+    if (!(v > 0)) { ctx->err = "wave speed must be positive"; return DDS_EINVAL; }
+  auto clampi = [](int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); };
+  std::vector<double> k2g(g.Nglob);
+  for (int p2 = 0; p2 < g.G[2]; ++p2)
+    for (int p1 = 0; p1 < g.G[1]; ++p1)
+      for (int p0 = 0; p0 < g.G[0]; ++p0) {
+        const int i0 = clampi(p0 - g.E, 0, g.n[0] - 1);
+        const int i1 = clampi(p1 - g.E, 0, g.n[1] - 1);
+        const int i2 = dim == 3 ? clampi(p2 - g.E, 0, g.n[2] - 1) : 0;
+        const double kk = p->omega / cint[i0 + (long long)g.n[0] * (i1 + (long long)g.n[1] * i2)];
+        k2g[p0 + (long long)g.G[0] * (p1 + (long long)g.G[1] * p2)] = kk * kk;
+      }
+  // per-subdomain kappa^2 on the extended grid; deduplicate identical fields
+  std::vector<std::vector<double>> fac_k2;
+  ctx->fac_of_sub.assign(g.nsub, -1);
+  for (int s = 0; s < g.nsub; ++s) {
+    int k[3];
+    sub_index(g, s, k);
+    std::vector<double> k2(g.Nloc);
+    for (int l2 = 0; l2 < g.M[2]; ++l2)
+      for (int l1 = 0; l1 < g.M[1]; ++l1)
+        for (int l0 = 0; l0 < g.M[0]; ++l0) {
+          const int i0 = clampi(k[0] * g.m[0] + l0 - g.E, k[0] * g.m[0], (k[0] + 1) * g.m[0] - 1);
+          const int i1 = clampi(k[1] * g.m[1] + l1 - g.E, k[1] * g.m[1], (k[1] + 1) * g.m[1] - 1);
+          const int i2 = dim == 3 ? clampi(k[2] * g.m[2] + l2 - g.E, k[2] * g.m[2], (k[2] + 1) * g.m[2] - 1) : 0;
+          const double kk = p->omega / cint[i0 + (long long)g.n[0] * (i1 + (long long)g.n[1] * i2)];
+          k2[l0 + (long long)g.M[0] * (l1 + (long long)g.M[1] * l2)] = kk * kk;
+        }
+    int found = -1;
+    for (size_t f = 0; f < fac_k2.size(); ++f)
+      if (fac_k2[f] == k2) { found = (int)f; break; }
+    if (found < 0) {
+      found = (int)fac_k2.size();
+      fac_k2.push_back(std::move(k2));
+    }
+    ctx->fac_of_sub[s] = found;
+  }
+  ctx->nfac = (int)fac_k2.size();
+  // ---- line-block coefficients of every distinct operator
+  const int Mb = g.Mb, Ml = g.Ml, la = dim - 1;
+  const long long per = (long long)Ml * Mb;
+  std::vector<double2> dg(ctx->nfac * per), offx(ctx->nfac * per), offy, cpl(ctx->nfac * per);
+  if (dim == 3) offy.resize(ctx->nfac * per);
+  auto tprod = [&](int a, const int i[3]) {  // prod_{b != a} alpha_b / h^2
+    cd t(ih2, 0.0);
+    for (int b = 0; b < dim; ++b)
+      if (b != a) t *= lan[b][i[b]];
+    return t;
+  };
+  for (int f = 0; f < ctx->nfac; ++f) {
+    for (long long q = 0; q < g.Nloc; ++q) {
+      int i[3] = {(int)(q % g.M[0]), (int)((q / g.M[0]) % g.M[1]), (int)(q / ((long long)g.M[0] * g.M[1]))};
+      cd J(1.0, 0.0);
+      for (int a = 0; a < dim; ++a) J *= lan[a][i[a]];
+      cd diag = fac_k2[f][q] * J;
+      for (int a = 0; a < dim; ++a) diag -= tprod(a, i) * (1.0 / lah[a][i[a]] + 1.0 / lah[a][i[a] + 1]);
+      const int j = i[la];
+      const int r = (int)(q - (long long)j * Mb);
+      const long long o = f * per + (long long)j * Mb + r;
+      dg[o] = make_double2(diag.real(), diag.imag());
+      cd ox = (i[0] + 1 < g.M[0]) ? tprod(0, i) / lah[0][i[0] + 1] : cd(0, 0);
+      offx[o] = make_double2(ox.real(), ox.imag());
+      if (dim == 3) {
+        cd oy = (i[1] + 1 < g.M[1]) ? tprod(1, i) / lah[1][i[1] + 1] : cd(0, 0);
+        offy[o] = make_double2(oy.real(), oy.imag());
+      }
+      cd cp = (i[la] + 1 < g.M[la]) ? tprod(la, i) / lah[la][i[la] + 1] : cd(0, 0);
+      cpl[o] = make_double2(cp.real(), cp.imag());
+    }
+  }
+  // ---- commutator couplings per side: prod_{tangential b} alpha_b / h^2
+  std::vector<double2> coef(g.T / 2);
+  std::vector<float2> coef32(g.T / 2);
+  for (int d = 0; d < g.nsides; ++d) {
+    const int a = d >> 1;
+    for (int t = 0; t < g.Lt[d]; ++t) {
+      int tt = t;
+      cd c(ih2, 0.0);
+      for (int b = 0; b < dim; ++b) {
+        if (b == a) continue;
+        c *= lan[b][tt % g.M[b]];
+        tt /= g.M[b];
+      }
+      coef[g.toff[d] / 2 + t] = make_double2(c.real(), c.imag());
+      coef32[g.toff[d] / 2 + t] = make_float2((float)c.real(), (float)c.imag());
+    }
+  }
+  // ---- step schedules (Eq. 2.10-2.11 / 4.3-4.4), subdomains grouped by factor
+  const auto dirs = sweep_dirs(dim);
+  ctx->ndirs = (int)dirs.size();
+  ctx->nsteps = 1;  // N1 + N2 - 1 (2D), N1 + N2 + N3 - 2 (3D)
+  for (int a = 0; a < dim; ++a) ctx->nsteps += g.parts[a] - 1;
+  ctx->step_subs.assign(ctx->ndirs, std::vector<std::vector<int>>(ctx->nsteps));
+  for (int di = 0; di < ctx->ndirs; ++di) {
+    for (int s = 0; s < g.nsub; ++s) {
+      int k[3];
+      sub_index(g, s, k);
+      int step = 0;
+      for (int a = 0; a < dim; ++a) step += dirs[di][a] == 1 ? k[a] : g.parts[a] - 1 - k[a];
+      ctx->step_subs[di][step].push_back(s);
+    }
+    for (auto &v : ctx->step_subs[di])
+      std::stable_sort(v.begin(), v.end(), [&](int a, int b) { return ctx->fac_of_sub[a] < ctx->fac_of_sub[b]; });
+  }
+  // ---- upload tables
+  cudaStream_t st = ctx->stream;
+  CK(upload(ctx->coef64, coef, st));
+  CK(upload(ctx->coef32, coef32, st));
+  CK(upload(ctx->k2glob, k2g, st));
+  for (int a = 0; a < 3; ++a) {
+    std::vector<double2> an(gan[a].size()), iah(gah[a].size());
+    for (size_t q = 0; q < an.size(); ++q) an[q] = make_double2(gan[a][q].real(), gan[a][q].imag());
+    for (size_t q = 0; q < iah.size(); ++q) {
+      const cd v = 1.0 / gah[a][q];
+      iah[q] = make_double2(v.real(), v.imag());
+    }
+    CK(upload(ctx->an_glob[a], an, st));
+    CK(upload(ctx->iah_glob[a], iah, st));
+    ctx->tb.an_glob64[a] = ctx->an_glob[a].as<double2>();
+    ctx->tb.iah_glob64[a] = ctx->iah_glob[a].as<double2>();
+  }
+  ctx->tb.coef64 = ctx->coef64.as<double2>();
+  ctx->tb.coef32 = ctx->coef32.as<float2>();
+  ctx->tb.k2_glob = ctx->k2glob.as<double>();
+  ctx->tb.inv_h2 = ih2;
+  // ---- factor (FP64 Schur chain on the GPU)
+  DBuf ddg, doffx, doffy, dcpl;
+  CK(upload(ddg, dg, st));
+  CK(upload(doffx, offx, st));
+  if (dim == 3) CK(upload(doffy, offy, st));
+  CK(upload(dcpl, cpl, st));
+  const long long sinv_elems = (long long)ctx->nfac * Ml * (long long)Mb * Mb;
+  CK(ctx->sinv64.ensure(sinv_elems * sizeof(double2)));
+  CK(ctx->sinv32.ensure(sinv_elems * sizeof(float2)));
+  CK(ctx->status.ensure(sizeof(int)));
+  CK(cudaMemsetAsync(ctx->status.p, 0, sizeof(int), st));
+  LAUNCH(launch_factor(st, ctx->nfac, Mb, Ml, g.M[0], ddg.as<double2>(), doffx.as<double2>(),
+                       dim == 3 ? doffy.as<double2>() : nullptr, dcpl.as<double2>(),
+                       ctx->sinv64.as<double2>(), ctx->sinv32.as<float2>(), ctx->status.as<int>()));
+  int status = 0;
+  CK(cudaMemcpyAsync(&status, ctx->status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (status != 0) { ctx->err = "singular pivot in the Schur-complement factorisation"; return DDS_EINVAL; }
+  CK(ctx->cpl64.ensure(ctx->nfac * per * sizeof(double2)));
+  CK(cudaMemcpyAsync(ctx->cpl64.p, dcpl.p, ctx->nfac * per * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+  CK(ctx->cpl32.ensure(ctx->nfac * per * sizeof(float2)));
+  LAUNCH(launch_convert_c64_c32(st, ctx->cpl64.as<double2>(), ctx->cpl32.as<float2>(), ctx->nfac * per));
+  CK(cudaStreamSynchronize(st));
+  if (ctx->plan == DDS_PLAN_TRACE) {
+    dds_status r = build_trace_map<double>(ctx);
+    if (r != DDS_OK) return r;
+  }
+  if (ctx->precision == DDS_MIXED) ctx->sinv64.release(), ctx->gmap64.release();
+  ctx->setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return DDS_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// host-pointer staging
+// ------------------------------------------------------------------------------------------
+struct Staged {
+  const double2 *in = nullptr;
+  double2 *out = nullptr;
+  bool in_host = false, out_host = false;
+};
+
+dds_status stage_in(dds_ctx *ctx, const void *ptr, size_t bytes, const double2 **dev) {
+  if (is_device_ptr(ptr)) { *dev = (const double2 *)ptr; return DDS_OK; }
+  CK(ctx->stage_in.ensure(bytes));
+  CK(cudaMemcpyAsync(ctx->stage_in.p, ptr, bytes, cudaMemcpyHostToDevice, ctx->stream));
+  *dev = ctx->stage_in.as<double2>();
+  return DDS_OK;
+}
+
+dds_status stage_out_ptr(dds_ctx *ctx, void *ptr, size_t bytes, double2 **dev, bool *host) {
+  if (is_device_ptr(ptr)) { *dev = (double2 *)ptr; *host = false; return DDS_OK; }
+  CK(ctx->stage_out.ensure(bytes));
+  *dev = ctx->stage_out.as<double2>();
+  *host = true;
+  return DDS_OK;
+}
+
+dds_status finish_out(dds_ctx *ctx, void *ptr, size_t bytes, bool host) {
+  if (host) CK(cudaMemcpyAsync(ptr, ctx->stage_out.p, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return DDS_OK;
+}
+
+struct Busy {
+  dds_ctx *c;
+  bool ok;
+  explicit Busy(dds_ctx *cc) : c(cc), ok(cc->mu.try_lock()) {}
+  ~Busy() { if (ok) c->mu.unlock(); }
+};
+
+// ------------------------------------------------------------------------------------------
+// FGMRES (right preconditioned, x0 = 0, classical Gram-Schmidt twice, Givens rotations)
+// ------------------------------------------------------------------------------------------
+dds_status fgmres(dds_ctx *ctx, const double2 *b, int nrhs, double2 *x, double tol, int maxit,
+                  int rounds, int *iters, std::vector<double> &relres) {
+  const Geom &g = ctx->g;
+  cudaStream_t st = ctx->stream;
+  const long long N = g.Nglob;
+  const size_t vbytes = (size_t)nrhs * N * sizeof(double2);
+  auto vec = [&](std::vector<std::unique_ptr<DBuf>> &pool, int i) -> double2 * {
+    while ((int)pool.size() <= i) pool.push_back(std::make_unique<DBuf>());
+    if (pool[i]->ensure(vbytes) != cudaSuccess) return nullptr;
+    return pool[i]->as<double2>();
+  };
+  const int nblk = 64;
+  CK(ctx->dots_part.ensure((size_t)nrhs * (maxit + 1) * nblk * sizeof(double2)));
+  CK(ctx->dots_out.ensure((size_t)nrhs * (maxit + 1) * sizeof(double2)));
+  CK(ctx->coefbuf.ensure((size_t)nrhs * (maxit + 1) * sizeof(double2)));
+  CK(ctx->scalebuf.ensure((size_t)nrhs * sizeof(double)));
+  auto dots = [&](const double2 *V0, int nv, const double2 *w, std::vector<cd> &out) -> dds_status {
+    LAUNCHK(DDS_K_KRYLOV, launch_dots(st, N, nrhs, nv, V0, (long long)nrhs * N, N, w, N, ctx->dots_part.as<double2>(),
+                       ctx->dots_out.as<double2>(), nblk));
+    out.resize((size_t)nrhs * nv);
+    CK(cudaMemcpyAsync(out.data(), ctx->dots_out.p, out.size() * sizeof(double2), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return DDS_OK;
+  };
+  // the V vectors are separate buffers: gather pointers by copying into contiguous calls
+  // (V_i lives in Vb[i]; launch_dots/sub_combination take a base and a stride, so each basis
+  // vector is processed with nv = 1 calls when buffers are not contiguous)
+  std::vector<cd> beta_c;
+  double2 *V0 = vec(ctx->Vb, 0);
+  if (!V0) { ctx->err = "out of device memory for the Krylov basis"; return DDS_ENOMEM; }
+  if (dots(b, 1, b, beta_c) != DDS_OK) return DDS_ECUDA;
+  std::vector<double> beta(nrhs), invs(nrhs);
+  for (int r = 0; r < nrhs; ++r) {
+    beta[r] = std::sqrt(std::max(beta_c[r].real(), 0.0));
+    invs[r] = beta[r] > 0 ? 1.0 / beta[r] : 0.0;
+  }
+  CK(cudaMemcpyAsync(ctx->scalebuf.p, invs.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
+  LAUNCHK(DDS_K_KRYLOV, launch_scale_vec(st, N, nrhs, b, ctx->scalebuf.as<double>(), V0));
+  const int m = maxit;
+  std::vector<cd> H((size_t)nrhs * (m + 1) * m, cd(0, 0)), cs((size_t)nrhs * m), sn((size_t)nrhs * m),
+      gg((size_t)nrhs * (m + 1), cd(0, 0));
+  std::vector<int> kused(nrhs, 0);
+  std::vector<char> done(nrhs, 0);
+  for (int r = 0; r < nrhs; ++r) {
+    gg[(size_t)r * (m + 1)] = beta[r];
+    if (beta[r] == 0) done[r] = 1;
+  }
+  auto Hat = [&](int r, int i, int j) -> cd & { return H[((size_t)r * (m + 1) + i) * m + j]; };
+  int k = 0;
+  std::vector<cd> hc, tmp;
+  for (int j = 0; j < m; ++j) {
+    double2 *Vj = vec(ctx->Vb, j), *Zj = vec(ctx->Zb, j), *W = vec(ctx->Vb, j + 1);
+    if (!Vj || !Zj || !W) { ctx->err = "out of device memory for the Krylov basis"; return DDS_ENOMEM; }
+    dds_status rs = ddm(ctx, Vj, nrhs, Zj, rounds);
+    if (rs != DDS_OK) return rs;
+    LAUNCHK(DDS_K_KRYLOV, launch_apply_A(st, g, ctx->tb, nrhs, Zj, W, 0));
+    std::vector<cd> hsum((size_t)nrhs * (j + 1), cd(0, 0));
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int i = 0; i <= j; ++i) {
+        if (dots(ctx->Vb[i]->as<double2>(), 1, W, hc) != DDS_OK) return DDS_ECUDA;
+        std::vector<double2> cf(nrhs);
+        for (int r = 0; r < nrhs; ++r) {
+          hsum[(size_t)r * (j + 1) + i] += hc[r];
+          cf[r] = make_double2(hc[r].real(), hc[r].imag());
+        }
+        CK(cudaMemcpyAsync(ctx->coefbuf.p, cf.data(), nrhs * sizeof(double2), cudaMemcpyHostToDevice, st));
+        LAUNCHK(DDS_K_KRYLOV, launch_sub_combination(st, N, nrhs, 1, ctx->Vb[i]->as<double2>(), 0, N,
+                                      ctx->coefbuf.as<double2>(), W, N, -1.0));
+      }
+    }
+    if (dots(W, 1, W, hc) != DDS_OK) return DDS_ECUDA;
+    for (int r = 0; r < nrhs; ++r) {
+      const double hn = std::sqrt(std::max(hc[r].real(), 0.0));
+      invs[r] = hn > 0 ? 1.0 / hn : 0.0;
+      for (int i = 0; i <= j; ++i) Hat(r, i, j) = hsum[(size_t)r * (j + 1) + i];
+      Hat(r, j + 1, j) = hn;
+    }
+    CK(cudaMemcpyAsync(ctx->scalebuf.p, invs.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
+    LAUNCHK(DDS_K_KRYLOV, launch_scale_vec(st, N, nrhs, W, ctx->scalebuf.as<double>(), W));
+    k = j + 1;
+    bool all = true;
+    for (int r = 0; r < nrhs; ++r) {
+      if (done[r]) continue;
+      for (int i = 0; i < j; ++i) {  // previous rotations
+        const cd a = Hat(r, i, j), bb = Hat(r, i + 1, j);
+        const cd c = cs[(size_t)r * m + i], s = sn[(size_t)r * m + i];
+        Hat(r, i, j) = c * a + s * bb;
+        Hat(r, i + 1, j) = -std::conj(s) * a + std::conj(c) * bb;
+      }
+      const cd a = Hat(r, j, j), bb = Hat(r, j + 1, j);
+      const double rr = std::hypot(std::abs(a), std::abs(bb));
+      cd c(1, 0), s(0, 0);
+      if (rr > 0) { c = std::conj(a / rr); s = std::conj(bb / rr); }
+      cs[(size_t)r * m + j] = c;
+      sn[(size_t)r * m + j] = s;
+      Hat(r, j, j) = c * a + s * bb;
+      Hat(r, j + 1, j) = 0.0;
+      const cd gj = gg[(size_t)r * (m + 1) + j];
+      gg[(size_t)r * (m + 1) + j + 1] = -std::conj(s) * gj;
+      gg[(size_t)r * (m + 1) + j] = c * gj;
+      kused[r] = j + 1;
+      const double res = std::abs(gg[(size_t)r * (m + 1) + j + 1]) / beta[r];
+      if (res < tol || invs[r] == 0.0) done[r] = 1;
+      else all = false;
+    }
+    if (all) break;
+  }
+  *iters = k;
+  // x = sum_i Z_i y_i per RHS
+  CK(cudaMemsetAsync(x, 0, vbytes, st));
+  std::vector<std::vector<cd>> y(nrhs);
+  for (int r = 0; r < nrhs; ++r) {
+    const int kr = kused[r];
+    y[r].assign(kr, cd(0, 0));
+    for (int i = kr - 1; i >= 0; --i) {
+      cd s = gg[(size_t)r * (m + 1) + i];
+      for (int q = i + 1; q < kr; ++q) s -= Hat(r, i, q) * y[r][q];
+      y[r][i] = s / Hat(r, i, i);
+    }
+  }
+  for (int i = 0; i < k; ++i) {
+    std::vector<double2> cf(nrhs);
+    for (int r = 0; r < nrhs; ++r) {
+      const cd v = i < kused[r] ? y[r][i] : cd(0, 0);
+      cf[r] = make_double2(v.real(), v.imag());
+    }
+    CK(cudaMemcpyAsync(ctx->coefbuf.p, cf.data(), nrhs * sizeof(double2), cudaMemcpyHostToDevice, st));
+    LAUNCHK(DDS_K_KRYLOV, launch_sub_combination(st, N, nrhs, 1, ctx->Zb[i]->as<double2>(), 0, N,
+                                  ctx->coefbuf.as<double2>(), x, N, 1.0));
+  }
+  // true residual
+  double2 *Rv = vec(ctx->Vb, 0);
+  LAUNCHK(DDS_K_KRYLOV, launch_apply_A(st, g, ctx->tb, nrhs, x, Rv, 0));
+  std::vector<double2> mone(nrhs, make_double2(-1.0, 0.0));
+  CK(cudaMemcpyAsync(ctx->coefbuf.p, mone.data(), nrhs * sizeof(double2), cudaMemcpyHostToDevice, st));
+  // Rv = A x - b  ->  Rv += (-1) * b
+  LAUNCHK(DDS_K_KRYLOV, launch_sub_combination(st, N, nrhs, 1, b, 0, N, ctx->coefbuf.as<double2>(), Rv, N, 1.0));
+  if (dots(Rv, 1, Rv, hc) != DDS_OK) return DDS_ECUDA;
+  relres.assign(nrhs, 0.0);
+  bool ok = true;
+  for (int r = 0; r < nrhs; ++r) {
+    relres[r] = beta[r] > 0 ? std::sqrt(std::max(hc[r].real(), 0.0)) / beta[r] : 0.0;
+    if (!(relres[r] < tol)) ok = false;
+  }
+  return ok ? DDS_OK : DDS_ENOCONV;
+}
+
+}  // namespace
+
+// ============================================================================================
+// C ABI
+// ============================================================================================
+extern "C" {
+
+dds_status dds_setup(const dds_problem *prob, dds_ctx **out) {
+  if (!out) return DDS_EINVAL;
+  std::unique_ptr<dds_ctx> ctx(new (std::nothrow) dds_ctx());
+  if (!ctx) return DDS_ENOMEM;
+  dds_status v = validate(prob, ctx->err);
+  if (v != DDS_OK) {
+    std::fprintf(stderr, "dds_setup: %s\n", ctx->err.c_str());
+    return v;
+  }
+  ctx->stream = nullptr;
+  dds_status r = setup_impl(ctx.get(), prob);
+  if (r != DDS_OK) {
+    std::fprintf(stderr, "dds_setup: %s\n", ctx->err.c_str());
+    return r;
+  }
+  *out = ctx.release();
+  return DDS_OK;
+}
+
+dds_status dds_sweep(dds_ctx *ctx, const void *f, int nrhs, void *u, int rounds) {
+  if (!ctx) return DDS_EINVAL;
+  Busy busy(ctx);
+  if (!busy.ok) return DDS_EBUSY;
+  ctx->err.clear();
+  if (!f || !u || nrhs <= 0 || rounds < 1) { ctx->err = "invalid argument"; return DDS_EINVAL; }
+  const size_t bytes = (size_t)nrhs * ctx->g.Nglob * sizeof(double2);
+  const double2 *fd;
+  double2 *ud;
+  bool uh;
+  dds_status r = stage_in(ctx, f, bytes, &fd);
+  if (r != DDS_OK) return r;
+  r = stage_out_ptr(ctx, u, bytes, &ud, &uh);
+  if (r != DDS_OK) return r;
+  CK(ctx->bbuf.ensure(bytes));
+  LAUNCHK(DDS_K_KRYLOV, launch_scale_J(ctx->stream, ctx->g, ctx->tb, nrhs, fd, ctx->bbuf.as<double2>()));
+  r = ddm(ctx, ctx->bbuf.as<double2>(), nrhs, ud, rounds);
+  if (r != DDS_OK) return r;
+  return finish_out(ctx, u, bytes, uh);
+}
+
+dds_status dds_solve(dds_ctx *ctx, const void *f, int nrhs, void *u, double tol, int maxit,
+                     int rounds, int *iters, double *relres) {
+  if (!ctx) return DDS_EINVAL;
+  Busy busy(ctx);
+  if (!busy.ok) return DDS_EBUSY;
+  ctx->err.clear();
+  if (!f || !u || nrhs <= 0 || rounds < 1 || maxit < 1 || !(tol > 0)) {
+    ctx->err = "invalid argument";
+    return DDS_EINVAL;
+  }
+  const size_t bytes = (size_t)nrhs * ctx->g.Nglob * sizeof(double2);
+  const double2 *fd;
+  double2 *ud;
+  bool uh;
+  dds_status r = stage_in(ctx, f, bytes, &fd);
+  if (r != DDS_OK) return r;
+  r = stage_out_ptr(ctx, u, bytes, &ud, &uh);
+  if (r != DDS_OK) return r;
+  CK(ctx->bbuf.ensure(bytes));
+  LAUNCHK(DDS_K_KRYLOV, launch_scale_J(ctx->stream, ctx->g, ctx->tb, nrhs, fd, ctx->bbuf.as<double2>()));
+  int it = 0;
+  std::vector<double> rel;
+  dds_status rs = fgmres(ctx, ctx->bbuf.as<double2>(), nrhs, ud, tol, maxit, rounds, &it, rel);
+  if (rs != DDS_OK && rs != DDS_ENOCONV) return rs;
+  if (iters) *iters = it;
+  if (relres) for (int q = 0; q < nrhs; ++q) relres[q] = rel[q];
+  r = finish_out(ctx, u, bytes, uh);
+  if (r != DDS_OK) return r;
+  if (rs == DDS_ENOCONV) ctx->err = "FGMRES did not reach the tolerance within maxit";
+  return rs;
+}
+
+dds_status dds_apply(dds_ctx *ctx, const void *u, int nrhs, void *Au) {
+  if (!ctx) return DDS_EINVAL;
+  Busy busy(ctx);
+  if (!busy.ok) return DDS_EBUSY;
+  ctx->err.clear();
+  if (!u || !Au || nrhs <= 0) { ctx->err = "invalid argument"; return DDS_EINVAL; }
+  const size_t bytes = (size_t)nrhs * ctx->g.Nglob * sizeof(double2);
+  const double2 *ud;
+  double2 *od;
+  bool oh;
+  dds_status r = stage_in(ctx, u, bytes, &ud);
+  if (r != DDS_OK) return r;
+  r = stage_out_ptr(ctx, Au, bytes, &od, &oh);
+  if (r != DDS_OK) return r;
+  LAUNCHK(DDS_K_KRYLOV, launch_apply_A(ctx->stream, ctx->g, ctx->tb, nrhs, ud, od, 1));
+  return finish_out(ctx, Au, bytes, oh);
+}
+
+dds_status dds_local_solve(dds_ctx *ctx, int sub, const void *b, int nrhs, void *x) {
+  if (!ctx) return DDS_EINVAL;
+  Busy busy(ctx);
+  if (!busy.ok) return DDS_EBUSY;
+  ctx->err.clear();
+  const Geom &g = ctx->g;
+  if (!b || !x || nrhs <= 0 || sub < 0 || sub >= g.nsub) { ctx->err = "invalid argument"; return DDS_EINVAL; }
+  const size_t bytes = (size_t)nrhs * g.Nloc * sizeof(double2);
+  const double2 *bd;
+  double2 *xd;
+  bool xh;
+  dds_status r = stage_in(ctx, b, bytes, &bd);
+  if (r != DDS_OK) return r;
+  r = stage_out_ptr(ctx, x, bytes, &xd, &xh);
+  if (r != DDS_OK) return r;
+  cudaStream_t st = ctx->stream;
+  std::vector<Col> cols(nrhs);
+  for (int q = 0; q < nrhs; ++q) cols[q] = Col{sub, q, q, 0};
+  const bool mixed = ctx->precision == DDS_MIXED;
+  const int pc = std::min(4, max_pc_for(ctx, mixed ? sizeof(float2) : sizeof(double2)));
+  std::vector<Panel> pans;
+  for (int i = 0; i < nrhs; i += pc) pans.push_back(Panel{i, std::min(pc, nrhs - i), ctx->fac_of_sub[sub], 0});
+  DBuf dcols, dpans;
+  CK(upload(dcols, cols, st));
+  CK(upload(dpans, pans, st));
+  const long long n = (long long)nrhs * g.Nloc;
+  if (mixed) {
+    CK(ctx->work.ensure(n * sizeof(float2)));
+    LAUNCH(launch_copy_local<float>(st, n, bd, ctx->work.as<float2>(), 1));
+    LAUNCHK(DDS_K_SUBST, launch_subst<float>(st, g, (int)pans.size(), dpans.as<Panel>(), dcols.as<Col>(),
+                               ctx->sinv32.as<float2>(), ctx->cpl32.as<float2>(), ctx->work.as<float2>(), pc));
+    LAUNCH(launch_copy_local_back<float>(st, n, ctx->work.as<float2>(), xd));
+  } else {
+    CK(ctx->work.ensure(n * sizeof(double2)));
+    LAUNCH(launch_copy_local<double>(st, n, bd, ctx->work.as<double2>(), 1));
+    LAUNCHK(DDS_K_SUBST, launch_subst<double>(st, g, (int)pans.size(), dpans.as<Panel>(), dcols.as<Col>(),
+                                ctx->sinv64.as<double2>(), ctx->cpl64.as<double2>(), ctx->work.as<double2>(), pc));
+    LAUNCH(launch_copy_local_back<double>(st, n, ctx->work.as<double2>(), xd));
+  }
+  return finish_out(ctx, x, bytes, xh);
+}
+
+dds_status dds_set_stream(dds_ctx *ctx, void *cuda_stream) {
+  if (!ctx) return DDS_EINVAL;
+  Busy busy(ctx);
+  if (!busy.ok) return DDS_EBUSY;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  return DDS_OK;
+}
+
+dds_status dds_get_info(const dds_ctx *ctx, dds_info_t *info) {
+  if (!ctx || !info) return DDS_EINVAL;
+  for (int a = 0; a < 3; ++a) {
+    info->G[a] = ctx->g.G[a];
+    info->M[a] = ctx->g.M[a];
+  }
+  info->n_sub = ctx->g.nsub;
+  info->n_factors = ctx->nfac;
+  info->trace_len = ctx->g.T;
+  info->plan = ctx->plan;
+  info->factor_bytes = (long long)(ctx->sinv64.n + ctx->sinv32.n + ctx->gmap64.n + ctx->gmap32.n);
+  info->setup_seconds = ctx->setup_seconds;
+  return DDS_OK;
+}
+
+long long dds_kernel_launches(const dds_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+dds_status dds_profile(dds_ctx *ctx, int enable) {
+  if (!ctx) return DDS_EINVAL;
+  Busy busy(ctx);
+  if (!busy.ok) return DDS_EBUSY;
+  CK(prof_fold(ctx));
+  ctx->profiling = enable != 0;
+  if (enable)
+    for (int k = 0; k < DDS_K_COUNT; ++k) ctx->prof_count[k] = 0, ctx->prof_ms[k] = 0.0;
+  return DDS_OK;
+}
+
+dds_status dds_profile_read(dds_ctx *ctx, int kind, long long *launches, double *ms) {
+  if (!ctx || kind < 0 || kind >= DDS_K_COUNT) return DDS_EINVAL;
+  Busy busy(ctx);
+  if (!busy.ok) return DDS_EBUSY;
+  CK(prof_fold(ctx));
+  if (launches) *launches = ctx->prof_count[kind];
+  if (ms) *ms = ctx->prof_ms[kind];
+  return DDS_OK;
+}
+
+const char *dds_last_error(const dds_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+void dds_destroy(dds_ctx *ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  else cudaDeviceSynchronize();
+  delete ctx;
+}
+
+}  // extern "C"

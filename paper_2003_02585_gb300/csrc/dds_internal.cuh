@@ -1,0 +1,197 @@
+// Internal declarations shared by the libdds translation units.
+//
+// Layouts (all device arrays, x1 fastest):
+//   global fields      [rhs][G2][G1][G0]             complex double (interleaved)
+//   local work         [slot][Ml][Mb]                complex R  (Ml blocks of Mb nodes; the
+//                                                    block axis is the last axis, x2 in 2D,
+//                                                    x3 in 3D)
+//   block inverses     [factor][j][s][r]             S_j^{-1}, complex R
+//   block couplings    [factor][j][r]                A(line j, line j+1) at in-block index r
+//   trace vectors      [..][T]                       per side d (d = 2a + (sign < 0)):
+//                                                    [a-line Lt_d][b-line Lt_d] at toff_d;
+//                                                    a on the holder's outer line, b on its
+//                                                    inner line; tangential index t runs over
+//                                                    the other axes, lowest axis fastest
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace dds {
+
+// ------------------------------------------------------------------------------------------
+// complex helpers (interleaved float2 / double2)
+// ------------------------------------------------------------------------------------------
+template <typename R> struct Cx;
+template <> struct Cx<float> { using T = float2; };
+template <> struct Cx<double> { using T = double2; };
+
+template <typename C> __host__ __device__ inline C cmk(double re, double im) {
+  C z; z.x = (decltype(z.x))re; z.y = (decltype(z.y))im; return z;
+}
+__host__ __device__ inline float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ inline double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ inline float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ inline double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ inline float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ inline double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// acc += a * b
+__host__ __device__ inline void cfma(float2 &acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x); acc.x = fmaf(-a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y); acc.y = fmaf(a.y, b.x, acc.y);
+}
+__host__ __device__ inline void cfma(double2 &acc, double2 a, double2 b) {
+  acc.x = fma(a.x, b.x, acc.x); acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y); acc.y = fma(a.y, b.x, acc.y);
+}
+template <typename C> __host__ __device__ inline C czero() { C z; z.x = 0; z.y = 0; return z; }
+__host__ __device__ inline float2 to_c(double2 a, float2) { return make_float2((float)a.x, (float)a.y); }
+__host__ __device__ inline double2 to_c(double2 a, double2) { return a; }
+__host__ __device__ inline double2 to_c64(float2 a) { return make_double2(a.x, a.y); }
+__host__ __device__ inline double2 to_c64(double2 a) { return a; }
+
+// ------------------------------------------------------------------------------------------
+// geometry of one problem
+// ------------------------------------------------------------------------------------------
+struct Geom {
+  int dim;
+  int n[3], parts[3], m[3], M[3], G[3];
+  int E;
+  int nsub;
+  long long Nloc, Nglob;   // nodes of one extended subdomain / of the global extended grid
+  int Mb, Ml;              // block size (nodes of a line/plane) and number of blocks
+  int nsides;              // 2 * dim
+  int Lt[6];               // line length of side d
+  int toff[6];             // offset of side d in a trace vector
+  int T;                   // trace vector length (sum of 2 * Lt)
+};
+
+// subdomain multi-index from its linear index (x1 fastest)
+__host__ __device__ inline void sub_index(const Geom &g, int s, int k[3]) {
+  k[0] = s % g.parts[0];
+  k[1] = (s / g.parts[0]) % g.parts[1];
+  k[2] = g.dim == 3 ? s / (g.parts[0] * g.parts[1]) : 0;
+}
+__host__ __device__ inline int sub_linear(const Geom &g, const int k[3]) {
+  return k[0] + g.parts[0] * (k[1] + g.parts[1] * k[2]);
+}
+// neighbour across side d or -1
+__host__ __device__ inline int sub_neighbour(const Geom &g, int s, int d) {
+  int k[3];
+  sub_index(g, s, k);
+  int a = d >> 1, sg = (d & 1) ? -1 : 1;
+  k[a] += sg;
+  if (k[a] < 0 || k[a] >= g.parts[a]) return -1;
+  return sub_linear(g, k);
+}
+// local index, along axis a of side d, of the inner (first own) / outer line
+__host__ __device__ inline int inner_line(const Geom &g, int d) {
+  int a = d >> 1;
+  return (d & 1) ? g.E : g.E + g.m[a] - 1;
+}
+__host__ __device__ inline int outer_line(const Geom &g, int d) {
+  int a = d >> 1;
+  return (d & 1) ? g.E - 1 : g.E + g.m[a];
+}
+// local linear index of the node at position l along axis a and tangential index t
+__host__ __device__ inline long long line_node(const Geom &g, int a, int l, int t) {
+  int i[3] = {0, 0, 0};
+  for (int b = 0; b < g.dim; ++b) {
+    if (b == a) { i[b] = l; continue; }
+    i[b] = t % g.M[b];
+    t /= g.M[b];
+  }
+  return i[0] + (long long)g.M[0] * (i[1] + (long long)g.M[1] * i[2]);
+}
+// own range [lo, hi) of subdomain k on axis a, in local indices (exterior sides not cut)
+__host__ __device__ inline void own_range(const Geom &g, const int k[3], int a, int &lo, int &hi) {
+  lo = (k[a] == 0) ? 0 : g.E;
+  hi = (k[a] == g.parts[a] - 1) ? g.M[a] : g.E + g.m[a];
+}
+
+// ------------------------------------------------------------------------------------------
+// work descriptors
+// ------------------------------------------------------------------------------------------
+struct Col { int sub; int rhs; int slot; int pad; };     // one (subdomain, RHS) local problem
+struct Panel { int col0; int ncol; int factor; int pad; }; // columns sharing one factor
+
+// device-side tables built at setup
+struct Tables {
+  const double2 *coef64;   // [T/2]: per side d, Lt_d commutator couplings c_d(t) at toff_d / 2
+  const float2 *coef32;
+  const double2 *an_glob64[3];  // alpha at global nodes per axis
+  const double2 *iah_glob64[3]; // 1 / alpha at global half points per axis (G+1 entries;
+                                // entry q lies between nodes q-1 and q)
+  const double *k2_glob;        // kappa^2 on the global extended grid
+  double inv_h2;                // 1 / h^2
+};
+
+// ------------------------------------------------------------------------------------------
+// launch wrappers (each returns the CUDA error of the launch)
+// ------------------------------------------------------------------------------------------
+cudaError_t launch_factor(cudaStream_t st, int nfac, int Mb, int Ml, int M0, const double2 *dg,
+                          const double2 *offx, const double2 *offy, const double2 *cpl,
+                          double2 *sinv64, float2 *sinv32, int *status);
+
+template <typename R>
+cudaError_t launch_assemble(cudaStream_t st, const Geom &g, const Tables &tb, int ncols,
+                            const Col *cols, typename Cx<R>::T *work, const double2 *f,
+                            const double2 *jglob_unused, int with_source,
+                            const typename Cx<R>::T *traces, long long trace_rhs_stride,
+                            long long trace_sub_stride);
+
+template <typename R>
+cudaError_t launch_subst(cudaStream_t st, const Geom &g, int npanels, const Panel *panels,
+                         const Col *cols, const typename Cx<R>::T *sinv,
+                         const typename Cx<R>::T *cpl, typename Cx<R>::T *work, int pc);
+
+template <typename R>
+cudaError_t launch_extract(cudaStream_t st, const Geom &g, int ncols, const Col *cols,
+                           const typename Cx<R>::T *work, double2 *u, int own_mode,
+                           typename Cx<R>::T *raw_out, typename Cx<R>::T *g_traces,
+                           const int *route, int l, int nrhs);
+
+template <typename R>
+cudaError_t launch_trace_step(cudaStream_t st, const Geom &g, int npanels, const Panel *panels,
+                              const Col *cols, const typename Cx<R>::T *gmap,
+                              typename Cx<R>::T *g_traces, typename Cx<R>::T *acc,
+                              const typename Cx<R>::T *rawf, const int *route, int l, int nrhs,
+                              int pc);
+
+template <typename R>
+cudaError_t launch_unit_traces(cudaStream_t st, const Geom &g, const Tables &tb, int k0, int nk,
+                               typename Cx<R>::T *work);
+
+template <typename R>
+cudaError_t launch_raw_lines(cudaStream_t st, const Geom &g, int nk, const typename Cx<R>::T *work,
+                             typename Cx<R>::T *gmapT, int k0);
+
+cudaError_t launch_gmap_backtrace(cudaStream_t st, const Geom &g, double2 *gmapT);
+cudaError_t launch_convert_c64_c32(cudaStream_t st, const double2 *in, float2 *out, long long n);
+template <typename R>
+cudaError_t launch_copy_local(cudaStream_t st, long long n, const double2 *in,
+                              typename Cx<R>::T *out, int to_work);
+template <typename R>
+cudaError_t launch_copy_local_back(cudaStream_t st, long long n, const typename Cx<R>::T *in,
+                                   double2 *out);
+
+// Krylov / operator kernels (FP64)
+cudaError_t launch_apply_A(cudaStream_t st, const Geom &g, const Tables &tb, int nrhs,
+                           const double2 *u, double2 *Au, int divide_by_J);
+cudaError_t launch_scale_J(cudaStream_t st, const Geom &g, const Tables &tb, int nrhs,
+                           const double2 *f, double2 *b);
+cudaError_t launch_dots(cudaStream_t st, long long N, int nrhs, int nv, const double2 *V,
+                        long long v_stride_vec, long long v_stride_rhs, const double2 *w,
+                        long long w_stride_rhs, double2 *partial, double2 *out, int nblk);
+cudaError_t launch_sub_combination(cudaStream_t st, long long N, int nrhs, int nv, const double2 *V,
+                                   long long v_stride_vec, long long v_stride_rhs,
+                                   const double2 *coef, double2 *w, long long w_stride_rhs,
+                                   double sign);
+cudaError_t launch_scale_vec(cudaStream_t st, long long N, int nrhs, const double2 *in,
+                             const double *inv_scale, double2 *out);
+
+}  // namespace dds

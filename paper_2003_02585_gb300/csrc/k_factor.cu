@@ -1,0 +1,154 @@
+// Block-tridiagonal LU of an extended subdomain operator, FP64 (set-up, once per distinct
+// operator).  With the unknowns ordered in blocks along the last axis,
+//   A = tridiag(C_{j-1}, D_j, C_j),   C_j = diag(cpl_j),
+//   S_0 = D_0,   S_j = D_j - C_{j-1} S_{j-1}^{-1} C_{j-1},
+// and the substitutions only need S_j^{-1}, which is formed explicitly.  One CTA walks the
+// whole Schur chain of one operator with S_j held in shared memory: the Schur update reads
+// S_{j-1}^{-1} in place, then S_j is inverted in place by Gauss-Jordan elimination with partial
+// (row) pivoting and a final column unscramble.
+#include "dds_internal.cuh"
+
+namespace dds {
+
+__device__ inline double2 crecip(double2 z) {
+  const double m = z.x * z.x + z.y * z.y;
+  return make_double2(z.x / m, -z.y / m);
+}
+
+__global__ void __launch_bounds__(1024) k_factor(int Mb, int Ml, int M0,
+                                                 const double2 *__restrict__ dg,
+                                                 const double2 *__restrict__ offx,
+                                                 const double2 *__restrict__ offy,
+                                                 const double2 *__restrict__ cpl,
+                                                 double2 *__restrict__ sinv64,
+                                                 float2 *__restrict__ sinv32,
+                                                 int *__restrict__ status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2 *S = reinterpret_cast<double2 *>(smem_raw);      // [Mb][Mb] row-major
+  double2 *colk = S + (size_t)Mb * Mb;                       // [Mb]
+  int *piv = reinterpret_cast<int *>(colk + Mb);             // [Mb]
+  const int f = blockIdx.x;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  const long long fb = (long long)f * Ml * Mb;
+  const long long MbMb = (long long)Mb * Mb;
+
+  for (int j = 0; j < Ml; ++j) {
+    // ---- S_j = D_j - C_{j-1} S_{j-1}^{-1} C_{j-1}
+    for (long long idx = tid; idx < MbMb; idx += nt) {
+      const int r = (int)(idx / Mb), s = (int)(idx % Mb);
+      double2 val = make_double2(0.0, 0.0);
+      if (j > 0) {
+        const double2 cr = cpl[fb + (long long)(j - 1) * Mb + r];
+        const double2 cs = cpl[fb + (long long)(j - 1) * Mb + s];
+        val = cmul(cmul(cr, S[idx]), cs);
+        val.x = -val.x;
+        val.y = -val.y;
+      }
+      const long long lb = fb + (long long)j * Mb;
+      if (r == s) val = cadd(val, dg[lb + r]);
+      else if (s == r + 1) val = cadd(val, offx[lb + r]);
+      else if (r == s + 1) val = cadd(val, offx[lb + s]);
+      if (offy != nullptr) {
+        if (s == r + M0) val = cadd(val, offy[lb + r]);
+        else if (r == s + M0) val = cadd(val, offy[lb + s]);
+      }
+      S[idx] = val;
+    }
+    __syncthreads();
+    // ---- in-place Gauss-Jordan inversion with partial pivoting
+    for (int k = 0; k < Mb; ++k) {
+      if (warp == 0) {
+        double best = -1.0;
+        int bi = k;
+        for (int r = k + lane; r < Mb; r += 32) {
+          const double2 z = S[(long long)r * Mb + k];
+          const double m = z.x * z.x + z.y * z.y;
+          if (m > best) { best = m; bi = r; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          const double ob = __shfl_down_sync(0xffffffffu, best, o);
+          const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (lane == 0) {
+          piv[k] = bi;
+          if (!(best > 0.0)) atomicExch(status, 1);
+        }
+      }
+      __syncthreads();
+      const int p = piv[k];
+      if (p != k) {
+        for (int s = tid; s < Mb; s += nt) {
+          const double2 t = S[(long long)k * Mb + s];
+          S[(long long)k * Mb + s] = S[(long long)p * Mb + s];
+          S[(long long)p * Mb + s] = t;
+        }
+        __syncthreads();
+      }
+      const double2 pinv = crecip(S[(long long)k * Mb + k]);
+      __syncthreads();
+      for (int s = tid; s < Mb; s += nt) {
+        const double2 v = S[(long long)k * Mb + s];
+        S[(long long)k * Mb + s] = (s == k) ? pinv : cmul(v, pinv);
+      }
+      for (int r = tid; r < Mb; r += nt) colk[r] = (r == k) ? make_double2(0.0, 0.0) : S[(long long)r * Mb + k];
+      __syncthreads();
+      for (long long idx = tid; idx < MbMb; idx += nt) {
+        const int r = (int)(idx / Mb), s = (int)(idx % Mb);
+        if (r == k) continue;
+        double2 v = (s == k) ? make_double2(0.0, 0.0) : S[idx];
+        const double2 prod = cmul(colk[r], S[(long long)k * Mb + s]);
+        v.x -= prod.x;
+        v.y -= prod.y;
+        S[idx] = v;
+      }
+      __syncthreads();
+    }
+    for (int k = Mb - 1; k >= 0; --k) {
+      const int p = piv[k];
+      if (p != k) {
+        for (int r = tid; r < Mb; r += nt) {
+          const double2 t = S[(long long)r * Mb + k];
+          S[(long long)r * Mb + k] = S[(long long)r * Mb + p];
+          S[(long long)r * Mb + p] = t;
+        }
+      }
+      __syncthreads();
+    }
+    // ---- store S_j^{-1} as [s][r] (thread r of a substitution reads along r)
+    const long long ob = ((long long)f * Ml + j) * MbMb;
+    for (long long idx = tid; idx < MbMb; idx += nt) {
+      const int s = (int)(idx / Mb), r = (int)(idx % Mb);
+      const double2 v = S[(long long)r * Mb + s];
+      sinv64[ob + idx] = v;
+      sinv32[ob + idx] = make_float2((float)v.x, (float)v.y);
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_factor(cudaStream_t st, int nfac, int Mb, int Ml, int M0, const double2 *dg,
+                          const double2 *offx, const double2 *offy, const double2 *cpl,
+                          double2 *sinv64, float2 *sinv32, int *status) {
+  const size_t smem = (size_t)Mb * Mb * sizeof(double2) + Mb * sizeof(double2) + Mb * sizeof(int);
+  cudaError_t e = cudaFuncSetAttribute(k_factor, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  k_factor<<<nfac, 1024, smem, st>>>(Mb, Ml, M0, dg, offx, offy, cpl, sinv64, sinv32, status);
+  return cudaGetLastError();
+}
+
+__global__ void k_convert(const double2 *__restrict__ in, float2 *__restrict__ out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = make_float2((float)in[i].x, (float)in[i].y);
+}
+
+cudaError_t launch_convert_c64_c32(cudaStream_t st, const double2 *in, float2 *out, long long n) {
+  if (n <= 0) return cudaSuccess;
+  k_convert<<<1024, 256, 0, st>>>(in, out, n);
+  return cudaGetLastError();
+}
+
+}  // namespace dds

@@ -1,0 +1,488 @@
+// Sweep kernels: right-hand-side assembly (own source + trace potentials), block-tridiagonal
+// forward/back substitution, trace extraction with the back-trace correction and routing,
+// own-node accumulation, and the trace-operator step.
+//
+// Trace potential (Section 2.3, discretised as a subdomain solve with a particular source):
+// for a trace (a, b) on side d, a on the outer line and b on the inner line of the receiver,
+//   rhs[outer_d] += c_d * b,   rhs[inner_d] -= c_d * a,
+// c_d = prod_{tangential axes} alpha / h^2 (the coupling of the two lines; alpha = 1 on the
+// interface), which is the commutator [A_R, chi_H] applied to the trace.
+#include "dds_internal.cuh"
+
+namespace dds {
+
+// ------------------------------------------------------------------------------------------
+// K1: assemble local right-hand sides
+// ------------------------------------------------------------------------------------------
+template <typename R>
+__global__ void k_assemble(Geom g, Tables tb, const Col *__restrict__ cols,
+                           typename Cx<R>::T *__restrict__ work, const double2 *__restrict__ b,
+                           int with_source, const typename Cx<R>::T *__restrict__ traces,
+                           long long trs_rhs, long long trs_sub) {
+  using C = typename Cx<R>::T;
+  const Col c = cols[blockIdx.x];
+  C *x = work + (long long)c.slot * g.Nloc;
+  for (long long i = threadIdx.x; i < g.Nloc; i += blockDim.x) x[i] = czero<C>();
+  __syncthreads();
+  int k[3];
+  sub_index(g, c.sub, k);
+  if (with_source) {
+    int lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
+    for (int a = 0; a < g.dim; ++a) own_range(g, k, a, lo[a], hi[a]);
+    const int w0 = hi[0] - lo[0], w1 = hi[1] - lo[1], w2 = hi[2] - lo[2];
+    const long long cnt = (long long)w0 * w1 * w2;
+    const double2 *bb = b + (long long)c.rhs * g.Nglob;
+    for (long long idx = threadIdx.x; idx < cnt; idx += blockDim.x) {
+      int i0 = lo[0] + (int)(idx % w0);
+      int i1 = lo[1] + (int)((idx / w0) % w1);
+      int i2 = lo[2] + (int)(idx / ((long long)w0 * w1));
+      long long loc = i0 + (long long)g.M[0] * (i1 + (long long)g.M[1] * i2);
+      long long p0 = (long long)k[0] * g.m[0] + i0;
+      long long p1 = (long long)k[1] * g.m[1] + i1;
+      long long p2 = g.dim == 3 ? (long long)k[2] * g.m[2] + i2 : 0;
+      long long glob = p0 + (long long)g.G[0] * (p1 + (long long)g.G[1] * p2);
+      x[loc] = to_c(bb[glob], C());
+    }
+  }
+  if (traces == nullptr) return;
+  const C *tr = traces + (long long)c.rhs * trs_rhs + (long long)c.sub * trs_sub;
+  for (int d = 0; d < g.nsides; ++d) {
+    __syncthreads();  // lines of different sides may share nodes
+    if (sub_neighbour(g, c.sub, d) < 0) continue;
+    const int a = d >> 1, Lt = g.Lt[d], off = g.toff[d];
+    const int li = inner_line(g, d), lo = outer_line(g, d);
+    for (int t = threadIdx.x; t < Lt; t += blockDim.x) {
+      C cd;
+      if constexpr (sizeof(R) == 4) cd = tb.coef32[off / 2 + t];
+      else cd = tb.coef64[off / 2 + t];
+      const C av = tr[off + t], bv = tr[off + Lt + t];
+      const long long no = line_node(g, a, lo, t), ni = line_node(g, a, li, t);
+      x[no] = cadd(x[no], cmul(cd, bv));
+      x[ni] = csub(x[ni], cmul(cd, av));
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// K2 + K3: block-tridiagonal substitutions for a panel of columns sharing one factor
+//   forward  y_0 = S_0^{-1} b_0,  y_j = S_j^{-1} (b_j - C_{j-1} y_{j-1})
+//   backward x_{Ml-1} = y_{Ml-1}, x_j = y_j - S_j^{-1} (C_j x_{j+1})
+// C_j = diag(cpl_j) couples block j and j+1 (A is complex symmetric).
+// ------------------------------------------------------------------------------------------
+template <typename R, int PC>
+__global__ void __launch_bounds__(128) k_subst(Geom g, const Panel *__restrict__ panels,
+                                               const Col *__restrict__ cols,
+                                               const typename Cx<R>::T *__restrict__ sinv,
+                                               const typename Cx<R>::T *__restrict__ cpl,
+                                               typename Cx<R>::T *__restrict__ work) {
+  using C = typename Cx<R>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *v = reinterpret_cast<C *>(smem_raw);  // [Mb][PC]
+  const Panel p = panels[blockIdx.x];
+  const int Mb = g.Mb, Ml = g.Ml;
+  const C *Sf = sinv + (long long)p.factor * Ml * (long long)Mb * Mb;
+  const C *cf = cpl + (long long)p.factor * Ml * (long long)Mb;
+  C *xs[PC];
+#pragma unroll
+  for (int c = 0; c < PC; ++c)
+    xs[c] = c < p.ncol ? work + (long long)cols[p.col0 + c].slot * g.Nloc : nullptr;
+
+  for (int pass = 0; pass < 2; ++pass) {
+    const int jbeg = pass == 0 ? 0 : Ml - 2;
+    const int jend = pass == 0 ? Ml : -1;
+    const int jstep = pass == 0 ? 1 : -1;
+    for (int j = jbeg; j != jend; j += jstep) {
+      for (int idx = threadIdx.x; idx < Mb * PC; idx += blockDim.x) {
+        const int r = idx / PC, c = idx % PC;
+        C val = czero<C>();
+        if (c < p.ncol) {
+          C *x = work + (long long)cols[p.col0 + c].slot * g.Nloc;
+          if (pass == 0) {
+            val = x[(long long)j * Mb + r];
+            if (j > 0) val = csub(val, cmul(cf[(long long)(j - 1) * Mb + r], x[(long long)(j - 1) * Mb + r]));
+          } else {
+            val = cmul(cf[(long long)j * Mb + r], x[(long long)(j + 1) * Mb + r]);
+          }
+        }
+        v[r * PC + c] = val;
+      }
+      __syncthreads();
+      const C *Sj = Sf + (long long)j * Mb * Mb;
+      for (int r = threadIdx.x; r < Mb; r += blockDim.x) {
+        C acc[PC];
+#pragma unroll
+        for (int c = 0; c < PC; ++c) acc[c] = czero<C>();
+#pragma unroll 4
+        for (int s = 0; s < Mb; ++s) {
+          const C a = Sj[(long long)s * Mb + r];
+#pragma unroll
+          for (int c = 0; c < PC; ++c) cfma(acc[c], a, v[s * PC + c]);
+        }
+#pragma unroll
+        for (int c = 0; c < PC; ++c) {
+          if (c < p.ncol) {
+            C *dst = xs[c] + (long long)j * Mb + r;
+            *dst = pass == 0 ? acc[c] : csub(*dst, acc[c]);
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// K4 + K5: own accumulation, raw trace lines, routed outgoing traces
+//   outgoing trace on side d: a = x[inner_d] - b_in_d, b = x[outer_d], added to the slot
+//   g[route[l][d]][rhs][neighbour][opposite side]
+// ------------------------------------------------------------------------------------------
+template <typename R>
+__global__ void k_extract(Geom g, const Col *__restrict__ cols,
+                          const typename Cx<R>::T *__restrict__ work, double2 *__restrict__ u,
+                          int own_mode, typename Cx<R>::T *__restrict__ raw_out,
+                          typename Cx<R>::T *__restrict__ gtr, const int *__restrict__ route,
+                          int l, int nrhs) {
+  using C = typename Cx<R>::T;
+  const Col c = cols[blockIdx.x];
+  const C *x = work + (long long)c.slot * g.Nloc;
+  int k[3];
+  sub_index(g, c.sub, k);
+  if (own_mode) {
+    int lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
+    for (int a = 0; a < g.dim; ++a) own_range(g, k, a, lo[a], hi[a]);
+    const int w0 = hi[0] - lo[0], w1 = hi[1] - lo[1], w2 = hi[2] - lo[2];
+    const long long cnt = (long long)w0 * w1 * w2;
+    double2 *uu = u + (long long)c.rhs * g.Nglob;
+    for (long long idx = threadIdx.x; idx < cnt; idx += blockDim.x) {
+      int i0 = lo[0] + (int)(idx % w0);
+      int i1 = lo[1] + (int)((idx / w0) % w1);
+      int i2 = lo[2] + (int)(idx / ((long long)w0 * w1));
+      long long loc = i0 + (long long)g.M[0] * (i1 + (long long)g.M[1] * i2);
+      long long p0 = (long long)k[0] * g.m[0] + i0;
+      long long p1 = (long long)k[1] * g.m[1] + i1;
+      long long p2 = g.dim == 3 ? (long long)k[2] * g.m[2] + i2 : 0;
+      long long glob = p0 + (long long)g.G[0] * (p1 + (long long)g.G[1] * p2);
+      const double2 xv = to_c64(x[loc]);
+      uu[glob] = own_mode == 1 ? cadd(uu[glob], xv) : xv;
+    }
+  }
+  if (raw_out != nullptr) {
+    C *raw = raw_out + ((long long)c.rhs * g.nsub + c.sub) * g.T;
+    for (int d = 0; d < g.nsides; ++d) {
+      const int a = d >> 1, Lt = g.Lt[d], off = g.toff[d];
+      const int li = inner_line(g, d), lo = outer_line(g, d);
+      for (int t = threadIdx.x; t < Lt; t += blockDim.x) {
+        raw[off + t] = x[line_node(g, a, li, t)];
+        raw[off + Lt + t] = x[line_node(g, a, lo, t)];
+      }
+    }
+  }
+  if (gtr != nullptr) {
+    const long long slot_stride = (long long)nrhs * g.nsub * g.T;
+    for (int d = 0; d < g.nsides; ++d) {
+      const int nb = sub_neighbour(g, c.sub, d);
+      const int lp = route[l * 6 + d];
+      if (nb < 0 || lp < 0) continue;
+      const int a = d >> 1, Lt = g.Lt[d];
+      const int li = inner_line(g, d), lo = outer_line(g, d);
+      const C *bin = gtr + l * slot_stride + ((long long)c.rhs * g.nsub + c.sub) * g.T +
+                     g.toff[d] + Lt;
+      C *dst = gtr + lp * slot_stride + ((long long)c.rhs * g.nsub + nb) * g.T + g.toff[d ^ 1];
+      for (int t = threadIdx.x; t < Lt; t += blockDim.x) {
+        const C av = csub(x[line_node(g, a, li, t)], bin[t]);
+        const C bv = x[line_node(g, a, lo, t)];
+        dst[t] = cadd(dst[t], av);
+        dst[Lt + t] = cadd(dst[Lt + t], bv);
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Trace-operator step (2D plan): out = Gmap_F * in (+ raw own-source lines in sweep 1),
+// in = incoming traces of (sub, rhs) for this sweep, routed like k_extract.  Gmap already
+// contains the back-trace correction.  acc += in (for the final own-node solve).
+// grid = (npanels, row chunks of blockDim rows); one thread per output row.
+// ------------------------------------------------------------------------------------------
+template <typename R, int PC>
+__global__ void __launch_bounds__(128) k_trace_step(Geom g, const Panel *__restrict__ panels,
+                                                    const Col *__restrict__ cols,
+                                                    const typename Cx<R>::T *__restrict__ gmapT,
+                                                    typename Cx<R>::T *__restrict__ gtr,
+                                                    typename Cx<R>::T *__restrict__ acc,
+                                                    const typename Cx<R>::T *__restrict__ rawf,
+                                                    const int *__restrict__ route, int l,
+                                                    int nrhs) {
+  using C = typename Cx<R>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *vin = reinterpret_cast<C *>(smem_raw);  // [T][PC]
+  const Panel p = panels[blockIdx.x];
+  const int T = g.T;
+  const long long slot_stride = (long long)nrhs * g.nsub * T;
+  for (int idx = threadIdx.x; idx < T * PC; idx += blockDim.x) {
+    const int kk = idx / PC, c = idx % PC;
+    C val = czero<C>();
+    if (c < p.ncol) {
+      const Col cc = cols[p.col0 + c];
+      const long long base = ((long long)cc.rhs * g.nsub + cc.sub) * T;
+      val = gtr[l * slot_stride + base + kk];
+      if (blockIdx.y == 0) acc[base + kk] = cadd(acc[base + kk], val);
+    }
+    vin[kk * PC + c] = val;
+  }
+  __syncthreads();
+  const int r = blockIdx.y * blockDim.x + threadIdx.x;
+  if (r >= T) return;
+  const C *Gf = gmapT + (long long)p.factor * T * T;
+  C out[PC];
+#pragma unroll
+  for (int c = 0; c < PC; ++c) out[c] = czero<C>();
+#pragma unroll 4
+  for (int kk = 0; kk < T; ++kk) {
+    const C a = Gf[(long long)kk * T + r];
+#pragma unroll
+    for (int c = 0; c < PC; ++c) cfma(out[c], a, vin[kk * PC + c]);
+  }
+  // which side / line / position is row r
+  int d = 0;
+  while (d + 1 < g.nsides && r >= g.toff[d + 1]) ++d;
+  const int lp = route[l * 6 + d];
+#pragma unroll
+  for (int c = 0; c < PC; ++c) {
+    if (c >= p.ncol) continue;
+    const Col cc = cols[p.col0 + c];
+    C val = out[c];
+    if (rawf != nullptr) val = cadd(val, rawf[((long long)cc.rhs * g.nsub + cc.sub) * T + r]);
+    const int nb = sub_neighbour(g, cc.sub, d);
+    if (nb < 0 || lp < 0) continue;
+    C *dst = gtr + lp * slot_stride + ((long long)cc.rhs * g.nsub + nb) * T + g.toff[d ^ 1] +
+             (r - g.toff[d]);
+    *dst = cadd(*dst, val);
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Trace-map construction helpers
+// ------------------------------------------------------------------------------------------
+// slot q holds the commutator source of the unit trace entry k0 + q
+template <typename R>
+__global__ void k_unit_traces(Geom g, Tables tb, int k0, int nk,
+                              typename Cx<R>::T *__restrict__ work) {
+  using C = typename Cx<R>::T;
+  const int q = blockIdx.x;
+  if (q >= nk) return;
+  C *x = work + (long long)q * g.Nloc;
+  for (long long i = threadIdx.x; i < g.Nloc; i += blockDim.x) x[i] = czero<C>();
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const int kk = k0 + q;
+  int d = 0;
+  while (d + 1 < g.nsides && kk >= g.toff[d + 1]) ++d;
+  const int Lt = g.Lt[d], within = kk - g.toff[d];
+  const int is_b = within >= Lt, t = is_b ? within - Lt : within;
+  C cd;
+  if constexpr (sizeof(R) == 4) cd = tb.coef32[g.toff[d] / 2 + t];
+  else cd = tb.coef64[g.toff[d] / 2 + t];
+  const int a = d >> 1;
+  if (is_b) {
+    x[line_node(g, a, outer_line(g, d), t)] = cd;
+  } else {
+    C z = czero<C>();
+    x[line_node(g, a, inner_line(g, d), t)] = csub(z, cd);
+  }
+}
+
+// gmapT[k0 + q][r] = raw trace line entry r of the solution in slot q
+template <typename R>
+__global__ void k_raw_lines(Geom g, const typename Cx<R>::T *__restrict__ work,
+                            typename Cx<R>::T *__restrict__ gmapT, int k0) {
+  using C = typename Cx<R>::T;
+  const int q = blockIdx.x;
+  const C *x = work + (long long)q * g.Nloc;
+  C *dst = gmapT + (long long)(k0 + q) * g.T;
+  for (int d = 0; d < g.nsides; ++d) {
+    const int a = d >> 1, Lt = g.Lt[d], off = g.toff[d];
+    const int li = inner_line(g, d), lo = outer_line(g, d);
+    for (int t = threadIdx.x; t < Lt; t += blockDim.x) {
+      dst[off + t] = x[line_node(g, a, li, t)];
+      dst[off + Lt + t] = x[line_node(g, a, lo, t)];
+    }
+  }
+}
+
+// back-trace correction folded into the map: a_out_d(t) -= b_in_d(t)
+__global__ void k_gmap_backtrace(Geom g, double2 *gmapT) {
+  for (int d = 0; d < g.nsides; ++d) {
+    const int Lt = g.Lt[d], off = g.toff[d];
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < Lt; t += gridDim.x * blockDim.x) {
+      double2 *e = gmapT + (long long)(off + Lt + t) * g.T + (off + t);
+      e->x -= 1.0;
+    }
+  }
+}
+
+template <typename R>
+__global__ void k_copy_local(long long n, const double2 *__restrict__ in,
+                             typename Cx<R>::T *__restrict__ out) {
+  using C = typename Cx<R>::T;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = to_c(in[i], C());
+}
+template <typename R>
+__global__ void k_copy_local_back(long long n, const typename Cx<R>::T *__restrict__ in,
+                                  double2 *__restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = to_c64(in[i]);
+}
+
+// ------------------------------------------------------------------------------------------
+// launch wrappers
+// ------------------------------------------------------------------------------------------
+template <typename R>
+cudaError_t launch_assemble(cudaStream_t st, const Geom &g, const Tables &tb, int ncols,
+                            const Col *cols, typename Cx<R>::T *work, const double2 *b,
+                            const double2 *, int with_source, const typename Cx<R>::T *traces,
+                            long long trs_rhs, long long trs_sub) {
+  if (ncols <= 0) return cudaSuccess;
+  k_assemble<R><<<ncols, 256, 0, st>>>(g, tb, cols, work, b, with_source, traces, trs_rhs,
+                                       trs_sub);
+  return cudaGetLastError();
+}
+
+template <typename R, int PC>
+static cudaError_t subst_pc(cudaStream_t st, const Geom &g, int npanels, const Panel *panels,
+                            const Col *cols, const typename Cx<R>::T *sinv,
+                            const typename Cx<R>::T *cpl, typename Cx<R>::T *work) {
+  using C = typename Cx<R>::T;
+  const size_t smem = (size_t)g.Mb * PC * sizeof(C);
+  cudaError_t e = cudaFuncSetAttribute(k_subst<R, PC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  k_subst<R, PC><<<npanels, 128, smem, st>>>(g, panels, cols, sinv, cpl, work);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_subst(cudaStream_t st, const Geom &g, int npanels, const Panel *panels,
+                         const Col *cols, const typename Cx<R>::T *sinv,
+                         const typename Cx<R>::T *cpl, typename Cx<R>::T *work, int pc) {
+  if (npanels <= 0) return cudaSuccess;
+  switch (pc) {
+    case 1: return subst_pc<R, 1>(st, g, npanels, panels, cols, sinv, cpl, work);
+    case 2: return subst_pc<R, 2>(st, g, npanels, panels, cols, sinv, cpl, work);
+    case 4: return subst_pc<R, 4>(st, g, npanels, panels, cols, sinv, cpl, work);
+    case 8: return subst_pc<R, 8>(st, g, npanels, panels, cols, sinv, cpl, work);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename R>
+cudaError_t launch_extract(cudaStream_t st, const Geom &g, int ncols, const Col *cols,
+                           const typename Cx<R>::T *work, double2 *u, int own_mode,
+                           typename Cx<R>::T *raw_out, typename Cx<R>::T *g_traces,
+                           const int *route, int l, int nrhs) {
+  if (ncols <= 0) return cudaSuccess;
+  k_extract<R><<<ncols, 256, 0, st>>>(g, cols, work, u, own_mode, raw_out, g_traces, route, l,
+                                      nrhs);
+  return cudaGetLastError();
+}
+
+template <typename R, int PC>
+static cudaError_t trace_step_pc(cudaStream_t st, const Geom &g, int npanels,
+                                 const Panel *panels, const Col *cols,
+                                 const typename Cx<R>::T *gmap, typename Cx<R>::T *gtr,
+                                 typename Cx<R>::T *acc, const typename Cx<R>::T *rawf,
+                                 const int *route, int l, int nrhs) {
+  using C = typename Cx<R>::T;
+  const size_t smem = (size_t)g.T * PC * sizeof(C);
+  cudaError_t e = cudaFuncSetAttribute(k_trace_step<R, PC>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(npanels, (g.T + 127) / 128);
+  k_trace_step<R, PC><<<grid, 128, smem, st>>>(g, panels, cols, gmap, gtr, acc, rawf, route, l,
+                                                nrhs);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_trace_step(cudaStream_t st, const Geom &g, int npanels, const Panel *panels,
+                              const Col *cols, const typename Cx<R>::T *gmap,
+                              typename Cx<R>::T *g_traces, typename Cx<R>::T *acc,
+                              const typename Cx<R>::T *rawf, const int *route, int l, int nrhs,
+                              int pc) {
+  if (npanels <= 0) return cudaSuccess;
+  switch (pc) {
+    case 1: return trace_step_pc<R, 1>(st, g, npanels, panels, cols, gmap, g_traces, acc, rawf, route, l, nrhs);
+    case 2: return trace_step_pc<R, 2>(st, g, npanels, panels, cols, gmap, g_traces, acc, rawf, route, l, nrhs);
+    case 4: return trace_step_pc<R, 4>(st, g, npanels, panels, cols, gmap, g_traces, acc, rawf, route, l, nrhs);
+    case 8: return trace_step_pc<R, 8>(st, g, npanels, panels, cols, gmap, g_traces, acc, rawf, route, l, nrhs);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename R>
+cudaError_t launch_unit_traces(cudaStream_t st, const Geom &g, const Tables &tb, int k0, int nk,
+                               typename Cx<R>::T *work) {
+  if (nk <= 0) return cudaSuccess;
+  k_unit_traces<R><<<nk, 256, 0, st>>>(g, tb, k0, nk, work);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_raw_lines(cudaStream_t st, const Geom &g, int nk,
+                             const typename Cx<R>::T *work, typename Cx<R>::T *gmapT, int k0) {
+  if (nk <= 0) return cudaSuccess;
+  k_raw_lines<R><<<nk, 128, 0, st>>>(g, work, gmapT, k0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gmap_backtrace(cudaStream_t st, const Geom &g, double2 *gmapT) {
+  k_gmap_backtrace<<<8, 128, 0, st>>>(g, gmapT);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_copy_local(cudaStream_t st, long long n, const double2 *in,
+                              typename Cx<R>::T *out, int) {
+  if (n <= 0) return cudaSuccess;
+  k_copy_local<R><<<(unsigned)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096), 256, 0, st>>>(n, in, out);
+  return cudaGetLastError();
+}
+template <typename R>
+cudaError_t launch_copy_local_back(cudaStream_t st, long long n, const typename Cx<R>::T *in,
+                                   double2 *out) {
+  if (n <= 0) return cudaSuccess;
+  k_copy_local_back<R><<<(unsigned)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096), 256, 0, st>>>(n, in, out);
+  return cudaGetLastError();
+}
+
+#define DDS_INST(R)                                                                             \
+  template cudaError_t launch_assemble<R>(cudaStream_t, const Geom &, const Tables &, int,     \
+                                          const Col *, Cx<R>::T *, const double2 *,           \
+                                          const double2 *, int, const Cx<R>::T *, long long,   \
+                                          long long);                                           \
+  template cudaError_t launch_subst<R>(cudaStream_t, const Geom &, int, const Panel *,         \
+                                       const Col *, const Cx<R>::T *, const Cx<R>::T *,        \
+                                       Cx<R>::T *, int);                                        \
+  template cudaError_t launch_extract<R>(cudaStream_t, const Geom &, int, const Col *,         \
+                                         const Cx<R>::T *, double2 *, int, Cx<R>::T *,         \
+                                         Cx<R>::T *, const int *, int, int);                    \
+  template cudaError_t launch_trace_step<R>(cudaStream_t, const Geom &, int, const Panel *,    \
+                                            const Col *, const Cx<R>::T *, Cx<R>::T *,         \
+                                            Cx<R>::T *, const Cx<R>::T *, const int *, int,    \
+                                            int, int);                                          \
+  template cudaError_t launch_unit_traces<R>(cudaStream_t, const Geom &, const Tables &, int,  \
+                                             int, Cx<R>::T *);                                  \
+  template cudaError_t launch_raw_lines<R>(cudaStream_t, const Geom &, int, const Cx<R>::T *,  \
+                                           Cx<R>::T *, int);                                    \
+  template cudaError_t launch_copy_local<R>(cudaStream_t, long long, const double2 *,          \
+                                            Cx<R>::T *, int);                                   \
+  template cudaError_t launch_copy_local_back<R>(cudaStream_t, long long, const Cx<R>::T *,    \
+                                                 double2 *);
+
+DDS_INST(float)
+DDS_INST(double)
+
+}  // namespace dds

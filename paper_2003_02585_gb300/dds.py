@@ -1,0 +1,266 @@
+"""ctypes binding of libdds (include/dds.h): argument marshalling only.
+
+Every step of set-up and solve runs inside libdds.so (CUDA kernels for sm_103a); this module
+only converts Python arguments to the C ABI.  Fields are complex128 arrays of shape
+(nrhs, *G[::-1]) on the global extended grid, either torch CUDA tensors (passed by device
+pointer, on torch's current stream) or numpy arrays (host buffers, staged by the library).
+There is no fallback: if libdds.so is missing, :func:`load` raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libdds.so")
+
+STATUS = {0: "DDS_OK", 1: "DDS_EINVAL", 2: "DDS_ENOMEM", 3: "DDS_ECUDA", 4: "DDS_ENOCONV",
+          5: "DDS_ETIMEOUT", 6: "DDS_EBUSY"}
+PRECISION = {"fp64": 0, "mixed": 1}
+PLAN = {"auto": 0, "direct": 1, "trace": 2}
+
+EXPORTS = ["dds_setup", "dds_sweep", "dds_solve", "dds_apply", "dds_local_solve",
+           "dds_set_stream", "dds_get_info", "dds_kernel_launches", "dds_last_error",
+           "dds_destroy", "dds_profile", "dds_profile_read"]
+KERNEL_KINDS = {"assemble": 0, "subst": 1, "extract": 2, "trace_step": 3, "krylov": 4,
+                "other": 5}
+
+
+class DDSError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("h", ctypes.c_double),
+                ("omega", ctypes.c_double), ("c", ctypes.POINTER(ctypes.c_double)),
+                ("parts", ctypes.c_int * 3), ("pml_cells", ctypes.c_int),
+                ("pml_strength", ctypes.c_double), ("pml_power", ctypes.c_int),
+                ("halo", ctypes.c_int), ("precision", ctypes.c_int), ("plan", ctypes.c_int)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("G", ctypes.c_int * 3), ("M", ctypes.c_int * 3), ("n_sub", ctypes.c_int),
+                ("n_factors", ctypes.c_int), ("trace_len", ctypes.c_int), ("plan", ctypes.c_int),
+                ("factor_bytes", ctypes.c_longlong), ("setup_seconds", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libdds.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libdds.so not found at {path}; run paper_2003_02585_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp = ctypes.c_void_p
+    lib.dds_setup.argtypes = [ctypes.POINTER(_Problem), ctypes.POINTER(vp)]
+    lib.dds_sweep.argtypes = [vp, vp, ctypes.c_int, vp, ctypes.c_int]
+    lib.dds_solve.argtypes = [vp, vp, ctypes.c_int, vp, ctypes.c_double, ctypes.c_int,
+                              ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                              ctypes.POINTER(ctypes.c_double)]
+    lib.dds_apply.argtypes = [vp, vp, ctypes.c_int, vp]
+    lib.dds_local_solve.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, vp]
+    lib.dds_set_stream.argtypes = [vp, vp]
+    lib.dds_get_info.argtypes = [vp, ctypes.POINTER(_Info)]
+    lib.dds_kernel_launches.argtypes = [vp]
+    lib.dds_kernel_launches.restype = ctypes.c_longlong
+    lib.dds_last_error.argtypes = [vp]
+    lib.dds_last_error.restype = ctypes.c_char_p
+    lib.dds_destroy.argtypes = [vp]
+    lib.dds_destroy.restype = None
+    lib.dds_profile.argtypes = [vp, ctypes.c_int]
+    lib.dds_profile_read.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
+                                     ctypes.POINTER(ctypes.c_double)]
+    for name in ["dds_setup", "dds_sweep", "dds_solve", "dds_apply", "dds_local_solve",
+                 "dds_set_stream", "dds_get_info", "dds_profile", "dds_profile_read"]:
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _is_torch(x):
+    try:
+        import torch
+        return isinstance(x, torch.Tensor)
+    except ImportError:  # pragma: no cover
+        return False
+
+
+class Context:
+    """One set-up problem (dds_setup); owns the device factors and buffers."""
+
+    def __init__(self, n, h, omega, c, parts, pml_cells, pml_strength=30.0, pml_power=2,
+                 halo=0, precision="fp64", plan="auto"):
+        self._lib = load()
+        n = tuple(int(v) for v in n)
+        parts = tuple(int(v) for v in parts)
+        dim = len(n)
+        c = np.ascontiguousarray(np.asarray(c, dtype=np.float64))
+        if c.shape != n[::-1]:
+            raise ValueError(f"c must have shape {n[::-1]}")
+        self._c = c
+        p = _Problem()
+        p.dim = dim
+        for a in range(3):
+            p.n[a] = n[a] if a < dim else 1
+            p.parts[a] = parts[a] if a < dim else 1
+        p.h = float(h)
+        p.omega = float(omega)
+        p.c = c.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        p.pml_cells = int(pml_cells)
+        p.pml_strength = float(pml_strength)
+        p.pml_power = int(pml_power)
+        p.halo = int(halo)
+        p.precision = PRECISION[precision]
+        p.plan = PLAN[plan]
+        handle = ctypes.c_void_p()
+        st = self._lib.dds_setup(ctypes.byref(p), ctypes.byref(handle))
+        if st != 0:
+            raise DDSError(st, "dds_setup failed (see stderr)")
+        self._h = handle
+        self.n, self.parts, self.dim = n, parts, dim
+        self.precision = precision
+        info = self.info()
+        self.G = tuple(info["G"][:dim])
+        self.M = tuple(info["M"][:dim])
+
+    # -- helpers -----------------------------------------------------------------------------
+    def _check(self, st):
+        if st != 0:
+            raise DDSError(st, self._lib.dds_last_error(self._h).decode())
+
+    def _bind_stream(self, *arrays):
+        if any(_is_torch(a) and a.is_cuda for a in arrays):
+            import torch
+            self._check(self._lib.dds_set_stream(self._h, torch.cuda.current_stream().cuda_stream))
+
+    @staticmethod
+    def _ptr(a):
+        if _is_torch(a):
+            if not a.is_contiguous():
+                raise ValueError("tensor must be contiguous")
+            return ctypes.c_void_p(a.data_ptr())
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return ctypes.c_void_p(a.ctypes.data)
+
+    def _like(self, a, shape):
+        if _is_torch(a):
+            import torch
+            return torch.empty(shape, dtype=torch.complex128, device=a.device)
+        return np.empty(shape, dtype=np.complex128)
+
+    def _fields(self, f):
+        if _is_torch(f):
+            import torch
+            if f.dtype != torch.complex128:
+                raise TypeError("fields must be complex128")
+        else:
+            f = np.ascontiguousarray(f, dtype=np.complex128)
+        if tuple(f.shape[-self.dim:]) != self.G[::-1]:
+            raise ValueError(f"field shape must end with {self.G[::-1]}")
+        nrhs = 1 if f.ndim == self.dim else int(f.shape[0])
+        return f, nrhs
+
+    # -- API -----------------------------------------------------------------------------------
+    def sweep(self, f, rounds=1):
+        """u_DDM of Algorithm 2.1 / 4.1 for sources f (dds_sweep)."""
+        f, nrhs = self._fields(f)
+        u = self._like(f, tuple(f.shape))
+        self._bind_stream(f, u)
+        self._check(self._lib.dds_sweep(self._h, self._ptr(f), nrhs, self._ptr(u), int(rounds)))
+        return u
+
+    def solve(self, f, tol=1e-6, maxit=50, rounds=1):
+        """FGMRES with the DDM preconditioner (dds_solve).  Returns (u, iters, relres)."""
+        f, nrhs = self._fields(f)
+        u = self._like(f, tuple(f.shape))
+        self._bind_stream(f, u)
+        it = ctypes.c_int(0)
+        rel = (ctypes.c_double * nrhs)()
+        st = self._lib.dds_solve(self._h, self._ptr(f), nrhs, self._ptr(u), float(tol),
+                                 int(maxit), int(rounds), ctypes.byref(it), rel)
+        if st not in (0, 4):
+            self._check(st)
+        return u, int(it.value), np.array(rel[:])
+
+    def apply(self, u):
+        """L u = J^{-1} A u (dds_apply)."""
+        u, nrhs = self._fields(u)
+        out = self._like(u, tuple(u.shape))
+        self._bind_stream(u, out)
+        self._check(self._lib.dds_apply(self._h, self._ptr(u), nrhs, self._ptr(out)))
+        return out
+
+    def local_solve(self, sub, b):
+        """Block-tridiagonal local solve on subdomain `sub` (dds_local_solve)."""
+        if _is_torch(b):
+            nrhs = 1 if b.ndim == self.dim else int(b.shape[0])
+        else:
+            b = np.ascontiguousarray(b, dtype=np.complex128)
+            nrhs = 1 if b.ndim == self.dim else int(b.shape[0])
+        x = self._like(b, tuple(b.shape))
+        self._bind_stream(b, x)
+        self._check(self._lib.dds_local_solve(self._h, int(sub), self._ptr(b), nrhs, self._ptr(x)))
+        return x
+
+    def info(self):
+        inf = _Info()
+        self._check(self._lib.dds_get_info(self._h, ctypes.byref(inf)))
+        return {"G": list(inf.G), "M": list(inf.M), "n_sub": inf.n_sub,
+                "n_factors": inf.n_factors, "trace_len": inf.trace_len, "plan": inf.plan,
+                "factor_bytes": inf.factor_bytes, "setup_seconds": inf.setup_seconds}
+
+    def launches(self):
+        return int(self._lib.dds_kernel_launches(self._h))
+
+    def profile(self, enable=True):
+        """Enable/disable per-launch CUDA-event timing (dds_profile)."""
+        self._check(self._lib.dds_profile(self._h, 1 if enable else 0))
+
+    def kernel_stats(self):
+        """{kind: (launches, device ms)} accumulated since profiling was enabled."""
+        out = {}
+        for name, k in KERNEL_KINDS.items():
+            n = ctypes.c_longlong(0)
+            ms = ctypes.c_double(0.0)
+            self._check(self._lib.dds_profile_read(self._h, k, ctypes.byref(n), ctypes.byref(ms)))
+            out[name] = (int(n.value), float(ms.value))
+        return out
+
+    def set_stream(self, stream_handle):
+        self._check(self._lib.dds_set_stream(self._h, ctypes.c_void_p(stream_handle)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.dds_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- layout helpers (no arithmetic) ----------------------------------------------------------
+    def extend(self, f_interior):
+        """Place interior-node fields on the global extended grid (zeros in halo/PML)."""
+        E = (self.G[0] - self.n[0]) // 2
+        lead = f_interior.shape[:-self.dim]
+        out = np.zeros(lead + self.G[::-1], dtype=np.complex128)
+        sl = tuple(slice(E, E + na) for na in self.n[::-1])
+        out[(Ellipsis,) + sl] = f_interior
+        return out
+
+    def interior(self, u_ext):
+        E = (self.G[0] - self.n[0]) // 2
+        sl = tuple(slice(E, E + na) for na in self.n[::-1])
+        return u_ext[(Ellipsis,) + sl]

@@ -1,0 +1,204 @@
+"""GPU parity: libdds (through its C ABI) against the CPU oracle.
+
+Tolerances.  FP64 mode: the GPU path factors line blocks instead of the oracle's banded LU and
+sums in another order, so results agree to rounding of a well-conditioned chain; 1e-10 relative
+L2 is asserted (observed ~1e-13).  Mixed mode: substitutions and trace transfer in complex FP32
+(unit roundoff 6e-8, amplified by the local solve's conditioning); the raw DDM output is
+checked to 1e-4 relative, and after FP64 FGMRES refinement the field must match the oracle's
+global solve to 1e-6 (the BASELINE accuracy target).
+"""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle.discretize import (Problem, assemble_global, assemble_local, extend_interior,
+                               rhs_from_source)
+from oracle.linsolve import global_solve
+from oracle.sweep import LocalProblems, ddm_solve
+from paper_2003_02585_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _dds():
+    from paper_2003_02585_gb300 import dds
+    return dds
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _case(n, parts, P, kappa, c=None, centres=None, H=0, width=None):
+    h = 1.0 / n[0]
+    c = synth.medium_constant(n) if c is None else c
+    centres = centres or [tuple(0.5 for _ in n)]
+    f = synth.gaussian_sources(n, h, centres, 2 * h if width is None else width)
+    prob = Problem(n, h, kappa, c, parts, P, 30.0, 2, H)
+    return prob, f
+
+
+def _ctx(prob, precision="fp64", plan="auto"):
+    return _dds().Context(prob.n, prob.h, prob.omega, prob.c, prob.parts, prob.pml_cells,
+                          prob.pml_strength, prob.pml_power, prob.halo, precision, plan)
+
+
+def _on_dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(DEV)
+
+
+# ----------------------------------------------------------------------------- operator ------
+
+@pytest.mark.parametrize("n,parts,H,P", [((40, 32), (2, 2), 0, 4), ((8, 12, 8), (2, 3, 2), 1, 2)])
+def test_apply_matches_oracle_operator(n, parts, H, P):
+    rng = np.random.default_rng(0)
+    c = 1.0 + 0.5 * rng.random(n[::-1])
+    prob, _ = _case(n, parts, P, 2 * np.pi * 3, c=c, H=H)
+    ctx = _ctx(prob)
+    A, J = assemble_global(prob)
+    u = rng.standard_normal((2,) + prob.G[::-1]) + 1j * rng.standard_normal((2,) + prob.G[::-1])
+    got = ctx.apply(_on_dev(u)).cpu().numpy()
+    for r in range(2):
+        ref = (A @ u[r].ravel()).reshape(prob.G[::-1]) / J
+        assert _rel(got[r], ref) < 1e-13
+
+
+# ----------------------------------------------------------------------------- local solve ---
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("mixed", 1e-4)])
+def test_local_solve_matches_banded_lu(precision, tol):
+    """K2/K3 (block substitutions with the FP64 Schur factors) vs the oracle's banded LU on one
+    extended subdomain, random right-hand sides (ragged: M = 50 is no multiple of a tile)."""
+    rng = np.random.default_rng(1)
+    prob, _ = _case((52, 52), (2, 2), 12, 2 * np.pi * 6)
+    ctx = _ctx(prob, precision)
+    loc = LocalProblems(prob)
+    dims = prob.M[::-1]
+    b = rng.standard_normal((3,) + dims) + 1j * rng.standard_normal((3,) + dims)
+    for sub_lin, sub in [(0, (0, 0)), (3, (1, 1))]:
+        x = ctx.local_solve(sub_lin, _on_dev(b)).cpu().numpy()
+        ref = loc.solve(sub, b)
+        assert _rel(x, ref) < tol
+
+
+# ----------------------------------------------------------------------------- DDM parity ----
+
+DDM_CASES = [
+    # (n, parts, P, kappa, medium, centres, rounds, H)
+    ((128, 128), (2, 2), 16, 2 * np.pi * 8, "const", [(0.5, 0.5)], 1, 0),   # 128^2 2x2, k=16 pi
+    ((60, 36), (3, 2), 6, 2 * np.pi * 3, "const", [(0.3, 0.6), (0.8, 0.2)], 1, 0),
+    ((48, 48), (4, 3), 5, 2 * np.pi * 3, "layer", [(0.4, 0.8)], 2, 1),
+    ((40, 40), (1, 4), 6, 2 * np.pi * 3, "layer", [(0.5, 0.3)], 1, 0),        # 1 x N strip
+    ((32, 32), (1, 1), 6, 2 * np.pi * 3, "const", [(0.5, 0.5)], 1, 0),        # one subdomain
+    ((12, 12, 12), (2, 2, 2), 2, 2 * np.pi * 1.5, "const", [(0.4, 0.5, 0.6)], 1, 0),
+    ((12, 12, 16), (2, 2, 4), 2, 2 * np.pi * 1.5, "layer", [(0.5, 0.4, 0.8)], 2, 0),
+]
+
+
+def _medium(kind, n):
+    if kind == "const":
+        return synth.medium_constant(n)
+    return synth.medium_two_layer(n, 1.0 / n[0], axis=len(n) - 1)
+
+
+@pytest.mark.parametrize("plan", ["direct", "trace"])
+@pytest.mark.parametrize("case", DDM_CASES,
+                         ids=lambda c: "x".join(map(str, c[0])) + f"-{c[1]}-r{c[6]}")
+def test_ddm_fp64_matches_oracle(case, plan):
+    n, parts, P, kappa, med, centres, rounds, H = case
+    prob, f = _case(n, parts, P, kappa, c=_medium(med, n), centres=centres, H=H)
+    b = rhs_from_source(prob, extend_interior(prob, f))
+    ref = ddm_solve(prob, b, rounds)
+    ctx = _ctx(prob, "fp64", plan)
+    got = ctx.sweep(_on_dev(ctx.extend(f)), rounds).cpu().numpy()
+    for r in range(len(centres)):
+        assert _rel(got[r], ref[r]) < 1e-10
+
+
+@pytest.mark.parametrize("plan", ["direct", "trace"])
+def test_ddm_mixed_matches_oracle(plan):
+    n = (96, 96)
+    prob, f = _case(n, (3, 3), 12, 2 * np.pi * 6, c=_medium("layer", n), centres=[(0.3, 0.3)])
+    b = rhs_from_source(prob, extend_interior(prob, f))
+    ref = ddm_solve(prob, b, 1)
+    ctx = _ctx(prob, "mixed", plan)
+    got = ctx.sweep(_on_dev(ctx.extend(f))).cpu().numpy()
+    assert _rel(got[0], ref[0]) < 1e-4
+
+
+def test_ddm_host_buffers_equal_device_buffers():
+    prob, f = _case((48, 48), (2, 2), 8, 2 * np.pi * 3)
+    ctx = _ctx(prob)
+    fe = ctx.extend(f)
+    u_dev = ctx.sweep(_on_dev(fe)).cpu().numpy()
+    u_host = ctx.sweep(fe)
+    assert isinstance(u_host, np.ndarray)
+    assert np.array_equal(u_dev, u_host)
+
+
+def test_ddm_batch_invariance_and_linearity():
+    prob, f = _case((64, 64), (4, 4), 8, 2 * np.pi * 4, centres=[(0.2, 0.3), (0.7, 0.6), (0.5, 0.9)])
+    for precision, tol in (("fp64", 1e-13), ("mixed", 1e-6)):
+        ctx = _ctx(prob, precision)
+        fe = ctx.extend(f)
+        batch = ctx.sweep(_on_dev(fe)).cpu().numpy()
+        for r in range(3):
+            alone = ctx.sweep(_on_dev(fe[r:r + 1])).cpu().numpy()[0]
+            assert _rel(alone, batch[r]) < tol
+        lin = ctx.sweep(_on_dev(fe[0:1] + 2 * fe[1:2])).cpu().numpy()[0]
+        assert _rel(lin, batch[0] + 2 * batch[1]) < max(tol, 1e-12) * 10
+
+
+def test_ddm_constant_medium_reproduces_global_solution():
+    """Theorem 3.3 on the GPU: the DDM gap to the global PML solve is PML-level."""
+    prob, f = _case((128, 128), (2, 2), 16, 2 * np.pi * 8)
+    ctx = _ctx(prob, "fp64")
+    u = ctx.sweep(_on_dev(ctx.extend(f))).cpu().numpy()[0]
+    ug = global_solve(prob, rhs_from_source(prob, extend_interior(prob, f))[0])
+    assert _rel(u, ug) < 3e-4
+
+
+# ----------------------------------------------------------------------------- FGMRES --------
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_fgmres_matches_global_solve(precision):
+    n = (96, 96)
+    prob, f = _case(n, (4, 4), 10, 2 * np.pi * 6, c=_medium("layer", n),
+                    centres=[(0.3, 0.7), (0.6, 0.2)])
+    ctx = _ctx(prob, precision)
+    u, it, rel = ctx.solve(_on_dev(ctx.extend(f)), tol=1e-9, maxit=40)
+    ug = global_solve(prob, rhs_from_source(prob, extend_interior(prob, f)))
+    u = u.cpu().numpy()
+    assert np.all(rel < 1e-9), rel
+    assert it <= 25
+    for r in range(2):
+        assert _rel(u[r], ug[r]) < 1e-6
+
+
+def test_fgmres_one_subdomain_converges_in_one_iteration():
+    prob, f = _case((40, 40), (1, 1), 8, 2 * np.pi * 3)
+    ctx = _ctx(prob, "fp64")
+    _, it, rel = ctx.solve(_on_dev(ctx.extend(f)), tol=1e-10, maxit=5)
+    assert it == 1 and rel[0] < 1e-10
+
+
+# ----------------------------------------------------------------------------- errors --------
+
+def test_invalid_problem_is_rejected():
+    dds = _dds()
+    with pytest.raises(dds.DDSError):
+        dds.Context((30, 30), 1 / 30, 10.0, np.ones((30, 30)), (4, 4), 4)   # 30 % 4 != 0
+    with pytest.raises(dds.DDSError):
+        dds.Context((30, 30), 1 / 30, 10.0, -np.ones((30, 30)), (3, 3), 4)  # c <= 0
