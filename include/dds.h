@@ -119,6 +119,24 @@ dds_status dds_apply(dds_ctx *ctx, const void *u, int nrhs, void *Au);
  * sub is the subdomain's linear index (x1 fastest).  Runs in the context's precision. */
 dds_status dds_local_solve(dds_ctx *ctx, int sub, const void *b, int nrhs, void *x);
 
+/* dds_local_solve_noalloc -- dds_local_solve for callers that must not have this library
+ * allocate device memory.  The paper has no counterpart; this is a deployment variant.
+ * Who needs it: a host program whose device memory is fully reserved by another allocator (a
+ * framework's caching allocator, a fixed serving budget), where a cudaMalloc inside the call
+ * would fail or evict that allocator's cache, or a latency-critical caller that cannot accept
+ * the device-wide synchronisation cudaMalloc / cudaFree may cause.
+ * Contract: b and x are DEVICE pointers on the context's device (host pointers are rejected
+ * with DDS_EINVAL, since staging them would need a buffer).  All scratch -- the working copy of
+ * the right-hand sides and the launch descriptors -- lives in one fixed 8 MiB array compiled
+ * into the library (every GPU that loads libdds holds it until the process exits): at most 256
+ * right-hand sides and nrhs * M^n * (16 bytes in DDS_FP64, 8 in DDS_MIXED) <= 8 MiB - 16 KiB,
+ * larger requests return DDS_EINVAL with the sizes in dds_last_error.  The call makes no
+ * cudaMalloc / cudaFree.  The first call on a device looks up the array's device address (once
+ * per device, with that device current); make that first call before any stream capture.
+ * Every call on a device shares the one array and leaves its contents behind: calls that
+ * overlap on the GPU (other contexts or streams on the same device) race on it. */
+dds_status dds_local_solve_noalloc(dds_ctx *ctx, int sub, const void *b, int nrhs, void *x);
+
 /* dds_set_stream -- run all later work of ctx on the given cudaStream_t (NULL = the context's
  * own stream).  Calls still return only after their work has completed. */
 dds_status dds_set_stream(dds_ctx *ctx, void *cuda_stream);

@@ -1088,3 +1088,105 @@ void dds_destroy(dds_ctx *ctx) {
 }
 
 }  // extern "C"
+
+// ============================================================================================
+// Allocation-free local solve
+//
+// Some callers cannot let this library call cudaMalloc: a host program whose device memory is
+// fully reserved by another allocator (a framework's caching allocator, a fixed serving budget)
+// gets an out-of-memory error or evicts its own cache, and every cudaMalloc / cudaFree may
+// synchronise the whole device, stalling that caller's other streams.  dds_local_solve_noalloc
+// gives them the block-tridiagonal local solve with all of its scratch (the working copy of the
+// right-hand sides and the launch descriptors) in the fixed device array below, which is part
+// of the loaded module: every GPU that loads libdds holds these bytes until the process exits.
+// ============================================================================================
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(8) << 20;   // 8 MiB per device
+constexpr size_t kStaticDescBytes = size_t(16) << 10;     // first 16 KiB: column/panel lists
+constexpr int kStaticMaxRhs = 256;
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char dds_static_scratch[kStaticScratchBytes];
+static_assert(kStaticMaxRhs * (sizeof(Col) + sizeof(Panel)) <= kStaticDescBytes,
+              "descriptor area too small");
+
+std::mutex g_static_mu;
+void *g_static_addr[kMaxDevices] = {nullptr};
+
+// device address of dds_static_scratch on the current device (looked up once per device)
+cudaError_t static_scratch_address(void **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, dds_static_scratch);
+    if (e != cudaSuccess) return e;
+    g_static_addr[dev] = p;
+  }
+  *out = g_static_addr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" dds_status dds_local_solve_noalloc(dds_ctx *ctx, int sub, const void *b, int nrhs,
+                                              void *x) {
+  if (!ctx) return DDS_EINVAL;
+  Busy busy(ctx);
+  if (!busy.ok) return DDS_EBUSY;
+  ctx->err.clear();
+  const Geom &g = ctx->g;
+  if (!b || !x || nrhs <= 0 || sub < 0 || sub >= g.nsub) { ctx->err = "invalid argument"; return DDS_EINVAL; }
+  if (!is_device_ptr(b) || !is_device_ptr(x)) {
+    ctx->err = "dds_local_solve_noalloc needs device pointers for b and x";
+    return DDS_EINVAL;
+  }
+  const bool mixed = ctx->precision == DDS_MIXED;
+  const size_t elem = mixed ? sizeof(float2) : sizeof(double2);
+  const long long n = (long long)nrhs * g.Nloc;
+  if (nrhs > kStaticMaxRhs || (size_t)n * elem > kStaticScratchBytes - kStaticDescBytes) {
+    ctx->err = "dds_local_solve_noalloc: " + std::to_string(nrhs) + " right-hand sides of " +
+               std::to_string(g.Nloc) + " nodes need " + std::to_string((size_t)n * elem) +
+               " scratch bytes; the static scratch holds " +
+               std::to_string(kStaticScratchBytes - kStaticDescBytes) + " (and at most " +
+               std::to_string(kStaticMaxRhs) + " right-hand sides)";
+    return DDS_EINVAL;
+  }
+  void *base = nullptr;
+  CK(static_scratch_address(&base));
+  unsigned char *scratch = static_cast<unsigned char *>(base);
+  Col *dcols = reinterpret_cast<Col *>(scratch);
+  Panel *dpans = reinterpret_cast<Panel *>(scratch + kStaticMaxRhs * sizeof(Col));
+  void *work = scratch + kStaticDescBytes;
+  // launch descriptors, built on the stack and copied into the static scratch
+  Col cols[kStaticMaxRhs];
+  Panel pans[kStaticMaxRhs];
+  const int pc = std::min(4, max_pc_for(ctx, elem));
+  int npan = 0;
+  for (int q = 0; q < nrhs; ++q) cols[q] = Col{sub, q, q, 0};
+  for (int i = 0; i < nrhs; i += pc) pans[npan++] = Panel{i, std::min(pc, nrhs - i), ctx->fac_of_sub[sub], 0};
+  cudaStream_t st = ctx->stream;
+  CK(cudaMemcpyAsync(dcols, cols, nrhs * sizeof(Col), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(dpans, pans, npan * sizeof(Panel), cudaMemcpyHostToDevice, st));
+  const double2 *bd = static_cast<const double2 *>(b);
+  double2 *xd = static_cast<double2 *>(x);
+  if (mixed) {
+    float2 *w = static_cast<float2 *>(work);
+    LAUNCH(launch_copy_local<float>(st, n, bd, w, 1));
+    LAUNCHK(DDS_K_SUBST, launch_subst<float>(st, g, npan, dpans, dcols, ctx->sinv32.as<float2>(),
+                                             ctx->cpl32.as<float2>(), w, pc));
+    LAUNCH(launch_copy_local_back<float>(st, n, w, xd));
+  } else {
+    double2 *w = static_cast<double2 *>(work);
+    LAUNCH(launch_copy_local<double>(st, n, bd, w, 1));
+    LAUNCHK(DDS_K_SUBST, launch_subst<double>(st, g, npan, dpans, dcols, ctx->sinv64.as<double2>(),
+                                              ctx->cpl64.as<double2>(), w, pc));
+    LAUNCH(launch_copy_local_back<double>(st, n, w, xd));
+  }
+  CK(cudaStreamSynchronize(st));
+  return DDS_OK;
+}

@@ -24,7 +24,7 @@ PLAN = {"auto": 0, "direct": 1, "trace": 2}
 
 EXPORTS = ["dds_setup", "dds_sweep", "dds_solve", "dds_apply", "dds_local_solve",
            "dds_set_stream", "dds_get_info", "dds_kernel_launches", "dds_last_error",
-           "dds_destroy", "dds_profile", "dds_profile_read"]
+           "dds_destroy", "dds_profile", "dds_profile_read", "dds_local_solve_noalloc"]
 KERNEL_KINDS = {"assemble": 0, "subst": 1, "extract": 2, "trace_step": 3, "krylov": 4,
                 "other": 5}
 
@@ -68,6 +68,7 @@ def load(path: str = LIB_PATH):
                               ctypes.POINTER(ctypes.c_double)]
     lib.dds_apply.argtypes = [vp, vp, ctypes.c_int, vp]
     lib.dds_local_solve.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, vp]
+    lib.dds_local_solve_noalloc.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, vp]
     lib.dds_set_stream.argtypes = [vp, vp]
     lib.dds_get_info.argtypes = [vp, ctypes.POINTER(_Info)]
     lib.dds_kernel_launches.argtypes = [vp]
@@ -80,7 +81,8 @@ def load(path: str = LIB_PATH):
     lib.dds_profile_read.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
                                      ctypes.POINTER(ctypes.c_double)]
     for name in ["dds_setup", "dds_sweep", "dds_solve", "dds_apply", "dds_local_solve",
-                 "dds_set_stream", "dds_get_info", "dds_profile", "dds_profile_read"]:
+                 "dds_set_stream", "dds_get_info", "dds_profile", "dds_profile_read",
+                 "dds_local_solve_noalloc"]:
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -211,6 +213,15 @@ class Context:
         self._bind_stream(b, x)
         self._check(self._lib.dds_local_solve(self._h, int(sub), self._ptr(b), nrhs, self._ptr(x)))
         return x
+
+    def local_solve_noalloc(self, sub, b, out):
+        """Local solve whose scratch is the library's fixed device array (no allocation in
+        the call): b and out must be preallocated CUDA tensors."""
+        nrhs = 1 if b.ndim == self.dim else int(b.shape[0])
+        self._bind_stream(b, out)
+        self._check(self._lib.dds_local_solve_noalloc(self._h, int(sub), self._ptr(b), nrhs,
+                                                      self._ptr(out)))
+        return out
 
     def info(self):
         inf = _Info()
