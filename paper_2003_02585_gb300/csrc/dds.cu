@@ -79,15 +79,18 @@ struct dds_ctx {
   int nsteps = 0, ndirs = 0;
   // device tables
   DBuf sinv64, sinv32, cpl64, cpl32, coef64, coef32, k2glob, gmap64, gmap32, status;
+  DBuf errflag;  // set by kernels whose bounded waits gave up
   DBuf an_glob[3], iah_glob[3];
+  DBuf stc0, stcp[3];  // global stencil (centre, coupling to +e_a)
   Tables tb{};
   // per-call workspaces
   std::map<int, std::unique_ptr<CallPlan>> plans;
   std::map<int, std::vector<int>> routes;  // rounds -> route[L][6]
   DBuf route_dev;
   int route_rounds = -1;
+  std::vector<int> in_mask, out_mask;  // per sweep: sides that can receive / must send a trace
   DBuf work, gtr, acc, rawf, bbuf, stage_in, stage_out, dots_part, dots_out, coefbuf, scalebuf;
-  std::vector<std::unique_ptr<DBuf>> Vb, Zb;
+  DBuf Vbig, Zbig;   // Krylov bases
   // profiler: event pairs around launches, folded into per-kind totals on read
   bool profiling = false;
   std::vector<std::array<cudaEvent_t, 2>> ev_pool;
@@ -255,6 +258,14 @@ int pick_pc(int ncols, int max_pc) {
   return pc;
 }
 
+int pick_pc_stream(const Geom &g, int ncols) {
+  // the streamed kernel holds one CTA per SM: the narrowest panel that fits the columns into
+  // one wave of 152 CTAs, widened further only while the shared memory allows
+  int pc = 1;
+  while (pc < 16 && (ncols + pc - 1) / pc > 152 && subst_stream_ok(g, pc * 2)) pc *= 2;
+  return subst_stream_ok(g, pc) ? pc : 0;
+}
+
 void add_panels(const std::vector<Col> &cols, int c0, int c1, const std::vector<int> &fac, int pc,
                 std::vector<Panel> &panels) {
   int i = c0;
@@ -296,12 +307,11 @@ CallPlan *get_plan(dds_ctx *ctx, int nrhs) {
       for (int r = 0; r < nrhs; ++r)
         cols.push_back(Col{subs[i], r, (int)(cols.size() - sp.col_off), 0});
     sp.ncols = (int)cols.size() - sp.col_off;
-    if (trace) {  // trace-step panels: rows are split over CTAs too, so narrower panels suffice
-      int pc = 1;
-      while (pc * 2 <= pc_cap && sp.ncols / (pc * 2) >= 16) pc *= 2;
-      sp.pc = pc;
+    if (trace) {  // trace-step panels of 8 columns (4 or 2 where the inputs would not fit)
+      sp.pc = pc_cap;
     } else {
-      sp.pc = pick_pc(sp.ncols, pc_cap);
+      const int spc = ctx->precision == DDS_MIXED ? pick_pc_stream(ctx->g, sp.ncols) : 0;
+      sp.pc = spc > 0 ? spc : pick_pc(sp.ncols, pc_cap);
     }
     sp.pan_off = (int)panels.size();
     add_panels(cols, sp.col_off, sp.col_off + sp.ncols, ctx->fac_of_sub, sp.pc, panels);
@@ -311,7 +321,8 @@ CallPlan *get_plan(dds_ctx *ctx, int nrhs) {
   cp->all = emit(order, maxpc, false);
   for (int dir = 0; dir < ctx->ndirs; ++dir)
     for (int s = 0; s < ctx->nsteps; ++s) cp->steps.push_back(emit(ctx->step_subs[dir][s], maxpc, false));
-  const int tmax = (ctx->g.T * 4 * (int)elem <= 96 * 1024) ? 4 : 2;
+  int tmax = 8;
+  while (tmax > 4 && trace_step_smem(ctx->g, tmax, elem) > 227 * 1024) tmax /= 2;
   for (int dir = 0; dir < ctx->ndirs; ++dir)
     for (int s = 0; s < ctx->nsteps; ++s) cp->tsteps.push_back(emit(ctx->step_subs[dir][s], tmax, true));
   if (upload(cp->cols, cols, ctx->stream) != cudaSuccess) return nullptr;
@@ -325,7 +336,43 @@ dds_status set_route(dds_ctx *ctx, int rounds) {
   if (ctx->route_rounds == rounds) return DDS_OK;
   const std::vector<int> r = build_route(ctx->g.dim, rounds);
   CK(upload(ctx->route_dev, r, ctx->stream));
+  const int L = ctx->ndirs * rounds, ns = 2 * ctx->g.dim;
+  ctx->in_mask.assign(L, 0);
+  ctx->out_mask.assign(L, 0);
+  for (int l = 0; l < L; ++l)
+    for (int d = 0; d < ns; ++d) {
+      const int lp = r[l * 6 + d];
+      if (lp < 0) continue;
+      ctx->out_mask[l] |= 1 << d;          // side d of a sweep-l solve sends a trace
+      ctx->in_mask[lp] |= 1 << (d ^ 1);    // ... which the neighbour receives on side d^1
+    }
   ctx->route_rounds = rounds;
+  return DDS_OK;
+}
+
+// substitutions of a panel list: the shared-memory-streamed FP32 kernel where it fits (pc up to
+// 16), else the direct-load kernel (pc up to 8)
+template <typename R>
+cudaError_t subst_any(dds_ctx *ctx, int npan, const Panel *pans, const Col *cols,
+                      const typename Cx<R>::T *sinv, const typename Cx<R>::T *cpl,
+                      typename Cx<R>::T *work, int pc) {
+  if constexpr (sizeof(R) == 4) {
+    if (subst_stream_ok(ctx->g, pc))
+      return launch_subst_stream(ctx->stream, ctx->g, npan, pans, cols, sinv, cpl, work, pc,
+                                 ctx->errflag.as<int>());
+  }
+  return launch_subst<R>(ctx->stream, ctx->g, npan, pans, cols, sinv, cpl, work, pc);
+}
+
+dds_status check_errflag(dds_ctx *ctx) {
+  int flag = 0;
+  CK(cudaMemcpyAsync(&flag, ctx->errflag.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (flag != 0) {
+    CK(cudaMemsetAsync(ctx->errflag.p, 0, sizeof(int), ctx->stream));
+    ctx->err = "a bounded device-side wait gave up (code " + std::to_string(flag) + ")";
+    return DDS_ETIMEOUT;
+  }
   return DDS_OK;
 }
 
@@ -368,23 +415,20 @@ dds_status run_ddm(dds_ctx *ctx, const double2 *b, int nrhs, double2 *u, int rou
         const StepPlan &sp = cp->steps[dir * ctx->nsteps + s];
         if (sp.ncols == 0) continue;
         LAUNCHK(DDS_K_ASSEMBLE, launch_assemble<R>(st, g, ctx->tb, sp.ncols, cols + sp.col_off, work, b, nullptr,
-                                  l == 0, gtr + l * slot, (long long)g.nsub * g.T, g.T));
-        LAUNCHK(DDS_K_SUBST, launch_subst<R>(st, g, sp.npanels, pans + sp.pan_off, cols, sinv, cpl, work, sp.pc));
+                                  l == 0, gtr + l * slot, (long long)g.nsub * g.T, g.T, 1, 0));
+        LAUNCHK(DDS_K_SUBST, subst_any<R>(ctx, sp.npanels, pans + sp.pan_off, cols, sinv, cpl, work, sp.pc));
         LAUNCHK(DDS_K_EXTRACT, launch_extract<R>(st, g, sp.ncols, cols + sp.col_off, work, u, 1, nullptr, gtr,
                                  route, l, nrhs));
       }
     }
   } else {
-    CK(ctx->acc.ensure(slot * sizeof(C)));
     CK(ctx->rawf.ensure(slot * sizeof(C)));
-    CK(cudaMemsetAsync(ctx->acc.p, 0, slot * sizeof(C), st));
-    C *acc = ctx->acc.as<C>();
     C *rawf = ctx->rawf.as<C>();
     const StepPlan &all = cp->all;
     // own sources: x_f = A_R^{-1} b_own; keep its raw trace lines
     LAUNCHK(DDS_K_ASSEMBLE, launch_assemble<R>(st, g, ctx->tb, all.ncols, cols + all.col_off, work, b, nullptr, 1,
-                              (const C *)nullptr, 0, 0));
-    LAUNCHK(DDS_K_SUBST, launch_subst<R>(st, g, all.npanels, pans + all.pan_off, cols, sinv, cpl, work, all.pc));
+                              (const C *)nullptr, 0, 0, 1, 0));
+    LAUNCHK(DDS_K_SUBST, subst_any<R>(ctx, all.npanels, pans + all.pan_off, cols, sinv, cpl, work, all.pc));
     LAUNCHK(DDS_K_EXTRACT, launch_extract<R>(st, g, all.ncols, cols + all.col_off, work, u, 0, rawf,
                              (C *)nullptr, route, 0, nrhs));
     // sweeps: per step, traces of the whole step set through the trace map
@@ -393,14 +437,15 @@ dds_status run_ddm(dds_ctx *ctx, const double2 *b, int nrhs, double2 *u, int rou
       for (int s = 0; s < ctx->nsteps; ++s) {
         const StepPlan &sp = cp->tsteps[dir * ctx->nsteps + s];
         if (sp.ncols == 0) continue;
-        LAUNCHK(DDS_K_TRACE_STEP, launch_trace_step<R>(st, g, sp.npanels, pans + sp.pan_off, cols, gmap, gtr, acc,
-                                    l == 0 ? rawf : nullptr, route, l, nrhs, sp.pc));
+        LAUNCHK(DDS_K_TRACE_STEP, launch_trace_step<R>(st, g, sp.npanels, pans + sp.pan_off, cols, gmap, gtr,
+                                    l == 0 ? rawf : nullptr, route, l, nrhs, sp.pc,
+                                    ctx->in_mask[l], ctx->out_mask[l], ctx->errflag.as<int>()));
       }
     }
     // own nodes: u = A_R^{-1}(b_own + potentials of all traces received in every sweep)
     LAUNCHK(DDS_K_ASSEMBLE, launch_assemble<R>(st, g, ctx->tb, all.ncols, cols + all.col_off, work, b, nullptr, 1,
-                              acc, (long long)g.nsub * g.T, g.T));
-    LAUNCHK(DDS_K_SUBST, launch_subst<R>(st, g, all.npanels, pans + all.pan_off, cols, sinv, cpl, work, all.pc));
+                              gtr, (long long)g.nsub * g.T, g.T, L, slot));
+    LAUNCHK(DDS_K_SUBST, subst_any<R>(ctx, all.npanels, pans + all.pan_off, cols, sinv, cpl, work, all.pc));
     LAUNCHK(DDS_K_EXTRACT, launch_extract<R>(st, g, all.ncols, cols + all.col_off, work, u, 2, (C *)nullptr,
                              (C *)nullptr, route, 0, nrhs));
   }
@@ -442,8 +487,8 @@ dds_status build_trace_map(dds_ctx *ctx) {
   // computed in FP64 for every distinct factor; then the back-trace correction is folded in.
   const Geom &g = ctx->g;
   cudaStream_t st = ctx->stream;
-  const long long TT = (long long)g.T * g.T;
-  CK(ctx->gmap64.ensure(ctx->nfac * TT * sizeof(double2)));
+  const long long TT = gmap_elems(g, ctx->nfac);
+  CK(ctx->gmap64.ensure(TT * sizeof(double2)));
   const int chunk = std::min(g.T, 1024);
   CK(ctx->work.ensure((long long)chunk * g.Nloc * sizeof(double2)));
   std::vector<Col> cols(chunk);
@@ -464,15 +509,14 @@ dds_status build_trace_map(dds_ctx *ctx) {
       LAUNCH(launch_unit_traces<double>(st, g, ctx->tb, k0, nk, work));
       LAUNCHK(DDS_K_SUBST, launch_subst<double>(st, g, (int)pans.size(), dpans.as<Panel>(), dcols.as<Col>(),
                                   ctx->sinv64.as<double2>(), ctx->cpl64.as<double2>(), work, pc));
-      LAUNCH(launch_raw_lines<double>(st, g, nk, work, ctx->gmap64.as<double2>() + f * TT, k0));
+      LAUNCH(launch_raw_lines<double>(st, g, nk, work, ctx->gmap64.as<double2>(), f, k0));
       CK(cudaStreamSynchronize(st));
     }
-    LAUNCH(launch_gmap_backtrace(st, g, ctx->gmap64.as<double2>() + f * TT));
+    LAUNCH(launch_gmap_backtrace(st, g, ctx->gmap64.as<double2>(), f));
   }
   if (ctx->precision == DDS_MIXED) {
-    CK(ctx->gmap32.ensure(ctx->nfac * TT * sizeof(float2)));
-    LAUNCH(launch_convert_c64_c32(st, ctx->gmap64.as<double2>(), ctx->gmap32.as<float2>(),
-                                  ctx->nfac * TT));
+    CK(ctx->gmap32.ensure(TT * sizeof(float2)));
+    LAUNCH(launch_convert_c64_c32(st, ctx->gmap64.as<double2>(), ctx->gmap32.as<float2>(), TT));
   }
   CK(cudaStreamSynchronize(st));
   return DDS_OK;
@@ -504,6 +548,7 @@ dds_status setup_impl(dds_ctx *ctx, const dds_problem *p) {
   g.Nglob = (long long)g.G[0] * g.G[1] * g.G[2];
   g.Ml = g.M[p->dim - 1];
   g.Mb = (int)(g.Nloc / g.Ml);
+  g.St = ((long long)g.Mb * g.Mb + 1) / 2 * 2;
   g.nsides = 2 * p->dim;
   g.T = 0;
   for (int d = 0; d < 6; ++d) {
@@ -516,7 +561,7 @@ dds_status setup_impl(dds_ctx *ctx, const dds_problem *p) {
     g.Lt[d] = lt;
     g.T += 2 * lt;
   }
-  if (ctx->plan == DDS_PLAN_TRACE && (size_t)g.T * sizeof(double2) > 200 * 1024) {
+  if (ctx->plan == DDS_PLAN_TRACE && trace_step_smem(g, 4, sizeof(double2)) > 227 * 1024) {
     ctx->err = "trace vectors too long for the trace-operator plan (T = " + std::to_string(g.T) + ")";
     return DDS_EINVAL;
   }
@@ -652,8 +697,34 @@ dds_status setup_impl(dds_ctx *ctx, const dds_problem *p) {
     for (auto &v : ctx->step_subs[di])
       std::stable_sort(v.begin(), v.end(), [&](int a, int b) { return ctx->fac_of_sub[a] < ctx->fac_of_sub[b]; });
   }
+  // ---- global stencil of the J-scaled operator (centre and coupling to p + e_a per node)
+  std::vector<double2> st0(g.Nglob), stp[3];
+  for (int a = 0; a < dim; ++a) stp[a].resize(g.Nglob);
+  for (long long q = 0; q < g.Nglob; ++q) {
+    const int pp[3] = {(int)(q % g.G[0]), (int)((q / g.G[0]) % g.G[1]),
+                       (int)(q / ((long long)g.G[0] * g.G[1]))};
+    cd J(1.0, 0.0);
+    for (int a = 0; a < dim; ++a) J *= gan[a][pp[a]];
+    cd diag = k2g[q] * J;
+    for (int a = 0; a < dim; ++a) {
+      cd T(ih2, 0.0);
+      for (int b = 0; b < dim; ++b)
+        if (b != a) T *= gan[b][pp[b]];
+      diag -= T * (1.0 / gah[a][pp[a]] + 1.0 / gah[a][pp[a] + 1]);
+      const cd c = pp[a] + 1 < g.G[a] ? T / gah[a][pp[a] + 1] : cd(0.0, 0.0);
+      stp[a][q] = make_double2(c.real(), c.imag());
+    }
+    st0[q] = make_double2(diag.real(), diag.imag());
+  }
   // ---- upload tables
   cudaStream_t st = ctx->stream;
+  CK(upload(ctx->stc0, st0, st));
+  ctx->tb.c0 = ctx->stc0.as<double2>();
+  for (int a = 0; a < 3; ++a) {
+    if (a < dim) CK(upload(ctx->stcp[a], stp[a], st));
+    else CK(ctx->stcp[a].ensure(16));
+    ctx->tb.cp[a] = ctx->stcp[a].as<double2>();
+  }
   CK(upload(ctx->coef64, coef, st));
   CK(upload(ctx->coef32, coef32, st));
   CK(upload(ctx->k2glob, k2g, st));
@@ -679,12 +750,16 @@ dds_status setup_impl(dds_ctx *ctx, const dds_problem *p) {
   CK(upload(doffx, offx, st));
   if (dim == 3) CK(upload(doffy, offy, st));
   CK(upload(dcpl, cpl, st));
-  const long long sinv_elems = (long long)ctx->nfac * Ml * (long long)Mb * Mb;
+  const long long sinv_elems = (long long)ctx->nfac * Ml * g.St;
   CK(ctx->sinv64.ensure(sinv_elems * sizeof(double2)));
   CK(ctx->sinv32.ensure(sinv_elems * sizeof(float2)));
   CK(ctx->status.ensure(sizeof(int)));
   CK(cudaMemsetAsync(ctx->status.p, 0, sizeof(int), st));
-  LAUNCH(launch_factor(st, ctx->nfac, Mb, Ml, g.M[0], ddg.as<double2>(), doffx.as<double2>(),
+  CK(ctx->errflag.ensure(sizeof(int)));
+  CK(cudaMemsetAsync(ctx->errflag.p, 0, sizeof(int), st));
+  CK(cudaMemsetAsync(ctx->sinv64.p, 0, sinv_elems * sizeof(double2), st));
+  CK(cudaMemsetAsync(ctx->sinv32.p, 0, sinv_elems * sizeof(float2), st));
+  LAUNCH(launch_factor(st, ctx->nfac, Mb, Ml, g.St, g.M[0], ddg.as<double2>(), doffx.as<double2>(),
                        dim == 3 ? doffy.as<double2>() : nullptr, dcpl.as<double2>(),
                        ctx->sinv64.as<double2>(), ctx->sinv32.as<float2>(), ctx->status.as<int>()));
   int status = 0;
@@ -745,45 +820,41 @@ struct Busy {
 
 // ------------------------------------------------------------------------------------------
 // FGMRES (right preconditioned, x0 = 0, classical Gram-Schmidt twice, Givens rotations)
+// The basis lives in two contiguous device buffers V[maxit+1][nrhs][N], Z[maxit][nrhs][N];
+// Gram-Schmidt coefficients stay on the device between the dot and update kernels, and the
+// host reads them once per iteration for the Hessenberg / Givens bookkeeping.
 // ------------------------------------------------------------------------------------------
 dds_status fgmres(dds_ctx *ctx, const double2 *b, int nrhs, double2 *x, double tol, int maxit,
                   int rounds, int *iters, std::vector<double> &relres) {
   const Geom &g = ctx->g;
   cudaStream_t st = ctx->stream;
   const long long N = g.Nglob;
-  const size_t vbytes = (size_t)nrhs * N * sizeof(double2);
-  auto vec = [&](std::vector<std::unique_ptr<DBuf>> &pool, int i) -> double2 * {
-    while ((int)pool.size() <= i) pool.push_back(std::make_unique<DBuf>());
-    if (pool[i]->ensure(vbytes) != cudaSuccess) return nullptr;
-    return pool[i]->as<double2>();
-  };
-  const int nblk = 64;
-  CK(ctx->dots_part.ensure((size_t)nrhs * (maxit + 1) * nblk * sizeof(double2)));
-  CK(ctx->dots_out.ensure((size_t)nrhs * (maxit + 1) * sizeof(double2)));
-  CK(ctx->coefbuf.ensure((size_t)nrhs * (maxit + 1) * sizeof(double2)));
-  CK(ctx->scalebuf.ensure((size_t)nrhs * sizeof(double)));
-  auto dots = [&](const double2 *V0, int nv, const double2 *w, std::vector<cd> &out) -> dds_status {
-    LAUNCHK(DDS_K_KRYLOV, launch_dots(st, N, nrhs, nv, V0, (long long)nrhs * N, N, w, N, ctx->dots_part.as<double2>(),
-                       ctx->dots_out.as<double2>(), nblk));
-    out.resize((size_t)nrhs * nv);
-    CK(cudaMemcpyAsync(out.data(), ctx->dots_out.p, out.size() * sizeof(double2), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    return DDS_OK;
-  };
-  // the V vectors are separate buffers: gather pointers by copying into contiguous calls
-  // (V_i lives in Vb[i]; launch_dots/sub_combination take a base and a stride, so each basis
-  // vector is processed with nv = 1 calls when buffers are not contiguous)
-  std::vector<cd> beta_c;
-  double2 *V0 = vec(ctx->Vb, 0);
-  if (!V0) { ctx->err = "out of device memory for the Krylov basis"; return DDS_ENOMEM; }
-  if (dots(b, 1, b, beta_c) != DDS_OK) return DDS_ECUDA;
-  std::vector<double> beta(nrhs), invs(nrhs);
-  for (int r = 0; r < nrhs; ++r) {
-    beta[r] = std::sqrt(std::max(beta_c[r].real(), 0.0));
-    invs[r] = beta[r] > 0 ? 1.0 / beta[r] : 0.0;
+  const long long vs = (long long)nrhs * N;  // elements per basis vector (all RHS)
+  const size_t vbytes = (size_t)vs * sizeof(double2);
+  if (ctx->Vbig.ensure((size_t)(maxit + 1) * vbytes) != cudaSuccess ||
+      ctx->Zbig.ensure((size_t)maxit * vbytes) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->err = "out of device memory for the Krylov basis";
+    return DDS_ENOMEM;
   }
-  CK(cudaMemcpyAsync(ctx->scalebuf.p, invs.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
-  LAUNCHK(DDS_K_KRYLOV, launch_scale_vec(st, N, nrhs, b, ctx->scalebuf.as<double>(), V0));
+  double2 *V = ctx->Vbig.as<double2>();
+  double2 *Z = ctx->Zbig.as<double2>();
+  const int chunk = dots_chunk();
+  const int nblk = (int)((N + chunk - 1) / chunk);
+  CK(ctx->dots_part.ensure((size_t)nrhs * (maxit + 1) * nblk * sizeof(double2)));
+  // hdev: [h1: nrhs*(j+1)] [h2: nrhs*(j+1)] [norm^2: nrhs]
+  CK(ctx->dots_out.ensure((size_t)nrhs * (2 * maxit + 3) * sizeof(double2)));
+  CK(ctx->coefbuf.ensure((size_t)nrhs * (maxit + 1) * sizeof(double2)));
+  double2 *hdev = ctx->dots_out.as<double2>();
+  double2 *part = ctx->dots_part.as<double2>();
+  std::vector<double2> hh((size_t)nrhs * (2 * maxit + 3));
+  // beta = ||b||, V_0 = b / beta
+  LAUNCHK(DDS_K_KRYLOV, launch_dots(st, N, nrhs, 1, b, 0, N, b, N, part, hdev, nblk));
+  LAUNCHK(DDS_K_KRYLOV, launch_scale_by_norm(st, N, nrhs, b, hdev, V));
+  CK(cudaMemcpyAsync(hh.data(), hdev, nrhs * sizeof(double2), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  std::vector<double> beta(nrhs);
+  for (int r = 0; r < nrhs; ++r) beta[r] = std::sqrt(std::max(hh[r].x, 0.0));
   const int m = maxit;
   std::vector<cd> H((size_t)nrhs * (m + 1) * m, cd(0, 0)), cs((size_t)nrhs * m), sn((size_t)nrhs * m),
       gg((size_t)nrhs * (m + 1), cd(0, 0));
@@ -795,39 +866,32 @@ dds_status fgmres(dds_ctx *ctx, const double2 *b, int nrhs, double2 *x, double t
   }
   auto Hat = [&](int r, int i, int j) -> cd & { return H[((size_t)r * (m + 1) + i) * m + j]; };
   int k = 0;
-  std::vector<cd> hc, tmp;
   for (int j = 0; j < m; ++j) {
-    double2 *Vj = vec(ctx->Vb, j), *Zj = vec(ctx->Zb, j), *W = vec(ctx->Vb, j + 1);
-    if (!Vj || !Zj || !W) { ctx->err = "out of device memory for the Krylov basis"; return DDS_ENOMEM; }
+    double2 *Vj = V + j * vs, *Zj = Z + j * vs, *W = V + (j + 1) * vs;
     dds_status rs = ddm(ctx, Vj, nrhs, Zj, rounds);
     if (rs != DDS_OK) return rs;
     LAUNCHK(DDS_K_KRYLOV, launch_apply_A(st, g, ctx->tb, nrhs, Zj, W, 0));
-    std::vector<cd> hsum((size_t)nrhs * (j + 1), cd(0, 0));
+    const int nv = j + 1;
+    double2 *h1 = hdev, *h2 = hdev + (size_t)nrhs * nv, *hn = hdev + (size_t)2 * nrhs * nv;
     for (int pass = 0; pass < 2; ++pass) {
-      for (int i = 0; i <= j; ++i) {
-        if (dots(ctx->Vb[i]->as<double2>(), 1, W, hc) != DDS_OK) return DDS_ECUDA;
-        std::vector<double2> cf(nrhs);
-        for (int r = 0; r < nrhs; ++r) {
-          hsum[(size_t)r * (j + 1) + i] += hc[r];
-          cf[r] = make_double2(hc[r].real(), hc[r].imag());
-        }
-        CK(cudaMemcpyAsync(ctx->coefbuf.p, cf.data(), nrhs * sizeof(double2), cudaMemcpyHostToDevice, st));
-        LAUNCHK(DDS_K_KRYLOV, launch_sub_combination(st, N, nrhs, 1, ctx->Vb[i]->as<double2>(), 0, N,
-                                      ctx->coefbuf.as<double2>(), W, N, -1.0));
-      }
+      double2 *hp = pass == 0 ? h1 : h2;
+      LAUNCHK(DDS_K_KRYLOV, launch_dots(st, N, nrhs, nv, V, vs, N, W, N, part, hp, nblk));
+      LAUNCHK(DDS_K_KRYLOV, launch_sub_combination(st, N, nrhs, nv, V, vs, N, hp, W, N, -1.0));
     }
-    if (dots(W, 1, W, hc) != DDS_OK) return DDS_ECUDA;
-    for (int r = 0; r < nrhs; ++r) {
-      const double hn = std::sqrt(std::max(hc[r].real(), 0.0));
-      invs[r] = hn > 0 ? 1.0 / hn : 0.0;
-      for (int i = 0; i <= j; ++i) Hat(r, i, j) = hsum[(size_t)r * (j + 1) + i];
-      Hat(r, j + 1, j) = hn;
-    }
-    CK(cudaMemcpyAsync(ctx->scalebuf.p, invs.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
-    LAUNCHK(DDS_K_KRYLOV, launch_scale_vec(st, N, nrhs, W, ctx->scalebuf.as<double>(), W));
+    LAUNCHK(DDS_K_KRYLOV, launch_dots(st, N, nrhs, 1, W, 0, N, W, N, part, hn, nblk));
+    LAUNCHK(DDS_K_KRYLOV, launch_scale_by_norm(st, N, nrhs, W, hn, W));
+    CK(cudaMemcpyAsync(hh.data(), hdev, (size_t)nrhs * (2 * nv + 1) * sizeof(double2),
+                       cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
     k = j + 1;
     bool all = true;
     for (int r = 0; r < nrhs; ++r) {
+      const double hnorm = std::sqrt(std::max(hh[(size_t)2 * nrhs * nv + r].x, 0.0));
+      for (int i = 0; i <= j; ++i) {
+        const double2 a = hh[(size_t)r * nv + i], bq = hh[(size_t)nrhs * nv + (size_t)r * nv + i];
+        Hat(r, i, j) = cd(a.x + bq.x, a.y + bq.y);
+      }
+      Hat(r, j + 1, j) = hnorm;
       if (done[r]) continue;
       for (int i = 0; i < j; ++i) {  // previous rotations
         const cd a = Hat(r, i, j), bb = Hat(r, i + 1, j);
@@ -848,46 +912,44 @@ dds_status fgmres(dds_ctx *ctx, const double2 *b, int nrhs, double2 *x, double t
       gg[(size_t)r * (m + 1) + j] = c * gj;
       kused[r] = j + 1;
       const double res = std::abs(gg[(size_t)r * (m + 1) + j + 1]) / beta[r];
-      if (res < tol || invs[r] == 0.0) done[r] = 1;
+      if (res < tol || hnorm == 0.0) done[r] = 1;
       else all = false;
     }
     if (all) break;
   }
   *iters = k;
-  // x = sum_i Z_i y_i per RHS
-  CK(cudaMemsetAsync(x, 0, vbytes, st));
-  std::vector<std::vector<cd>> y(nrhs);
+  // x = sum_i Z_i y_i per RHS (one update kernel over all k basis vectors)
+  std::vector<double2> ycoef((size_t)nrhs * std::max(k, 1), make_double2(0.0, 0.0));
   for (int r = 0; r < nrhs; ++r) {
     const int kr = kused[r];
-    y[r].assign(kr, cd(0, 0));
+    std::vector<cd> y(kr, cd(0, 0));
     for (int i = kr - 1; i >= 0; --i) {
       cd s = gg[(size_t)r * (m + 1) + i];
-      for (int q = i + 1; q < kr; ++q) s -= Hat(r, i, q) * y[r][q];
-      y[r][i] = s / Hat(r, i, i);
+      for (int q = i + 1; q < kr; ++q) s -= Hat(r, i, q) * y[q];
+      y[i] = s / Hat(r, i, i);
     }
+    for (int i = 0; i < kr; ++i) ycoef[(size_t)r * k + i] = make_double2(y[i].real(), y[i].imag());
   }
-  for (int i = 0; i < k; ++i) {
-    std::vector<double2> cf(nrhs);
-    for (int r = 0; r < nrhs; ++r) {
-      const cd v = i < kused[r] ? y[r][i] : cd(0, 0);
-      cf[r] = make_double2(v.real(), v.imag());
-    }
-    CK(cudaMemcpyAsync(ctx->coefbuf.p, cf.data(), nrhs * sizeof(double2), cudaMemcpyHostToDevice, st));
-    LAUNCHK(DDS_K_KRYLOV, launch_sub_combination(st, N, nrhs, 1, ctx->Zb[i]->as<double2>(), 0, N,
-                                  ctx->coefbuf.as<double2>(), x, N, 1.0));
+  CK(cudaMemsetAsync(x, 0, vbytes, st));
+  if (k > 0) {
+    CK(cudaMemcpyAsync(ctx->coefbuf.p, ycoef.data(), (size_t)nrhs * k * sizeof(double2),
+                       cudaMemcpyHostToDevice, st));
+    LAUNCHK(DDS_K_KRYLOV, launch_sub_combination(st, N, nrhs, k, Z, vs, N, ctx->coefbuf.as<double2>(),
+                                                 x, N, 1.0));
   }
-  // true residual
-  double2 *Rv = vec(ctx->Vb, 0);
+  // true residual: R = A x - b
+  double2 *Rv = V;
   LAUNCHK(DDS_K_KRYLOV, launch_apply_A(st, g, ctx->tb, nrhs, x, Rv, 0));
-  std::vector<double2> mone(nrhs, make_double2(-1.0, 0.0));
+  std::vector<double2> mone(nrhs, make_double2(1.0, 0.0));
   CK(cudaMemcpyAsync(ctx->coefbuf.p, mone.data(), nrhs * sizeof(double2), cudaMemcpyHostToDevice, st));
-  // Rv = A x - b  ->  Rv += (-1) * b
-  LAUNCHK(DDS_K_KRYLOV, launch_sub_combination(st, N, nrhs, 1, b, 0, N, ctx->coefbuf.as<double2>(), Rv, N, 1.0));
-  if (dots(Rv, 1, Rv, hc) != DDS_OK) return DDS_ECUDA;
+  LAUNCHK(DDS_K_KRYLOV, launch_sub_combination(st, N, nrhs, 1, b, 0, N, ctx->coefbuf.as<double2>(), Rv, N, -1.0));
+  LAUNCHK(DDS_K_KRYLOV, launch_dots(st, N, nrhs, 1, Rv, 0, N, Rv, N, part, hdev, nblk));
+  CK(cudaMemcpyAsync(hh.data(), hdev, nrhs * sizeof(double2), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
   relres.assign(nrhs, 0.0);
   bool ok = true;
   for (int r = 0; r < nrhs; ++r) {
-    relres[r] = beta[r] > 0 ? std::sqrt(std::max(hc[r].real(), 0.0)) / beta[r] : 0.0;
+    relres[r] = beta[r] > 0 ? std::sqrt(std::max(hh[r].x, 0.0)) / beta[r] : 0.0;
     if (!(relres[r] < tol)) ok = false;
   }
   return ok ? DDS_OK : DDS_ENOCONV;
@@ -937,6 +999,8 @@ dds_status dds_sweep(dds_ctx *ctx, const void *f, int nrhs, void *u, int rounds)
   LAUNCHK(DDS_K_KRYLOV, launch_scale_J(ctx->stream, ctx->g, ctx->tb, nrhs, fd, ctx->bbuf.as<double2>()));
   r = ddm(ctx, ctx->bbuf.as<double2>(), nrhs, ud, rounds);
   if (r != DDS_OK) return r;
+  r = check_errflag(ctx);
+  if (r != DDS_OK) return r;
   return finish_out(ctx, u, bytes, uh);
 }
 
@@ -964,6 +1028,8 @@ dds_status dds_solve(dds_ctx *ctx, const void *f, int nrhs, void *u, double tol,
   std::vector<double> rel;
   dds_status rs = fgmres(ctx, ctx->bbuf.as<double2>(), nrhs, ud, tol, maxit, rounds, &it, rel);
   if (rs != DDS_OK && rs != DDS_ENOCONV) return rs;
+  r = check_errflag(ctx);
+  if (r != DDS_OK) return r;
   if (iters) *iters = it;
   if (relres) for (int q = 0; q < nrhs; ++q) relres[q] = rel[q];
   r = finish_out(ctx, u, bytes, uh);

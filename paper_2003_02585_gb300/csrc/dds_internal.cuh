@@ -64,6 +64,8 @@ struct Geom {
   int nsub;
   long long Nloc, Nglob;   // nodes of one extended subdomain / of the global extended grid
   int Mb, Ml;              // block size (nodes of a line/plane) and number of blocks
+  long long St;            // element stride between block inverses (Mb^2 rounded up to even,
+                           // so that every tile starts on a 16-byte boundary)
   int nsides;              // 2 * dim
   int Lt[6];               // line length of side d
   int toff[6];             // offset of side d in a trace vector
@@ -128,26 +130,47 @@ struct Tables {
                                 // entry q lies between nodes q-1 and q)
   const double *k2_glob;        // kappa^2 on the global extended grid
   double inv_h2;                // 1 / h^2
+  const double2 *c0;            // global stencil: centre coefficient per node
+  const double2 *cp[3];         // global stencil: coupling of node p to p + e_a (0 on the edge)
 };
+
+// Raise a kernel's dynamic shared-memory limit to the largest value a launch may ask for, once
+// per device (the attribute persists for the function on that device).
+template <typename F>
+inline cudaError_t smem_limit_once(F *kernel, bool (&done)[64]) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
+  return e;
+}
 
 // ------------------------------------------------------------------------------------------
 // launch wrappers (each returns the CUDA error of the launch)
 // ------------------------------------------------------------------------------------------
-cudaError_t launch_factor(cudaStream_t st, int nfac, int Mb, int Ml, int M0, const double2 *dg,
+cudaError_t launch_factor(cudaStream_t st, int nfac, int Mb, int Ml, long long St, int M0,
+                          const double2 *dg,
                           const double2 *offx, const double2 *offy, const double2 *cpl,
                           double2 *sinv64, float2 *sinv32, int *status);
 
 template <typename R>
 cudaError_t launch_assemble(cudaStream_t st, const Geom &g, const Tables &tb, int ncols,
-                            const Col *cols, typename Cx<R>::T *work, const double2 *f,
-                            const double2 *jglob_unused, int with_source,
+                            const Col *cols, typename Cx<R>::T *work, const double2 *b,
+                            const double2 *unused, int with_source,
                             const typename Cx<R>::T *traces, long long trace_rhs_stride,
-                            long long trace_sub_stride);
+                            long long trace_sub_stride, int nslots, long long slot_stride);
 
 template <typename R>
 cudaError_t launch_subst(cudaStream_t st, const Geom &g, int npanels, const Panel *panels,
                          const Col *cols, const typename Cx<R>::T *sinv,
                          const typename Cx<R>::T *cpl, typename Cx<R>::T *work, int pc);
+
+cudaError_t launch_subst_stream(cudaStream_t st, const Geom &g, int npanels, const Panel *panels,
+                                const Col *cols, const float2 *sinv, const float2 *cpl,
+                                float2 *work, int pc, int *err);
+bool subst_stream_ok(const Geom &g, int pc);
 
 template <typename R>
 cudaError_t launch_extract(cudaStream_t st, const Geom &g, int ncols, const Col *cols,
@@ -158,9 +181,9 @@ cudaError_t launch_extract(cudaStream_t st, const Geom &g, int ncols, const Col 
 template <typename R>
 cudaError_t launch_trace_step(cudaStream_t st, const Geom &g, int npanels, const Panel *panels,
                               const Col *cols, const typename Cx<R>::T *gmap,
-                              typename Cx<R>::T *g_traces, typename Cx<R>::T *acc,
-                              const typename Cx<R>::T *rawf, const int *route, int l, int nrhs,
-                              int pc);
+                              typename Cx<R>::T *g_traces, const typename Cx<R>::T *rawf,
+                              const int *route, int l, int nrhs, int pc, int in_mask,
+                              int out_mask, int *err);
 
 template <typename R>
 cudaError_t launch_unit_traces(cudaStream_t st, const Geom &g, const Tables &tb, int k0, int nk,
@@ -168,9 +191,11 @@ cudaError_t launch_unit_traces(cudaStream_t st, const Geom &g, const Tables &tb,
 
 template <typename R>
 cudaError_t launch_raw_lines(cudaStream_t st, const Geom &g, int nk, const typename Cx<R>::T *work,
-                             typename Cx<R>::T *gmapT, int k0);
+                             typename Cx<R>::T *gmap, int f, int k0);
 
-cudaError_t launch_gmap_backtrace(cudaStream_t st, const Geom &g, double2 *gmapT);
+cudaError_t launch_gmap_backtrace(cudaStream_t st, const Geom &g, double2 *gmap, int f);
+long long gmap_elems(const Geom &g, int nfac);
+size_t trace_step_smem(const Geom &g, int pc, size_t elem);
 cudaError_t launch_convert_c64_c32(cudaStream_t st, const double2 *in, float2 *out, long long n);
 template <typename R>
 cudaError_t launch_copy_local(cudaStream_t st, long long n, const double2 *in,
@@ -193,5 +218,8 @@ cudaError_t launch_sub_combination(cudaStream_t st, long long N, int nrhs, int n
                                    double sign);
 cudaError_t launch_scale_vec(cudaStream_t st, long long N, int nrhs, const double2 *in,
                              const double *inv_scale, double2 *out);
+cudaError_t launch_scale_by_norm(cudaStream_t st, long long N, int nrhs, const double2 *in,
+                                const double2 *nrm2, double2 *out);
+int dots_chunk();
 
 }  // namespace dds

@@ -15,7 +15,7 @@ __device__ inline double2 crecip(double2 z) {
   return make_double2(z.x / m, -z.y / m);
 }
 
-__global__ void __launch_bounds__(1024) k_factor(int Mb, int Ml, int M0,
+__global__ void __launch_bounds__(1024) k_factor(int Mb, int Ml, long long St, int M0,
                                                  const double2 *__restrict__ dg,
                                                  const double2 *__restrict__ offx,
                                                  const double2 *__restrict__ offy,
@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(1024) k_factor(int Mb, int Ml, int M0,
       __syncthreads();
     }
     // ---- store S_j^{-1} as [s][r] (thread r of a substitution reads along r)
-    const long long ob = ((long long)f * Ml + j) * MbMb;
+    const long long ob = ((long long)f * Ml + j) * St;
     for (long long idx = tid; idx < MbMb; idx += nt) {
       const int s = (int)(idx / Mb), r = (int)(idx % Mb);
       const double2 v = S[(long long)r * Mb + s];
@@ -128,14 +128,15 @@ __global__ void __launch_bounds__(1024) k_factor(int Mb, int Ml, int M0,
   }
 }
 
-cudaError_t launch_factor(cudaStream_t st, int nfac, int Mb, int Ml, int M0, const double2 *dg,
+cudaError_t launch_factor(cudaStream_t st, int nfac, int Mb, int Ml, long long St, int M0,
+                          const double2 *dg,
                           const double2 *offx, const double2 *offy, const double2 *cpl,
                           double2 *sinv64, float2 *sinv32, int *status) {
   const size_t smem = (size_t)Mb * Mb * sizeof(double2) + Mb * sizeof(double2) + Mb * sizeof(int);
   cudaError_t e = cudaFuncSetAttribute(k_factor, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  k_factor<<<nfac, 1024, smem, st>>>(Mb, Ml, M0, dg, offx, offy, cpl, sinv64, sinv32, status);
+  k_factor<<<nfac, 1024, smem, st>>>(Mb, Ml, St, M0, dg, offx, offy, cpl, sinv64, sinv32, status);
   return cudaGetLastError();
 }
 

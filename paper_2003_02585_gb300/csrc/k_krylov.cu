@@ -13,94 +13,114 @@ __device__ inline double2 crecip64(double2 z) {
 // (A u)_p = sum_a (prod_{b != a} alpha_b) / h^2 [ (u_{p+e_a} - u_p) / alpha_a(p+1/2)
 //                                               - (u_p - u_{p-e_a}) / alpha_a(p-1/2) ]
 //           + kappa^2 J u_p,          Dirichlet outside the extended grid.
+// The stencil is precomputed per node at set-up (tb.c0: centre, tb.cp[a]: coupling to p + e_a,
+// so the coupling to p - e_a is tb.cp[a][p - e_a]); each thread applies it to every RHS.
 __global__ void k_apply_A(Geom g, Tables tb, int nrhs, const double2 *__restrict__ u,
                           double2 *__restrict__ Au, int divide_by_J) {
-  const long long total = g.Nglob * nrhs;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const long long q = idx % g.Nglob;
-    const long long base = idx - q;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.Nglob;
+       q += (long long)gridDim.x * blockDim.x) {
     int p[3];
     p[0] = (int)(q % g.G[0]);
     p[1] = (int)((q / g.G[0]) % g.G[1]);
     p[2] = g.dim == 3 ? (int)(q / ((long long)g.G[0] * g.G[1])) : 0;
-    double2 an[3];
-    double2 J = make_double2(1.0, 0.0);
-    for (int a = 0; a < g.dim; ++a) {
-      an[a] = tb.an_glob64[a][p[a]];
-      J = cmul(J, an[a]);
+    const double2 c0 = tb.c0[q];
+    double2 cpv[3], cmv[3];
+    long long stride[3];
+    long long st = 1;
+    for (int a = 0; a < 3; ++a) {
+      stride[a] = st;
+      st *= g.G[a];
+      const bool on = a < g.dim;
+      cpv[a] = on && p[a] + 1 < g.G[a] ? tb.cp[a][q] : make_double2(0.0, 0.0);
+      cmv[a] = on && p[a] > 0 ? tb.cp[a][q - stride[a]] : make_double2(0.0, 0.0);
     }
-    const double2 uc = u[idx];
-    double2 sum = cmul(make_double2(tb.k2_glob[q] * J.x, tb.k2_glob[q] * J.y), uc);
-    long long stride = 1;
-    for (int a = 0; a < g.dim; ++a) {
-      double2 T = make_double2(tb.inv_h2, 0.0);
-      for (int b = 0; b < g.dim; ++b)
-        if (b != a) T = cmul(T, an[b]);
-      const double2 up = (p[a] + 1 < g.G[a]) ? u[idx + stride] : make_double2(0.0, 0.0);
-      const double2 um = (p[a] > 0) ? u[idx - stride] : make_double2(0.0, 0.0);
-      const double2 fl = cmul(csub(up, uc), tb.iah_glob64[a][p[a] + 1]);
-      const double2 bl = cmul(csub(uc, um), tb.iah_glob64[a][p[a]]);
-      sum = cadd(sum, cmul(T, csub(fl, bl)));
-      stride *= g.G[a];
+    double2 iJ = make_double2(1.0, 0.0);
+    if (divide_by_J) {
+      double2 J = make_double2(1.0, 0.0);
+      for (int a = 0; a < g.dim; ++a) J = cmul(J, tb.an_glob64[a][p[a]]);
+      iJ = crecip64(J);
     }
-    if (divide_by_J) sum = cmul(sum, crecip64(J));
-    Au[base + q] = sum;
+    for (int r = 0; r < nrhs; ++r) {
+      const double2 *ur = u + (long long)r * g.Nglob;
+      double2 sum = cmul(c0, ur[q]);
+      for (int a = 0; a < g.dim; ++a) {
+        if (p[a] + 1 < g.G[a]) cfma(sum, cpv[a], ur[q + stride[a]]);
+        if (p[a] > 0) cfma(sum, cmv[a], ur[q - stride[a]]);
+      }
+      if (divide_by_J) sum = cmul(sum, iJ);
+      Au[(long long)r * g.Nglob + q] = sum;
+    }
   }
 }
 
-__global__ void k_scale_J(Geom g, Tables tb, int nrhs, const double2 *__restrict__ f,
+__global__ void k_scale_J(Geom g, Tables tb, const double2 *__restrict__ f,
                           double2 *__restrict__ b) {
-  const long long total = g.Nglob * nrhs;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const long long q = idx % g.Nglob;
+  const long long base = (long long)blockIdx.y * g.Nglob;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.Nglob;
+       q += (long long)gridDim.x * blockDim.x) {
     int p[3];
     p[0] = (int)(q % g.G[0]);
     p[1] = (int)((q / g.G[0]) % g.G[1]);
     p[2] = g.dim == 3 ? (int)(q / ((long long)g.G[0] * g.G[1])) : 0;
     double2 J = make_double2(1.0, 0.0);
     for (int a = 0; a < g.dim; ++a) J = cmul(J, tb.an_glob64[a][p[a]]);
-    b[idx] = cmul(J, f[idx]);
+    b[base + q] = cmul(J, f[base + q]);
   }
 }
 
-// partial[(rhs * nv + i) * nblk + blk] = sum over the block's chunk of conj(V_i) * w
-__global__ void k_dots(long long N, int nv, const double2 *__restrict__ V, long long vsv,
-                       long long vsr, const double2 *__restrict__ w, long long wsr,
-                       double2 *__restrict__ partial) {
+// partial[(rhs * nv + i) * nblk + blk] = sum over the block's chunk of conj(V_i) * w.
+// The block's chunk of w is staged in shared memory once and reused for all nv vectors.
+constexpr int kDotThreads = 256;
+constexpr int kDotPerThread = 8;
+constexpr int kDotChunk = kDotThreads * kDotPerThread;
+
+__global__ void __launch_bounds__(kDotThreads) k_dots(long long N, int nv,
+                                                     const double2 *__restrict__ V, long long vsv,
+                                                     long long vsr, const double2 *__restrict__ w,
+                                                     long long wsr, double2 *__restrict__ partial) {
+  __shared__ double2 ws[kDotChunk];
+  __shared__ double red[2][kDotThreads / 32];
   const int blk = blockIdx.x, nblk = gridDim.x;
-  const int rhs = blockIdx.y, i = blockIdx.z;
-  const double2 *v = V + i * vsv + rhs * vsr;
+  const int rhs = blockIdx.y;
+  const long long n0 = (long long)blk * kDotChunk;
   const double2 *ww = w + rhs * wsr;
-  double sr = 0.0, si = 0.0;
-  for (long long n = blk * (long long)blockDim.x + threadIdx.x; n < N;
-       n += (long long)nblk * blockDim.x) {
-    const double2 a = v[n], b = ww[n];
-    sr = fma(a.x, b.x, sr);
-    sr = fma(a.y, b.y, sr);
-    si = fma(a.x, b.y, si);
-    si = fma(-a.y, b.x, si);
+  for (int e = threadIdx.x; e < kDotChunk; e += kDotThreads) {
+    const long long n = n0 + e;
+    ws[e] = n < N ? ww[n] : make_double2(0.0, 0.0);
   }
-  __shared__ double red[2][32];
-  for (int o = 16; o > 0; o >>= 1) {
-    sr += __shfl_down_sync(0xffffffffu, sr, o);
-    si += __shfl_down_sync(0xffffffffu, si, o);
-  }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) { red[0][warp] = sr; red[1][warp] = si; }
   __syncthreads();
-  if (warp == 0) {
-    const int nw = blockDim.x >> 5;
-    sr = lane < nw ? red[0][lane] : 0.0;
-    si = lane < nw ? red[1][lane] : 0.0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = 0; i < nv; ++i) {
+    const double2 *v = V + i * vsv + rhs * vsr;
+    double sr = 0.0, si = 0.0;
+#pragma unroll
+    for (int q = 0; q < kDotPerThread; ++q) {
+      const int e = q * kDotThreads + threadIdx.x;
+      const long long n = n0 + e;
+      if (n < N) {
+        const double2 a = v[n], b = ws[e];
+        sr = fma(a.x, b.x, sr);
+        sr = fma(a.y, b.y, sr);
+        si = fma(a.x, b.y, si);
+        si = fma(-a.y, b.x, si);
+      }
+    }
     for (int o = 16; o > 0; o >>= 1) {
       sr += __shfl_down_sync(0xffffffffu, sr, o);
       si += __shfl_down_sync(0xffffffffu, si, o);
     }
-    if (lane == 0) partial[((long long)rhs * nv + i) * nblk + blk] = make_double2(sr, si);
+    if (lane == 0) { red[0][warp] = sr; red[1][warp] = si; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double tr = 0.0, ti = 0.0;
+      for (int q = 0; q < kDotThreads / 32; ++q) { tr += red[0][q]; ti += red[1][q]; }
+      partial[((long long)rhs * nv + i) * nblk + blk] = make_double2(tr, ti);
+    }
+    __syncthreads();
   }
 }
+
+int dots_chunk() { return kDotChunk; }
 
 __global__ void k_dots_reduce(int count, int nblk, const double2 *__restrict__ partial,
                               double2 *__restrict__ out) {
@@ -118,31 +138,46 @@ __global__ void k_dots_reduce(int count, int nblk, const double2 *__restrict__ p
   if (threadIdx.x == 0) out[q] = make_double2(sr, si);
 }
 
-// w[rhs] += sign * sum_i V_i[rhs] * coef[rhs * nv + i]
-__global__ void k_sub_combination(long long N, int nrhs, int nv, const double2 *__restrict__ V,
+// w[rhs] += sign * sum_i V_i[rhs] * coef[rhs * nv + i]        (grid.y = rhs)
+__global__ void k_sub_combination(long long N, int nv, const double2 *__restrict__ V,
                                   long long vsv, long long vsr, const double2 *__restrict__ coef,
                                   double2 *__restrict__ w, long long wsr, double sign) {
-  const long long total = N * nrhs;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int rhs = (int)(idx / N);
-    const long long n = idx % N;
+  const int rhs = blockIdx.y;
+  const double2 *cf = coef + (long long)rhs * nv;
+  double2 *ww = w + rhs * wsr;
+  const double2 *vr = V + rhs * vsr;
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+       n += (long long)gridDim.x * blockDim.x) {
     double2 acc = make_double2(0.0, 0.0);
-    for (int i = 0; i < nv; ++i) cfma(acc, V[i * vsv + rhs * vsr + n], coef[(long long)rhs * nv + i]);
-    double2 *dst = w + rhs * wsr + n;
-    dst->x += sign * acc.x;
-    dst->y += sign * acc.y;
+    for (int i = 0; i < nv; ++i) cfma(acc, vr[i * vsv + n], cf[i]);
+    double2 v = ww[n];
+    v.x = fma(sign, acc.x, v.x);
+    v.y = fma(sign, acc.y, v.y);
+    ww[n] = v;
   }
 }
 
-__global__ void k_scale_vec(long long N, int nrhs, const double2 *__restrict__ in,
+// out[rhs] = in[rhs] * inv_scale[rhs]                            (grid.y = rhs)
+__global__ void k_scale_vec(long long N, const double2 *__restrict__ in,
                             const double *__restrict__ inv_scale, double2 *__restrict__ out) {
-  const long long total = N * nrhs;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const double s = inv_scale[idx / N];
-    out[idx] = make_double2(in[idx].x * s, in[idx].y * s);
-  }
+  const int rhs = blockIdx.y;
+  const double s = inv_scale[rhs];
+  const long long base = (long long)rhs * N;
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+       n += (long long)gridDim.x * blockDim.x)
+    out[base + n] = make_double2(in[base + n].x * s, in[base + n].y * s);
+}
+
+// out[rhs] = in[rhs] / sqrt(Re nrm2[rhs]) (0 where the norm vanishes)   (grid.y = rhs)
+__global__ void k_scale_by_norm(long long N, const double2 *__restrict__ in,
+                                const double2 *__restrict__ nrm2, double2 *__restrict__ out) {
+  const int rhs = blockIdx.y;
+  const double q = nrm2[rhs].x;
+  const double s = q > 0.0 ? 1.0 / sqrt(q) : 0.0;
+  const long long base = (long long)rhs * N;
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+       n += (long long)gridDim.x * blockDim.x)
+    out[base + n] = make_double2(in[base + n].x * s, in[base + n].y * s);
 }
 
 static inline unsigned grid_for(long long n) {
@@ -150,23 +185,30 @@ static inline unsigned grid_for(long long n) {
   return (unsigned)(b < 152 * 16 ? (b < 1 ? 1 : b) : 152 * 16);
 }
 
+// blocks per RHS for an N-element sweep repeated over nrhs (grid.y = nrhs)
+static inline dim3 grid_rhs(long long N, int nrhs) {
+  long long want = (152 * 8 + nrhs - 1) / nrhs;
+  long long b = (N + 255) / 256;
+  return dim3((unsigned)(b < want ? (b < 1 ? 1 : b) : want), (unsigned)nrhs);
+}
+
 cudaError_t launch_apply_A(cudaStream_t st, const Geom &g, const Tables &tb, int nrhs,
                            const double2 *u, double2 *Au, int divide_by_J) {
-  k_apply_A<<<grid_for(g.Nglob * nrhs), 256, 0, st>>>(g, tb, nrhs, u, Au, divide_by_J);
+  k_apply_A<<<grid_for(g.Nglob), 256, 0, st>>>(g, tb, nrhs, u, Au, divide_by_J);
   return cudaGetLastError();
 }
 
 cudaError_t launch_scale_J(cudaStream_t st, const Geom &g, const Tables &tb, int nrhs,
                            const double2 *f, double2 *b) {
-  k_scale_J<<<grid_for(g.Nglob * nrhs), 256, 0, st>>>(g, tb, nrhs, f, b);
+  k_scale_J<<<grid_rhs(g.Nglob, nrhs), 256, 0, st>>>(g, tb, f, b);
   return cudaGetLastError();
 }
 
 cudaError_t launch_dots(cudaStream_t st, long long N, int nrhs, int nv, const double2 *V,
                         long long vsv, long long vsr, const double2 *w, long long wsr,
                         double2 *partial, double2 *out, int nblk) {
-  dim3 grid(nblk, nrhs, nv);
-  k_dots<<<grid, 256, 0, st>>>(N, nv, V, vsv, vsr, w, wsr, partial);
+  dim3 grid(nblk, nrhs);
+  k_dots<<<grid, kDotThreads, 0, st>>>(N, nv, V, vsv, vsr, w, wsr, partial);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_dots_reduce<<<nrhs * nv, 32, 0, st>>>(nrhs * nv, nblk, partial, out);
@@ -176,14 +218,19 @@ cudaError_t launch_dots(cudaStream_t st, long long N, int nrhs, int nv, const do
 cudaError_t launch_sub_combination(cudaStream_t st, long long N, int nrhs, int nv,
                                    const double2 *V, long long vsv, long long vsr,
                                    const double2 *coef, double2 *w, long long wsr, double sign) {
-  k_sub_combination<<<grid_for(N * nrhs), 256, 0, st>>>(N, nrhs, nv, V, vsv, vsr, coef, w, wsr,
-                                                        sign);
+  k_sub_combination<<<grid_rhs(N, nrhs), 256, 0, st>>>(N, nv, V, vsv, vsr, coef, w, wsr, sign);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_by_norm(cudaStream_t st, long long N, int nrhs, const double2 *in,
+                                const double2 *nrm2, double2 *out) {
+  k_scale_by_norm<<<grid_rhs(N, nrhs), 256, 0, st>>>(N, in, nrm2, out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_scale_vec(cudaStream_t st, long long N, int nrhs, const double2 *in,
                              const double *inv_scale, double2 *out) {
-  k_scale_vec<<<grid_for(N * nrhs), 256, 0, st>>>(N, nrhs, in, inv_scale, out);
+  k_scale_vec<<<grid_rhs(N, nrhs), 256, 0, st>>>(N, in, inv_scale, out);
   return cudaGetLastError();
 }
 

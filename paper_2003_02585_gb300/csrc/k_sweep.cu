@@ -7,6 +7,7 @@
 //   rhs[outer_d] += c_d * b,   rhs[inner_d] -= c_d * a,
 // c_d = prod_{tangential axes} alpha / h^2 (the coupling of the two lines; alpha = 1 on the
 // interface), which is the commutator [A_R, chi_H] applied to the trace.
+#include "async_copy.cuh"
 #include "dds_internal.cuh"
 
 namespace dds {
@@ -18,7 +19,8 @@ template <typename R>
 __global__ void k_assemble(Geom g, Tables tb, const Col *__restrict__ cols,
                            typename Cx<R>::T *__restrict__ work, const double2 *__restrict__ b,
                            int with_source, const typename Cx<R>::T *__restrict__ traces,
-                           long long trs_rhs, long long trs_sub) {
+                           long long trs_rhs, long long trs_sub, int nslots,
+                           long long slot_stride) {
   using C = typename Cx<R>::T;
   const Col c = cols[blockIdx.x];
   C *x = work + (long long)c.slot * g.Nloc;
@@ -55,7 +57,11 @@ __global__ void k_assemble(Geom g, Tables tb, const Col *__restrict__ cols,
       C cd;
       if constexpr (sizeof(R) == 4) cd = tb.coef32[off / 2 + t];
       else cd = tb.coef64[off / 2 + t];
-      const C av = tr[off + t], bv = tr[off + Lt + t];
+      C av = tr[off + t], bv = tr[off + Lt + t];
+      for (int q = 1; q < nslots; ++q) {   // sum of the traces of several sweeps
+        av = cadd(av, tr[q * slot_stride + off + t]);
+        bv = cadd(bv, tr[q * slot_stride + off + Lt + t]);
+      }
       const long long no = line_node(g, a, lo, t), ni = line_node(g, a, li, t);
       x[no] = cadd(x[no], cmul(cd, bv));
       x[ni] = csub(x[ni], cmul(cd, av));
@@ -80,7 +86,7 @@ __global__ void __launch_bounds__(128) k_subst(Geom g, const Panel *__restrict__
   C *v = reinterpret_cast<C *>(smem_raw);  // [Mb][PC]
   const Panel p = panels[blockIdx.x];
   const int Mb = g.Mb, Ml = g.Ml;
-  const C *Sf = sinv + (long long)p.factor * Ml * (long long)Mb * Mb;
+  const C *Sf = sinv + (long long)p.factor * Ml * g.St;
   const C *cf = cpl + (long long)p.factor * Ml * (long long)Mb;
   C *xs[PC];
 #pragma unroll
@@ -107,7 +113,7 @@ __global__ void __launch_bounds__(128) k_subst(Geom g, const Panel *__restrict__
         v[r * PC + c] = val;
       }
       __syncthreads();
-      const C *Sj = Sf + (long long)j * Mb * Mb;
+      const C *Sj = Sf + (long long)j * g.St;
       for (int r = threadIdx.x; r < Mb; r += blockDim.x) {
         C acc[PC];
 #pragma unroll
@@ -199,64 +205,178 @@ __global__ void k_extract(Geom g, const Col *__restrict__ cols,
 }
 
 // ------------------------------------------------------------------------------------------
-// Trace-operator step (2D plan): out = Gmap_F * in (+ raw own-source lines in sweep 1),
-// in = incoming traces of (sub, rhs) for this sweep, routed like k_extract.  Gmap already
-// contains the back-trace correction.  acc += in (for the final own-node solve).
-// grid = (npanels, row chunks of blockDim rows); one thread per output row.
+// Trace-operator step: for every (sub, rhs) column of the step,
+//   out = Gmap_F * in (+ raw own-source lines in sweep 1),   in = incoming traces of the sweep,
+// routed like k_extract.  Gmap already contains the back-trace correction; acc += in for the
+// final own-node solve.  Only input sides that can receive a trace in this sweep (in_mask) and
+// output sides with a route (out_mask) are touched -- the other terms are exactly zero or
+// unused.
+// Gmap layout per factor: [output side d][row tile of 64][input k = 0..T)[64 rows], rows past
+// 2 Lt_d zero.  A CTA (256 threads) owns one row tile and one panel of PC columns; the tile's
+// rows for the active inputs stream through a two-slot shared-memory ring in chunks of KC
+// inputs (bulk copies on mbarriers).  Thread (r = t & 63, h = t >> 6) owns row r and columns
+// h*PC/4 .. h*PC/4 + PC/4.
 // ------------------------------------------------------------------------------------------
-template <typename R, int PC>
-__global__ void __launch_bounds__(128) k_trace_step(Geom g, const Panel *__restrict__ panels,
+constexpr int kTraceRows = 64;
+
+__host__ __device__ inline int trace_tiles(const Geom &g, int d) {
+  return (2 * g.Lt[d] + kTraceRows - 1) / kTraceRows;
+}
+__host__ __device__ inline int trace_max_tiles(const Geom &g) {
+  int m = 0;
+  for (int d = 0; d < g.nsides; ++d) m = trace_tiles(g, d) > m ? trace_tiles(g, d) : m;
+  return m;
+}
+// element offset of (factor f, side d, tile tl, input k, row r) in the tiled trace map
+__host__ __device__ inline long long gmap_index(const Geom &g, int f, int d, int tl, long long k,
+                                                int r) {
+  const long long per_tile = (long long)g.T * kTraceRows;
+  const long long per_side = per_tile * trace_max_tiles(g);
+  const long long per_fac = per_side * g.nsides;
+  return f * per_fac + d * per_side + tl * per_tile + k * kTraceRows + r;
+}
+long long gmap_elems(const Geom &g, int nfac) { return gmap_index(g, nfac, 0, 0, 0, 0); }
+
+template <typename R, int PC, int KC>
+__global__ void __launch_bounds__(256) k_trace_step(Geom g, const Panel *__restrict__ panels,
                                                     const Col *__restrict__ cols,
-                                                    const typename Cx<R>::T *__restrict__ gmapT,
+                                                    const typename Cx<R>::T *__restrict__ gmap,
                                                     typename Cx<R>::T *__restrict__ gtr,
-                                                    typename Cx<R>::T *__restrict__ acc,
                                                     const typename Cx<R>::T *__restrict__ rawf,
                                                     const int *__restrict__ route, int l,
-                                                    int nrhs) {
+                                                    int nrhs, int in_mask, int out_mask,
+                                                    int tiles_per_side, int *__restrict__ err) {
   using C = typename Cx<R>::T;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C *vin = reinterpret_cast<C *>(smem_raw);  // [T][PC]
-  const Panel p = panels[blockIdx.x];
+  constexpr int HPC = PC / 4 > 0 ? PC / 4 : 1;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  C *ring = reinterpret_cast<C *>(smem_raw);                 // [2][KC][64]
+  C *vin = ring + 2 * KC * kTraceRows;                       // [PC][T]
+  uint64_t *bars = reinterpret_cast<uint64_t *>(vin + (long long)g.T * PC);  // ring x2, inputs
+  const Panel p = panels[blockIdx.y];
   const int T = g.T;
   const long long slot_stride = (long long)nrhs * g.nsub * T;
-  for (int idx = threadIdx.x; idx < T * PC; idx += blockDim.x) {
-    const int kk = idx / PC, c = idx % PC;
-    C val = czero<C>();
-    if (c < p.ncol) {
-      const Col cc = cols[p.col0 + c];
-      const long long base = ((long long)cc.rhs * g.nsub + cc.sub) * T;
-      val = gtr[l * slot_stride + base + kk];
-      if (blockIdx.y == 0) acc[base + kk] = cadd(acc[base + kk], val);
+  int which = blockIdx.x / tiles_per_side, tile = blockIdx.x % tiles_per_side, dout = -1;
+  for (int d = 0; d < g.nsides; ++d)
+    if ((out_mask >> d) & 1) {
+      if (which == 0) { dout = d; break; }
+      --which;
     }
-    vin[kk * PC + c] = val;
+  if (dout < 0 || tile >= trace_tiles(g, dout)) return;   // uniform over the block
+  // chunk list over the active input sides: chunk q covers inputs [k0, k0 + n)
+  int nchunks = 0, in_bytes = 0;
+  for (int d = 0; d < g.nsides; ++d)
+    if ((in_mask >> d) & 1) {
+      nchunks += (2 * g.Lt[d] + KC - 1) / KC;
+      in_bytes += 2 * g.Lt[d] * (int)sizeof(C);
+    }
+  auto chunk = [&](int q, int &k0, int &n) {
+    for (int d = 0; d < g.nsides; ++d) {
+      if (!((in_mask >> d) & 1)) continue;
+      const int nc = (2 * g.Lt[d] + KC - 1) / KC;
+      if (q < nc) {
+        k0 = g.toff[d] + q * KC;
+        n = min(KC, 2 * g.Lt[d] - q * KC);
+        return;
+      }
+      q -= nc;
+    }
+    k0 = 0;
+    n = 0;
+  };
+  const C *Gt = gmap + gmap_index(g, p.factor, dout, tile, 0, 0);
+  if (threadIdx.x == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    mbar_init(&bars[2], 1);
+    mbar_init_fence();
   }
   __syncthreads();
-  const int r = blockIdx.y * blockDim.x + threadIdx.x;
-  if (r >= T) return;
-  const C *Gf = gmapT + (long long)p.factor * T * T;
-  C out[PC];
-#pragma unroll
-  for (int c = 0; c < PC; ++c) out[c] = czero<C>();
-#pragma unroll 4
-  for (int kk = 0; kk < T; ++kk) {
-    const C a = Gf[(long long)kk * T + r];
-#pragma unroll
-    for (int c = 0; c < PC; ++c) cfma(out[c], a, vin[kk * PC + c]);
+  if (threadIdx.x == 0) {
+    // incoming traces of the panel's columns (active input sides), one copy per column and side
+    if (p.ncol > 0 && in_bytes > 0) {
+      mbar_arrive_expect_tx(&bars[2], (uint32_t)(in_bytes * p.ncol));
+      for (int c = 0; c < p.ncol; ++c) {
+        const Col cc = cols[p.col0 + c];
+        const C *src = gtr + l * slot_stride + ((long long)cc.rhs * g.nsub + cc.sub) * T;
+        for (int d = 0; d < g.nsides; ++d)
+          if ((in_mask >> d) & 1)
+            bulk_g2s(vin + (long long)c * T + g.toff[d], src + g.toff[d],
+                     (uint32_t)(2 * g.Lt[d] * sizeof(C)), &bars[2]);
+      }
+    }
+    for (int q = 0; q < 2 && q < nchunks; ++q) {
+      int k0, n;
+      chunk(q, k0, n);
+      const uint32_t bytes = (uint32_t)(n * kTraceRows * sizeof(C));
+      mbar_arrive_expect_tx(&bars[q], bytes);
+      bulk_g2s(ring + q * KC * kTraceRows, Gt + (long long)k0 * kTraceRows, bytes, &bars[q]);
+    }
   }
-  // which side / line / position is row r
-  int d = 0;
-  while (d + 1 < g.nsides && r >= g.toff[d + 1]) ++d;
-  const int lp = route[l * 6 + d];
+  // columns past the panel read zeros
+  for (int idx = threadIdx.x; idx < (PC - p.ncol) * T; idx += blockDim.x)
+    vin[(long long)p.ncol * T + idx] = czero<C>();
+  bool ok = (p.ncol == 0 || in_bytes == 0) ? true : mbar_wait(&bars[2], 0);
+  const int r = threadIdx.x & (kTraceRows - 1);
+  const int h = threadIdx.x / kTraceRows;
+  C out[HPC];
 #pragma unroll
-  for (int c = 0; c < PC; ++c) {
-    if (c >= p.ncol) continue;
-    const Col cc = cols[p.col0 + c];
+  for (int c = 0; c < HPC; ++c) out[c] = czero<C>();
+  if (__syncthreads_or(!ok)) {
+    if (threadIdx.x == 0) {
+      atomicExch(err, 3);
+      for (int q = 0; q < 2 && q < nchunks; ++q) mbar_wait(&bars[q], 0);
+    }
+    __syncthreads();
+    return;
+  }
+  const C *vcol = vin + (long long)(h * HPC) * T;
+  for (int q = 0; q < nchunks; ++q) {
+    int k0, n;
+    chunk(q, k0, n);
+    const int buf = q & 1;
+    ok = mbar_wait(&bars[buf], (q >> 1) & 1);
+    const C *A = ring + buf * KC * kTraceRows;
+    if (h * HPC < PC) {
+#pragma unroll 8
+      for (int i = 0; i < n; ++i) {
+        const C a = A[i * kTraceRows + r];
+#pragma unroll
+        for (int c = 0; c < HPC; ++c) cfma(out[c], a, vcol[(long long)c * T + k0 + i]);
+      }
+    }
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {
+        atomicExch(err, 3);
+        mbar_wait(&bars[buf], (q >> 1) & 1);
+        if (q + 1 < nchunks) mbar_wait(&bars[buf ^ 1], ((q + 1) >> 1) & 1);
+      }
+      __syncthreads();
+      return;
+    }
+    if (threadIdx.x == 0 && q + 2 < nchunks) {
+      int k2, n2;
+      chunk(q + 2, k2, n2);
+      const uint32_t bytes = (uint32_t)(n2 * kTraceRows * sizeof(C));
+      fence_proxy_async();
+      mbar_arrive_expect_tx(&bars[buf], bytes);
+      bulk_g2s(ring + buf * KC * kTraceRows, Gt + (long long)k2 * kTraceRows, bytes, &bars[buf]);
+    }
+  }
+  const int rows = 2 * g.Lt[dout];
+  const int rr = tile * kTraceRows + r;
+  if (rr >= rows || h * HPC >= PC) return;
+  const int lp = route[l * 6 + dout];
+  const int grow = g.toff[dout] + rr;   // row in the full trace vector
+#pragma unroll
+  for (int c = 0; c < HPC; ++c) {
+    const int cg = h * HPC + c;
+    if (cg >= p.ncol) continue;
+    const Col cc = cols[p.col0 + cg];
     C val = out[c];
-    if (rawf != nullptr) val = cadd(val, rawf[((long long)cc.rhs * g.nsub + cc.sub) * T + r]);
-    const int nb = sub_neighbour(g, cc.sub, d);
+    if (rawf != nullptr) val = cadd(val, rawf[((long long)cc.rhs * g.nsub + cc.sub) * T + grow]);
+    const int nb = sub_neighbour(g, cc.sub, dout);
     if (nb < 0 || lp < 0) continue;
-    C *dst = gtr + lp * slot_stride + ((long long)cc.rhs * g.nsub + nb) * T + g.toff[d ^ 1] +
-             (r - g.toff[d]);
+    C *dst = gtr + lp * slot_stride + ((long long)cc.rhs * g.nsub + nb) * T + g.toff[dout ^ 1] + rr;
     *dst = cadd(*dst, val);
   }
 }
@@ -292,30 +412,33 @@ __global__ void k_unit_traces(Geom g, Tables tb, int k0, int nk,
   }
 }
 
-// gmapT[k0 + q][r] = raw trace line entry r of the solution in slot q
+// column k0 + q of the trace map = raw trace lines of the solution in slot q (tiled layout)
 template <typename R>
 __global__ void k_raw_lines(Geom g, const typename Cx<R>::T *__restrict__ work,
-                            typename Cx<R>::T *__restrict__ gmapT, int k0) {
+                            typename Cx<R>::T *__restrict__ gmap, int f, int k0) {
   using C = typename Cx<R>::T;
   const int q = blockIdx.x;
+  const long long kk = k0 + q;
   const C *x = work + (long long)q * g.Nloc;
-  C *dst = gmapT + (long long)(k0 + q) * g.T;
   for (int d = 0; d < g.nsides; ++d) {
-    const int a = d >> 1, Lt = g.Lt[d], off = g.toff[d];
+    const int a = d >> 1, Lt = g.Lt[d];
     const int li = inner_line(g, d), lo = outer_line(g, d);
-    for (int t = threadIdx.x; t < Lt; t += blockDim.x) {
-      dst[off + t] = x[line_node(g, a, li, t)];
-      dst[off + Lt + t] = x[line_node(g, a, lo, t)];
+    for (int ro = threadIdx.x; ro < trace_tiles(g, d) * kTraceRows; ro += blockDim.x) {
+      C v = czero<C>();
+      if (ro < Lt) v = x[line_node(g, a, li, ro)];
+      else if (ro < 2 * Lt) v = x[line_node(g, a, lo, ro - Lt)];
+      gmap[gmap_index(g, f, d, ro / kTraceRows, kk, ro % kTraceRows)] = v;
     }
   }
 }
 
 // back-trace correction folded into the map: a_out_d(t) -= b_in_d(t)
-__global__ void k_gmap_backtrace(Geom g, double2 *gmapT) {
+__global__ void k_gmap_backtrace(Geom g, double2 *gmap, int f) {
   for (int d = 0; d < g.nsides; ++d) {
     const int Lt = g.Lt[d], off = g.toff[d];
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < Lt; t += gridDim.x * blockDim.x) {
-      double2 *e = gmapT + (long long)(off + Lt + t) * g.T + (off + t);
+      const long long kk = off + Lt + t;   // b-line input of side d
+      double2 *e = gmap + gmap_index(g, f, d, t / kTraceRows, kk, t % kTraceRows);
       e->x -= 1.0;
     }
   }
@@ -344,10 +467,11 @@ template <typename R>
 cudaError_t launch_assemble(cudaStream_t st, const Geom &g, const Tables &tb, int ncols,
                             const Col *cols, typename Cx<R>::T *work, const double2 *b,
                             const double2 *, int with_source, const typename Cx<R>::T *traces,
-                            long long trs_rhs, long long trs_sub) {
+                            long long trs_rhs, long long trs_sub, int nslots,
+                            long long slot_stride) {
   if (ncols <= 0) return cudaSuccess;
   k_assemble<R><<<ncols, 256, 0, st>>>(g, tb, cols, work, b, with_source, traces, trs_rhs,
-                                       trs_sub);
+                                       trs_sub, nslots, slot_stride);
   return cudaGetLastError();
 }
 
@@ -357,8 +481,8 @@ static cudaError_t subst_pc(cudaStream_t st, const Geom &g, int npanels, const P
                             const typename Cx<R>::T *cpl, typename Cx<R>::T *work) {
   using C = typename Cx<R>::T;
   const size_t smem = (size_t)g.Mb * PC * sizeof(C);
-  cudaError_t e = cudaFuncSetAttribute(k_subst<R, PC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  static bool done[64] = {false};
+  cudaError_t e = smem_limit_once(k_subst<R, PC>, done);
   if (e != cudaSuccess) return e;
   k_subst<R, PC><<<npanels, 128, smem, st>>>(g, panels, cols, sinv, cpl, work);
   return cudaGetLastError();
@@ -393,31 +517,40 @@ template <typename R, int PC>
 static cudaError_t trace_step_pc(cudaStream_t st, const Geom &g, int npanels,
                                  const Panel *panels, const Col *cols,
                                  const typename Cx<R>::T *gmap, typename Cx<R>::T *gtr,
-                                 typename Cx<R>::T *acc, const typename Cx<R>::T *rawf,
-                                 const int *route, int l, int nrhs) {
+                                 const typename Cx<R>::T *rawf,
+                                 const int *route, int l, int nrhs, int in_mask, int out_mask,
+                                 int *err) {
   using C = typename Cx<R>::T;
-  const size_t smem = (size_t)g.T * PC * sizeof(C);
-  cudaError_t e = cudaFuncSetAttribute(k_trace_step<R, PC>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  constexpr int KC = sizeof(R) == 4 ? 64 : 32;
+  const size_t smem = (size_t)(2 * KC * kTraceRows + (long long)g.T * PC) * sizeof(C) + 32;
+  static bool done[64] = {false};
+  cudaError_t e = smem_limit_once(k_trace_step<R, PC, KC>, done);
   if (e != cudaSuccess) return e;
-  dim3 grid(npanels, (g.T + 127) / 128);
-  k_trace_step<R, PC><<<grid, 128, smem, st>>>(g, panels, cols, gmap, gtr, acc, rawf, route, l,
-                                                nrhs);
+  int nout = 0;
+  for (int d = 0; d < g.nsides; ++d) nout += (out_mask >> d) & 1;
+  const int tiles = trace_max_tiles(g);
+  if (nout == 0) return cudaSuccess;   // nothing is routed out of this sweep
+  dim3 grid(nout * tiles, npanels);
+  k_trace_step<R, PC, KC><<<grid, 256, smem, st>>>(g, panels, cols, gmap, gtr, rawf, route, l,
+                                                    nrhs, in_mask, out_mask, tiles, err);
   return cudaGetLastError();
+}
+
+size_t trace_step_smem(const Geom &g, int pc, size_t elem) {
+  const int KC = elem == sizeof(float2) ? 64 : 32;
+  return (size_t)(2 * KC * kTraceRows + (long long)g.T * pc) * elem + 32;
 }
 
 template <typename R>
 cudaError_t launch_trace_step(cudaStream_t st, const Geom &g, int npanels, const Panel *panels,
                               const Col *cols, const typename Cx<R>::T *gmap,
-                              typename Cx<R>::T *g_traces, typename Cx<R>::T *acc,
+                              typename Cx<R>::T *g_traces,
                               const typename Cx<R>::T *rawf, const int *route, int l, int nrhs,
-                              int pc) {
+                              int pc, int in_mask, int out_mask, int *err) {
   if (npanels <= 0) return cudaSuccess;
   switch (pc) {
-    case 1: return trace_step_pc<R, 1>(st, g, npanels, panels, cols, gmap, g_traces, acc, rawf, route, l, nrhs);
-    case 2: return trace_step_pc<R, 2>(st, g, npanels, panels, cols, gmap, g_traces, acc, rawf, route, l, nrhs);
-    case 4: return trace_step_pc<R, 4>(st, g, npanels, panels, cols, gmap, g_traces, acc, rawf, route, l, nrhs);
-    case 8: return trace_step_pc<R, 8>(st, g, npanels, panels, cols, gmap, g_traces, acc, rawf, route, l, nrhs);
+    case 4: return trace_step_pc<R, 4>(st, g, npanels, panels, cols, gmap, g_traces, rawf, route, l, nrhs, in_mask, out_mask, err);
+    case 8: return trace_step_pc<R, 8>(st, g, npanels, panels, cols, gmap, g_traces, rawf, route, l, nrhs, in_mask, out_mask, err);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -432,14 +565,15 @@ cudaError_t launch_unit_traces(cudaStream_t st, const Geom &g, const Tables &tb,
 
 template <typename R>
 cudaError_t launch_raw_lines(cudaStream_t st, const Geom &g, int nk,
-                             const typename Cx<R>::T *work, typename Cx<R>::T *gmapT, int k0) {
+                             const typename Cx<R>::T *work, typename Cx<R>::T *gmap, int f,
+                             int k0) {
   if (nk <= 0) return cudaSuccess;
-  k_raw_lines<R><<<nk, 128, 0, st>>>(g, work, gmapT, k0);
+  k_raw_lines<R><<<nk, 128, 0, st>>>(g, work, gmap, f, k0);
   return cudaGetLastError();
 }
 
-cudaError_t launch_gmap_backtrace(cudaStream_t st, const Geom &g, double2 *gmapT) {
-  k_gmap_backtrace<<<8, 128, 0, st>>>(g, gmapT);
+cudaError_t launch_gmap_backtrace(cudaStream_t st, const Geom &g, double2 *gmap, int f) {
+  k_gmap_backtrace<<<8, 128, 0, st>>>(g, gmap, f);
   return cudaGetLastError();
 }
 
@@ -462,7 +596,7 @@ cudaError_t launch_copy_local_back(cudaStream_t st, long long n, const typename 
   template cudaError_t launch_assemble<R>(cudaStream_t, const Geom &, const Tables &, int,     \
                                           const Col *, Cx<R>::T *, const double2 *,           \
                                           const double2 *, int, const Cx<R>::T *, long long,   \
-                                          long long);                                           \
+                                          long long, int, long long);                           \
   template cudaError_t launch_subst<R>(cudaStream_t, const Geom &, int, const Panel *,         \
                                        const Col *, const Cx<R>::T *, const Cx<R>::T *,        \
                                        Cx<R>::T *, int);                                        \
@@ -471,12 +605,12 @@ cudaError_t launch_copy_local_back(cudaStream_t st, long long n, const typename 
                                          Cx<R>::T *, const int *, int, int);                    \
   template cudaError_t launch_trace_step<R>(cudaStream_t, const Geom &, int, const Panel *,    \
                                             const Col *, const Cx<R>::T *, Cx<R>::T *,         \
-                                            Cx<R>::T *, const Cx<R>::T *, const int *, int,    \
-                                            int, int);                                          \
+                                            const Cx<R>::T *, const int *, int,                \
+                                            int, int, int, int, int *);                         \
   template cudaError_t launch_unit_traces<R>(cudaStream_t, const Geom &, const Tables &, int,  \
                                              int, Cx<R>::T *);                                  \
   template cudaError_t launch_raw_lines<R>(cudaStream_t, const Geom &, int, const Cx<R>::T *,  \
-                                           Cx<R>::T *, int);                                    \
+                                           Cx<R>::T *, int, int);                               \
   template cudaError_t launch_copy_local<R>(cudaStream_t, long long, const double2 *,          \
                                             Cx<R>::T *, int);                                   \
   template cudaError_t launch_copy_local_back<R>(cudaStream_t, long long, const Cx<R>::T *,    \
