@@ -321,8 +321,7 @@ CallPlan *get_plan(dds_ctx *ctx, int nrhs) {
   cp->all = emit(order, maxpc, false);
   for (int dir = 0; dir < ctx->ndirs; ++dir)
     for (int s = 0; s < ctx->nsteps; ++s) cp->steps.push_back(emit(ctx->step_subs[dir][s], maxpc, false));
-  int tmax = 8;
-  while (tmax > 4 && trace_step_smem(ctx->g, tmax, elem) > 227 * 1024) tmax /= 2;
+  const int tmax = 8;   // trace-step panels: 8 columns
   for (int dir = 0; dir < ctx->ndirs; ++dir)
     for (int s = 0; s < ctx->nsteps; ++s) cp->tsteps.push_back(emit(ctx->step_subs[dir][s], tmax, true));
   if (upload(cp->cols, cols, ctx->stream) != cudaSuccess) return nullptr;
@@ -561,7 +560,7 @@ dds_status setup_impl(dds_ctx *ctx, const dds_problem *p) {
     g.Lt[d] = lt;
     g.T += 2 * lt;
   }
-  if (ctx->plan == DDS_PLAN_TRACE && trace_step_smem(g, 4, sizeof(double2)) > 227 * 1024) {
+  if (ctx->plan == DDS_PLAN_TRACE && trace_step_smem(g, 8, sizeof(double2)) > 227 * 1024) {
     ctx->err = "trace vectors too long for the trace-operator plan (T = " + std::to_string(g.T) + ")";
     return DDS_EINVAL;
   }
@@ -841,13 +840,13 @@ dds_status fgmres(dds_ctx *ctx, const double2 *b, int nrhs, double2 *x, double t
   double2 *Z = ctx->Zbig.as<double2>();
   const int chunk = dots_chunk();
   const int nblk = (int)((N + chunk - 1) / chunk);
-  CK(ctx->dots_part.ensure((size_t)nrhs * (maxit + 1) * nblk * sizeof(double2)));
+  CK(ctx->dots_part.ensure((size_t)nrhs * (maxit + 2) * nblk * sizeof(double2)));
   // hdev: [h1: nrhs*(j+1)] [h2: nrhs*(j+1)] [norm^2: nrhs]
-  CK(ctx->dots_out.ensure((size_t)nrhs * (2 * maxit + 3) * sizeof(double2)));
+  CK(ctx->dots_out.ensure((size_t)nrhs * (2 * maxit + 4) * sizeof(double2)));
   CK(ctx->coefbuf.ensure((size_t)nrhs * (maxit + 1) * sizeof(double2)));
   double2 *hdev = ctx->dots_out.as<double2>();
   double2 *part = ctx->dots_part.as<double2>();
-  std::vector<double2> hh((size_t)nrhs * (2 * maxit + 3));
+  std::vector<double2> hh((size_t)nrhs * (2 * maxit + 4));
   // beta = ||b||, V_0 = b / beta
   LAUNCHK(DDS_K_KRYLOV, launch_dots(st, N, nrhs, 1, b, 0, N, b, N, part, hdev, nblk));
   LAUNCHK(DDS_K_KRYLOV, launch_scale_by_norm(st, N, nrhs, b, hdev, V));
@@ -872,26 +871,45 @@ dds_status fgmres(dds_ctx *ctx, const double2 *b, int nrhs, double2 *x, double t
     if (rs != DDS_OK) return rs;
     LAUNCHK(DDS_K_KRYLOV, launch_apply_A(st, g, ctx->tb, nrhs, Zj, W, 0));
     const int nv = j + 1;
-    double2 *h1 = hdev, *h2 = hdev + (size_t)nrhs * nv, *hn = hdev + (size_t)2 * nrhs * nv;
-    for (int pass = 0; pass < 2; ++pass) {
-      double2 *hp = pass == 0 ? h1 : h2;
-      LAUNCHK(DDS_K_KRYLOV, launch_dots(st, N, nrhs, nv, V, vs, N, W, N, part, hp, nblk));
-      LAUNCHK(DDS_K_KRYLOV, launch_sub_combination(st, N, nrhs, nv, V, vs, N, hp, W, N, -1.0));
-    }
+    // classical Gram-Schmidt with the second pass only where it is needed (DGKS criterion):
+    // pass 1 also returns ||W||^2 (W is basis slot j+1, the last of the nv+1 vectors)
+    double2 *h1 = hdev;                                        // [nrhs][nv + 1]
+    double2 *h2 = hdev + (size_t)nrhs * (nv + 1);              // [nrhs][nv]
+    double2 *hn = h2 + (size_t)nrhs * nv;                      // [nrhs]
+    LAUNCHK(DDS_K_KRYLOV, launch_dots(st, N, nrhs, nv + 1, V, vs, N, W, N, part, h1, nblk));
+    LAUNCHK(DDS_K_KRYLOV, launch_sub_combination(st, N, nrhs, nv, V, vs, N, h1, W, N, -1.0, nv + 1));
     LAUNCHK(DDS_K_KRYLOV, launch_dots(st, N, nrhs, 1, W, 0, N, W, N, part, hn, nblk));
-    LAUNCHK(DDS_K_KRYLOV, launch_scale_by_norm(st, N, nrhs, W, hn, W));
-    CK(cudaMemcpyAsync(hh.data(), hdev, (size_t)nrhs * (2 * nv + 1) * sizeof(double2),
+    CK(cudaMemcpyAsync(hh.data(), hdev, (size_t)nrhs * (2 * nv + 2) * sizeof(double2),
                        cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    k = j + 1;
-    bool all = true;
+    bool second = false;
     for (int r = 0; r < nrhs; ++r) {
-      const double hnorm = std::sqrt(std::max(hh[(size_t)2 * nrhs * nv + r].x, 0.0));
+      const double w0 = hh[(size_t)r * (nv + 1) + nv].x, w1 = hh[(size_t)nrhs * (2 * nv + 1) + r].x;
+      if (!(w1 > 0.5 * w0)) second = true;   // ||w1|| <= ||w0|| / sqrt(2): cancellation
+    }
+    std::vector<double2> h2h((size_t)nrhs * nv, make_double2(0.0, 0.0));
+    if (second) {
+      LAUNCHK(DDS_K_KRYLOV, launch_dots(st, N, nrhs, nv, V, vs, N, W, N, part, h2, nblk));
+      LAUNCHK(DDS_K_KRYLOV, launch_sub_combination(st, N, nrhs, nv, V, vs, N, h2, W, N, -1.0, nv));
+      LAUNCHK(DDS_K_KRYLOV, launch_dots(st, N, nrhs, 1, W, 0, N, W, N, part, hn, nblk));
+      CK(cudaMemcpyAsync(h2h.data(), h2, (size_t)nrhs * nv * sizeof(double2), cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(hh.data() + (size_t)nrhs * (2 * nv + 1), hn, nrhs * sizeof(double2),
+                         cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+    }
+    LAUNCHK(DDS_K_KRYLOV, launch_scale_by_norm(st, N, nrhs, W, hn, W));
+    for (int r = 0; r < nrhs; ++r) {
+      const double hnorm = std::sqrt(std::max(hh[(size_t)nrhs * (2 * nv + 1) + r].x, 0.0));
       for (int i = 0; i <= j; ++i) {
-        const double2 a = hh[(size_t)r * nv + i], bq = hh[(size_t)nrhs * nv + (size_t)r * nv + i];
+        const double2 a = hh[(size_t)r * (nv + 1) + i], bq = h2h[(size_t)r * nv + i];
         Hat(r, i, j) = cd(a.x + bq.x, a.y + bq.y);
       }
       Hat(r, j + 1, j) = hnorm;
+    }
+    k = j + 1;
+    bool all = true;
+    for (int r = 0; r < nrhs; ++r) {
+      const double hnorm = std::abs(Hat(r, j + 1, j));
       if (done[r]) continue;
       for (int i = 0; i < j; ++i) {  // previous rotations
         const cd a = Hat(r, i, j), bb = Hat(r, i + 1, j);
@@ -935,14 +953,14 @@ dds_status fgmres(dds_ctx *ctx, const double2 *b, int nrhs, double2 *x, double t
     CK(cudaMemcpyAsync(ctx->coefbuf.p, ycoef.data(), (size_t)nrhs * k * sizeof(double2),
                        cudaMemcpyHostToDevice, st));
     LAUNCHK(DDS_K_KRYLOV, launch_sub_combination(st, N, nrhs, k, Z, vs, N, ctx->coefbuf.as<double2>(),
-                                                 x, N, 1.0));
+                                                 x, N, 1.0, k));
   }
   // true residual: R = A x - b
   double2 *Rv = V;
   LAUNCHK(DDS_K_KRYLOV, launch_apply_A(st, g, ctx->tb, nrhs, x, Rv, 0));
   std::vector<double2> mone(nrhs, make_double2(1.0, 0.0));
   CK(cudaMemcpyAsync(ctx->coefbuf.p, mone.data(), nrhs * sizeof(double2), cudaMemcpyHostToDevice, st));
-  LAUNCHK(DDS_K_KRYLOV, launch_sub_combination(st, N, nrhs, 1, b, 0, N, ctx->coefbuf.as<double2>(), Rv, N, -1.0));
+  LAUNCHK(DDS_K_KRYLOV, launch_sub_combination(st, N, nrhs, 1, b, 0, N, ctx->coefbuf.as<double2>(), Rv, N, -1.0, 1));
   LAUNCHK(DDS_K_KRYLOV, launch_dots(st, N, nrhs, 1, Rv, 0, N, Rv, N, part, hdev, nblk));
   CK(cudaMemcpyAsync(hh.data(), hdev, nrhs * sizeof(double2), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));

@@ -134,15 +134,19 @@ struct Tables {
   const double2 *cp[3];         // global stencil: coupling of node p to p + e_a (0 on the edge)
 };
 
-// Raise a kernel's dynamic shared-memory limit to the largest value a launch may ask for, once
-// per device (the attribute persists for the function on that device).
+// Raise a kernel's dynamic shared-memory limit to the largest value a launch may ask for (227 KB
+// minus its static shared memory), once per device (the attribute persists on that device).
 template <typename F>
 inline cudaError_t smem_limit_once(F *kernel, bool (&done)[64]) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
-  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           227 * 1024 - (int)fa.sharedSizeBytes);
   if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
   return e;
 }
@@ -215,7 +219,7 @@ cudaError_t launch_dots(cudaStream_t st, long long N, int nrhs, int nv, const do
 cudaError_t launch_sub_combination(cudaStream_t st, long long N, int nrhs, int nv, const double2 *V,
                                    long long v_stride_vec, long long v_stride_rhs,
                                    const double2 *coef, double2 *w, long long w_stride_rhs,
-                                   double sign);
+                                   double sign, int coef_stride);
 cudaError_t launch_scale_vec(cudaStream_t st, long long N, int nrhs, const double2 *in,
                              const double *inv_scale, double2 *out);
 cudaError_t launch_scale_by_norm(cudaStream_t st, long long N, int nrhs, const double2 *in,

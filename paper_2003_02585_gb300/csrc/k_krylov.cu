@@ -138,12 +138,13 @@ __global__ void k_dots_reduce(int count, int nblk, const double2 *__restrict__ p
   if (threadIdx.x == 0) out[q] = make_double2(sr, si);
 }
 
-// w[rhs] += sign * sum_i V_i[rhs] * coef[rhs * nv + i]        (grid.y = rhs)
+// w[rhs] += sign * sum_{i < nv} V_i[rhs] * coef[rhs * cstride + i]        (grid.y = rhs)
 __global__ void k_sub_combination(long long N, int nv, const double2 *__restrict__ V,
                                   long long vsv, long long vsr, const double2 *__restrict__ coef,
-                                  double2 *__restrict__ w, long long wsr, double sign) {
+                                  double2 *__restrict__ w, long long wsr, double sign,
+                                  int cstride) {
   const int rhs = blockIdx.y;
-  const double2 *cf = coef + (long long)rhs * nv;
+  const double2 *cf = coef + (long long)rhs * cstride;
   double2 *ww = w + rhs * wsr;
   const double2 *vr = V + rhs * vsr;
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
@@ -217,8 +218,10 @@ cudaError_t launch_dots(cudaStream_t st, long long N, int nrhs, int nv, const do
 
 cudaError_t launch_sub_combination(cudaStream_t st, long long N, int nrhs, int nv,
                                    const double2 *V, long long vsv, long long vsr,
-                                   const double2 *coef, double2 *w, long long wsr, double sign) {
-  k_sub_combination<<<grid_rhs(N, nrhs), 256, 0, st>>>(N, nv, V, vsv, vsr, coef, w, wsr, sign);
+                                   const double2 *coef, double2 *w, long long wsr, double sign,
+                                   int cstride) {
+  k_sub_combination<<<grid_rhs(N, nrhs), 256, 0, st>>>(N, nv, V, vsv, vsr, coef, w, wsr, sign,
+                                                       cstride);
   return cudaGetLastError();
 }
 

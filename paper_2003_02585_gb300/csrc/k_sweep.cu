@@ -237,8 +237,34 @@ __host__ __device__ inline long long gmap_index(const Geom &g, int f, int d, int
 }
 long long gmap_elems(const Geom &g, int nfac) { return gmap_index(g, nfac, 0, 0, 0, 0); }
 
-template <typename R, int PC, int KC>
-__global__ void __launch_bounds__(256) k_trace_step(Geom g, const Panel *__restrict__ panels,
+// The active inputs of a sweep (the sides in in_mask) are cut into segments of at most
+// kTraceSeg consecutive inputs of one side.  A CTA (128 threads) owns one 64-row tile of one
+// output side, one panel of PC = 8 columns and one input segment: its map slice
+// (segment x 64 rows, contiguous in the tiled layout) arrives by one bulk copy while the threads
+// gather the panel's inputs, then thread (rp = t & 31, cq = t >> 5) accumulates rows 2 rp,
+// 2 rp + 1 x columns 2 cq, 2 cq + 1 from shared memory.  Segments of one output add into the
+// destination slot with atomics (the slot accumulates with += in any case).
+constexpr int kTraceSeg = 104;
+
+__host__ __device__ inline int trace_nseg(const Geom &g, int in_mask) {
+  int n = 0;
+  for (int d = 0; d < g.nsides; ++d)
+    if ((in_mask >> d) & 1) n += (2 * g.Lt[d] + kTraceSeg - 1) / kTraceSeg;
+  return n;
+}
+
+template <typename C> __device__ inline void atomic_cadd(C *dst, C v);
+template <> __device__ inline void atomic_cadd<float2>(float2 *dst, float2 v) {
+  atomicAdd(&dst->x, v.x);
+  atomicAdd(&dst->y, v.y);
+}
+template <> __device__ inline void atomic_cadd<double2>(double2 *dst, double2 v) {
+  atomicAdd(&dst->x, v.x);
+  atomicAdd(&dst->y, v.y);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(128) k_trace_step(Geom g, const Panel *__restrict__ panels,
                                                     const Col *__restrict__ cols,
                                                     const typename Cx<R>::T *__restrict__ gmap,
                                                     typename Cx<R>::T *__restrict__ gtr,
@@ -247,11 +273,12 @@ __global__ void __launch_bounds__(256) k_trace_step(Geom g, const Panel *__restr
                                                     int nrhs, int in_mask, int out_mask,
                                                     int tiles_per_side, int *__restrict__ err) {
   using C = typename Cx<R>::T;
-  constexpr int HPC = PC / 4 > 0 ? PC / 4 : 1;
+  constexpr int PC = 8;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  C *ring = reinterpret_cast<C *>(smem_raw);                 // [2][KC][64]
-  C *vin = ring + 2 * KC * kTraceRows;                       // [PC][T]
-  uint64_t *bars = reinterpret_cast<uint64_t *>(vin + (long long)g.T * PC);  // ring x2, inputs
+  C *Gs = reinterpret_cast<C *>(smem_raw);                   // map slice [k][64]
+  C *vin = Gs + kTraceSeg * kTraceRows;                      // inputs [col][k]
+  uint64_t &bar = *reinterpret_cast<uint64_t *>(vin + PC * kTraceSeg);
+  __shared__ long long cbase[PC];
   const Panel p = panels[blockIdx.y];
   const int T = g.T;
   const long long slot_stride = (long long)nrhs * g.nsub * T;
@@ -262,122 +289,85 @@ __global__ void __launch_bounds__(256) k_trace_step(Geom g, const Panel *__restr
       --which;
     }
   if (dout < 0 || tile >= trace_tiles(g, dout)) return;   // uniform over the block
-  // chunk list over the active input sides: chunk q covers inputs [k0, k0 + n)
-  int nchunks = 0, in_bytes = 0;
-  for (int d = 0; d < g.nsides; ++d)
-    if ((in_mask >> d) & 1) {
-      nchunks += (2 * g.Lt[d] + KC - 1) / KC;
-      in_bytes += 2 * g.Lt[d] * (int)sizeof(C);
+  // this CTA's input segment: global inputs [k0, k0 + n)
+  int sgi = blockIdx.z, k0 = 0, n = 0;
+  for (int d = 0; d < g.nsides; ++d) {
+    if (!((in_mask >> d) & 1)) continue;
+    const int ns = (2 * g.Lt[d] + kTraceSeg - 1) / kTraceSeg;
+    if (sgi < ns) {
+      k0 = g.toff[d] + sgi * kTraceSeg;
+      n = min(kTraceSeg, 2 * g.Lt[d] - sgi * kTraceSeg);
+      break;
     }
-  auto chunk = [&](int q, int &k0, int &n) {
-    for (int d = 0; d < g.nsides; ++d) {
-      if (!((in_mask >> d) & 1)) continue;
-      const int nc = (2 * g.Lt[d] + KC - 1) / KC;
-      if (q < nc) {
-        k0 = g.toff[d] + q * KC;
-        n = min(KC, 2 * g.Lt[d] - q * KC);
-        return;
-      }
-      q -= nc;
-    }
-    k0 = 0;
-    n = 0;
-  };
-  const C *Gt = gmap + gmap_index(g, p.factor, dout, tile, 0, 0);
+    sgi -= ns;
+  }
   if (threadIdx.x == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
-    mbar_init(&bars[2], 1);
+    mbar_init(&bar, 1);
     mbar_init_fence();
+  }
+  if (threadIdx.x < PC) {
+    const int c = threadIdx.x;
+    cbase[c] = c < p.ncol ? l * slot_stride +
+                                ((long long)cols[p.col0 + c].rhs * g.nsub + cols[p.col0 + c].sub) * T
+                          : -1;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    // incoming traces of the panel's columns (active input sides), one copy per column and side
-    if (p.ncol > 0 && in_bytes > 0) {
-      mbar_arrive_expect_tx(&bars[2], (uint32_t)(in_bytes * p.ncol));
-      for (int c = 0; c < p.ncol; ++c) {
-        const Col cc = cols[p.col0 + c];
-        const C *src = gtr + l * slot_stride + ((long long)cc.rhs * g.nsub + cc.sub) * T;
-        for (int d = 0; d < g.nsides; ++d)
-          if ((in_mask >> d) & 1)
-            bulk_g2s(vin + (long long)c * T + g.toff[d], src + g.toff[d],
-                     (uint32_t)(2 * g.Lt[d] * sizeof(C)), &bars[2]);
-      }
-    }
-    for (int q = 0; q < 2 && q < nchunks; ++q) {
-      int k0, n;
-      chunk(q, k0, n);
-      const uint32_t bytes = (uint32_t)(n * kTraceRows * sizeof(C));
-      mbar_arrive_expect_tx(&bars[q], bytes);
-      bulk_g2s(ring + q * KC * kTraceRows, Gt + (long long)k0 * kTraceRows, bytes, &bars[q]);
-    }
+    const uint32_t bytes = (uint32_t)(n * kTraceRows * sizeof(C));
+    mbar_arrive_expect_tx(&bar, bytes);
+    bulk_g2s(Gs, gmap + gmap_index(g, p.factor, dout, tile, k0, 0), bytes, &bar);
   }
-  // columns past the panel read zeros
-  for (int idx = threadIdx.x; idx < (PC - p.ncol) * T; idx += blockDim.x)
-    vin[(long long)p.ncol * T + idx] = czero<C>();
-  bool ok = (p.ncol == 0 || in_bytes == 0) ? true : mbar_wait(&bars[2], 0);
-  const int r = threadIdx.x & (kTraceRows - 1);
-  const int h = threadIdx.x / kTraceRows;
-  C out[HPC];
-#pragma unroll
-  for (int c = 0; c < HPC; ++c) out[c] = czero<C>();
+  for (int idx = threadIdx.x; idx < PC * kTraceSeg; idx += blockDim.x) {
+    const int c = idx / kTraceSeg, kk = idx - c * kTraceSeg;
+    const long long b = cbase[c];
+    vin[idx] = (b >= 0 && kk < n) ? gtr[b + k0 + kk] : czero<C>();
+  }
+  const bool ok = mbar_wait(&bar, 0);
   if (__syncthreads_or(!ok)) {
     if (threadIdx.x == 0) {
       atomicExch(err, 3);
-      for (int q = 0; q < 2 && q < nchunks; ++q) mbar_wait(&bars[q], 0);
+      mbar_wait(&bar, 0);
     }
     __syncthreads();
     return;
   }
-  const C *vcol = vin + (long long)(h * HPC) * T;
-  for (int q = 0; q < nchunks; ++q) {
-    int k0, n;
-    chunk(q, k0, n);
-    const int buf = q & 1;
-    ok = mbar_wait(&bars[buf], (q >> 1) & 1);
-    const C *A = ring + buf * KC * kTraceRows;
-    if (h * HPC < PC) {
+  const int rp = threadIdx.x & 31, cq = threadIdx.x >> 5;
+  const C *A = Gs + 2 * rp;
+  const C *v0 = vin + (2 * cq) * kTraceSeg;
+  const C *v1 = v0 + kTraceSeg;
+  C o00 = czero<C>(), o01 = czero<C>(), o10 = czero<C>(), o11 = czero<C>();
 #pragma unroll 8
-      for (int i = 0; i < n; ++i) {
-        const C a = A[i * kTraceRows + r];
-#pragma unroll
-        for (int c = 0; c < HPC; ++c) cfma(out[c], a, vcol[(long long)c * T + k0 + i]);
-      }
-    }
-    if (__syncthreads_or(!ok)) {
-      if (threadIdx.x == 0) {
-        atomicExch(err, 3);
-        mbar_wait(&bars[buf], (q >> 1) & 1);
-        if (q + 1 < nchunks) mbar_wait(&bars[buf ^ 1], ((q + 1) >> 1) & 1);
-      }
-      __syncthreads();
-      return;
-    }
-    if (threadIdx.x == 0 && q + 2 < nchunks) {
-      int k2, n2;
-      chunk(q + 2, k2, n2);
-      const uint32_t bytes = (uint32_t)(n2 * kTraceRows * sizeof(C));
-      fence_proxy_async();
-      mbar_arrive_expect_tx(&bars[buf], bytes);
-      bulk_g2s(ring + buf * KC * kTraceRows, Gt + (long long)k2 * kTraceRows, bytes, &bars[buf]);
-    }
+  for (int i = 0; i < n; ++i) {
+    const C a0 = A[i * kTraceRows], a1 = A[i * kTraceRows + 1];
+    const C b0 = v0[i], b1 = v1[i];
+    cfma(o00, a0, b0);
+    cfma(o01, a0, b1);
+    cfma(o10, a1, b0);
+    cfma(o11, a1, b1);
   }
   const int rows = 2 * g.Lt[dout];
-  const int rr = tile * kTraceRows + r;
-  if (rr >= rows || h * HPC >= PC) return;
   const int lp = route[l * 6 + dout];
-  const int grow = g.toff[dout] + rr;   // row in the full trace vector
+  const bool first_seg = blockIdx.z == 0;
+  const C res[2][2] = {{o00, o01}, {o10, o11}};
 #pragma unroll
-  for (int c = 0; c < HPC; ++c) {
-    const int cg = h * HPC + c;
-    if (cg >= p.ncol) continue;
-    const Col cc = cols[p.col0 + cg];
-    C val = out[c];
-    if (rawf != nullptr) val = cadd(val, rawf[((long long)cc.rhs * g.nsub + cc.sub) * T + grow]);
-    const int nb = sub_neighbour(g, cc.sub, dout);
-    if (nb < 0 || lp < 0) continue;
-    C *dst = gtr + lp * slot_stride + ((long long)cc.rhs * g.nsub + nb) * T + g.toff[dout ^ 1] + rr;
-    *dst = cadd(*dst, val);
+  for (int i = 0; i < 2; ++i) {
+    const int rr = tile * kTraceRows + 2 * rp + i;
+    if (rr >= rows) continue;
+    const int grow = g.toff[dout] + rr;   // row in the full trace vector
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int cg = 2 * cq + j;
+      if (cg >= p.ncol) continue;
+      const Col cc = cols[p.col0 + cg];
+      C val = res[i][j];
+      if (rawf != nullptr && first_seg)
+        val = cadd(val, rawf[((long long)cc.rhs * g.nsub + cc.sub) * T + grow]);
+      const int nb = sub_neighbour(g, cc.sub, dout);
+      if (nb < 0 || lp < 0) continue;
+      atomic_cadd(gtr + lp * slot_stride + ((long long)cc.rhs * g.nsub + nb) * T +
+                      g.toff[dout ^ 1] + rr,
+                  val);
+    }
   }
 }
 
@@ -513,46 +503,32 @@ cudaError_t launch_extract(cudaStream_t st, const Geom &g, int ncols, const Col 
   return cudaGetLastError();
 }
 
-template <typename R, int PC>
-static cudaError_t trace_step_pc(cudaStream_t st, const Geom &g, int npanels,
-                                 const Panel *panels, const Col *cols,
-                                 const typename Cx<R>::T *gmap, typename Cx<R>::T *gtr,
-                                 const typename Cx<R>::T *rawf,
-                                 const int *route, int l, int nrhs, int in_mask, int out_mask,
-                                 int *err) {
-  using C = typename Cx<R>::T;
-  constexpr int KC = sizeof(R) == 4 ? 64 : 32;
-  const size_t smem = (size_t)(2 * KC * kTraceRows + (long long)g.T * PC) * sizeof(C) + 32;
-  static bool done[64] = {false};
-  cudaError_t e = smem_limit_once(k_trace_step<R, PC, KC>, done);
-  if (e != cudaSuccess) return e;
-  int nout = 0;
-  for (int d = 0; d < g.nsides; ++d) nout += (out_mask >> d) & 1;
-  const int tiles = trace_max_tiles(g);
-  if (nout == 0) return cudaSuccess;   // nothing is routed out of this sweep
-  dim3 grid(nout * tiles, npanels);
-  k_trace_step<R, PC, KC><<<grid, 256, smem, st>>>(g, panels, cols, gmap, gtr, rawf, route, l,
-                                                    nrhs, in_mask, out_mask, tiles, err);
-  return cudaGetLastError();
-}
-
-size_t trace_step_smem(const Geom &g, int pc, size_t elem) {
-  const int KC = elem == sizeof(float2) ? 64 : 32;
-  return (size_t)(2 * KC * kTraceRows + (long long)g.T * pc) * elem + 32;
-}
-
 template <typename R>
 cudaError_t launch_trace_step(cudaStream_t st, const Geom &g, int npanels, const Panel *panels,
                               const Col *cols, const typename Cx<R>::T *gmap,
-                              typename Cx<R>::T *g_traces,
-                              const typename Cx<R>::T *rawf, const int *route, int l, int nrhs,
-                              int pc, int in_mask, int out_mask, int *err) {
+                              typename Cx<R>::T *gtr, const typename Cx<R>::T *rawf,
+                              const int *route, int l, int nrhs, int pc, int in_mask,
+                              int out_mask, int *err) {
   if (npanels <= 0) return cudaSuccess;
-  switch (pc) {
-    case 4: return trace_step_pc<R, 4>(st, g, npanels, panels, cols, gmap, g_traces, rawf, route, l, nrhs, in_mask, out_mask, err);
-    case 8: return trace_step_pc<R, 8>(st, g, npanels, panels, cols, gmap, g_traces, rawf, route, l, nrhs, in_mask, out_mask, err);
-    default: return cudaErrorInvalidValue;
-  }
+  if (pc != 8) return cudaErrorInvalidValue;
+  int nout = 0;
+  for (int d = 0; d < g.nsides; ++d) nout += (out_mask >> d) & 1;
+  const int nseg = trace_nseg(g, in_mask);
+  if (nout == 0 || nseg == 0) return cudaSuccess;   // nothing routed out / nothing came in
+  using C = typename Cx<R>::T;
+  const size_t smem = ((size_t)kTraceSeg * kTraceRows + 8 * kTraceSeg) * sizeof(C) + 16;
+  static bool done[64] = {false};
+  cudaError_t e = smem_limit_once(k_trace_step<R>, done);
+  if (e != cudaSuccess) return e;
+  const int tiles = trace_max_tiles(g);
+  dim3 grid(nout * tiles, npanels, nseg);
+  k_trace_step<R><<<grid, 128, smem, st>>>(g, panels, cols, gmap, gtr, rawf, route, l, nrhs,
+                                           in_mask, out_mask, tiles, err);
+  return cudaGetLastError();
+}
+
+size_t trace_step_smem(const Geom &, int pc, size_t elem) {
+  return ((size_t)kTraceSeg * kTraceRows + (size_t)pc * kTraceSeg) * elem + 16;
 }
 
 template <typename R>
