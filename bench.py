@@ -228,6 +228,8 @@ def run_gpu(args):
     dev = torch.device("cuda", local)
     lbuild.build()
     wl = synth.workload(args.workload)
+    if args.rounds is not None:
+        wl.rounds = args.rounds
     R = wl.f.shape[0]
 
     ctx = dds.Context(wl.n, wl.h, wl.omega, wl.c, wl.parts, wl.pml_cells, wl.pml_strength,
@@ -378,6 +380,8 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--maxit", type=int, default=40)
     ap.add_argument("--plan", default="auto", choices=["auto", "direct", "trace"])
+    ap.add_argument("--rounds", type=int, default=None,
+                    help="DDM rounds per preconditioner application (default: the workload's)")
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--profile-steps", type=int, default=2)

@@ -91,6 +91,17 @@ struct dds_ctx {
   std::vector<int> in_mask, out_mask;  // per sweep: sides that can receive / must send a trace
   DBuf work, gtr, acc, rawf, bbuf, stage_in, stage_out, dots_part, dots_out, coefbuf, scalebuf;
   DBuf Vbig, Zbig;   // Krylov bases
+  // CUDA graphs of whole DDM applications, keyed by (b, u, nrhs, rounds); captured on gstream
+  struct GraphEntry { cudaGraphExec_t exec = nullptr; long long nodes = 0; };
+  std::map<std::array<long long, 4>, GraphEntry> graphs;
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t gev[2] = {nullptr, nullptr};
+  bool use_graphs = true;
+  void clear_graphs() {
+    for (auto &kv : graphs)
+      if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    graphs.clear();
+  }
   // profiler: event pairs around launches, folded into per-kind totals on read
   bool profiling = false;
   std::vector<std::array<cudaEvent_t, 2>> ev_pool;
@@ -99,6 +110,10 @@ struct dds_ctx {
   long long prof_count[DDS_K_COUNT] = {0};
   double prof_ms[DDS_K_COUNT] = {0};
   ~dds_ctx() {
+    clear_graphs();
+    if (gstream) cudaStreamDestroy(gstream);
+    for (auto &e : gev)
+      if (e) cudaEventDestroy(e);
     for (auto &e : ev_pool) {
       cudaEventDestroy(e[0]);
       cudaEventDestroy(e[1]);
@@ -378,13 +393,36 @@ dds_status check_errflag(dds_ctx *ctx) {
 // ------------------------------------------------------------------------------------------
 // one DDM application (Algorithm 2.1 / 4.1): b (J-scaled, device, nrhs fields) -> u (device)
 // ------------------------------------------------------------------------------------------
+// workspaces of one DDM application; *grown is set if any buffer moved (cached graphs go stale)
+template <typename R>
+dds_status prepare_ddm(dds_ctx *ctx, int nrhs, int rounds, bool *grown) {
+  using C = typename Cx<R>::T;
+  const Geom &g = ctx->g;
+  dds_status rs = set_route(ctx, rounds);
+  if (rs != DDS_OK) return rs;
+  CallPlan *cp = get_plan(ctx, nrhs);
+  if (!cp) { ctx->err = "failed to upload launch lists"; return DDS_ENOMEM; }
+  const int L = ctx->ndirs * rounds;
+  const long long slot = (long long)nrhs * g.nsub * g.T;
+  const bool trace_plan = ctx->plan == DDS_PLAN_TRACE;
+  long long work_cols = (long long)g.nsub * nrhs;
+  if (!trace_plan) {
+    work_cols = 0;
+    for (auto &sp : cp->steps) work_cols = std::max<long long>(work_cols, sp.ncols);
+  }
+  void *w0 = ctx->work.p, *g0 = ctx->gtr.p, *r0 = ctx->rawf.p;
+  CK(ctx->work.ensure(work_cols * g.Nloc * sizeof(C)));
+  CK(ctx->gtr.ensure(L * slot * sizeof(C)));
+  if (trace_plan) CK(ctx->rawf.ensure(slot * sizeof(C)));
+  *grown = w0 != ctx->work.p || g0 != ctx->gtr.p || r0 != ctx->rawf.p;
+  return DDS_OK;
+}
+
 template <typename R>
 dds_status run_ddm(dds_ctx *ctx, const double2 *b, int nrhs, double2 *u, int rounds) {
   using C = typename Cx<R>::T;
   const Geom &g = ctx->g;
   cudaStream_t st = ctx->stream;
-  dds_status rs = set_route(ctx, rounds);
-  if (rs != DDS_OK) return rs;
   CallPlan *cp = get_plan(ctx, nrhs);
   if (!cp) { ctx->err = "failed to upload launch lists"; return DDS_ENOMEM; }
   const C *sinv = ctx->precision == DDS_MIXED ? (const C *)ctx->sinv32.p : (const C *)ctx->sinv64.p;
@@ -393,13 +431,6 @@ dds_status run_ddm(dds_ctx *ctx, const double2 *b, int nrhs, double2 *u, int rou
   const int L = ctx->ndirs * rounds;
   const long long slot = (long long)nrhs * g.nsub * g.T;
   const bool trace_plan = ctx->plan == DDS_PLAN_TRACE;
-  const long long work_cols = trace_plan ? (long long)g.nsub * nrhs : [&] {
-    long long mx = 0;
-    for (auto &sp : cp->steps) mx = std::max<long long>(mx, sp.ncols);
-    return mx;
-  }();
-  CK(ctx->work.ensure(work_cols * g.Nloc * sizeof(C)));
-  CK(ctx->gtr.ensure(L * slot * sizeof(C)));
   CK(cudaMemsetAsync(ctx->gtr.p, 0, L * slot * sizeof(C), st));
   C *work = ctx->work.as<C>();
   C *gtr = ctx->gtr.as<C>();
@@ -421,7 +452,6 @@ dds_status run_ddm(dds_ctx *ctx, const double2 *b, int nrhs, double2 *u, int rou
       }
     }
   } else {
-    CK(ctx->rawf.ensure(slot * sizeof(C)));
     C *rawf = ctx->rawf.as<C>();
     const StepPlan &all = cp->all;
     // own sources: x_f = A_R^{-1} b_own; keep its raw trace lines
@@ -451,11 +481,65 @@ dds_status run_ddm(dds_ctx *ctx, const double2 *b, int nrhs, double2 *u, int rou
   return DDS_OK;
 }
 
+dds_status enqueue_ddm(dds_ctx *ctx, const double2 *b, int nrhs, double2 *u, int rounds) {
+  return ctx->precision == DDS_MIXED ? run_ddm<float>(ctx, b, nrhs, u, rounds)
+                                     : run_ddm<double>(ctx, b, nrhs, u, rounds);
+}
+
+// One DDM application.  Without profiling, the ~2 + (sweeps x steps) dependent launches are
+// captured once into a CUDA graph per (b, u, nrhs, rounds) and replayed on an internal stream
+// ordered after and before the caller's stream by events.
 dds_status ddm(dds_ctx *ctx, const double2 *b, int nrhs, double2 *u, int rounds) {
-  dds_status r = ctx->precision == DDS_MIXED ? run_ddm<float>(ctx, b, nrhs, u, rounds)
-                                             : run_ddm<double>(ctx, b, nrhs, u, rounds);
-  if (r == DDS_OK && ctx->ev_used > 4096) CK(prof_fold(ctx));
-  return r;
+  bool grown = false;
+  dds_status r = ctx->precision == DDS_MIXED ? prepare_ddm<float>(ctx, nrhs, rounds, &grown)
+                                             : prepare_ddm<double>(ctx, nrhs, rounds, &grown);
+  if (r != DDS_OK) return r;
+  if (grown) ctx->clear_graphs();
+  if (!ctx->use_graphs || ctx->profiling) {
+    r = enqueue_ddm(ctx, b, nrhs, u, rounds);
+    if (r == DDS_OK && ctx->ev_used > 4096) CK(prof_fold(ctx));
+    return r;
+  }
+  if (!ctx->gstream) {
+    CK(cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&ctx->gev[0], cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ctx->gev[1], cudaEventDisableTiming));
+  }
+  const std::array<long long, 4> key = {(long long)(uintptr_t)b, (long long)(uintptr_t)u, nrhs,
+                                         rounds};
+  auto it = ctx->graphs.find(key);
+  if (it == ctx->graphs.end()) {
+    if (ctx->graphs.size() >= 64) ctx->clear_graphs();
+    cudaStream_t caller = ctx->stream;
+    const long long l0 = ctx->launches;
+    ctx->stream = ctx->gstream;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      r = enqueue_ddm(ctx, b, nrhs, u, rounds);
+      e = cudaStreamEndCapture(ctx->gstream, &graph);
+    }
+    ctx->stream = caller;
+    if (e != cudaSuccess || r != DDS_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      if (r != DDS_OK) return r;
+      CK(e);
+    }
+    dds_ctx::GraphEntry ge;
+    ge.nodes = ctx->launches - l0;
+    ctx->launches = l0;
+    e = cudaGraphInstantiate(&ge.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(e);
+    it = ctx->graphs.emplace(key, ge).first;
+  }
+  CK(cudaEventRecord(ctx->gev[0], ctx->stream));
+  CK(cudaStreamWaitEvent(ctx->gstream, ctx->gev[0], 0));
+  CK(cudaGraphLaunch(it->second.exec, ctx->gstream));
+  CK(cudaEventRecord(ctx->gev[1], ctx->gstream));
+  CK(cudaStreamWaitEvent(ctx->stream, ctx->gev[1], 0));
+  ctx->launches += it->second.nodes;
+  return DDS_OK;
 }
 
 // ------------------------------------------------------------------------------------------

@@ -243,7 +243,8 @@ long long gmap_elems(const Geom &g, int nfac) { return gmap_index(g, nfac, 0, 0,
 // (segment x 64 rows, contiguous in the tiled layout) arrives by one bulk copy while the threads
 // gather the panel's inputs, then thread (rp = t & 31, cq = t >> 5) accumulates rows 2 rp,
 // 2 rp + 1 x columns 2 cq, 2 cq + 1 from shared memory.  Segments of one output add into the
-// destination slot with atomics (the slot accumulates with += in any case).
+// destination slot with atomics (the slot accumulates with += in any case).  The CTA has 256
+// threads: two halves share the segment and meet in shared memory.
 constexpr int kTraceSeg = 104;
 
 __host__ __device__ inline int trace_nseg(const Geom &g, int in_mask) {
@@ -264,7 +265,7 @@ template <> __device__ inline void atomic_cadd<double2>(double2 *dst, double2 v)
 }
 
 template <typename R>
-__global__ void __launch_bounds__(128) k_trace_step(Geom g, const Panel *__restrict__ panels,
+__global__ void __launch_bounds__(256) k_trace_step(Geom g, const Panel *__restrict__ panels,
                                                     const Col *__restrict__ cols,
                                                     const typename Cx<R>::T *__restrict__ gmap,
                                                     typename Cx<R>::T *__restrict__ gtr,
@@ -301,6 +302,7 @@ __global__ void __launch_bounds__(128) k_trace_step(Geom g, const Panel *__restr
     }
     sgi -= ns;
   }
+  // independent of the previous sweep step: barrier, column descriptors, the map slice
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
     mbar_init_fence();
@@ -317,6 +319,10 @@ __global__ void __launch_bounds__(128) k_trace_step(Geom g, const Panel *__restr
     mbar_arrive_expect_tx(&bar, bytes);
     bulk_g2s(Gs, gmap + gmap_index(g, p.factor, dout, tile, k0, 0), bytes, &bar);
   }
+  // the previous step's traces (programmatic dependent launch: wait for it only here, and let
+  // the next step start its own prologue)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   for (int idx = threadIdx.x; idx < PC * kTraceSeg; idx += blockDim.x) {
     const int c = idx / kTraceSeg, kk = idx - c * kTraceSeg;
     const long long b = cbase[c];
@@ -331,20 +337,75 @@ __global__ void __launch_bounds__(128) k_trace_step(Geom g, const Panel *__restr
     __syncthreads();
     return;
   }
-  const int rp = threadIdx.x & 31, cq = threadIdx.x >> 5;
+  // two halves of the segment, 128 threads each; thread (rp, cq) of a half: rows 2rp, 2rp+1,
+  // columns 2cq, 2cq+1.  Inputs are consumed four at a time with the next four prefetched.
+  const int half = threadIdx.x >> 7, lt = threadIdx.x & 127;
+  const int rp = lt & 31, cq = lt >> 5;
+  const int nh = ((n + 7) / 8) * 4;                 // inputs of half 0 (a multiple of 4)
+  const int i0 = half == 0 ? 0 : nh, i1 = half == 0 ? min(n, nh) : n;
   const C *A = Gs + 2 * rp;
   const C *v0 = vin + (2 * cq) * kTraceSeg;
   const C *v1 = v0 + kTraceSeg;
   C o00 = czero<C>(), o01 = czero<C>(), o10 = czero<C>(), o11 = czero<C>();
-#pragma unroll 8
-  for (int i = 0; i < n; ++i) {
-    const C a0 = A[i * kTraceRows], a1 = A[i * kTraceRows + 1];
-    const C b0 = v0[i], b1 = v1[i];
-    cfma(o00, a0, b0);
-    cfma(o01, a0, b1);
-    cfma(o10, a1, b0);
-    cfma(o11, a1, b1);
+  auto step4 = [&](const C (&a)[4][2], const C (&b0)[4], const C (&b1)[4]) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      cfma(o00, a[u][0], b0[u]);
+      cfma(o01, a[u][0], b1[u]);
+      cfma(o10, a[u][1], b0[u]);
+      cfma(o11, a[u][1], b1[u]);
+    }
+  };
+  auto load4 = [&](int i, C (&a)[4][2], C (&b0)[4], C (&b1)[4]) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      a[u][0] = A[(i + u) * kTraceRows];
+      a[u][1] = A[(i + u) * kTraceRows + 1];
+      b0[u] = v0[i + u];
+      b1[u] = v1[i + u];
+    }
+  };
+  int i = i0;
+  if (i + 4 <= i1) {
+    C a[4][2], b0[4], b1[4];
+    load4(i, a, b0, b1);
+    for (; i + 8 <= i1; i += 4) {
+      C an[4][2], bn0[4], bn1[4];
+      load4(i + 4, an, bn0, bn1);
+      step4(a, b0, b1);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a[u][0] = an[u][0];
+        a[u][1] = an[u][1];
+        b0[u] = bn0[u];
+        b1[u] = bn1[u];
+      }
+    }
+    step4(a, b0, b1);
+    i += 4;
   }
+  for (; i < i1; ++i) {
+    const C a0 = A[i * kTraceRows], a1 = A[i * kTraceRows + 1];
+    cfma(o00, a0, v0[i]);
+    cfma(o01, a0, v1[i]);
+    cfma(o10, a1, v0[i]);
+    cfma(o11, a1, v1[i]);
+  }
+  // half 1 hands its partial sums to half 0 (the input buffer is free once both are done)
+  __syncthreads();
+  C *red = vin + (long long)lt * 4;
+  if (half == 1) {
+    red[0] = o00;
+    red[1] = o01;
+    red[2] = o10;
+    red[3] = o11;
+  }
+  __syncthreads();
+  if (half == 1) return;
+  o00 = cadd(o00, red[0]);
+  o01 = cadd(o01, red[1]);
+  o10 = cadd(o10, red[2]);
+  o11 = cadd(o11, red[3]);
   const int rows = 2 * g.Lt[dout];
   const int lp = route[l * 6 + dout];
   const bool first_seg = blockIdx.z == 0;
@@ -521,10 +582,18 @@ cudaError_t launch_trace_step(cudaStream_t st, const Geom &g, int npanels, const
   cudaError_t e = smem_limit_once(k_trace_step<R>, done);
   if (e != cudaSuccess) return e;
   const int tiles = trace_max_tiles(g);
-  dim3 grid(nout * tiles, npanels, nseg);
-  k_trace_step<R><<<grid, 128, smem, st>>>(g, panels, cols, gmap, gtr, rawf, route, l, nrhs,
-                                           in_mask, out_mask, tiles, err);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nout * tiles, npanels, nseg);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_trace_step<R>, g, panels, cols, gmap, gtr, rawf, route, l,
+                            nrhs, in_mask, out_mask, tiles, err);
 }
 
 size_t trace_step_smem(const Geom &, int pc, size_t elem) {

@@ -105,7 +105,8 @@ def workload(name: str, nrhs: int | None = None) -> Workload:
     const2d_128   2D, 128^2 interior, h = 1/128, kappa = 2 pi 8, 2x2 subdomains, 16-cell PML,
                   one Gaussian (w = 2h) at (0.5, 0.5), direct FP64 DDM, one round.
     const2d_640   2D, 640^2, kappa = 2 pi 40, 8x8 subdomains of 80^2, 12-cell PML, 16 Gaussians
-                  at seeded uniform centres, mixed precision + FGMRES to 1e-6.
+                  at seeded uniform centres, mixed precision + FGMRES to 1e-6 with two rounds of
+                  sweeps per preconditioner application.
     layer2d_1024  2D two-layer (c = 1 below y = 0.37, 1.5 above), omega = 2 pi 50, 1024^2,
                   16x16 subdomains, 12-cell PML, 64 seeded Gaussians, FGMRES to 1e-6.
     const3d_128   3D, 128^3, kappa = 2 pi 10, 4x4x4 subdomains of 32^3, 8-cell PML, 8 Gaussians.
@@ -123,7 +124,7 @@ def workload(name: str, nrhs: int | None = None) -> Workload:
         w = 2 * h
         cen = uniform_centres(np.random.default_rng(2), R, 2, 6 * w, 1 - 6 * w)
         return Workload(name, n, (8, 8), 2 * math.pi * 40, 12, 30.0, medium_constant(n),
-                        gaussian_sources(n, h, cen, w), "mixed", 1, 1e-6)
+                        gaussian_sources(n, h, cen, w), "mixed", 2, 1e-6)
     if name == "layer2d_1024":
         n = (1024, 1024)
         h = 1.0 / 1024
