@@ -293,9 +293,13 @@ def run_gpu(args):
 
     # roofline of the dominant kernel family, timed with CUDA events on the library's stream
     ctx.profile(True)
+    ddm_apps = 0
     for _ in range(args.profile_steps):
-        ctx.solve(f_dev, tol=args.tol, maxit=args.maxit, rounds=wl.rounds)
+        _, it_p, _ = ctx.solve(f_dev, tol=args.tol, maxit=args.maxit, rounds=wl.rounds)
+        ddm_apps += it_p
     stats = ctx.kernel_stats()
+    # local solves of the direct plan during the profiled solves (2^n sweeps per round)
+    args.ddm_solves_profiled = ddm_apps * (2 ** len(wl.n)) * wl.rounds * info["n_sub"] * R
     ctx.profile(False)
     roofline = roofline_entry(stats, info, wl, R, args) if args.profile_steps > 0 else None
 
@@ -352,14 +356,27 @@ def roofline_entry(stats, info, wl, R, args):
     """
     peaks, src = _peaks()
     n_sub = info["n_sub"]
-    M = info["M"][0]
-    Ml, Mb = M, M                                  # 2D: lines of M nodes
+    dim = len(wl.n)
+    Mext = info["M"][:dim]
+    Ml = Mext[-1]                                  # blocks along the last axis
+    Mb = 1
+    for m in Mext[:-1]:
+        Mb *= m                                    # nodes of one line (2D) / plane (3D)
     flops_per_solve = 16.0 * Ml * Mb * Mb
     n_launch, ms = stats["subst"]
     if n_launch == 0 or ms <= 0:
         return None
-    # each DDM application runs two substitution launches over all (subdomain, RHS) columns
-    solves_per_launch = n_sub * R
+    # trace plan: each DDM application runs two substitution launches over all (subdomain, RHS)
+    # columns; direct plan: one launch per sweep step over that step's columns
+    if info["plan"] == 2:
+        solves_per_launch = n_sub * R
+    else:
+        # (sweeps x subdomains x RHS local solves per DDM, spread over its step launches)
+        solves_per_launch = None
+    if solves_per_launch is None:
+        # total local solves of the profiled solves / launches: the FGMRES iteration count is
+        # not known here, so take the per-launch average over the whole profiled run
+        solves_per_launch = args.ddm_solves_profiled / n_launch
     achieved = flops_per_solve * solves_per_launch / (ms / n_launch / 1e3) / 1e12
     fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12       # FP32 FMA lanes x 2 flop x max SM clock
     return {"kernel": "k_subst<float> (block forward+back substitution)", "bound": "alu",

@@ -648,12 +648,9 @@ dds_status setup_impl(dds_ctx *ctx, const dds_problem *p) {
     ctx->err = "trace vectors too long for the trace-operator plan (T = " + std::to_string(g.T) + ")";
     return DDS_EINVAL;
   }
-  const size_t smem_need = (size_t)g.Mb * g.Mb * 16 + g.Mb * 20;
-  if (smem_need > 227 * 1024) {
-    ctx->err = "line block too large for the in-shared-memory Schur factorisation (Mb = " +
-               std::to_string(g.Mb) + ")";
-    return DDS_EINVAL;
-  }
+  // line blocks that fit in shared memory are factored by one CTA per operator; larger ones
+  // in global memory, one pivot step per launch
+  const bool big_blocks = (size_t)g.Mb * g.Mb * 16 + g.Mb * 20 > 227 * 1024;
   const int dim = p->dim;
   const double h = p->h;
   const double ih2 = 1.0 / (h * h);
@@ -842,9 +839,23 @@ dds_status setup_impl(dds_ctx *ctx, const dds_problem *p) {
   CK(cudaMemsetAsync(ctx->errflag.p, 0, sizeof(int), st));
   CK(cudaMemsetAsync(ctx->sinv64.p, 0, sinv_elems * sizeof(double2), st));
   CK(cudaMemsetAsync(ctx->sinv32.p, 0, sinv_elems * sizeof(float2), st));
-  LAUNCH(launch_factor(st, ctx->nfac, Mb, Ml, g.St, g.M[0], ddg.as<double2>(), doffx.as<double2>(),
-                       dim == 3 ? doffy.as<double2>() : nullptr, dcpl.as<double2>(),
-                       ctx->sinv64.as<double2>(), ctx->sinv32.as<float2>(), ctx->status.as<int>()));
+  if (!big_blocks) {
+    LAUNCH(launch_factor(st, ctx->nfac, Mb, Ml, g.St, g.M[0], ddg.as<double2>(), doffx.as<double2>(),
+                         dim == 3 ? doffy.as<double2>() : nullptr, dcpl.as<double2>(),
+                         ctx->sinv64.as<double2>(), ctx->sinv32.as<float2>(), ctx->status.as<int>()));
+  } else {
+    DBuf Sbuf, colk, piv;
+    CK(Sbuf.ensure((size_t)Mb * Mb * sizeof(double2)));
+    CK(colk.ensure((size_t)Mb * sizeof(double2)));
+    CK(piv.ensure((size_t)Mb * sizeof(int)));
+    for (int f = 0; f < ctx->nfac; ++f)
+      CK(launch_factor_big(st, f, Mb, Ml, g.St, g.M[0], ddg.as<double2>(), doffx.as<double2>(),
+                           dim == 3 ? doffy.as<double2>() : nullptr, dcpl.as<double2>(),
+                           Sbuf.as<double2>(), colk.as<double2>(), piv.as<int>(),
+                           ctx->sinv64.as<double2>(), ctx->sinv32.as<float2>(),
+                           ctx->status.as<int>(), &ctx->launches));
+    CK(cudaStreamSynchronize(st));
+  }
   int status = 0;
   CK(cudaMemcpyAsync(&status, ctx->status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));

@@ -159,6 +159,12 @@ cudaError_t launch_factor(cudaStream_t st, int nfac, int Mb, int Ml, long long S
                           const double2 *offx, const double2 *offy, const double2 *cpl,
                           double2 *sinv64, float2 *sinv32, int *status);
 
+cudaError_t launch_factor_big(cudaStream_t st, int f, int Mb, int Ml, long long St, int M0,
+                              const double2 *dg, const double2 *offx, const double2 *offy,
+                              const double2 *cpl, double2 *S, double2 *colk, int *piv,
+                              double2 *sinv64, float2 *sinv32, int *status,
+                              long long *launches);
+
 template <typename R>
 cudaError_t launch_assemble(cudaStream_t st, const Geom &g, const Tables &tb, int ncols,
                             const Col *cols, typename Cx<R>::T *work, const double2 *b,

@@ -202,3 +202,41 @@ def test_invalid_problem_is_rejected():
         dds.Context((30, 30), 1 / 30, 10.0, np.ones((30, 30)), (4, 4), 4)   # 30 % 4 != 0
     with pytest.raises(dds.DDSError):
         dds.Context((30, 30), 1 / 30, 10.0, -np.ones((30, 30)), (3, 3), 4)  # c <= 0
+
+
+# ----------------------------------------------------------------------------- large blocks --
+
+def test_large_block_local_solve_and_ddm_2d():
+    """Line blocks too large for the in-shared-memory factorisation (Mb = 136): the global-memory
+    Schur / Gauss-Jordan path, checked by a local solve and a whole FP64 DDM."""
+    n = (240, 240)
+    prob, f = _case(n, (2, 2), 8, 2 * np.pi * 6, c=_medium("layer", n), centres=[(0.4, 0.3)])
+    assert prob.M[0] == 136
+    ctx = _ctx(prob, "fp64", "direct")
+    rng = np.random.default_rng(3)
+    dims = prob.M[::-1]
+    b = rng.standard_normal((2,) + dims) + 1j * rng.standard_normal((2,) + dims)
+    loc = LocalProblems(prob)
+    x = ctx.local_solve(3, _on_dev(b)).cpu().numpy()
+    assert _rel(x, loc.solve((1, 1), b)) < 1e-11
+    bb = rhs_from_source(prob, extend_interior(prob, f))
+    ref = ddm_solve(prob, bb, 1, loc)
+    got = ctx.sweep(_on_dev(ctx.extend(f))).cpu().numpy()
+    assert _rel(got[0], ref[0]) < 1e-10
+
+
+def test_large_block_3d_ddm_and_fgmres():
+    """3D with plane blocks of 400 nodes (7-point stencil, 2x2x2): FP64 DDM vs the oracle, and
+    mixed FGMRES vs the global solve."""
+    n = (24, 24, 24)
+    prob, f = _case(n, (2, 2, 2), 4, 2 * np.pi * 2, centres=[(0.45, 0.55, 0.5)])
+    assert prob.M[0] * prob.M[1] == 400
+    ctx = _ctx(prob, "fp64", "direct")
+    bb = rhs_from_source(prob, extend_interior(prob, f))
+    ref = ddm_solve(prob, bb, 1)
+    got = ctx.sweep(_on_dev(ctx.extend(f))).cpu().numpy()
+    assert _rel(got[0], ref[0]) < 1e-10
+    ctxm = _ctx(prob, "mixed", "direct")
+    u, it, rel = ctxm.solve(_on_dev(ctx.extend(f)), tol=1e-9, maxit=30)
+    ug = global_solve(prob, bb)
+    assert rel[0] < 1e-9 and _rel(u.cpu().numpy()[0], ug[0]) < 1e-6
