@@ -137,6 +137,32 @@ dds_status dds_local_solve(dds_ctx *ctx, int sub, const void *b, int nrhs, void 
  * overlap on the GPU (other contexts or streams on the same device) race on it. */
 dds_status dds_local_solve_noalloc(dds_ctx *ctx, int sub, const void *b, int nrhs, void *x);
 
+/* ---- continuous-batching server (serving several requests against one set-up context) ------
+ * A server owns max_slots right-hand-side slots, each running its own right-preconditioned
+ * FGMRES (the dds_solve algorithm).  dds_server_step admits queued right-hand sides into free
+ * slots, applies ONE batched DDM application (`rounds` rounds) to the current Krylov vector of
+ * every active slot, completes that iteration's FP64 Arnoldi step per slot, and retires slots
+ * whose relative residual is below tol (or that reached maxit).  Requests submitted while others
+ * are in flight therefore join at the next iteration.  Slot memory ((2 maxit + 3) fields per
+ * slot) is allocated by dds_server_create; max_slots is the admission limit. */
+typedef struct dds_server dds_server;
+
+dds_status dds_server_create(dds_ctx *ctx, int max_slots, double tol, int maxit, int rounds,
+                             dds_server **out);
+
+/* queue one source field f (global extended grid, complex double, host or device); tag is
+ * returned with its solution.  The field is copied before the call returns. */
+dds_status dds_server_submit(dds_server *srv, const void *f, long long tag);
+
+/* one batched iteration; *active = slots in flight after it, *queued = requests still waiting */
+dds_status dds_server_step(dds_server *srv, int *active, int *queued);
+
+/* pop one finished request: tag, solution u (host or device, one field), FGMRES iterations and
+ * final true relative residual.  Returns DDS_EBUSY (and touches nothing) when none is ready. */
+dds_status dds_server_poll(dds_server *srv, long long *tag, void *u, int *iters, double *relres);
+
+void dds_server_destroy(dds_server *srv);
+
 /* dds_set_stream -- run all later work of ctx on the given cudaStream_t (NULL = the context's
  * own stream).  Calls still return only after their work has completed. */
 dds_status dds_set_stream(dds_ctx *ctx, void *cuda_stream);

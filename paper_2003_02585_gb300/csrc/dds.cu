@@ -10,6 +10,7 @@
 #include <complex>
 #include <cstdio>
 #include <cstring>
+#include <deque>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -1264,6 +1265,297 @@ void dds_destroy(dds_ctx *ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   else cudaDeviceSynchronize();
   delete ctx;
+}
+
+}  // extern "C"
+
+// ============================================================================================
+// Continuous-batching server: one FGMRES per slot, one batched DDM per step for all slots
+// ============================================================================================
+struct dds_server {
+  dds_ctx *ctx = nullptr;
+  int S = 0, maxit = 0, rounds = 1;
+  double tol = 1e-6;
+  long long N = 0;
+  DBuf V, Z, B, U, bin, bout, hdev, part, coef;
+  struct Slot {
+    int state = 0;              // 0 free, 1 active, 2 finished (waiting for poll)
+    long long tag = 0;
+    int j = 0, kused = 0;
+    double beta = 0, relres = 0;
+    std::vector<cd> H, cs, sn, g;
+  };
+  std::vector<Slot> slots;
+  std::deque<std::pair<long long, std::unique_ptr<DBuf>>> queue;
+  std::deque<int> finished;
+  double2 *Vs(int s, int j) { return V.as<double2>() + ((long long)s * (maxit + 1) + j) * N; }
+  double2 *Zs(int s, int j) { return Z.as<double2>() + ((long long)s * maxit + j) * N; }
+  double2 *Bs(int s) { return B.as<double2>() + (long long)s * N; }
+  double2 *Us(int s) { return U.as<double2>() + (long long)s * N; }
+  double2 *Hd(int s) { return hdev.as<double2>() + (long long)s * (2 * maxit + 3); }
+};
+
+namespace {
+
+#define SCK(call)                                                                \
+  do {                                                                           \
+    cudaError_t e_ = (call);                                                     \
+    if (e_ != cudaSuccess) {                                                     \
+      srv->ctx->err = std::string(#call) + ": " + cudaGetErrorString(e_);        \
+      return DDS_ECUDA;                                                          \
+    }                                                                            \
+  } while (0)
+
+int server_nblk(const dds_server *srv) {
+  return (int)((srv->N + dots_chunk() - 1) / dots_chunk());
+}
+
+// x = sum_i Z_i y_i from the slot's Hessenberg system, then the true residual
+dds_status server_finalize(dds_server *srv, int s) {
+  dds_ctx *ctx = srv->ctx;
+  auto &sl = srv->slots[s];
+  const int m = srv->maxit, kr = sl.kused;
+  auto Hat = [&](int i, int jj) -> cd & { return sl.H[(size_t)i * m + jj]; };
+  std::vector<cd> y(kr, cd(0, 0));
+  for (int i = kr - 1; i >= 0; --i) {
+    cd t = sl.g[i];
+    for (int q = i + 1; q < kr; ++q) t -= Hat(i, q) * y[q];
+    y[i] = t / Hat(i, i);
+  }
+  cudaStream_t st = ctx->stream;
+  const long long N = srv->N;
+  SCK(cudaMemsetAsync(srv->Us(s), 0, N * sizeof(double2), st));
+  if (kr > 0) {
+    std::vector<double2> yc(kr);
+    for (int i = 0; i < kr; ++i) yc[i] = make_double2(y[i].real(), y[i].imag());
+    SCK(cudaMemcpyAsync(srv->coef.p, yc.data(), kr * sizeof(double2), cudaMemcpyHostToDevice, st));
+    ++ctx->launches;
+    SCK(launch_sub_combination(st, N, 1, kr, srv->Zs(s, 0), N, 0, srv->coef.as<double2>(),
+                               srv->Us(s), 0, 1.0, kr));
+  }
+  // residual: W = A x - b in the slot's last basis vector (no longer needed)
+  double2 *W = srv->Vs(s, 0);
+  ctx->launches += 4;
+  SCK(launch_apply_A(st, ctx->g, ctx->tb, 1, srv->Us(s), W, 0));
+  const double2 one = make_double2(1.0, 0.0);
+  SCK(cudaMemcpyAsync(srv->coef.p, &one, sizeof(double2), cudaMemcpyHostToDevice, st));
+  SCK(launch_sub_combination(st, N, 1, 1, srv->Bs(s), 0, 0, srv->coef.as<double2>(), W, 0, -1.0, 1));
+  SCK(launch_dots(st, N, 1, 1, W, 0, 0, W, 0, srv->part.as<double2>(), srv->Hd(s),
+                  server_nblk(srv)));
+  double2 r2;
+  SCK(cudaMemcpyAsync(&r2, srv->Hd(s), sizeof(double2), cudaMemcpyDeviceToHost, st));
+  SCK(cudaStreamSynchronize(st));
+  sl.relres = sl.beta > 0 ? std::sqrt(std::max(r2.x, 0.0)) / sl.beta : 0.0;
+  sl.state = 2;
+  srv->finished.push_back(s);
+  return DDS_OK;
+}
+
+dds_status server_admit(dds_server *srv) {
+  dds_ctx *ctx = srv->ctx;
+  cudaStream_t st = ctx->stream;
+  const long long N = srv->N;
+  for (int s = 0; s < srv->S && !srv->queue.empty(); ++s) {
+    auto &sl = srv->slots[s];
+    if (sl.state != 0) continue;
+    auto req = std::move(srv->queue.front());
+    srv->queue.pop_front();
+    sl = dds_server::Slot();
+    sl.state = 1;
+    sl.tag = req.first;
+    const int m = srv->maxit;
+    sl.H.assign((size_t)(m + 1) * m, cd(0, 0));
+    sl.cs.assign(m, cd(0, 0));
+    sl.sn.assign(m, cd(0, 0));
+    sl.g.assign(m + 1, cd(0, 0));
+    ctx->launches += 3;
+    SCK(launch_scale_J(st, ctx->g, ctx->tb, 1, req.second->as<double2>(), srv->Bs(s)));
+    SCK(launch_dots(st, N, 1, 1, srv->Bs(s), 0, 0, srv->Bs(s), 0, srv->part.as<double2>(),
+                    srv->Hd(s), server_nblk(srv)));
+    SCK(launch_scale_by_norm(st, N, 1, srv->Bs(s), srv->Hd(s), srv->Vs(s, 0)));
+    double2 b2;
+    SCK(cudaMemcpyAsync(&b2, srv->Hd(s), sizeof(double2), cudaMemcpyDeviceToHost, st));
+    SCK(cudaStreamSynchronize(st));
+    sl.beta = std::sqrt(std::max(b2.x, 0.0));
+    sl.g[0] = sl.beta;
+    if (sl.beta == 0.0) {   // zero source: the solution is zero
+      sl.kused = 0;
+      dds_status r = server_finalize(srv, s);
+      if (r != DDS_OK) return r;
+    }
+  }
+  return DDS_OK;
+}
+
+dds_status server_step(dds_server *srv, int *active_out, int *queued_out) {
+  dds_ctx *ctx = srv->ctx;
+  cudaStream_t st = ctx->stream;
+  const long long N = srv->N;
+  dds_status r = server_admit(srv);
+  if (r != DDS_OK) return r;
+  std::vector<int> act;
+  for (int s = 0; s < srv->S; ++s)
+    if (srv->slots[s].state == 1) act.push_back(s);
+  const int k = (int)act.size();
+  if (k > 0) {
+    // one batched DDM application over every active slot's current Krylov vector
+    for (int i = 0; i < k; ++i)
+      SCK(cudaMemcpyAsync(srv->bin.as<double2>() + (long long)i * N,
+                          srv->Vs(act[i], srv->slots[act[i]].j), N * sizeof(double2),
+                          cudaMemcpyDeviceToDevice, st));
+    r = ddm(ctx, srv->bin.as<double2>(), k, srv->bout.as<double2>(), srv->rounds);
+    if (r != DDS_OK) return r;
+    const int nblk = server_nblk(srv);
+    for (int i = 0; i < k; ++i) {
+      const int s = act[i];
+      const int j = srv->slots[s].j;
+      double2 *Zj = srv->Zs(s, j), *W = srv->Vs(s, j + 1), *h = srv->Hd(s);
+      SCK(cudaMemcpyAsync(Zj, srv->bout.as<double2>() + (long long)i * N, N * sizeof(double2),
+                          cudaMemcpyDeviceToDevice, st));
+      // FP64 Arnoldi step: classical Gram-Schmidt applied twice, then normalisation
+      ctx->launches += 7;
+      SCK(launch_apply_A(st, ctx->g, ctx->tb, 1, Zj, W, 0));
+      SCK(launch_dots(st, N, 1, j + 1, srv->Vs(s, 0), N, 0, W, 0, srv->part.as<double2>(), h, nblk));
+      SCK(launch_sub_combination(st, N, 1, j + 1, srv->Vs(s, 0), N, 0, h, W, 0, -1.0, j + 1));
+      SCK(launch_dots(st, N, 1, j + 1, srv->Vs(s, 0), N, 0, W, 0, srv->part.as<double2>(),
+                      h + srv->maxit + 1, nblk));
+      SCK(launch_sub_combination(st, N, 1, j + 1, srv->Vs(s, 0), N, 0, h + srv->maxit + 1, W, 0,
+                                 -1.0, j + 1));
+      SCK(launch_dots(st, N, 1, 1, W, 0, 0, W, 0, srv->part.as<double2>(), h + 2 * srv->maxit + 2,
+                      nblk));
+      SCK(launch_scale_by_norm(st, N, 1, W, h + 2 * srv->maxit + 2, W));
+    }
+    const int stride = 2 * srv->maxit + 3;
+    std::vector<double2> hh((size_t)srv->S * stride);
+    SCK(cudaMemcpyAsync(hh.data(), srv->hdev.p, hh.size() * sizeof(double2), cudaMemcpyDeviceToHost, st));
+    SCK(cudaStreamSynchronize(st));
+    const int m = srv->maxit;
+    for (int i = 0; i < k; ++i) {
+      const int s = act[i];
+      auto &sl = srv->slots[s];
+      const int j = sl.j;
+      const double2 *h = hh.data() + (size_t)s * stride;
+      auto Hat = [&](int a, int b) -> cd & { return sl.H[(size_t)a * m + b]; };
+      for (int q = 0; q <= j; ++q) Hat(q, j) = cd(h[q].x + h[m + 1 + q].x, h[q].y + h[m + 1 + q].y);
+      const double hn = std::sqrt(std::max(h[2 * m + 2].x, 0.0));
+      Hat(j + 1, j) = hn;
+      for (int q = 0; q < j; ++q) {
+        const cd a = Hat(q, j), bb = Hat(q + 1, j), c = sl.cs[q], sn = sl.sn[q];
+        Hat(q, j) = c * a + sn * bb;
+        Hat(q + 1, j) = -std::conj(sn) * a + std::conj(c) * bb;
+      }
+      const cd a = Hat(j, j), bb = Hat(j + 1, j);
+      const double rr = std::hypot(std::abs(a), std::abs(bb));
+      cd c(1, 0), sn(0, 0);
+      if (rr > 0) { c = std::conj(a / rr); sn = std::conj(bb / rr); }
+      sl.cs[j] = c;
+      sl.sn[j] = sn;
+      Hat(j, j) = c * a + sn * bb;
+      Hat(j + 1, j) = 0.0;
+      const cd gj = sl.g[j];
+      sl.g[j + 1] = -std::conj(sn) * gj;
+      sl.g[j] = c * gj;
+      sl.j = j + 1;
+      sl.kused = j + 1;
+      const double res = std::abs(sl.g[j + 1]) / sl.beta;
+      if (res < srv->tol || hn == 0.0 || sl.j >= m) {
+        r = server_finalize(srv, s);
+        if (r != DDS_OK) return r;
+      }
+    }
+  }
+  r = check_errflag(ctx);
+  if (r != DDS_OK) return r;
+  int a = 0;
+  for (auto &sl : srv->slots) a += sl.state == 1;
+  if (active_out) *active_out = a;
+  if (queued_out) *queued_out = (int)srv->queue.size();
+  return DDS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dds_status dds_server_create(dds_ctx *ctx, int max_slots, double tol, int maxit, int rounds,
+                             dds_server **out) {
+  if (!ctx || !out || max_slots < 1 || maxit < 1 || rounds < 1 || !(tol > 0)) return DDS_EINVAL;
+  std::unique_ptr<dds_server> srv(new (std::nothrow) dds_server());
+  if (!srv) return DDS_ENOMEM;
+  srv->ctx = ctx;
+  srv->S = max_slots;
+  srv->maxit = maxit;
+  srv->rounds = rounds;
+  srv->tol = tol;
+  srv->N = ctx->g.Nglob;
+  const size_t fb = (size_t)srv->N * sizeof(double2);
+  const size_t S = (size_t)max_slots;
+  bool ok = srv->V.ensure(S * (maxit + 1) * fb) == cudaSuccess &&
+            srv->Z.ensure(S * maxit * fb) == cudaSuccess &&
+            srv->B.ensure(S * fb) == cudaSuccess && srv->U.ensure(S * fb) == cudaSuccess &&
+            srv->bin.ensure(S * fb) == cudaSuccess && srv->bout.ensure(S * fb) == cudaSuccess &&
+            srv->hdev.ensure(S * (2 * maxit + 3) * sizeof(double2)) == cudaSuccess &&
+            srv->part.ensure((size_t)(maxit + 2) * (srv->N / dots_chunk() + 2) * sizeof(double2)) ==
+                cudaSuccess &&
+            srv->coef.ensure((size_t)(maxit + 2) * sizeof(double2)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    ctx->err = "dds_server_create: device memory for " + std::to_string(max_slots) +
+               " slots is not available";
+    return DDS_ENOMEM;
+  }
+  srv->slots.resize(max_slots);
+  *out = srv.release();
+  return DDS_OK;
+}
+
+dds_status dds_server_submit(dds_server *srv, const void *f, long long tag) {
+  if (!srv || !f) return DDS_EINVAL;
+  dds_ctx *ctx = srv->ctx;
+  Busy busy(ctx);
+  if (!busy.ok) return DDS_EBUSY;
+  auto buf = std::make_unique<DBuf>();
+  const size_t fb = (size_t)srv->N * sizeof(double2);
+  CK(buf->ensure(fb));
+  CK(cudaMemcpyAsync(buf->p, f, fb, is_device_ptr(f) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                     ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  srv->queue.emplace_back(tag, std::move(buf));
+  return DDS_OK;
+}
+
+dds_status dds_server_step(dds_server *srv, int *active, int *queued) {
+  if (!srv) return DDS_EINVAL;
+  Busy busy(srv->ctx);
+  if (!busy.ok) return DDS_EBUSY;
+  srv->ctx->err.clear();
+  return server_step(srv, active, queued);
+}
+
+dds_status dds_server_poll(dds_server *srv, long long *tag, void *u, int *iters, double *relres) {
+  if (!srv || !u) return DDS_EINVAL;
+  dds_ctx *ctx = srv->ctx;
+  Busy busy(ctx);
+  if (!busy.ok) return DDS_EBUSY;
+  if (srv->finished.empty()) return DDS_EBUSY;
+  const int s = srv->finished.front();
+  auto &sl = srv->slots[s];
+  const size_t fb = (size_t)srv->N * sizeof(double2);
+  CK(cudaMemcpyAsync(u, srv->Us(s), fb, is_device_ptr(u) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (tag) *tag = sl.tag;
+  if (iters) *iters = sl.kused;
+  if (relres) *relres = sl.relres;
+  srv->finished.pop_front();
+  sl.state = 0;
+  return DDS_OK;
+}
+
+void dds_server_destroy(dds_server *srv) {
+  if (!srv) return;
+  if (srv->ctx && srv->ctx->stream) cudaStreamSynchronize(srv->ctx->stream);
+  delete srv;
 }
 
 }  // extern "C"

@@ -24,7 +24,9 @@ PLAN = {"auto": 0, "direct": 1, "trace": 2}
 
 EXPORTS = ["dds_setup", "dds_sweep", "dds_solve", "dds_apply", "dds_local_solve",
            "dds_set_stream", "dds_get_info", "dds_kernel_launches", "dds_last_error",
-           "dds_destroy", "dds_profile", "dds_profile_read", "dds_local_solve_noalloc"]
+           "dds_destroy", "dds_profile", "dds_profile_read", "dds_local_solve_noalloc",
+           "dds_server_create", "dds_server_submit", "dds_server_step", "dds_server_poll",
+           "dds_server_destroy"]
 KERNEL_KINDS = {"assemble": 0, "subst": 1, "extract": 2, "trace_step": 3, "krylov": 4,
                 "other": 5}
 
@@ -77,12 +79,21 @@ def load(path: str = LIB_PATH):
     lib.dds_last_error.restype = ctypes.c_char_p
     lib.dds_destroy.argtypes = [vp]
     lib.dds_destroy.restype = None
+    lib.dds_server_create.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                      ctypes.c_int, ctypes.POINTER(vp)]
+    lib.dds_server_submit.argtypes = [vp, vp, ctypes.c_longlong]
+    lib.dds_server_step.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    lib.dds_server_poll.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), vp,
+                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
+    lib.dds_server_destroy.argtypes = [vp]
+    lib.dds_server_destroy.restype = None
     lib.dds_profile.argtypes = [vp, ctypes.c_int]
     lib.dds_profile_read.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
                                      ctypes.POINTER(ctypes.c_double)]
     for name in ["dds_setup", "dds_sweep", "dds_solve", "dds_apply", "dds_local_solve",
                  "dds_set_stream", "dds_get_info", "dds_profile", "dds_profile_read",
-                 "dds_local_solve_noalloc"]:
+                 "dds_local_solve_noalloc", "dds_server_create", "dds_server_submit",
+                 "dds_server_step", "dds_server_poll"]:
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -275,3 +286,58 @@ class Context:
         E = (self.G[0] - self.n[0]) // 2
         sl = tuple(slice(E, E + na) for na in self.n[::-1])
         return u_ext[(Ellipsis,) + sl]
+
+
+class Server:
+    """Continuous-batching server over one Context (dds_server_*): every step admits queued
+    right-hand sides into free slots and advances all active ones by one FGMRES iteration with a
+    single batched DDM application."""
+
+    def __init__(self, ctx: Context, max_slots: int, tol: float = 1e-6, maxit: int = 30,
+                 rounds: int = 1):
+        self.ctx = ctx
+        self._lib = ctx._lib
+        h = ctypes.c_void_p()
+        st = self._lib.dds_server_create(ctx._h, int(max_slots), float(tol), int(maxit),
+                                         int(rounds), ctypes.byref(h))
+        if st != 0:
+            raise DDSError(st, self._lib.dds_last_error(ctx._h).decode())
+        self._h = h
+        self.G = ctx.G
+
+    def submit(self, f, tag: int):
+        f, _ = self.ctx._fields(f)
+        self.ctx._bind_stream(f)
+        self.ctx._check(self._lib.dds_server_submit(self._h, self.ctx._ptr(f), int(tag)))
+
+    def step(self):
+        a = ctypes.c_int(0)
+        q = ctypes.c_int(0)
+        self.ctx._check(self._lib.dds_server_step(self._h, ctypes.byref(a), ctypes.byref(q)))
+        return int(a.value), int(q.value)
+
+    def poll(self, out=None):
+        """(tag, u, iterations, relres) of one finished request, or None."""
+        if out is None:
+            out = np.empty(self.G[::-1], dtype=np.complex128)
+        tag = ctypes.c_longlong(0)
+        it = ctypes.c_int(0)
+        rel = ctypes.c_double(0.0)
+        self.ctx._bind_stream(out)
+        st = self._lib.dds_server_poll(self._h, ctypes.byref(tag), self.ctx._ptr(out),
+                                       ctypes.byref(it), ctypes.byref(rel))
+        if st == 6:
+            return None
+        self.ctx._check(st)
+        return int(tag.value), out, int(it.value), float(rel.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.dds_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

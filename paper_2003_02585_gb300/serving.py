@@ -1,0 +1,165 @@
+"""Serving loop: Poisson request streams over several cached media, continuous batching.
+
+Each medium has one set-up Context (its cached factorisation) and one dds_server whose slot
+count is the admission limit derived from a device-memory budget.  A request carries 1..32
+point sources (right-hand sides); each right-hand side becomes one server submission, and the
+request completes when all of them have.  One worker thread per medium steps its server (the
+C calls release the GIL), so the media's batched iterations overlap on the GPU; inside a
+medium, sources that arrive while others are in flight join at the next FGMRES iteration.
+
+This module only schedules: every arithmetic step runs inside libdds.
+"""
+
+from __future__ import annotations
+
+import dataclasses
+import threading
+import time
+
+import numpy as np
+
+from . import dds, synth
+
+
+@dataclasses.dataclass
+class Medium:
+    name: str
+    n: tuple
+    parts: tuple
+    omega: float
+    c: np.ndarray
+    pml_cells: int = 12
+
+
+def serving_media(seed: int = 5):
+    """The three cached media of the serving workload: 256^2 constant (4x4 of 64, kappa = 32 pi),
+    512^2 two-layer (8x8 of 64, omega = 64 pi), 1024^2 smooth random c in [1, 2] (16x16 of 64,
+    omega = 128 pi, Gaussian covariance length 0.1); 12-cell PML."""
+    return [
+        Medium("const256", (256, 256), (4, 4), 32 * np.pi, synth.medium_constant((256, 256))),
+        Medium("layer512", (512, 512), (8, 8), 64 * np.pi,
+               synth.medium_two_layer((512, 512), 1.0 / 512)),
+        Medium("random1024", (1024, 1024), (16, 16), 128 * np.pi,
+               synth.medium_random((1024, 1024), 1.0 / 1024, seed)),
+    ]
+
+
+def slots_for_budget(ctx: dds.Context, budget_bytes: float, maxit: int, cap: int = 64) -> int:
+    """Admission limit: slots whose Krylov storage ((2 maxit + 4) fields each, plus the batch
+    buffers of the DDM) fits the device-memory budget."""
+    field = 16.0 * float(np.prod(ctx.G))
+    per_slot = field * (2 * maxit + 6)
+    return int(max(1, min(cap, budget_bytes // per_slot)))
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    medium: int
+    arrival: float
+    centres: np.ndarray
+    done_rhs: int = 0
+    completion: float = 0.0
+    iters: list = dataclasses.field(default_factory=list)
+    relres: list = dataclasses.field(default_factory=list)
+
+
+def poisson_requests(rng, count: int, rate: float, n_media: int, max_sources: int = 32):
+    """Arrival times (s), medium (uniform) and 1..max_sources seeded source centres each."""
+    t = 0.0
+    out = []
+    for rid in range(count):
+        t += rng.exponential(1.0 / rate)
+        m = int(rng.integers(0, n_media))
+        k = int(rng.integers(1, max_sources + 1))
+        out.append(Request(rid, m, t, rng.uniform(0.1, 0.9, size=(k, 2))))
+    return out
+
+
+class MediumWorker(threading.Thread):
+    def __init__(self, idx, medium: Medium, budget_bytes, tol, maxit, rounds, t0):
+        super().__init__(daemon=True)
+        self.idx = idx
+        self.medium = medium
+        self.ctx = dds.Context(medium.n, 1.0 / medium.n[0], medium.omega, medium.c, medium.parts,
+                               medium.pml_cells, 30.0, precision="mixed")
+        self.slots = slots_for_budget(self.ctx, budget_bytes, maxit)
+        self.server = dds.Server(self.ctx, self.slots, tol, maxit, rounds)
+        self.inbox = []
+        self.lock = threading.Lock()
+        self.pending = {}
+        self.t0 = t0
+        self.stop = False
+        self.steps = 0
+        self.rhs_done = 0
+        self.error = None
+
+    def put(self, req: Request):
+        with self.lock:
+            self.inbox.append(req)
+
+    def run(self):
+        h = 1.0 / self.medium.n[0]
+        out = np.empty(self.ctx.G[::-1], dtype=np.complex128)
+        try:
+            while True:
+                with self.lock:
+                    new, self.inbox = self.inbox, []
+                for req in new:
+                    f = synth.gaussian_sources(self.medium.n, h, req.centres, 2 * h)
+                    fe = self.ctx.extend(f)
+                    for k in range(fe.shape[0]):
+                        self.server.submit(fe[k], req.rid * 64 + k)
+                    self.pending[req.rid] = req
+                active, queued = self.server.step()
+                self.steps += 1
+                while True:
+                    res = self.server.poll(out)
+                    if res is None:
+                        break
+                    tag, _, it, rel = res
+                    req = self.pending[tag // 64]
+                    req.done_rhs += 1
+                    req.iters.append(it)
+                    req.relres.append(rel)
+                    self.rhs_done += 1
+                    if req.done_rhs == len(req.centres):
+                        req.completion = time.perf_counter() - self.t0
+                        del self.pending[req.rid]
+                if active == 0 and queued == 0 and not new:
+                    if self.stop and not self.pending:
+                        return
+                    time.sleep(0.0005)
+        except Exception as e:  # surfaced by the driver
+            self.error = e
+
+
+def run(requests, media=None, budget_bytes=40e9, tol=1e-6, maxit=30, rounds=2):
+    """Serve `requests` (arrival times in seconds from the start) in real time.  Returns per-
+    request latencies (s), wall time, RHS count and worker statistics."""
+    media = serving_media() if media is None else media
+    t0 = time.perf_counter()
+    workers = [MediumWorker(i, m, budget_bytes / len(media), tol, maxit, rounds, t0)
+               for i, m in enumerate(media)]
+    setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for w in workers:
+        w.t0 = t0
+        w.start()
+    for req in sorted(requests, key=lambda r: r.arrival):
+        delay = req.arrival - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        workers[req.medium].put(req)
+    for w in workers:
+        w.stop = True
+    for w in workers:
+        w.join()
+        if w.error is not None:
+            raise w.error
+    wall = time.perf_counter() - t0
+    lat = np.array([r.completion - r.arrival for r in requests])
+    return {"latency_s": lat, "wall_s": wall, "setup_s": setup,
+            "rhs": int(sum(len(r.centres) for r in requests)),
+            "slots": [w.slots for w in workers], "steps": [w.steps for w in workers],
+            "max_relres": float(max(max(r.relres) for r in requests))}

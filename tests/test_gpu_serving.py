@@ -1,0 +1,77 @@
+"""Continuous batching: a right-hand side solved alone and in the mix gives the same field.
+
+The mixed run submits other sources first, steps the server so they are in flight, then submits
+the probe source, which joins at a later FGMRES iteration; every result must match the oracle's
+global solve to 1e-6 and the probe must equal its solo result to 1e-6.
+"""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle.discretize import Problem, extend_interior, rhs_from_source
+from oracle.linsolve import global_solve
+from paper_2003_02585_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_server_result_alone_equals_result_in_the_mix():
+    from paper_2003_02585_gb300 import dds
+    n = (96, 96)
+    h = 1.0 / 96
+    c = synth.medium_two_layer(n, h)
+    kappa = 2 * np.pi * 6
+    ctx = dds.Context(n, h, kappa, c, (3, 3), 10, 30.0, precision="mixed")
+    prob = Problem(n, h, kappa, c, (3, 3), 10, 30.0)
+    centres = [(0.3, 0.7), (0.6, 0.2), (0.5, 0.5), (0.8, 0.8)]
+    f = ctx.extend(synth.gaussian_sources(n, h, centres, 2 * h))
+    ug = global_solve(prob, rhs_from_source(prob, extend_interior(
+        prob, synth.gaussian_sources(n, h, centres, 2 * h))))
+
+    solo = dds.Server(ctx, 4, 1e-9, 30, 1)
+    solo.submit(f[0], 0)
+    res = None
+    while res is None:
+        solo.step()
+        res = solo.poll()
+    u_alone = res[1].copy()
+    assert res[3] < 1e-9 and _rel(u_alone, ug[0]) < 1e-6
+
+    mix = dds.Server(ctx, 3, 1e-9, 30, 1)
+    mix.submit(f[1], 1)
+    mix.submit(f[2], 2)
+    active, _ = mix.step()
+    assert active == 2
+    mix.submit(f[0], 0)            # arrives while 1 and 2 are in flight
+    mix.submit(f[3], 3)            # waits for a free slot (3 slots)
+    got = {}
+    overlap = False
+    for _ in range(200):
+        active, queued = mix.step()
+        overlap |= active == 3
+        while True:
+            r = mix.poll()
+            if r is None:
+                break
+            got[r[0]] = (r[1].copy(), r[2], r[3])
+        if len(got) == 4:
+            break
+    assert overlap and sorted(got) == [0, 1, 2, 3]
+    for k in range(4):
+        assert got[k][2] < 1e-9
+        assert _rel(got[k][0], ug[k]) < 1e-6
+    assert _rel(got[0][0], u_alone) < 1e-6
