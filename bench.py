@@ -233,7 +233,7 @@ def run_gpu(args):
     R = wl.f.shape[0]
 
     ctx = dds.Context(wl.n, wl.h, wl.omega, wl.c, wl.parts, wl.pml_cells, wl.pml_strength,
-                      precision="mixed", plan=args.plan)
+                      precision=args.precision, plan=args.plan)
     info = ctx.info()
     f_host = ctx.extend(wl.f)
     f_dev = torch.from_numpy(f_host).to(dev)
@@ -320,8 +320,9 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "c64 sweeps + c128 FGMRES", "data": "synthetic",
+        "dtype": DTYPE[args.precision], "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC, "name": args.workload, "global_batch": R * world,
+                   "precision": args.precision,
                    "grid": list(wl.n), "parts": list(wl.parts), "pml_cells": wl.pml_cells,
                    "tol": args.tol, "rounds": wl.rounds, "plan": args.plan,
                    "parallelism": f"replicas x{world} (RHS sharding)",
@@ -348,11 +349,20 @@ def run_gpu(args):
     return 0
 
 
+DTYPE = {"mixed": "c64 sweeps (3xTF32 tensor-core substitutions) + c128 FGMRES",
+         "mixed_bf16": "c64 sweeps (3xBF16 tensor-core substitutions) + c128 FGMRES",
+         "mixed_fp32": "c64 sweeps (FP32 CUDA-core substitutions) + c128 FGMRES"}
+SPLIT_KIND = {"mixed": "tf32", "mixed_bf16": "bf16", "mixed_fp32": "fp32"}
+
+
 def roofline_entry(stats, info, wl, R, args):
     """Roofline of the substitution kernel family (algorithmic FLOPs per launch / event time).
 
     Algorithmic work of one block-tridiagonal solve: forward + back substitution touch every
     block inverse once each, 2 * Ml * Mb^2 complex multiply-adds = 16 * Ml * Mb^2 real flops.
+    Peak: for the tensor-core substitutions, the dense tensor rate of the piece type divided by
+    the three split products each useful product costs (TF32 = measured BF16 rate x 1.1/2.25,
+    the nominal TF32:BF16 ratio); for the CUDA-core kernel, the FP32 FMA rate.
     """
     peaks, src = _peaks()
     n_sub = info["n_sub"]
@@ -378,13 +388,27 @@ def roofline_entry(stats, info, wl, R, args):
         # not known here, so take the per-launch average over the whole profiled run
         solves_per_launch = args.ddm_solves_profiled / n_launch
     achieved = flops_per_solve * solves_per_launch / (ms / n_launch / 1e3) / 1e12
-    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12       # FP32 FMA lanes x 2 flop x max SM clock
-    return {"kernel": "k_subst<float> (block forward+back substitution)", "bound": "alu",
-            "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-            "frac": achieved / fp32_peak, "traffic": None,
-            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
-            "launches": n_launch, "avg_launch_ms": ms / n_launch,
-            "family_share": {k: v[1] for k, v in stats.items()}}
+    kind = SPLIT_KIND.get(args.precision, "fp32")
+    tc = kind != "fp32" and Mb <= 128
+    if tc:
+        bf16 = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+        base = bf16 * (1.1 / 2.25) if kind == "tf32" else bf16
+        peak = base / 3.0
+        entry = {"kernel": f"k_subst_tc<{kind}> (block forward+back substitution, 3x{kind.upper()} "
+                           f"split products on tcgen05)", "bound": "tensor",
+                 "peak_source": f"{src} bf16 sustained {bf16:.0f} TF/s"
+                                + (" x 1.1/2.25 (nominal TF32:BF16)" if kind == "tf32" else "")
+                                + " / 3 split products"}
+    else:
+        peak = 152 * 128 * 2 * 2.07e9 / 1e12       # FP32 FMA lanes x 2 flop x max SM clock
+        entry = {"kernel": "k_subst_stream<float> (block forward+back substitution)",
+                 "bound": "alu",
+                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
+    entry.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                  "frac": achieved / peak, "traffic": None,
+                  "launches": n_launch, "avg_launch_ms": ms / n_launch,
+                  "family_share": {k: v[1] for k, v in stats.items()}})
+    return entry
 
 
 def run_serving(args):
@@ -430,6 +454,8 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--maxit", type=int, default=40)
     ap.add_argument("--plan", default="auto", choices=["auto", "direct", "trace"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_bf16", "mixed_fp32"],
+                    help="single-precision sweep variant of the timed solver")
     ap.add_argument("--rounds", type=int, default=None,
                     help="DDM rounds per preconditioner application (default: the workload's)")
     ap.add_argument("--fp64-steps", type=int, default=1)

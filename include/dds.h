@@ -48,9 +48,15 @@ typedef enum {
 } dds_status;
 
 typedef enum {
-  DDS_FP64 = 0,      /* every step in complex double                                          */
-  DDS_MIXED = 1      /* factors in FP64; sweeps (substitutions, trace transfer) in complex    */
-                     /* single; FGMRES residual / orthogonalisation in FP64                   */
+  DDS_FP64 = 0,       /* every step in complex double                                         */
+  DDS_MIXED = 1,      /* factors in FP64; sweeps (substitutions, trace transfer) in complex   */
+                      /* single; FGMRES residual / orthogonalisation in FP64.  Substitutions  */
+                      /* on the tensor cores as 3xTF32 split products (a b ~ a0 b0 + a0 b1 +  */
+                      /* a1 b0, TF32 pieces, FP32 accumulation) where a line/plane block has  */
+                      /* at most 128 nodes, FP32 CUDA cores otherwise                        */
+  DDS_MIXED_BF16 = 2, /* as DDS_MIXED with BF16 pieces (16 K columns per MMA instead of 8;    */
+                      /* about 4e-6 relative error per block product instead of 1e-6)         */
+  DDS_MIXED_FP32 = 3  /* as DDS_MIXED with every substitution on the FP32 CUDA cores          */
 } dds_precision;
 
 typedef enum {

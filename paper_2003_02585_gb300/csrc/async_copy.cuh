@@ -32,6 +32,15 @@ __device__ inline void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
   (void)state;
 }
 
+__device__ inline void mbar_arrive(uint64_t *bar) {
+  uint64_t state;
+  asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];"
+               : "=l"(state)
+               : "r"(smem_addr(bar))
+               : "memory");
+  (void)state;
+}
+
 // bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned) into shared memory,
 // completing `bytes` transactions on `bar`
 __device__ inline void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {

@@ -69,6 +69,8 @@ struct dds_ctx {
   std::string err;
   Geom g{};
   int precision = 0, plan = 0;
+  bool single = false;   // sweeps in complex single precision (every precision but DDS_FP64)
+  int split = -1;        // tensor-core substitution pieces: 0 = TF32, 1 = BF16, -1 = none
   double h = 0, omega = 0, S = 0;
   int P = 0, power = 2, H = 0;
   cudaStream_t stream = nullptr;
@@ -80,6 +82,7 @@ struct dds_ctx {
   int nsteps = 0, ndirs = 0;
   // device tables
   DBuf sinv64, sinv32, cpl64, cpl32, coef64, coef32, k2glob, gmap64, gmap32, status;
+  DBuf tctiles;  // block inverses split into tensor-core pieces (layout of k_subst_tc.cu)
   DBuf errflag;  // set by kernels whose bounded waits gave up
   DBuf an_glob[3], iah_glob[3];
   DBuf stc0, stcp[3];  // global stencil (centre, coupling to +e_a)
@@ -274,6 +277,16 @@ int pick_pc(int ncols, int max_pc) {
   return pc;
 }
 
+int pick_pc_stream(const Geom &g, int ncols);
+
+int pick_pc_tc(const Geom &g, int split, int ncols) {
+  // the tensor-core kernel holds one CTA per SM and its MMA time does not depend on the panel
+  // width: the narrowest panel (8, 16 or 32 columns) that fits the columns into one wave
+  int pc = 8;
+  while (pc < 32 && (ncols + pc - 1) / pc > 152 && subst_tc_ok(g, split, pc * 2)) pc *= 2;
+  return subst_tc_ok(g, split, pc) ? pc : 0;
+}
+
 int pick_pc_stream(const Geom &g, int ncols) {
   // the streamed kernel holds one CTA per SM: the narrowest panel that fits the columns into
   // one wave of 152 CTAs, widened further only while the shared memory allows
@@ -307,7 +320,7 @@ CallPlan *get_plan(dds_ctx *ctx, int nrhs) {
   auto cp = std::make_unique<CallPlan>();
   cp->nrhs = nrhs;
   const Geom &g = ctx->g;
-  const size_t elem = ctx->precision == DDS_MIXED ? sizeof(float2) : sizeof(double2);
+  const size_t elem = ctx->single ? sizeof(float2) : sizeof(double2);
   const int maxpc = max_pc_for(ctx, elem);
   std::vector<Col> cols;
   std::vector<Panel> panels;
@@ -326,7 +339,9 @@ CallPlan *get_plan(dds_ctx *ctx, int nrhs) {
     if (trace) {  // trace-step panels of 8 columns (4 or 2 where the inputs would not fit)
       sp.pc = pc_cap;
     } else {
-      const int spc = ctx->precision == DDS_MIXED ? pick_pc_stream(ctx->g, sp.ncols) : 0;
+      int spc = 0;
+      if (ctx->single && ctx->split >= 0) spc = pick_pc_tc(ctx->g, ctx->split, sp.ncols);
+      if (ctx->single && spc == 0) spc = pick_pc_stream(ctx->g, sp.ncols);
       sp.pc = spc > 0 ? spc : pick_pc(sp.ncols, pc_cap);
     }
     sp.pan_off = (int)panels.size();
@@ -372,6 +387,10 @@ cudaError_t subst_any(dds_ctx *ctx, int npan, const Panel *pans, const Col *cols
                       const typename Cx<R>::T *sinv, const typename Cx<R>::T *cpl,
                       typename Cx<R>::T *work, int pc) {
   if constexpr (sizeof(R) == 4) {
+    if (ctx->split >= 0 && subst_tc_ok(ctx->g, ctx->split, pc))
+      return launch_subst_tc(ctx->stream, ctx->g, ctx->split, npan, pans, cols,
+                             ctx->tctiles.as<unsigned char>(), cpl, work, pc,
+                             ctx->errflag.as<int>());
     if (subst_stream_ok(ctx->g, pc))
       return launch_subst_stream(ctx->stream, ctx->g, npan, pans, cols, sinv, cpl, work, pc,
                                  ctx->errflag.as<int>());
@@ -426,9 +445,9 @@ dds_status run_ddm(dds_ctx *ctx, const double2 *b, int nrhs, double2 *u, int rou
   cudaStream_t st = ctx->stream;
   CallPlan *cp = get_plan(ctx, nrhs);
   if (!cp) { ctx->err = "failed to upload launch lists"; return DDS_ENOMEM; }
-  const C *sinv = ctx->precision == DDS_MIXED ? (const C *)ctx->sinv32.p : (const C *)ctx->sinv64.p;
-  const C *cpl = ctx->precision == DDS_MIXED ? (const C *)ctx->cpl32.p : (const C *)ctx->cpl64.p;
-  const C *gmap = ctx->precision == DDS_MIXED ? (const C *)ctx->gmap32.p : (const C *)ctx->gmap64.p;
+  const C *sinv = ctx->single ? (const C *)ctx->sinv32.p : (const C *)ctx->sinv64.p;
+  const C *cpl = ctx->single ? (const C *)ctx->cpl32.p : (const C *)ctx->cpl64.p;
+  const C *gmap = ctx->single ? (const C *)ctx->gmap32.p : (const C *)ctx->gmap64.p;
   const int L = ctx->ndirs * rounds;
   const long long slot = (long long)nrhs * g.nsub * g.T;
   const bool trace_plan = ctx->plan == DDS_PLAN_TRACE;
@@ -483,7 +502,7 @@ dds_status run_ddm(dds_ctx *ctx, const double2 *b, int nrhs, double2 *u, int rou
 }
 
 dds_status enqueue_ddm(dds_ctx *ctx, const double2 *b, int nrhs, double2 *u, int rounds) {
-  return ctx->precision == DDS_MIXED ? run_ddm<float>(ctx, b, nrhs, u, rounds)
+  return ctx->single ? run_ddm<float>(ctx, b, nrhs, u, rounds)
                                      : run_ddm<double>(ctx, b, nrhs, u, rounds);
 }
 
@@ -492,7 +511,7 @@ dds_status enqueue_ddm(dds_ctx *ctx, const double2 *b, int nrhs, double2 *u, int
 // ordered after and before the caller's stream by events.
 dds_status ddm(dds_ctx *ctx, const double2 *b, int nrhs, double2 *u, int rounds) {
   bool grown = false;
-  dds_status r = ctx->precision == DDS_MIXED ? prepare_ddm<float>(ctx, nrhs, rounds, &grown)
+  dds_status r = ctx->single ? prepare_ddm<float>(ctx, nrhs, rounds, &grown)
                                              : prepare_ddm<double>(ctx, nrhs, rounds, &grown);
   if (r != DDS_OK) return r;
   if (grown) ctx->clear_graphs();
@@ -560,7 +579,7 @@ dds_status validate(const dds_problem *p, std::string &err) {
     err = "invalid PML / grid parameters";
     return DDS_EINVAL;
   }
-  if (p->precision != DDS_FP64 && p->precision != DDS_MIXED) { err = "bad precision"; return DDS_EINVAL; }
+  if (p->precision < DDS_FP64 || p->precision > DDS_MIXED_FP32) { err = "bad precision"; return DDS_EINVAL; }
   if (p->plan < 0 || p->plan > 2) { err = "bad plan"; return DDS_EINVAL; }
   return DDS_OK;
 }
@@ -598,7 +617,7 @@ dds_status build_trace_map(dds_ctx *ctx) {
     }
     LAUNCH(launch_gmap_backtrace(st, g, ctx->gmap64.as<double2>(), f));
   }
-  if (ctx->precision == DDS_MIXED) {
+  if (ctx->single) {
     CK(ctx->gmap32.ensure(TT * sizeof(float2)));
     LAUNCH(launch_convert_c64_c32(st, ctx->gmap64.as<double2>(), ctx->gmap32.as<float2>(), TT));
   }
@@ -611,6 +630,8 @@ dds_status setup_impl(dds_ctx *ctx, const dds_problem *p) {
   Geom &g = ctx->g;
   g.dim = p->dim;
   ctx->precision = p->precision;
+  ctx->single = p->precision != DDS_FP64;
+  ctx->split = p->precision == DDS_MIXED ? 0 : (p->precision == DDS_MIXED_BF16 ? 1 : -1);
   ctx->plan = p->plan == DDS_PLAN_AUTO ? (p->dim == 2 ? DDS_PLAN_TRACE : DDS_PLAN_DIRECT) : p->plan;
   ctx->h = p->h;
   ctx->omega = p->omega;
@@ -870,7 +891,16 @@ dds_status setup_impl(dds_ctx *ctx, const dds_problem *p) {
     dds_status r = build_trace_map<double>(ctx);
     if (r != DDS_OK) return r;
   }
-  if (ctx->precision == DDS_MIXED) ctx->sinv64.release(), ctx->gmap64.release();
+  if (ctx->split >= 0 && subst_tc_ok(g, ctx->split, 8)) {
+    // block inverses split into tensor-core pieces, from the FP64 inverses
+    CK(ctx->tctiles.ensure((size_t)tc_tiles_bytes(g, ctx->split, ctx->nfac)));
+    LAUNCH(launch_split_tc(st, g, ctx->split, ctx->nfac, ctx->sinv64.as<double2>(),
+                           ctx->tctiles.as<unsigned char>()));
+    CK(cudaStreamSynchronize(st));
+  } else {
+    ctx->split = -1;   // blocks wider than 128 nodes: FP32 CUDA-core substitutions
+  }
+  if (ctx->single) ctx->sinv64.release(), ctx->gmap64.release();
   ctx->setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   return DDS_OK;
 }
@@ -1188,8 +1218,9 @@ dds_status dds_local_solve(dds_ctx *ctx, int sub, const void *b, int nrhs, void 
   cudaStream_t st = ctx->stream;
   std::vector<Col> cols(nrhs);
   for (int q = 0; q < nrhs; ++q) cols[q] = Col{sub, q, q, 0};
-  const bool mixed = ctx->precision == DDS_MIXED;
-  const int pc = std::min(4, max_pc_for(ctx, mixed ? sizeof(float2) : sizeof(double2)));
+  const bool mixed = ctx->single;
+  const bool tc = mixed && ctx->split >= 0 && subst_tc_ok(g, ctx->split, 8);
+  const int pc = tc ? 8 : std::min(4, max_pc_for(ctx, mixed ? sizeof(float2) : sizeof(double2)));
   std::vector<Panel> pans;
   for (int i = 0; i < nrhs; i += pc) pans.push_back(Panel{i, std::min(pc, nrhs - i), ctx->fac_of_sub[sub], 0});
   DBuf dcols, dpans;
@@ -1199,7 +1230,12 @@ dds_status dds_local_solve(dds_ctx *ctx, int sub, const void *b, int nrhs, void 
   if (mixed) {
     CK(ctx->work.ensure(n * sizeof(float2)));
     LAUNCH(launch_copy_local<float>(st, n, bd, ctx->work.as<float2>(), 1));
-    LAUNCHK(DDS_K_SUBST, launch_subst<float>(st, g, (int)pans.size(), dpans.as<Panel>(), dcols.as<Col>(),
+    if (tc)
+      LAUNCHK(DDS_K_SUBST, subst_any<float>(ctx, (int)pans.size(), dpans.as<Panel>(), dcols.as<Col>(),
+                                            ctx->sinv32.as<float2>(), ctx->cpl32.as<float2>(),
+                                            ctx->work.as<float2>(), pc));
+    else
+      LAUNCHK(DDS_K_SUBST, launch_subst<float>(st, g, (int)pans.size(), dpans.as<Panel>(), dcols.as<Col>(),
                                ctx->sinv32.as<float2>(), ctx->cpl32.as<float2>(), ctx->work.as<float2>(), pc));
     LAUNCH(launch_copy_local_back<float>(st, n, ctx->work.as<float2>(), xd));
   } else {
@@ -1230,7 +1266,8 @@ dds_status dds_get_info(const dds_ctx *ctx, dds_info_t *info) {
   info->n_factors = ctx->nfac;
   info->trace_len = ctx->g.T;
   info->plan = ctx->plan;
-  info->factor_bytes = (long long)(ctx->sinv64.n + ctx->sinv32.n + ctx->gmap64.n + ctx->gmap32.n);
+  info->factor_bytes = (long long)(ctx->sinv64.n + ctx->sinv32.n + ctx->gmap64.n + ctx->gmap32.n +
+                                   ctx->tctiles.n);
   info->setup_seconds = ctx->setup_seconds;
   return DDS_OK;
 }
@@ -1616,7 +1653,7 @@ extern "C" dds_status dds_local_solve_noalloc(dds_ctx *ctx, int sub, const void 
     ctx->err = "dds_local_solve_noalloc needs device pointers for b and x";
     return DDS_EINVAL;
   }
-  const bool mixed = ctx->precision == DDS_MIXED;
+  const bool mixed = ctx->single;
   const size_t elem = mixed ? sizeof(float2) : sizeof(double2);
   const long long n = (long long)nrhs * g.Nloc;
   if (nrhs > kStaticMaxRhs || (size_t)n * elem > kStaticScratchBytes - kStaticDescBytes) {
@@ -1636,7 +1673,8 @@ extern "C" dds_status dds_local_solve_noalloc(dds_ctx *ctx, int sub, const void 
   // launch descriptors, built on the stack and copied into the static scratch
   Col cols[kStaticMaxRhs];
   Panel pans[kStaticMaxRhs];
-  const int pc = std::min(4, max_pc_for(ctx, elem));
+  const bool tc = mixed && ctx->split >= 0 && subst_tc_ok(g, ctx->split, 8);
+  const int pc = tc ? 8 : std::min(4, max_pc_for(ctx, elem));
   int npan = 0;
   for (int q = 0; q < nrhs; ++q) cols[q] = Col{sub, q, q, 0};
   for (int i = 0; i < nrhs; i += pc) pans[npan++] = Panel{i, std::min(pc, nrhs - i), ctx->fac_of_sub[sub], 0};
@@ -1648,8 +1686,12 @@ extern "C" dds_status dds_local_solve_noalloc(dds_ctx *ctx, int sub, const void 
   if (mixed) {
     float2 *w = static_cast<float2 *>(work);
     LAUNCH(launch_copy_local<float>(st, n, bd, w, 1));
-    LAUNCHK(DDS_K_SUBST, launch_subst<float>(st, g, npan, dpans, dcols, ctx->sinv32.as<float2>(),
-                                             ctx->cpl32.as<float2>(), w, pc));
+    if (tc)
+      LAUNCHK(DDS_K_SUBST, subst_any<float>(ctx, npan, dpans, dcols, ctx->sinv32.as<float2>(),
+                                            ctx->cpl32.as<float2>(), w, pc));
+    else
+      LAUNCHK(DDS_K_SUBST, launch_subst<float>(st, g, npan, dpans, dcols, ctx->sinv32.as<float2>(),
+                                               ctx->cpl32.as<float2>(), w, pc));
     LAUNCH(launch_copy_local_back<float>(st, n, w, xd));
   } else {
     double2 *w = static_cast<double2 *>(work);

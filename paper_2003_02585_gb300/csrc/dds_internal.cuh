@@ -182,6 +182,15 @@ cudaError_t launch_subst_stream(cudaStream_t st, const Geom &g, int npanels, con
                                 float2 *work, int pc, int *err);
 bool subst_stream_ok(const Geom &g, int pc);
 
+// tensor-core substitutions (k_subst_tc.cu); kind 0 = TF32 pieces, 1 = BF16 pieces
+cudaError_t launch_subst_tc(cudaStream_t st, const Geom &g, int kind, int npanels,
+                            const Panel *panels, const Col *cols, const unsigned char *tiles,
+                            const float2 *cpl, float2 *work, int pc, int *err);
+bool subst_tc_ok(const Geom &g, int kind, int pc);
+long long tc_tiles_bytes(const Geom &g, int kind, int nfac);
+cudaError_t launch_split_tc(cudaStream_t st, const Geom &g, int kind, int nfac,
+                            const double2 *sinv64, unsigned char *tiles);
+
 template <typename R>
 cudaError_t launch_extract(cudaStream_t st, const Geom &g, int ncols, const Col *cols,
                            const typename Cx<R>::T *work, double2 *u, int own_mode,

@@ -1,0 +1,432 @@
+// Block-tridiagonal substitutions on the 5th-generation tensor cores (tcgen05), complex single
+// precision through split products with FP32 accumulation in tensor memory.
+//
+// Same recurrences as k_subst / k_subst_stream:
+//   forward  y_0 = S_0^{-1} b_0,  y_j = S_j^{-1} (b_j - C_{j-1} y_{j-1})
+//   backward x_{Ml-1} = y_{Ml-1}, x_j = y_j - S_j^{-1} (C_j x_{j+1})
+// Stage q of the 2 Ml - 1 stage chain is one complex product S_j^{-1} V (Mb x Mb times Mb x PC).
+//
+// Split products.  Every real operand is a sum of two pieces, x = x0 + x1 with x0 = rn(x) and
+// x1 = rn(x - x0) in TF32 (10 explicit mantissa bits, 8 K columns per instruction) or BF16
+// (7 bits, 16 K columns per instruction), and a b ~ a0 b0 + a0 b1 + a1 b0.  The complex product
+// is real-ified with the right-hand sides' real and imaginary parts side by side in N:
+//   B = [V0_re V0_im | V1_re V1_im]   (4 PC rows of the K-major B operand; pieces 0 then 1)
+//   D1 = A0_re B + A1_re B[:2PC]      = Re(S^{-1}) V   (pieces summed in the epilogue)
+//   D2 = A0_im B + A1_im B[:2PC]      = Im(S^{-1}) V
+//   S^{-1} V = (D1_re - D2_im) + i (D1_im + D2_re)
+// so one K-step is four MMAs (M = 128, N = 4 PC or 2 PC) into two TMEM accumulators of 4 PC
+// FP32 columns each.
+//
+// Pipeline per CTA (one panel of PC right-hand sides sharing one factor):
+//   producer warp   streams the pre-split S_j^{-1} tiles in stage order through a two-slot
+//                   shared-memory ring with bulk copies completed on mbarriers;
+//   MMA warp        one elected thread issues the stage's MMAs once the ring slot is full and
+//                   the epilogue has written the stage's B operand, and commits to mbarriers
+//                   that free the slot and signal the accumulator;
+//   epilogue warps  4 NG warps (TMEM lane quarter = warp % 4 = row block, warp / 4 = column
+//                   group) read the accumulator, form x_j, store it, and write the next
+//                   stage's B operand (split into pieces) into shared memory.
+// Every wait is bounded; on a timeout the CTA records an error code, lets its copies and MMAs
+// drain, frees its tensor memory and exits.
+#include "async_copy.cuh"
+#include "dds_internal.cuh"
+#include "umma.cuh"
+
+namespace dds {
+
+// ---------------------------------------------------------------------------------------------
+// Layout of the split block inverses.  Tile (f, j) = S_j^{-1} of factor f, ks K-steps of
+// 128 * Mp bytes each: [K-step t][comp][g][row m < Mp][16 bytes], comp 0/1 = pieces 0/1 of the
+// real part, 2/3 = pieces 0/1 of the imaginary part, g = which 16-byte core-matrix column of
+// the K-step.  Element (m, k) sits at t = k / (2 EK), g = (k / EK) % 2, byte (k % EK) * es
+// (EK elements of es bytes per 16 bytes).  Zero outside m < Mb, k < Mb.
+
+struct TcShape {
+  int kind;      // 0 = TF32 pieces, 1 = BF16 pieces
+  int EK;        // elements per 16 bytes
+  int Mp, Kp;    // rows (Mb rounded up to 8) and K columns (rounded up to one K-step)
+  int ks;        // K-steps per tile
+  int KS;        // K-steps per ring chunk
+  int nch;       // chunks per stage
+  int LB;        // bytes per 16-byte K group of the B operand (4 PC rows + 16 bytes of pad)
+  long long tile_bytes;
+  size_t smem;
+};
+
+static size_t tc_static_smem() { return 1024; }
+
+bool tc_shape(const Geom &g, int kind, int pc, TcShape *s) {
+  TcShape t;
+  t.kind = kind;
+  t.EK = kind == 0 ? 4 : 8;
+  t.Mp = (g.Mb + 7) / 8 * 8;
+  t.Kp = (g.Mb + 2 * t.EK - 1) / (2 * t.EK) * (2 * t.EK);
+  if (t.Mp > 128 || t.Kp > 128) return false;
+  if (pc != 8 && pc != 16 && pc != 32) return false;
+  t.ks = t.Kp / (2 * t.EK);
+  t.LB = 4 * pc * 16 + 16;
+  t.tile_bytes = (long long)t.ks * 128 * t.Mp;
+  const size_t bbytes = (size_t)(t.Kp / t.EK) * t.LB;
+  const size_t budget = 227 * 1024 - tc_static_smem();
+  for (int nch = 1; nch <= t.ks; ++nch) {
+    const int KS = (t.ks + nch - 1) / nch;
+    const size_t smem = 2 * (size_t)KS * 128 * t.Mp + bbytes + 2048;
+    if (smem <= budget) {
+      t.KS = KS;
+      t.nch = (t.ks + KS - 1) / KS;
+      t.smem = smem;
+      if (s) *s = t;
+      return true;
+    }
+  }
+  return false;
+}
+
+long long tc_tiles_bytes(const Geom &g, int kind, int nfac) {
+  TcShape t;
+  if (!tc_shape(g, kind, 8, &t)) return 0;
+  return (long long)nfac * g.Ml * t.tile_bytes;
+}
+
+template <int KIND>
+__global__ void k_split_tc(const double2 *__restrict__ sinv, unsigned char *__restrict__ out,
+                           int nfac, int Mb, int Ml, long long St, int Mp, int Kp) {
+  constexpr int EK = KIND == 0 ? 4 : 8, ES = 16 / EK;
+  const long long total = (long long)nfac * Ml * Kp * Mp;
+  const long long tile = (long long)(Kp / (2 * EK)) * 128 * Mp;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int m = (int)(i % Mp);
+    const int k = (int)((i / Mp) % Kp);
+    const long long fj = i / ((long long)Mp * Kp);
+    double2 a = make_double2(0.0, 0.0);
+    if (m < Mb && k < Mb) a = sinv[fj * St + (long long)k * Mb + m];
+    const int t = k / (2 * EK), gg = (k / EK) & 1;
+    unsigned char *base = out + fj * tile + (long long)t * 128 * Mp + (long long)m * 16 + (k % EK) * ES;
+    const double parts[2] = {a.x, a.y};
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const double x = parts[e];
+      unsigned char *p0 = base + (long long)((2 * e + 0) * 2 + gg) * Mp * 16;
+      unsigned char *p1 = base + (long long)((2 * e + 1) * 2 + gg) * Mp * 16;
+      if (KIND == 0) {
+        const float x0 = umma::tf32_rna((float)x);
+        const float x1 = umma::tf32_rna((float)(x - (double)x0));
+        *reinterpret_cast<float *>(p0) = x0;
+        *reinterpret_cast<float *>(p1) = x1;
+      } else {
+        const unsigned short b0 = umma::bf16_rn_bits((float)x);
+        const unsigned short b1 = umma::bf16_rn_bits((float)(x - (double)umma::bf16_to_float(b0)));
+        *reinterpret_cast<unsigned short *>(p0) = b0;
+        *reinterpret_cast<unsigned short *>(p1) = b1;
+      }
+    }
+  }
+}
+
+cudaError_t launch_split_tc(cudaStream_t st, const Geom &g, int kind, int nfac,
+                            const double2 *sinv64, unsigned char *tiles) {
+  TcShape t;
+  if (!tc_shape(g, kind, 8, &t)) return cudaErrorInvalidValue;
+  const long long total = (long long)nfac * g.Ml * t.Kp * t.Mp;
+  const int threads = 256;
+  const int blocks = (int)std::min<long long>((total + threads - 1) / threads, 152LL * 16);
+  if (kind == 0)
+    k_split_tc<0><<<blocks, threads, 0, st>>>(sinv64, tiles, nfac, g.Mb, g.Ml, g.St, t.Mp, t.Kp);
+  else
+    k_split_tc<1><<<blocks, threads, 0, st>>>(sinv64, tiles, nfac, g.Mb, g.Ml, g.St, t.Mp, t.Kp);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+
+struct TcArgs {
+  int Mp, Kp, ks, KS, nch, LB;
+  long long tile_bytes;
+};
+
+// write the two pieces of v (row k of the B operand) for rows n0 (real part) and n0 + H
+// (imaginary part) of piece 0, and the same rows + 2 PC of piece 1
+template <int KIND, int PC>
+__device__ __forceinline__ void put_b(unsigned char *sB, int LB, int k, int n_re, int n_im,
+                                      float2 v) {
+  constexpr int EK = KIND == 0 ? 4 : 8, ES = 16 / EK;
+  const int off = (k / EK) * LB + (k % EK) * ES;
+  const int n[4] = {n_re, n_im, n_re + 2 * PC, n_im + 2 * PC};
+  float w[4];
+  if (KIND == 0) {
+    w[0] = umma::tf32_rna(v.x);
+    w[1] = umma::tf32_rna(v.y);
+    w[2] = umma::tf32_rna(v.x - w[0]);
+    w[3] = umma::tf32_rna(v.y - w[1]);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      *reinterpret_cast<float *>(sB + off + (n[i] >> 3) * 128 + (n[i] & 7) * 16) = w[i];
+  } else {
+    unsigned short b[4];
+    b[0] = umma::bf16_rn_bits(v.x);
+    b[1] = umma::bf16_rn_bits(v.y);
+    b[2] = umma::bf16_rn_bits(v.x - umma::bf16_to_float(b[0]));
+    b[3] = umma::bf16_rn_bits(v.y - umma::bf16_to_float(b[1]));
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      *reinterpret_cast<unsigned short *>(sB + off + (n[i] >> 3) * 128 + (n[i] & 7) * 16) = b[i];
+  }
+}
+
+template <int PC, int KIND, int NG>
+__global__ void __launch_bounds__(32 * (4 * NG + 2), 1)
+    k_subst_tc(Geom g, TcArgs a, const Panel *__restrict__ panels, const Col *__restrict__ cols,
+               const unsigned char *__restrict__ tiles, const float2 *__restrict__ cpl,
+               float2 *__restrict__ work, int *__restrict__ err) {
+  constexpr int H = PC / NG;            // columns per epilogue thread
+  constexpr int NEPI = 128 * NG;        // epilogue threads
+  constexpr int NCOL = 8 * PC;          // TMEM columns: D1 [0, 4PC), D2 [4PC, 8PC)
+  constexpr int NALLOC = NCOL <= 32 ? 32 : (NCOL <= 64 ? 64 : (NCOL <= 128 ? 128 : 256));
+  constexpr uint32_t kIdN4 = KIND == 0 ? umma::idesc_tf32(128, 4 * PC) : umma::idesc_bf16(128, 4 * PC);
+  constexpr uint32_t kIdN2 = KIND == 0 ? umma::idesc_tf32(128, 2 * PC) : umma::idesc_bf16(128, 2 * PC);
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ uint64_t bars[7];   // full[2], empty[2], dready, bready, drain
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+  uint64_t *full = bars, *empty = bars + 2, *dready = bars + 4, *bready = bars + 5,
+           *drain = bars + 6;
+
+  const int Mb = g.Mb, Ml = g.Ml;
+  const int nst = 2 * Ml - 1;
+  const long long chunk_bytes = (long long)a.KS * 128 * a.Mp;
+  unsigned char *ring = smem_raw;
+  unsigned char *sB = smem_raw + 2 * chunk_bytes;
+  const Panel p = panels[blockIdx.x];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  auto block_of = [&](int q) { return q < Ml ? q : 2 * Ml - 2 - q; };
+  auto aborted = [&]() { return *reinterpret_cast<volatile int *>(&abort_flag) != 0; };
+  auto fail = [&](int code) {
+    atomicExch(err, code);
+    *reinterpret_cast<volatile int *>(&abort_flag) = 1;
+  };
+
+  if (tid == 0) {
+    mbar_init(&full[0], 1);
+    mbar_init(&full[1], 1);
+    mbar_init(&empty[0], 1);
+    mbar_init(&empty[1], 1);
+    mbar_init(dready, 1);
+    mbar_init(bready, NEPI / 32);   // one arrival per epilogue warp
+    mbar_init(drain, 1);
+    abort_flag = 0;
+    mbar_init_fence();
+  }
+  if (warp == 4 * NG + 1) {
+    umma::tmem_alloc(&tmem_base, NALLOC);
+    umma::tmem_relinquish();
+  }
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  const uint32_t tmem = tmem_base;
+
+  if (warp == 4 * NG) {
+    // ---------------- producer: S_j^{-1} tiles in stage order through the two-slot ring
+    if (lane == 0) {
+      int last[2] = {-1, -1};
+      const int nchunks = nst * a.nch;
+      for (int i = 0; i < nchunks; ++i) {
+        const int s = i & 1;
+        if (i >= 2 && !mbar_wait(&empty[s], ((i >> 1) - 1) & 1)) { fail(11); break; }
+        if (aborted()) break;
+        const int q = i / a.nch, c = i % a.nch;
+        const int nks = min(a.KS, a.ks - c * a.KS);
+        const uint32_t bytes = (uint32_t)nks * 128u * (uint32_t)a.Mp;
+        const unsigned char *src = tiles + ((long long)p.factor * Ml + block_of(q)) * a.tile_bytes +
+                                   (long long)c * a.KS * 128 * a.Mp;
+        mbar_arrive_expect_tx(&full[s], bytes);
+        bulk_g2s(ring + s * chunk_bytes, src, bytes, &full[s]);
+        last[s] = i;
+      }
+      // no copy may still be landing when the CTA leaves
+      for (int s = 0; s < 2; ++s)
+        if (last[s] >= 0 && !mbar_wait(&full[s], (last[s] >> 1) & 1)) atomicExch(err, 12);
+    }
+  } else if (warp == 4 * NG + 1) {
+    // ---------------- MMA issuer
+    if (lane == 0) {
+      const uint32_t lbo_a = (uint32_t)a.Mp * 16u;
+      const uint64_t dA = (uint64_t)8 * a.Mp;              // one K-step of A, in 16-byte units
+      const uint64_t dC = (uint64_t)2 * a.Mp;              // one component of A
+      const uint64_t dB = (uint64_t)(2 * a.LB) >> 4;       // one K-step of B
+      const uint64_t b0 = umma::smem_desc(umma::saddr(sB), (uint32_t)a.LB, 128);
+      const uint32_t d1 = tmem, d2 = tmem + 4 * PC;
+      for (int q = 0; q < nst; ++q) {
+        if (!mbar_wait(bready, q & 1)) { fail(13); break; }
+        if (aborted()) break;
+        umma::fence_after_sync();
+        bool ok = true;
+        for (int c = 0; c < a.nch; ++c) {
+          const int i = q * a.nch + c, s = i & 1;
+          if (!mbar_wait(&full[s], (i >> 1) & 1)) { fail(14); ok = false; break; }
+          umma::fence_after_sync();
+          const int nks = min(a.KS, a.ks - c * a.KS);
+          uint64_t ad = umma::smem_desc(umma::saddr(ring + s * chunk_bytes), lbo_a, 128);
+          uint64_t bd = b0 + (uint64_t)(c * a.KS) * dB;
+          for (int t = 0; t < nks; ++t) {
+            const uint32_t acc = (c > 0 || t > 0) ? 1u : 0u;
+            if (KIND == 0) {
+              umma::mma_tf32(d1, ad, bd, kIdN4, acc);
+              umma::mma_tf32(d1, ad + dC, bd, kIdN2, 1);
+              umma::mma_tf32(d2, ad + 2 * dC, bd, kIdN4, acc);
+              umma::mma_tf32(d2, ad + 3 * dC, bd, kIdN2, 1);
+            } else {
+              umma::mma_bf16(d1, ad, bd, kIdN4, acc);
+              umma::mma_bf16(d1, ad + dC, bd, kIdN2, 1);
+              umma::mma_bf16(d2, ad + 2 * dC, bd, kIdN4, acc);
+              umma::mma_bf16(d2, ad + 3 * dC, bd, kIdN2, 1);
+            }
+            ad += dA;
+            bd += dB;
+          }
+          umma::mma_commit(&empty[s]);   // the slot is free once these MMAs have read it
+        }
+        if (!ok) break;
+        umma::mma_commit(dready);
+      }
+      umma::mma_commit(drain);
+      if (!mbar_wait(drain, 0)) atomicExch(err, 15);
+    }
+  } else {
+    // ---------------- epilogue: row r of the block, columns grp*H .. grp*H + H - 1
+    const int r = tid & 127, grp = tid >> 7;
+    const bool row = r < Mb, krow = r < a.Kp;
+    const float2 *cf = cpl + (long long)p.factor * Ml * (long long)Mb;
+    float2 *xs[H];
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+      const int c = grp * H + h;
+      xs[h] = c < p.ncol ? work + (long long)cols[p.col0 + c].slot * g.Nloc : nullptr;
+    }
+    // B operand of stage 0: b_0
+    if (krow) {
+#pragma unroll
+      for (int h = 0; h < H; ++h) {
+        const float2 v = (row && xs[h]) ? xs[h][r] : make_float2(0.f, 0.f);
+        put_b<KIND, PC>(sB, a.LB, r, grp * 2 * H + h, grp * 2 * H + H + h, v);
+      }
+    }
+    fence_proxy_async();
+    umma::fence_before_sync();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(bready);
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+    for (int q = 0; q < nst; ++q) {
+      const int j = block_of(q);
+      const bool fwd = q < Ml;
+      float2 pre[H];
+      float2 cn = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int h = 0; h < H; ++h) pre[h] = make_float2(0.f, 0.f);
+      if (row) {
+        if (fwd) {
+          if (j + 1 < Ml) {
+#pragma unroll
+            for (int h = 0; h < H; ++h)
+              if (xs[h]) pre[h] = xs[h][(long long)(j + 1) * Mb + r];
+            cn = cf[(long long)j * Mb + r];
+          } else if (Ml >= 2) {
+            cn = cf[(long long)(Ml - 2) * Mb + r];
+          }
+        } else {
+#pragma unroll
+          for (int h = 0; h < H; ++h)
+            if (xs[h]) pre[h] = xs[h][(long long)j * Mb + r];
+          if (j > 0) cn = cf[(long long)(j - 1) * Mb + r];
+        }
+      }
+      // one lane per warp polls the accumulator barrier; the warp follows it
+      int ok = 1;
+      if (lane == 0) ok = mbar_wait(dready, q & 1) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) { if (lane == 0) fail(16); break; }
+      if (aborted()) break;
+      umma::fence_after_sync();
+      // accumulator runs of this column group: D1 piece 0, D1 piece 1, D2 piece 0, D2 piece 1
+      float d[4][2 * H];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const uint32_t col = (uint32_t)((u >> 1) * 4 * PC + (u & 1) * 2 * PC + grp * 2 * H);
+#pragma unroll
+        for (int c8 = 0; c8 < 2 * H; c8 += 8) umma::tmem_ld8(tmem + lane_base + col + c8, &d[u][c8]);
+      }
+      umma::tmem_wait_ld();
+      const bool more = q + 1 < nst;
+#pragma unroll
+      for (int h = 0; h < H; ++h) {
+        const float p_re = d[0][h] + d[1][h], p_im = d[0][H + h] + d[1][H + h];
+        const float q_re = d[2][h] + d[3][h], q_im = d[2][H + h] + d[3][H + h];
+        const float2 acc = make_float2(p_re - q_im, p_im + q_re);
+        float2 v;
+        if (fwd) {
+          if (row && xs[h]) xs[h][(long long)j * Mb + r] = acc;
+          v = (j + 1 < Ml) ? csub(pre[h], cmul(cn, acc)) : cmul(cn, acc);
+        } else {
+          const float2 xv = csub(pre[h], acc);
+          if (row && xs[h]) xs[h][(long long)j * Mb + r] = xv;
+          v = cmul(cn, xv);
+        }
+        if (!row) v = make_float2(0.f, 0.f);
+        if (more && krow) put_b<KIND, PC>(sB, a.LB, r, grp * 2 * H + h, grp * 2 * H + H + h, v);
+      }
+      if (more) {
+        fence_proxy_async();
+        umma::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bready);
+      }
+    }
+  }
+  umma::fence_before_sync();
+  __syncthreads();
+  if (warp == 4 * NG + 1) {
+    umma::fence_after_sync();
+    umma::tmem_dealloc(tmem, NALLOC);
+  }
+}
+
+template <int PC, int KIND>
+static cudaError_t tc_launch(cudaStream_t st, const Geom &g, const TcShape &t, int npanels,
+                             const Panel *panels, const Col *cols, const unsigned char *tiles,
+                             const float2 *cpl, float2 *work, int *err) {
+  constexpr int NG = 2;
+  static bool done[64] = {false};
+  cudaError_t e = smem_limit_once(k_subst_tc<PC, KIND, NG>, done);
+  if (e != cudaSuccess) return e;
+  TcArgs a{t.Mp, t.Kp, t.ks, t.KS, t.nch, t.LB, t.tile_bytes};
+  k_subst_tc<PC, KIND, NG><<<npanels, 32 * (4 * NG + 2), t.smem, st>>>(g, a, panels, cols, tiles,
+                                                                      cpl, work, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_subst_tc(cudaStream_t st, const Geom &g, int kind, int npanels,
+                            const Panel *panels, const Col *cols, const unsigned char *tiles,
+                            const float2 *cpl, float2 *work, int pc, int *err) {
+  if (npanels <= 0) return cudaSuccess;
+  TcShape t;
+  if (!tc_shape(g, kind, pc, &t)) return cudaErrorInvalidValue;
+  if (kind == 0) {
+    switch (pc) {
+      case 8: return tc_launch<8, 0>(st, g, t, npanels, panels, cols, tiles, cpl, work, err);
+      case 16: return tc_launch<16, 0>(st, g, t, npanels, panels, cols, tiles, cpl, work, err);
+      case 32: return tc_launch<32, 0>(st, g, t, npanels, panels, cols, tiles, cpl, work, err);
+    }
+  } else {
+    switch (pc) {
+      case 8: return tc_launch<8, 1>(st, g, t, npanels, panels, cols, tiles, cpl, work, err);
+      case 16: return tc_launch<16, 1>(st, g, t, npanels, panels, cols, tiles, cpl, work, err);
+      case 32: return tc_launch<32, 1>(st, g, t, npanels, panels, cols, tiles, cpl, work, err);
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+bool subst_tc_ok(const Geom &g, int kind, int pc) { return tc_shape(g, kind, pc, nullptr); }
+
+}  // namespace dds

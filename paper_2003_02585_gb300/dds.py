@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_PKG, "libdds.so")
 
 STATUS = {0: "DDS_OK", 1: "DDS_EINVAL", 2: "DDS_ENOMEM", 3: "DDS_ECUDA", 4: "DDS_ENOCONV",
           5: "DDS_ETIMEOUT", 6: "DDS_EBUSY"}
-PRECISION = {"fp64": 0, "mixed": 1}
+PRECISION = {"fp64": 0, "mixed": 1, "mixed_bf16": 2, "mixed_fp32": 3}
 PLAN = {"auto": 0, "direct": 1, "trace": 2}
 
 EXPORTS = ["dds_setup", "dds_sweep", "dds_solve", "dds_apply", "dds_local_solve",
