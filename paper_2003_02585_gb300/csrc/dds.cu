@@ -60,6 +60,8 @@ struct CallPlan {            // all launch lists for one nrhs
   std::vector<StepPlan> tsteps;  // [dir][step] for the trace plan (trace-step panels)
   StepPlan all;                  // every (sub, rhs) column (trace plan phases, local solves)
   DBuf cols, panels;
+  struct TraceTable { int n = -1; DBuf buf; };
+  std::map<int, TraceTable> trace_steps;   // rounds -> step table of the cooperative launch
 };
 
 }  // namespace
@@ -84,6 +86,7 @@ struct dds_ctx {
   DBuf sinv64, sinv32, cpl64, cpl32, coef64, coef32, k2glob, gmap64, gmap32, status;
   DBuf tctiles;  // block inverses split into tensor-core pieces (layout of k_subst_tc.cu)
   DBuf errflag;  // set by kernels whose bounded waits gave up
+  DBuf gbar;     // step counters of the cooperative trace-sweep launch
   DBuf an_glob[3], iah_glob[3];
   DBuf stc0, stcp[3];  // global stencil (centre, coupling to +e_a)
   Tables tb{};
@@ -430,11 +433,35 @@ dds_status prepare_ddm(dds_ctx *ctx, int nrhs, int rounds, bool *grown) {
     work_cols = 0;
     for (auto &sp : cp->steps) work_cols = std::max<long long>(work_cols, sp.ncols);
   }
+  if (trace_plan) {
+    // step table of the cooperative trace-sweep launch (uploaded outside any stream capture)
+    auto &tt = cp->trace_steps[rounds];
+    if (tt.n < 0) {
+      std::vector<TraceStep> ts;
+      for (int l = 0; l < L; ++l) {
+        const int dir = l % ctx->ndirs;
+        for (int s = 0; s < ctx->nsteps; ++s) {
+          const StepPlan &sp = cp->tsteps[dir * ctx->nsteps + s];
+          if (sp.ncols == 0) continue;
+          int nout = 0, nseg = 0;
+          const int ni = trace_step_items(g, sp.npanels, ctx->in_mask[l], ctx->out_mask[l], &nout, &nseg);
+          if (ni == 0) continue;   // nothing routed out or nothing can come in
+          ts.push_back(TraceStep{l, sp.pan_off, sp.npanels, ctx->in_mask[l], ctx->out_mask[l],
+                                 nout, nseg, ni});
+        }
+      }
+      CK(upload(tt.buf, ts, ctx->stream));
+      tt.n = (int)ts.size();
+      void *gb0 = ctx->gbar.p;
+      CK(ctx->gbar.ensure(trace_counter_bytes(tt.n)));
+      if (gb0 != ctx->gbar.p) *grown = true;
+    }
+  }
   void *w0 = ctx->work.p, *g0 = ctx->gtr.p, *r0 = ctx->rawf.p;
   CK(ctx->work.ensure(work_cols * g.Nloc * sizeof(C)));
   CK(ctx->gtr.ensure(L * slot * sizeof(C)));
   if (trace_plan) CK(ctx->rawf.ensure(slot * sizeof(C)));
-  *grown = w0 != ctx->work.p || g0 != ctx->gtr.p || r0 != ctx->rawf.p;
+  *grown = *grown || w0 != ctx->work.p || g0 != ctx->gtr.p || r0 != ctx->rawf.p;
   return DDS_OK;
 }
 
@@ -480,17 +507,17 @@ dds_status run_ddm(dds_ctx *ctx, const double2 *b, int nrhs, double2 *u, int rou
     LAUNCHK(DDS_K_SUBST, subst_any<R>(ctx, all.npanels, pans + all.pan_off, cols, sinv, cpl, work, all.pc));
     LAUNCHK(DDS_K_EXTRACT, launch_extract<R>(st, g, all.ncols, cols + all.col_off, work, u, 0, rawf,
                              (C *)nullptr, route, 0, nrhs));
-    // sweeps: per step, traces of the whole step set through the trace map
-    for (int l = 0; l < L; ++l) {
-      const int dir = l % ctx->ndirs;
-      for (int s = 0; s < ctx->nsteps; ++s) {
-        const StepPlan &sp = cp->tsteps[dir * ctx->nsteps + s];
-        if (sp.ncols == 0) continue;
-        LAUNCHK(DDS_K_TRACE_STEP, launch_trace_step<R>(st, g, sp.npanels, pans + sp.pan_off, cols, gmap, gtr,
-                                    l == 0 ? rawf : nullptr, route, l, nrhs, sp.pc,
-                                    ctx->in_mask[l], ctx->out_mask[l], ctx->errflag.as<int>()));
-      }
+    // sweeps: every step of every sweep, traces of the step set through the trace map, in one
+    // cooperative launch with a grid barrier between steps
+    auto tti = cp->trace_steps.find(rounds);   // built by prepare_ddm
+    if (tti == cp->trace_steps.end() || tti->second.n < 0) {
+      ctx->err = "trace-step table missing";
+      return DDS_EINVAL;
     }
+    const CallPlan::TraceTable &tt = tti->second;
+    LAUNCHK(DDS_K_TRACE_STEP, launch_trace_sweeps<R>(st, g, tt.buf.as<TraceStep>(), tt.n, pans, cols, gmap,
+                                                     gtr, rawf, route, nrhs, ctx->gbar.as<unsigned>(),
+                                                     ctx->errflag.as<int>()));
     // own nodes: u = A_R^{-1}(b_own + potentials of all traces received in every sweep)
     LAUNCHK(DDS_K_ASSEMBLE, launch_assemble<R>(st, g, ctx->tb, all.ncols, cols + all.col_off, work, b, nullptr, 1,
                               gtr, (long long)g.nsub * g.T, g.T, L, slot));
@@ -651,6 +678,10 @@ dds_status setup_impl(dds_ctx *ctx, const dds_problem *p) {
   g.nsub = g.parts[0] * g.parts[1] * g.parts[2];
   g.Nloc = (long long)g.M[0] * g.M[1] * g.M[2];
   g.Nglob = (long long)g.G[0] * g.G[1] * g.G[2];
+  if (g.Nglob >= (1LL << 31)) {   // the global-grid kernels index nodes with 32-bit integers
+    ctx->err = "global extended grid of " + std::to_string(g.Nglob) + " nodes exceeds 2^31 - 1";
+    return DDS_EINVAL;
+  }
   g.Ml = g.M[p->dim - 1];
   g.Mb = (int)(g.Nloc / g.Ml);
   g.St = ((long long)g.Mb * g.Mb + 1) / 2 * 2;
@@ -859,6 +890,7 @@ dds_status setup_impl(dds_ctx *ctx, const dds_problem *p) {
   CK(cudaMemsetAsync(ctx->status.p, 0, sizeof(int), st));
   CK(ctx->errflag.ensure(sizeof(int)));
   CK(cudaMemsetAsync(ctx->errflag.p, 0, sizeof(int), st));
+
   CK(cudaMemsetAsync(ctx->sinv64.p, 0, sinv_elems * sizeof(double2), st));
   CK(cudaMemsetAsync(ctx->sinv32.p, 0, sinv_elems * sizeof(float2), st));
   if (!big_blocks) {
@@ -1083,10 +1115,7 @@ dds_status fgmres(dds_ctx *ctx, const double2 *b, int nrhs, double2 *x, double t
   }
   // true residual: R = A x - b
   double2 *Rv = V;
-  LAUNCHK(DDS_K_KRYLOV, launch_apply_A(st, g, ctx->tb, nrhs, x, Rv, 0));
-  std::vector<double2> mone(nrhs, make_double2(1.0, 0.0));
-  CK(cudaMemcpyAsync(ctx->coefbuf.p, mone.data(), nrhs * sizeof(double2), cudaMemcpyHostToDevice, st));
-  LAUNCHK(DDS_K_KRYLOV, launch_sub_combination(st, N, nrhs, 1, b, 0, N, ctx->coefbuf.as<double2>(), Rv, N, -1.0, 1));
+  LAUNCHK(DDS_K_KRYLOV, launch_apply_A(st, g, ctx->tb, nrhs, x, Rv, 0, b));
   LAUNCHK(DDS_K_KRYLOV, launch_dots(st, N, nrhs, 1, Rv, 0, N, Rv, N, part, hdev, nblk));
   CK(cudaMemcpyAsync(hh.data(), hdev, nrhs * sizeof(double2), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));

@@ -197,12 +197,21 @@ cudaError_t launch_extract(cudaStream_t st, const Geom &g, int ncols, const Col 
                            typename Cx<R>::T *raw_out, typename Cx<R>::T *g_traces,
                            const int *route, int l, int nrhs);
 
+// one sweep step of the trace plan: sweep l, its panels, and its work items
+struct TraceStep {
+  int l, pan_off, npanels, in_mask, out_mask, nout, nseg, nitems;
+};
+int trace_step_items(const Geom &g, int npanels, int in_mask, int out_mask, int *nout, int *nseg);
+size_t trace_counter_bytes(int nsteps);   // step counters of one launch (gbar)
+
+// every trace step of one DDM application in one cooperative launch (gbar: the step counters,
+// zeroed by the launch)
 template <typename R>
-cudaError_t launch_trace_step(cudaStream_t st, const Geom &g, int npanels, const Panel *panels,
-                              const Col *cols, const typename Cx<R>::T *gmap,
-                              typename Cx<R>::T *g_traces, const typename Cx<R>::T *rawf,
-                              const int *route, int l, int nrhs, int pc, int in_mask,
-                              int out_mask, int *err);
+cudaError_t launch_trace_sweeps(cudaStream_t st, const Geom &g, const TraceStep *steps, int nsteps,
+                                const Panel *panels, const Col *cols,
+                                const typename Cx<R>::T *gmap, typename Cx<R>::T *g_traces,
+                                const typename Cx<R>::T *rawf, const int *route, int nrhs,
+                                unsigned *gbar, int *err);
 
 template <typename R>
 cudaError_t launch_unit_traces(cudaStream_t st, const Geom &g, const Tables &tb, int k0, int nk,
@@ -224,8 +233,10 @@ cudaError_t launch_copy_local_back(cudaStream_t st, long long n, const typename 
                                    double2 *out);
 
 // Krylov / operator kernels (FP64)
+// Au = A u (divided by J if divide_by_J), minus sub when sub is not null
 cudaError_t launch_apply_A(cudaStream_t st, const Geom &g, const Tables &tb, int nrhs,
-                           const double2 *u, double2 *Au, int divide_by_J);
+                           const double2 *u, double2 *Au, int divide_by_J,
+                           const double2 *sub = nullptr);
 cudaError_t launch_scale_J(cudaStream_t st, const Geom &g, const Tables &tb, int nrhs,
                            const double2 *f, double2 *b);
 cudaError_t launch_dots(cudaStream_t st, long long N, int nrhs, int nv, const double2 *V,

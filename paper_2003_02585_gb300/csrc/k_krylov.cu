@@ -16,23 +16,28 @@ __device__ inline double2 crecip64(double2 z) {
 // The stencil is precomputed per node at set-up (tb.c0: centre, tb.cp[a]: coupling to p + e_a,
 // so the coupling to p - e_a is tb.cp[a][p - e_a]); each thread applies it to every RHS.
 __global__ void k_apply_A(Geom g, Tables tb, int nrhs, const double2 *__restrict__ u,
-                          double2 *__restrict__ Au, int divide_by_J) {
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.Nglob;
-       q += (long long)gridDim.x * blockDim.x) {
+                          double2 *__restrict__ Au, int divide_by_J,
+                          const double2 *__restrict__ sub) {
+  const int N = (int)g.Nglob;
+  const int G0 = g.G[0], G1 = g.G[1];
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < N; q += gridDim.x * blockDim.x) {
     int p[3];
-    p[0] = (int)(q % g.G[0]);
-    p[1] = (int)((q / g.G[0]) % g.G[1]);
-    p[2] = g.dim == 3 ? (int)(q / ((long long)g.G[0] * g.G[1])) : 0;
+    p[0] = q % G0;
+    p[1] = (q / G0) % G1;
+    p[2] = g.dim == 3 ? q / (G0 * G1) : 0;
     const double2 c0 = tb.c0[q];
     double2 cpv[3], cmv[3];
-    long long stride[3];
-    long long st = 1;
+    int stride[3];
+    int st = 1;
+    bool real = c0.y == 0.0;
+#pragma unroll
     for (int a = 0; a < 3; ++a) {
       stride[a] = st;
       st *= g.G[a];
       const bool on = a < g.dim;
       cpv[a] = on && p[a] + 1 < g.G[a] ? tb.cp[a][q] : make_double2(0.0, 0.0);
       cmv[a] = on && p[a] > 0 ? tb.cp[a][q - stride[a]] : make_double2(0.0, 0.0);
+      real = real && cpv[a].y == 0.0 && cmv[a].y == 0.0;
     }
     double2 iJ = make_double2(1.0, 0.0);
     if (divide_by_J) {
@@ -41,30 +46,62 @@ __global__ void k_apply_A(Geom g, Tables tb, int nrhs, const double2 *__restrict
       iJ = crecip64(J);
     }
     for (int r = 0; r < nrhs; ++r) {
-      const double2 *ur = u + (long long)r * g.Nglob;
-      double2 sum = cmul(c0, ur[q]);
-      for (int a = 0; a < g.dim; ++a) {
-        if (p[a] + 1 < g.G[a]) cfma(sum, cpv[a], ur[q + stride[a]]);
-        if (p[a] > 0) cfma(sum, cmv[a], ur[q - stride[a]]);
+      const double2 *ur = u + (long long)r * N;
+      double2 sum;
+      if (real) {
+        // outside the PML every coefficient is real: two FMAs per stencil term
+        const double2 uc = ur[q];
+        sum = make_double2(c0.x * uc.x, c0.x * uc.y);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          if (a >= g.dim) break;
+          if (p[a] + 1 < g.G[a]) {
+            const double2 un = ur[q + stride[a]];
+            sum.x = fma(cpv[a].x, un.x, sum.x);
+            sum.y = fma(cpv[a].x, un.y, sum.y);
+          }
+          if (p[a] > 0) {
+            const double2 un = ur[q - stride[a]];
+            sum.x = fma(cmv[a].x, un.x, sum.x);
+            sum.y = fma(cmv[a].x, un.y, sum.y);
+          }
+        }
+      } else {
+        sum = cmul(c0, ur[q]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          if (a >= g.dim) break;
+          if (p[a] + 1 < g.G[a]) cfma(sum, cpv[a], ur[q + stride[a]]);
+          if (p[a] > 0) cfma(sum, cmv[a], ur[q - stride[a]]);
+        }
       }
       if (divide_by_J) sum = cmul(sum, iJ);
-      Au[(long long)r * g.Nglob + q] = sum;
+      if (sub) sum = csub(sum, sub[(long long)r * N + q]);
+      Au[(long long)r * N + q] = sum;
     }
   }
 }
 
-__global__ void k_scale_J(Geom g, Tables tb, const double2 *__restrict__ f,
+// b[rhs] = J f[rhs], J = prod_a alpha_a(x_a) at the node; one thread per node, all RHS
+__global__ void k_scale_J(Geom g, Tables tb, int nrhs, const double2 *__restrict__ f,
                           double2 *__restrict__ b) {
-  const long long base = (long long)blockIdx.y * g.Nglob;
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.Nglob;
-       q += (long long)gridDim.x * blockDim.x) {
+  const int N = (int)g.Nglob;
+  const int G0 = g.G[0], G1 = g.G[1];
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < N; q += gridDim.x * blockDim.x) {
     int p[3];
-    p[0] = (int)(q % g.G[0]);
-    p[1] = (int)((q / g.G[0]) % g.G[1]);
-    p[2] = g.dim == 3 ? (int)(q / ((long long)g.G[0] * g.G[1])) : 0;
+    p[0] = q % G0;
+    p[1] = (q / G0) % G1;
+    p[2] = g.dim == 3 ? q / (G0 * G1) : 0;
     double2 J = make_double2(1.0, 0.0);
     for (int a = 0; a < g.dim; ++a) J = cmul(J, tb.an_glob64[a][p[a]]);
-    b[base + q] = cmul(J, f[base + q]);
+    if (J.y == 0.0) {
+      for (int r = 0; r < nrhs; ++r) {
+        const double2 v = f[(long long)r * N + q];
+        b[(long long)r * N + q] = make_double2(J.x * v.x, J.x * v.y);
+      }
+    } else {
+      for (int r = 0; r < nrhs; ++r) b[(long long)r * N + q] = cmul(J, f[(long long)r * N + q]);
+    }
   }
 }
 
@@ -93,16 +130,26 @@ __global__ void __launch_bounds__(kDotThreads) k_dots(long long N, int nv,
   for (int i = 0; i < nv; ++i) {
     const double2 *v = V + i * vsv + rhs * vsr;
     double sr = 0.0, si = 0.0;
+    if (v == ww) {
+      // ||w||^2: two FMAs per element
 #pragma unroll
-    for (int q = 0; q < kDotPerThread; ++q) {
-      const int e = q * kDotThreads + threadIdx.x;
-      const long long n = n0 + e;
-      if (n < N) {
-        const double2 a = v[n], b = ws[e];
-        sr = fma(a.x, b.x, sr);
-        sr = fma(a.y, b.y, sr);
-        si = fma(a.x, b.y, si);
-        si = fma(-a.y, b.x, si);
+      for (int q = 0; q < kDotPerThread; ++q) {
+        const double2 b = ws[q * kDotThreads + threadIdx.x];
+        sr = fma(b.x, b.x, sr);
+        sr = fma(b.y, b.y, sr);
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < kDotPerThread; ++q) {
+        const int e = q * kDotThreads + threadIdx.x;
+        const long long n = n0 + e;
+        if (n < N) {
+          const double2 a = v[n], b = ws[e];
+          sr = fma(a.x, b.x, sr);
+          sr = fma(a.y, b.y, sr);
+          si = fma(a.x, b.y, si);
+          si = fma(-a.y, b.x, si);
+        }
       }
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -194,14 +241,14 @@ static inline dim3 grid_rhs(long long N, int nrhs) {
 }
 
 cudaError_t launch_apply_A(cudaStream_t st, const Geom &g, const Tables &tb, int nrhs,
-                           const double2 *u, double2 *Au, int divide_by_J) {
-  k_apply_A<<<grid_for(g.Nglob), 256, 0, st>>>(g, tb, nrhs, u, Au, divide_by_J);
+                           const double2 *u, double2 *Au, int divide_by_J, const double2 *sub) {
+  k_apply_A<<<grid_for(g.Nglob), 256, 0, st>>>(g, tb, nrhs, u, Au, divide_by_J, sub);
   return cudaGetLastError();
 }
 
 cudaError_t launch_scale_J(cudaStream_t st, const Geom &g, const Tables &tb, int nrhs,
                            const double2 *f, double2 *b) {
-  k_scale_J<<<grid_rhs(g.Nglob, nrhs), 256, 0, st>>>(g, tb, f, b);
+  k_scale_J<<<grid_for(g.Nglob), 256, 0, st>>>(g, tb, nrhs, f, b);
   return cudaGetLastError();
 }
 

@@ -145,7 +145,17 @@ struct TcArgs {
   long long tile_bytes;
 };
 
-// write the two pieces of v (row k of the B operand) for rows n0 (real part) and n0 + H
+// Pieces of an FP32 value by rounding its bit pattern to nearest (ties away from zero): the
+// 10 (TF32) or 7 (BF16) explicit mantissa bits of x0, then the same for x1 = x - x0, which is
+// exact in FP32.  Integer adds and masks, no conversion instructions.
+__device__ __forceinline__ float round_tf32(float x) {
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+__device__ __forceinline__ unsigned short round_bf16(float x) {
+  return (unsigned short)((__float_as_uint(x) + 0x8000u) >> 16);
+}
+
+// write the two pieces of v (row k of the B operand) for rows n_re (real part) and n_im
 // (imaginary part) of piece 0, and the same rows + 2 PC of piece 1
 template <int KIND, int PC>
 __device__ __forceinline__ void put_b(unsigned char *sB, int LB, int k, int n_re, int n_im,
@@ -153,21 +163,21 @@ __device__ __forceinline__ void put_b(unsigned char *sB, int LB, int k, int n_re
   constexpr int EK = KIND == 0 ? 4 : 8, ES = 16 / EK;
   const int off = (k / EK) * LB + (k % EK) * ES;
   const int n[4] = {n_re, n_im, n_re + 2 * PC, n_im + 2 * PC};
-  float w[4];
   if (KIND == 0) {
-    w[0] = umma::tf32_rna(v.x);
-    w[1] = umma::tf32_rna(v.y);
-    w[2] = umma::tf32_rna(v.x - w[0]);
-    w[3] = umma::tf32_rna(v.y - w[1]);
+    float w[4];
+    w[0] = round_tf32(v.x);
+    w[1] = round_tf32(v.y);
+    w[2] = round_tf32(v.x - w[0]);
+    w[3] = round_tf32(v.y - w[1]);
 #pragma unroll
     for (int i = 0; i < 4; ++i)
       *reinterpret_cast<float *>(sB + off + (n[i] >> 3) * 128 + (n[i] & 7) * 16) = w[i];
   } else {
     unsigned short b[4];
-    b[0] = umma::bf16_rn_bits(v.x);
-    b[1] = umma::bf16_rn_bits(v.y);
-    b[2] = umma::bf16_rn_bits(v.x - umma::bf16_to_float(b[0]));
-    b[3] = umma::bf16_rn_bits(v.y - umma::bf16_to_float(b[1]));
+    b[0] = round_bf16(v.x);
+    b[1] = round_bf16(v.y);
+    b[2] = round_bf16(v.x - umma::bf16_to_float(b[0]));
+    b[3] = round_bf16(v.y - umma::bf16_to_float(b[1]));
 #pragma unroll
     for (int i = 0; i < 4; ++i)
       *reinterpret_cast<unsigned short *>(sB + off + (n[i] >> 3) * 128 + (n[i] & 7) * 16) = b[i];
@@ -358,6 +368,7 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1)
       }
       umma::tmem_wait_ld();
       const bool more = q + 1 < nst;
+      float2 xo[H];
 #pragma unroll
       for (int h = 0; h < H; ++h) {
         const float p_re = d[0][h] + d[1][h], p_im = d[0][H + h] + d[1][H + h];
@@ -365,12 +376,11 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1)
         const float2 acc = make_float2(p_re - q_im, p_im + q_re);
         float2 v;
         if (fwd) {
-          if (row && xs[h]) xs[h][(long long)j * Mb + r] = acc;
+          xo[h] = acc;
           v = (j + 1 < Ml) ? csub(pre[h], cmul(cn, acc)) : cmul(cn, acc);
         } else {
-          const float2 xv = csub(pre[h], acc);
-          if (row && xs[h]) xs[h][(long long)j * Mb + r] = xv;
-          v = cmul(cn, xv);
+          xo[h] = csub(pre[h], acc);
+          v = cmul(cn, xo[h]);
         }
         if (!row) v = make_float2(0.f, 0.f);
         if (more && krow) put_b<KIND, PC>(sB, a.LB, r, grp * 2 * H + h, grp * 2 * H + H + h, v);
@@ -381,6 +391,10 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1)
         __syncwarp();
         if (lane == 0) mbar_arrive(bready);
       }
+      // x_j leaves for global memory while the next stage's MMAs run
+#pragma unroll
+      for (int h = 0; h < H; ++h)
+        if (row && xs[h]) xs[h][(long long)j * Mb + r] = xo[h];
     }
   }
   umma::fence_before_sync();

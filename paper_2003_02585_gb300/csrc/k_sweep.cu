@@ -264,75 +264,102 @@ template <> __device__ inline void atomic_cadd<double2>(double2 *dst, double2 v)
   atomicAdd(&dst->y, v.y);
 }
 
-template <typename R>
-__global__ void __launch_bounds__(256) k_trace_step(Geom g, const Panel *__restrict__ panels,
-                                                    const Col *__restrict__ cols,
-                                                    const typename Cx<R>::T *__restrict__ gmap,
-                                                    typename Cx<R>::T *__restrict__ gtr,
-                                                    const typename Cx<R>::T *__restrict__ rawf,
-                                                    const int *__restrict__ route, int l,
-                                                    int nrhs, int in_mask, int out_mask,
-                                                    int tiles_per_side, int *__restrict__ err) {
-  using C = typename Cx<R>::T;
-  constexpr int PC = 8;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  C *Gs = reinterpret_cast<C *>(smem_raw);                   // map slice [k][64]
-  C *vin = Gs + kTraceSeg * kTraceRows;                      // inputs [col][k]
-  uint64_t &bar = *reinterpret_cast<uint64_t *>(vin + PC * kTraceSeg);
-  __shared__ long long cbase[PC];
-  const Panel p = panels[blockIdx.y];
-  const int T = g.T;
-  const long long slot_stride = (long long)nrhs * g.nsub * T;
-  int which = blockIdx.x / tiles_per_side, tile = blockIdx.x % tiles_per_side, dout = -1;
-  for (int d = 0; d < g.nsides; ++d)
-    if ((out_mask >> d) & 1) {
-      if (which == 0) { dout = d; break; }
-      --which;
-    }
-  if (dout < 0 || tile >= trace_tiles(g, dout)) return;   // uniform over the block
-  // this CTA's input segment: global inputs [k0, k0 + n)
-  int sgi = blockIdx.z, k0 = 0, n = 0;
-  for (int d = 0; d < g.nsides; ++d) {
-    if (!((in_mask >> d) & 1)) continue;
-    const int ns = (2 * g.Lt[d] + kTraceSeg - 1) / kTraceSeg;
-    if (sgi < ns) {
-      k0 = g.toff[d] + sgi * kTraceSeg;
-      n = min(kTraceSeg, 2 * g.Lt[d] - sgi * kTraceSeg);
-      break;
-    }
-    sgi -= ns;
-  }
-  // independent of the previous sweep step: barrier, column descriptors, the map slice
-  if (threadIdx.x == 0) {
-    mbar_init(&bar, 1);
-    mbar_init_fence();
-  }
-  if (threadIdx.x < PC) {
-    const int c = threadIdx.x;
-    cbase[c] = c < p.ncol ? l * slot_stride +
-                                ((long long)cols[p.col0 + c].rhs * g.nsub + cols[p.col0 + c].sub) * T
-                          : -1;
-  }
+// Step completion counters of the cooperative launch: after its items of step s a CTA adds 1
+// to cnt[8 s + (blockIdx % 8)] (eight words, so arrivals do not all hit one address); a CTA
+// with items in step s + 1 first waits until the eight words of step s sum to gridDim.x.  CTAs
+// without items never wait.  The counters are zeroed before every launch.  The wait is bounded:
+// on a timeout the CTA records code 4 and goes on (results wrong, launch ends, the host reports
+// DDS_ETIMEOUT).
+constexpr int kStepCounters = 8;
+
+__device__ inline unsigned ld_acquire_gpu(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ inline void step_arrive(unsigned *cnt, int s) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    const uint32_t bytes = (uint32_t)(n * kTraceRows * sizeof(C));
-    mbar_arrive_expect_tx(&bar, bytes);
-    bulk_g2s(Gs, gmap + gmap_index(g, p.factor, dout, tile, k0, 0), bytes, &bar);
+    __threadfence();
+    atomicAdd(cnt + s * kStepCounters + (blockIdx.x % kStepCounters), 1u);
   }
-  // the previous step's traces (programmatic dependent launch: wait for it only here, and let
-  // the next step start its own prologue)
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  for (int idx = threadIdx.x; idx < PC * kTraceSeg; idx += blockDim.x) {
-    const int c = idx / kTraceSeg, kk = idx - c * kTraceSeg;
-    const long long b = cbase[c];
-    vin[idx] = (b >= 0 && kk < n) ? gtr[b + k0 + kk] : czero<C>();
+}
+__device__ inline void step_wait(const unsigned *cnt, int s, int *err) {
+  if (threadIdx.x < 32) {
+    // warp 0 polls the eight counters; the full-warp sum keeps every lane's exit decision
+    // identical.  Once any wait has given up (err set) no later wait spins.
+    const int lane = threadIdx.x;
+    uint32_t spins = 0;
+    for (;;) {
+      unsigned v = lane < kStepCounters ? ld_acquire_gpu(cnt + s * kStepCounters + lane) : 0u;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (v >= gridDim.x) break;
+      int stop = 0;
+      if (lane == 0) stop = (++spins > (1u << 20)) || *reinterpret_cast<volatile int *>(err) != 0;
+      stop = __shfl_sync(0xffffffffu, stop, 0);
+      if (stop) {
+        if (lane == 0) atomicExch(err, 4);
+        break;
+      }
+      __nanosleep(64);
+    }
   }
-  const bool ok = mbar_wait(&bar, 0);
+  __syncthreads();
+}
+
+// per-item descriptors staged in shared memory before the item's inputs are ready
+struct TraceItemSmem {
+  long long cbase[8];   // input trace base of each column (-1: no column)
+  Col col[8];
+};
+
+// Work item of a trace step: output side dout, 64-row tile `tile`, panel p, input segment
+// [k0, k0 + n).  The map slice is in Gs (bulk copy on `bar`, issued with the descriptors by
+// trace_prep); inputs come from L2 (ld.global.cg: other CTAs of this launch wrote them).
+template <typename R>
+__device__ void trace_item(const Geom &g, const Panel &p, typename Cx<R>::T *__restrict__ gtr,
+                           const typename Cx<R>::T *__restrict__ rawf, const int *__restrict__ route,
+                           int l, int nrhs, int dout, int tile, int k0, int n, bool first_seg,
+                           typename Cx<R>::T *Gs, typename Cx<R>::T *vin, uint64_t *bar,
+                           uint32_t phase, const TraceItemSmem &it, int *err) {
+  using C = typename Cx<R>::T;
+  constexpr int PC = 8;
+  constexpr int kPer = (PC * kTraceSeg + 255) / 256;
+  const int T = g.T;
+  const long long slot_stride = (long long)nrhs * g.nsub * T;
+  {
+    C v[kPer];
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int idx = threadIdx.x + u * 256;
+      v[u] = czero<C>();
+      if (idx < PC * kTraceSeg) {
+        const int c = idx / kTraceSeg, kk = idx - c * kTraceSeg;
+        const long long b = it.cbase[c];
+        if (b >= 0 && kk < n) {
+          const C *src = gtr + b + k0 + kk;
+          if constexpr (sizeof(R) == 4) {
+            const float2 t = __ldcg(reinterpret_cast<const float2 *>(src));
+            v[u].x = t.x; v[u].y = t.y;
+          } else {
+            const double2 t = __ldcg(reinterpret_cast<const double2 *>(src));
+            v[u].x = t.x; v[u].y = t.y;
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int idx = threadIdx.x + u * 256;
+      if (idx < PC * kTraceSeg) vin[idx] = v[u];
+    }
+  }
+  const bool ok = mbar_wait(bar, phase);
   if (__syncthreads_or(!ok)) {
     if (threadIdx.x == 0) {
       atomicExch(err, 3);
-      mbar_wait(&bar, 0);
+      mbar_wait(bar, phase);
     }
     __syncthreads();
     return;
@@ -391,7 +418,7 @@ __global__ void __launch_bounds__(256) k_trace_step(Geom g, const Panel *__restr
     cfma(o10, a1, v0[i]);
     cfma(o11, a1, v1[i]);
   }
-  // half 1 hands its partial sums to half 0 (the input buffer is free once both are done)
+  // half 1 hands its partial sums to half 0 through the input buffer
   __syncthreads();
   C *red = vin + (long long)lt * 4;
   if (half == 1) {
@@ -401,35 +428,150 @@ __global__ void __launch_bounds__(256) k_trace_step(Geom g, const Panel *__restr
     red[3] = o11;
   }
   __syncthreads();
-  if (half == 1) return;
-  o00 = cadd(o00, red[0]);
-  o01 = cadd(o01, red[1]);
-  o10 = cadd(o10, red[2]);
-  o11 = cadd(o11, red[3]);
-  const int rows = 2 * g.Lt[dout];
-  const int lp = route[l * 6 + dout];
-  const bool first_seg = blockIdx.z == 0;
-  const C res[2][2] = {{o00, o01}, {o10, o11}};
+  if (half == 0) {
+    o00 = cadd(o00, red[0]);
+    o01 = cadd(o01, red[1]);
+    o10 = cadd(o10, red[2]);
+    o11 = cadd(o11, red[3]);
+    const int rows = 2 * g.Lt[dout];
+    const int lp = route[l * 6 + dout];
+    const int rr = tile * kTraceRows + 2 * rp;     // rows rr, rr + 1 (rows is even)
+    if (rr < rows && lp >= 0) {
+      const int grow = g.toff[dout] + rr;          // row in the full trace vector
+      const C res[2][2] = {{o00, o10}, {o01, o11}}; // [column][row]
 #pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    const int rr = tile * kTraceRows + 2 * rp + i;
-    if (rr >= rows) continue;
-    const int grow = g.toff[dout] + rr;   // row in the full trace vector
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int cg = 2 * cq + j;
-      if (cg >= p.ncol) continue;
-      const Col cc = cols[p.col0 + cg];
-      C val = res[i][j];
-      if (rawf != nullptr && first_seg)
-        val = cadd(val, rawf[((long long)cc.rhs * g.nsub + cc.sub) * T + grow]);
-      const int nb = sub_neighbour(g, cc.sub, dout);
-      if (nb < 0 || lp < 0) continue;
-      atomic_cadd(gtr + lp * slot_stride + ((long long)cc.rhs * g.nsub + nb) * T +
-                      g.toff[dout ^ 1] + rr,
-                  val);
+      for (int jj = 0; jj < 2; ++jj) {
+        const int cg = 2 * cq + jj;
+        if (cg >= p.ncol) continue;
+        const Col cc = it.col[cg];
+        C v0r = res[jj][0], v1r = res[jj][1];
+        if (rawf != nullptr && first_seg) {
+          const C *rw = rawf + ((long long)cc.rhs * g.nsub + cc.sub) * T + grow;
+          v0r = cadd(v0r, rw[0]);
+          v1r = cadd(v1r, rw[1]);
+        }
+        const int nb = sub_neighbour(g, cc.sub, dout);
+        if (nb < 0) continue;
+        C *dst = gtr + lp * slot_stride + ((long long)cc.rhs * g.nsub + nb) * T + g.toff[dout ^ 1] + rr;
+        if constexpr (sizeof(R) == 4) {
+          // both rows in one 16-byte vector atomic (T, the side offsets and rr are even)
+          atomicAdd(reinterpret_cast<float4 *>(dst), make_float4(v0r.x, v0r.y, v1r.x, v1r.y));
+        } else {
+          atomic_cadd(dst, v0r);
+          atomic_cadd(dst + 1, v1r);
+        }
+      }
     }
   }
+  __syncthreads();   // Gs, vin and the descriptors are reused by the next item
+}
+
+// item -> (output side, tile, panel, input segment) of step sd; false if the item is empty
+__device__ inline bool trace_decode(const Geom &g, const TraceStep &sd, int tiles_per_side,
+                                    int item, int &dout, int &tile, int &panel, int &k0, int &n,
+                                    int &seg) {
+  seg = item % sd.nseg;
+  int rest = item / sd.nseg;
+  const int xt = rest % (sd.nout * tiles_per_side);
+  panel = rest / (sd.nout * tiles_per_side);
+  int which = xt / tiles_per_side;
+  tile = xt % tiles_per_side;
+  dout = -1;
+  for (int d = 0; d < g.nsides; ++d)
+    if ((sd.out_mask >> d) & 1) {
+      if (which == 0) { dout = d; break; }
+      --which;
+    }
+  if (dout < 0 || tile >= trace_tiles(g, dout)) return false;
+  int sgi = seg;
+  n = 0;
+  for (int d = 0; d < g.nsides; ++d) {
+    if (!((sd.in_mask >> d) & 1)) continue;
+    const int ns = (2 * g.Lt[d] + kTraceSeg - 1) / kTraceSeg;
+    if (sgi < ns) {
+      k0 = g.toff[d] + sgi * kTraceSeg;
+      n = min(kTraceSeg, 2 * g.Lt[d] - sgi * kTraceSeg);
+      break;
+    }
+    sgi -= ns;
+  }
+  return n > 0;
+}
+
+// Every trace step of every sweep of one DDM application in one cooperative launch: the CTAs
+// share each step's items round-robin; a CTA starts its items of step s + 1 once every CTA is
+// done with step s (step counters above).  Descriptors and map slice of a CTA's first item of
+// the next step depend on no trace, so they are staged before that wait.
+template <typename R>
+__global__ void __launch_bounds__(256) k_trace_sweeps(Geom g, const TraceStep *__restrict__ steps,
+                                                      int nsteps, const Panel *__restrict__ panels,
+                                                      const Col *__restrict__ cols,
+                                                      const typename Cx<R>::T *__restrict__ gmap,
+                                                      typename Cx<R>::T *__restrict__ gtr,
+                                                      const typename Cx<R>::T *__restrict__ rawf,
+                                                      const int *__restrict__ route, int nrhs,
+                                                      int tiles_per_side, unsigned *cnt,
+                                                      int *__restrict__ err) {
+  using C = typename Cx<R>::T;
+  constexpr int PC = 8;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  C *Gs = reinterpret_cast<C *>(smem_raw);                   // map slice [k][64]
+  C *vin = Gs + kTraceSeg * kTraceRows;                      // inputs [col][k]
+  uint64_t *bar = reinterpret_cast<uint64_t *>(vin + PC * kTraceSeg);
+  __shared__ TraceItemSmem it;
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  uint32_t phase = 0;
+  // stage item descriptors and issue the map-slice copy (all threads call; ends with a barrier)
+  auto prep = [&](const TraceStep &sd, int panel, int dout, int tile, int k0, int n) {
+    const Panel p = panels[sd.pan_off + panel];
+    if (threadIdx.x == 0) {
+      const uint32_t bytes = (uint32_t)(n * kTraceRows * sizeof(C));
+      fence_proxy_async();   // earlier generic reads of Gs before the async write
+      mbar_arrive_expect_tx(bar, bytes);
+      bulk_g2s(Gs, gmap + gmap_index(g, p.factor, dout, tile, k0, 0), bytes, bar);
+    }
+    if (threadIdx.x < PC) {
+      const int c = threadIdx.x;
+      const long long slot_stride = (long long)nrhs * g.nsub * g.T;
+      if (c < p.ncol) {
+        const Col cc = cols[p.col0 + c];
+        it.col[c] = cc;
+        it.cbase[c] = sd.l * slot_stride + ((long long)cc.rhs * g.nsub + cc.sub) * g.T;
+      } else {
+        it.cbase[c] = -1;
+      }
+    }
+    __syncthreads();
+  };
+  int prefetched = -1;   // item of the current step whose descriptors and slice are staged
+  for (int s = 0; s < nsteps; ++s) {
+    const TraceStep sd = steps[s];
+    if (s > 0 && (int)blockIdx.x < sd.nitems) step_wait(cnt, s - 1, err);
+    for (int item = blockIdx.x; item < sd.nitems; item += gridDim.x) {
+      int dout, tile, panel, k0, n, seg;
+      if (!trace_decode(g, sd, tiles_per_side, item, dout, tile, panel, k0, n, seg)) continue;
+      if (item != prefetched) prep(sd, panel, dout, tile, k0, n);
+      trace_item<R>(g, panels[sd.pan_off + panel], gtr, sd.l == 0 ? rawf : nullptr, route, sd.l,
+                    nrhs, dout, tile, k0, n, seg == 0, Gs, vin, bar, phase, it, err);
+      phase ^= 1u;
+    }
+    prefetched = -1;
+    if (s + 1 < nsteps) {
+      step_arrive(cnt, s);
+      const TraceStep sn = steps[s + 1];
+      int dout, tile, panel, k0, n, seg;
+      if ((int)blockIdx.x < sn.nitems &&
+          trace_decode(g, sn, tiles_per_side, blockIdx.x, dout, tile, panel, k0, n, seg)) {
+        prep(sn, panel, dout, tile, k0, n);
+        prefetched = blockIdx.x;
+      }
+    }
+  }
+  // a prefetch is staged only for an item that the next step consumes, so none is in flight
 }
 
 // ------------------------------------------------------------------------------------------
@@ -565,35 +707,49 @@ cudaError_t launch_extract(cudaStream_t st, const Geom &g, int ncols, const Col 
 }
 
 template <typename R>
-cudaError_t launch_trace_step(cudaStream_t st, const Geom &g, int npanels, const Panel *panels,
-                              const Col *cols, const typename Cx<R>::T *gmap,
-                              typename Cx<R>::T *gtr, const typename Cx<R>::T *rawf,
-                              const int *route, int l, int nrhs, int pc, int in_mask,
-                              int out_mask, int *err) {
-  if (npanels <= 0) return cudaSuccess;
-  if (pc != 8) return cudaErrorInvalidValue;
-  int nout = 0;
-  for (int d = 0; d < g.nsides; ++d) nout += (out_mask >> d) & 1;
-  const int nseg = trace_nseg(g, in_mask);
-  if (nout == 0 || nseg == 0) return cudaSuccess;   // nothing routed out / nothing came in
+cudaError_t launch_trace_sweeps(cudaStream_t st, const Geom &g, const TraceStep *steps, int nsteps,
+                                const Panel *panels, const Col *cols,
+                                const typename Cx<R>::T *gmap, typename Cx<R>::T *gtr,
+                                const typename Cx<R>::T *rawf, const int *route, int nrhs,
+                                unsigned *gbar, int *err) {
+  if (nsteps <= 0) return cudaSuccess;
   using C = typename Cx<R>::T;
-  const size_t smem = ((size_t)kTraceSeg * kTraceRows + 8 * kTraceSeg) * sizeof(C) + 16;
+  const size_t smem = trace_step_smem(g, 8, sizeof(C));
   static bool done[64] = {false};
-  cudaError_t e = smem_limit_once(k_trace_step<R>, done);
+  cudaError_t e = smem_limit_once(k_trace_sweeps<R>, done);
   if (e != cudaSuccess) return e;
-  const int tiles = trace_max_tiles(g);
+  int dev = 0, nsm = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_sweeps<R>, 256, smem)) !=
+      cudaSuccess)
+    return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(nout * tiles, npanels, nseg);
+  e = cudaMemsetAsync(gbar, 0, (size_t)nsteps * kStepCounters * sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  cfg.gridDim = dim3((unsigned)(nsm * std::min(per_sm, 2)));
   cfg.blockDim = dim3(256);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_trace_step<R>, g, panels, cols, gmap, gtr, rawf, route, l,
-                            nrhs, in_mask, out_mask, tiles, err);
+  return cudaLaunchKernelEx(&cfg, k_trace_sweeps<R>, g, steps, nsteps, panels, cols, gmap, gtr,
+                            rawf, route, nrhs, trace_max_tiles(g), gbar, err);
+}
+
+size_t trace_counter_bytes(int nsteps) { return (size_t)nsteps * kStepCounters * sizeof(unsigned); }
+
+int trace_step_items(const Geom &g, int npanels, int in_mask, int out_mask, int *nout, int *nseg) {
+  int no = 0;
+  for (int d = 0; d < g.nsides; ++d) no += (out_mask >> d) & 1;
+  const int ns = trace_nseg(g, in_mask);
+  if (nout) *nout = no;
+  if (nseg) *nseg = ns;
+  return no * trace_max_tiles(g) * npanels * ns;
 }
 
 size_t trace_step_smem(const Geom &, int pc, size_t elem) {
@@ -648,10 +804,10 @@ cudaError_t launch_copy_local_back(cudaStream_t st, long long n, const typename 
   template cudaError_t launch_extract<R>(cudaStream_t, const Geom &, int, const Col *,         \
                                          const Cx<R>::T *, double2 *, int, Cx<R>::T *,         \
                                          Cx<R>::T *, const int *, int, int);                    \
-  template cudaError_t launch_trace_step<R>(cudaStream_t, const Geom &, int, const Panel *,    \
-                                            const Col *, const Cx<R>::T *, Cx<R>::T *,         \
-                                            const Cx<R>::T *, const int *, int,                \
-                                            int, int, int, int, int *);                         \
+  template cudaError_t launch_trace_sweeps<R>(cudaStream_t, const Geom &, const TraceStep *,   \
+                                              int, const Panel *, const Col *,                 \
+                                              const Cx<R>::T *, Cx<R>::T *, const Cx<R>::T *,  \
+                                              const int *, int, unsigned *, int *);             \
   template cudaError_t launch_unit_traces<R>(cudaStream_t, const Geom &, const Tables &, int,  \
                                              int, Cx<R>::T *);                                  \
   template cudaError_t launch_raw_lines<R>(cudaStream_t, const Geom &, int, const Cx<R>::T *,  \
