@@ -59,7 +59,7 @@ struct CallPlan {            // all launch lists for one nrhs
   std::vector<StepPlan> steps;   // [dir][step] for the direct plan (substitution panels)
   std::vector<StepPlan> tsteps;  // [dir][step] for the trace plan (trace-step panels)
   StepPlan all;                  // every (sub, rhs) column (trace plan phases, local solves)
-  DBuf cols, panels;
+  DBuf cols, panels, tpanels;
   struct TraceTable { int n = -1; DBuf buf; };
   std::map<int, TraceTable> trace_steps;   // rounds -> step table of the cooperative launch
 };
@@ -360,6 +360,20 @@ CallPlan *get_plan(dds_ctx *ctx, int nrhs) {
     for (int s = 0; s < ctx->nsteps; ++s) cp->tsteps.push_back(emit(ctx->step_subs[dir][s], tmax, true));
   if (upload(cp->cols, cols, ctx->stream) != cudaSuccess) return nullptr;
   if (upload(cp->panels, panels, ctx->stream) != cudaSuccess) return nullptr;
+  // trace-step panels with their columns inline (panels wider than 8 columns keep the first 8,
+  // and only trace-step panels, which have at most 8, are read through this table)
+  std::vector<TracePanel> tp(panels.size());
+  for (size_t i = 0; i < panels.size(); ++i) {
+    TracePanel t{};
+    t.factor = panels[i].factor;
+    t.ncol = std::min(panels[i].ncol, 8);
+    for (int c = 0; c < t.ncol; ++c) {
+      t.sub[c] = cols[panels[i].col0 + c].sub;
+      t.rhs[c] = cols[panels[i].col0 + c].rhs;
+    }
+    tp[i] = t;
+  }
+  if (upload(cp->tpanels, tp, ctx->stream) != cudaSuccess) return nullptr;
   CallPlan *raw = cp.get();
   ctx->plans[nrhs] = std::move(cp);
   return raw;
@@ -515,7 +529,7 @@ dds_status run_ddm(dds_ctx *ctx, const double2 *b, int nrhs, double2 *u, int rou
       return DDS_EINVAL;
     }
     const CallPlan::TraceTable &tt = tti->second;
-    LAUNCHK(DDS_K_TRACE_STEP, launch_trace_sweeps<R>(st, g, tt.buf.as<TraceStep>(), tt.n, pans, cols, gmap,
+    LAUNCHK(DDS_K_TRACE_STEP, launch_trace_sweeps<R>(st, g, tt.buf.as<TraceStep>(), tt.n, cp->tpanels.as<TracePanel>(), gmap,
                                                      gtr, rawf, route, nrhs, ctx->gbar.as<unsigned>(),
                                                      ctx->errflag.as<int>()));
     // own nodes: u = A_R^{-1}(b_own + potentials of all traces received in every sweep)

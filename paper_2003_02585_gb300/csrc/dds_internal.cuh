@@ -197,6 +197,12 @@ cudaError_t launch_extract(cudaStream_t st, const Geom &g, int ncols, const Col 
                            typename Cx<R>::T *raw_out, typename Cx<R>::T *g_traces,
                            const int *route, int l, int nrhs);
 
+// a trace-step panel with its columns' (subdomain, RHS) inline (one load level in the kernel)
+struct TracePanel {
+  int factor, ncol;
+  int sub[8], rhs[8];
+};
+
 // one sweep step of the trace plan: sweep l, its panels, and its work items
 struct TraceStep {
   int l, pan_off, npanels, in_mask, out_mask, nout, nseg, nitems;
@@ -208,7 +214,7 @@ size_t trace_counter_bytes(int nsteps);   // step counters of one launch (gbar)
 // zeroed by the launch)
 template <typename R>
 cudaError_t launch_trace_sweeps(cudaStream_t st, const Geom &g, const TraceStep *steps, int nsteps,
-                                const Panel *panels, const Col *cols,
+                                const TracePanel *panels,
                                 const typename Cx<R>::T *gmap, typename Cx<R>::T *g_traces,
                                 const typename Cx<R>::T *rawf, const int *route, int nrhs,
                                 unsigned *gbar, int *err);

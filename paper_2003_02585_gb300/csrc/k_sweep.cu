@@ -311,14 +311,15 @@ __device__ inline void step_wait(const unsigned *cnt, int s, int *err) {
 // per-item descriptors staged in shared memory before the item's inputs are ready
 struct TraceItemSmem {
   long long cbase[8];   // input trace base of each column (-1: no column)
-  Col col[8];
+  int sub[8], rhs[8];
+  int ncol;
 };
 
 // Work item of a trace step: output side dout, 64-row tile `tile`, panel p, input segment
 // [k0, k0 + n).  The map slice is in Gs (bulk copy on `bar`, issued with the descriptors by
 // trace_prep); inputs come from L2 (ld.global.cg: other CTAs of this launch wrote them).
 template <typename R>
-__device__ void trace_item(const Geom &g, const Panel &p, typename Cx<R>::T *__restrict__ gtr,
+__device__ void trace_item(const Geom &g, typename Cx<R>::T *__restrict__ gtr,
                            const typename Cx<R>::T *__restrict__ rawf, const int *__restrict__ route,
                            int l, int nrhs, int dout, int tile, int k0, int n, bool first_seg,
                            typename Cx<R>::T *Gs, typename Cx<R>::T *vin, uint64_t *bar,
@@ -442,17 +443,17 @@ __device__ void trace_item(const Geom &g, const Panel &p, typename Cx<R>::T *__r
 #pragma unroll
       for (int jj = 0; jj < 2; ++jj) {
         const int cg = 2 * cq + jj;
-        if (cg >= p.ncol) continue;
-        const Col cc = it.col[cg];
+        if (cg >= it.ncol) continue;
+        const int csub_ = it.sub[cg], crhs = it.rhs[cg];
         C v0r = res[jj][0], v1r = res[jj][1];
         if (rawf != nullptr && first_seg) {
-          const C *rw = rawf + ((long long)cc.rhs * g.nsub + cc.sub) * T + grow;
+          const C *rw = rawf + ((long long)crhs * g.nsub + csub_) * T + grow;
           v0r = cadd(v0r, rw[0]);
           v1r = cadd(v1r, rw[1]);
         }
-        const int nb = sub_neighbour(g, cc.sub, dout);
+        const int nb = sub_neighbour(g, csub_, dout);
         if (nb < 0) continue;
-        C *dst = gtr + lp * slot_stride + ((long long)cc.rhs * g.nsub + nb) * T + g.toff[dout ^ 1] + rr;
+        C *dst = gtr + lp * slot_stride + ((long long)crhs * g.nsub + nb) * T + g.toff[dout ^ 1] + rr;
         if constexpr (sizeof(R) == 4) {
           // both rows in one 16-byte vector atomic (T, the side offsets and rr are even)
           atomicAdd(reinterpret_cast<float4 *>(dst), make_float4(v0r.x, v0r.y, v1r.x, v1r.y));
@@ -500,12 +501,15 @@ __device__ inline bool trace_decode(const Geom &g, const TraceStep &sd, int tile
 
 // Every trace step of every sweep of one DDM application in one cooperative launch: the CTAs
 // share each step's items round-robin; a CTA starts its items of step s + 1 once every CTA is
-// done with step s (step counters above).  Descriptors and map slice of a CTA's first item of
-// the next step depend on no trace, so they are staged before that wait.
+// done with step s (step counters above).  The step table sits in shared memory; the
+// descriptors of a CTA's first item of step s + 1 are loaded into registers at the top of step s
+// and staged, with that item's map-slice copy, before the wait -- none of it depends on a trace.
+constexpr int kMaxSmemSteps = 512;
+
 template <typename R>
 __global__ void __launch_bounds__(256) k_trace_sweeps(Geom g, const TraceStep *__restrict__ steps,
-                                                      int nsteps, const Panel *__restrict__ panels,
-                                                      const Col *__restrict__ cols,
+                                                      int nsteps,
+                                                      const TracePanel *__restrict__ panels,
                                                       const typename Cx<R>::T *__restrict__ gmap,
                                                       typename Cx<R>::T *__restrict__ gtr,
                                                       const typename Cx<R>::T *__restrict__ rawf,
@@ -518,55 +522,76 @@ __global__ void __launch_bounds__(256) k_trace_sweeps(Geom g, const TraceStep *_
   C *Gs = reinterpret_cast<C *>(smem_raw);                   // map slice [k][64]
   C *vin = Gs + kTraceSeg * kTraceRows;                      // inputs [col][k]
   uint64_t *bar = reinterpret_cast<uint64_t *>(vin + PC * kTraceSeg);
+  TraceStep *st_s = reinterpret_cast<TraceStep *>(bar + 2);  // step table (nsteps <= 512)
   __shared__ TraceItemSmem it;
+  const bool smem_steps = nsteps <= kMaxSmemSteps;
+  for (int i = threadIdx.x; smem_steps && i < nsteps; i += blockDim.x) st_s[i] = steps[i];
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
     mbar_init_fence();
   }
   __syncthreads();
+  auto step_at = [&](int s) { return smem_steps ? st_s[s] : steps[s]; };
+  const long long slot_stride = (long long)nrhs * g.nsub * g.T;
   uint32_t phase = 0;
-  // stage item descriptors and issue the map-slice copy (all threads call; ends with a barrier)
-  auto prep = [&](const TraceStep &sd, int panel, int dout, int tile, int k0, int n) {
-    const Panel p = panels[sd.pan_off + panel];
+  // descriptors of one item, loaded by threads 0..7 (column c = thread) into registers
+  struct Pre { int factor, ncol, sub, rhs; };
+  auto load_pre = [&](const TraceStep &sd, int panel) {
+    Pre q{0, 0, 0, 0};
+    if (threadIdx.x < PC) {
+      const TracePanel *tp = panels + sd.pan_off + panel;
+      q.factor = tp->factor;
+      q.ncol = tp->ncol;
+      q.sub = tp->sub[threadIdx.x];
+      q.rhs = tp->rhs[threadIdx.x];
+    }
+    return q;
+  };
+  // stage the descriptors and issue the map-slice copy (all threads call; ends with a barrier)
+  auto prep = [&](const Pre &q, int l, int dout, int tile, int k0, int n) {
     if (threadIdx.x == 0) {
       const uint32_t bytes = (uint32_t)(n * kTraceRows * sizeof(C));
       fence_proxy_async();   // earlier generic reads of Gs before the async write
       mbar_arrive_expect_tx(bar, bytes);
-      bulk_g2s(Gs, gmap + gmap_index(g, p.factor, dout, tile, k0, 0), bytes, bar);
+      bulk_g2s(Gs, gmap + gmap_index(g, q.factor, dout, tile, k0, 0), bytes, bar);
+      it.ncol = q.ncol;
     }
     if (threadIdx.x < PC) {
       const int c = threadIdx.x;
-      const long long slot_stride = (long long)nrhs * g.nsub * g.T;
-      if (c < p.ncol) {
-        const Col cc = cols[p.col0 + c];
-        it.col[c] = cc;
-        it.cbase[c] = sd.l * slot_stride + ((long long)cc.rhs * g.nsub + cc.sub) * g.T;
-      } else {
-        it.cbase[c] = -1;
-      }
+      it.sub[c] = q.sub;
+      it.rhs[c] = q.rhs;
+      it.cbase[c] = c < q.ncol ? l * slot_stride + ((long long)q.rhs * g.nsub + q.sub) * g.T : -1;
     }
     __syncthreads();
   };
   int prefetched = -1;   // item of the current step whose descriptors and slice are staged
   for (int s = 0; s < nsteps; ++s) {
-    const TraceStep sd = steps[s];
+    const TraceStep sd = step_at(s);
+    // the next step's first item: its descriptors travel while this step runs
+    TraceStep sn{};
+    bool have_next = false;
+    int nd = 0, nt = 0, npan = 0, nk0 = 0, nn = 0, nseg = 0;
+    Pre qn{0, 0, 0, 0};
+    if (s + 1 < nsteps) {
+      sn = step_at(s + 1);
+      have_next = (int)blockIdx.x < sn.nitems &&
+                  trace_decode(g, sn, tiles_per_side, blockIdx.x, nd, nt, npan, nk0, nn, nseg);
+      if (have_next) qn = load_pre(sn, npan);
+    }
     if (s > 0 && (int)blockIdx.x < sd.nitems) step_wait(cnt, s - 1, err);
     for (int item = blockIdx.x; item < sd.nitems; item += gridDim.x) {
       int dout, tile, panel, k0, n, seg;
       if (!trace_decode(g, sd, tiles_per_side, item, dout, tile, panel, k0, n, seg)) continue;
-      if (item != prefetched) prep(sd, panel, dout, tile, k0, n);
-      trace_item<R>(g, panels[sd.pan_off + panel], gtr, sd.l == 0 ? rawf : nullptr, route, sd.l,
-                    nrhs, dout, tile, k0, n, seg == 0, Gs, vin, bar, phase, it, err);
+      if (item != prefetched) prep(load_pre(sd, panel), sd.l, dout, tile, k0, n);
+      trace_item<R>(g, gtr, sd.l == 0 ? rawf : nullptr, route, sd.l, nrhs, dout, tile, k0, n,
+                    seg == 0, Gs, vin, bar, phase, it, err);
       phase ^= 1u;
     }
     prefetched = -1;
     if (s + 1 < nsteps) {
       step_arrive(cnt, s);
-      const TraceStep sn = steps[s + 1];
-      int dout, tile, panel, k0, n, seg;
-      if ((int)blockIdx.x < sn.nitems &&
-          trace_decode(g, sn, tiles_per_side, blockIdx.x, dout, tile, panel, k0, n, seg)) {
-        prep(sn, panel, dout, tile, k0, n);
+      if (have_next) {
+        prep(qn, sn.l, nd, nt, nk0, nn);
         prefetched = blockIdx.x;
       }
     }
@@ -708,7 +733,7 @@ cudaError_t launch_extract(cudaStream_t st, const Geom &g, int ncols, const Col 
 
 template <typename R>
 cudaError_t launch_trace_sweeps(cudaStream_t st, const Geom &g, const TraceStep *steps, int nsteps,
-                                const Panel *panels, const Col *cols,
+                                const TracePanel *panels,
                                 const typename Cx<R>::T *gmap, typename Cx<R>::T *gtr,
                                 const typename Cx<R>::T *rawf, const int *route, int nrhs,
                                 unsigned *gbar, int *err) {
@@ -737,7 +762,7 @@ cudaError_t launch_trace_sweeps(cudaStream_t st, const Geom &g, const TraceStep 
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_trace_sweeps<R>, g, steps, nsteps, panels, cols, gmap, gtr,
+  return cudaLaunchKernelEx(&cfg, k_trace_sweeps<R>, g, steps, nsteps, panels, gmap, gtr,
                             rawf, route, nrhs, trace_max_tiles(g), gbar, err);
 }
 
@@ -753,7 +778,8 @@ int trace_step_items(const Geom &g, int npanels, int in_mask, int out_mask, int 
 }
 
 size_t trace_step_smem(const Geom &, int pc, size_t elem) {
-  return ((size_t)kTraceSeg * kTraceRows + (size_t)pc * kTraceSeg) * elem + 16;
+  return ((size_t)kTraceSeg * kTraceRows + (size_t)pc * kTraceSeg) * elem + 16 +
+         (size_t)kMaxSmemSteps * sizeof(TraceStep);
 }
 
 template <typename R>
@@ -805,7 +831,7 @@ cudaError_t launch_copy_local_back(cudaStream_t st, long long n, const typename 
                                          const Cx<R>::T *, double2 *, int, Cx<R>::T *,         \
                                          Cx<R>::T *, const int *, int, int);                    \
   template cudaError_t launch_trace_sweeps<R>(cudaStream_t, const Geom &, const TraceStep *,   \
-                                              int, const Panel *, const Col *,                 \
+                                              int, const TracePanel *,                          \
                                               const Cx<R>::T *, Cx<R>::T *, const Cx<R>::T *,  \
                                               const int *, int, unsigned *, int *);             \
   template cudaError_t launch_unit_traces<R>(cudaStream_t, const Geom &, const Tables &, int,  \
