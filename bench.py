@@ -211,8 +211,43 @@ def fp64_check(args, wl, R, f_dev, u_mixed, stream):
         fp64_ms.append(e0.elapsed_time(e1))
     fp64_value = R * len(fp64_ms) / (sum(fp64_ms) / 1e3) if fp64_ms else None
     ctx64.close()
-    del ctx64, u64
-    return err, fp64_ms, fp64_value
+    del ctx64
+    return err, fp64_ms, fp64_value, u64
+
+
+def time_variant(args, wl, R, f_dev, stream, flush, precision, u64):
+    """The same timed solve loop for another single-precision sweep variant (same workload,
+    steps, L2 flush), with its accuracy against the FP64 GPU solve."""
+    import torch
+
+    from paper_2003_02585_gb300 import dds
+
+    ctx = dds.Context(wl.n, wl.h, wl.omega, wl.c, wl.parts, wl.pml_cells, wl.pml_strength,
+                      precision=precision, plan=args.plan)
+    its = []
+    for _ in range(args.warmup):
+        ctx.solve(f_dev, tol=args.tol, maxit=args.maxit, rounds=wl.rounds)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        u, it, _ = ctx.solve(f_dev, tol=args.tol, maxit=args.maxit, rounds=wl.rounds)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        its.append(it)
+    err = None
+    if u64 is not None:
+        err = max(float(torch.linalg.vector_norm(u[r] - u64[r]) / torch.linalg.vector_norm(u64[r]))
+                  for r in range(R))
+    ctx.close()
+    return {"precision": precision, "dtype": DTYPE[precision],
+            "value": R * len(ms) / (sum(ms) / 1e3), "unit": "RHS/s",
+            "ms_per_step": sum(ms) / len(ms), "max_rel_l2_vs_fp64_gpu": err,
+            "fgmres_iterations": sorted(set(its))}
 
 def run_gpu(args):
     import torch
@@ -271,9 +306,13 @@ def run_gpu(args):
 
     # accuracy against the plain FP64 GPU solve, and that solve's own throughput
     if args.no_fp64:
-        err, fp64_ms, fp64_value = [float("nan")], [], None
+        err, fp64_ms, fp64_value, u64 = [float("nan")], [], None, None
     else:
-        err, fp64_ms, fp64_value = fp64_check(args, wl, R, f_dev, u_mixed, stream)
+        err, fp64_ms, fp64_value, u64 = fp64_check(args, wl, R, f_dev, u_mixed, stream)
+    # the other single-precision sweep variants, timed the same way
+    variants = [time_variant(args, wl, R, f_dev, stream, flush, p, u64)
+                for p in args.variants.split(",") if p and p != args.precision]
+    del u64
 
     # end to end through the C ABI with host (pinned) buffers
     f_pin = torch.from_numpy(f_host).pin_memory()
@@ -340,6 +379,7 @@ def run_gpu(args):
         "roofline": roofline,
         "cpu_baseline": cpu,
         "clocks": clocks,
+        "variants": variants,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -353,6 +393,9 @@ DTYPE = {"mixed": "c64 sweeps (3xTF32 tensor-core substitutions) + c128 FGMRES",
          "mixed_bf16": "c64 sweeps (3xBF16 tensor-core substitutions) + c128 FGMRES",
          "mixed_fp32": "c64 sweeps (FP32 CUDA-core substitutions) + c128 FGMRES"}
 SPLIT_KIND = {"mixed": "tf32", "mixed_bf16": "bf16", "mixed_fp32": "fp32"}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the substitution kernel,
+# from one ncu capture of the kernel as it stands, on the same workload and launch configuration
+SUBST_TRAFFIC = {("mixed", "const2d_640"): 128.78e6 + 62.24e6}
 
 
 def roofline_entry(stats, info, wl, R, args):
@@ -405,7 +448,8 @@ def roofline_entry(stats, info, wl, R, args):
                  "bound": "alu",
                  "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
     entry.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                  "frac": achieved / peak, "traffic": None,
+                  "frac": achieved / peak,
+                  "traffic": SUBST_TRAFFIC.get((args.precision, args.workload)),
                   "launches": n_launch, "avg_launch_ms": ms / n_launch,
                   "family_share": {k: v[1] for k, v in stats.items()}})
     return entry
@@ -456,6 +500,8 @@ def main():
     ap.add_argument("--plan", default="auto", choices=["auto", "direct", "trace"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_bf16", "mixed_fp32"],
                     help="single-precision sweep variant of the timed solver")
+    ap.add_argument("--variants", default="mixed_bf16,mixed_fp32",
+                    help="other sweep variants timed the same way and reported beside the line")
     ap.add_argument("--rounds", type=int, default=None,
                     help="DDM rounds per preconditioner application (default: the workload's)")
     ap.add_argument("--fp64-steps", type=int, default=1)
