@@ -311,7 +311,8 @@ def run_gpu(args):
         err, fp64_ms, fp64_value, u64 = fp64_check(args, wl, R, f_dev, u_mixed, stream)
     # the other single-precision sweep variants, timed the same way
     variants = [time_variant(args, wl, R, f_dev, stream, flush, p, u64)
-                for p in args.variants.split(",") if p and p != args.precision]
+                for p in args.variants.split(",")
+                if p and p != "none" and p != args.precision]
     del u64
 
     # end to end through the C ABI with host (pinned) buffers
@@ -337,10 +338,10 @@ def run_gpu(args):
         _, it_p, _ = ctx.solve(f_dev, tol=args.tol, maxit=args.maxit, rounds=wl.rounds)
         ddm_apps += it_p
     stats = ctx.kernel_stats()
-    # local solves of the direct plan during the profiled solves (2^n sweeps per round)
-    args.ddm_solves_profiled = ddm_apps * (2 ** len(wl.n)) * wl.rounds * info["n_sub"] * R
     ctx.profile(False)
-    roofline = roofline_entry(stats, info, wl, R, args) if args.profile_steps > 0 else None
+    work = ctx.work_per_ddm(R, wl.rounds)
+    roofline, roofline_kernels = (roofline_entry(stats, work, ddm_apps, args)
+                                  if args.profile_steps > 0 else (None, []))
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -377,6 +378,7 @@ def run_gpu(args):
         "gpu_launches": launches,
         "setup_seconds": info["setup_seconds"],
         "roofline": roofline,
+        "roofline_kernels": roofline_kernels,
         "cpu_baseline": cpu,
         "clocks": clocks,
         "variants": variants,
@@ -395,64 +397,61 @@ DTYPE = {"mixed": "c64 sweeps (3xTF32 tensor-core substitutions) + c128 FGMRES",
 SPLIT_KIND = {"mixed": "tf32", "mixed_bf16": "bf16", "mixed_fp32": "fp32"}
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the substitution kernel,
 # from one ncu capture of the kernel as it stands, on the same workload and launch configuration
-SUBST_TRAFFIC = {("mixed", "const2d_640"): 128.78e6 + 62.24e6}
+SUBST_TRAFFIC = {}
+TRACE_TRAFFIC = {("mixed", "const2d_640"): 40.98e6 + 0.11e6}
 
 
-def roofline_entry(stats, info, wl, R, args):
-    """Roofline of the substitution kernel family (algorithmic FLOPs per launch / event time).
+def roofline_entry(stats, work, ddm_apps, args):
+    """Rooflines of the two sweep kernel families from their event-timed totals.
 
-    Algorithmic work of one block-tridiagonal solve: forward + back substitution touch every
-    block inverse once each, 2 * Ml * Mb^2 complex multiply-adds = 16 * Ml * Mb^2 real flops.
-    Peak: for the tensor-core substitutions, the dense tensor rate of the piece type divided by
-    the three split products each useful product costs (TF32 = measured BF16 rate x 1.1/2.25,
-    the nominal TF32:BF16 ratio); for the CUDA-core kernel, the FP32 FMA rate.
+    work = (substitution flops, trace-map flops) of one DDM application (dds_work_per_ddm:
+    16 Ml Mb^2 flop per local solve; 8 x routed map rows x received inputs per sweep, subdomain
+    and RHS); ddm_apps = DDM applications in the profiled solves.  Achieved = algorithmic flops /
+    device time of the family.  Peaks: the tensor-core substitutions take the dense tensor rate of
+    their piece type divided by the three split products each useful product costs (TF32 =
+    measured BF16 rate x 1.1/2.25, the nominal TF32:BF16 ratio); FP32 CUDA-core kernels take
+    152 SMs x 128 lanes x 2 flop x 2070 MHz.  The entry of the family with the larger device time
+    is the line's roofline; both are listed.
     """
     peaks, src = _peaks()
-    n_sub = info["n_sub"]
-    dim = len(wl.n)
-    Mext = info["M"][:dim]
-    Ml = Mext[-1]                                  # blocks along the last axis
-    Mb = 1
-    for m in Mext[:-1]:
-        Mb *= m                                    # nodes of one line (2D) / plane (3D)
-    flops_per_solve = 16.0 * Ml * Mb * Mb
-    n_launch, ms = stats["subst"]
-    if n_launch == 0 or ms <= 0:
-        return None
-    # trace plan: each DDM application runs two substitution launches over all (subdomain, RHS)
-    # columns; direct plan: one launch per sweep step over that step's columns
-    if info["plan"] == 2:
-        solves_per_launch = n_sub * R
-    else:
-        # (sweeps x subdomains x RHS local solves per DDM, spread over its step launches)
-        solves_per_launch = None
-    if solves_per_launch is None:
-        # total local solves of the profiled solves / launches: the FGMRES iteration count is
-        # not known here, so take the per-launch average over the whole profiled run
-        solves_per_launch = args.ddm_solves_profiled / n_launch
-    achieved = flops_per_solve * solves_per_launch / (ms / n_launch / 1e3) / 1e12
+    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
     kind = SPLIT_KIND.get(args.precision, "fp32")
-    tc = kind != "fp32" and Mb <= 128
-    if tc:
-        bf16 = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
-        base = bf16 * (1.1 / 2.25) if kind == "tf32" else bf16
-        peak = base / 3.0
-        entry = {"kernel": f"k_subst_tc<{kind}> (block forward+back substitution, 3x{kind.upper()} "
+    entries = []
+    n_s, ms_s = stats["subst"]
+    if n_s > 0 and ms_s > 0 and work[0] > 0:
+        achieved = work[0] * ddm_apps / (ms_s / 1e3) / 1e12
+        if kind != "fp32":
+            bf16 = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+            base = bf16 * (1.1 / 2.25) if kind == "tf32" else bf16
+            peak = base / 3.0
+            e = {"kernel": f"k_subst_tc<{kind}> (block forward+back substitution, 3x{kind.upper()} "
                            f"split products on tcgen05)", "bound": "tensor",
                  "peak_source": f"{src} bf16 sustained {bf16:.0f} TF/s"
                                 + (" x 1.1/2.25 (nominal TF32:BF16)" if kind == "tf32" else "")
                                 + " / 3 split products"}
-    else:
-        peak = 152 * 128 * 2 * 2.07e9 / 1e12       # FP32 FMA lanes x 2 flop x max SM clock
-        entry = {"kernel": "k_subst_stream<float> (block forward+back substitution)",
-                 "bound": "alu",
+        else:
+            peak = fp32_peak
+            e = {"kernel": "k_subst_stream<float> (block forward+back substitution)", "bound": "alu",
                  "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
-    entry.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                  "frac": achieved / peak,
+        e.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                   "traffic": SUBST_TRAFFIC.get((args.precision, args.workload)),
-                  "launches": n_launch, "avg_launch_ms": ms / n_launch,
-                  "family_share": {k: v[1] for k, v in stats.items()}})
-    return entry
+                  "launches": n_s, "avg_launch_ms": ms_s / n_s, "device_ms": ms_s})
+        entries.append(e)
+    n_t, ms_t = stats["trace_step"]
+    if n_t > 0 and ms_t > 0 and work[1] > 0:
+        achieved = work[1] * ddm_apps / (ms_t / 1e3) / 1e12
+        entries.append({"kernel": "k_trace_sweeps<float> (every trace step of a DDM application, "
+                                  "one cooperative launch)", "bound": "alu",
+                        "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                        "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                        "frac": achieved / fp32_peak,
+                        "traffic": TRACE_TRAFFIC.get((args.precision, args.workload)),
+                        "launches": n_t, "avg_launch_ms": ms_t / n_t, "device_ms": ms_t})
+    if not entries:
+        return None, []
+    main = dict(max(entries, key=lambda e: e["device_ms"]))
+    main["family_share"] = {k: v[1] for k, v in stats.items()}
+    return main, entries
 
 
 def run_serving(args):

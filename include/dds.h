@@ -179,6 +179,17 @@ dds_status dds_get_info(const dds_ctx *ctx, dds_info_t *info);
 /* dds_kernel_launches -- number of kernels this context has launched so far. */
 long long dds_kernel_launches(const dds_ctx *ctx);
 
+/* dds_work_per_ddm -- algorithmic floating-point work of one DDM application (Algorithm 2.1 /
+ * 4.1, `rounds` rounds of 2^n sweeps) for nrhs right-hand sides, computed on the host:
+ *   *subst_flops  block forward + back substitutions, 16 Ml Mb^2 real flops per local solve
+ *                 (2 Ml Mb^2 complex multiply-adds), times the local solves of the plan;
+ *   *trace_flops  trace-map applications of the trace plan: 8 x (map rows of routed sides that
+ *                 have a neighbour) x (inputs of receiving sides that have one) per (sweep,
+ *                 subdomain, RHS); 0 for the direct plan.
+ * Used to turn kernel times into achieved rates.  DDS_EINVAL on bad arguments. */
+dds_status dds_work_per_ddm(dds_ctx *ctx, int nrhs, int rounds, double *subst_flops,
+                            double *trace_flops);
+
 /* Kernel families timed by the profiler (dds_profile_read). */
 typedef enum {
   DDS_K_ASSEMBLE = 0,   /* own-source + trace-potential right-hand sides                    */

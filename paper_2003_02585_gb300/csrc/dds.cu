@@ -73,6 +73,7 @@ struct dds_ctx {
   int precision = 0, plan = 0;
   bool single = false;   // sweeps in complex single precision (every precision but DDS_FP64)
   int split = -1;        // tensor-core substitution pieces: 0 = TF32, 1 = BF16, -1 = none
+  int tc_m = 0;          // middle block of the two-sided tensor-core chain (0: one-sided)
   double h = 0, omega = 0, S = 0;
   int P = 0, power = 2, H = 0;
   cudaStream_t stream = nullptr;
@@ -282,12 +283,15 @@ int pick_pc(int ncols, int max_pc) {
 
 int pick_pc_stream(const Geom &g, int ncols);
 
-int pick_pc_tc(const Geom &g, int split, int ncols) {
-  // the tensor-core kernel holds one CTA per SM and its MMA time does not depend on the panel
-  // width: the narrowest panel (8, 16 or 32 columns) that fits the columns into one wave
+int pick_pc_tc(const Geom &g, int split, bool twisted, int ncols) {
+  // the tensor-core kernel holds one CTA per SM (two per panel for the two-sided chain) and its
+  // MMA time does not depend on the panel width: the narrowest panel (8, 16 or 32 columns)
+  // that fits the columns into one wave
+  const int per = twisted ? 2 : 1;
   int pc = 8;
-  while (pc < 32 && (ncols + pc - 1) / pc > 152 && subst_tc_ok(g, split, pc * 2)) pc *= 2;
-  return subst_tc_ok(g, split, pc) ? pc : 0;
+  while (pc < 32 && per * ((ncols + pc - 1) / pc) > 152 && subst_tc_ok(g, split, pc * 2, twisted))
+    pc *= 2;
+  return subst_tc_ok(g, split, pc, twisted) ? pc : 0;
 }
 
 int pick_pc_stream(const Geom &g, int ncols) {
@@ -343,7 +347,7 @@ CallPlan *get_plan(dds_ctx *ctx, int nrhs) {
       sp.pc = pc_cap;
     } else {
       int spc = 0;
-      if (ctx->single && ctx->split >= 0) spc = pick_pc_tc(ctx->g, ctx->split, sp.ncols);
+      if (ctx->single && ctx->split >= 0) spc = pick_pc_tc(ctx->g, ctx->split, ctx->tc_m > 0, sp.ncols);
       if (ctx->single && spc == 0) spc = pick_pc_stream(ctx->g, sp.ncols);
       sp.pc = spc > 0 ? spc : pick_pc(sp.ncols, pc_cap);
     }
@@ -404,10 +408,10 @@ cudaError_t subst_any(dds_ctx *ctx, int npan, const Panel *pans, const Col *cols
                       const typename Cx<R>::T *sinv, const typename Cx<R>::T *cpl,
                       typename Cx<R>::T *work, int pc) {
   if constexpr (sizeof(R) == 4) {
-    if (ctx->split >= 0 && subst_tc_ok(ctx->g, ctx->split, pc))
+    if (ctx->split >= 0 && subst_tc_ok(ctx->g, ctx->split, pc, ctx->tc_m > 0))
       return launch_subst_tc(ctx->stream, ctx->g, ctx->split, npan, pans, cols,
                              ctx->tctiles.as<unsigned char>(), cpl, work, pc,
-                             ctx->errflag.as<int>());
+                             ctx->errflag.as<int>(), ctx->tc_m);
     if (subst_stream_ok(ctx->g, pc))
       return launch_subst_stream(ctx->stream, ctx->g, npan, pans, cols, sinv, cpl, work, pc,
                                  ctx->errflag.as<int>());
@@ -937,12 +941,28 @@ dds_status setup_impl(dds_ctx *ctx, const dds_problem *p) {
     dds_status r = build_trace_map<double>(ctx);
     if (r != DDS_OK) return r;
   }
-  if (ctx->split >= 0 && subst_tc_ok(g, ctx->split, 8)) {
-    // block inverses split into tensor-core pieces, from the FP64 inverses
+  if (ctx->split >= 0 && subst_tc_ok(g, ctx->split, 8, false)) {
+    // Two-sided (twisted) factorisation where the chain is long enough and the blocks fit the
+    // in-shared-memory factor kernel: T_j^{-1} (j > m) and Z_m^{-1} in FP64, then every inverse
+    // split into tensor-core pieces.
+    const int m = (!big_blocks && subst_tc_ok(g, ctx->split, 8, true)) ? tc_middle_block(g) : 0;
+    DBuf tw;
+    if (m > 0) {
+      CK(tw.ensure(sinv_elems * sizeof(double2)));
+      LAUNCH(launch_factor_twisted(st, ctx->nfac, Mb, Ml, g.St, g.M[0], m, ddg.as<double2>(),
+                                   doffx.as<double2>(), dim == 3 ? doffy.as<double2>() : nullptr,
+                                   dcpl.as<double2>(), ctx->sinv64.as<double2>(),
+                                   tw.as<double2>(), ctx->status.as<int>()));
+      int status2 = 0;
+      CK(cudaMemcpyAsync(&status2, ctx->status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      if (status2 != 0) { ctx->err = "singular pivot in the two-sided factorisation"; return DDS_EINVAL; }
+    }
     CK(ctx->tctiles.ensure((size_t)tc_tiles_bytes(g, ctx->split, ctx->nfac)));
     LAUNCH(launch_split_tc(st, g, ctx->split, ctx->nfac, ctx->sinv64.as<double2>(),
-                           ctx->tctiles.as<unsigned char>()));
+                           m > 0 ? tw.as<double2>() : nullptr, m, ctx->tctiles.as<unsigned char>()));
     CK(cudaStreamSynchronize(st));
+    ctx->tc_m = m;
   } else {
     ctx->split = -1;   // blocks wider than 128 nodes: FP32 CUDA-core substitutions
   }
@@ -1262,7 +1282,7 @@ dds_status dds_local_solve(dds_ctx *ctx, int sub, const void *b, int nrhs, void 
   std::vector<Col> cols(nrhs);
   for (int q = 0; q < nrhs; ++q) cols[q] = Col{sub, q, q, 0};
   const bool mixed = ctx->single;
-  const bool tc = mixed && ctx->split >= 0 && subst_tc_ok(g, ctx->split, 8);
+  const bool tc = mixed && ctx->split >= 0 && subst_tc_ok(g, ctx->split, 8, ctx->tc_m > 0);
   const int pc = tc ? 8 : std::min(4, max_pc_for(ctx, mixed ? sizeof(float2) : sizeof(double2)));
   std::vector<Panel> pans;
   for (int i = 0; i < nrhs; i += pc) pans.push_back(Panel{i, std::min(pc, nrhs - i), ctx->fac_of_sub[sub], 0});
@@ -1316,6 +1336,40 @@ dds_status dds_get_info(const dds_ctx *ctx, dds_info_t *info) {
 }
 
 long long dds_kernel_launches(const dds_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+dds_status dds_work_per_ddm(dds_ctx *ctx, int nrhs, int rounds, double *subst_flops,
+                            double *trace_flops) {
+  if (!ctx || nrhs <= 0 || rounds < 1 || !subst_flops || !trace_flops) return DDS_EINVAL;
+  Busy busy(ctx);
+  if (!busy.ok) return DDS_EBUSY;
+  const Geom &g = ctx->g;
+  dds_status r = set_route(ctx, rounds);
+  if (r != DDS_OK) return r;
+  const std::vector<int> route = build_route(g.dim, rounds);
+  const int L = ctx->ndirs * rounds;
+  const double per_solve = 16.0 * g.Ml * (double)g.Mb * g.Mb;
+  // substitutions: trace plan = own-source solves + final solves of every (sub, RHS);
+  // direct plan = one solve per (sub, RHS) per sweep
+  const double nsolves = ctx->plan == DDS_PLAN_TRACE ? 2.0 * g.nsub * nrhs : (double)L * g.nsub * nrhs;
+  *subst_flops = per_solve * nsolves;
+  // trace map applications (trace plan): per (sweep, sub, RHS), complex map rows of the routed
+  // sides that have a neighbour times the inputs of the receiving sides that have one
+  double tf = 0.0;
+  if (ctx->plan == DDS_PLAN_TRACE) {
+    for (int l = 0; l < L; ++l)
+      for (int sub = 0; sub < g.nsub; ++sub) {
+        double rows = 0.0, inputs = 0.0;
+        for (int d = 0; d < g.nsides; ++d) {
+          if (sub_neighbour(g, sub, d) < 0) continue;
+          if (((ctx->out_mask[l] >> d) & 1) && route[l * 6 + d] >= 0) rows += 2.0 * g.Lt[d];
+          if ((ctx->in_mask[l] >> d) & 1) inputs += 2.0 * g.Lt[d];
+        }
+        tf += 8.0 * rows * inputs * nrhs;
+      }
+  }
+  *trace_flops = tf;
+  return DDS_OK;
+}
 
 dds_status dds_profile(dds_ctx *ctx, int enable) {
   if (!ctx) return DDS_EINVAL;
@@ -1716,7 +1770,7 @@ extern "C" dds_status dds_local_solve_noalloc(dds_ctx *ctx, int sub, const void 
   // launch descriptors, built on the stack and copied into the static scratch
   Col cols[kStaticMaxRhs];
   Panel pans[kStaticMaxRhs];
-  const bool tc = mixed && ctx->split >= 0 && subst_tc_ok(g, ctx->split, 8);
+  const bool tc = mixed && ctx->split >= 0 && subst_tc_ok(g, ctx->split, 8, ctx->tc_m > 0);
   const int pc = tc ? 8 : std::min(4, max_pc_for(ctx, elem));
   int npan = 0;
   for (int q = 0; q < nrhs; ++q) cols[q] = Col{sub, q, q, 0};

@@ -159,6 +159,10 @@ cudaError_t launch_factor(cudaStream_t st, int nfac, int Mb, int Ml, long long S
                           const double2 *offx, const double2 *offy, const double2 *cpl,
                           double2 *sinv64, float2 *sinv32, int *status);
 
+cudaError_t launch_factor_twisted(cudaStream_t st, int nfac, int Mb, int Ml, long long St, int M0,
+                                  int m, const double2 *dg, const double2 *offx,
+                                  const double2 *offy, const double2 *cpl,
+                                  const double2 *sinv64, double2 *tw64, int *status);
 cudaError_t launch_factor_big(cudaStream_t st, int f, int Mb, int Ml, long long St, int M0,
                               const double2 *dg, const double2 *offx, const double2 *offy,
                               const double2 *cpl, double2 *S, double2 *colk, int *piv,
@@ -183,13 +187,17 @@ cudaError_t launch_subst_stream(cudaStream_t st, const Geom &g, int npanels, con
 bool subst_stream_ok(const Geom &g, int pc);
 
 // tensor-core substitutions (k_subst_tc.cu); kind 0 = TF32 pieces, 1 = BF16 pieces
+// m > 0: two-sided chain split at block m, one 2-CTA cluster per panel; m = 0: one-sided
 cudaError_t launch_subst_tc(cudaStream_t st, const Geom &g, int kind, int npanels,
                             const Panel *panels, const Col *cols, const unsigned char *tiles,
-                            const float2 *cpl, float2 *work, int pc, int *err);
-bool subst_tc_ok(const Geom &g, int kind, int pc);
+                            const float2 *cpl, float2 *work, int pc, int *err, int m);
+bool subst_tc_ok(const Geom &g, int kind, int pc, bool twisted);
+int tc_middle_block(const Geom &g);   // m of the two-sided chain (0: too few blocks)
 long long tc_tiles_bytes(const Geom &g, int kind, int nfac);
+// tiles j < m from sinv64, j >= m from tw64 (m = 0 or tw64 null: all from sinv64)
 cudaError_t launch_split_tc(cudaStream_t st, const Geom &g, int kind, int nfac,
-                            const double2 *sinv64, unsigned char *tiles);
+                            const double2 *sinv64, const double2 *tw64, int m,
+                            unsigned char *tiles);
 
 template <typename R>
 cudaError_t launch_extract(cudaStream_t st, const Geom &g, int ncols, const Col *cols,

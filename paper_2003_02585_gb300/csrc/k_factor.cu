@@ -15,6 +15,15 @@ __device__ inline double2 crecip(double2 z) {
   return make_double2(z.x / m, -z.y / m);
 }
 
+// One chain of the factorisation per CTA (factor f = blockIdx.x), over `count` blocks starting
+// at j0 in direction dir:
+//   dir = +1 (from the top):    S_j = D_j - C_{j-1} S_{j-1}^{-1} C_{j-1}
+//   dir = -1 (from the bottom): T_j = D_j - C_j T_{j+1}^{-1} C_j
+// The previous block's inverse is either the chain's own last result (in shared memory) or, for
+// the first block when prev_inv is given, tile j0 - dir of prev_inv.  When extra_inv is given,
+// the last block of the chain also subtracts C_j X C_j with X = tile j + 1 of extra_inv (the
+// middle block of the two-sided factorisation: Z_m = D_m - C_{m-1} S_{m-1}^{-1} C_{m-1}
+// - C_m T_{m+1}^{-1} C_m).  Each inverse is stored as [s][r] at tile j of out64 (and out32).
 __global__ void __launch_bounds__(1024) k_factor(int Mb, int Ml, long long St, int M0,
                                                  const double2 *__restrict__ dg,
                                                  const double2 *__restrict__ offx,
@@ -22,7 +31,9 @@ __global__ void __launch_bounds__(1024) k_factor(int Mb, int Ml, long long St, i
                                                  const double2 *__restrict__ cpl,
                                                  double2 *__restrict__ sinv64,
                                                  float2 *__restrict__ sinv32,
-                                                 int *__restrict__ status) {
+                                                 int *__restrict__ status, int j0, int count,
+                                                 int dir, const double2 *__restrict__ prev_inv,
+                                                 const double2 *__restrict__ extra_inv) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2 *S = reinterpret_cast<double2 *>(smem_raw);      // [Mb][Mb] row-major
   double2 *colk = S + (size_t)Mb * Mb;                       // [Mb]
@@ -32,18 +43,39 @@ __global__ void __launch_bounds__(1024) k_factor(int Mb, int Ml, long long St, i
   const int lane = tid & 31, warp = tid >> 5;
   const long long fb = (long long)f * Ml * Mb;
   const long long MbMb = (long long)Mb * Mb;
+  if (prev_inv != nullptr) {
+    const long long pb = ((long long)f * Ml + (j0 - dir)) * St;
+    for (long long idx = tid; idx < MbMb; idx += nt) {
+      const int r = (int)(idx / Mb), s = (int)(idx % Mb);
+      S[idx] = prev_inv[pb + (long long)s * Mb + r];
+    }
+    __syncthreads();
+  }
 
-  for (int j = 0; j < Ml; ++j) {
-    // ---- S_j = D_j - C_{j-1} S_{j-1}^{-1} C_{j-1}
+  for (int jj = 0; jj < count; ++jj) {
+    const int j = j0 + dir * jj;
+    const bool has_prev = jj > 0 || prev_inv != nullptr;
+    // coupling between block j and the previous block of the chain
+    const int jc = dir > 0 ? j - 1 : j;
+    const bool extra = extra_inv != nullptr && jj == count - 1;
+    const long long xb = ((long long)f * Ml + (j + 1)) * St;
+    // ---- S_j = D_j - C S_prev^{-1} C  (- C_j X C_j for the middle block)
     for (long long idx = tid; idx < MbMb; idx += nt) {
       const int r = (int)(idx / Mb), s = (int)(idx % Mb);
       double2 val = make_double2(0.0, 0.0);
-      if (j > 0) {
-        const double2 cr = cpl[fb + (long long)(j - 1) * Mb + r];
-        const double2 cs = cpl[fb + (long long)(j - 1) * Mb + s];
+      if (has_prev) {
+        const double2 cr = cpl[fb + (long long)jc * Mb + r];
+        const double2 cs = cpl[fb + (long long)jc * Mb + s];
         val = cmul(cmul(cr, S[idx]), cs);
         val.x = -val.x;
         val.y = -val.y;
+      }
+      if (extra) {
+        const double2 cr = cpl[fb + (long long)j * Mb + r];
+        const double2 cs = cpl[fb + (long long)j * Mb + s];
+        const double2 t = cmul(cmul(cr, extra_inv[xb + (long long)s * Mb + r]), cs);
+        val.x -= t.x;
+        val.y -= t.y;
       }
       const long long lb = fb + (long long)j * Mb;
       if (r == s) val = cadd(val, dg[lb + r]);
@@ -122,21 +154,45 @@ __global__ void __launch_bounds__(1024) k_factor(int Mb, int Ml, long long St, i
       const int s = (int)(idx / Mb), r = (int)(idx % Mb);
       const double2 v = S[(long long)r * Mb + s];
       sinv64[ob + idx] = v;
-      sinv32[ob + idx] = make_float2((float)v.x, (float)v.y);
+      if (sinv32 != nullptr) sinv32[ob + idx] = make_float2((float)v.x, (float)v.y);
     }
     __syncthreads();
   }
+}
+
+static size_t factor_smem(int Mb) {
+  return (size_t)Mb * Mb * sizeof(double2) + Mb * sizeof(double2) + Mb * sizeof(int);
 }
 
 cudaError_t launch_factor(cudaStream_t st, int nfac, int Mb, int Ml, long long St, int M0,
                           const double2 *dg,
                           const double2 *offx, const double2 *offy, const double2 *cpl,
                           double2 *sinv64, float2 *sinv32, int *status) {
-  const size_t smem = (size_t)Mb * Mb * sizeof(double2) + Mb * sizeof(double2) + Mb * sizeof(int);
+  const size_t smem = factor_smem(Mb);
   cudaError_t e = cudaFuncSetAttribute(k_factor, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  k_factor<<<nfac, 1024, smem, st>>>(Mb, Ml, St, M0, dg, offx, offy, cpl, sinv64, sinv32, status);
+  k_factor<<<nfac, 1024, smem, st>>>(Mb, Ml, St, M0, dg, offx, offy, cpl, sinv64, sinv32, status,
+                                     0, Ml, 1, nullptr, nullptr);
+  return cudaGetLastError();
+}
+
+// The blocks m..Ml-1 of the two-sided factorisation, given the top chain S_j^{-1} (sinv64):
+// T_j^{-1} for j = Ml-1 down to m+1, then Z_m^{-1}; written as tiles m..Ml-1 of tw64.
+cudaError_t launch_factor_twisted(cudaStream_t st, int nfac, int Mb, int Ml, long long St, int M0,
+                                  int m, const double2 *dg, const double2 *offx,
+                                  const double2 *offy, const double2 *cpl,
+                                  const double2 *sinv64, double2 *tw64, int *status) {
+  if (m < 1 || m > Ml - 2) return cudaErrorInvalidValue;
+  const size_t smem = factor_smem(Mb);
+  cudaError_t e = cudaFuncSetAttribute(k_factor, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  k_factor<<<nfac, 1024, smem, st>>>(Mb, Ml, St, M0, dg, offx, offy, cpl, tw64, nullptr, status,
+                                     Ml - 1, Ml - 1 - m, -1, nullptr, nullptr);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_factor<<<nfac, 1024, smem, st>>>(Mb, Ml, St, M0, dg, offx, offy, cpl, tw64, nullptr, status,
+                                     m, 1, 1, sinv64, tw64);
   return cudaGetLastError();
 }
 

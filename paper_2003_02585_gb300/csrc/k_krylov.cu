@@ -15,7 +15,8 @@ __device__ inline double2 crecip64(double2 z) {
 //           + kappa^2 J u_p,          Dirichlet outside the extended grid.
 // The stencil is precomputed per node at set-up (tb.c0: centre, tb.cp[a]: coupling to p + e_a,
 // so the coupling to p - e_a is tb.cp[a][p - e_a]); each thread applies it to every RHS.
-__global__ void k_apply_A(Geom g, Tables tb, int nrhs, const double2 *__restrict__ u,
+template <int DIM>
+__global__ void __launch_bounds__(256) k_apply_A(Geom g, Tables tb, int nrhs, const double2 *__restrict__ u,
                           double2 *__restrict__ Au, int divide_by_J,
                           const double2 *__restrict__ sub) {
   const int N = (int)g.Nglob;
@@ -24,25 +25,24 @@ __global__ void k_apply_A(Geom g, Tables tb, int nrhs, const double2 *__restrict
     int p[3];
     p[0] = q % G0;
     p[1] = (q / G0) % G1;
-    p[2] = g.dim == 3 ? q / (G0 * G1) : 0;
+    p[2] = DIM == 3 ? q / (G0 * G1) : 0;
     const double2 c0 = tb.c0[q];
-    double2 cpv[3], cmv[3];
-    int stride[3];
+    double2 cpv[DIM], cmv[DIM];
+    int stride[DIM];
     int st = 1;
     bool real = c0.y == 0.0;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
+    for (int a = 0; a < DIM; ++a) {
       stride[a] = st;
       st *= g.G[a];
-      const bool on = a < g.dim;
-      cpv[a] = on && p[a] + 1 < g.G[a] ? tb.cp[a][q] : make_double2(0.0, 0.0);
-      cmv[a] = on && p[a] > 0 ? tb.cp[a][q - stride[a]] : make_double2(0.0, 0.0);
+      cpv[a] = p[a] + 1 < g.G[a] ? tb.cp[a][q] : make_double2(0.0, 0.0);
+      cmv[a] = p[a] > 0 ? tb.cp[a][q - stride[a]] : make_double2(0.0, 0.0);
       real = real && cpv[a].y == 0.0 && cmv[a].y == 0.0;
     }
     double2 iJ = make_double2(1.0, 0.0);
     if (divide_by_J) {
       double2 J = make_double2(1.0, 0.0);
-      for (int a = 0; a < g.dim; ++a) J = cmul(J, tb.an_glob64[a][p[a]]);
+      for (int a = 0; a < DIM; ++a) J = cmul(J, tb.an_glob64[a][p[a]]);
       iJ = crecip64(J);
     }
     for (int r = 0; r < nrhs; ++r) {
@@ -53,8 +53,7 @@ __global__ void k_apply_A(Geom g, Tables tb, int nrhs, const double2 *__restrict
         const double2 uc = ur[q];
         sum = make_double2(c0.x * uc.x, c0.x * uc.y);
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          if (a >= g.dim) break;
+        for (int a = 0; a < DIM; ++a) {
           if (p[a] + 1 < g.G[a]) {
             const double2 un = ur[q + stride[a]];
             sum.x = fma(cpv[a].x, un.x, sum.x);
@@ -69,8 +68,7 @@ __global__ void k_apply_A(Geom g, Tables tb, int nrhs, const double2 *__restrict
       } else {
         sum = cmul(c0, ur[q]);
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          if (a >= g.dim) break;
+        for (int a = 0; a < DIM; ++a) {
           if (p[a] + 1 < g.G[a]) cfma(sum, cpv[a], ur[q + stride[a]]);
           if (p[a] > 0) cfma(sum, cmv[a], ur[q - stride[a]]);
         }
@@ -105,65 +103,97 @@ __global__ void k_scale_J(Geom g, Tables tb, int nrhs, const double2 *__restrict
   }
 }
 
-// partial[(rhs * nv + i) * nblk + blk] = sum over the block's chunk of conj(V_i) * w.
-// The block's chunk of w is staged in shared memory once and reused for all nv vectors.
+// partial[(rhs * nv + i) * nblk + blk] = sum over the block's elements of conj(V_i) * w.
+// Grid-stride over elements, up to four vectors per pass over w, four elements per iteration in
+// flight; each thread keeps its running sums in registers and the block reduces them once.  A
+// vector that is w itself (a norm) costs two FMAs per element instead of four.
 constexpr int kDotThreads = 256;
-constexpr int kDotPerThread = 8;
-constexpr int kDotChunk = kDotThreads * kDotPerThread;
+constexpr int kDotChunk = kDotThreads * 24;   // elements per block (sets nblk)
 
-__global__ void __launch_bounds__(kDotThreads) k_dots(long long N, int nv,
+template <int NV>
+__global__ void __launch_bounds__(kDotThreads) k_dots(long long N, int nv, int i0,
                                                      const double2 *__restrict__ V, long long vsv,
                                                      long long vsr, const double2 *__restrict__ w,
                                                      long long wsr, double2 *__restrict__ partial) {
-  __shared__ double2 ws[kDotChunk];
-  __shared__ double red[2][kDotThreads / 32];
+  __shared__ double red[2 * NV][kDotThreads / 32];
   const int blk = blockIdx.x, nblk = gridDim.x;
   const int rhs = blockIdx.y;
-  const long long n0 = (long long)blk * kDotChunk;
   const double2 *ww = w + rhs * wsr;
-  for (int e = threadIdx.x; e < kDotChunk; e += kDotThreads) {
-    const long long n = n0 + e;
-    ws[e] = n < N ? ww[n] : make_double2(0.0, 0.0);
+  const double2 *v[NV];
+  bool self[NV];
+  double sr[NV], si[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    v[i] = V + (i0 + i) * vsv + rhs * vsr;
+    self[i] = v[i] == ww;
+    sr[i] = 0.0;
+    si[i] = 0.0;
   }
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i = 0; i < nv; ++i) {
-    const double2 *v = V + i * vsv + rhs * vsr;
-    double sr = 0.0, si = 0.0;
-    if (v == ww) {
-      // ||w||^2: two FMAs per element
+  const long long stride = (long long)nblk * kDotThreads;
+  long long n = (long long)blk * kDotThreads + threadIdx.x;
+  for (; n + 3 * stride < N; n += 4 * stride) {
+    double2 b[4];
 #pragma unroll
-      for (int q = 0; q < kDotPerThread; ++q) {
-        const double2 b = ws[q * kDotThreads + threadIdx.x];
-        sr = fma(b.x, b.x, sr);
-        sr = fma(b.y, b.y, sr);
-      }
-    } else {
+    for (int u = 0; u < 4; ++u) b[u] = ww[n + u * stride];
 #pragma unroll
-      for (int q = 0; q < kDotPerThread; ++q) {
-        const int e = q * kDotThreads + threadIdx.x;
-        const long long n = n0 + e;
-        if (n < N) {
-          const double2 a = v[n], b = ws[e];
-          sr = fma(a.x, b.x, sr);
-          sr = fma(a.y, b.y, sr);
-          si = fma(a.x, b.y, si);
-          si = fma(-a.y, b.x, si);
+    for (int i = 0; i < NV; ++i) {
+      if (self[i]) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          sr[i] = fma(b[u].x, b[u].x, sr[i]);
+          sr[i] = fma(b[u].y, b[u].y, sr[i]);
+        }
+      } else {
+        double2 a[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) a[u] = v[i][n + u * stride];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          sr[i] = fma(a[u].x, b[u].x, sr[i]);
+          sr[i] = fma(a[u].y, b[u].y, sr[i]);
+          si[i] = fma(a[u].x, b[u].y, si[i]);
+          si[i] = fma(-a[u].y, b[u].x, si[i]);
         }
       }
     }
+  }
+  for (; n < N; n += stride) {
+    const double2 b = ww[n];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      if (self[i]) {
+        sr[i] = fma(b.x, b.x, sr[i]);
+        sr[i] = fma(b.y, b.y, sr[i]);
+      } else {
+        const double2 a = v[i][n];
+        sr[i] = fma(a.x, b.x, sr[i]);
+        sr[i] = fma(a.y, b.y, sr[i]);
+        si[i] = fma(a.x, b.y, si[i]);
+        si[i] = fma(-a.y, b.x, si[i]);
+      }
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
     for (int o = 16; o > 0; o >>= 1) {
-      sr += __shfl_down_sync(0xffffffffu, sr, o);
-      si += __shfl_down_sync(0xffffffffu, si, o);
+      sr[i] += __shfl_down_sync(0xffffffffu, sr[i], o);
+      si[i] += __shfl_down_sync(0xffffffffu, si[i], o);
     }
-    if (lane == 0) { red[0][warp] = sr; red[1][warp] = si; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double tr = 0.0, ti = 0.0;
-      for (int q = 0; q < kDotThreads / 32; ++q) { tr += red[0][q]; ti += red[1][q]; }
-      partial[((long long)rhs * nv + i) * nblk + blk] = make_double2(tr, ti);
+    if (lane == 0) {
+      red[2 * i][warp] = sr[i];
+      red[2 * i + 1][warp] = si[i];
     }
-    __syncthreads();
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    const int i = threadIdx.x;
+    double tr = 0.0, ti = 0.0;
+    for (int q = 0; q < kDotThreads / 32; ++q) {
+      tr += red[2 * i][q];
+      ti += red[2 * i + 1][q];
+    }
+    partial[((long long)rhs * nv + i0 + i) * nblk + blk] = make_double2(tr, ti);
   }
 }
 
@@ -242,7 +272,10 @@ static inline dim3 grid_rhs(long long N, int nrhs) {
 
 cudaError_t launch_apply_A(cudaStream_t st, const Geom &g, const Tables &tb, int nrhs,
                            const double2 *u, double2 *Au, int divide_by_J, const double2 *sub) {
-  k_apply_A<<<grid_for(g.Nglob), 256, 0, st>>>(g, tb, nrhs, u, Au, divide_by_J, sub);
+  if (g.dim == 2)
+    k_apply_A<2><<<grid_for(g.Nglob), 256, 0, st>>>(g, tb, nrhs, u, Au, divide_by_J, sub);
+  else
+    k_apply_A<3><<<grid_for(g.Nglob), 256, 0, st>>>(g, tb, nrhs, u, Au, divide_by_J, sub);
   return cudaGetLastError();
 }
 
@@ -256,9 +289,16 @@ cudaError_t launch_dots(cudaStream_t st, long long N, int nrhs, int nv, const do
                         long long vsv, long long vsr, const double2 *w, long long wsr,
                         double2 *partial, double2 *out, int nblk) {
   dim3 grid(nblk, nrhs);
-  k_dots<<<grid, kDotThreads, 0, st>>>(N, nv, V, vsv, vsr, w, wsr, partial);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  for (int i0 = 0; i0 < nv; i0 += 4) {
+    switch (std::min(4, nv - i0)) {
+      case 1: k_dots<1><<<grid, kDotThreads, 0, st>>>(N, nv, i0, V, vsv, vsr, w, wsr, partial); break;
+      case 2: k_dots<2><<<grid, kDotThreads, 0, st>>>(N, nv, i0, V, vsv, vsr, w, wsr, partial); break;
+      case 3: k_dots<3><<<grid, kDotThreads, 0, st>>>(N, nv, i0, V, vsv, vsr, w, wsr, partial); break;
+      default: k_dots<4><<<grid, kDotThreads, 0, st>>>(N, nv, i0, V, vsv, vsr, w, wsr, partial); break;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   k_dots_reduce<<<nrhs * nv, 32, 0, st>>>(nrhs * nv, nblk, partial, out);
   return cudaGetLastError();
 }

@@ -55,7 +55,7 @@ struct TcShape {
 
 static size_t tc_static_smem() { return 1024; }
 
-bool tc_shape(const Geom &g, int kind, int pc, TcShape *s) {
+bool tc_shape(const Geom &g, int kind, int pc, TcShape *s, bool twisted = false) {
   TcShape t;
   t.kind = kind;
   t.EK = kind == 0 ? 4 : 8;
@@ -66,7 +66,8 @@ bool tc_shape(const Geom &g, int kind, int pc, TcShape *s) {
   t.ks = t.Kp / (2 * t.EK);
   t.LB = 4 * pc * 16 + 16;
   t.tile_bytes = (long long)t.ks * 128 * t.Mp;
-  const size_t bbytes = (size_t)(t.Kp / t.EK) * t.LB;
+  // B operand, plus the exchange buffer [128 rows][pc] of the two-sided chain
+  const size_t bbytes = (size_t)(t.Kp / t.EK) * t.LB + (twisted ? (size_t)128 * pc * 8 : 0);
   const size_t budget = 227 * 1024 - tc_static_smem();
   for (int nch = 1; nch <= t.ks; ++nch) {
     const int KS = (t.ks + nch - 1) / nch;
@@ -89,20 +90,25 @@ long long tc_tiles_bytes(const Geom &g, int kind, int nfac) {
 }
 
 template <int KIND>
-__global__ void k_split_tc(const double2 *__restrict__ sinv, unsigned char *__restrict__ out,
-                           int nfac, int Mb, int Ml, long long St, int Mp, int Kp) {
+__global__ void k_split_tc(const double2 *__restrict__ sinv, const double2 *__restrict__ tw,
+                           int m, unsigned char *__restrict__ out, int nfac, int Mb, int Ml,
+                           long long St, int Mp, int Kp) {
   constexpr int EK = KIND == 0 ? 4 : 8, ES = 16 / EK;
   const long long total = (long long)nfac * Ml * Kp * Mp;
   const long long tile = (long long)(Kp / (2 * EK)) * 128 * Mp;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
-    const int m = (int)(i % Mp);
+    const int mm = (int)(i % Mp);
     const int k = (int)((i / Mp) % Kp);
     const long long fj = i / ((long long)Mp * Kp);
     double2 a = make_double2(0.0, 0.0);
-    if (m < Mb && k < Mb) a = sinv[fj * St + (long long)k * Mb + m];
+    if (mm < Mb && k < Mb) {
+      // two-sided factorisation: tiles from the middle block down come from tw
+      const double2 *src = (tw != nullptr && (int)(fj % Ml) >= m) ? tw : sinv;
+      a = src[fj * St + (long long)k * Mb + mm];
+    }
     const int t = k / (2 * EK), gg = (k / EK) & 1;
-    unsigned char *base = out + fj * tile + (long long)t * 128 * Mp + (long long)m * 16 + (k % EK) * ES;
+    unsigned char *base = out + fj * tile + (long long)t * 128 * Mp + (long long)mm * 16 + (k % EK) * ES;
     const double parts[2] = {a.x, a.y};
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
@@ -125,16 +131,19 @@ __global__ void k_split_tc(const double2 *__restrict__ sinv, unsigned char *__re
 }
 
 cudaError_t launch_split_tc(cudaStream_t st, const Geom &g, int kind, int nfac,
-                            const double2 *sinv64, unsigned char *tiles) {
+                            const double2 *sinv64, const double2 *tw64, int m,
+                            unsigned char *tiles) {
   TcShape t;
   if (!tc_shape(g, kind, 8, &t)) return cudaErrorInvalidValue;
   const long long total = (long long)nfac * g.Ml * t.Kp * t.Mp;
   const int threads = 256;
   const int blocks = (int)std::min<long long>((total + threads - 1) / threads, 152LL * 16);
   if (kind == 0)
-    k_split_tc<0><<<blocks, threads, 0, st>>>(sinv64, tiles, nfac, g.Mb, g.Ml, g.St, t.Mp, t.Kp);
+    k_split_tc<0><<<blocks, threads, 0, st>>>(sinv64, tw64, m, tiles, nfac, g.Mb, g.Ml, g.St, t.Mp,
+                                              t.Kp);
   else
-    k_split_tc<1><<<blocks, threads, 0, st>>>(sinv64, tiles, nfac, g.Mb, g.Ml, g.St, t.Mp, t.Kp);
+    k_split_tc<1><<<blocks, threads, 0, st>>>(sinv64, tw64, m, tiles, nfac, g.Mb, g.Ml, g.St, t.Mp,
+                                              t.Kp);
   return cudaGetLastError();
 }
 
@@ -184,11 +193,40 @@ __device__ __forceinline__ void put_b(unsigned char *sB, int LB, int k, int n_re
   }
 }
 
-template <int PC, int KIND, int NG>
+// Stage map of one CTA.  The chain is split at block m: role 0 runs blocks 0..m-1 forward, the
+// middle block m, then m-1..0 backward; role 1 (two-sided factorisation only) runs Ml-1..m+1
+// forward, the middle block, then m+1..Ml-1 backward.  The one-sided chain is role 0 with
+// m = Ml - 1 (its "middle" is the last block).  Tiles: S_j^{-1} for j < m, the middle inverse
+// (Z_m^{-1}, or S_{Ml-1}^{-1} one-sided) at m, T_j^{-1} for j > m.
+struct TcStage {
+  int j;      // block
+  int kind;   // 0 forward, 1 middle, 2 backward
+  int jn;     // block of the next stage of this CTA (-1: none)
+};
+__device__ inline TcStage tc_stage(int role, int q, int m, int Ml) {
+  TcStage t;
+  if (role == 0) {
+    if (q < m) { t.j = q; t.kind = 0; t.jn = q + 1; }
+    else if (q == m) { t.j = m; t.kind = 1; t.jn = m - 1; }
+    else { t.j = 2 * m - q; t.kind = 2; t.jn = t.j - 1; }
+  } else {
+    const int nf = Ml - 1 - m;
+    if (q < nf) { t.j = Ml - 1 - q; t.kind = 0; t.jn = t.j - 1; }
+    else if (q == nf) { t.j = m; t.kind = 1; t.jn = m + 1 < Ml ? m + 1 : -1; }
+    else { t.j = m + (q - nf); t.kind = 2; t.jn = t.j + 1 < Ml ? t.j + 1 : -1; }
+  }
+  if (t.jn < 0) t.jn = -1;
+  return t;
+}
+__device__ inline int tc_nstages(int role, int m, int Ml) {
+  return role == 0 ? 2 * m + 1 : 2 * (Ml - 1 - m) + 1;
+}
+
+template <int PC, int KIND, int NG, bool TW>
 __global__ void __launch_bounds__(32 * (4 * NG + 2), 1)
     k_subst_tc(Geom g, TcArgs a, const Panel *__restrict__ panels, const Col *__restrict__ cols,
                const unsigned char *__restrict__ tiles, const float2 *__restrict__ cpl,
-               float2 *__restrict__ work, int *__restrict__ err) {
+               float2 *__restrict__ work, int *__restrict__ err, int m) {
   constexpr int H = PC / NG;            // columns per epilogue thread
   constexpr int NEPI = 128 * NG;        // epilogue threads
   constexpr int NCOL = 8 * PC;          // TMEM columns: D1 [0, 4PC), D2 [4PC, 8PC)
@@ -196,20 +234,23 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1)
   constexpr uint32_t kIdN4 = KIND == 0 ? umma::idesc_tf32(128, 4 * PC) : umma::idesc_bf16(128, 4 * PC);
   constexpr uint32_t kIdN2 = KIND == 0 ? umma::idesc_tf32(128, 2 * PC) : umma::idesc_bf16(128, 2 * PC);
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  __shared__ uint64_t bars[7];   // full[2], empty[2], dready, bready, drain
+  __shared__ uint64_t bars[8];   // full[2], empty[2], dready, bready, drain, xbar
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   uint64_t *full = bars, *empty = bars + 2, *dready = bars + 4, *bready = bars + 5,
-           *drain = bars + 6;
+           *drain = bars + 6, *xbar = bars + 7;
 
   const int Mb = g.Mb, Ml = g.Ml;
-  const int nst = 2 * Ml - 1;
+  const int role = TW ? (int)cluster_ctarank() : 0;
+  const int nst = tc_nstages(role, m, Ml);
+  const int nfwd = role == 0 ? m : Ml - 1 - m;   // forward stages before the middle block
   const long long chunk_bytes = (long long)a.KS * 128 * a.Mp;
   unsigned char *ring = smem_raw;
   unsigned char *sB = smem_raw + 2 * chunk_bytes;
-  const Panel p = panels[blockIdx.x];
+  // exchange buffer of the two-sided chain: the peer's coupling term, [row][PC]
+  float2 *xch = reinterpret_cast<float2 *>(sB + (size_t)(a.Kp / (KIND == 0 ? 4 : 8)) * a.LB);
+  const Panel p = panels[TW ? blockIdx.x / 2 : blockIdx.x];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  auto block_of = [&](int q) { return q < Ml ? q : 2 * Ml - 2 - q; };
   auto aborted = [&]() { return *reinterpret_cast<volatile int *>(&abort_flag) != 0; };
   auto fail = [&](int code) {
     atomicExch(err, code);
@@ -224,6 +265,7 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1)
     mbar_init(dready, 1);
     mbar_init(bready, NEPI / 32);   // one arrival per epilogue warp
     mbar_init(drain, 1);
+    mbar_init(xbar, NEPI);          // one remote arrival per epilogue thread of the peer
     abort_flag = 0;
     mbar_init_fence();
   }
@@ -232,14 +274,15 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1)
     umma::tmem_relinquish();
   }
   umma::fence_before_sync();
-  __syncthreads();
+  if (TW) cluster_sync_all();   // both CTAs' barriers exist before any remote arrival
+  else __syncthreads();
   umma::fence_after_sync();
   const uint32_t tmem = tmem_base;
 
   if (warp == 4 * NG) {
-    // ---------------- producer: S_j^{-1} tiles in stage order through the two-slot ring
+    // ---------------- producer: the tiles of this CTA's stages through the two-slot ring
     if (lane == 0) {
-      int last[2] = {-1, -1};
+      int last0 = -1, last1 = -1;
       const int nchunks = nst * a.nch;
       for (int i = 0; i < nchunks; ++i) {
         const int s = i & 1;
@@ -248,15 +291,16 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1)
         const int q = i / a.nch, c = i % a.nch;
         const int nks = min(a.KS, a.ks - c * a.KS);
         const uint32_t bytes = (uint32_t)nks * 128u * (uint32_t)a.Mp;
-        const unsigned char *src = tiles + ((long long)p.factor * Ml + block_of(q)) * a.tile_bytes +
+        const int j = tc_stage(role, q, m, Ml).j;
+        const unsigned char *src = tiles + ((long long)p.factor * Ml + j) * a.tile_bytes +
                                    (long long)c * a.KS * 128 * a.Mp;
         mbar_arrive_expect_tx(&full[s], bytes);
         bulk_g2s(ring + s * chunk_bytes, src, bytes, &full[s]);
-        last[s] = i;
+        if (s == 0) last0 = i; else last1 = i;
       }
       // no copy may still be landing when the CTA leaves
-      for (int s = 0; s < 2; ++s)
-        if (last[s] >= 0 && !mbar_wait(&full[s], (last[s] >> 1) & 1)) atomicExch(err, 12);
+      if (last0 >= 0 && !mbar_wait(&full[0], (last0 >> 1) & 1)) atomicExch(err, 12);
+      if (last1 >= 0 && !mbar_wait(&full[1], (last1 >> 1) & 1)) atomicExch(err, 12);
     }
   } else if (warp == 4 * NG + 1) {
     // ---------------- MMA issuer
@@ -314,12 +358,15 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1)
       const int c = grp * H + h;
       xs[h] = c < p.ncol ? work + (long long)cols[p.col0 + c].slot * g.Nloc : nullptr;
     }
-    // B operand of stage 0: b_0
-    if (krow) {
+    // B operand of the first stage: the right-hand side of its block
+    {
+      const int j = tc_stage(role, 0, m, Ml).j;
+      if (krow) {
 #pragma unroll
-      for (int h = 0; h < H; ++h) {
-        const float2 v = (row && xs[h]) ? xs[h][r] : make_float2(0.f, 0.f);
-        put_b<KIND, PC>(sB, a.LB, r, grp * 2 * H + h, grp * 2 * H + H + h, v);
+        for (int h = 0; h < H; ++h) {
+          const float2 v = (row && xs[h]) ? xs[h][(long long)j * Mb + r] : make_float2(0.f, 0.f);
+          put_b<KIND, PC>(sB, a.LB, r, grp * 2 * H + h, grp * 2 * H + H + h, v);
+        }
       }
     }
     fence_proxy_async();
@@ -328,28 +375,22 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1)
     if (lane == 0) mbar_arrive(bready);
     const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
     for (int q = 0; q < nst; ++q) {
-      const int j = block_of(q);
-      const bool fwd = q < Ml;
+      const TcStage st = tc_stage(role, q, m, Ml);
+      const bool exch = TW && st.kind == 0 && q == nfwd - 1;   // last forward stage
+      // epilogue operands, loaded before the accumulator is ready: the right-hand side of the
+      // next block (forward), this block's forward result (backward), the coupling to the next
       float2 pre[H];
       float2 cn = make_float2(0.f, 0.f);
 #pragma unroll
       for (int h = 0; h < H; ++h) pre[h] = make_float2(0.f, 0.f);
       if (row) {
-        if (fwd) {
-          if (j + 1 < Ml) {
-#pragma unroll
-            for (int h = 0; h < H; ++h)
-              if (xs[h]) pre[h] = xs[h][(long long)(j + 1) * Mb + r];
-            cn = cf[(long long)j * Mb + r];
-          } else if (Ml >= 2) {
-            cn = cf[(long long)(Ml - 2) * Mb + r];
-          }
-        } else {
+        const int jp = st.kind == 0 ? st.jn : (st.kind == 2 ? st.j : -1);
+        if (jp >= 0) {
 #pragma unroll
           for (int h = 0; h < H; ++h)
-            if (xs[h]) pre[h] = xs[h][(long long)j * Mb + r];
-          if (j > 0) cn = cf[(long long)(j - 1) * Mb + r];
+            if (xs[h]) pre[h] = xs[h][(long long)jp * Mb + r];
         }
+        if (st.jn >= 0) cn = cf[(long long)min(st.j, st.jn) * Mb + r];
       }
       // one lane per warp polls the accumulator barrier; the warp follows it
       int ok = 1;
@@ -368,22 +409,46 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1)
       }
       umma::tmem_wait_ld();
       const bool more = q + 1 < nst;
-      float2 xo[H];
+      float2 xo[H], vv[H];
 #pragma unroll
       for (int h = 0; h < H; ++h) {
         const float p_re = d[0][h] + d[1][h], p_im = d[0][H + h] + d[1][H + h];
         const float q_re = d[2][h] + d[3][h], q_im = d[2][H + h] + d[3][H + h];
         const float2 acc = make_float2(p_re - q_im, p_im + q_re);
-        float2 v;
-        if (fwd) {
-          xo[h] = acc;
-          v = (j + 1 < Ml) ? csub(pre[h], cmul(cn, acc)) : cmul(cn, acc);
+        if (st.kind == 2) {
+          xo[h] = csub(pre[h], acc);            // x_j = y_j - S_j^{-1} C x_next
+          vv[h] = cmul(cn, xo[h]);
+        } else if (st.kind == 1) {
+          xo[h] = acc;                          // middle block: x_m
+          vv[h] = cmul(cn, acc);
         } else {
-          xo[h] = csub(pre[h], acc);
-          v = cmul(cn, xo[h]);
+          xo[h] = acc;                          // forward: y_j (or z_j)
+          vv[h] = exch ? cmul(cn, acc) : csub(pre[h], cmul(cn, acc));
         }
-        if (!row) v = make_float2(0.f, 0.f);
-        if (more && krow) put_b<KIND, PC>(sB, a.LB, r, grp * 2 * H + h, grp * 2 * H + H + h, v);
+        if (!row) vv[h] = make_float2(0.f, 0.f);
+      }
+      if (exch) {
+        // the coupling term C y of this half goes to the peer; the peer's comes back
+        const uint32_t peer = (uint32_t)(role ^ 1);
+        if (row) {
+#pragma unroll
+          for (int h = 0; h < H; ++h)
+            st_cluster_f2(cluster_map(xch + r * PC + grp * H + h, peer), vv[h]);
+        }
+        // every thread releases its own remote writes and acquires the peer's
+        mbar_arrive_remote(cluster_map(xbar, peer));
+        const int okx = __all_sync(0xffffffffu, mbar_wait_cluster(xbar, 0) ? 1 : 0);
+        if (!okx) { if (lane == 0) fail(17); break; }
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+          const float2 other = row ? xch[r * PC + grp * H + h] : make_float2(0.f, 0.f);
+          vv[h] = row ? csub(csub(pre[h], vv[h]), other) : make_float2(0.f, 0.f);
+        }
+      }
+      if (more && krow) {
+#pragma unroll
+        for (int h = 0; h < H; ++h)
+          put_b<KIND, PC>(sB, a.LB, r, grp * 2 * H + h, grp * 2 * H + H + h, vv[h]);
       }
       if (more) {
         fence_proxy_async();
@@ -391,10 +456,11 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1)
         __syncwarp();
         if (lane == 0) mbar_arrive(bready);
       }
-      // x_j leaves for global memory while the next stage's MMAs run
+      // x_j leaves for global memory while the next stage's MMAs run (the middle block once)
+      const bool store = !(TW && st.kind == 1 && role == 1);
 #pragma unroll
       for (int h = 0; h < H; ++h)
-        if (row && xs[h]) xs[h][(long long)j * Mb + r] = xo[h];
+        if (store && row && xs[h]) xs[h][(long long)st.j * Mb + r] = xo[h];
     }
   }
   umma::fence_before_sync();
@@ -403,44 +469,64 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1)
     umma::fence_after_sync();
     umma::tmem_dealloc(tmem, NALLOC);
   }
+  if (TW) cluster_sync_all();   // no CTA leaves while its peer may still touch its memory
 }
 
-template <int PC, int KIND>
+template <int PC, int KIND, bool TW>
 static cudaError_t tc_launch(cudaStream_t st, const Geom &g, const TcShape &t, int npanels,
                              const Panel *panels, const Col *cols, const unsigned char *tiles,
-                             const float2 *cpl, float2 *work, int *err) {
+                             const float2 *cpl, float2 *work, int *err, int m) {
   constexpr int NG = 2;
   static bool done[64] = {false};
-  cudaError_t e = smem_limit_once(k_subst_tc<PC, KIND, NG>, done);
+  cudaError_t e = smem_limit_once(k_subst_tc<PC, KIND, NG, TW>, done);
   if (e != cudaSuccess) return e;
   TcArgs a{t.Mp, t.Kp, t.ks, t.KS, t.nch, t.LB, t.tile_bytes};
-  k_subst_tc<PC, KIND, NG><<<npanels, 32 * (4 * NG + 2), t.smem, st>>>(g, a, panels, cols, tiles,
-                                                                      cpl, work, err);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(TW ? 2 * npanels : npanels));
+  cfg.blockDim = dim3(32 * (4 * NG + 2));
+  cfg.dynamicSmemBytes = t.smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = TW ? 2 : 1;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = TW ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k_subst_tc<PC, KIND, NG, TW>, g, a, panels, cols, tiles, cpl,
+                            work, err, TW ? m : g.Ml - 1);
 }
 
-cudaError_t launch_subst_tc(cudaStream_t st, const Geom &g, int kind, int npanels,
-                            const Panel *panels, const Col *cols, const unsigned char *tiles,
-                            const float2 *cpl, float2 *work, int pc, int *err) {
-  if (npanels <= 0) return cudaSuccess;
-  TcShape t;
-  if (!tc_shape(g, kind, pc, &t)) return cudaErrorInvalidValue;
-  if (kind == 0) {
-    switch (pc) {
-      case 8: return tc_launch<8, 0>(st, g, t, npanels, panels, cols, tiles, cpl, work, err);
-      case 16: return tc_launch<16, 0>(st, g, t, npanels, panels, cols, tiles, cpl, work, err);
-      case 32: return tc_launch<32, 0>(st, g, t, npanels, panels, cols, tiles, cpl, work, err);
-    }
-  } else {
-    switch (pc) {
-      case 8: return tc_launch<8, 1>(st, g, t, npanels, panels, cols, tiles, cpl, work, err);
-      case 16: return tc_launch<16, 1>(st, g, t, npanels, panels, cols, tiles, cpl, work, err);
-      case 32: return tc_launch<32, 1>(st, g, t, npanels, panels, cols, tiles, cpl, work, err);
-    }
+template <int KIND, bool TW>
+static cudaError_t tc_dispatch(cudaStream_t st, const Geom &g, const TcShape &t, int npanels,
+                               const Panel *panels, const Col *cols, const unsigned char *tiles,
+                               const float2 *cpl, float2 *work, int pc, int *err, int m) {
+  switch (pc) {
+    case 8: return tc_launch<8, KIND, TW>(st, g, t, npanels, panels, cols, tiles, cpl, work, err, m);
+    case 16: return tc_launch<16, KIND, TW>(st, g, t, npanels, panels, cols, tiles, cpl, work, err, m);
+    case 32: return tc_launch<32, KIND, TW>(st, g, t, npanels, panels, cols, tiles, cpl, work, err, m);
   }
   return cudaErrorInvalidValue;
 }
 
-bool subst_tc_ok(const Geom &g, int kind, int pc) { return tc_shape(g, kind, pc, nullptr); }
+cudaError_t launch_subst_tc(cudaStream_t st, const Geom &g, int kind, int npanels,
+                            const Panel *panels, const Col *cols, const unsigned char *tiles,
+                            const float2 *cpl, float2 *work, int pc, int *err, int m) {
+  if (npanels <= 0) return cudaSuccess;
+  const bool tw = m > 0;
+  TcShape t;
+  if (!tc_shape(g, kind, pc, &t, tw)) return cudaErrorInvalidValue;
+  if (kind == 0)
+    return tw ? tc_dispatch<0, true>(st, g, t, npanels, panels, cols, tiles, cpl, work, pc, err, m)
+              : tc_dispatch<0, false>(st, g, t, npanels, panels, cols, tiles, cpl, work, pc, err, m);
+  return tw ? tc_dispatch<1, true>(st, g, t, npanels, panels, cols, tiles, cpl, work, pc, err, m)
+            : tc_dispatch<1, false>(st, g, t, npanels, panels, cols, tiles, cpl, work, pc, err, m);
+}
+
+bool subst_tc_ok(const Geom &g, int kind, int pc, bool twisted) {
+  return tc_shape(g, kind, pc, nullptr, twisted);
+}
+
+int tc_middle_block(const Geom &g) { return g.Ml >= 4 ? (g.Ml - 1) / 2 : 0; }
 
 }  // namespace dds

@@ -26,7 +26,7 @@ EXPORTS = ["dds_setup", "dds_sweep", "dds_solve", "dds_apply", "dds_local_solve"
            "dds_set_stream", "dds_get_info", "dds_kernel_launches", "dds_last_error",
            "dds_destroy", "dds_profile", "dds_profile_read", "dds_local_solve_noalloc",
            "dds_server_create", "dds_server_submit", "dds_server_step", "dds_server_poll",
-           "dds_server_destroy"]
+           "dds_server_destroy", "dds_work_per_ddm"]
 KERNEL_KINDS = {"assemble": 0, "subst": 1, "extract": 2, "trace_step": 3, "krylov": 4,
                 "other": 5}
 
@@ -78,6 +78,9 @@ def load(path: str = LIB_PATH):
     lib.dds_last_error.argtypes = [vp]
     lib.dds_last_error.restype = ctypes.c_char_p
     lib.dds_destroy.argtypes = [vp]
+    lib.dds_work_per_ddm.argtypes = [vp, ctypes.c_int, ctypes.c_int,
+                                     ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double)]
     lib.dds_destroy.restype = None
     lib.dds_server_create.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                       ctypes.c_int, ctypes.POINTER(vp)]
@@ -243,6 +246,14 @@ class Context:
 
     def launches(self):
         return int(self._lib.dds_kernel_launches(self._h))
+
+    def work_per_ddm(self, nrhs, rounds=1):
+        """(substitution flops, trace-map flops) of one DDM application (dds_work_per_ddm)."""
+        a = ctypes.c_double(0.0)
+        b = ctypes.c_double(0.0)
+        self._check(self._lib.dds_work_per_ddm(self._h, int(nrhs), int(rounds), ctypes.byref(a),
+                                               ctypes.byref(b)))
+        return a.value, b.value
 
     def profile(self, enable=True):
         """Enable/disable per-launch CUDA-event timing (dds_profile)."""
