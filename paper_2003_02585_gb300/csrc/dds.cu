@@ -60,7 +60,7 @@ struct CallPlan {            // all launch lists for one nrhs
   std::vector<StepPlan> tsteps;  // [dir][step] for the trace plan (trace-step panels)
   StepPlan all;                  // every (sub, rhs) column (trace plan phases, local solves)
   DBuf cols, panels, tpanels;
-  struct TraceTable { int n = -1; DBuf buf; };
+  struct TraceTable { int n = -1, nlev = 0; DBuf buf, tpan; };
   std::map<int, TraceTable> trace_steps;   // rounds -> step table of the cooperative launch
 };
 
@@ -434,6 +434,74 @@ dds_status check_errflag(dds_ctx *ctx) {
 // ------------------------------------------------------------------------------------------
 // one DDM application (Algorithm 2.1 / 4.1): b (J-scaled, device, nrhs fields) -> u (device)
 // ------------------------------------------------------------------------------------------
+// Dataflow schedule of the trace solves of one DDM application (trace plan).  The trace solve
+// (sweep l, subdomain X) reads only slot l of X, which receives the traces of every (l', Y) with
+// route[l'][d] = l and X the neighbour of Y across d.  Its level is one more than the deepest of
+// those producers (0 without any), computed in sweep and step order.  Per level and sweep one
+// entry holds that sweep's subdomains of the level, as panels of 8 (subdomain, RHS) columns of
+// one factor.  Returns the number of levels.
+int build_trace_schedule(dds_ctx *ctx, int nrhs, int rounds, std::vector<TraceStep> &ts,
+                         std::vector<TracePanel> &tp) {
+  const Geom &g = ctx->g;
+  const int L = ctx->ndirs * rounds, ns = g.nsub;
+  const std::vector<int> route = build_route(g.dim, rounds);
+  std::vector<std::vector<int>> prod((size_t)L * ns);
+  for (int lq = 0; lq < L; ++lq)
+    for (int y = 0; y < ns; ++y)
+      for (int d = 0; d < g.nsides; ++d) {
+        const int lp = route[lq * 6 + d], x = sub_neighbour(g, y, d);
+        if (lp >= 0 && x >= 0) prod[(size_t)lp * ns + x].push_back(lq * ns + y);
+      }
+  std::vector<int> depth((size_t)L * ns, -1);
+  int nlev = 0;
+  for (int l = 0; l < L; ++l) {
+    const int dir = l % ctx->ndirs;
+    for (int s = 0; s < ctx->nsteps; ++s)
+      for (int x : ctx->step_subs[dir][s]) {
+        int dmax = -1;
+        for (int q : prod[(size_t)l * ns + x]) dmax = std::max(dmax, depth[q]);
+        depth[(size_t)l * ns + x] = dmax + 1;
+        nlev = std::max(nlev, dmax + 2);
+      }
+  }
+  for (int v = 0; v < nlev; ++v) {
+    int level_items = 0;
+    const size_t first = ts.size();
+    for (int l = 0; l < L; ++l) {
+      std::vector<int> subs;
+      for (int x = 0; x < ns; ++x)
+        if (depth[(size_t)l * ns + x] == v) subs.push_back(x);
+      if (subs.empty()) continue;
+      std::stable_sort(subs.begin(), subs.end(),
+                       [&](int a, int b) { return ctx->fac_of_sub[a] < ctx->fac_of_sub[b]; });
+      const int pan_off = (int)tp.size();
+      TracePanel cur{};
+      cur.factor = -1;
+      for (int x : subs)
+        for (int r = 0; r < nrhs; ++r) {
+          if (cur.ncol == 8 || (cur.ncol > 0 && cur.factor != ctx->fac_of_sub[x])) {
+            tp.push_back(cur);
+            cur = TracePanel{};
+          }
+          cur.factor = ctx->fac_of_sub[x];
+          cur.sub[cur.ncol] = x;
+          cur.rhs[cur.ncol] = r;
+          ++cur.ncol;
+        }
+      if (cur.ncol > 0) tp.push_back(cur);
+      const int npan = (int)tp.size() - pan_off;
+      int nout = 0, nseg = 0;
+      const int ni = trace_step_items(g, npan, ctx->in_mask[l], ctx->out_mask[l], &nout, &nseg);
+      if (ni == 0) continue;   // nothing routed out or nothing can come in
+      ts.push_back(TraceStep{l, pan_off, npan, ctx->in_mask[l], ctx->out_mask[l], nout, nseg, ni,
+                             v, level_items, 0});
+      level_items += ni;
+    }
+    for (size_t e = first; e < ts.size(); ++e) ts[e].level_items = level_items;
+  }
+  return nlev;
+}
+
 // workspaces of one DDM application; *grown is set if any buffer moved (cached graphs go stale)
 template <typename R>
 dds_status prepare_ddm(dds_ctx *ctx, int nrhs, int rounds, bool *grown) {
@@ -452,26 +520,17 @@ dds_status prepare_ddm(dds_ctx *ctx, int nrhs, int rounds, bool *grown) {
     for (auto &sp : cp->steps) work_cols = std::max<long long>(work_cols, sp.ncols);
   }
   if (trace_plan) {
-    // step table of the cooperative trace-sweep launch (uploaded outside any stream capture)
+    // schedule of the cooperative trace launch (uploaded outside any stream capture)
     auto &tt = cp->trace_steps[rounds];
     if (tt.n < 0) {
       std::vector<TraceStep> ts;
-      for (int l = 0; l < L; ++l) {
-        const int dir = l % ctx->ndirs;
-        for (int s = 0; s < ctx->nsteps; ++s) {
-          const StepPlan &sp = cp->tsteps[dir * ctx->nsteps + s];
-          if (sp.ncols == 0) continue;
-          int nout = 0, nseg = 0;
-          const int ni = trace_step_items(g, sp.npanels, ctx->in_mask[l], ctx->out_mask[l], &nout, &nseg);
-          if (ni == 0) continue;   // nothing routed out or nothing can come in
-          ts.push_back(TraceStep{l, sp.pan_off, sp.npanels, ctx->in_mask[l], ctx->out_mask[l],
-                                 nout, nseg, ni});
-        }
-      }
+      std::vector<TracePanel> tp;
+      tt.nlev = build_trace_schedule(ctx, nrhs, rounds, ts, tp);
       CK(upload(tt.buf, ts, ctx->stream));
+      CK(upload(tt.tpan, tp, ctx->stream));
       tt.n = (int)ts.size();
       void *gb0 = ctx->gbar.p;
-      CK(ctx->gbar.ensure(trace_counter_bytes(tt.n)));
+      CK(ctx->gbar.ensure(trace_counter_bytes(std::max(tt.nlev, 1))));
       if (gb0 != ctx->gbar.p) *grown = true;
     }
   }
@@ -533,7 +592,8 @@ dds_status run_ddm(dds_ctx *ctx, const double2 *b, int nrhs, double2 *u, int rou
       return DDS_EINVAL;
     }
     const CallPlan::TraceTable &tt = tti->second;
-    LAUNCHK(DDS_K_TRACE_STEP, launch_trace_sweeps<R>(st, g, tt.buf.as<TraceStep>(), tt.n, cp->tpanels.as<TracePanel>(), gmap,
+    LAUNCHK(DDS_K_TRACE_STEP, launch_trace_sweeps<R>(st, g, tt.buf.as<TraceStep>(), tt.n, tt.nlev,
+                                                     tt.tpan.as<TracePanel>(), gmap,
                                                      gtr, rawf, route, nrhs, ctx->gbar.as<unsigned>(),
                                                      ctx->errflag.as<int>()));
     // own nodes: u = A_R^{-1}(b_own + potentials of all traces received in every sweep)

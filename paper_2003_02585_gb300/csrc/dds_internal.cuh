@@ -211,17 +211,22 @@ struct TracePanel {
   int sub[8], rhs[8];
 };
 
-// one sweep step of the trace plan: sweep l, its panels, and its work items
+// One entry of the trace schedule: the trace solves of sweep l in one dataflow level, as panels
+// of (subdomain, RHS) columns, and their work items.  The items of all entries of a level are
+// dealt round-robin over the CTAs as one list (off = items of the level's earlier entries,
+// level_items = the level's total).
 struct TraceStep {
   int l, pan_off, npanels, in_mask, out_mask, nout, nseg, nitems;
+  int level, off, level_items;
 };
 int trace_step_items(const Geom &g, int npanels, int in_mask, int out_mask, int *nout, int *nseg);
-size_t trace_counter_bytes(int nsteps);   // step counters of one launch (gbar)
+size_t trace_counter_bytes(int nlevels);  // level counters of one launch (gbar)
 
-// every trace step of one DDM application in one cooperative launch (gbar: the step counters,
-// zeroed by the launch)
+// every trace solve of one DDM application in one cooperative launch (gbar: the level
+// counters, zeroed by the launch)
 template <typename R>
 cudaError_t launch_trace_sweeps(cudaStream_t st, const Geom &g, const TraceStep *steps, int nsteps,
+                                int nlevels,
                                 const TracePanel *panels,
                                 const typename Cx<R>::T *gmap, typename Cx<R>::T *g_traces,
                                 const typename Cx<R>::T *rawf, const int *route, int nrhs,

@@ -499,12 +499,14 @@ __device__ inline bool trace_decode(const Geom &g, const TraceStep &sd, int tile
   return n > 0;
 }
 
-// Every trace step of every sweep of one DDM application in one cooperative launch: the CTAs
-// share each step's items round-robin; a CTA starts its items of step s + 1 once every CTA is
-// done with step s (step counters above).  The step table sits in shared memory; the
-// descriptors of a CTA's first item of step s + 1 are loaded into registers at the top of step s
-// and staged, with that item's map-slice copy, before the wait -- none of it depends on a trace.
-constexpr int kMaxSmemSteps = 512;
+// Every trace solve of one DDM application in one cooperative launch.  The schedule is a list of
+// dataflow levels: a trace solve (sweep l, subdomain X) sits one level below the deepest solve
+// whose traces are routed into its slot l, so every level only reads slots that earlier levels
+// completed.  The items of a level are dealt round-robin over the CTAs; a CTA with items in
+// level v first waits until every CTA is done with level v - 1 (counters above).  The step
+// table sits in shared memory; the descriptors and map slice of a CTA's first item of the next
+// level depend on no trace and are staged before that wait.
+constexpr int kMaxSmemSteps = 384;
 
 template <typename R>
 __global__ void __launch_bounds__(256) k_trace_sweeps(Geom g, const TraceStep *__restrict__ steps,
@@ -522,7 +524,7 @@ __global__ void __launch_bounds__(256) k_trace_sweeps(Geom g, const TraceStep *_
   C *Gs = reinterpret_cast<C *>(smem_raw);                   // map slice [k][64]
   C *vin = Gs + kTraceSeg * kTraceRows;                      // inputs [col][k]
   uint64_t *bar = reinterpret_cast<uint64_t *>(vin + PC * kTraceSeg);
-  TraceStep *st_s = reinterpret_cast<TraceStep *>(bar + 2);  // step table (nsteps <= 512)
+  TraceStep *st_s = reinterpret_cast<TraceStep *>(bar + 2);  // schedule (nsteps <= kMaxSmemSteps)
   __shared__ TraceItemSmem it;
   const bool smem_steps = nsteps <= kMaxSmemSteps;
   for (int i = threadIdx.x; smem_steps && i < nsteps; i += blockDim.x) st_s[i] = steps[i];
@@ -531,72 +533,75 @@ __global__ void __launch_bounds__(256) k_trace_sweeps(Geom g, const TraceStep *_
     mbar_init_fence();
   }
   __syncthreads();
-  auto step_at = [&](int s) { return smem_steps ? st_s[s] : steps[s]; };
+  auto step_at = [&](int e) { return smem_steps ? st_s[e] : steps[e]; };
   const long long slot_stride = (long long)nrhs * g.nsub * g.T;
+  const int G = (int)gridDim.x, b = (int)blockIdx.x;
   uint32_t phase = 0;
-  // descriptors of one item, loaded by threads 0..7 (column c = thread) into registers
-  struct Pre { int factor, ncol, sub, rhs; };
-  auto load_pre = [&](const TraceStep &sd, int panel) {
-    Pre q{0, 0, 0, 0};
-    if (threadIdx.x < PC) {
-      const TracePanel *tp = panels + sd.pan_off + panel;
-      q.factor = tp->factor;
-      q.ncol = tp->ncol;
-      q.sub = tp->sub[threadIdx.x];
-      q.rhs = tp->rhs[threadIdx.x];
-    }
-    return q;
-  };
   // stage the descriptors and issue the map-slice copy (all threads call; ends with a barrier)
-  auto prep = [&](const Pre &q, int l, int dout, int tile, int k0, int n) {
+  auto prep = [&](const TraceStep &sd, int panel, int dout, int tile, int k0, int n) {
+    const TracePanel *tp = panels + sd.pan_off + panel;
     if (threadIdx.x == 0) {
       const uint32_t bytes = (uint32_t)(n * kTraceRows * sizeof(C));
       fence_proxy_async();   // earlier generic reads of Gs before the async write
       mbar_arrive_expect_tx(bar, bytes);
-      bulk_g2s(Gs, gmap + gmap_index(g, q.factor, dout, tile, k0, 0), bytes, bar);
-      it.ncol = q.ncol;
+      bulk_g2s(Gs, gmap + gmap_index(g, tp->factor, dout, tile, k0, 0), bytes, bar);
+      it.ncol = tp->ncol;
     }
     if (threadIdx.x < PC) {
       const int c = threadIdx.x;
-      it.sub[c] = q.sub;
-      it.rhs[c] = q.rhs;
-      it.cbase[c] = c < q.ncol ? l * slot_stride + ((long long)q.rhs * g.nsub + q.sub) * g.T : -1;
+      const int sub = tp->sub[c], rhs = tp->rhs[c];
+      it.sub[c] = sub;
+      it.rhs[c] = rhs;
+      it.cbase[c] = c < tp->ncol ? sd.l * slot_stride + ((long long)rhs * g.nsub + sub) * g.T : -1;
     }
     __syncthreads();
   };
-  int prefetched = -1;   // item of the current step whose descriptors and slice are staged
-  for (int s = 0; s < nsteps; ++s) {
-    const TraceStep sd = step_at(s);
-    // the next step's first item: its descriptors travel while this step runs
-    TraceStep sn{};
-    bool have_next = false;
-    int nd = 0, nt = 0, npan = 0, nk0 = 0, nn = 0, nseg = 0;
-    Pre qn{0, 0, 0, 0};
-    if (s + 1 < nsteps) {
-      sn = step_at(s + 1);
-      have_next = (int)blockIdx.x < sn.nitems &&
-                  trace_decode(g, sn, tiles_per_side, blockIdx.x, nd, nt, npan, nk0, nn, nseg);
-      if (have_next) qn = load_pre(sn, npan);
+  // the entry and item of this CTA's first work in the level starting at entry e0 (or -1)
+  auto first_in_level = [&](int e0, int &item) {
+    const TraceStep s0 = step_at(e0);
+    if (b >= s0.level_items) return -1;
+    for (int e = e0; e < nsteps; ++e) {
+      const TraceStep se = step_at(e);
+      if (se.level != s0.level) break;
+      if (b >= se.off && b < se.off + se.nitems) { item = b - se.off; return e; }
     }
-    if (s > 0 && (int)blockIdx.x < sd.nitems) step_wait(cnt, s - 1, err);
-    for (int item = blockIdx.x; item < sd.nitems; item += gridDim.x) {
+    return -1;
+  };
+  int pre_e = -1, pre_item = -1;   // staged item (descriptors + map slice in flight)
+  int level = -1;
+  for (int e = 0; e < nsteps; ++e) {
+    const TraceStep sd = step_at(e);
+    if (sd.level != level) {
+      if (level >= 0) {
+        step_arrive(cnt, level);
+        // stage this CTA's first item of the new level, then wait for the previous level
+        int item = -1;
+        const int ef = first_in_level(e, item);
+        if (ef >= 0) {
+          const TraceStep sf = step_at(ef);
+          int dout, tile, panel, k0, n, seg;
+          if (trace_decode(g, sf, tiles_per_side, item, dout, tile, panel, k0, n, seg)) {
+            prep(sf, panel, dout, tile, k0, n);
+            pre_e = ef;
+            pre_item = item;
+          }
+        }
+        if (b < sd.level_items) step_wait(cnt, level, err);
+      }
+      level = sd.level;
+    }
+    // this CTA's items of entry e: global level index off + item = b (mod G)
+    int item = ((b - sd.off) % G + G) % G;
+    for (; item < sd.nitems; item += G) {
       int dout, tile, panel, k0, n, seg;
       if (!trace_decode(g, sd, tiles_per_side, item, dout, tile, panel, k0, n, seg)) continue;
-      if (item != prefetched) prep(load_pre(sd, panel), sd.l, dout, tile, k0, n);
+      if (!(e == pre_e && item == pre_item)) prep(sd, panel, dout, tile, k0, n);
       trace_item<R>(g, gtr, sd.l == 0 ? rawf : nullptr, route, sd.l, nrhs, dout, tile, k0, n,
                     seg == 0, Gs, vin, bar, phase, it, err);
       phase ^= 1u;
     }
-    prefetched = -1;
-    if (s + 1 < nsteps) {
-      step_arrive(cnt, s);
-      if (have_next) {
-        prep(qn, sn.l, nd, nt, nk0, nn);
-        prefetched = blockIdx.x;
-      }
-    }
   }
-  // a prefetch is staged only for an item that the next step consumes, so none is in flight
+  // a staged item is always consumed by its level, so no copy is in flight here
 }
 
 // ------------------------------------------------------------------------------------------
@@ -733,7 +738,7 @@ cudaError_t launch_extract(cudaStream_t st, const Geom &g, int ncols, const Col 
 
 template <typename R>
 cudaError_t launch_trace_sweeps(cudaStream_t st, const Geom &g, const TraceStep *steps, int nsteps,
-                                const TracePanel *panels,
+                                int nlevels, const TracePanel *panels,
                                 const typename Cx<R>::T *gmap, typename Cx<R>::T *gtr,
                                 const typename Cx<R>::T *rawf, const int *route, int nrhs,
                                 unsigned *gbar, int *err) {
@@ -751,7 +756,7 @@ cudaError_t launch_trace_sweeps(cudaStream_t st, const Geom &g, const TraceStep 
     return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   cudaLaunchConfig_t cfg = {};
-  e = cudaMemsetAsync(gbar, 0, (size_t)nsteps * kStepCounters * sizeof(unsigned), st);
+  e = cudaMemsetAsync(gbar, 0, trace_counter_bytes(nlevels), st);
   if (e != cudaSuccess) return e;
   cfg.gridDim = dim3((unsigned)(nsm * std::min(per_sm, 2)));
   cfg.blockDim = dim3(256);
@@ -766,7 +771,7 @@ cudaError_t launch_trace_sweeps(cudaStream_t st, const Geom &g, const TraceStep 
                             rawf, route, nrhs, trace_max_tiles(g), gbar, err);
 }
 
-size_t trace_counter_bytes(int nsteps) { return (size_t)nsteps * kStepCounters * sizeof(unsigned); }
+size_t trace_counter_bytes(int nlevels) { return (size_t)nlevels * kStepCounters * sizeof(unsigned); }
 
 int trace_step_items(const Geom &g, int npanels, int in_mask, int out_mask, int *nout, int *nseg) {
   int no = 0;
@@ -831,7 +836,7 @@ cudaError_t launch_copy_local_back(cudaStream_t st, long long n, const typename 
                                          const Cx<R>::T *, double2 *, int, Cx<R>::T *,         \
                                          Cx<R>::T *, const int *, int, int);                    \
   template cudaError_t launch_trace_sweeps<R>(cudaStream_t, const Geom &, const TraceStep *,   \
-                                              int, const TracePanel *,                          \
+                                              int, int, const TracePanel *,                     \
                                               const Cx<R>::T *, Cx<R>::T *, const Cx<R>::T *,  \
                                               const int *, int, unsigned *, int *);             \
   template cudaError_t launch_unit_traces<R>(cudaStream_t, const Geom &, const Tables &, int,  \
