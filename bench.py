@@ -224,6 +224,8 @@ def time_variant(args, wl, R, f_dev, stream, flush, precision, u64):
 
     ctx = dds.Context(wl.n, wl.h, wl.omega, wl.c, wl.parts, wl.pml_cells, wl.pml_strength,
                       precision=precision, plan=args.plan)
+    if not args.no_autotune:
+        ctx.autotune(R, wl.rounds)
     its = []
     for _ in range(args.warmup):
         ctx.solve(f_dev, tol=args.tol, maxit=args.maxit, rounds=wl.rounds)
@@ -269,6 +271,8 @@ def run_gpu(args):
 
     ctx = dds.Context(wl.n, wl.h, wl.omega, wl.c, wl.parts, wl.pml_cells, wl.pml_strength,
                       precision=args.precision, plan=args.plan)
+    # launch shapes picked by measurement on this workload (set-up work, outside the timing)
+    tuned = ctx.autotune(R, wl.rounds) if not args.no_autotune else None
     info = ctx.info()
     f_host = ctx.extend(wl.f)
     f_dev = torch.from_numpy(f_host).to(dev)
@@ -382,6 +386,7 @@ def run_gpu(args):
         "cpu_baseline": cpu,
         "clocks": clocks,
         "variants": variants,
+        "autotune": tuned,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -499,6 +504,8 @@ def main():
     ap.add_argument("--plan", default="auto", choices=["auto", "direct", "trace"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_bf16", "mixed_fp32"],
                     help="single-precision sweep variant of the timed solver")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default launch shapes instead of timing the candidates")
     ap.add_argument("--variants", default="mixed_bf16,mixed_fp32",
                     help="other sweep variants timed the same way and reported beside the line")
     ap.add_argument("--rounds", type=int, default=None,

@@ -179,6 +179,20 @@ dds_status dds_get_info(const dds_ctx *ctx, dds_info_t *info);
 /* dds_kernel_launches -- number of kernels this context has launched so far. */
 long long dds_kernel_launches(const dds_ctx *ctx);
 
+/* dds_autotune -- time the tunable launch shapes of one DDM application on this context's
+ * geometry for nrhs right-hand sides and `rounds` rounds, and keep the fastest:
+ *   the tensor-core substitution panel width (8, 16 or 32 columns per CTA or CTA pair;
+ *   mixed modes with tensor-core substitutions), and the CTAs per SM of the cooperative trace
+ *   launch (1 or 2; trace plan).
+ * Each candidate is captured once and then timed over three DDM applications with CUDA events
+ * on the context's stream, with synthetic (zero) right-hand sides in scratch the call allocates
+ * and frees.  table (row-major [n][3]: panel width (0 = automatic), CTAs per SM, ms per DDM
+ * application) receives at most max_entries rows; *n_entries is the number of candidates timed;
+ * best[0], best[1] the chosen panel width and CTAs per SM.  Cached plans and graphs are dropped.
+ * Not part of the paper: it picks block and panel tile shapes by measurement. */
+dds_status dds_autotune(dds_ctx *ctx, int nrhs, int rounds, int max_entries, int *n_entries,
+                        double *table, int *best);
+
 /* dds_work_per_ddm -- algorithmic floating-point work of one DDM application (Algorithm 2.1 /
  * 4.1, `rounds` rounds of 2^n sweeps) for nrhs right-hand sides, computed on the host:
  *   *subst_flops  block forward + back substitutions, 16 Ml Mb^2 real flops per local solve

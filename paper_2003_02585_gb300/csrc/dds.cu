@@ -74,6 +74,8 @@ struct dds_ctx {
   bool single = false;   // sweeps in complex single precision (every precision but DDS_FP64)
   int split = -1;        // tensor-core substitution pieces: 0 = TF32, 1 = BF16, -1 = none
   int tc_m = 0;          // middle block of the two-sided tensor-core chain (0: one-sided)
+  int tune_pc = 0;       // tensor-core panel width chosen by dds_autotune (0: automatic)
+  int trace_per_sm = 2;  // CTAs per SM of the cooperative trace launch
   double h = 0, omega = 0, S = 0;
   int P = 0, power = 2, H = 0;
   cudaStream_t stream = nullptr;
@@ -347,7 +349,11 @@ CallPlan *get_plan(dds_ctx *ctx, int nrhs) {
       sp.pc = pc_cap;
     } else {
       int spc = 0;
-      if (ctx->single && ctx->split >= 0) spc = pick_pc_tc(ctx->g, ctx->split, ctx->tc_m > 0, sp.ncols);
+      if (ctx->single && ctx->split >= 0) {
+        spc = pick_pc_tc(ctx->g, ctx->split, ctx->tc_m > 0, sp.ncols);
+        if (ctx->tune_pc > 0 && subst_tc_ok(ctx->g, ctx->split, ctx->tune_pc, ctx->tc_m > 0))
+          spc = ctx->tune_pc;
+      }
       if (ctx->single && spc == 0) spc = pick_pc_stream(ctx->g, sp.ncols);
       sp.pc = spc > 0 ? spc : pick_pc(sp.ncols, pc_cap);
     }
@@ -595,7 +601,7 @@ dds_status run_ddm(dds_ctx *ctx, const double2 *b, int nrhs, double2 *u, int rou
     LAUNCHK(DDS_K_TRACE_STEP, launch_trace_sweeps<R>(st, g, tt.buf.as<TraceStep>(), tt.n, tt.nlev,
                                                      tt.tpan.as<TracePanel>(), gmap,
                                                      gtr, rawf, route, nrhs, ctx->gbar.as<unsigned>(),
-                                                     ctx->errflag.as<int>()));
+                                                     ctx->errflag.as<int>(), ctx->trace_per_sm));
     // own nodes: u = A_R^{-1}(b_own + potentials of all traces received in every sweep)
     LAUNCHK(DDS_K_ASSEMBLE, launch_assemble<R>(st, g, ctx->tb, all.ncols, cols + all.col_off, work, b, nullptr, 1,
                               gtr, (long long)g.nsub * g.T, g.T, L, slot));
@@ -1396,6 +1402,78 @@ dds_status dds_get_info(const dds_ctx *ctx, dds_info_t *info) {
 }
 
 long long dds_kernel_launches(const dds_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+dds_status dds_autotune(dds_ctx *ctx, int nrhs, int rounds, int max_entries, int *n_entries,
+                        double *table, int *best) {
+  if (!ctx || nrhs <= 0 || rounds < 1 || !n_entries || !best || (max_entries > 0 && !table))
+    return DDS_EINVAL;
+  Busy busy(ctx);
+  if (!busy.ok) return DDS_EBUSY;
+  ctx->err.clear();
+  const Geom &g = ctx->g;
+  std::vector<int> pcs = {0};
+  if (ctx->single && ctx->split >= 0) {
+    pcs.clear();
+    for (int pc : {8, 16, 32})
+      if (subst_tc_ok(g, ctx->split, pc, ctx->tc_m > 0)) pcs.push_back(pc);
+  }
+  std::vector<int> pers = {ctx->trace_per_sm};
+  if (ctx->plan == DDS_PLAN_TRACE) pers = {1, 2};
+  // synthetic right-hand sides: the kernels do the same work for any values
+  DBuf bb, uu;
+  const size_t bytes = (size_t)nrhs * g.Nglob * sizeof(double2);
+  CK(bb.ensure(bytes));
+  CK(uu.ensure(bytes));
+  CK(cudaMemsetAsync(bb.p, 0, bytes, ctx->stream));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const bool prof = ctx->profiling;
+  ctx->profiling = false;
+  double best_ms = 1e300;
+  int best_pc = ctx->tune_pc, best_per = ctx->trace_per_sm;
+  int n = 0;
+  dds_status r = DDS_OK;
+  for (int pc : pcs)
+    for (int per : pers) {
+      ctx->tune_pc = pc;
+      ctx->trace_per_sm = per;
+      ctx->clear_graphs();
+      ctx->plans.clear();
+      r = ddm(ctx, bb.as<double2>(), nrhs, uu.as<double2>(), rounds);   // build + capture
+      if (r != DDS_OK) break;
+      const int reps = 3;
+      cudaEventRecord(e0, ctx->stream);
+      for (int k = 0; k < reps && r == DDS_OK; ++k)
+        r = ddm(ctx, bb.as<double2>(), nrhs, uu.as<double2>(), rounds);
+      cudaEventRecord(e1, ctx->stream);
+      if (r != DDS_OK) break;
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      const double per_app = ms / reps;
+      if (n < max_entries) {
+        table[3 * n + 0] = pc;
+        table[3 * n + 1] = per;
+        table[3 * n + 2] = per_app;
+      }
+      ++n;
+      if (per_app < best_ms) { best_ms = per_app; best_pc = pc; best_per = per; }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->profiling = prof;
+  ctx->tune_pc = best_pc;
+  ctx->trace_per_sm = best_per;
+  ctx->clear_graphs();
+  ctx->plans.clear();
+  if (r != DDS_OK) return r;
+  CK(cudaStreamSynchronize(ctx->stream));
+  *n_entries = n;
+  best[0] = best_pc;
+  best[1] = best_per;
+  return check_errflag(ctx);
+}
 
 dds_status dds_work_per_ddm(dds_ctx *ctx, int nrhs, int rounds, double *subst_flops,
                             double *trace_flops) {

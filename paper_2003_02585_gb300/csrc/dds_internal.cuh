@@ -230,7 +230,7 @@ cudaError_t launch_trace_sweeps(cudaStream_t st, const Geom &g, const TraceStep 
                                 const TracePanel *panels,
                                 const typename Cx<R>::T *gmap, typename Cx<R>::T *g_traces,
                                 const typename Cx<R>::T *rawf, const int *route, int nrhs,
-                                unsigned *gbar, int *err);
+                                unsigned *gbar, int *err, int ctas_per_sm);
 
 template <typename R>
 cudaError_t launch_unit_traces(cudaStream_t st, const Geom &g, const Tables &tb, int k0, int nk,

@@ -741,7 +741,7 @@ cudaError_t launch_trace_sweeps(cudaStream_t st, const Geom &g, const TraceStep 
                                 int nlevels, const TracePanel *panels,
                                 const typename Cx<R>::T *gmap, typename Cx<R>::T *gtr,
                                 const typename Cx<R>::T *rawf, const int *route, int nrhs,
-                                unsigned *gbar, int *err) {
+                                unsigned *gbar, int *err, int ctas_per_sm) {
   if (nsteps <= 0) return cudaSuccess;
   using C = typename Cx<R>::T;
   const size_t smem = trace_step_smem(g, 8, sizeof(C));
@@ -758,7 +758,7 @@ cudaError_t launch_trace_sweeps(cudaStream_t st, const Geom &g, const TraceStep 
   cudaLaunchConfig_t cfg = {};
   e = cudaMemsetAsync(gbar, 0, trace_counter_bytes(nlevels), st);
   if (e != cudaSuccess) return e;
-  cfg.gridDim = dim3((unsigned)(nsm * std::min(per_sm, 2)));
+  cfg.gridDim = dim3((unsigned)(nsm * std::max(1, std::min(per_sm, ctas_per_sm))));
   cfg.blockDim = dim3(256);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
@@ -838,7 +838,7 @@ cudaError_t launch_copy_local_back(cudaStream_t st, long long n, const typename 
   template cudaError_t launch_trace_sweeps<R>(cudaStream_t, const Geom &, const TraceStep *,   \
                                               int, int, const TracePanel *,                     \
                                               const Cx<R>::T *, Cx<R>::T *, const Cx<R>::T *,  \
-                                              const int *, int, unsigned *, int *);             \
+                                              const int *, int, unsigned *, int *, int);        \
   template cudaError_t launch_unit_traces<R>(cudaStream_t, const Geom &, const Tables &, int,  \
                                              int, Cx<R>::T *);                                  \
   template cudaError_t launch_raw_lines<R>(cudaStream_t, const Geom &, int, const Cx<R>::T *,  \

@@ -26,7 +26,7 @@ EXPORTS = ["dds_setup", "dds_sweep", "dds_solve", "dds_apply", "dds_local_solve"
            "dds_set_stream", "dds_get_info", "dds_kernel_launches", "dds_last_error",
            "dds_destroy", "dds_profile", "dds_profile_read", "dds_local_solve_noalloc",
            "dds_server_create", "dds_server_submit", "dds_server_step", "dds_server_poll",
-           "dds_server_destroy", "dds_work_per_ddm"]
+           "dds_server_destroy", "dds_work_per_ddm", "dds_autotune"]
 KERNEL_KINDS = {"assemble": 0, "subst": 1, "extract": 2, "trace_step": 3, "krylov": 4,
                 "other": 5}
 
@@ -78,6 +78,9 @@ def load(path: str = LIB_PATH):
     lib.dds_last_error.argtypes = [vp]
     lib.dds_last_error.restype = ctypes.c_char_p
     lib.dds_destroy.argtypes = [vp]
+    lib.dds_autotune.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                 ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                                 ctypes.POINTER(ctypes.c_int)]
     lib.dds_work_per_ddm.argtypes = [vp, ctypes.c_int, ctypes.c_int,
                                      ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_double)]
@@ -246,6 +249,18 @@ class Context:
 
     def launches(self):
         return int(self._lib.dds_kernel_launches(self._h))
+
+    def autotune(self, nrhs, rounds=1):
+        """Time the tunable launch shapes (dds_autotune) and keep the fastest; returns
+        {"panel_width", "trace_ctas_per_sm", "table": [(width, ctas, ms per DDM application)]}."""
+        n = ctypes.c_int(0)
+        table = (ctypes.c_double * (3 * 16))()
+        best = (ctypes.c_int * 2)()
+        self._check(self._lib.dds_autotune(self._h, int(nrhs), int(rounds), 16, ctypes.byref(n),
+                                           table, best))
+        rows = [(int(table[3 * i]), int(table[3 * i + 1]), float(table[3 * i + 2]))
+                for i in range(min(n.value, 16))]
+        return {"panel_width": int(best[0]), "trace_ctas_per_sm": int(best[1]), "table": rows}
 
     def work_per_ddm(self, nrhs, rounds=1):
         """(substitution flops, trace-map flops) of one DDM application (dds_work_per_ddm)."""

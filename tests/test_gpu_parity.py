@@ -269,3 +269,22 @@ def test_large_block_3d_ddm_and_fgmres():
     u, it, rel = ctxm.solve(_on_dev(ctx.extend(f)), tol=1e-9, maxit=30)
     ug = global_solve(prob, bb)
     assert rel[0] < 1e-9 and _rel(u.cpu().numpy()[0], ug[0]) < 1e-6
+
+
+# ----------------------------------------------------------------------------- autotuner -----
+
+def test_autotune_picks_a_valid_shape_and_keeps_results():
+    """dds_autotune times every candidate launch shape and keeps the fastest; the DDM output
+    after tuning equals the output before it to single-precision rounding."""
+    n = (128, 128)
+    prob, f = _case(n, (8, 8), 4, 2 * np.pi * 5, c=_medium("layer", n),
+                    centres=[(0.2, 0.3), (0.7, 0.6), (0.5, 0.8)])
+    ctx = _ctx(prob, "mixed", "trace")
+    fe = _on_dev(ctx.extend(f))
+    before = ctx.sweep(fe, 2).cpu().numpy()
+    t = ctx.autotune(3, 2)
+    assert t["panel_width"] in (8, 16, 32) and t["trace_ctas_per_sm"] in (1, 2)
+    assert len(t["table"]) >= 2 and all(row[2] > 0 for row in t["table"])
+    after = ctx.sweep(fe, 2).cpu().numpy()
+    for r in range(3):
+        assert _rel(after[r], before[r]) < 1e-5
