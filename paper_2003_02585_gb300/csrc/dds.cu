@@ -88,6 +88,8 @@ struct dds_ctx {
   // device tables
   DBuf sinv64, sinv32, cpl64, cpl32, coef64, coef32, k2glob, gmap64, gmap32, status;
   DBuf tctiles;  // block inverses split into tensor-core pieces (layout of k_subst_tc.cu)
+  DBuf bigtiles, bigB, bigacc;   // blocks wider than 128 nodes: tiles, B pieces, accumulator
+  bool big_tc = false;
   DBuf errflag;  // set by kernels whose bounded waits gave up
   DBuf gbar;     // step counters of the cooperative trace-sweep launch
   DBuf an_glob[3], iah_glob[3];
@@ -349,7 +351,9 @@ CallPlan *get_plan(dds_ctx *ctx, int nrhs) {
       sp.pc = pc_cap;
     } else {
       int spc = 0;
-      if (ctx->single && ctx->split >= 0) {
+      if (ctx->single && ctx->big_tc) {
+        spc = sp.ncols <= 8 ? 8 : (sp.ncols <= 16 ? 16 : 32);
+      } else if (ctx->single && ctx->split >= 0) {
         spc = pick_pc_tc(ctx->g, ctx->split, ctx->tc_m > 0, sp.ncols);
         if (ctx->tune_pc > 0 && subst_tc_ok(ctx->g, ctx->split, ctx->tune_pc, ctx->tc_m > 0))
           spc = ctx->tune_pc;
@@ -414,6 +418,23 @@ cudaError_t subst_any(dds_ctx *ctx, int npan, const Panel *pans, const Col *cols
                       const typename Cx<R>::T *sinv, const typename Cx<R>::T *cpl,
                       typename Cx<R>::T *work, int pc) {
   if constexpr (sizeof(R) == 4) {
+    if (ctx->big_tc) {
+      // all columns of the launch, stage by stage over the whole GPU: K-split so that the units
+      // of one stage fill about two waves of SMs
+      const Geom &g = ctx->g;
+      const int rt = (g.Mb + 127) / 128;
+      const int ksplit = std::max(1, (2 * 152 + rt * npan - 1) / (rt * npan));
+      size_t acc_bytes = 0;
+      const size_t bbytes = big_scratch_bytes(g, ctx->split, pc, npan, &acc_bytes);
+      if (ctx->bigB.n < bbytes || ctx->bigacc.n < acc_bytes) return cudaErrorInvalidValue;
+      cudaError_t e = cudaMemsetAsync(ctx->bigB.p, 0, bbytes, ctx->stream);
+      if (e == cudaSuccess) e = cudaMemsetAsync(ctx->bigacc.p, 0, acc_bytes, ctx->stream);
+      if (e != cudaSuccess) return e;
+      return launch_subst_big(ctx->stream, g, ctx->split, npan, pans, cols,
+                              ctx->bigtiles.as<unsigned char>(), cpl, work, pc, ksplit,
+                              ctx->bigacc.as<float2>(), ctx->bigB.as<unsigned char>(),
+                              ctx->errflag.as<int>(), &ctx->launches);
+    }
     if (ctx->split >= 0 && subst_tc_ok(ctx->g, ctx->split, pc, ctx->tc_m > 0))
       return launch_subst_tc(ctx->stream, ctx->g, ctx->split, npan, pans, cols,
                              ctx->tctiles.as<unsigned char>(), cpl, work, pc,
@@ -539,6 +560,23 @@ dds_status prepare_ddm(dds_ctx *ctx, int nrhs, int rounds, bool *grown) {
       CK(ctx->gbar.ensure(trace_counter_bytes(std::max(tt.nlev, 1))));
       if (gb0 != ctx->gbar.p) *grown = true;
     }
+  }
+  if (ctx->big_tc && ctx->single) {
+    // scratch of the stage-parallel substitutions, sized for the widest launch (allocated here,
+    // outside any stream capture)
+    size_t bmax = 0, amax = 0;
+    auto need = [&](const StepPlan &sp) {
+      if (sp.npanels <= 0) return;
+      size_t ab = 0;
+      bmax = std::max(bmax, big_scratch_bytes(g, ctx->split, sp.pc, sp.npanels, &ab));
+      amax = std::max(amax, ab);
+    };
+    need(cp->all);
+    for (auto &sp : cp->steps) need(sp);
+    void *b0 = ctx->bigB.p, *a0 = ctx->bigacc.p;
+    CK(ctx->bigB.ensure(bmax));
+    CK(ctx->bigacc.ensure(amax));
+    *grown = *grown || b0 != ctx->bigB.p || a0 != ctx->bigacc.p;
   }
   void *w0 = ctx->work.p, *g0 = ctx->gtr.p, *r0 = ctx->rawf.p;
   CK(ctx->work.ensure(work_cols * g.Nloc * sizeof(C)));
@@ -1029,8 +1067,15 @@ dds_status setup_impl(dds_ctx *ctx, const dds_problem *p) {
                            m > 0 ? tw.as<double2>() : nullptr, m, ctx->tctiles.as<unsigned char>()));
     CK(cudaStreamSynchronize(st));
     ctx->tc_m = m;
+  } else if (ctx->split >= 0 && g.Mb > 128) {
+    // blocks wider than 128 nodes: stage-parallel tensor-core substitutions (k_subst_big.cu)
+    CK(ctx->bigtiles.ensure((size_t)big_tiles_bytes(g, ctx->split, ctx->nfac)));
+    LAUNCH(launch_split_big(st, g, ctx->split, ctx->nfac, ctx->sinv64.as<double2>(),
+                            ctx->bigtiles.as<unsigned char>()));
+    CK(cudaStreamSynchronize(st));
+    ctx->big_tc = true;
   } else {
-    ctx->split = -1;   // blocks wider than 128 nodes: FP32 CUDA-core substitutions
+    ctx->split = -1;   // FP32 CUDA-core substitutions
   }
   if (ctx->single) ctx->sinv64.release(), ctx->gmap64.release();
   ctx->setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

@@ -187,6 +187,16 @@ cudaError_t launch_subst_stream(cudaStream_t st, const Geom &g, int npanels, con
 bool subst_stream_ok(const Geom &g, int pc);
 
 // tensor-core substitutions (k_subst_tc.cu); kind 0 = TF32 pieces, 1 = BF16 pieces
+// stage-parallel tensor-core substitutions for blocks wider than 128 nodes (k_subst_big.cu)
+long long big_tiles_bytes(const Geom &g, int kind, int nfac);
+cudaError_t launch_split_big(cudaStream_t st, const Geom &g, int kind, int nfac,
+                             const double2 *sinv64, unsigned char *tiles);
+size_t big_scratch_bytes(const Geom &g, int kind, int pc, int npanels, size_t *acc_bytes);
+cudaError_t launch_subst_big(cudaStream_t st, const Geom &g, int kind, int npanels,
+                             const Panel *panels, const Col *cols, const unsigned char *tiles,
+                             const float2 *cpl, float2 *work, int pc, int ksplit, float2 *acc,
+                             unsigned char *B, int *err, long long *launches);
+
 // m > 0: two-sided chain split at block m, one 2-CTA cluster per panel; m = 0: one-sided
 cudaError_t launch_subst_tc(cudaStream_t st, const Geom &g, int kind, int npanels,
                             const Panel *panels, const Col *cols, const unsigned char *tiles,

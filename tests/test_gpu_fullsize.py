@@ -107,3 +107,17 @@ def test_zero_source_gives_zero_and_empty_batch_is_rejected(precision):
     assert np.count_nonzero(u.cpu().numpy()) == 0
     with pytest.raises(dds.DDSError):
         ctx.sweep(torch.zeros((0, G[1], G[0]), dtype=torch.complex128, device=DEV))
+
+
+def test_const3d_128_full_size_residual_under_oracle_operator():
+    """128^3, 4x4x4 subdomains (plane blocks of 2304 nodes: stage-parallel tensor-core
+    substitutions), 8 RHS, FGMRES to 1e-6: every field's residual under the oracle's own 7-point
+    operator.  (The oracle's global LU at 144^3 is too large to sample here.)"""
+    wl, prob, u, it, rel = _solve_workload("const3d_128")
+    assert u.shape[0] == 8
+    A, _ = assemble_global(prob)
+    b = rhs_from_source(prob, extend_interior(prob, wl.f))
+    assert np.all(np.asarray(rel) < wl.tol)
+    for r in range(8):
+        res = A @ u[r].ravel() - b[r].ravel()
+        assert np.linalg.norm(res) / np.linalg.norm(b[r]) < 2 * wl.tol
