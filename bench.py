@@ -459,6 +459,58 @@ def roofline_entry(stats, work, ddm_apps, args):
     return main, entries
 
 
+# Table 5 as printed: GMRES iterations and solve seconds of the trace-transfer method on the
+# paper's cluster (N x N subdomains of 300^2, one core per subdomain)
+TABLE5_PAPER = {2: (3, 29.3), 4: (3, 64.4), 8: (3, 123.5), 16: (3, 268.4), 32: (4, 715.3)}
+
+
+def run_table5(args):
+    """The weak-scaling series of Table 5: fixed 300^2 subdomains (30-point PML), N x N
+    partitions at the printed frequencies, one right-hand side of four approximated delta
+    sources (Eq. 5.4), FGMRES to 1e-6 with the DDM as preconditioner (one round)."""
+    import torch
+
+    from paper_2003_02585_gb300 import build as lbuild
+    from paper_2003_02585_gb300 import dds, synth
+
+    torch.cuda.set_device(0)
+    lbuild.build()
+    series = []
+    for N in [int(x) for x in args.table5.split(",") if x]:
+        wl = synth.workload(f"table5_{N}")
+        t0 = time.perf_counter()
+        ctx = dds.Context(wl.n, wl.h, wl.omega, wl.c, wl.parts, wl.pml_cells, wl.pml_strength,
+                          precision=args.precision, plan=args.plan)
+        setup_s = time.perf_counter() - t0
+        f = torch.from_numpy(ctx.extend(wl.f)).cuda()
+        ctx.solve(f, tol=args.tol, maxit=args.maxit, rounds=wl.rounds)      # warm-up (graphs)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            u, it, rel = ctx.solve(f, tol=args.tol, maxit=args.maxit, rounds=wl.rounds)
+            e1.record()
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        info = ctx.info()
+        series.append({"parts": f"{N}x{N}", "grid": list(wl.n), "freq": wl.meta["paper_freq"],
+                       "n_iter": it, "relres": float(max(rel)), "solve_ms": min(ms),
+                       "setup_s": setup_s, "factors": info["n_factors"],
+                       "factor_gb": info["factor_bytes"] / 1e9,
+                       "paper_n_iter": TABLE5_PAPER[N][0], "paper_solve_s": TABLE5_PAPER[N][1]})
+        ctx.close()
+        del f
+        torch.cuda.empty_cache()
+    print(json.dumps({"metric": "Table 5 weak scaling: FGMRES iterations and solve time, one RHS",
+                      "unit": "ms", "higher_is_better": False, "precision": args.precision,
+                      "data": "synthetic (Eq. 5.4 sources)", "series": series,
+                      "paper_context": "trace transfer on the paper's cluster, one core per "
+                                       "subdomain; other hardware"}), flush=True)
+    return 0
+
+
 def run_serving(args):
     """Serving workload: Poisson request stream (each request 1-32 point sources) over three
     cached media, continuous batching per medium; RHS/s and per-request p50/p99 latency."""
@@ -504,6 +556,8 @@ def main():
     ap.add_argument("--plan", default="auto", choices=["auto", "direct", "trace"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_bf16", "mixed_fp32"],
                     help="single-precision sweep variant of the timed solver")
+    ap.add_argument("--table5", default="2,4,8,16",
+                    help="partitions N of the Table 5 series (--workload table5)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch shapes instead of timing the candidates")
     ap.add_argument("--variants", default="mixed_bf16,mixed_fp32",
@@ -523,6 +577,8 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "table5":
+        return run_table5(args)
     if args.workload == "serve":
         return run_serving(args)
     return run_gpu(args)

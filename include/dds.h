@@ -60,7 +60,8 @@ typedef enum {
 } dds_precision;
 
 typedef enum {
-  DDS_PLAN_AUTO = 0,   /* trace-operator plan in 2D, direct plan in 3D                        */
+  DDS_PLAN_AUTO = 0,   /* trace-operator plan in 2D with lines of at most 128 nodes, direct   */
+                       /* plan otherwise (3D, or wide 2D subdomains)                          */
   DDS_PLAN_DIRECT = 1, /* one batched local solve per (subdomain, RHS) per sweep step         */
   DDS_PLAN_TRACE = 2   /* local solves of the own sources and of the summed traces, sweep     */
                        /* steps through the precomputed trace-to-trace map (needs 16 T bytes  */

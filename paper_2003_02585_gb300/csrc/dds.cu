@@ -781,7 +781,7 @@ dds_status setup_impl(dds_ctx *ctx, const dds_problem *p) {
   ctx->precision = p->precision;
   ctx->single = p->precision != DDS_FP64;
   ctx->split = p->precision == DDS_MIXED ? 0 : (p->precision == DDS_MIXED_BF16 ? 1 : -1);
-  ctx->plan = p->plan == DDS_PLAN_AUTO ? (p->dim == 2 ? DDS_PLAN_TRACE : DDS_PLAN_DIRECT) : p->plan;
+  ctx->plan = p->plan;   // DDS_PLAN_AUTO is resolved once the block size is known
   ctx->h = p->h;
   ctx->omega = p->omega;
   ctx->S = p->pml_strength;
@@ -806,6 +806,9 @@ dds_status setup_impl(dds_ctx *ctx, const dds_problem *p) {
   }
   g.Ml = g.M[p->dim - 1];
   g.Mb = (int)(g.Nloc / g.Ml);
+  // automatic plan: the trace-operator plan in 2D while lines have at most 128 nodes (its T x T
+  // map takes T unit-trace solves to build); the direct plan otherwise
+  if (ctx->plan == DDS_PLAN_AUTO) ctx->plan = (p->dim == 2 && g.Mb <= 128) ? DDS_PLAN_TRACE : DDS_PLAN_DIRECT;
   g.St = ((long long)g.Mb * g.Mb + 1) / 2 * 2;
   g.nsides = 2 * p->dim;
   g.T = 0;

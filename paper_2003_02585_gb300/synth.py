@@ -46,6 +46,36 @@ def gaussian_sources(n, h, centres, width):
     return np.stack([gaussian_source(n, h, c, width) for c in centres]).astype(np.complex128)
 
 
+def delta_sources(n, h, points):
+    """Approximated delta sources (Eq. 5.4): a unit mass 1/(h1 h2) per point, spread bilinearly
+    over the cell-centred nodes around the point.  All points sum into one field."""
+    d = len(n)
+    f = np.zeros(tuple(n[::-1]))
+    for pt in points:
+        idx, wts = [], []
+        for a in range(d):
+            s = pt[a] / h - 0.5                   # node coordinate: x_p = (p + 1/2) h
+            p0 = int(math.floor(s))
+            t = s - p0
+            idx.append((p0, p0 + 1))
+            wts.append((1.0 - t, t))
+        for corner in range(1 << d):
+            pos, w = [], 1.0
+            for a in range(d):
+                bit = (corner >> a) & 1
+                pos.append(idx[a][bit])
+                w *= wts[a][bit]
+            if w == 0.0 or any(q < 0 or q >= n[a] for a, q in enumerate(pos)):
+                continue
+            f[tuple(pos[::-1])] += w / h ** d
+    return f
+
+
+# Table 5: subdomains of 300^2 nodes with a 30-point PML, N x N partitions, frequencies as printed
+TABLE5_FREQ = {2: 65.9, 4: 126.0, 8: 246.0, 16: 486.0, 32: 966.0}
+TABLE5_POINTS = [(0.25, 0.25), (0.25, 0.75), (0.75, 0.25), (0.75, 0.75)]
+
+
 def medium_constant(n, c0: float = 1.0):
     return np.full(tuple(n[::-1]), c0, dtype=np.float64)
 
@@ -113,6 +143,10 @@ def workload(name: str, nrhs: int | None = None) -> Workload:
                   stalled near 0.25 relative residual at this size, the interface reflections
                   needing the extra round of Theorem 3.10).
     const3d_128   3D, 128^3, kappa = 2 pi 10, 4x4x4 subdomains of 32^3, 8-cell PML, 8 Gaussians.
+    table5_N      the weak-scaling series of Table 5: N x N subdomains of 300^2 nodes, 30-point
+                  PML, omega / 2 pi as printed for N = 2, 4, 8, 16, 32, one right-hand side of four
+                  approximated delta sources at (1/4, 1/4), (1/4, 3/4), (3/4, 1/4), (3/4, 3/4)
+                  (Eq. 5.4), FGMRES to 1e-6 with one round of sweeps.
     """
     if name == "const2d_128":
         n = (128, 128)
@@ -145,4 +179,12 @@ def workload(name: str, nrhs: int | None = None) -> Workload:
         cen = uniform_centres(np.random.default_rng(4), R, 3, 6 * w, 1 - 6 * w)
         return Workload(name, n, (4, 4, 4), 2 * math.pi * 10, 8, 30.0, medium_constant(n),
                         gaussian_sources(n, h, cen, w), "mixed", 1, 1e-6)
+    if name.startswith("table5_"):
+        N = int(name.split("_")[1])
+        n = (300 * N, 300 * N)
+        h = 1.0 / n[0]
+        f = delta_sources(n, h, TABLE5_POINTS)[None].astype(np.complex128)
+        return Workload(name, n, (N, N), 2 * math.pi * TABLE5_FREQ[N], 30, 30.0,
+                        medium_constant(n), f, "mixed", 1, 1e-6,
+                        {"paper_freq": TABLE5_FREQ[N]})
     raise KeyError(name)
