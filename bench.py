@@ -402,8 +402,8 @@ DTYPE = {"mixed": "c64 sweeps (3xTF32 tensor-core substitutions) + c128 FGMRES",
 SPLIT_KIND = {"mixed": "tf32", "mixed_bf16": "bf16", "mixed_fp32": "fp32"}
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the substitution kernel,
 # from one ncu capture of the kernel as it stands, on the same workload and launch configuration
-SUBST_TRAFFIC = {}
-TRACE_TRAFFIC = {("mixed", "const2d_640"): 40.98e6 + 0.11e6}
+SUBST_TRAFFIC = {("mixed", "const2d_640"): 128.55e6 + 62.62e6}
+TRACE_TRAFFIC = {("mixed", "const2d_640"): 41.01e6 + 0.06e6}
 
 
 def roofline_entry(stats, work, ddm_apps, args):
