@@ -186,7 +186,7 @@ long long dds_kernel_launches(const dds_ctx *ctx);
  *   mixed modes with tensor-core substitutions), and the CTAs per SM of the cooperative trace
  *   launch (1 or 2; trace plan).
  * Each candidate is captured once and then timed over three DDM applications with CUDA events
- * on the context's stream, with synthetic (zero) right-hand sides in scratch the call allocates
+ * on the context's stream, with synthetic nonzero right-hand sides in scratch the call allocates
  * and frees.  table (row-major [n][3]: panel width (0 = automatic), CTAs per SM, ms per DDM
  * application) receives at most max_entries rows; *n_entries is the number of candidates timed;
  * best[0], best[1] the chosen panel width and CTAs per SM.  Cached plans and graphs are dropped.

@@ -92,6 +92,7 @@ struct dds_ctx {
   bool big_tc = false;
   DBuf errflag;  // set by kernels whose bounded waits gave up
   DBuf gbar;     // step counters of the cooperative trace-sweep launch
+  DBuf nzflag;   // per work slot: the assembled right-hand side has a nonzero entry
   DBuf an_glob[3], iah_glob[3];
   DBuf stc0, stcp[3];  // global stencil (centre, coupling to +e_a)
   Tables tb{};
@@ -416,7 +417,7 @@ dds_status set_route(dds_ctx *ctx, int rounds) {
 template <typename R>
 cudaError_t subst_any(dds_ctx *ctx, int npan, const Panel *pans, const Col *cols,
                       const typename Cx<R>::T *sinv, const typename Cx<R>::T *cpl,
-                      typename Cx<R>::T *work, int pc) {
+                      typename Cx<R>::T *work, int pc, const int *nz = nullptr) {
   if constexpr (sizeof(R) == 4) {
     if (ctx->big_tc) {
       // all columns of the launch, stage by stage over the whole GPU: K-split so that the units
@@ -438,7 +439,7 @@ cudaError_t subst_any(dds_ctx *ctx, int npan, const Panel *pans, const Col *cols
     if (ctx->split >= 0 && subst_tc_ok(ctx->g, ctx->split, pc, ctx->tc_m > 0))
       return launch_subst_tc(ctx->stream, ctx->g, ctx->split, npan, pans, cols,
                              ctx->tctiles.as<unsigned char>(), cpl, work, pc,
-                             ctx->errflag.as<int>(), ctx->tc_m);
+                             ctx->errflag.as<int>(), ctx->tc_m, nz);
     if (subst_stream_ok(ctx->g, pc))
       return launch_subst_stream(ctx->stream, ctx->g, npan, pans, cols, sinv, cpl, work, pc,
                                  ctx->errflag.as<int>());
@@ -578,7 +579,9 @@ dds_status prepare_ddm(dds_ctx *ctx, int nrhs, int rounds, bool *grown) {
     CK(ctx->bigacc.ensure(amax));
     *grown = *grown || b0 != ctx->bigB.p || a0 != ctx->bigacc.p;
   }
-  void *w0 = ctx->work.p, *g0 = ctx->gtr.p, *r0 = ctx->rawf.p;
+  void *w0 = ctx->work.p, *g0 = ctx->gtr.p, *r0 = ctx->rawf.p, *z0 = ctx->nzflag.p;
+  CK(ctx->nzflag.ensure(work_cols * sizeof(int)));
+  *grown = *grown || z0 != ctx->nzflag.p;
   CK(ctx->work.ensure(work_cols * g.Nloc * sizeof(C)));
   CK(ctx->gtr.ensure(L * slot * sizeof(C)));
   if (trace_plan) CK(ctx->rawf.ensure(slot * sizeof(C)));
@@ -603,6 +606,7 @@ dds_status run_ddm(dds_ctx *ctx, const double2 *b, int nrhs, double2 *u, int rou
   C *work = ctx->work.as<C>();
   C *gtr = ctx->gtr.as<C>();
   const Col *cols = cp->cols.as<Col>();
+  int *nzf = ctx->nzflag.as<int>();   // per work slot: nonzero right-hand side
   const Panel *pans = cp->panels.as<Panel>();
   const int *route = ctx->route_dev.as<int>();
   if (!trace_plan) {
@@ -613,8 +617,8 @@ dds_status run_ddm(dds_ctx *ctx, const double2 *b, int nrhs, double2 *u, int rou
         const StepPlan &sp = cp->steps[dir * ctx->nsteps + s];
         if (sp.ncols == 0) continue;
         LAUNCHK(DDS_K_ASSEMBLE, launch_assemble<R>(st, g, ctx->tb, sp.ncols, cols + sp.col_off, work, b, nullptr,
-                                  l == 0, gtr + l * slot, (long long)g.nsub * g.T, g.T, 1, 0));
-        LAUNCHK(DDS_K_SUBST, subst_any<R>(ctx, sp.npanels, pans + sp.pan_off, cols, sinv, cpl, work, sp.pc));
+                                  l == 0, gtr + l * slot, (long long)g.nsub * g.T, g.T, 1, 0, nzf));
+        LAUNCHK(DDS_K_SUBST, subst_any<R>(ctx, sp.npanels, pans + sp.pan_off, cols, sinv, cpl, work, sp.pc, nzf));
         LAUNCHK(DDS_K_EXTRACT, launch_extract<R>(st, g, sp.ncols, cols + sp.col_off, work, u, 1, nullptr, gtr,
                                  route, l, nrhs));
       }
@@ -624,8 +628,8 @@ dds_status run_ddm(dds_ctx *ctx, const double2 *b, int nrhs, double2 *u, int rou
     const StepPlan &all = cp->all;
     // own sources: x_f = A_R^{-1} b_own; keep its raw trace lines
     LAUNCHK(DDS_K_ASSEMBLE, launch_assemble<R>(st, g, ctx->tb, all.ncols, cols + all.col_off, work, b, nullptr, 1,
-                              (const C *)nullptr, 0, 0, 1, 0));
-    LAUNCHK(DDS_K_SUBST, subst_any<R>(ctx, all.npanels, pans + all.pan_off, cols, sinv, cpl, work, all.pc));
+                              (const C *)nullptr, 0, 0, 1, 0, nzf));
+    LAUNCHK(DDS_K_SUBST, subst_any<R>(ctx, all.npanels, pans + all.pan_off, cols, sinv, cpl, work, all.pc, nzf));
     LAUNCHK(DDS_K_EXTRACT, launch_extract<R>(st, g, all.ncols, cols + all.col_off, work, u, 0, rawf,
                              (C *)nullptr, route, 0, nrhs));
     // sweeps: every step of every sweep, traces of the step set through the trace map, in one
@@ -642,8 +646,8 @@ dds_status run_ddm(dds_ctx *ctx, const double2 *b, int nrhs, double2 *u, int rou
                                                      ctx->errflag.as<int>(), ctx->trace_per_sm));
     // own nodes: u = A_R^{-1}(b_own + potentials of all traces received in every sweep)
     LAUNCHK(DDS_K_ASSEMBLE, launch_assemble<R>(st, g, ctx->tb, all.ncols, cols + all.col_off, work, b, nullptr, 1,
-                              gtr, (long long)g.nsub * g.T, g.T, L, slot));
-    LAUNCHK(DDS_K_SUBST, subst_any<R>(ctx, all.npanels, pans + all.pan_off, cols, sinv, cpl, work, all.pc));
+                              gtr, (long long)g.nsub * g.T, g.T, L, slot, nzf));
+    LAUNCHK(DDS_K_SUBST, subst_any<R>(ctx, all.npanels, pans + all.pan_off, cols, sinv, cpl, work, all.pc, nzf));
     LAUNCHK(DDS_K_EXTRACT, launch_extract<R>(st, g, all.ncols, cols + all.col_off, work, u, 2, (C *)nullptr,
                              (C *)nullptr, route, 0, nrhs));
   }
@@ -1467,12 +1471,13 @@ dds_status dds_autotune(dds_ctx *ctx, int nrhs, int rounds, int max_entries, int
   }
   std::vector<int> pers = {ctx->trace_per_sm};
   if (ctx->plan == DDS_PLAN_TRACE) pers = {1, 2};
-  // synthetic right-hand sides: the kernels do the same work for any values
+  // synthetic right-hand sides, nonzero everywhere so that no local solve is skipped as zero
+  // work (every byte 0x3F: each double is a finite ~5e-4)
   DBuf bb, uu;
   const size_t bytes = (size_t)nrhs * g.Nglob * sizeof(double2);
   CK(bb.ensure(bytes));
   CK(uu.ensure(bytes));
-  CK(cudaMemsetAsync(bb.p, 0, bytes, ctx->stream));
+  CK(cudaMemsetAsync(bb.p, 0x3F, bytes, ctx->stream));
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));

@@ -174,7 +174,8 @@ cudaError_t launch_assemble(cudaStream_t st, const Geom &g, const Tables &tb, in
                             const Col *cols, typename Cx<R>::T *work, const double2 *b,
                             const double2 *unused, int with_source,
                             const typename Cx<R>::T *traces, long long trace_rhs_stride,
-                            long long trace_sub_stride, int nslots, long long slot_stride);
+                            long long trace_sub_stride, int nslots, long long slot_stride,
+                            int *nzflag = nullptr);
 
 template <typename R>
 cudaError_t launch_subst(cudaStream_t st, const Geom &g, int npanels, const Panel *panels,
@@ -198,9 +199,12 @@ cudaError_t launch_subst_big(cudaStream_t st, const Geom &g, int kind, int npane
                              unsigned char *B, int *err, long long *launches);
 
 // m > 0: two-sided chain split at block m, one 2-CTA cluster per panel; m = 0: one-sided
+// nz (optional): per work slot, nonzero if the column's right-hand side has a nonzero entry;
+// CTAs whose columns are all zero leave at once (their solution is the zero already in work)
 cudaError_t launch_subst_tc(cudaStream_t st, const Geom &g, int kind, int npanels,
                             const Panel *panels, const Col *cols, const unsigned char *tiles,
-                            const float2 *cpl, float2 *work, int pc, int *err, int m);
+                            const float2 *cpl, float2 *work, int pc, int *err, int m,
+                            const int *nz = nullptr);
 bool subst_tc_ok(const Geom &g, int kind, int pc, bool twisted);
 int tc_middle_block(const Geom &g);   // m of the two-sided chain (0: too few blocks)
 long long tc_tiles_bytes(const Geom &g, int kind, int nfac);

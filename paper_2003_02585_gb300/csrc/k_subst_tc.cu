@@ -226,7 +226,8 @@ template <int PC, int KIND, int NG, bool TW>
 __global__ void __launch_bounds__(32 * (4 * NG + 2), 1)
     k_subst_tc(Geom g, TcArgs a, const Panel *__restrict__ panels, const Col *__restrict__ cols,
                const unsigned char *__restrict__ tiles, const float2 *__restrict__ cpl,
-               float2 *__restrict__ work, int *__restrict__ err, int m) {
+               float2 *__restrict__ work, int *__restrict__ err, int m,
+               const int *__restrict__ nz) {
   constexpr int H = PC / NG;            // columns per epilogue thread
   constexpr int NEPI = 128 * NG;        // epilogue threads
   constexpr int NCOL = 8 * PC;          // TMEM columns: D1 [0, 4PC), D2 [4PC, 8PC)
@@ -251,6 +252,13 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1)
   float2 *xch = reinterpret_cast<float2 *>(sB + (size_t)(a.Kp / (KIND == 0 ? 4 : 8)) * a.LB);
   const Panel p = panels[TW ? blockIdx.x / 2 : blockIdx.x];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (nz != nullptr) {
+    // zero-work skipping: the solve of a zero right-hand side is zero, which work already holds
+    // (both CTAs of a cluster see the same columns and leave together)
+    int any = 0;
+    for (int c = 0; c < p.ncol; ++c) any |= nz[cols[p.col0 + c].slot];
+    if (!any) return;
+  }
   auto aborted = [&]() { return *reinterpret_cast<volatile int *>(&abort_flag) != 0; };
   auto fail = [&](int code) {
     atomicExch(err, code);
@@ -475,7 +483,7 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1)
 template <int PC, int KIND, bool TW>
 static cudaError_t tc_launch(cudaStream_t st, const Geom &g, const TcShape &t, int npanels,
                              const Panel *panels, const Col *cols, const unsigned char *tiles,
-                             const float2 *cpl, float2 *work, int *err, int m) {
+                             const float2 *cpl, float2 *work, int *err, int m, const int *nz) {
   constexpr int NG = 2;
   static bool done[64] = {false};
   cudaError_t e = smem_limit_once(k_subst_tc<PC, KIND, NG, TW>, done);
@@ -494,33 +502,35 @@ static cudaError_t tc_launch(cudaStream_t st, const Geom &g, const TcShape &t, i
   cfg.attrs = attr;
   cfg.numAttrs = TW ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, k_subst_tc<PC, KIND, NG, TW>, g, a, panels, cols, tiles, cpl,
-                            work, err, TW ? m : g.Ml - 1);
+                            work, err, TW ? m : g.Ml - 1, nz);
 }
 
 template <int KIND, bool TW>
 static cudaError_t tc_dispatch(cudaStream_t st, const Geom &g, const TcShape &t, int npanels,
                                const Panel *panels, const Col *cols, const unsigned char *tiles,
-                               const float2 *cpl, float2 *work, int pc, int *err, int m) {
+                               const float2 *cpl, float2 *work, int pc, int *err, int m,
+                               const int *nz) {
   switch (pc) {
-    case 8: return tc_launch<8, KIND, TW>(st, g, t, npanels, panels, cols, tiles, cpl, work, err, m);
-    case 16: return tc_launch<16, KIND, TW>(st, g, t, npanels, panels, cols, tiles, cpl, work, err, m);
-    case 32: return tc_launch<32, KIND, TW>(st, g, t, npanels, panels, cols, tiles, cpl, work, err, m);
+    case 8: return tc_launch<8, KIND, TW>(st, g, t, npanels, panels, cols, tiles, cpl, work, err, m, nz);
+    case 16: return tc_launch<16, KIND, TW>(st, g, t, npanels, panels, cols, tiles, cpl, work, err, m, nz);
+    case 32: return tc_launch<32, KIND, TW>(st, g, t, npanels, panels, cols, tiles, cpl, work, err, m, nz);
   }
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_subst_tc(cudaStream_t st, const Geom &g, int kind, int npanels,
                             const Panel *panels, const Col *cols, const unsigned char *tiles,
-                            const float2 *cpl, float2 *work, int pc, int *err, int m) {
+                            const float2 *cpl, float2 *work, int pc, int *err, int m,
+                            const int *nz) {
   if (npanels <= 0) return cudaSuccess;
   const bool tw = m > 0;
   TcShape t;
   if (!tc_shape(g, kind, pc, &t, tw)) return cudaErrorInvalidValue;
   if (kind == 0)
-    return tw ? tc_dispatch<0, true>(st, g, t, npanels, panels, cols, tiles, cpl, work, pc, err, m)
-              : tc_dispatch<0, false>(st, g, t, npanels, panels, cols, tiles, cpl, work, pc, err, m);
-  return tw ? tc_dispatch<1, true>(st, g, t, npanels, panels, cols, tiles, cpl, work, pc, err, m)
-            : tc_dispatch<1, false>(st, g, t, npanels, panels, cols, tiles, cpl, work, pc, err, m);
+    return tw ? tc_dispatch<0, true>(st, g, t, npanels, panels, cols, tiles, cpl, work, pc, err, m, nz)
+              : tc_dispatch<0, false>(st, g, t, npanels, panels, cols, tiles, cpl, work, pc, err, m, nz);
+  return tw ? tc_dispatch<1, true>(st, g, t, npanels, panels, cols, tiles, cpl, work, pc, err, m, nz)
+            : tc_dispatch<1, false>(st, g, t, npanels, panels, cols, tiles, cpl, work, pc, err, m, nz);
 }
 
 bool subst_tc_ok(const Geom &g, int kind, int pc, bool twisted) {

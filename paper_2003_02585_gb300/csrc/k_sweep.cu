@@ -20,9 +20,10 @@ __global__ void k_assemble(Geom g, Tables tb, const Col *__restrict__ cols,
                            typename Cx<R>::T *__restrict__ work, const double2 *__restrict__ b,
                            int with_source, const typename Cx<R>::T *__restrict__ traces,
                            long long trs_rhs, long long trs_sub, int nslots,
-                           long long slot_stride) {
+                           long long slot_stride, int *__restrict__ nzflag) {
   using C = typename Cx<R>::T;
   const Col c = cols[blockIdx.x];
+  bool nz = false;   // any nonzero entry written (the local solve of a zero source is zero)
   C *x = work + (long long)c.slot * g.Nloc;
   for (long long i = threadIdx.x; i < g.Nloc; i += blockDim.x) x[i] = czero<C>();
   __syncthreads();
@@ -43,12 +44,13 @@ __global__ void k_assemble(Geom g, Tables tb, const Col *__restrict__ cols,
       long long p1 = (long long)k[1] * g.m[1] + i1;
       long long p2 = g.dim == 3 ? (long long)k[2] * g.m[2] + i2 : 0;
       long long glob = p0 + (long long)g.G[0] * (p1 + (long long)g.G[1] * p2);
-      x[loc] = to_c(bb[glob], C());
+      const C v = to_c(bb[glob], C());
+      nz = nz || v.x != 0 || v.y != 0;
+      x[loc] = v;
     }
   }
-  if (traces == nullptr) return;
-  const C *tr = traces + (long long)c.rhs * trs_rhs + (long long)c.sub * trs_sub;
-  for (int d = 0; d < g.nsides; ++d) {
+  const C *tr = traces ? traces + (long long)c.rhs * trs_rhs + (long long)c.sub * trs_sub : nullptr;
+  for (int d = 0; tr != nullptr && d < g.nsides; ++d) {
     __syncthreads();  // lines of different sides may share nodes
     if (sub_neighbour(g, c.sub, d) < 0) continue;
     const int a = d >> 1, Lt = g.Lt[d], off = g.toff[d];
@@ -65,7 +67,12 @@ __global__ void k_assemble(Geom g, Tables tb, const Col *__restrict__ cols,
       const long long no = line_node(g, a, lo, t), ni = line_node(g, a, li, t);
       x[no] = cadd(x[no], cmul(cd, bv));
       x[ni] = csub(x[ni], cmul(cd, av));
+      nz = nz || av.x != 0 || av.y != 0 || bv.x != 0 || bv.y != 0;
     }
+  }
+  if (nzflag != nullptr) {
+    const int any = __syncthreads_or(nz);
+    if (threadIdx.x == 0) nzflag[c.slot] = any;
   }
 }
 
@@ -691,10 +698,10 @@ cudaError_t launch_assemble(cudaStream_t st, const Geom &g, const Tables &tb, in
                             const Col *cols, typename Cx<R>::T *work, const double2 *b,
                             const double2 *, int with_source, const typename Cx<R>::T *traces,
                             long long trs_rhs, long long trs_sub, int nslots,
-                            long long slot_stride) {
+                            long long slot_stride, int *nzflag) {
   if (ncols <= 0) return cudaSuccess;
   k_assemble<R><<<ncols, 256, 0, st>>>(g, tb, cols, work, b, with_source, traces, trs_rhs,
-                                       trs_sub, nslots, slot_stride);
+                                       trs_sub, nslots, slot_stride, nzflag);
   return cudaGetLastError();
 }
 
@@ -828,7 +835,7 @@ cudaError_t launch_copy_local_back(cudaStream_t st, long long n, const typename 
   template cudaError_t launch_assemble<R>(cudaStream_t, const Geom &, const Tables &, int,     \
                                           const Col *, Cx<R>::T *, const double2 *,           \
                                           const double2 *, int, const Cx<R>::T *, long long,   \
-                                          long long, int, long long);                           \
+                                          long long, int, long long, int *);                    \
   template cudaError_t launch_subst<R>(cudaStream_t, const Geom &, int, const Panel *,         \
                                        const Col *, const Cx<R>::T *, const Cx<R>::T *,        \
                                        Cx<R>::T *, int);                                        \
