@@ -15,68 +15,70 @@ __device__ inline double2 crecip64(double2 z) {
 //           + kappa^2 J u_p,          Dirichlet outside the extended grid.
 // The stencil is precomputed per node at set-up (tb.c0: centre, tb.cp[a]: coupling to p + e_a,
 // so the coupling to p - e_a is tb.cp[a][p - e_a]); each thread applies it to every RHS.
+// One thread per (node, RHS): the stencil coefficients of a node are re-read per RHS (from L1/L2)
+// so that every FP64 pipe has independent work.  Outside the PML every coefficient is real: two
+// FMAs per stencil term.
 template <int DIM>
 __global__ void __launch_bounds__(256) k_apply_A(Geom g, Tables tb, int nrhs, const double2 *__restrict__ u,
                           double2 *__restrict__ Au, int divide_by_J,
                           const double2 *__restrict__ sub) {
   const int N = (int)g.Nglob;
   const int G0 = g.G[0], G1 = g.G[1];
-  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < N; q += gridDim.x * blockDim.x) {
+  const long long total = (long long)nrhs * N;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(i / N), q = (int)(i - (long long)r * N);
     int p[3];
     p[0] = q % G0;
     p[1] = (q / G0) % G1;
     p[2] = DIM == 3 ? q / (G0 * G1) : 0;
+    const double2 *ur = u + (long long)r * N + q;
     const double2 c0 = tb.c0[q];
-    double2 cpv[DIM], cmv[DIM];
-    int stride[DIM];
+    double2 cpv[DIM], cmv[DIM], up[DIM], um[DIM];
     int st = 1;
-    bool real = c0.y == 0.0;
+    // "every imaginary part is zero" on the integer pipe (the FP64 pipe is the scarce one):
+    // OR of the bit patterns with the sign bit dropped
+    unsigned long long imag = (unsigned long long)__double_as_longlong(c0.y) << 1;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
-      stride[a] = st;
+      const bool hp = p[a] + 1 < g.G[a], hm = p[a] > 0;
+      cpv[a] = hp ? tb.cp[a][q] : make_double2(0.0, 0.0);
+      cmv[a] = hm ? tb.cp[a][q - st] : make_double2(0.0, 0.0);
+      up[a] = hp ? ur[st] : make_double2(0.0, 0.0);
+      um[a] = hm ? ur[-st] : make_double2(0.0, 0.0);
+      imag |= ((unsigned long long)__double_as_longlong(cpv[a].y) << 1) |
+              ((unsigned long long)__double_as_longlong(cmv[a].y) << 1);
       st *= g.G[a];
-      cpv[a] = p[a] + 1 < g.G[a] ? tb.cp[a][q] : make_double2(0.0, 0.0);
-      cmv[a] = p[a] > 0 ? tb.cp[a][q - stride[a]] : make_double2(0.0, 0.0);
-      real = real && cpv[a].y == 0.0 && cmv[a].y == 0.0;
     }
-    double2 iJ = make_double2(1.0, 0.0);
+    const bool real = imag == 0ull;
+    const double2 uc = ur[0];
+    double2 sum;
+    if (real) {
+      // two independent chains per component
+      double sx0 = c0.x * uc.x, sy0 = c0.x * uc.y, sx1 = 0.0, sy1 = 0.0;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        sx0 = fma(cpv[a].x, up[a].x, sx0);
+        sy0 = fma(cpv[a].x, up[a].y, sy0);
+        sx1 = fma(cmv[a].x, um[a].x, sx1);
+        sy1 = fma(cmv[a].x, um[a].y, sy1);
+      }
+      sum = make_double2(sx0 + sx1, sy0 + sy1);
+    } else {
+      sum = cmul(c0, uc);
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        cfma(sum, cpv[a], up[a]);
+        cfma(sum, cmv[a], um[a]);
+      }
+    }
     if (divide_by_J) {
       double2 J = make_double2(1.0, 0.0);
       for (int a = 0; a < DIM; ++a) J = cmul(J, tb.an_glob64[a][p[a]]);
-      iJ = crecip64(J);
+      sum = cmul(sum, crecip64(J));
     }
-    for (int r = 0; r < nrhs; ++r) {
-      const double2 *ur = u + (long long)r * N;
-      double2 sum;
-      if (real) {
-        // outside the PML every coefficient is real: two FMAs per stencil term
-        const double2 uc = ur[q];
-        sum = make_double2(c0.x * uc.x, c0.x * uc.y);
-#pragma unroll
-        for (int a = 0; a < DIM; ++a) {
-          if (p[a] + 1 < g.G[a]) {
-            const double2 un = ur[q + stride[a]];
-            sum.x = fma(cpv[a].x, un.x, sum.x);
-            sum.y = fma(cpv[a].x, un.y, sum.y);
-          }
-          if (p[a] > 0) {
-            const double2 un = ur[q - stride[a]];
-            sum.x = fma(cmv[a].x, un.x, sum.x);
-            sum.y = fma(cmv[a].x, un.y, sum.y);
-          }
-        }
-      } else {
-        sum = cmul(c0, ur[q]);
-#pragma unroll
-        for (int a = 0; a < DIM; ++a) {
-          if (p[a] + 1 < g.G[a]) cfma(sum, cpv[a], ur[q + stride[a]]);
-          if (p[a] > 0) cfma(sum, cmv[a], ur[q - stride[a]]);
-        }
-      }
-      if (divide_by_J) sum = cmul(sum, iJ);
-      if (sub) sum = csub(sum, sub[(long long)r * N + q]);
-      Au[(long long)r * N + q] = sum;
-    }
+    if (sub) sum = csub(sum, sub[i]);
+    Au[i] = sum;
   }
 }
 
@@ -272,10 +274,11 @@ static inline dim3 grid_rhs(long long N, int nrhs) {
 
 cudaError_t launch_apply_A(cudaStream_t st, const Geom &g, const Tables &tb, int nrhs,
                            const double2 *u, double2 *Au, int divide_by_J, const double2 *sub) {
+  const unsigned grid = grid_for(g.Nglob * (long long)nrhs);
   if (g.dim == 2)
-    k_apply_A<2><<<grid_for(g.Nglob), 256, 0, st>>>(g, tb, nrhs, u, Au, divide_by_J, sub);
+    k_apply_A<2><<<grid, 256, 0, st>>>(g, tb, nrhs, u, Au, divide_by_J, sub);
   else
-    k_apply_A<3><<<grid_for(g.Nglob), 256, 0, st>>>(g, tb, nrhs, u, Au, divide_by_J, sub);
+    k_apply_A<3><<<grid, 256, 0, st>>>(g, tb, nrhs, u, Au, divide_by_J, sub);
   return cudaGetLastError();
 }
 
