@@ -67,6 +67,16 @@ __device__ inline bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
   return ok != 0;
 }
 
+// ---- reductions into global memory without a returned value (fire and forget)
+__device__ inline void red_add_f4(float4 *p, float4 v) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x), "f"(v.y),
+               "f"(v.z), "f"(v.w)
+               : "memory");
+}
+__device__ inline void red_add_f2(float2 *p, float2 v) {
+  asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(v.x), "f"(v.y) : "memory");
+}
+
 // ---- thread-block clusters: distributed shared memory and remote mbarrier arrivals
 
 __device__ inline uint32_t cluster_ctarank() {

@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(192, 1)
             if (c >= p.ncol) break;
             const float p_re = d[0][h] + d[1][h], p_im = d[0][8 + h] + d[1][8 + h];
             const float q_re = d[2][h] + d[3][h], q_im = d[2][8 + h] + d[3][8 + h];
-            atomicAdd(dst + c, make_float2(p_re - q_im, p_im + q_re));
+            red_add_f2(dst + c, make_float2(p_re - q_im, p_im + q_re));
           }
         }
       }

@@ -463,7 +463,7 @@ __device__ void trace_item(const Geom &g, typename Cx<R>::T *__restrict__ gtr,
         C *dst = gtr + lp * slot_stride + ((long long)crhs * g.nsub + nb) * T + g.toff[dout ^ 1] + rr;
         if constexpr (sizeof(R) == 4) {
           // both rows in one 16-byte vector atomic (T, the side offsets and rr are even)
-          atomicAdd(reinterpret_cast<float4 *>(dst), make_float4(v0r.x, v0r.y, v1r.x, v1r.y));
+          red_add_f4(reinterpret_cast<float4 *>(dst), make_float4(v0r.x, v0r.y, v1r.x, v1r.y));
         } else {
           atomic_cadd(dst, v0r);
           atomic_cadd(dst + 1, v1r);
