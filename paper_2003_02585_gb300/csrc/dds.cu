@@ -60,8 +60,8 @@ struct CallPlan {            // all launch lists for one nrhs
   std::vector<StepPlan> tsteps;  // [dir][step] for the trace plan (trace-step panels)
   StepPlan all;                  // every (sub, rhs) column (trace plan phases, local solves)
   DBuf cols, panels, tpanels;
-  struct TraceTable { int n = -1, nlev = 0; DBuf buf, tpan; };
-  std::map<int, TraceTable> trace_steps;   // rounds -> step table of the cooperative launch
+  struct TraceTable { int n = -1, nlev = 0; DBuf buf, levs, tpan; };   // items, level offsets
+  std::map<int, TraceTable> trace_steps;   // rounds -> item lists of the cooperative launch
 };
 
 }  // namespace
@@ -468,8 +468,8 @@ dds_status check_errflag(dds_ctx *ctx) {
 // those producers (0 without any), computed in sweep and step order.  Per level and sweep one
 // entry holds that sweep's subdomains of the level, as panels of 8 (subdomain, RHS) columns of
 // one factor.  Returns the number of levels.
-int build_trace_schedule(dds_ctx *ctx, int nrhs, int rounds, std::vector<TraceStep> &ts,
-                         std::vector<TracePanel> &tp) {
+int build_trace_schedule(dds_ctx *ctx, int nrhs, int rounds, std::vector<int4> &items,
+                         std::vector<int> &lev_off, std::vector<TracePanel> &tp) {
   const Geom &g = ctx->g;
   const int L = ctx->ndirs * rounds, ns = g.nsub;
   const std::vector<int> route = build_route(g.dim, rounds);
@@ -493,8 +493,8 @@ int build_trace_schedule(dds_ctx *ctx, int nrhs, int rounds, std::vector<TraceSt
       }
   }
   for (int v = 0; v < nlev; ++v) {
-    int level_items = 0;
-    const size_t first = ts.size();
+    const size_t first = items.size();
+    lev_off.push_back((int)first);
     for (int l = 0; l < L; ++l) {
       std::vector<int> subs;
       for (int x = 0; x < ns; ++x)
@@ -517,16 +517,15 @@ int build_trace_schedule(dds_ctx *ctx, int nrhs, int rounds, std::vector<TraceSt
           ++cur.ncol;
         }
       if (cur.ncol > 0) tp.push_back(cur);
-      const int npan = (int)tp.size() - pan_off;
-      int nout = 0, nseg = 0;
-      const int ni = trace_step_items(g, npan, ctx->in_mask[l], ctx->out_mask[l], &nout, &nseg);
-      if (ni == 0) continue;   // nothing routed out or nothing can come in
-      ts.push_back(TraceStep{l, pan_off, npan, ctx->in_mask[l], ctx->out_mask[l], nout, nseg, ni,
-                             v, level_items, 0});
-      level_items += ni;
+      trace_items_for(g, tp.data(), pan_off, (int)tp.size(), l, route.data(), ctx->in_mask[l],
+                      items);
     }
-    for (size_t e = first; e < ts.size(); ++e) ts[e].level_items = level_items;
+    // heaviest items first (input count), so that the snake deal over the CTAs balances
+    std::stable_sort(items.begin() + first, items.end(), [](const int4 &a, const int4 &b) {
+      return ((a.z >> 16) & 0xFFFF) > ((b.z >> 16) & 0xFFFF);
+    });
   }
+  lev_off.push_back((int)items.size());
   return nlev;
 }
 
@@ -551,12 +550,14 @@ dds_status prepare_ddm(dds_ctx *ctx, int nrhs, int rounds, bool *grown) {
     // schedule of the cooperative trace launch (uploaded outside any stream capture)
     auto &tt = cp->trace_steps[rounds];
     if (tt.n < 0) {
-      std::vector<TraceStep> ts;
+      std::vector<int4> items;
+      std::vector<int> lev;
       std::vector<TracePanel> tp;
-      tt.nlev = build_trace_schedule(ctx, nrhs, rounds, ts, tp);
-      CK(upload(tt.buf, ts, ctx->stream));
+      tt.nlev = build_trace_schedule(ctx, nrhs, rounds, items, lev, tp);
+      CK(upload(tt.buf, items, ctx->stream));
+      CK(upload(tt.levs, lev, ctx->stream));
       CK(upload(tt.tpan, tp, ctx->stream));
-      tt.n = (int)ts.size();
+      tt.n = (int)items.size();
       void *gb0 = ctx->gbar.p;
       CK(ctx->gbar.ensure(trace_counter_bytes(std::max(tt.nlev, 1))));
       if (gb0 != ctx->gbar.p) *grown = true;
@@ -640,9 +641,10 @@ dds_status run_ddm(dds_ctx *ctx, const double2 *b, int nrhs, double2 *u, int rou
       return DDS_EINVAL;
     }
     const CallPlan::TraceTable &tt = tti->second;
-    LAUNCHK(DDS_K_TRACE_STEP, launch_trace_sweeps<R>(st, g, tt.buf.as<TraceStep>(), tt.n, tt.nlev,
-                                                     tt.tpan.as<TracePanel>(), gmap,
-                                                     gtr, rawf, route, nrhs, ctx->gbar.as<unsigned>(),
+    LAUNCHK(DDS_K_TRACE_STEP, launch_trace_sweeps<R>(st, g, tt.buf.as<int4>(), tt.n,
+                                                     tt.levs.as<int>(), tt.nlev,
+                                                     tt.tpan.as<TracePanel>(), gmap, gtr, rawf,
+                                                     nrhs, ctx->gbar.as<unsigned>(),
                                                      ctx->errflag.as<int>(), ctx->trace_per_sm));
     // own nodes: u = A_R^{-1}(b_own + potentials of all traces received in every sweep)
     LAUNCHK(DDS_K_ASSEMBLE, launch_assemble<R>(st, g, ctx->tb, all.ncols, cols + all.col_off, work, b, nullptr, 1,
@@ -826,7 +828,7 @@ dds_status setup_impl(dds_ctx *ctx, const dds_problem *p) {
     g.Lt[d] = lt;
     g.T += 2 * lt;
   }
-  if (ctx->plan == DDS_PLAN_TRACE && trace_step_smem(g, 8, sizeof(double2)) > 227 * 1024) {
+  if (ctx->plan == DDS_PLAN_TRACE && g.T >= 65536) {   // trace items pack input indices in 16 bits
     ctx->err = "trace vectors too long for the trace-operator plan (T = " + std::to_string(g.T) + ")";
     return DDS_EINVAL;
   }

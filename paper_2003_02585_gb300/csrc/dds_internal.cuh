@@ -16,6 +16,7 @@
 
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <vector>
 
 namespace dds {
 
@@ -225,26 +226,24 @@ struct TracePanel {
   int sub[8], rhs[8];
 };
 
-// One entry of the trace schedule: the trace solves of sweep l in one dataflow level, as panels
-// of (subdomain, RHS) columns, and their work items.  The items of all entries of a level are
-// dealt round-robin over the CTAs as one list (off = items of the level's earlier entries,
-// level_items = the level's total).
-struct TraceStep {
-  int l, pan_off, npanels, in_mask, out_mask, nout, nseg, nitems;
-  int level, off, level_items;
-};
-int trace_step_items(const Geom &g, int npanels, int in_mask, int out_mask, int *nout, int *nseg);
 size_t trace_counter_bytes(int nlevels);  // level counters of one launch (gbar)
+size_t trace_smem_bytes(size_t elem, int nlevels);
 
-// every trace solve of one DDM application in one cooperative launch (gbar: the level
-// counters, zeroed by the launch)
+// Work items of the cooperative trace launch, 16 bytes each:
+//   x = panel index, y = sweep l | (target slot << 16), z = first input | (inputs << 16),
+//   w = output side | (row tile << 8) | (add the raw own-source lines << 16)
+// trace_items_for appends the items of the sweep-l trace solves of panels [p0, p1).
+void trace_items_for(const Geom &g, const TracePanel *tp, int p0, int p1, int l, const int *route,
+                     int in_mask, std::vector<int4> &out);
+
+// every trace solve of one DDM application in one cooperative launch: level v's items are
+// items[lev_off[v], lev_off[v + 1]) (gbar: the level counters, zeroed by the launch)
 template <typename R>
-cudaError_t launch_trace_sweeps(cudaStream_t st, const Geom &g, const TraceStep *steps, int nsteps,
-                                int nlevels,
-                                const TracePanel *panels,
+cudaError_t launch_trace_sweeps(cudaStream_t st, const Geom &g, const int4 *items, int nitems,
+                                const int *lev_off, int nlevels, const TracePanel *panels,
                                 const typename Cx<R>::T *gmap, typename Cx<R>::T *g_traces,
-                                const typename Cx<R>::T *rawf, const int *route, int nrhs,
-                                unsigned *gbar, int *err, int ctas_per_sm);
+                                const typename Cx<R>::T *rawf, int nrhs, unsigned *gbar, int *err,
+                                int ctas_per_sm);
 
 template <typename R>
 cudaError_t launch_unit_traces(cudaStream_t st, const Geom &g, const Tables &tb, int k0, int nk,
@@ -256,7 +255,6 @@ cudaError_t launch_raw_lines(cudaStream_t st, const Geom &g, int nk, const typen
 
 cudaError_t launch_gmap_backtrace(cudaStream_t st, const Geom &g, double2 *gmap, int f);
 long long gmap_elems(const Geom &g, int nfac);
-size_t trace_step_smem(const Geom &g, int pc, size_t elem);
 cudaError_t launch_convert_c64_c32(cudaStream_t st, const double2 *in, float2 *out, long long n);
 template <typename R>
 cudaError_t launch_copy_local(cudaStream_t st, long long n, const double2 *in,

@@ -212,17 +212,15 @@ __global__ void k_extract(Geom g, const Col *__restrict__ cols,
 }
 
 // ------------------------------------------------------------------------------------------
-// Trace-operator step: for every (sub, rhs) column of the step,
-//   out = Gmap_F * in (+ raw own-source lines in sweep 1),   in = incoming traces of the sweep,
-// routed like k_extract.  Gmap already contains the back-trace correction; acc += in for the
-// final own-node solve.  Only input sides that can receive a trace in this sweep (in_mask) and
-// output sides with a route (out_mask) are touched -- the other terms are exactly zero or
-// unused.
+// Trace operator of every sweep (the trace-transfer form of the sweeps): for every (sub, rhs)
+// column of a sweep-l subdomain solve,
+//   out_d = Gmap_F,d * in (+ the raw own-source lines in the first sweep),
+// where in = the traces received in slot l and out_d goes to the neighbour across side d, into
+// the slot the route names.  Gmap already holds the back-trace correction.  Only output sides
+// with a route and a neighbour, and receiving sides with a neighbour (in_mask), are touched:
+// every other term is exactly zero or unused.
 // Gmap layout per factor: [output side d][row tile of 64][input k = 0..T)[64 rows], rows past
-// 2 Lt_d zero.  A CTA (256 threads) owns one row tile and one panel of PC columns; the tile's
-// rows for the active inputs stream through a two-slot shared-memory ring in chunks of KC
-// inputs (bulk copies on mbarriers).  Thread (r = t & 63, h = t >> 6) owns row r and columns
-// h*PC/4 .. h*PC/4 + PC/4.
+// 2 Lt_d zero, so the rows of one tile for a run of consecutive inputs are one contiguous slice.
 // ------------------------------------------------------------------------------------------
 constexpr int kTraceRows = 64;
 
@@ -244,22 +242,20 @@ __host__ __device__ inline long long gmap_index(const Geom &g, int f, int d, int
 }
 long long gmap_elems(const Geom &g, int nfac) { return gmap_index(g, nfac, 0, 0, 0, 0); }
 
-// The active inputs of a sweep (the sides in in_mask) are cut into segments of at most
-// kTraceSeg consecutive inputs of one side.  A CTA (128 threads) owns one 64-row tile of one
-// output side, one panel of PC = 8 columns and one input segment: its map slice
-// (segment x 64 rows, contiguous in the tiled layout) arrives by one bulk copy while the threads
-// gather the panel's inputs, then thread (rp = t & 31, cq = t >> 5) accumulates rows 2 rp,
-// 2 rp + 1 x columns 2 cq, 2 cq + 1 from shared memory.  Segments of one output add into the
-// destination slot with atomics (the slot accumulates with += in any case).  The CTA has 256
-// threads: two halves share the segment and meet in shared memory.
+// Work items of the cooperative trace launch (built on the host, TraceItem): one output side,
+// one 64-row tile, one panel of up to 8 columns and one segment of at most kTraceSeg consecutive
+// inputs of one receiving side.  A CTA (256 threads) runs an item as
+//   map slice (n inputs x 64 rows) -> shared memory by one bulk copy on an mbarrier,
+//   inputs (n x 8 columns) -> shared memory from L2 (ld.global.cg: written by earlier levels),
+//   four K-groups of 64 threads; thread (row pair rp, column group cg) of a group accumulates
+//   rows 2 rp, 2 rp + 1 x columns 4 cg .. 4 cg + 3 over its quarter of the inputs,
+//   the four partial tiles meet in shared memory; every thread then owns one (column, row pair)
+//   and adds it into the receiver's slot with one vector reduction (segments of one output meet
+//   there; the slot accumulates with += in any case).
+// The next item of the CTA is staged while the current one finishes: its descriptor and panel
+// are fetched during the FMAs, its map-slice copy issued as soon as the slice buffer is free and
+// its inputs loaded while the partial tiles are reduced.
 constexpr int kTraceSeg = 104;
-
-__host__ __device__ inline int trace_nseg(const Geom &g, int in_mask) {
-  int n = 0;
-  for (int d = 0; d < g.nsides; ++d)
-    if ((in_mask >> d) & 1) n += (2 * g.Lt[d] + kTraceSeg - 1) / kTraceSeg;
-  return n;
-}
 
 template <typename C> __device__ inline void atomic_cadd(C *dst, C v);
 template <> __device__ inline void atomic_cadd<float2>(float2 *dst, float2 v) {
@@ -271,9 +267,9 @@ template <> __device__ inline void atomic_cadd<double2>(double2 *dst, double2 v)
   atomicAdd(&dst->y, v.y);
 }
 
-// Step completion counters of the cooperative launch: after its items of step s a CTA adds 1
-// to cnt[8 s + (blockIdx % 8)] (eight words, so arrivals do not all hit one address); a CTA
-// with items in step s + 1 first waits until the eight words of step s sum to gridDim.x.  CTAs
+// Level completion counters of the cooperative launch: after its items of level v a CTA adds 1
+// to cnt[8 v + (blockIdx % 8)] (eight words, so arrivals do not all hit one address); a CTA with
+// items in level v + 1 first waits until the eight words of level v sum to gridDim.x.  CTAs
 // without items never wait.  The counters are zeroed before every launch.  The wait is bounded:
 // on a timeout the CTA records code 4 and goes on (results wrong, launch ends, the host reports
 // DDS_ETIMEOUT).
@@ -315,300 +311,252 @@ __device__ inline void step_wait(const unsigned *cnt, int s, int *err) {
   __syncthreads();
 }
 
-// per-item descriptors staged in shared memory before the item's inputs are ready
+// descriptors of a staged item in shared memory (two buffers: the current item and the next)
 struct TraceItemSmem {
-  long long cbase[8];   // input trace base of each column (-1: no column)
-  int sub[8], rhs[8];
-  int ncol;
+  long long cbase[8];   // input trace base of each column in the trace slots (-1: no column)
+  long long dbase[8];   // output base in the receiver's slot (-1: no receiver)
+  long long rbase[8];   // raw own-source line base of the output side
+  int ncol, n, k0, tile, dout, raw;
 };
 
-// Work item of a trace step: output side dout, 64-row tile `tile`, panel p, input segment
-// [k0, k0 + n).  The map slice is in Gs (bulk copy on `bar`, issued with the descriptors by
-// trace_prep); inputs come from L2 (ld.global.cg: other CTAs of this launch wrote them).
-template <typename R>
-__device__ void trace_item(const Geom &g, typename Cx<R>::T *__restrict__ gtr,
-                           const typename Cx<R>::T *__restrict__ rawf, const int *__restrict__ route,
-                           int l, int nrhs, int dout, int tile, int k0, int n, bool first_seg,
-                           typename Cx<R>::T *Gs, typename Cx<R>::T *vin, uint64_t *bar,
-                           uint32_t phase, const TraceItemSmem &it, int *err) {
-  using C = typename Cx<R>::T;
-  constexpr int PC = 8;
-  constexpr int kPer = (PC * kTraceSeg + 255) / 256;
-  const int T = g.T;
-  const long long slot_stride = (long long)nrhs * g.nsub * T;
-  {
-    C v[kPer];
-#pragma unroll
-    for (int u = 0; u < kPer; ++u) {
-      const int idx = threadIdx.x + u * 256;
-      v[u] = czero<C>();
-      if (idx < PC * kTraceSeg) {
-        const int c = idx / kTraceSeg, kk = idx - c * kTraceSeg;
-        const long long b = it.cbase[c];
-        if (b >= 0 && kk < n) {
-          const C *src = gtr + b + k0 + kk;
-          if constexpr (sizeof(R) == 4) {
-            const float2 t = __ldcg(reinterpret_cast<const float2 *>(src));
-            v[u].x = t.x; v[u].y = t.y;
-          } else {
-            const double2 t = __ldcg(reinterpret_cast<const double2 *>(src));
-            v[u].x = t.x; v[u].y = t.y;
-          }
-        }
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < kPer; ++u) {
-      const int idx = threadIdx.x + u * 256;
-      if (idx < PC * kTraceSeg) vin[idx] = v[u];
-    }
-  }
-  const bool ok = mbar_wait(bar, phase);
-  if (__syncthreads_or(!ok)) {
-    if (threadIdx.x == 0) {
-      atomicExch(err, 3);
-      mbar_wait(bar, phase);
-    }
-    __syncthreads();
-    return;
-  }
-  // two halves of the segment, 128 threads each; thread (rp, cq) of a half: rows 2rp, 2rp+1,
-  // columns 2cq, 2cq+1.  Inputs are consumed four at a time with the next four prefetched.
-  const int half = threadIdx.x >> 7, lt = threadIdx.x & 127;
-  const int rp = lt & 31, cq = lt >> 5;
-  const int nh = ((n + 7) / 8) * 4;                 // inputs of half 0 (a multiple of 4)
-  const int i0 = half == 0 ? 0 : nh, i1 = half == 0 ? min(n, nh) : n;
-  const C *A = Gs + 2 * rp;
-  const C *v0 = vin + (2 * cq) * kTraceSeg;
-  const C *v1 = v0 + kTraceSeg;
-  C o00 = czero<C>(), o01 = czero<C>(), o10 = czero<C>(), o11 = czero<C>();
-  auto step4 = [&](const C (&a)[4][2], const C (&b0)[4], const C (&b1)[4]) {
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      cfma(o00, a[u][0], b0[u]);
-      cfma(o01, a[u][0], b1[u]);
-      cfma(o10, a[u][1], b0[u]);
-      cfma(o11, a[u][1], b1[u]);
-    }
-  };
-  auto load4 = [&](int i, C (&a)[4][2], C (&b0)[4], C (&b1)[4]) {
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      a[u][0] = A[(i + u) * kTraceRows];
-      a[u][1] = A[(i + u) * kTraceRows + 1];
-      b0[u] = v0[i + u];
-      b1[u] = v1[i + u];
-    }
-  };
-  int i = i0;
-  if (i + 4 <= i1) {
-    C a[4][2], b0[4], b1[4];
-    load4(i, a, b0, b1);
-    for (; i + 8 <= i1; i += 4) {
-      C an[4][2], bn0[4], bn1[4];
-      load4(i + 4, an, bn0, bn1);
-      step4(a, b0, b1);
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        a[u][0] = an[u][0];
-        a[u][1] = an[u][1];
-        b0[u] = bn0[u];
-        b1[u] = bn1[u];
-      }
-    }
-    step4(a, b0, b1);
-    i += 4;
-  }
-  for (; i < i1; ++i) {
-    const C a0 = A[i * kTraceRows], a1 = A[i * kTraceRows + 1];
-    cfma(o00, a0, v0[i]);
-    cfma(o01, a0, v1[i]);
-    cfma(o10, a1, v0[i]);
-    cfma(o11, a1, v1[i]);
-  }
-  // half 1 hands its partial sums to half 0 through the input buffer
-  __syncthreads();
-  C *red = vin + (long long)lt * 4;
-  if (half == 1) {
-    red[0] = o00;
-    red[1] = o01;
-    red[2] = o10;
-    red[3] = o11;
-  }
-  __syncthreads();
-  if (half == 0) {
-    o00 = cadd(o00, red[0]);
-    o01 = cadd(o01, red[1]);
-    o10 = cadd(o10, red[2]);
-    o11 = cadd(o11, red[3]);
-    const int rows = 2 * g.Lt[dout];
-    const int lp = route[l * 6 + dout];
-    const int rr = tile * kTraceRows + 2 * rp;     // rows rr, rr + 1 (rows is even)
-    if (rr < rows && lp >= 0) {
-      const int grow = g.toff[dout] + rr;          // row in the full trace vector
-      const C res[2][2] = {{o00, o10}, {o01, o11}}; // [column][row]
-#pragma unroll
-      for (int jj = 0; jj < 2; ++jj) {
-        const int cg = 2 * cq + jj;
-        if (cg >= it.ncol) continue;
-        const int csub_ = it.sub[cg], crhs = it.rhs[cg];
-        C v0r = res[jj][0], v1r = res[jj][1];
-        if (rawf != nullptr && first_seg) {
-          const C *rw = rawf + ((long long)crhs * g.nsub + csub_) * T + grow;
-          v0r = cadd(v0r, rw[0]);
-          v1r = cadd(v1r, rw[1]);
-        }
-        const int nb = sub_neighbour(g, csub_, dout);
-        if (nb < 0) continue;
-        C *dst = gtr + lp * slot_stride + ((long long)crhs * g.nsub + nb) * T + g.toff[dout ^ 1] + rr;
-        if constexpr (sizeof(R) == 4) {
-          // both rows in one 16-byte vector atomic (T, the side offsets and rr are even)
-          red_add_f4(reinterpret_cast<float4 *>(dst), make_float4(v0r.x, v0r.y, v1r.x, v1r.y));
-        } else {
-          atomic_cadd(dst, v0r);
-          atomic_cadd(dst + 1, v1r);
-        }
-      }
-    }
-  }
-  __syncthreads();   // Gs, vin and the descriptors are reused by the next item
+// an item descriptor and its panel's columns, fetched by warp 0 ahead of staging
+struct TracePre {
+  int4 d;
+  int factor, ncol, sub, rhs;   // sub / rhs of column `lane` (lanes < 8)
+};
+
+__device__ inline TracePre trace_fetch(const int4 *__restrict__ items,
+                                       const TracePanel *__restrict__ panels, long long idx) {
+  TracePre p;
+  const int lane = threadIdx.x & 31;
+  p.d = __ldg(items + idx);
+  const TracePanel *tp = panels + p.d.x;
+  p.factor = __ldg(&tp->factor);
+  p.ncol = __ldg(&tp->ncol);
+  p.sub = lane < 8 ? __ldg(&tp->sub[lane]) : 0;
+  p.rhs = lane < 8 ? __ldg(&tp->rhs[lane]) : 0;
+  return p;
 }
 
-// item -> (output side, tile, panel, input segment) of step sd; false if the item is empty
-__device__ inline bool trace_decode(const Geom &g, const TraceStep &sd, int tiles_per_side,
-                                    int item, int &dout, int &tile, int &panel, int &k0, int &n,
-                                    int &seg) {
-  seg = item % sd.nseg;
-  int rest = item / sd.nseg;
-  const int xt = rest % (sd.nout * tiles_per_side);
-  panel = rest / (sd.nout * tiles_per_side);
-  int which = xt / tiles_per_side;
-  tile = xt % tiles_per_side;
-  dout = -1;
-  for (int d = 0; d < g.nsides; ++d)
-    if ((sd.out_mask >> d) & 1) {
-      if (which == 0) { dout = d; break; }
-      --which;
+// warp 0: write the item's descriptors and issue its map-slice copy (a plain arrival for a
+// raw-only item), so that every staged item completes exactly one phase of `bar`
+template <typename C>
+__device__ inline void trace_stage(const Geom &g, const TracePre &p, TraceItemSmem &it, C *Gs,
+                                   uint64_t *bar, const C *__restrict__ gmap,
+                                   long long slot_stride) {
+  const int lane = threadIdx.x & 31;
+  const int l = p.d.y & 0xFFFF, lp = (p.d.y >> 16) & 0xFFFF;
+  const int k0 = p.d.z & 0xFFFF, n = (p.d.z >> 16) & 0xFFFF;
+  const int dout = p.d.w & 0xFF, tile = (p.d.w >> 8) & 0xFF, raw = (p.d.w >> 16) & 1;
+  if (lane == 0) {
+    if (n > 0) {
+      const uint32_t bytes = (uint32_t)(n * kTraceRows * sizeof(C));
+      fence_proxy_async();   // earlier generic reads of Gs before the async write
+      mbar_arrive_expect_tx(bar, bytes);
+      bulk_g2s(Gs, gmap + gmap_index(g, p.factor, dout, tile, k0, 0), bytes, bar);
+    } else {
+      mbar_arrive(bar);
     }
-  if (dout < 0 || tile >= trace_tiles(g, dout)) return false;
-  int sgi = seg;
-  n = 0;
-  for (int d = 0; d < g.nsides; ++d) {
-    if (!((sd.in_mask >> d) & 1)) continue;
-    const int ns = (2 * g.Lt[d] + kTraceSeg - 1) / kTraceSeg;
-    if (sgi < ns) {
-      k0 = g.toff[d] + sgi * kTraceSeg;
-      n = min(kTraceSeg, 2 * g.Lt[d] - sgi * kTraceSeg);
-      break;
-    }
-    sgi -= ns;
+    it.ncol = p.ncol;
+    it.n = n;
+    it.k0 = k0;
+    it.tile = tile;
+    it.dout = dout;
+    it.raw = raw;
   }
-  return n > 0;
+  if (lane < 8) {
+    const bool col = lane < p.ncol;
+    const int nb = col ? sub_neighbour(g, p.sub, dout) : -1;
+    const long long own = (long long)p.rhs * g.nsub + p.sub;
+    it.cbase[lane] = col ? l * slot_stride + own * g.T : -1;
+    it.dbase[lane] = nb >= 0 ? lp * slot_stride + ((long long)p.rhs * g.nsub + nb) * g.T +
+                                   g.toff[dout ^ 1]
+                             : -1;
+    it.rbase[lane] = own * g.T + g.toff[dout];
+  }
+}
+
+// the item's inputs: element (column c, input kk) of thread idx = c * kTraceSeg + kk (runs of
+// one column are contiguous in the slot), stored to vin[kk][c]
+constexpr int kTraceInPer = (8 * kTraceSeg + 255) / 256;
+
+template <typename C>
+__device__ inline void trace_gather_load(const TraceItemSmem &it, const C *gtr,
+                                         C (&v)[kTraceInPer]) {
+#pragma unroll
+  for (int u = 0; u < kTraceInPer; ++u) {
+    const int idx = threadIdx.x + u * 256;
+    v[u] = czero<C>();
+    if (idx < 8 * kTraceSeg) {
+      const int c = idx / kTraceSeg, kk = idx - c * kTraceSeg;
+      const long long b = it.cbase[c];
+      if (b >= 0 && kk < it.n) {
+        const C *src = gtr + b + it.k0 + kk;
+        if constexpr (sizeof(C) == 8) {
+          const float2 t = __ldcg(reinterpret_cast<const float2 *>(src));
+          v[u].x = t.x; v[u].y = t.y;
+        } else {
+          const double2 t = __ldcg(reinterpret_cast<const double2 *>(src));
+          v[u].x = t.x; v[u].y = t.y;
+        }
+      }
+    }
+  }
+}
+template <typename C>
+__device__ inline void trace_gather_store(C *vin, const C (&v)[kTraceInPer]) {
+#pragma unroll
+  for (int u = 0; u < kTraceInPer; ++u) {
+    const int idx = threadIdx.x + u * 256;
+    if (idx < 8 * kTraceSeg) {
+      const int c = idx / kTraceSeg, kk = idx - c * kTraceSeg;
+      vin[kk * 8 + c] = v[u];
+    }
+  }
+}
+
+// two consecutive complex values from shared memory (one 16-byte load in single precision)
+__device__ inline void lds2(const float2 *p, float2 &x, float2 &y) {
+  const float4 t = *reinterpret_cast<const float4 *>(p);
+  x = make_float2(t.x, t.y);
+  y = make_float2(t.z, t.w);
+}
+__device__ inline void lds2(const double2 *p, double2 &x, double2 &y) {
+  x = p[0];
+  y = p[1];
 }
 
 // Every trace solve of one DDM application in one cooperative launch.  The schedule is a list of
 // dataflow levels: a trace solve (sweep l, subdomain X) sits one level below the deepest solve
 // whose traces are routed into its slot l, so every level only reads slots that earlier levels
-// completed.  The items of a level are dealt round-robin over the CTAs; a CTA with items in
-// level v first waits until every CTA is done with level v - 1 (counters above).  The step
-// table sits in shared memory; the descriptors and map slice of a CTA's first item of the next
-// level depend on no trace and are staged before that wait.
-constexpr int kMaxSmemSteps = 384;
+// completed.  The items of level v are items[lev_off[v] .. lev_off[v + 1]), heaviest first;
+// CTA b takes positions b, 2G - 1 - b, 2G + b, ... (a snake over the G CTAs).  A CTA with items
+// in level v first waits until every CTA is done with level v - 1 (counters above); the
+// descriptors and map slice of its first item depend on no trace and are staged before that wait.
+constexpr int kMaxSmemLevels = 1024;
 
 template <typename R>
-__global__ void __launch_bounds__(256) k_trace_sweeps(Geom g, const TraceStep *__restrict__ steps,
-                                                      int nsteps,
-                                                      const TracePanel *__restrict__ panels,
-                                                      const typename Cx<R>::T *__restrict__ gmap,
-                                                      typename Cx<R>::T *__restrict__ gtr,
-                                                      const typename Cx<R>::T *__restrict__ rawf,
-                                                      const int *__restrict__ route, int nrhs,
-                                                      int tiles_per_side, unsigned *cnt,
-                                                      int *__restrict__ err) {
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
+    k_trace_sweeps(Geom g, const int4 *__restrict__ items, const int *__restrict__ lev_off,
+                   int nlev, const TracePanel *__restrict__ panels,
+                   const typename Cx<R>::T *__restrict__ gmap, typename Cx<R>::T *__restrict__ gtr,
+                   const typename Cx<R>::T *__restrict__ rawf, int nrhs, unsigned *cnt,
+                   int *__restrict__ err) {
   using C = typename Cx<R>::T;
-  constexpr int PC = 8;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  C *Gs = reinterpret_cast<C *>(smem_raw);                   // map slice [k][64]
-  C *vin = Gs + kTraceSeg * kTraceRows;                      // inputs [col][k]
-  uint64_t *bar = reinterpret_cast<uint64_t *>(vin + PC * kTraceSeg);
-  TraceStep *st_s = reinterpret_cast<TraceStep *>(bar + 2);  // schedule (nsteps <= kMaxSmemSteps)
-  __shared__ TraceItemSmem it;
-  const bool smem_steps = nsteps <= kMaxSmemSteps;
-  for (int i = threadIdx.x; smem_steps && i < nsteps; i += blockDim.x) st_s[i] = steps[i];
+  C *Gs = reinterpret_cast<C *>(smem_raw);            // map slice [k][64 rows]
+  C *vin = Gs + kTraceSeg * kTraceRows;               // inputs [k][8 columns]
+  C *red = vin + 8 * kTraceSeg;                       // partial tiles [K-group][col][row pair][2]
+  uint64_t *bar = reinterpret_cast<uint64_t *>(red + 4 * 8 * 64);
+  int *lo_s = reinterpret_cast<int *>(bar + 2);       // level offsets (nlev < kMaxSmemLevels)
+  __shared__ TraceItemSmem its[2];
+  const bool lv_smem = nlev < kMaxSmemLevels;
+  for (int i = threadIdx.x; lv_smem && i <= nlev; i += blockDim.x) lo_s[i] = lev_off[i];
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
     mbar_init_fence();
   }
   __syncthreads();
-  auto step_at = [&](int e) { return smem_steps ? st_s[e] : steps[e]; };
+  auto lev = [&](int v) { return lv_smem ? lo_s[v] : __ldg(lev_off + v); };
+  const int G = (int)gridDim.x, b = (int)blockIdx.x, tid = threadIdx.x, warp = tid >> 5;
+  auto pos = [&](int r) { return r * G + ((r & 1) ? G - 1 - b : b); };
   const long long slot_stride = (long long)nrhs * g.nsub * g.T;
-  const int G = (int)gridDim.x, b = (int)blockIdx.x;
+  // compute roles: K-group kg, row pair rp, column group cg; epilogue: column ec, row pair rp
+  const int kg = tid >> 6, rp = tid & 31, cg = (tid >> 5) & 1, ec = tid >> 5;
+  int s = 0;
   uint32_t phase = 0;
-  // stage the descriptors and issue the map-slice copy (all threads call; ends with a barrier)
-  auto prep = [&](const TraceStep &sd, int panel, int dout, int tile, int k0, int n) {
-    const TracePanel *tp = panels + sd.pan_off + panel;
-    if (threadIdx.x == 0) {
-      const uint32_t bytes = (uint32_t)(n * kTraceRows * sizeof(C));
-      fence_proxy_async();   // earlier generic reads of Gs before the async write
-      mbar_arrive_expect_tx(bar, bytes);
-      bulk_g2s(Gs, gmap + gmap_index(g, tp->factor, dout, tile, k0, 0), bytes, bar);
-      it.ncol = tp->ncol;
-    }
-    if (threadIdx.x < PC) {
-      const int c = threadIdx.x;
-      const int sub = tp->sub[c], rhs = tp->rhs[c];
-      it.sub[c] = sub;
-      it.rhs[c] = rhs;
-      it.cbase[c] = c < tp->ncol ? sd.l * slot_stride + ((long long)rhs * g.nsub + sub) * g.T : -1;
+  TracePre pre;
+  for (int v = 0; v < nlev; ++v) {
+    const int base = lev(v), Nv = lev(v + 1) - base;
+    if (v > 0) step_arrive(cnt, v - 1);
+    if (pos(0) >= Nv) continue;
+    if (warp == 0) {
+      pre = trace_fetch(items, panels, base + pos(0));
+      trace_stage<C>(g, pre, its[s], Gs, bar, gmap, slot_stride);
     }
     __syncthreads();
-  };
-  // the entry and item of this CTA's first work in the level starting at entry e0 (or -1)
-  auto first_in_level = [&](int e0, int &item) {
-    const TraceStep s0 = step_at(e0);
-    if (b >= s0.level_items) return -1;
-    for (int e = e0; e < nsteps; ++e) {
-      const TraceStep se = step_at(e);
-      if (se.level != s0.level) break;
-      if (b >= se.off && b < se.off + se.nitems) { item = b - se.off; return e; }
+    if (v > 0) step_wait(cnt, v - 1, err);
+    {
+      C x[kTraceInPer];
+      trace_gather_load<C>(its[s], gtr, x);
+      trace_gather_store<C>(vin, x);
     }
-    return -1;
-  };
-  int pre_e = -1, pre_item = -1;   // staged item (descriptors + map slice in flight)
-  int level = -1;
-  for (int e = 0; e < nsteps; ++e) {
-    const TraceStep sd = step_at(e);
-    if (sd.level != level) {
-      if (level >= 0) {
-        step_arrive(cnt, level);
-        // stage this CTA's first item of the new level, then wait for the previous level
-        int item = -1;
-        const int ef = first_in_level(e, item);
-        if (ef >= 0) {
-          const TraceStep sf = step_at(ef);
-          int dout, tile, panel, k0, n, seg;
-          if (trace_decode(g, sf, tiles_per_side, item, dout, tile, panel, k0, n, seg)) {
-            prep(sf, panel, dout, tile, k0, n);
-            pre_e = ef;
-            pre_item = item;
+    __syncthreads();
+    for (int r = 0; pos(r) < Nv; ++r) {
+      const TraceItemSmem &it = its[s];
+      const bool next = pos(r + 1) < Nv;
+      if (next && warp == 0) pre = trace_fetch(items, panels, base + pos(r + 1));
+      const bool ok = mbar_wait(bar, phase);
+      if (__syncthreads_or(!ok) && tid == 0) {
+        atomicExch(err, 3);
+        mbar_wait(bar, phase);   // bounded second wait for the copy in flight
+      }
+      // partial tile of K-group kg over its quarter of the n inputs
+      C acc[2][4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[0][j] = acc[1][j] = czero<C>();
+      {
+        const int n = it.n, nq = (n + 3) >> 2;
+        const int i0 = min(n, kg * nq), i1 = min(n, i0 + nq);
+        const C *A = Gs + 2 * rp;
+        const C *B = vin + 4 * cg;
+#pragma unroll 4
+        for (int i = i0; i < i1; ++i) {
+          C a0, a1, b0, b1, b2, b3;
+          lds2(A + i * kTraceRows, a0, a1);
+          lds2(B + i * 8, b0, b1);
+          lds2(B + i * 8 + 2, b2, b3);
+          cfma(acc[0][0], a0, b0); cfma(acc[0][1], a0, b1);
+          cfma(acc[0][2], a0, b2); cfma(acc[0][3], a0, b3);
+          cfma(acc[1][0], a1, b0); cfma(acc[1][1], a1, b1);
+          cfma(acc[1][2], a1, b2); cfma(acc[1][3], a1, b3);
+        }
+      }
+      __syncthreads();   // Gs and vin are free
+      if (next && warp == 0) trace_stage<C>(g, pre, its[s ^ 1], Gs, bar, gmap, slot_stride);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        C *p = red + (((kg * 8 + 4 * cg + j) * 32 + rp) << 1);
+        p[0] = acc[0][j];
+        p[1] = acc[1][j];
+      }
+      __syncthreads();   // partial tiles and the next item's descriptors are in place
+      C x[kTraceInPer];
+      if (next) trace_gather_load<C>(its[s ^ 1], gtr, x);
+      {
+        C o0 = czero<C>(), o1 = czero<C>();
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          C u0, u1;
+          lds2(red + (((q * 8 + ec) * 32 + rp) << 1), u0, u1);
+          o0 = cadd(o0, u0);
+          o1 = cadd(o1, u1);
+        }
+        const int rr = it.tile * kTraceRows + 2 * rp;   // rows rr, rr + 1 (2 Lt is even)
+        const long long db = it.dbase[ec];
+        if (ec < it.ncol && db >= 0 && rr < 2 * g.Lt[it.dout]) {
+          if (it.raw) {
+            const C *rw = rawf + it.rbase[ec] + rr;
+            o0 = cadd(o0, rw[0]);
+            o1 = cadd(o1, rw[1]);
+          }
+          C *dst = gtr + db + rr;
+          if constexpr (sizeof(R) == 4) {
+            // both rows in one 16-byte vector reduction (T, the side offsets and rr are even)
+            red_add_f4(reinterpret_cast<float4 *>(dst), make_float4(o0.x, o0.y, o1.x, o1.y));
+          } else {
+            atomic_cadd(dst, o0);
+            atomic_cadd(dst + 1, o1);
           }
         }
-        if (b < sd.level_items) step_wait(cnt, level, err);
       }
-      level = sd.level;
-    }
-    // this CTA's items of entry e: global level index off + item = b (mod G)
-    int item = ((b - sd.off) % G + G) % G;
-    for (; item < sd.nitems; item += G) {
-      int dout, tile, panel, k0, n, seg;
-      if (!trace_decode(g, sd, tiles_per_side, item, dout, tile, panel, k0, n, seg)) continue;
-      if (!(e == pre_e && item == pre_item)) prep(sd, panel, dout, tile, k0, n);
-      trace_item<R>(g, gtr, sd.l == 0 ? rawf : nullptr, route, sd.l, nrhs, dout, tile, k0, n,
-                    seg == 0, Gs, vin, bar, phase, it, err);
+      if (next) trace_gather_store<C>(vin, x);
+      __syncthreads();   // vin holds the next inputs; red and its[s] are free
+      s ^= 1;
       phase ^= 1u;
     }
   }
-  // a staged item is always consumed by its level, so no copy is in flight here
+  // every staged item is consumed in its level, so no copy is in flight here
 }
 
 // ------------------------------------------------------------------------------------------
@@ -744,14 +692,13 @@ cudaError_t launch_extract(cudaStream_t st, const Geom &g, int ncols, const Col 
 }
 
 template <typename R>
-cudaError_t launch_trace_sweeps(cudaStream_t st, const Geom &g, const TraceStep *steps, int nsteps,
-                                int nlevels, const TracePanel *panels,
+cudaError_t launch_trace_sweeps(cudaStream_t st, const Geom &g, const int4 *items, int nitems,
+                                const int *lev_off, int nlevels, const TracePanel *panels,
                                 const typename Cx<R>::T *gmap, typename Cx<R>::T *gtr,
-                                const typename Cx<R>::T *rawf, const int *route, int nrhs,
-                                unsigned *gbar, int *err, int ctas_per_sm) {
-  if (nsteps <= 0) return cudaSuccess;
-  using C = typename Cx<R>::T;
-  const size_t smem = trace_step_smem(g, 8, sizeof(C));
+                                const typename Cx<R>::T *rawf, int nrhs, unsigned *gbar, int *err,
+                                int ctas_per_sm) {
+  if (nitems <= 0 || nlevels <= 0) return cudaSuccess;
+  const size_t smem = trace_smem_bytes(sizeof(typename Cx<R>::T), nlevels);
   static bool done[64] = {false};
   cudaError_t e = smem_limit_once(k_trace_sweeps<R>, done);
   if (e != cudaSuccess) return e;
@@ -774,24 +721,51 @@ cudaError_t launch_trace_sweeps(cudaStream_t st, const Geom &g, const TraceStep 
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_trace_sweeps<R>, g, steps, nsteps, panels, gmap, gtr,
-                            rawf, route, nrhs, trace_max_tiles(g), gbar, err);
+  return cudaLaunchKernelEx(&cfg, k_trace_sweeps<R>, g, items, lev_off, nlevels, panels, gmap, gtr,
+                            rawf, nrhs, gbar, err);
 }
 
 size_t trace_counter_bytes(int nlevels) { return (size_t)nlevels * kStepCounters * sizeof(unsigned); }
 
-int trace_step_items(const Geom &g, int npanels, int in_mask, int out_mask, int *nout, int *nseg) {
-  int no = 0;
-  for (int d = 0; d < g.nsides; ++d) no += (out_mask >> d) & 1;
-  const int ns = trace_nseg(g, in_mask);
-  if (nout) *nout = no;
-  if (nseg) *nseg = ns;
-  return no * trace_max_tiles(g) * npanels * ns;
+size_t trace_smem_bytes(size_t elem, int nlevels) {
+  size_t b = ((size_t)kTraceSeg * kTraceRows + 8 * kTraceSeg + 4 * 8 * 64) * elem + 16;
+  if (nlevels < kMaxSmemLevels) b += (size_t)(nlevels + 1) * sizeof(int);
+  return b;
 }
 
-size_t trace_step_smem(const Geom &, int pc, size_t elem) {
-  return ((size_t)kTraceSeg * kTraceRows + (size_t)pc * kTraceSeg) * elem + 16 +
-         (size_t)kMaxSmemSteps * sizeof(TraceStep);
+// Items of the sweep-l trace solves of the panels tp[p0, p1): per panel, every output side with a
+// route and a neighbour of some column, every 64-row tile of it and every input segment of the
+// receiving sides (in_mask) that have a neighbour of some column; a side's 2 Lt inputs are cut
+// into the fewest segments of at most kTraceSeg, of equal length.  In the first sweep one item
+// per output tile also adds the raw own-source lines (an input-free item if nothing is received).
+void trace_items_for(const Geom &g, const TracePanel *tp, int p0, int p1, int l, const int *route,
+                     int in_mask, std::vector<int4> &out) {
+  for (int p = p0; p < p1; ++p) {
+    const TracePanel &pn = tp[p];
+    auto any_nb = [&](int d) {
+      for (int c = 0; c < pn.ncol; ++c)
+        if (sub_neighbour(g, pn.sub[c], d) >= 0) return true;
+      return false;
+    };
+    for (int dout = 0; dout < g.nsides; ++dout) {
+      const int lp = route[l * 6 + dout];
+      if (lp < 0 || !any_nb(dout)) continue;
+      for (int tile = 0; tile < trace_tiles(g, dout); ++tile) {
+        int raw = l == 0 ? 1 : 0;
+        for (int sd = 0; sd < g.nsides; ++sd) {
+          if (!((in_mask >> sd) & 1) || !any_nb(sd)) continue;
+          const int len = 2 * g.Lt[sd], ns = (len + kTraceSeg - 1) / kTraceSeg;
+          for (int j = 0; j < ns; ++j) {
+            const int a = j * len / ns, e = (j + 1) * len / ns;
+            out.push_back(make_int4(p, l | (lp << 16), (g.toff[sd] + a) | ((e - a) << 16),
+                                    dout | (tile << 8) | (raw << 16)));
+            raw = 0;
+          }
+        }
+        if (raw) out.push_back(make_int4(p, l | (lp << 16), 0, dout | (tile << 8) | (1 << 16)));
+      }
+    }
+  }
 }
 
 template <typename R>
@@ -842,10 +816,10 @@ cudaError_t launch_copy_local_back(cudaStream_t st, long long n, const typename 
   template cudaError_t launch_extract<R>(cudaStream_t, const Geom &, int, const Col *,         \
                                          const Cx<R>::T *, double2 *, int, Cx<R>::T *,         \
                                          Cx<R>::T *, const int *, int, int);                    \
-  template cudaError_t launch_trace_sweeps<R>(cudaStream_t, const Geom &, const TraceStep *,   \
-                                              int, int, const TracePanel *,                     \
+  template cudaError_t launch_trace_sweeps<R>(cudaStream_t, const Geom &, const int4 *, int,    \
+                                              const int *, int, const TracePanel *,             \
                                               const Cx<R>::T *, Cx<R>::T *, const Cx<R>::T *,  \
-                                              const int *, int, unsigned *, int *, int);        \
+                                              int, unsigned *, int *, int);                     \
   template cudaError_t launch_unit_traces<R>(cudaStream_t, const Geom &, const Tables &, int,  \
                                              int, Cx<R>::T *);                                  \
   template cudaError_t launch_raw_lines<R>(cudaStream_t, const Geom &, int, const Cx<R>::T *,  \
