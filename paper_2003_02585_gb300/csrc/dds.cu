@@ -60,7 +60,7 @@ struct CallPlan {            // all launch lists for one nrhs
   std::vector<StepPlan> tsteps;  // [dir][step] for the trace plan (trace-step panels)
   StepPlan all;                  // every (sub, rhs) column (trace plan phases, local solves)
   DBuf cols, panels, tpanels;
-  struct TraceTable { int n = -1, nlev = 0; DBuf buf, levs, tpan; };   // items, level offsets
+  struct TraceTable { int n = -1, nlev = 0; DBuf buf, cols, levs; };   // items, level offsets
   std::map<int, TraceTable> trace_steps;   // rounds -> item lists of the cooperative launch
 };
 
@@ -468,8 +468,9 @@ dds_status check_errflag(dds_ctx *ctx) {
 // those producers (0 without any), computed in sweep and step order.  Per level and sweep one
 // entry holds that sweep's subdomains of the level, as panels of 8 (subdomain, RHS) columns of
 // one factor.  Returns the number of levels.
-int build_trace_schedule(dds_ctx *ctx, int nrhs, int rounds, std::vector<int4> &items,
-                         std::vector<int> &lev_off, std::vector<TracePanel> &tp) {
+int build_trace_schedule(dds_ctx *ctx, int nrhs, int rounds, std::vector<TraceItem> &items,
+                         std::vector<int> &lev_off) {
+  std::vector<TracePanel> tp;
   const Geom &g = ctx->g;
   const int L = ctx->ndirs * rounds, ns = g.nsub;
   const std::vector<int> route = build_route(g.dim, rounds);
@@ -521,8 +522,8 @@ int build_trace_schedule(dds_ctx *ctx, int nrhs, int rounds, std::vector<int4> &
                       items);
     }
     // heaviest items first (input count), so that the snake deal over the CTAs balances
-    std::stable_sort(items.begin() + first, items.end(), [](const int4 &a, const int4 &b) {
-      return ((a.z >> 16) & 0xFFFF) > ((b.z >> 16) & 0xFFFF);
+    std::stable_sort(items.begin() + first, items.end(), [](const TraceItem &a, const TraceItem &b) {
+      return ((a.h.z >> 16) & 0xFFFF) > ((b.h.z >> 16) & 0xFFFF);
     });
   }
   lev_off.push_back((int)items.size());
@@ -549,14 +550,23 @@ dds_status prepare_ddm(dds_ctx *ctx, int nrhs, int rounds, bool *grown) {
   if (trace_plan) {
     // schedule of the cooperative trace launch (uploaded outside any stream capture)
     auto &tt = cp->trace_steps[rounds];
+    if (tt.n < 0 && (long long)nrhs * g.nsub > INT32_MAX) {   // item column words are 32-bit
+      ctx->err = "trace-operator plan: right-hand sides x subdomains exceed 2^31";
+      return DDS_EINVAL;
+    }
     if (tt.n < 0) {
-      std::vector<int4> items;
+      std::vector<TraceItem> items;
       std::vector<int> lev;
-      std::vector<TracePanel> tp;
-      tt.nlev = build_trace_schedule(ctx, nrhs, rounds, items, lev, tp);
-      CK(upload(tt.buf, items, ctx->stream));
+      tt.nlev = build_trace_schedule(ctx, nrhs, rounds, items, lev);
+      std::vector<int4> hdr(items.size());
+      std::vector<int2> cw(items.size() * 8);
+      for (size_t i = 0; i < items.size(); ++i) {
+        hdr[i] = items[i].h;
+        for (int c = 0; c < 8; ++c) cw[i * 8 + c] = items[i].col[c];
+      }
+      CK(upload(tt.buf, hdr, ctx->stream));
+      CK(upload(tt.cols, cw, ctx->stream));
       CK(upload(tt.levs, lev, ctx->stream));
-      CK(upload(tt.tpan, tp, ctx->stream));
       tt.n = (int)items.size();
       void *gb0 = ctx->gbar.p;
       CK(ctx->gbar.ensure(trace_counter_bytes(std::max(tt.nlev, 1))));
@@ -641,10 +651,9 @@ dds_status run_ddm(dds_ctx *ctx, const double2 *b, int nrhs, double2 *u, int rou
       return DDS_EINVAL;
     }
     const CallPlan::TraceTable &tt = tti->second;
-    LAUNCHK(DDS_K_TRACE_STEP, launch_trace_sweeps<R>(st, g, tt.buf.as<int4>(), tt.n,
-                                                     tt.levs.as<int>(), tt.nlev,
-                                                     tt.tpan.as<TracePanel>(), gmap, gtr, rawf,
-                                                     nrhs, ctx->gbar.as<unsigned>(),
+    LAUNCHK(DDS_K_TRACE_STEP, launch_trace_sweeps<R>(st, g, tt.buf.as<int4>(), tt.cols.as<int2>(),
+                                                     tt.n, tt.levs.as<int>(), tt.nlev, gmap, gtr,
+                                                     rawf, nrhs, ctx->gbar.as<unsigned>(),
                                                      ctx->errflag.as<int>(), ctx->trace_per_sm));
     // own nodes: u = A_R^{-1}(b_own + potentials of all traces received in every sweep)
     LAUNCHK(DDS_K_ASSEMBLE, launch_assemble<R>(st, g, ctx->tb, all.ncols, cols + all.col_off, work, b, nullptr, 1,

@@ -229,18 +229,26 @@ struct TracePanel {
 size_t trace_counter_bytes(int nlevels);  // level counters of one launch (gbar)
 size_t trace_smem_bytes(size_t elem, int nlevels);
 
-// Work items of the cooperative trace launch, 16 bytes each:
-//   x = panel index, y = sweep l | (target slot << 16), z = first input | (inputs << 16),
-//   w = output side | (row tile << 8) | (add the raw own-source lines << 16)
-// trace_items_for appends the items of the sweep-l trace solves of panels [p0, p1).
+// Work items of the cooperative trace launch (80 bytes each):
+//   h.x = factor | (columns << 24), h.y = sweep l | (target slot << 16),
+//   h.z = first input | (inputs << 16), h.w = output side | (row tile << 8) | (raw << 16)
+//   col[c] = (RHS * nsub + subdomain of column c, RHS * nsub + its neighbour across the output
+//            side or -1), (-1, -1) past the last column
+// (raw: add the raw own-source lines).  trace_items_for appends the items of the sweep-l trace
+// solves of panels [p0, p1).
+struct TraceItem {
+  int4 h;
+  int2 col[8];
+};
 void trace_items_for(const Geom &g, const TracePanel *tp, int p0, int p1, int l, const int *route,
-                     int in_mask, std::vector<int4> &out);
+                     int in_mask, std::vector<TraceItem> &out);
 
 // every trace solve of one DDM application in one cooperative launch: level v's items are
-// items[lev_off[v], lev_off[v + 1]) (gbar: the level counters, zeroed by the launch)
+// records lev_off[v] .. lev_off[v + 1] - 1 of hdr (headers) and cols (8 column pairs each);
+// gbar: the level counters, zeroed by the launch
 template <typename R>
-cudaError_t launch_trace_sweeps(cudaStream_t st, const Geom &g, const int4 *items, int nitems,
-                                const int *lev_off, int nlevels, const TracePanel *panels,
+cudaError_t launch_trace_sweeps(cudaStream_t st, const Geom &g, const int4 *hdr, const int2 *cols,
+                                int nitems, const int *lev_off, int nlevels,
                                 const typename Cx<R>::T *gmap, typename Cx<R>::T *g_traces,
                                 const typename Cx<R>::T *rawf, int nrhs, unsigned *gbar, int *err,
                                 int ctas_per_sm);

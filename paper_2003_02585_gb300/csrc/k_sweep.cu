@@ -311,108 +311,85 @@ __device__ inline void step_wait(const unsigned *cnt, int s, int *err) {
   __syncthreads();
 }
 
-// descriptors of a staged item in shared memory (two buffers: the current item and the next)
+// descriptors of a staged item in shared memory (three buffers: the item in flight, the next
+// one, whose inputs are loaded during the current FMAs, and the one after, written meanwhile)
 struct TraceItemSmem {
   long long cbase[8];   // input trace base of each column in the trace slots (-1: no column)
   long long dbase[8];   // output base in the receiver's slot (-1: no receiver)
   long long rbase[8];   // raw own-source line base of the output side
-  int ncol, n, k0, tile, dout, raw;
+  int factor, ncol, n, k0, tile, dout, raw, pad;
 };
 
-// an item descriptor and its panel's columns, fetched by warp 0 ahead of staging
+// an item record, fetched by warp 0 one item ahead of its staging: the header (every lane) and
+// the column pair of lane c < 8 (independent loads, no chain)
 struct TracePre {
-  int4 d;
-  int factor, ncol, sub, rhs;   // sub / rhs of column `lane` (lanes < 8)
+  int4 h;
+  int2 col;
 };
 
-__device__ inline TracePre trace_fetch(const int4 *__restrict__ items,
-                                       const TracePanel *__restrict__ panels, long long idx) {
+__device__ inline TracePre trace_fetch(const int4 *__restrict__ hdr, const int2 *__restrict__ cols,
+                                       long long idx) {
   TracePre p;
   const int lane = threadIdx.x & 31;
-  p.d = __ldg(items + idx);
-  const TracePanel *tp = panels + p.d.x;
-  p.factor = __ldg(&tp->factor);
-  p.ncol = __ldg(&tp->ncol);
-  p.sub = lane < 8 ? __ldg(&tp->sub[lane]) : 0;
-  p.rhs = lane < 8 ? __ldg(&tp->rhs[lane]) : 0;
+  p.h = __ldg(hdr + idx);
+  p.col = lane < 8 ? __ldg(cols + idx * 8 + lane) : make_int2(-1, -1);
   return p;
 }
 
-// warp 0: write the item's descriptors and issue its map-slice copy (a plain arrival for a
-// raw-only item), so that every staged item completes exactly one phase of `bar`
-template <typename C>
-__device__ inline void trace_stage(const Geom &g, const TracePre &p, TraceItemSmem &it, C *Gs,
-                                   uint64_t *bar, const C *__restrict__ gmap,
-                                   long long slot_stride) {
+// warp 0: write an item's descriptors (no copy yet)
+__device__ inline void trace_describe(const Geom &g, const TracePre &p, TraceItemSmem &it,
+                                      long long slot_stride) {
   const int lane = threadIdx.x & 31;
-  const int l = p.d.y & 0xFFFF, lp = (p.d.y >> 16) & 0xFFFF;
-  const int k0 = p.d.z & 0xFFFF, n = (p.d.z >> 16) & 0xFFFF;
-  const int dout = p.d.w & 0xFF, tile = (p.d.w >> 8) & 0xFF, raw = (p.d.w >> 16) & 1;
+  const int l = p.h.y & 0xFFFF, lp = (p.h.y >> 16) & 0xFFFF;
+  const int dout = p.h.w & 0xFF;
   if (lane == 0) {
-    if (n > 0) {
-      const uint32_t bytes = (uint32_t)(n * kTraceRows * sizeof(C));
-      fence_proxy_async();   // earlier generic reads of Gs before the async write
-      mbar_arrive_expect_tx(bar, bytes);
-      bulk_g2s(Gs, gmap + gmap_index(g, p.factor, dout, tile, k0, 0), bytes, bar);
-    } else {
-      mbar_arrive(bar);
-    }
-    it.ncol = p.ncol;
-    it.n = n;
-    it.k0 = k0;
-    it.tile = tile;
+    it.factor = p.h.x & 0xFFFFFF;
+    it.ncol = (p.h.x >> 24) & 0xFF;
+    it.k0 = p.h.z & 0xFFFF;
+    it.n = (p.h.z >> 16) & 0xFFFF;
     it.dout = dout;
-    it.raw = raw;
+    it.tile = (p.h.w >> 8) & 0xFF;
+    it.raw = (p.h.w >> 16) & 1;
   }
   if (lane < 8) {
-    const bool col = lane < p.ncol;
-    const int nb = col ? sub_neighbour(g, p.sub, dout) : -1;
-    const long long own = (long long)p.rhs * g.nsub + p.sub;
-    it.cbase[lane] = col ? l * slot_stride + own * g.T : -1;
-    it.dbase[lane] = nb >= 0 ? lp * slot_stride + ((long long)p.rhs * g.nsub + nb) * g.T +
-                                   g.toff[dout ^ 1]
-                             : -1;
-    it.rbase[lane] = own * g.T + g.toff[dout];
+    const int own = p.col.x, nbo = p.col.y;   // (RHS, subdomain) column / its receiver
+    it.cbase[lane] = own >= 0 ? l * slot_stride + (long long)own * g.T : -1;
+    it.dbase[lane] = nbo >= 0 ? lp * slot_stride + (long long)nbo * g.T + g.toff[dout ^ 1] : -1;
+    it.rbase[lane] = (long long)own * g.T + g.toff[dout];
   }
 }
 
-// the item's inputs: element (column c, input kk) of thread idx = c * kTraceSeg + kk (runs of
-// one column are contiguous in the slot), stored to vin[kk][c]
-constexpr int kTraceInPer = (8 * kTraceSeg + 255) / 256;
-
+// thread 0: issue the map-slice copy of a described item (a plain arrival for a raw-only item),
+// so that every item completes exactly one phase of `bar`
 template <typename C>
-__device__ inline void trace_gather_load(const TraceItemSmem &it, const C *gtr,
-                                         C (&v)[kTraceInPer]) {
-#pragma unroll
-  for (int u = 0; u < kTraceInPer; ++u) {
-    const int idx = threadIdx.x + u * 256;
-    v[u] = czero<C>();
-    if (idx < 8 * kTraceSeg) {
-      const int c = idx / kTraceSeg, kk = idx - c * kTraceSeg;
-      const long long b = it.cbase[c];
-      if (b >= 0 && kk < it.n) {
-        const C *src = gtr + b + it.k0 + kk;
-        if constexpr (sizeof(C) == 8) {
-          const float2 t = __ldcg(reinterpret_cast<const float2 *>(src));
-          v[u].x = t.x; v[u].y = t.y;
-        } else {
-          const double2 t = __ldcg(reinterpret_cast<const double2 *>(src));
-          v[u].x = t.x; v[u].y = t.y;
-        }
-      }
-    }
+__device__ inline void trace_copy(const Geom &g, const TraceItemSmem &it, C *Gs, uint64_t *bar,
+                                  const C *__restrict__ gmap) {
+  if (it.n > 0) {
+    const uint32_t bytes = (uint32_t)(it.n * kTraceRows * sizeof(C));
+    fence_proxy_async();   // earlier generic reads of Gs before the async write
+    mbar_arrive_expect_tx(bar, bytes);
+    bulk_g2s(Gs, gmap + gmap_index(g, it.factor, it.dout, it.tile, it.k0, 0), bytes, bar);
+  } else {
+    mbar_arrive(bar);
   }
 }
+
+// the item's inputs, copied asynchronously (cp.async, zero fill for missing columns and past n):
+// element (column c, input kk) of thread idx = c * kTraceSeg + kk (runs of one column are
+// contiguous in the slot) goes to vin[kk][c]; the caller commits and waits
 template <typename C>
-__device__ inline void trace_gather_store(C *vin, const C (&v)[kTraceInPer]) {
-#pragma unroll
-  for (int u = 0; u < kTraceInPer; ++u) {
-    const int idx = threadIdx.x + u * 256;
-    if (idx < 8 * kTraceSeg) {
-      const int c = idx / kTraceSeg, kk = idx - c * kTraceSeg;
-      vin[kk * 8 + c] = v[u];
-    }
+__device__ inline void trace_gather(const TraceItemSmem &it, const C *gtr, C *vin) {
+  for (int idx = threadIdx.x; idx < 8 * kTraceSeg; idx += 256) {
+    const int c = idx / kTraceSeg, kk = idx - c * kTraceSeg;
+    const long long b = it.cbase[c];
+    const bool live = b >= 0 && kk < it.n;
+    const C *src = live ? gtr + b + it.k0 + kk : gtr;
+    if constexpr (sizeof(C) == 8)
+      cp_async8(vin + kk * 8 + c, src, live ? 8u : 0u);
+    else
+      cp_async16(vin + kk * 8 + c, src, live ? 16u : 0u);
   }
+  cp_async_commit();
 }
 
 // two consecutive complex values from shared memory (one 16-byte load in single precision)
@@ -426,30 +403,90 @@ __device__ inline void lds2(const double2 *p, double2 &x, double2 &y) {
   y = p[1];
 }
 
+// Partial tile of K-group kg: rows 2 rp, 2 rp + 1 (A = map slice + 2 rp, row stride 64) times
+// columns 4 cg .. 4 cg + 3 (B = inputs + 4 cg, input stride 8) over the group's quarter of the n
+// inputs.  Single precision runs on packed two-lane FMAs: per (row, column)
+//   P += (a.re, a.re) * (b.re, b.im),   Q += (a.im, a.im) * (b.im, b.re),
+//   a b = (P.re - Q.re, P.im + Q.im),
+// which halves the FMA instructions issued against four scalar FMAs per complex product.
+__device__ inline void trace_tile_fma(const float2 *A, const float2 *B, int n, int kg,
+                                      float2 (&acc)[2][4]) {
+  const int nq = (n + 3) >> 2;
+  const int i0 = min(n, kg * nq), i1 = min(n, i0 + nq);
+  float2 P[2][4], Q[2][4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) P[0][j] = P[1][j] = Q[0][j] = Q[1][j] = make_float2(0.f, 0.f);
+#pragma unroll 4
+  for (int i = i0; i < i1; ++i) {
+    float2 a0, a1, b[4];
+    lds2(A + i * kTraceRows, a0, a1);
+    lds2(B + i * 8, b[0], b[1]);
+    lds2(B + i * 8 + 2, b[2], b[3]);
+    const float2 a0r = make_float2(a0.x, a0.x), a0i = make_float2(a0.y, a0.y);
+    const float2 a1r = make_float2(a1.x, a1.x), a1i = make_float2(a1.y, a1.y);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float2 bs = make_float2(b[j].y, b[j].x);
+      P[0][j] = __ffma2_rn(a0r, b[j], P[0][j]);
+      Q[0][j] = __ffma2_rn(a0i, bs, Q[0][j]);
+      P[1][j] = __ffma2_rn(a1r, b[j], P[1][j]);
+      Q[1][j] = __ffma2_rn(a1i, bs, Q[1][j]);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    acc[0][j] = make_float2(P[0][j].x - Q[0][j].x, P[0][j].y + Q[0][j].y);
+    acc[1][j] = make_float2(P[1][j].x - Q[1][j].x, P[1][j].y + Q[1][j].y);
+  }
+}
+__device__ inline void trace_tile_fma(const double2 *A, const double2 *B, int n, int kg,
+                                      double2 (&acc)[2][4]) {
+  const int nq = (n + 3) >> 2;
+  const int i0 = min(n, kg * nq), i1 = min(n, i0 + nq);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) acc[0][j] = acc[1][j] = make_double2(0.0, 0.0);
+#pragma unroll 4
+  for (int i = i0; i < i1; ++i) {
+    double2 a0, a1, b0, b1, b2, b3;
+    lds2(A + i * kTraceRows, a0, a1);
+    lds2(B + i * 8, b0, b1);
+    lds2(B + i * 8 + 2, b2, b3);
+    cfma(acc[0][0], a0, b0); cfma(acc[0][1], a0, b1);
+    cfma(acc[0][2], a0, b2); cfma(acc[0][3], a0, b3);
+    cfma(acc[1][0], a1, b0); cfma(acc[1][1], a1, b1);
+    cfma(acc[1][2], a1, b2); cfma(acc[1][3], a1, b3);
+  }
+}
+
 // Every trace solve of one DDM application in one cooperative launch.  The schedule is a list of
 // dataflow levels: a trace solve (sweep l, subdomain X) sits one level below the deepest solve
 // whose traces are routed into its slot l, so every level only reads slots that earlier levels
-// completed.  The items of level v are items[lev_off[v] .. lev_off[v + 1]), heaviest first;
+// completed.  The items of level v are records lev_off[v] .. lev_off[v + 1] - 1, heaviest first;
 // CTA b takes positions b, 2G - 1 - b, 2G + b, ... (a snake over the G CTAs).  A CTA with items
 // in level v first waits until every CTA is done with level v - 1 (counters above); the
-// descriptors and map slice of its first item depend on no trace and are staged before that wait.
+// descriptors and map slice of its first item depend on no trace and are staged before that
+// wait.  Per item (two CTA barriers):
+//   wait for the map slice; the next item's inputs are loaded into registers; FMAs;
+//   barrier; the next item's map-slice copy is issued and its inputs stored, the partial tiles
+//   written, the item after it described;  barrier;  reduction and vector reductions into the
+//   receivers' slots.
 constexpr int kMaxSmemLevels = 1024;
 
 template <typename R>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
-    k_trace_sweeps(Geom g, const int4 *__restrict__ items, const int *__restrict__ lev_off,
-                   int nlev, const TracePanel *__restrict__ panels,
+    k_trace_sweeps(Geom g, const int4 *__restrict__ hdr, const int2 *__restrict__ cols,
+                   const int *__restrict__ lev_off, int nlev,
                    const typename Cx<R>::T *__restrict__ gmap, typename Cx<R>::T *__restrict__ gtr,
                    const typename Cx<R>::T *__restrict__ rawf, int nrhs, unsigned *cnt,
                    int *__restrict__ err) {
   using C = typename Cx<R>::T;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   C *Gs = reinterpret_cast<C *>(smem_raw);            // map slice [k][64 rows]
-  C *vin = Gs + kTraceSeg * kTraceRows;               // inputs [k][8 columns]
-  C *red = vin + 8 * kTraceSeg;                       // partial tiles [K-group][col][row pair][2]
+  C *vin2 = Gs + kTraceSeg * kTraceRows;              // inputs [2 buffers][k][8 columns]
+  C *red = vin2 + 2 * 8 * kTraceSeg;                  // partial tiles [K-group][col][row pair][2]
   uint64_t *bar = reinterpret_cast<uint64_t *>(red + 4 * 8 * 64);
   int *lo_s = reinterpret_cast<int *>(bar + 2);       // level offsets (nlev < kMaxSmemLevels)
-  __shared__ TraceItemSmem its[2];
+  __shared__ TraceItemSmem its[3];
   const bool lv_smem = nlev < kMaxSmemLevels;
   for (int i = threadIdx.x; lv_smem && i <= nlev; i += blockDim.x) lo_s[i] = lev_off[i];
   if (threadIdx.x == 0) {
@@ -463,66 +500,58 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
   const long long slot_stride = (long long)nrhs * g.nsub * g.T;
   // compute roles: K-group kg, row pair rp, column group cg; epilogue: column ec, row pair rp
   const int kg = tid >> 6, rp = tid & 31, cg = (tid >> 5) & 1, ec = tid >> 5;
-  int s = 0;
+  int s = 0;   // descriptor buffer of the current item (the next ones: s + 1, s + 2 mod 3)
+  int vb = 0;  // input buffer of the current item
   uint32_t phase = 0;
-  TracePre pre;
+  TracePre pre;   // warp 0: the record of the item after the next
   for (int v = 0; v < nlev; ++v) {
     const int base = lev(v), Nv = lev(v + 1) - base;
     if (v > 0) step_arrive(cnt, v - 1);
     if (pos(0) >= Nv) continue;
     if (warp == 0) {
-      pre = trace_fetch(items, panels, base + pos(0));
-      trace_stage<C>(g, pre, its[s], Gs, bar, gmap, slot_stride);
+      // the first three records of the level in one round of loads
+      const bool h1 = pos(1) < Nv, h2 = pos(2) < Nv;
+      const TracePre p0 = trace_fetch(hdr, cols, base + pos(0));
+      const TracePre p1 = h1 ? trace_fetch(hdr, cols, base + pos(1)) : p0;
+      if (h2) pre = trace_fetch(hdr, cols, base + pos(2));
+      trace_describe(g, p0, its[s], slot_stride);
+      __syncwarp();
+      if (tid == 0) trace_copy<C>(g, its[s], Gs, bar, gmap);
+      if (h1) trace_describe(g, p1, its[(s + 1) % 3], slot_stride);
     }
     __syncthreads();
     if (v > 0) step_wait(cnt, v - 1, err);
-    {
-      C x[kTraceInPer];
-      trace_gather_load<C>(its[s], gtr, x);
-      trace_gather_store<C>(vin, x);
-    }
-    __syncthreads();
+    trace_gather<C>(its[s], gtr, vin2 + vb * 8 * kTraceSeg);
+    cp_async_wait_all();
     for (int r = 0; pos(r) < Nv; ++r) {
       const TraceItemSmem &it = its[s];
-      const bool next = pos(r + 1) < Nv;
-      if (next && warp == 0) pre = trace_fetch(items, panels, base + pos(r + 1));
+      TraceItemSmem &nx = its[(s + 1) % 3];
+      const bool next = pos(r + 1) < Nv, next2 = pos(r + 2) < Nv;
+      const C *vin = vin2 + vb * 8 * kTraceSeg;
       const bool ok = mbar_wait(bar, phase);
       if (__syncthreads_or(!ok) && tid == 0) {
         atomicExch(err, 3);
         mbar_wait(bar, phase);   // bounded second wait for the copy in flight
       }
+      // the next item's inputs (slots of earlier levels) land in the other buffer meanwhile
+      if (next) trace_gather<C>(nx, gtr, vin2 + (vb ^ 1) * 8 * kTraceSeg);
       // partial tile of K-group kg over its quarter of the n inputs
       C acc[2][4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) acc[0][j] = acc[1][j] = czero<C>();
-      {
-        const int n = it.n, nq = (n + 3) >> 2;
-        const int i0 = min(n, kg * nq), i1 = min(n, i0 + nq);
-        const C *A = Gs + 2 * rp;
-        const C *B = vin + 4 * cg;
-#pragma unroll 4
-        for (int i = i0; i < i1; ++i) {
-          C a0, a1, b0, b1, b2, b3;
-          lds2(A + i * kTraceRows, a0, a1);
-          lds2(B + i * 8, b0, b1);
-          lds2(B + i * 8 + 2, b2, b3);
-          cfma(acc[0][0], a0, b0); cfma(acc[0][1], a0, b1);
-          cfma(acc[0][2], a0, b2); cfma(acc[0][3], a0, b3);
-          cfma(acc[1][0], a1, b0); cfma(acc[1][1], a1, b1);
-          cfma(acc[1][2], a1, b2); cfma(acc[1][3], a1, b3);
-        }
+      trace_tile_fma(Gs + 2 * rp, vin + 4 * cg, it.n, kg, acc);
+      __syncthreads();   // Gs and this item's inputs are free
+      if (next && tid == 32) trace_copy<C>(g, nx, Gs, bar, gmap);
+      if (next2 && warp == 0) {
+        trace_describe(g, pre, its[(s + 2) % 3], slot_stride);
+        if (pos(r + 3) < Nv) pre = trace_fetch(hdr, cols, base + pos(r + 3));
       }
-      __syncthreads();   // Gs and vin are free
-      if (next && warp == 0) trace_stage<C>(g, pre, its[s ^ 1], Gs, bar, gmap, slot_stride);
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         C *p = red + (((kg * 8 + 4 * cg + j) * 32 + rp) << 1);
         p[0] = acc[0][j];
         p[1] = acc[1][j];
       }
-      __syncthreads();   // partial tiles and the next item's descriptors are in place
-      C x[kTraceInPer];
-      if (next) trace_gather_load<C>(its[s ^ 1], gtr, x);
+      cp_async_wait_all();
+      __syncthreads();   // partial tiles, next inputs and descriptors are in place
       {
         C o0 = czero<C>(), o1 = czero<C>();
 #pragma unroll
@@ -550,10 +579,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
           }
         }
       }
-      if (next) trace_gather_store<C>(vin, x);
-      __syncthreads();   // vin holds the next inputs; red and its[s] are free
-      s ^= 1;
+      s = (s + 1) % 3;
       phase ^= 1u;
+      vb ^= 1;
     }
   }
   // every staged item is consumed in its level, so no copy is in flight here
@@ -692,8 +720,8 @@ cudaError_t launch_extract(cudaStream_t st, const Geom &g, int ncols, const Col 
 }
 
 template <typename R>
-cudaError_t launch_trace_sweeps(cudaStream_t st, const Geom &g, const int4 *items, int nitems,
-                                const int *lev_off, int nlevels, const TracePanel *panels,
+cudaError_t launch_trace_sweeps(cudaStream_t st, const Geom &g, const int4 *hdr, const int2 *cols,
+                                int nitems, const int *lev_off, int nlevels,
                                 const typename Cx<R>::T *gmap, typename Cx<R>::T *gtr,
                                 const typename Cx<R>::T *rawf, int nrhs, unsigned *gbar, int *err,
                                 int ctas_per_sm) {
@@ -721,14 +749,14 @@ cudaError_t launch_trace_sweeps(cudaStream_t st, const Geom &g, const int4 *item
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_trace_sweeps<R>, g, items, lev_off, nlevels, panels, gmap, gtr,
+  return cudaLaunchKernelEx(&cfg, k_trace_sweeps<R>, g, hdr, cols, lev_off, nlevels, gmap, gtr,
                             rawf, nrhs, gbar, err);
 }
 
 size_t trace_counter_bytes(int nlevels) { return (size_t)nlevels * kStepCounters * sizeof(unsigned); }
 
 size_t trace_smem_bytes(size_t elem, int nlevels) {
-  size_t b = ((size_t)kTraceSeg * kTraceRows + 8 * kTraceSeg + 4 * 8 * 64) * elem + 16;
+  size_t b = ((size_t)kTraceSeg * kTraceRows + 2 * 8 * kTraceSeg + 4 * 8 * 64) * elem + 16;
   if (nlevels < kMaxSmemLevels) b += (size_t)(nlevels + 1) * sizeof(int);
   return b;
 }
@@ -739,7 +767,7 @@ size_t trace_smem_bytes(size_t elem, int nlevels) {
 // into the fewest segments of at most kTraceSeg, of equal length.  In the first sweep one item
 // per output tile also adds the raw own-source lines (an input-free item if nothing is received).
 void trace_items_for(const Geom &g, const TracePanel *tp, int p0, int p1, int l, const int *route,
-                     int in_mask, std::vector<int4> &out) {
+                     int in_mask, std::vector<TraceItem> &out) {
   for (int p = p0; p < p1; ++p) {
     const TracePanel &pn = tp[p];
     auto any_nb = [&](int d) {
@@ -747,22 +775,32 @@ void trace_items_for(const Geom &g, const TracePanel *tp, int p0, int p1, int l,
         if (sub_neighbour(g, pn.sub[c], d) >= 0) return true;
       return false;
     };
+    TraceItem it{};
     for (int dout = 0; dout < g.nsides; ++dout) {
       const int lp = route[l * 6 + dout];
       if (lp < 0 || !any_nb(dout)) continue;
+      for (int c = 0; c < 8; ++c) {
+        if (c >= pn.ncol) { it.col[c] = make_int2(-1, -1); continue; }
+        const int nb = sub_neighbour(g, pn.sub[c], dout);
+        it.col[c] = make_int2(pn.rhs[c] * g.nsub + pn.sub[c], nb >= 0 ? pn.rhs[c] * g.nsub + nb : -1);
+      }
       for (int tile = 0; tile < trace_tiles(g, dout); ++tile) {
         int raw = l == 0 ? 1 : 0;
+        auto emit = [&](int k0, int n) {
+          it.h = make_int4(pn.factor | (pn.ncol << 24), l | (lp << 16), k0 | (n << 16),
+                           dout | (tile << 8) | (raw << 16));
+          out.push_back(it);
+          raw = 0;
+        };
         for (int sd = 0; sd < g.nsides; ++sd) {
           if (!((in_mask >> sd) & 1) || !any_nb(sd)) continue;
           const int len = 2 * g.Lt[sd], ns = (len + kTraceSeg - 1) / kTraceSeg;
           for (int j = 0; j < ns; ++j) {
             const int a = j * len / ns, e = (j + 1) * len / ns;
-            out.push_back(make_int4(p, l | (lp << 16), (g.toff[sd] + a) | ((e - a) << 16),
-                                    dout | (tile << 8) | (raw << 16)));
-            raw = 0;
+            emit(g.toff[sd] + a, e - a);
           }
         }
-        if (raw) out.push_back(make_int4(p, l | (lp << 16), 0, dout | (tile << 8) | (1 << 16)));
+        if (raw) emit(0, 0);
       }
     }
   }
@@ -816,8 +854,8 @@ cudaError_t launch_copy_local_back(cudaStream_t st, long long n, const typename 
   template cudaError_t launch_extract<R>(cudaStream_t, const Geom &, int, const Col *,         \
                                          const Cx<R>::T *, double2 *, int, Cx<R>::T *,         \
                                          Cx<R>::T *, const int *, int, int);                    \
-  template cudaError_t launch_trace_sweeps<R>(cudaStream_t, const Geom &, const int4 *, int,    \
-                                              const int *, int, const TracePanel *,             \
+  template cudaError_t launch_trace_sweeps<R>(cudaStream_t, const Geom &, const int4 *,         \
+                                              const int2 *, int, const int *, int,              \
                                               const Cx<R>::T *, Cx<R>::T *, const Cx<R>::T *,  \
                                               int, unsigned *, int *, int);                     \
   template cudaError_t launch_unit_traces<R>(cudaStream_t, const Geom &, const Tables &, int,  \
