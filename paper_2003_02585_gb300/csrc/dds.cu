@@ -1198,8 +1198,8 @@ dds_status fgmres(dds_ctx *ctx, const double2 *b, int nrhs, double2 *x, double t
     double2 *h2 = hdev + (size_t)nrhs * (nv + 1);              // [nrhs][nv]
     double2 *hn = h2 + (size_t)nrhs * nv;                      // [nrhs]
     LAUNCHK(DDS_K_KRYLOV, launch_dots(st, N, nrhs, nv + 1, V, vs, N, W, N, part, h1, nblk));
-    LAUNCHK(DDS_K_KRYLOV, launch_sub_combination(st, N, nrhs, nv, V, vs, N, h1, W, N, -1.0, nv + 1));
-    LAUNCHK(DDS_K_KRYLOV, launch_dots(st, N, nrhs, 1, W, 0, N, W, N, part, hn, nblk));
+    LAUNCHK(DDS_K_KRYLOV, launch_combination(st, N, nrhs, nv, V, vs, N, h1, nv + 1, -1.0, W, N,
+                                             false, part, hn, nblk));
     CK(cudaMemcpyAsync(hh.data(), hdev, (size_t)nrhs * (2 * nv + 2) * sizeof(double2),
                        cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -1211,8 +1211,8 @@ dds_status fgmres(dds_ctx *ctx, const double2 *b, int nrhs, double2 *x, double t
     std::vector<double2> h2h((size_t)nrhs * nv, make_double2(0.0, 0.0));
     if (second) {
       LAUNCHK(DDS_K_KRYLOV, launch_dots(st, N, nrhs, nv, V, vs, N, W, N, part, h2, nblk));
-      LAUNCHK(DDS_K_KRYLOV, launch_sub_combination(st, N, nrhs, nv, V, vs, N, h2, W, N, -1.0, nv));
-      LAUNCHK(DDS_K_KRYLOV, launch_dots(st, N, nrhs, 1, W, 0, N, W, N, part, hn, nblk));
+      LAUNCHK(DDS_K_KRYLOV, launch_combination(st, N, nrhs, nv, V, vs, N, h2, nv, -1.0, W, N,
+                                               false, part, hn, nblk));
       CK(cudaMemcpyAsync(h2h.data(), h2, (size_t)nrhs * nv * sizeof(double2), cudaMemcpyDeviceToHost, st));
       CK(cudaMemcpyAsync(hh.data() + (size_t)nrhs * (2 * nv + 1), hn, nrhs * sizeof(double2),
                          cudaMemcpyDeviceToHost, st));
@@ -1269,12 +1269,13 @@ dds_status fgmres(dds_ctx *ctx, const double2 *b, int nrhs, double2 *x, double t
     }
     for (int i = 0; i < kr; ++i) ycoef[(size_t)r * k + i] = make_double2(y[i].real(), y[i].imag());
   }
-  CK(cudaMemsetAsync(x, 0, vbytes, st));
   if (k > 0) {
     CK(cudaMemcpyAsync(ctx->coefbuf.p, ycoef.data(), (size_t)nrhs * k * sizeof(double2),
                        cudaMemcpyHostToDevice, st));
-    LAUNCHK(DDS_K_KRYLOV, launch_sub_combination(st, N, nrhs, k, Z, vs, N, ctx->coefbuf.as<double2>(),
-                                                 x, N, 1.0, k));
+    LAUNCHK(DDS_K_KRYLOV, launch_combination(st, N, nrhs, k, Z, vs, N, ctx->coefbuf.as<double2>(),
+                                             k, 1.0, x, N, true, nullptr, nullptr, 0));
+  } else {
+    CK(cudaMemsetAsync(x, 0, vbytes, st));
   }
   // true residual: R = A x - b
   double2 *Rv = V;

@@ -217,23 +217,66 @@ __global__ void k_dots_reduce(int count, int nblk, const double2 *__restrict__ p
   if (threadIdx.x == 0) out[q] = make_double2(sr, si);
 }
 
-// w[rhs] += sign * sum_{i < nv} V_i[rhs] * coef[rhs * cstride + i]        (grid.y = rhs)
-__global__ void k_sub_combination(long long N, int nv, const double2 *__restrict__ V,
-                                  long long vsv, long long vsr, const double2 *__restrict__ coef,
-                                  double2 *__restrict__ w, long long wsr, double sign,
-                                  int cstride) {
+// w[rhs] = (overwrite ? 0 : w[rhs]) + sign * sum_{i < nv} V_i[rhs] * coef[rhs * cstride + i]
+// (grid.y = rhs).  The signed coefficients sit in shared memory; two elements per thread and
+// iteration are in flight.  With `partial`, the block also sums |w|^2 of the result into
+// partial[rhs * gridDim.x + blockIdx.x] (the norm of a Gram-Schmidt update in the same pass).
+constexpr int kCombMaxNv = 64;
+
+__global__ void __launch_bounds__(256) k_combination(long long N, int nv,
+                                                     const double2 *__restrict__ V, long long vsv,
+                                                     long long vsr, const double2 *__restrict__ coef,
+                                                     int cstride, double sign,
+                                                     double2 *__restrict__ w, long long wsr,
+                                                     int overwrite, double2 *__restrict__ partial) {
+  __shared__ double2 cs[kCombMaxNv];
+  __shared__ double red[8];
   const int rhs = blockIdx.y;
-  const double2 *cf = coef + (long long)rhs * cstride;
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+    const double2 c = coef[(long long)rhs * cstride + i];
+    cs[i] = make_double2(sign * c.x, sign * c.y);
+  }
+  __syncthreads();
   double2 *ww = w + rhs * wsr;
   const double2 *vr = V + rhs * vsr;
-  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
-       n += (long long)gridDim.x * blockDim.x) {
-    double2 acc = make_double2(0.0, 0.0);
-    for (int i = 0; i < nv; ++i) cfma(acc, vr[i * vsv + n], cf[i]);
-    double2 v = ww[n];
-    v.x = fma(sign, acc.x, v.x);
-    v.y = fma(sign, acc.y, v.y);
-    ww[n] = v;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  double nrm = 0.0;
+  for (; n + stride < N; n += 2 * stride) {
+    double2 a0 = make_double2(0.0, 0.0), a1 = a0;
+    if (!overwrite) {
+      a0 = ww[n];
+      a1 = ww[n + stride];
+    }
+    for (int i = 0; i < nv; ++i) {
+      const double2 c = cs[i];
+      const double2 v0 = vr[i * vsv + n], v1 = vr[i * vsv + n + stride];
+      cfma(a0, v0, c);
+      cfma(a1, v1, c);
+    }
+    ww[n] = a0;
+    ww[n + stride] = a1;
+    nrm = fma(a0.x, a0.x, nrm);
+    nrm = fma(a0.y, a0.y, nrm);
+    nrm = fma(a1.x, a1.x, nrm);
+    nrm = fma(a1.y, a1.y, nrm);
+  }
+  for (; n < N; n += stride) {
+    double2 a0 = overwrite ? make_double2(0.0, 0.0) : ww[n];
+    for (int i = 0; i < nv; ++i) cfma(a0, vr[i * vsv + n], cs[i]);
+    ww[n] = a0;
+    nrm = fma(a0.x, a0.x, nrm);
+    nrm = fma(a0.y, a0.y, nrm);
+  }
+  if (partial == nullptr) return;
+  for (int o = 16; o > 0; o >>= 1) nrm += __shfl_down_sync(0xffffffffu, nrm, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = nrm;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
+    partial[(long long)rhs * gridDim.x + blockIdx.x] = make_double2(t, 0.0);
   }
 }
 
@@ -306,13 +349,32 @@ cudaError_t launch_dots(cudaStream_t st, long long N, int nrhs, int nv, const do
   return cudaGetLastError();
 }
 
+cudaError_t launch_combination(cudaStream_t st, long long N, int nrhs, int nv, const double2 *V,
+                               long long vsv, long long vsr, const double2 *coef, int cstride,
+                               double sign, double2 *w, long long wsr, bool overwrite,
+                               double2 *partial, double2 *nrm2, int nblk) {
+  const dim3 grid = nrm2 != nullptr ? dim3((unsigned)nblk, (unsigned)nrhs) : grid_rhs(N, nrhs);
+  // groups of at most kCombMaxNv vectors; the norm comes with the last group
+  for (int i0 = 0; i0 < nv || i0 == 0; i0 += kCombMaxNv) {
+    const int cnt = std::min(kCombMaxNv, nv - i0);
+    const bool last = i0 + kCombMaxNv >= nv;
+    k_combination<<<grid, 256, 0, st>>>(N, std::max(cnt, 0), V + i0 * vsv, vsv, vsr, coef + i0,
+                                        cstride, sign, w, wsr, overwrite && i0 == 0 ? 1 : 0,
+                                        nrm2 != nullptr && last ? partial : nullptr);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || last) break;
+  }
+  if (nrm2 == nullptr) return cudaGetLastError();
+  k_dots_reduce<<<nrhs, 32, 0, st>>>(nrhs, nblk, partial, nrm2);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_sub_combination(cudaStream_t st, long long N, int nrhs, int nv,
                                    const double2 *V, long long vsv, long long vsr,
                                    const double2 *coef, double2 *w, long long wsr, double sign,
                                    int cstride) {
-  k_sub_combination<<<grid_rhs(N, nrhs), 256, 0, st>>>(N, nv, V, vsv, vsr, coef, w, wsr, sign,
-                                                       cstride);
-  return cudaGetLastError();
+  return launch_combination(st, N, nrhs, nv, V, vsv, vsr, coef, cstride, sign, w, wsr, false,
+                            nullptr, nullptr, 0);
 }
 
 cudaError_t launch_scale_by_norm(cudaStream_t st, long long N, int nrhs, const double2 *in,

@@ -25,28 +25,38 @@ __global__ void k_assemble(Geom g, Tables tb, const Col *__restrict__ cols,
   const Col c = cols[blockIdx.x];
   bool nz = false;   // any nonzero entry written (the local solve of a zero source is zero)
   C *x = work + (long long)c.slot * g.Nloc;
-  for (long long i = threadIdx.x; i < g.Nloc; i += blockDim.x) x[i] = czero<C>();
-  __syncthreads();
   int k[3];
   sub_index(g, c.sub, k);
-  if (with_source) {
-    int lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
-    for (int a = 0; a < g.dim; ++a) own_range(g, k, a, lo[a], hi[a]);
-    const int w0 = hi[0] - lo[0], w1 = hi[1] - lo[1], w2 = hi[2] - lo[2];
-    const long long cnt = (long long)w0 * w1 * w2;
-    const double2 *bb = b + (long long)c.rhs * g.Nglob;
-    for (long long idx = threadIdx.x; idx < cnt; idx += blockDim.x) {
-      int i0 = lo[0] + (int)(idx % w0);
-      int i1 = lo[1] + (int)((idx / w0) % w1);
-      int i2 = lo[2] + (int)(idx / ((long long)w0 * w1));
-      long long loc = i0 + (long long)g.M[0] * (i1 + (long long)g.M[1] * i2);
-      long long p0 = (long long)k[0] * g.m[0] + i0;
-      long long p1 = (long long)k[1] * g.m[1] + i1;
-      long long p2 = g.dim == 3 ? (long long)k[2] * g.m[2] + i2 : 0;
-      long long glob = p0 + (long long)g.G[0] * (p1 + (long long)g.G[1] * p2);
-      const C v = to_c(bb[glob], C());
-      nz = nz || v.x != 0 || v.y != 0;
-      x[loc] = v;
+  // every local node written once: the source on the own range, zero elsewhere; consecutive
+  // threads take consecutive nodes (32-bit index arithmetic), four loads in flight per thread
+  {
+    int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    if (with_source)
+      for (int a = 0; a < g.dim; ++a) own_range(g, k, a, lo[a], hi[a]);
+    const double2 *bb = b + (long long)c.rhs * g.Nglob + (long long)k[0] * g.m[0] +
+                        (long long)g.G[0] * ((long long)k[1] * g.m[1] +
+                                             (long long)g.G[1] * (g.dim == 3 ? (long long)k[2] * g.m[2] : 0));
+    const int M0 = g.M[0], M1 = g.M[1], nloc = (int)g.Nloc;
+    const long long G0 = g.G[0], G01 = (long long)g.G[0] * g.G[1];
+    constexpr int U = 4;
+    for (int e0 = threadIdx.x; e0 < nloc; e0 += U * blockDim.x) {
+      C v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * blockDim.x;
+        v[u] = czero<C>();
+        const int i0 = e % M0, r = e / M0, i1 = r % M1, i2 = r / M1;
+        if (e < nloc && i0 >= lo[0] && i0 < hi[0] && i1 >= lo[1] && i1 < hi[1] &&
+            (g.dim < 3 || (i2 >= lo[2] && i2 < hi[2]))) {
+          v[u] = to_c(bb[i0 + G0 * i1 + G01 * i2], C());
+          nz = nz || v[u].x != 0 || v[u].y != 0;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * blockDim.x;
+        if (e < nloc) x[e] = v[u];
+      }
     }
   }
   const C *tr = traces ? traces + (long long)c.rhs * trs_rhs + (long long)c.sub * trs_sub : nullptr;
@@ -161,22 +171,22 @@ __global__ void k_extract(Geom g, const Col *__restrict__ cols,
   int k[3];
   sub_index(g, c.sub, k);
   if (own_mode) {
+    // the own range, one warp per grid row (x1 fastest, coalesced on both sides)
     int lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
     for (int a = 0; a < g.dim; ++a) own_range(g, k, a, lo[a], hi[a]);
-    const int w0 = hi[0] - lo[0], w1 = hi[1] - lo[1], w2 = hi[2] - lo[2];
-    const long long cnt = (long long)w0 * w1 * w2;
+    const int w1 = hi[1] - lo[1], rows = w1 * (hi[2] - lo[2]);
     double2 *uu = u + (long long)c.rhs * g.Nglob;
-    for (long long idx = threadIdx.x; idx < cnt; idx += blockDim.x) {
-      int i0 = lo[0] + (int)(idx % w0);
-      int i1 = lo[1] + (int)((idx / w0) % w1);
-      int i2 = lo[2] + (int)(idx / ((long long)w0 * w1));
-      long long loc = i0 + (long long)g.M[0] * (i1 + (long long)g.M[1] * i2);
-      long long p0 = (long long)k[0] * g.m[0] + i0;
-      long long p1 = (long long)k[1] * g.m[1] + i1;
-      long long p2 = g.dim == 3 ? (long long)k[2] * g.m[2] + i2 : 0;
-      long long glob = p0 + (long long)g.G[0] * (p1 + (long long)g.G[1] * p2);
-      const double2 xv = to_c64(x[loc]);
-      uu[glob] = own_mode == 1 ? cadd(uu[glob], xv) : xv;
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int row = threadIdx.x >> 5; row < rows; row += nw) {
+      const int i1 = lo[1] + row % w1, i2 = lo[2] + row / w1;
+      const long long p1 = (long long)k[1] * g.m[1] + i1;
+      const long long p2 = g.dim == 3 ? (long long)k[2] * g.m[2] + i2 : 0;
+      double2 *urow = uu + (long long)k[0] * g.m[0] + (long long)g.G[0] * (p1 + (long long)g.G[1] * p2);
+      const C *xr = x + (long long)g.M[0] * (i1 + (long long)g.M[1] * i2);
+      for (int i0 = lo[0] + lane; i0 < hi[0]; i0 += 32) {
+        const double2 xv = to_c64(xr[i0]);
+        urow[i0] = own_mode == 1 ? cadd(urow[i0], xv) : xv;
+      }
     }
   }
   if (raw_out != nullptr) {
