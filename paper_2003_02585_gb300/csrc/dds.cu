@@ -1208,6 +1208,36 @@ dds_status fgmres(dds_ctx *ctx, const double2 *b, int nrhs, double2 *x, double t
       const double w0 = hh[(size_t)r * (nv + 1) + nv].x, w1 = hh[(size_t)nrhs * (2 * nv + 1) + r].x;
       if (!(w1 > 0.5 * w0)) second = true;   // ||w1|| <= ||w0|| / sqrt(2): cancellation
     }
+    // The second pass only keeps V_{j+1} orthogonal.  If the first-pass column already meets the
+    // tolerance for every active RHS (or this is the last iteration), V_{j+1} is never used and
+    // the pass is skipped: the first-pass coefficients are accurate to rounding in ||w0||, and
+    // the true residual below decides convergence.
+    if (second) {
+      bool last = j + 1 == m;
+      if (!last) {
+        last = true;
+        for (int r = 0; r < nrhs && last; ++r) {
+          if (done[r]) continue;
+          std::vector<cd> col(j + 2);
+          for (int i = 0; i <= j; ++i) {
+            const double2 a = hh[(size_t)r * (nv + 1) + i];
+            col[i] = cd(a.x, a.y);
+          }
+          col[j + 1] = std::sqrt(std::max(hh[(size_t)nrhs * (2 * nv + 1) + r].x, 0.0));
+          for (int i = 0; i < j; ++i) {
+            const cd a = col[i], bb = col[i + 1];
+            const cd c = cs[(size_t)r * m + i], sv = sn[(size_t)r * m + i];
+            col[i] = c * a + sv * bb;
+            col[i + 1] = -std::conj(sv) * a + std::conj(c) * bb;
+          }
+          const double rr = std::hypot(std::abs(col[j]), std::abs(col[j + 1]));
+          const cd gj = gg[(size_t)r * (m + 1) + j];
+          const double est = rr > 0 ? std::abs(col[j + 1]) / rr * std::abs(gj) : 0.0;
+          if (!(est / beta[r] < tol)) last = false;
+        }
+      }
+      if (last) second = false;
+    }
     std::vector<double2> h2h((size_t)nrhs * nv, make_double2(0.0, 0.0));
     if (second) {
       LAUNCHK(DDS_K_KRYLOV, launch_dots(st, N, nrhs, nv, V, vs, N, W, N, part, h2, nblk));
