@@ -1248,7 +1248,6 @@ dds_status fgmres(dds_ctx *ctx, const double2 *b, int nrhs, double2 *x, double t
                          cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
     }
-    LAUNCHK(DDS_K_KRYLOV, launch_scale_by_norm(st, N, nrhs, W, hn, W));
     for (int r = 0; r < nrhs; ++r) {
       const double hnorm = std::sqrt(std::max(hh[(size_t)nrhs * (2 * nv + 1) + r].x, 0.0));
       for (int i = 0; i <= j; ++i) {
@@ -1285,6 +1284,8 @@ dds_status fgmres(dds_ctx *ctx, const double2 *b, int nrhs, double2 *x, double t
       else all = false;
     }
     if (all) break;
+    // V_{j+1} = W / ||W|| only when another iteration follows
+    if (j + 1 < m) LAUNCHK(DDS_K_KRYLOV, launch_scale_by_norm(st, N, nrhs, W, hn, W));
   }
   *iters = k;
   // x = sum_i Z_i y_i per RHS (one update kernel over all k basis vectors)
