@@ -521,10 +521,16 @@ int build_trace_schedule(dds_ctx *ctx, int nrhs, int rounds, std::vector<TraceIt
       trace_items_for(g, tp.data(), pan_off, (int)tp.size(), l, route.data(), ctx->in_mask[l],
                       items);
     }
-    // heaviest items first (input count), so that the snake deal over the CTAs balances
-    std::stable_sort(items.begin() + first, items.end(), [](const TraceItem &a, const TraceItem &b) {
-      return ((a.h.z >> 16) & 0xFFFF) > ((b.h.z >> 16) & 0xFFFF);
-    });
+    // heaviest items first, so that the snake deal over the CTAs balances: cost ~ a fixed part
+    // (staging, reduction, barriers; about 0.7 of a full tile's FMAs at 80 inputs) plus the
+    // FMAs, which a tile with at most 32 live rows runs in half the time
+    auto cost = [&](const TraceItem &t) {
+      const int n = (t.h.z >> 16) & 0xFFFF, dout = t.h.w & 0xFF, tile = (t.h.w >> 8) & 0xFF;
+      const bool half = 2 * g.Lt[dout] - tile * 64 <= 32;
+      return 56 + (half ? n / 2 : n);
+    };
+    std::stable_sort(items.begin() + first, items.end(),
+                     [&](const TraceItem &a, const TraceItem &b) { return cost(a) > cost(b); });
   }
   lev_off.push_back((int)items.size());
   return nlev;

@@ -413,15 +413,15 @@ __device__ inline void lds2(const double2 *p, double2 &x, double2 &y) {
   y = p[1];
 }
 
-// Partial tile of K-group kg: rows 2 rp, 2 rp + 1 (A = map slice + 2 rp, row stride 64) times
-// columns 4 cg .. 4 cg + 3 (B = inputs + 4 cg, input stride 8) over the group's quarter of the n
-// inputs.  Single precision runs on packed two-lane FMAs: per (row, column)
+// Partial tile of K-group kg of KG: rows 2 rp, 2 rp + 1 (A = map slice + 2 rp, row stride 64)
+// times columns 4 cg .. 4 cg + 3 (B = inputs + 4 cg, input stride 8) over the group's share of
+// the n inputs.  Single precision runs on packed two-lane FMAs: per (row, column)
 //   P += (a.re, a.re) * (b.re, b.im),   Q += (a.im, a.im) * (b.im, b.re),
 //   a b = (P.re - Q.re, P.im + Q.im),
 // which halves the FMA instructions issued against four scalar FMAs per complex product.
-__device__ inline void trace_tile_fma(const float2 *A, const float2 *B, int n, int kg,
+__device__ inline void trace_tile_fma(const float2 *A, const float2 *B, int n, int kg, int KG,
                                       float2 (&acc)[2][4]) {
-  const int nq = (n + 3) >> 2;
+  const int nq = (n + KG - 1) / KG;
   const int i0 = min(n, kg * nq), i1 = min(n, i0 + nq);
   float2 P[2][4], Q[2][4];
 #pragma unroll
@@ -449,9 +449,9 @@ __device__ inline void trace_tile_fma(const float2 *A, const float2 *B, int n, i
     acc[1][j] = make_float2(P[1][j].x - Q[1][j].x, P[1][j].y + Q[1][j].y);
   }
 }
-__device__ inline void trace_tile_fma(const double2 *A, const double2 *B, int n, int kg,
+__device__ inline void trace_tile_fma(const double2 *A, const double2 *B, int n, int kg, int KG,
                                       double2 (&acc)[2][4]) {
-  const int nq = (n + 3) >> 2;
+  const int nq = (n + KG - 1) / KG;
   const int i0 = min(n, kg * nq), i1 = min(n, i0 + nq);
 #pragma unroll
   for (int j = 0; j < 4; ++j) acc[0][j] = acc[1][j] = make_double2(0.0, 0.0);
@@ -494,6 +494,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
   C *Gs = reinterpret_cast<C *>(smem_raw);            // map slice [k][64 rows]
   C *vin2 = Gs + kTraceSeg * kTraceRows;              // inputs [2 buffers][k][8 columns]
   C *red = vin2 + 2 * 8 * kTraceSeg;                  // partial tiles [K-group][col][row pair][2]
+                                                      // (4 K-groups x 32 row pairs, or 8 x 16)
   uint64_t *bar = reinterpret_cast<uint64_t *>(red + 4 * 8 * 64);
   int *lo_s = reinterpret_cast<int *>(bar + 2);       // level offsets (nlev < kMaxSmemLevels)
   __shared__ TraceItemSmem its[3];
@@ -508,8 +509,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
   const int G = (int)gridDim.x, b = (int)blockIdx.x, tid = threadIdx.x, warp = tid >> 5;
   auto pos = [&](int r) { return r * G + ((r & 1) ? G - 1 - b : b); };
   const long long slot_stride = (long long)nrhs * g.nsub * g.T;
-  // compute roles: K-group kg, row pair rp, column group cg; epilogue: column ec, row pair rp
-  const int kg = tid >> 6, rp = tid & 31, cg = (tid >> 5) & 1, ec = tid >> 5;
+  // epilogue roles: column ec, row pair rp (compute roles per item below)
+  const int rp = tid & 31, ec = tid >> 5;
   int s = 0;   // descriptor buffer of the current item (the next ones: s + 1, s + 2 mod 3)
   int vb = 0;  // input buffer of the current item
   uint32_t phase = 0;
@@ -545,9 +546,16 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
       }
       // the next item's inputs (slots of earlier levels) land in the other buffer meanwhile
       if (next) trace_gather<C>(nx, gtr, vin2 + (vb ^ 1) * 8 * kTraceSeg);
-      // partial tile of K-group kg over its quarter of the n inputs
+      // Compute roles: a full tile has four K-groups of 64 threads (32 row pairs x 2 column
+      // groups); a tile with at most 32 live rows (the last tile of a side) has eight K-groups of
+      // 32 threads over its 16 live row pairs, so its FMAs take half the time.
+      const bool half = 2 * g.Lt[it.dout] - it.tile * kTraceRows <= kTraceRows / 2;
+      const int KG = half ? 8 : 4;
+      const int kg = half ? tid >> 5 : tid >> 6, crp = half ? tid & 15 : tid & 31;
+      const int cg = half ? (tid >> 4) & 1 : (tid >> 5) & 1;
+      const int RPS = half ? 16 : 32;   // row pairs per (K-group, column) in the partial tiles
       C acc[2][4];
-      trace_tile_fma(Gs + 2 * rp, vin + 4 * cg, it.n, kg, acc);
+      trace_tile_fma(Gs + 2 * crp, vin + 4 * cg, it.n, kg, KG, acc);
       __syncthreads();   // Gs and this item's inputs are free
       if (next && tid == 32) trace_copy<C>(g, nx, Gs, bar, gmap);
       if (next2 && warp == 0) {
@@ -556,7 +564,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
       }
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        C *p = red + (((kg * 8 + 4 * cg + j) * 32 + rp) << 1);
+        C *p = red + (((kg * 8 + 4 * cg + j) * RPS + crp) << 1);
         p[0] = acc[0][j];
         p[1] = acc[1][j];
       }
@@ -564,10 +572,10 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
       __syncthreads();   // partial tiles, next inputs and descriptors are in place
       {
         C o0 = czero<C>(), o1 = czero<C>();
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        // (a half tile has no row pairs past 16: their rows are past 2 Lt)
+        for (int q = 0; q < KG && rp < RPS; ++q) {
           C u0, u1;
-          lds2(red + (((q * 8 + ec) * 32 + rp) << 1), u0, u1);
+          lds2(red + (((q * 8 + ec) * RPS + rp) << 1), u0, u1);
           o0 = cadd(o0, u0);
           o1 = cadd(o1, u1);
         }
