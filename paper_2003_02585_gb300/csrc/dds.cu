@@ -1165,8 +1165,7 @@ dds_status fgmres(dds_ctx *ctx, const double2 *b, int nrhs, double2 *x, double t
   }
   double2 *V = ctx->Vbig.as<double2>();
   double2 *Z = ctx->Zbig.as<double2>();
-  const int chunk = dots_chunk();
-  const int nblk = (int)((N + chunk - 1) / chunk);
+  const int nblk = dots_blocks(N, nrhs);
   CK(ctx->dots_part.ensure((size_t)nrhs * (maxit + 2) * nblk * sizeof(double2)));
   // hdev: [h1: nrhs*(j+1)] [h2: nrhs*(j+1)] [norm^2: nrhs]
   CK(ctx->dots_out.ensure((size_t)nrhs * (2 * maxit + 4) * sizeof(double2)));

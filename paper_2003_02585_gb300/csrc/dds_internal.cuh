@@ -297,5 +297,6 @@ cudaError_t launch_scale_vec(cudaStream_t st, long long N, int nrhs, const doubl
 cudaError_t launch_scale_by_norm(cudaStream_t st, long long N, int nrhs, const double2 *in,
                                 const double2 *nrm2, double2 *out);
 int dots_chunk();
+int dots_blocks(long long N, int nrhs);   // blocks per RHS of the dot / norm kernels
 
 }  // namespace dds

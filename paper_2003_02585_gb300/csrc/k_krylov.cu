@@ -52,18 +52,29 @@ __global__ void __launch_bounds__(256) k_apply_A(Geom g, Tables tb, int nrhs, co
     }
     const bool real = imag == 0ull;
     const double2 uc = ur[0];
+    // a subtracted vector (the residual) starts the chain when no J division follows
+    const bool fold = sub != nullptr && !divide_by_J;
     double2 sum;
     if (real) {
-      // two independent chains per component
-      double sx0 = c0.x * uc.x, sy0 = c0.x * uc.y, sx1 = 0.0, sy1 = 0.0;
+      // one FMA chain per component: 2 + 4 DIM FP64 operations per node and RHS (the FP64
+      // pipe, not latency, bounds this kernel: every node and RHS is an independent thread)
+      double sx, sy;
+      if (fold) {
+        const double2 s0 = sub[i];
+        sx = fma(c0.x, uc.x, -s0.x);
+        sy = fma(c0.x, uc.y, -s0.y);
+      } else {
+        sx = c0.x * uc.x;
+        sy = c0.x * uc.y;
+      }
 #pragma unroll
       for (int a = 0; a < DIM; ++a) {
-        sx0 = fma(cpv[a].x, up[a].x, sx0);
-        sy0 = fma(cpv[a].x, up[a].y, sy0);
-        sx1 = fma(cmv[a].x, um[a].x, sx1);
-        sy1 = fma(cmv[a].x, um[a].y, sy1);
+        sx = fma(cpv[a].x, up[a].x, sx);
+        sy = fma(cpv[a].x, up[a].y, sy);
+        sx = fma(cmv[a].x, um[a].x, sx);
+        sy = fma(cmv[a].x, um[a].y, sy);
       }
-      sum = make_double2(sx0 + sx1, sy0 + sy1);
+      sum = make_double2(sx, sy);
     } else {
       sum = cmul(c0, uc);
 #pragma unroll
@@ -77,7 +88,7 @@ __global__ void __launch_bounds__(256) k_apply_A(Geom g, Tables tb, int nrhs, co
       for (int a = 0; a < DIM; ++a) J = cmul(J, tb.an_glob64[a][p[a]]);
       sum = cmul(sum, crecip64(J));
     }
-    if (sub) sum = csub(sum, sub[i]);
+    if (sub != nullptr && !(fold && real)) sum = csub(sum, sub[i]);
     Au[i] = sum;
   }
 }
@@ -200,6 +211,22 @@ __global__ void __launch_bounds__(kDotThreads) k_dots(long long N, int nv, int i
 }
 
 int dots_chunk() { return kDotChunk; }
+
+// Blocks per RHS for the dot and norm kernels: one resident wave over the whole GPU (at the
+// occupancy of the widest dot kernel), never more than one block per 256 elements.  A grid of
+// ceil(N / kDotChunk) blocks per RHS left a half-empty second wave at 640^2 x 16 RHS.
+int dots_blocks(long long N, int nrhs) {
+  int dev = 0, nsm = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dots<4>, kDotThreads, 0) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return (int)std::max<long long>(1, (N + kDotChunk - 1) / kDotChunk);
+  }
+  const long long want = ((long long)nsm * std::max(per_sm, 1) + nrhs - 1) / std::max(nrhs, 1);
+  return (int)std::max<long long>(1, std::min(want, (N + kDotThreads - 1) / kDotThreads));
+}
 
 __global__ void k_dots_reduce(int count, int nblk, const double2 *__restrict__ partial,
                               double2 *__restrict__ out) {
