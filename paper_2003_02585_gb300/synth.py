@@ -108,6 +108,54 @@ def medium_random(n, h, seed: int, corr_len: float = 0.1, c_min: float = 1.0,
     return c_min + (c_max - c_min) * phi
 
 
+# Convergence tests of Section 5.1: the computational box B_L = [0, 1]^2 holds the interior box
+# (side 8/9 of it, cells 240 / 270 at the coarsest mesh) surrounded by a PML of 1/18 of the box on
+# every side, partitioned 4 x 4; kappa = 50 pi below the smooth two-layer interface.
+CONV_OFFSET = 1.0 / 18.0                 # interior-box origin in B_L coordinates
+CONV_KAPPA_DOWN = 50.0 * math.pi
+CONV_KAPPA_UP = 62.5 * math.pi
+CONV_ETA, CONV_EPS = 0.65, 0.01
+CONV_SOURCE = (0.28, 0.27)               # centre of Eq. (5.1)'s smooth source, B_L coordinates
+
+
+def conv_mesh(total: int):
+    """(interior nodes per axis, PML cells, h) of a Section 5.1 mesh of total^2 cells on B_L."""
+    if total % 18:
+        raise ValueError("the total mesh must be a multiple of 18 cells")
+    return total * 8 // 9, total // 18, 1.0 / total
+
+
+def medium_smooth_two_layer(n, h, offset: float = CONV_OFFSET):
+    """Wave speed of the smooth two-layer medium of Section 5.1 for omega = kappa_down:
+    kappa = kappa_down below eta, kappa_up above eta + eps, kappa_down (1 - w) + kappa_up w
+    in between with w = (x2 - eta) / eps (x2 in B_L coordinates); c = kappa_down / kappa."""
+    x2 = node_coords(n[1], h) + offset
+    w = np.clip((x2 - CONV_ETA) / CONV_EPS, 0.0, 1.0)
+    kappa = CONV_KAPPA_DOWN * (1.0 - w) + CONV_KAPPA_UP * w
+    c = (CONV_KAPPA_DOWN / kappa).reshape(n[1], 1)
+    return np.broadcast_to(c, (n[1], n[0])).astype(np.float64).copy()
+
+
+def smooth_source(n, h, kappa: float = CONV_KAPPA_DOWN, centre=CONV_SOURCE,
+                  offset: float = CONV_OFFSET, symmetric: bool = False):
+    """Eq. (5.1): f = 16 kappa^2 / pi^3 exp(-(4 kappa / pi)^2 |x - r|^2) at the interior nodes
+    (r in B_L coordinates); symmetric=True adds its mirror images in x1 -> 1 - x1, x2 -> 1 - x2
+    and both (the four-source case)."""
+    x1 = node_coords(n[0], h) + offset
+    x2 = node_coords(n[1], h) + offset
+    X2, X1 = np.meshgrid(x2, x1, indexing="ij")
+    a = (4.0 * kappa / math.pi) ** 2
+    amp = 16.0 * kappa * kappa / math.pi ** 3
+    cs = [centre]
+    if symmetric:
+        r1, r2 = centre
+        cs += [(1.0 - r1, r2), (r1, 1.0 - r2), (1.0 - r1, 1.0 - r2)]
+    f = np.zeros((n[1], n[0]))
+    for r1, r2 in cs:
+        f += amp * np.exp(-a * ((X1 - r1) ** 2 + (X2 - r2) ** 2))
+    return f
+
+
 @dataclass
 class Workload:
     """A named synthetic workload: problem parameters plus its seeded right-hand sides."""
