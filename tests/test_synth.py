@@ -25,3 +25,26 @@ def test_delta_source_off_node_weights():
     # x: 0.32 / 0.1 - 0.5 = 2.7 -> nodes 2 (weight 0.3) and 3 (0.7); y: midway between 4 and 5
     assert np.isclose(f[4, 2], 0.3 * 0.5 / h ** 2) and np.isclose(f[5, 3], 0.7 * 0.5 / h ** 2)
     assert np.isclose(f.sum() * h * h, 1.0)
+
+
+def test_section51_mesh_source_and_medium():
+    """Section 5.1 recipe: mesh geometry of the printed tables, the smooth source of Eq. (5.1)
+    (unit mass: 16 k^2 / pi^3 * pi / (4 k / pi)^2 = 1), its four mirror images, and the smooth
+    two-layer wave speed (c = 1 below 0.65, 0.8 above 0.66, monotone ramp between)."""
+    from paper_2003_02585_gb300 import synth
+    assert synth.conv_mesh(270) == (240, 15, 1.0 / 270)
+    assert synth.conv_mesh(1080) == (960, 60, 1.0 / 1080)
+    n_int, pml, h = synth.conv_mesh(540)
+    n = (n_int, n_int)
+    f1 = synth.smooth_source(n, h)
+    f4 = synth.smooth_source(n, h, symmetric=True)
+    assert abs(f1.sum() * h * h - 1.0) < 1e-6
+    assert abs(f4.sum() * h * h - 4.0) < 1e-6
+    # mirror symmetry of the four-source field about the centre of B_L (= centre of the interior)
+    assert np.allclose(f4, f4[::-1, :]) and np.allclose(f4, f4[:, ::-1])
+    c = synth.medium_smooth_two_layer(n, h)
+    x2 = (np.arange(n_int) + 0.5) * h + synth.CONV_OFFSET
+    assert np.all(c[x2 < 0.65] == 1.0) and np.allclose(c[x2 > 0.66], 0.8)
+    ramp = c[(x2 >= 0.65) & (x2 <= 0.66), 0]
+    assert ramp.size > 0 and np.all(np.diff(ramp) < 0)
+    assert np.all(c == c[:, :1])   # layered along x2 only
