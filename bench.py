@@ -344,7 +344,12 @@ def run_gpu(args):
     stats = ctx.kernel_stats()
     ctx.profile(False)
     work = ctx.work_per_ddm(R, wl.rounds)
-    roofline, roofline_kernels = (roofline_entry(stats, work, ddm_apps, args)
+    inf = ctx.info()
+    geometry = {"plan": inf["plan"], "nrhs": R, "nsub": inf["n_sub"], "T": inf["trace_len"],
+                "Nglob": int(np.prod(inf["G"][:len(wl.n)])),
+                "Nloc": int(np.prod(inf["M"][:len(wl.n)])),
+                "sweeps": (2 ** len(wl.n)) * wl.rounds}
+    roofline, roofline_kernels = (roofline_entry(stats, work, ddm_apps, args, geometry)
                                   if args.profile_steps > 0 else (None, []))
 
     cpu = None
@@ -407,7 +412,7 @@ SUBST_TRAFFIC = {("mixed", "const2d_640"): 48.68e6 + 0.99e6}
 TRACE_TRAFFIC = {("mixed", "const2d_640"): 40.26e6 + 0.08e6}
 
 
-def roofline_entry(stats, work, ddm_apps, args):
+def roofline_entry(stats, work, ddm_apps, args, geometry=None):
     """Rooflines of the two sweep kernel families from their event-timed totals.
 
     work = (substitution flops, trace-map flops) of one DDM application (dds_work_per_ddm:
@@ -453,6 +458,33 @@ def roofline_entry(stats, work, ddm_apps, args):
                         "frac": achieved / fp32_peak,
                         "traffic": TRACE_TRAFFIC.get((args.precision, args.workload)),
                         "launches": n_t, "avg_launch_ms": ms_t / n_t, "device_ms": ms_t})
+    # HBM-side kernels of the trace plan, from their algorithmic bytes per DDM application:
+    #   assembly (two launches): every local right-hand side written once, the source read once
+    #   over the owned ranges (which tile the global grid), and the final launch reads the trace
+    #   slots of every sweep;  extraction (two launches): the raw trace lines read and written,
+    #   then the owned nodes read locally and written to the global field (FP64).
+    geo = geometry or {}
+    if geo.get("plan") == 2 and geo.get("Nloc"):   # DDS_PLAN_TRACE
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        el = 16 if args.precision == "fp64" else 8
+        R, Ng, Nl, T = geo["nrhs"], geo["Nglob"], geo["Nloc"], geo["T"]
+        cols = R * geo["nsub"]
+        L = geo["sweeps"]
+        fam = {
+            "assemble": ("k_assemble (local right-hand sides: source + trace potentials)",
+                         2 * cols * Nl * el + 2 * R * Ng * 16 + cols * L * T * el),
+            "extract": ("k_extract (trace lines, owned nodes to the global field)",
+                        2 * cols * T * el + R * Ng * (el + 16)),
+        }
+        for key, (name, nbytes) in fam.items():
+            n_k, ms_k = stats.get(key, (0, 0.0))
+            if n_k > 0 and ms_k > 0:
+                achieved = nbytes * ddm_apps / (ms_k / 1e3) / 1e9
+                entries.append({"kernel": name, "bound": "hbm",
+                                "peak_source": f"{src} hbm_gbs", "achieved": achieved,
+                                "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                                "traffic": None, "bytes_per_ddm": nbytes,
+                                "launches": n_k, "avg_launch_ms": ms_k / n_k, "device_ms": ms_k})
     if not entries:
         return None, []
     main = dict(max(entries, key=lambda e: e["device_ms"]))
