@@ -558,7 +558,7 @@ def run_serving(args):
     media = serving.serving_media()
     reqs = serving.poisson_requests(rng, args.serve_requests, args.serve_rate, len(media))
     out = serving.run(reqs, media, budget_bytes=args.serve_budget_gb * 1e9, tol=args.tol,
-                      maxit=args.maxit, rounds=args.rounds or 2)
+                      maxit=args.serve_maxit, rounds=args.rounds or 2)
     lat = np.sort(out["latency_s"]) * 1e3
     line = {
         "metric": METRIC, "value": out["rhs"] / out["wall_s"], "unit": "RHS/s", "n_gpus": 1,
@@ -568,10 +568,12 @@ def run_serving(args):
         "config": {"workload": "serving: Poisson requests (1-32 sources) over 256^2 constant, "
                                "512^2 two-layer and 1024^2 random media, continuous batching",
                    "requests": len(reqs), "arrival_rate_per_s": args.serve_rate,
-                   "slots": out["slots"], "budget_gb": args.serve_budget_gb},
+                   "slots": out["slots"], "budget_gb": args.serve_budget_gb,
+                   "maxit": args.serve_maxit},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
         "setup_seconds": out["setup_s"], "max_relres": out["max_relres"],
-        "server_steps": out["steps"],
+        "server_steps": out["steps"], "max_iters_per_medium": out["max_iters"],
+        "p99_ms_per_medium": [1e3 * v for v in out["p99_s"]],
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -604,7 +606,9 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-rate", type=float, default=10.0, help="requests per second")
-    ap.add_argument("--serve-budget-gb", type=float, default=60.0)
+    ap.add_argument("--serve-budget-gb", type=float, default=120.0)
+    ap.add_argument("--serve-maxit", type=int, default=16,
+                    help="FGMRES iterations a serving slot is sized for (slot memory grows with it)")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -1660,6 +1660,9 @@ struct dds_server {
   };
   std::vector<Slot> slots;
   std::deque<std::pair<long long, std::unique_ptr<DBuf>>> queue;
+  // spent queue buffers, reused by later submissions (no cudaMalloc / cudaFree per request,
+  // both of which synchronise the whole device); reuse is ordered by the context's stream
+  std::vector<std::unique_ptr<DBuf>> pool;
   std::deque<int> finished;
   double2 *Vs(int s, int j) { return V.as<double2>() + ((long long)s * (maxit + 1) + j) * N; }
   double2 *Zs(int s, int j) { return Z.as<double2>() + ((long long)s * maxit + j) * N; }
@@ -1728,6 +1731,9 @@ dds_status server_admit(dds_server *srv) {
   dds_ctx *ctx = srv->ctx;
   cudaStream_t st = ctx->stream;
   const long long N = srv->N;
+  // every admission of this step is launched first; their norms come back in one read
+  std::vector<int> admitted;
+  std::vector<double2> b2(srv->S);
   for (int s = 0; s < srv->S && !srv->queue.empty(); ++s) {
     auto &sl = srv->slots[s];
     if (sl.state != 0) continue;
@@ -1743,13 +1749,18 @@ dds_status server_admit(dds_server *srv) {
     sl.g.assign(m + 1, cd(0, 0));
     ctx->launches += 3;
     SCK(launch_scale_J(st, ctx->g, ctx->tb, 1, req.second->as<double2>(), srv->Bs(s)));
+    srv->pool.push_back(std::move(req.second));   // later copies into it follow on the stream
     SCK(launch_dots(st, N, 1, 1, srv->Bs(s), 0, 0, srv->Bs(s), 0, srv->part.as<double2>(),
                     srv->Hd(s), server_nblk(srv)));
     SCK(launch_scale_by_norm(st, N, 1, srv->Bs(s), srv->Hd(s), srv->Vs(s, 0)));
-    double2 b2;
-    SCK(cudaMemcpyAsync(&b2, srv->Hd(s), sizeof(double2), cudaMemcpyDeviceToHost, st));
-    SCK(cudaStreamSynchronize(st));
-    sl.beta = std::sqrt(std::max(b2.x, 0.0));
+    SCK(cudaMemcpyAsync(&b2[s], srv->Hd(s), sizeof(double2), cudaMemcpyDeviceToHost, st));
+    admitted.push_back(s);
+  }
+  if (admitted.empty()) return DDS_OK;
+  SCK(cudaStreamSynchronize(st));
+  for (int s : admitted) {
+    auto &sl = srv->slots[s];
+    sl.beta = std::sqrt(std::max(b2[s].x, 0.0));
     sl.g[0] = sl.beta;
     if (sl.beta == 0.0) {   // zero source: the solution is zero
       sl.kused = 0;
@@ -1887,7 +1898,13 @@ dds_status dds_server_submit(dds_server *srv, const void *f, long long tag) {
   dds_ctx *ctx = srv->ctx;
   Busy busy(ctx);
   if (!busy.ok) return DDS_EBUSY;
-  auto buf = std::make_unique<DBuf>();
+  std::unique_ptr<DBuf> buf;
+  if (!srv->pool.empty()) {
+    buf = std::move(srv->pool.back());
+    srv->pool.pop_back();
+  } else {
+    buf = std::make_unique<DBuf>();
+  }
   const size_t fb = (size_t)srv->N * sizeof(double2);
   CK(buf->ensure(fb));
   CK(cudaMemcpyAsync(buf->p, f, fb, is_device_ptr(f) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,

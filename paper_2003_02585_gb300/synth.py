@@ -37,6 +37,25 @@ def gaussian_source(n, h, centre, width, cutoff: float = 6.0):
     return f
 
 
+def gaussian_source_patch(n, h, centre, width, cutoff: float = 6.0):
+    """The nonzero part of gaussian_source(n, h, centre, width, cutoff): (slices into the
+    n[::-1]-shaped field, values there).  Same formula on the same nodes, evaluated only inside
+    the bounding box of the cutoff sphere."""
+    d = len(n)
+    lo, hi = [], []
+    for a in range(d):
+        lo.append(max(0, int(math.floor((centre[a] - cutoff * width) / h - 0.5))))
+        hi.append(min(n[a], int(math.ceil((centre[a] + cutoff * width) / h - 0.5)) + 1))
+    coords = [(np.arange(lo[a], hi[a]) + 0.5) * h for a in range(d)]
+    grids = np.meshgrid(*coords[::-1], indexing="ij")
+    r2 = np.zeros(tuple(hi[a] - lo[a] for a in range(d))[::-1])
+    for a in range(d):
+        r2 = r2 + (grids[d - 1 - a] - centre[a]) ** 2
+    f = np.exp(-r2 / (2.0 * width * width)) / (2.0 * math.pi * width * width) ** (d / 2.0)
+    f[r2 > (cutoff * width) ** 2] = 0.0
+    return tuple(slice(lo[a], hi[a]) for a in range(d))[::-1], f
+
+
 def uniform_centres(rng, count: int, dim: int, lo: float, hi: float):
     return rng.uniform(lo, hi, size=(count, dim))
 
