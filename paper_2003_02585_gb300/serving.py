@@ -133,7 +133,11 @@ class MediumWorker(threading.Thread):
                         req.completion = time.perf_counter() - self.t0
                         del self.pending[req.rid]
                 if active == 0 and queued == 0 and not new:
-                    if self.stop and not self.pending:
+                    # stop only once nothing is in flight and nothing waits in the inbox (the
+                    # driver may add a request between this iteration's read and the stop flag)
+                    with self.lock:
+                        idle = not self.inbox
+                    if self.stop and not self.pending and idle:
                         return
                     time.sleep(0.0005)
         except Exception as e:  # surfaced by the driver
