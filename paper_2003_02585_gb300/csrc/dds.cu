@@ -109,6 +109,10 @@ struct dds_ctx {
   std::map<std::array<long long, 4>, GraphEntry> graphs;
   cudaStream_t gstream = nullptr;
   cudaEvent_t gev[2] = {nullptr, nullptr};
+  // host results: the solution's device-to-host copy runs on its own stream, overlapping the
+  // final true-residual computation
+  cudaStream_t out_stream = nullptr;
+  cudaEvent_t out_ev = nullptr;
   bool use_graphs = true;
   void clear_graphs() {
     for (auto &kv : graphs)
@@ -125,6 +129,8 @@ struct dds_ctx {
   ~dds_ctx() {
     clear_graphs();
     if (gstream) cudaStreamDestroy(gstream);
+    if (out_stream) cudaStreamDestroy(out_stream);
+    if (out_ev) cudaEventDestroy(out_ev);
     for (auto &e : gev)
       if (e) cudaEventDestroy(e);
     for (auto &e : ev_pool) {
@@ -1151,7 +1157,7 @@ struct Busy {
 // host reads them once per iteration for the Hessenberg / Givens bookkeeping.
 // ------------------------------------------------------------------------------------------
 dds_status fgmres(dds_ctx *ctx, const double2 *b, int nrhs, double2 *x, double tol, int maxit,
-                  int rounds, int *iters, std::vector<double> &relres) {
+                  int rounds, int *iters, std::vector<double> &relres, void *x_host = nullptr) {
   const Geom &g = ctx->g;
   cudaStream_t st = ctx->stream;
   const long long N = g.Nglob;
@@ -1313,6 +1319,14 @@ dds_status fgmres(dds_ctx *ctx, const double2 *b, int nrhs, double2 *x, double t
   } else {
     CK(cudaMemsetAsync(x, 0, vbytes, st));
   }
+  if (x_host != nullptr) {
+    // x is final: its copy to the host overlaps the true-residual computation below
+    if (!ctx->out_stream) CK(cudaStreamCreateWithFlags(&ctx->out_stream, cudaStreamNonBlocking));
+    if (!ctx->out_ev) CK(cudaEventCreateWithFlags(&ctx->out_ev, cudaEventDisableTiming));
+    CK(cudaEventRecord(ctx->out_ev, st));
+    CK(cudaStreamWaitEvent(ctx->out_stream, ctx->out_ev, 0));
+    CK(cudaMemcpyAsync(x_host, x, vbytes, cudaMemcpyDeviceToHost, ctx->out_stream));
+  }
   // true residual: R = A x - b
   double2 *Rv = V;
   LAUNCHK(DDS_K_KRYLOV, launch_apply_A(st, g, ctx->tb, nrhs, x, Rv, 0, b));
@@ -1399,13 +1413,19 @@ dds_status dds_solve(dds_ctx *ctx, const void *f, int nrhs, void *u, double tol,
   LAUNCHK(DDS_K_KRYLOV, launch_scale_J(ctx->stream, ctx->g, ctx->tb, nrhs, fd, ctx->bbuf.as<double2>()));
   int it = 0;
   std::vector<double> rel;
-  dds_status rs = fgmres(ctx, ctx->bbuf.as<double2>(), nrhs, ud, tol, maxit, rounds, &it, rel);
+  dds_status rs = fgmres(ctx, ctx->bbuf.as<double2>(), nrhs, ud, tol, maxit, rounds, &it, rel,
+                         uh ? u : nullptr);
+  if (uh && ctx->out_stream) {
+    // the host copy started inside fgmres (once x was final); wait for it on every path
+    const cudaError_t e = cudaStreamSynchronize(ctx->out_stream);
+    if (e != cudaSuccess && rs == DDS_OK) CK(e);
+  }
   if (rs != DDS_OK && rs != DDS_ENOCONV) return rs;
   r = check_errflag(ctx);
   if (r != DDS_OK) return r;
   if (iters) *iters = it;
   if (relres) for (int q = 0; q < nrhs; ++q) relres[q] = rel[q];
-  r = finish_out(ctx, u, bytes, uh);
+  r = finish_out(ctx, u, bytes, false);   // host results were copied by fgmres
   if (r != DDS_OK) return r;
   if (rs == DDS_ENOCONV) ctx->err = "FGMRES did not reach the tolerance within maxit";
   return rs;
