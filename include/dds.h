@@ -101,7 +101,10 @@ typedef struct {
  * success and is left untouched on failure. */
 dds_status dds_setup(const dds_problem *prob, dds_ctx **out);
 
-/* dds_sweep -- the DDM as a direct solver: `rounds` rounds of the 2^n diagonal sweeps of
+/* dds_sweep, dds_solve and dds_apply take 1 <= nrhs <= 65535 right-hand sides per call
+ * (DDS_EINVAL otherwise).
+ *
+ * dds_sweep -- the DDM as a direct solver: `rounds` rounds of the 2^n diagonal sweeps of
  * Algorithm 2.1 / 4.1 on the sources f (nrhs fields on the global extended grid), writing
  * u_DDM (Algorithm 2.1, last line) to u.  rounds >= 1 (Theorem 3.10 needs 2 in two-layer
  * media). */

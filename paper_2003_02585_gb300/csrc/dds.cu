@@ -54,6 +54,9 @@ struct StepPlan {            // launch lists of one (direction, step) or one pha
   int pan_off = 0, npanels = 0, pc = 1;
 };
 
+// right-hand sides per call: the batched FP64 kernels put the RHS on gridDim.y
+constexpr int kMaxRhs = 65535;
+
 struct CallPlan {            // all launch lists for one nrhs
   int nrhs = 0;
   std::vector<StepPlan> steps;   // [dir][step] for the direct plan (substitution panels)
@@ -1373,7 +1376,7 @@ dds_status dds_sweep(dds_ctx *ctx, const void *f, int nrhs, void *u, int rounds)
   Busy busy(ctx);
   if (!busy.ok) return DDS_EBUSY;
   ctx->err.clear();
-  if (!f || !u || nrhs <= 0 || rounds < 1) { ctx->err = "invalid argument"; return DDS_EINVAL; }
+  if (!f || !u || nrhs <= 0 || nrhs > kMaxRhs || rounds < 1) { ctx->err = "invalid argument"; return DDS_EINVAL; }
   const size_t bytes = (size_t)nrhs * ctx->g.Nglob * sizeof(double2);
   const double2 *fd;
   double2 *ud;
@@ -1397,7 +1400,7 @@ dds_status dds_solve(dds_ctx *ctx, const void *f, int nrhs, void *u, double tol,
   Busy busy(ctx);
   if (!busy.ok) return DDS_EBUSY;
   ctx->err.clear();
-  if (!f || !u || nrhs <= 0 || rounds < 1 || maxit < 1 || !(tol > 0)) {
+  if (!f || !u || nrhs <= 0 || nrhs > kMaxRhs || rounds < 1 || maxit < 1 || !(tol > 0)) {
     ctx->err = "invalid argument";
     return DDS_EINVAL;
   }
@@ -1436,7 +1439,7 @@ dds_status dds_apply(dds_ctx *ctx, const void *u, int nrhs, void *Au) {
   Busy busy(ctx);
   if (!busy.ok) return DDS_EBUSY;
   ctx->err.clear();
-  if (!u || !Au || nrhs <= 0) { ctx->err = "invalid argument"; return DDS_EINVAL; }
+  if (!u || !Au || nrhs <= 0 || nrhs > kMaxRhs) { ctx->err = "invalid argument"; return DDS_EINVAL; }
   const size_t bytes = (size_t)nrhs * ctx->g.Nglob * sizeof(double2);
   const double2 *ud;
   double2 *od;
