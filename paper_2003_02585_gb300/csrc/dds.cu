@@ -1217,10 +1217,15 @@ dds_status fgmres(dds_ctx *ctx, const double2 *b, int nrhs, double2 *x, double t
     CK(cudaMemcpyAsync(hh.data(), hdev, (size_t)nrhs * (2 * nv + 2) * sizeof(double2),
                        cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    // Reorthogonalise where the first pass cancelled enough to matter.  After one classical pass
+    // the new vector's loss of orthogonality is about sqrt(N) eps ||w0|| / ||w1|| (inner products
+    // of length N rounded in FP64); FGMRES to tol needs it well below tol, so the second pass runs
+    // where ||w1|| < eta ||w0||, eta = sqrt(N) eps / (0.01 tol), capped at the DGKS 1/sqrt(2).
+    const double eta = std::min(std::sqrt(0.5), std::sqrt((double)N) * 2.2e-16 / (0.01 * tol));
     bool second = false;
     for (int r = 0; r < nrhs; ++r) {
       const double w0 = hh[(size_t)r * (nv + 1) + nv].x, w1 = hh[(size_t)nrhs * (2 * nv + 1) + r].x;
-      if (!(w1 > 0.5 * w0)) second = true;   // ||w1|| <= ||w0|| / sqrt(2): cancellation
+      if (!(w1 > eta * eta * w0)) second = true;   // squared norms
     }
     // The second pass only keeps V_{j+1} orthogonal.  If the first-pass column already meets the
     // tolerance for every active RHS (or this is the last iteration), V_{j+1} is never used and
