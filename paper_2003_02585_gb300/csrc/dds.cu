@@ -1159,7 +1159,7 @@ struct Busy {
 // Gram-Schmidt coefficients stay on the device between the dot and update kernels, and the
 // host reads them once per iteration for the Hessenberg / Givens bookkeeping.
 // ------------------------------------------------------------------------------------------
-dds_status fgmres(dds_ctx *ctx, const double2 *b, int nrhs, double2 *x, double tol, int maxit,
+dds_status fgmres(dds_ctx *ctx, const double2 *f, int nrhs, double2 *x, double tol, int maxit,
                   int rounds, int *iters, std::vector<double> &relres, void *x_host = nullptr) {
   const Geom &g = ctx->g;
   cudaStream_t st = ctx->stream;
@@ -1181,14 +1181,27 @@ dds_status fgmres(dds_ctx *ctx, const double2 *b, int nrhs, double2 *x, double t
   CK(ctx->coefbuf.ensure((size_t)nrhs * (maxit + 1) * sizeof(double2)));
   double2 *hdev = ctx->dots_out.as<double2>();
   double2 *part = ctx->dots_part.as<double2>();
+  CK(ctx->scalebuf.ensure((size_t)nrhs * (2 * maxit + 2) * sizeof(double)));   // both passes
   std::vector<double2> hh((size_t)nrhs * (2 * maxit + 4));
-  // beta = ||b||, V_0 = b / beta
+  // The basis is kept unnormalised: slot i holds V'_i = s_i V_i with host scales s_i per RHS
+  // (no normalisation pass over the data).  Inner products d_i = V'_i^H w' give
+  // h_ij = d_i / (s_i s_j), the update w' -= sum_i (d_i / s_i^2) V'_i removes the same
+  // projections, the DDM is linear so Z'_j = s_j Z_j, and x = sum_j (y_j / s_j) Z'_j.
+  // V'_0 = b = J f, s_0 = beta = ||b||.
+  const double2 *b = V;
+  LAUNCHK(DDS_K_KRYLOV, launch_scale_J(st, g, ctx->tb, nrhs, f, V));
   LAUNCHK(DDS_K_KRYLOV, launch_dots(st, N, nrhs, 1, b, 0, N, b, N, part, hdev, nblk));
-  LAUNCHK(DDS_K_KRYLOV, launch_scale_by_norm(st, N, nrhs, b, hdev, V));
   CK(cudaMemcpyAsync(hh.data(), hdev, nrhs * sizeof(double2), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   std::vector<double> beta(nrhs);
   for (int r = 0; r < nrhs; ++r) beta[r] = std::sqrt(std::max(hh[r].x, 0.0));
+  std::vector<double> sc((size_t)nrhs * (maxit + 1), 0.0);   // s_i per RHS
+  for (int r = 0; r < nrhs; ++r) sc[(size_t)r * (maxit + 1)] = beta[r];
+  auto inv2 = [](double v) {   // 1 / v^2, 0 for a vanished vector
+    const double q = v > 0.0 ? 1.0 / (v * v) : 0.0;
+    return std::isfinite(q) ? q : 0.0;
+  };
+  std::vector<double> cscale((size_t)nrhs * (maxit + 1));
   const int m = maxit;
   std::vector<cd> H((size_t)nrhs * (m + 1) * m, cd(0, 0)), cs((size_t)nrhs * m), sn((size_t)nrhs * m),
       gg((size_t)nrhs * (m + 1), cd(0, 0));
@@ -1211,9 +1224,16 @@ dds_status fgmres(dds_ctx *ctx, const double2 *b, int nrhs, double2 *x, double t
     double2 *h1 = hdev;                                        // [nrhs][nv + 1]
     double2 *h2 = hdev + (size_t)nrhs * (nv + 1);              // [nrhs][nv]
     double2 *hn = h2 + (size_t)nrhs * nv;                      // [nrhs]
+    // update scales 1 / s_i^2, laid out like h1 ([nrhs][nv + 1]) and like h2 ([nrhs][nv])
+    for (int r = 0; r < nrhs; ++r)
+      for (int i = 0; i <= nv; ++i)
+        cscale[(size_t)r * (nv + 1) + i] = i < nv ? inv2(sc[(size_t)r * (m + 1) + i]) : 0.0;
+    double *cs1 = ctx->scalebuf.as<double>();
+    CK(cudaMemcpyAsync(cs1, cscale.data(), (size_t)nrhs * (nv + 1) * sizeof(double),
+                       cudaMemcpyHostToDevice, st));
     LAUNCHK(DDS_K_KRYLOV, launch_dots(st, N, nrhs, nv + 1, V, vs, N, W, N, part, h1, nblk));
     LAUNCHK(DDS_K_KRYLOV, launch_combination(st, N, nrhs, nv, V, vs, N, h1, nv + 1, -1.0, W, N,
-                                             false, part, hn, nblk));
+                                             false, part, hn, nblk, cs1));
     CK(cudaMemcpyAsync(hh.data(), hdev, (size_t)nrhs * (2 * nv + 2) * sizeof(double2),
                        cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -1238,11 +1258,14 @@ dds_status fgmres(dds_ctx *ctx, const double2 *b, int nrhs, double2 *x, double t
         for (int r = 0; r < nrhs && last; ++r) {
           if (done[r]) continue;
           std::vector<cd> col(j + 2);
+          const double sj = sc[(size_t)r * (m + 1) + j];
+          if (!(sj > 0.0)) continue;
           for (int i = 0; i <= j; ++i) {
             const double2 a = hh[(size_t)r * (nv + 1) + i];
-            col[i] = cd(a.x, a.y);
+            const double si = sc[(size_t)r * (m + 1) + i];
+            col[i] = si > 0.0 ? cd(a.x, a.y) / (si * sj) : cd(0, 0);
           }
-          col[j + 1] = std::sqrt(std::max(hh[(size_t)nrhs * (2 * nv + 1) + r].x, 0.0));
+          col[j + 1] = std::sqrt(std::max(hh[(size_t)nrhs * (2 * nv + 1) + r].x, 0.0)) / sj;
           for (int i = 0; i < j; ++i) {
             const cd a = col[i], bb = col[i + 1];
             const cd c = cs[(size_t)r * m + i], sv = sn[(size_t)r * m + i];
@@ -1259,21 +1282,31 @@ dds_status fgmres(dds_ctx *ctx, const double2 *b, int nrhs, double2 *x, double t
     }
     std::vector<double2> h2h((size_t)nrhs * nv, make_double2(0.0, 0.0));
     if (second) {
+      for (int r = 0; r < nrhs; ++r)
+        for (int i = 0; i < nv; ++i)
+          cscale[(size_t)r * nv + i] = inv2(sc[(size_t)r * (m + 1) + i]);
+      double *cs2 = ctx->scalebuf.as<double>() + (size_t)nrhs * (nv + 1);
+      CK(cudaMemcpyAsync(cs2, cscale.data(), (size_t)nrhs * nv * sizeof(double),
+                         cudaMemcpyHostToDevice, st));
       LAUNCHK(DDS_K_KRYLOV, launch_dots(st, N, nrhs, nv, V, vs, N, W, N, part, h2, nblk));
       LAUNCHK(DDS_K_KRYLOV, launch_combination(st, N, nrhs, nv, V, vs, N, h2, nv, -1.0, W, N,
-                                               false, part, hn, nblk));
+                                               false, part, hn, nblk, cs2));
       CK(cudaMemcpyAsync(h2h.data(), h2, (size_t)nrhs * nv * sizeof(double2), cudaMemcpyDeviceToHost, st));
       CK(cudaMemcpyAsync(hh.data() + (size_t)nrhs * (2 * nv + 1), hn, nrhs * sizeof(double2),
                          cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
     }
     for (int r = 0; r < nrhs; ++r) {
-      const double hnorm = std::sqrt(std::max(hh[(size_t)nrhs * (2 * nv + 1) + r].x, 0.0));
+      // s_{j+1} = ||W'||, and the Hessenberg column in normalised terms
+      const double wn = std::sqrt(std::max(hh[(size_t)nrhs * (2 * nv + 1) + r].x, 0.0));
+      const double sj = sc[(size_t)r * (m + 1) + j];
+      sc[(size_t)r * (m + 1) + j + 1] = wn;
       for (int i = 0; i <= j; ++i) {
         const double2 a = hh[(size_t)r * (nv + 1) + i], bq = h2h[(size_t)r * nv + i];
-        Hat(r, i, j) = cd(a.x + bq.x, a.y + bq.y);
+        const double si = sc[(size_t)r * (m + 1) + i];
+        Hat(r, i, j) = si > 0.0 && sj > 0.0 ? cd(a.x + bq.x, a.y + bq.y) / (si * sj) : cd(0, 0);
       }
-      Hat(r, j + 1, j) = hnorm;
+      Hat(r, j + 1, j) = sj > 0.0 ? wn / sj : 0.0;
     }
     k = j + 1;
     bool all = true;
@@ -1303,8 +1336,6 @@ dds_status fgmres(dds_ctx *ctx, const double2 *b, int nrhs, double2 *x, double t
       else all = false;
     }
     if (all) break;
-    // V_{j+1} = W / ||W|| only when another iteration follows
-    if (j + 1 < m) LAUNCHK(DDS_K_KRYLOV, launch_scale_by_norm(st, N, nrhs, W, hn, W));
   }
   *iters = k;
   // x = sum_i Z_i y_i per RHS (one update kernel over all k basis vectors)
@@ -1317,7 +1348,11 @@ dds_status fgmres(dds_ctx *ctx, const double2 *b, int nrhs, double2 *x, double t
       for (int q = i + 1; q < kr; ++q) s -= Hat(r, i, q) * y[q];
       y[i] = s / Hat(r, i, i);
     }
-    for (int i = 0; i < kr; ++i) ycoef[(size_t)r * k + i] = make_double2(y[i].real(), y[i].imag());
+    for (int i = 0; i < kr; ++i) {   // x = sum_i (y_i / s_i) Z'_i
+      const double si = sc[(size_t)r * (m + 1) + i];
+      const cd yi = si > 0.0 ? y[i] / si : cd(0, 0);
+      ycoef[(size_t)r * k + i] = make_double2(yi.real(), yi.imag());
+    }
   }
   if (k > 0) {
     CK(cudaMemcpyAsync(ctx->coefbuf.p, ycoef.data(), (size_t)nrhs * k * sizeof(double2),
@@ -1335,8 +1370,8 @@ dds_status fgmres(dds_ctx *ctx, const double2 *b, int nrhs, double2 *x, double t
     CK(cudaStreamWaitEvent(ctx->out_stream, ctx->out_ev, 0));
     CK(cudaMemcpyAsync(x_host, x, vbytes, cudaMemcpyDeviceToHost, ctx->out_stream));
   }
-  // true residual: R = A x - b
-  double2 *Rv = V;
+  // true residual: R = A x - b (b = V'_0 stays in slot 0; slot 1 is free now)
+  double2 *Rv = V + vs;
   LAUNCHK(DDS_K_KRYLOV, launch_apply_A(st, g, ctx->tb, nrhs, x, Rv, 0, b));
   LAUNCHK(DDS_K_KRYLOV, launch_dots(st, N, nrhs, 1, Rv, 0, N, Rv, N, part, hdev, nblk));
   CK(cudaMemcpyAsync(hh.data(), hdev, nrhs * sizeof(double2), cudaMemcpyDeviceToHost, st));
@@ -1417,12 +1452,9 @@ dds_status dds_solve(dds_ctx *ctx, const void *f, int nrhs, void *u, double tol,
   if (r != DDS_OK) return r;
   r = stage_out_ptr(ctx, u, bytes, &ud, &uh);
   if (r != DDS_OK) return r;
-  CK(ctx->bbuf.ensure(bytes));
-  LAUNCHK(DDS_K_KRYLOV, launch_scale_J(ctx->stream, ctx->g, ctx->tb, nrhs, fd, ctx->bbuf.as<double2>()));
   int it = 0;
   std::vector<double> rel;
-  dds_status rs = fgmres(ctx, ctx->bbuf.as<double2>(), nrhs, ud, tol, maxit, rounds, &it, rel,
-                         uh ? u : nullptr);
+  dds_status rs = fgmres(ctx, fd, nrhs, ud, tol, maxit, rounds, &it, rel, uh ? u : nullptr);
   if (uh && ctx->out_stream) {
     // the host copy started inside fgmres (once x was final); wait for it on every path
     const cudaError_t e = cudaStreamSynchronize(ctx->out_stream);

@@ -281,13 +281,14 @@ cudaError_t launch_scale_J(cudaStream_t st, const Geom &g, const Tables &tb, int
 cudaError_t launch_dots(cudaStream_t st, long long N, int nrhs, int nv, const double2 *V,
                         long long v_stride_vec, long long v_stride_rhs, const double2 *w,
                         long long w_stride_rhs, double2 *partial, double2 *out, int nblk);
-// w = (overwrite ? 0 : w) + sign * sum_i V_i coef_i per RHS; with nrm2, also
+// w = (overwrite ? 0 : w) + sign * sum_i V_i coef_i (x cscale_i if given) per RHS; with nrm2, also
 // nrm2[rhs] = ||w[rhs]||^2 of the result in the same pass (nblk blocks per RHS, partial sized
 // nrhs * nblk)
 cudaError_t launch_combination(cudaStream_t st, long long N, int nrhs, int nv, const double2 *V,
                                long long vsv, long long vsr, const double2 *coef, int cstride,
                                double sign, double2 *w, long long wsr, bool overwrite,
-                               double2 *partial, double2 *nrm2, int nblk);
+                               double2 *partial, double2 *nrm2, int nblk,
+                               const double *cscale = nullptr);
 cudaError_t launch_sub_combination(cudaStream_t st, long long N, int nrhs, int nv, const double2 *V,
                                    long long v_stride_vec, long long v_stride_rhs,
                                    const double2 *coef, double2 *w, long long w_stride_rhs,

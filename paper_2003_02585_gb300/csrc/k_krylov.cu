@@ -245,6 +245,7 @@ __global__ void k_dots_reduce(int count, int nblk, const double2 *__restrict__ p
 }
 
 // w[rhs] = (overwrite ? 0 : w[rhs]) + sign * sum_{i < nv} V_i[rhs] * coef[rhs * cstride + i]
+//          (* cscale[rhs * cstride + i] when cscale is given)
 // (grid.y = rhs).  The signed coefficients sit in shared memory; two elements per thread and
 // iteration are in flight.  With `partial`, the block also sums |w|^2 of the result into
 // partial[rhs * gridDim.x + blockIdx.x] (the norm of a Gram-Schmidt update in the same pass).
@@ -254,6 +255,7 @@ __global__ void __launch_bounds__(256) k_combination(long long N, int nv,
                                                      const double2 *__restrict__ V, long long vsv,
                                                      long long vsr, const double2 *__restrict__ coef,
                                                      int cstride, double sign,
+                                                     const double *__restrict__ cscale,
                                                      double2 *__restrict__ w, long long wsr,
                                                      int overwrite, double2 *__restrict__ partial) {
   __shared__ double2 cs[kCombMaxNv];
@@ -261,7 +263,8 @@ __global__ void __launch_bounds__(256) k_combination(long long N, int nv,
   const int rhs = blockIdx.y;
   for (int i = threadIdx.x; i < nv; i += blockDim.x) {
     const double2 c = coef[(long long)rhs * cstride + i];
-    cs[i] = make_double2(sign * c.x, sign * c.y);
+    const double f = cscale != nullptr ? sign * cscale[(long long)rhs * cstride + i] : sign;
+    cs[i] = make_double2(f * c.x, f * c.y);
   }
   __syncthreads();
   double2 *ww = w + rhs * wsr;
@@ -379,14 +382,15 @@ cudaError_t launch_dots(cudaStream_t st, long long N, int nrhs, int nv, const do
 cudaError_t launch_combination(cudaStream_t st, long long N, int nrhs, int nv, const double2 *V,
                                long long vsv, long long vsr, const double2 *coef, int cstride,
                                double sign, double2 *w, long long wsr, bool overwrite,
-                               double2 *partial, double2 *nrm2, int nblk) {
+                               double2 *partial, double2 *nrm2, int nblk, const double *cscale) {
   const dim3 grid = nrm2 != nullptr ? dim3((unsigned)nblk, (unsigned)nrhs) : grid_rhs(N, nrhs);
   // groups of at most kCombMaxNv vectors; the norm comes with the last group
   for (int i0 = 0; i0 < nv || i0 == 0; i0 += kCombMaxNv) {
     const int cnt = std::min(kCombMaxNv, nv - i0);
     const bool last = i0 + kCombMaxNv >= nv;
     k_combination<<<grid, 256, 0, st>>>(N, std::max(cnt, 0), V + i0 * vsv, vsv, vsr, coef + i0,
-                                        cstride, sign, w, wsr, overwrite && i0 == 0 ? 1 : 0,
+                                        cstride, sign, cscale != nullptr ? cscale + i0 : nullptr,
+                                        w, wsr, overwrite && i0 == 0 ? 1 : 0,
                                         nrm2 != nullptr && last ? partial : nullptr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || last) break;
