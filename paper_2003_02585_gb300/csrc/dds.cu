@@ -1711,6 +1711,7 @@ struct dds_server {
   double tol = 1e-6;
   long long N = 0;
   DBuf V, Z, B, U, bin, bout, hdev, part, coef;
+  DBuf offs, hb;   // batched Arnoldi: per-entry base offsets, and h / norms in batch order
   struct Slot {
     int state = 0;              // 0 free, 1 active, 2 finished (waiting for poll)
     long long tag = 0;
@@ -1850,38 +1851,62 @@ dds_status server_step(dds_server *srv, int *active_out, int *queued_out) {
     r = ddm(ctx, srv->bin.as<double2>(), k, srv->bout.as<double2>(), srv->rounds);
     if (r != DDS_OK) return r;
     const int nblk = server_nblk(srv);
+    const long long vslot = (long long)(srv->maxit + 1) * N, zslot = (long long)srv->maxit * N;
     for (int i = 0; i < k; ++i) {
       const int s = act[i];
-      const int j = srv->slots[s].j;
-      double2 *Zj = srv->Zs(s, j), *W = srv->Vs(s, j + 1), *h = srv->Hd(s);
-      SCK(cudaMemcpyAsync(Zj, srv->bout.as<double2>() + (long long)i * N, N * sizeof(double2),
-                          cudaMemcpyDeviceToDevice, st));
-      // FP64 Arnoldi step: classical Gram-Schmidt applied twice, then normalisation
-      ctx->launches += 7;
-      SCK(launch_apply_A(st, ctx->g, ctx->tb, 1, Zj, W, 0));
-      SCK(launch_dots(st, N, 1, j + 1, srv->Vs(s, 0), N, 0, W, 0, srv->part.as<double2>(), h, nblk));
-      SCK(launch_sub_combination(st, N, 1, j + 1, srv->Vs(s, 0), N, 0, h, W, 0, -1.0, j + 1));
-      SCK(launch_dots(st, N, 1, j + 1, srv->Vs(s, 0), N, 0, W, 0, srv->part.as<double2>(),
-                      h + srv->maxit + 1, nblk));
-      SCK(launch_sub_combination(st, N, 1, j + 1, srv->Vs(s, 0), N, 0, h + srv->maxit + 1, W, 0,
-                                 -1.0, j + 1));
-      SCK(launch_dots(st, N, 1, 1, W, 0, 0, W, 0, srv->part.as<double2>(), h + 2 * srv->maxit + 2,
-                      nblk));
-      SCK(launch_scale_by_norm(st, N, 1, W, h + 2 * srv->maxit + 2, W));
+      SCK(cudaMemcpyAsync(srv->Zs(s, srv->slots[s].j), srv->bout.as<double2>() + (long long)i * N,
+                          N * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     }
-    const int stride = 2 * srv->maxit + 3;
-    std::vector<double2> hh((size_t)srv->S * stride);
-    SCK(cudaMemcpyAsync(hh.data(), srv->hdev.p, hh.size() * sizeof(double2), cudaMemcpyDeviceToHost, st));
+    // FP64 Arnoldi step, batched over the active slots at the same iteration j (their vectors
+    // are addressed through offset tables): classical Gram-Schmidt twice, the norm with the
+    // second update, then normalisation.  hb holds, per group, h1 [k][j+1], h2 [k][j+1] and
+    // the squared norms [k].
+    std::map<int, std::vector<int>> groups;   // j -> slots
+    for (int s : act) groups[srv->slots[s].j].push_back(s);
+    std::vector<long long> off(3 * (size_t)srv->S);
+    std::vector<std::array<long long, 3>> where(srv->S);   // slot -> (h1, h2, norm) offsets in hb
+    long long used = 0;
+    double2 *hb = srv->hb.as<double2>();
+    long long *doff = srv->offs.as<long long>();
+    for (auto &grp : groups) {
+      const int j = grp.first, kg = (int)grp.second.size(), nv = j + 1;
+      for (int i = 0; i < kg; ++i) {
+        const int s = grp.second[i];
+        off[i] = (long long)s * zslot + (long long)j * N;                   // Z_j
+        off[srv->S + i] = (long long)s * vslot;                             // V_0
+        off[2 * srv->S + i] = (long long)s * vslot + (long long)(j + 1) * N;   // W = V_{j+1}
+        where[s] = {used + (long long)i * nv, used + (long long)kg * nv + (long long)i * nv,
+                    used + 2LL * kg * nv + i};
+      }
+      SCK(cudaMemcpyAsync(doff, off.data(), 3 * srv->S * sizeof(long long),
+                          cudaMemcpyHostToDevice, st));
+      const long long *zo = doff, *vo = doff + srv->S, *wo = doff + 2 * srv->S;
+      double2 *h1 = hb + used, *h2 = h1 + (long long)kg * nv, *hn = h2 + (long long)kg * nv;
+      double2 *Vb = srv->V.as<double2>();
+      ctx->launches += 6;
+      SCK(launch_apply_A(st, ctx->g, ctx->tb, kg, srv->Z.as<double2>(), Vb, 0, nullptr, zo, wo));
+      SCK(launch_dots(st, N, kg, nv, Vb, N, 0, Vb, 0, srv->part.as<double2>(), h1, nblk, vo, wo));
+      SCK(launch_combination(st, N, kg, nv, Vb, N, 0, h1, nv, -1.0, Vb, 0, false, nullptr,
+                             nullptr, 0, nullptr, vo, wo));
+      SCK(launch_dots(st, N, kg, nv, Vb, N, 0, Vb, 0, srv->part.as<double2>(), h2, nblk, vo, wo));
+      SCK(launch_combination(st, N, kg, nv, Vb, N, 0, h2, nv, -1.0, Vb, 0, false,
+                             srv->part.as<double2>(), hn, nblk, nullptr, vo, wo));
+      SCK(launch_scale_by_norm(st, N, kg, Vb, hn, Vb, wo));
+      used += 2LL * kg * nv + kg;
+      // (the next group's offset table is copied in stream order, after these kernels)
+    }
+    std::vector<double2> hh((size_t)used);
+    SCK(cudaMemcpyAsync(hh.data(), hb, (size_t)used * sizeof(double2), cudaMemcpyDeviceToHost, st));
     SCK(cudaStreamSynchronize(st));
     const int m = srv->maxit;
     for (int i = 0; i < k; ++i) {
       const int s = act[i];
       auto &sl = srv->slots[s];
       const int j = sl.j;
-      const double2 *h = hh.data() + (size_t)s * stride;
+      const double2 *h1 = hh.data() + where[s][0], *h2 = hh.data() + where[s][1];
       auto Hat = [&](int a, int b) -> cd & { return sl.H[(size_t)a * m + b]; };
-      for (int q = 0; q <= j; ++q) Hat(q, j) = cd(h[q].x + h[m + 1 + q].x, h[q].y + h[m + 1 + q].y);
-      const double hn = std::sqrt(std::max(h[2 * m + 2].x, 0.0));
+      for (int q = 0; q <= j; ++q) Hat(q, j) = cd(h1[q].x + h2[q].x, h1[q].y + h2[q].y);
+      const double hn = std::sqrt(std::max(hh[where[s][2]].x, 0.0));
       Hat(j + 1, j) = hn;
       for (int q = 0; q < j; ++q) {
         const cd a = Hat(q, j), bb = Hat(q + 1, j), c = sl.cs[q], sn = sl.sn[q];
@@ -1939,9 +1964,11 @@ dds_status dds_server_create(dds_ctx *ctx, int max_slots, double tol, int maxit,
             srv->B.ensure(S * fb) == cudaSuccess && srv->U.ensure(S * fb) == cudaSuccess &&
             srv->bin.ensure(S * fb) == cudaSuccess && srv->bout.ensure(S * fb) == cudaSuccess &&
             srv->hdev.ensure(S * (2 * maxit + 3) * sizeof(double2)) == cudaSuccess &&
-            srv->part.ensure((size_t)(maxit + 2) * (srv->N / dots_chunk() + 2) * sizeof(double2)) ==
+            srv->part.ensure(S * (maxit + 2) * (srv->N / dots_chunk() + 2) * sizeof(double2)) ==
                 cudaSuccess &&
-            srv->coef.ensure((size_t)(maxit + 2) * sizeof(double2)) == cudaSuccess;
+            srv->coef.ensure((size_t)(maxit + 2) * sizeof(double2)) == cudaSuccess &&
+            srv->offs.ensure(3 * S * sizeof(long long)) == cudaSuccess &&
+            srv->hb.ensure(S * (2 * maxit + 3) * sizeof(double2)) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     ctx->err = "dds_server_create: device memory for " + std::to_string(max_slots) +

@@ -273,14 +273,18 @@ cudaError_t launch_copy_local_back(cudaStream_t st, long long n, const typename 
 
 // Krylov / operator kernels (FP64)
 // Au = A u (divided by J if divide_by_J), minus sub when sub is not null
+// Batched FP64 kernels: entry r of a vector family starts at base + r * stride, or at
+// base + off[r] when an offset table (device memory) is given (non-contiguous server slots).
 cudaError_t launch_apply_A(cudaStream_t st, const Geom &g, const Tables &tb, int nrhs,
                            const double2 *u, double2 *Au, int divide_by_J,
-                           const double2 *sub = nullptr);
+                           const double2 *sub = nullptr, const long long *uoff = nullptr,
+                           const long long *aoff = nullptr);
 cudaError_t launch_scale_J(cudaStream_t st, const Geom &g, const Tables &tb, int nrhs,
                            const double2 *f, double2 *b);
 cudaError_t launch_dots(cudaStream_t st, long long N, int nrhs, int nv, const double2 *V,
                         long long v_stride_vec, long long v_stride_rhs, const double2 *w,
-                        long long w_stride_rhs, double2 *partial, double2 *out, int nblk);
+                        long long w_stride_rhs, double2 *partial, double2 *out, int nblk,
+                        const long long *voff = nullptr, const long long *woff = nullptr);
 // w = (overwrite ? 0 : w) + sign * sum_i V_i coef_i (x cscale_i if given) per RHS; with nrm2, also
 // nrm2[rhs] = ||w[rhs]||^2 of the result in the same pass (nblk blocks per RHS, partial sized
 // nrhs * nblk)
@@ -288,7 +292,8 @@ cudaError_t launch_combination(cudaStream_t st, long long N, int nrhs, int nv, c
                                long long vsv, long long vsr, const double2 *coef, int cstride,
                                double sign, double2 *w, long long wsr, bool overwrite,
                                double2 *partial, double2 *nrm2, int nblk,
-                               const double *cscale = nullptr);
+                               const double *cscale = nullptr, const long long *voff = nullptr,
+                               const long long *woff = nullptr);
 cudaError_t launch_sub_combination(cudaStream_t st, long long N, int nrhs, int nv, const double2 *V,
                                    long long v_stride_vec, long long v_stride_rhs,
                                    const double2 *coef, double2 *w, long long w_stride_rhs,
@@ -296,7 +301,7 @@ cudaError_t launch_sub_combination(cudaStream_t st, long long N, int nrhs, int n
 cudaError_t launch_scale_vec(cudaStream_t st, long long N, int nrhs, const double2 *in,
                              const double *inv_scale, double2 *out);
 cudaError_t launch_scale_by_norm(cudaStream_t st, long long N, int nrhs, const double2 *in,
-                                const double2 *nrm2, double2 *out);
+                                const double2 *nrm2, double2 *out, const long long *off = nullptr);
 int dots_chunk();
 int dots_blocks(long long N, int nrhs);   // blocks per RHS of the dot / norm kernels
 

@@ -21,7 +21,8 @@ __device__ inline double2 crecip64(double2 z) {
 template <int DIM>
 __global__ void __launch_bounds__(256) k_apply_A(Geom g, Tables tb, int nrhs, const double2 *__restrict__ u,
                           double2 *__restrict__ Au, int divide_by_J,
-                          const double2 *__restrict__ sub) {
+                          const double2 *__restrict__ sub, const long long *__restrict__ uoff,
+                          const long long *__restrict__ aoff) {
   const int N = (int)g.Nglob;
   const int G0 = g.G[0], G1 = g.G[1];
   const long long total = (long long)nrhs * N;
@@ -32,7 +33,7 @@ __global__ void __launch_bounds__(256) k_apply_A(Geom g, Tables tb, int nrhs, co
     p[0] = q % G0;
     p[1] = (q / G0) % G1;
     p[2] = DIM == 3 ? q / (G0 * G1) : 0;
-    const double2 *ur = u + (long long)r * N + q;
+    const double2 *ur = u + (uoff != nullptr ? uoff[r] : (long long)r * N) + q;
     const double2 c0 = tb.c0[q];
     double2 cpv[DIM], cmv[DIM], up[DIM], um[DIM];
     int st = 1;
@@ -89,7 +90,7 @@ __global__ void __launch_bounds__(256) k_apply_A(Geom g, Tables tb, int nrhs, co
       sum = cmul(sum, crecip64(J));
     }
     if (sub != nullptr && !(fold && real)) sum = csub(sum, sub[i]);
-    Au[i] = sum;
+    Au[aoff != nullptr ? aoff[r] + q : i] = sum;
   }
 }
 
@@ -127,17 +128,20 @@ template <int NV>
 __global__ void __launch_bounds__(kDotThreads) k_dots(long long N, int nv, int i0,
                                                      const double2 *__restrict__ V, long long vsv,
                                                      long long vsr, const double2 *__restrict__ w,
-                                                     long long wsr, double2 *__restrict__ partial) {
+                                                     long long wsr, double2 *__restrict__ partial,
+                                                     const long long *__restrict__ voff,
+                                                     const long long *__restrict__ woff) {
   __shared__ double red[2 * NV][kDotThreads / 32];
   const int blk = blockIdx.x, nblk = gridDim.x;
   const int rhs = blockIdx.y;
-  const double2 *ww = w + rhs * wsr;
+  const double2 *ww = w + (woff != nullptr ? woff[rhs] : rhs * wsr);
+  const double2 *vb = V + (voff != nullptr ? voff[rhs] : rhs * vsr);
   const double2 *v[NV];
   bool self[NV];
   double sr[NV], si[NV];
 #pragma unroll
   for (int i = 0; i < NV; ++i) {
-    v[i] = V + (i0 + i) * vsv + rhs * vsr;
+    v[i] = vb + (i0 + i) * vsv;
     self[i] = v[i] == ww;
     sr[i] = 0.0;
     si[i] = 0.0;
@@ -257,7 +261,9 @@ __global__ void __launch_bounds__(256) k_combination(long long N, int nv,
                                                      int cstride, double sign,
                                                      const double *__restrict__ cscale,
                                                      double2 *__restrict__ w, long long wsr,
-                                                     int overwrite, double2 *__restrict__ partial) {
+                                                     int overwrite, double2 *__restrict__ partial,
+                                                     const long long *__restrict__ voff,
+                                                     const long long *__restrict__ woff) {
   __shared__ double2 cs[kCombMaxNv];
   __shared__ double red[8];
   const int rhs = blockIdx.y;
@@ -267,8 +273,8 @@ __global__ void __launch_bounds__(256) k_combination(long long N, int nv,
     cs[i] = make_double2(f * c.x, f * c.y);
   }
   __syncthreads();
-  double2 *ww = w + rhs * wsr;
-  const double2 *vr = V + rhs * vsr;
+  double2 *ww = w + (woff != nullptr ? woff[rhs] : rhs * wsr);
+  const double2 *vr = V + (voff != nullptr ? voff[rhs] : rhs * vsr);
   const long long stride = (long long)gridDim.x * blockDim.x;
   long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   double nrm = 0.0;
@@ -323,11 +329,12 @@ __global__ void k_scale_vec(long long N, const double2 *__restrict__ in,
 
 // out[rhs] = in[rhs] / sqrt(Re nrm2[rhs]) (0 where the norm vanishes)   (grid.y = rhs)
 __global__ void k_scale_by_norm(long long N, const double2 *__restrict__ in,
-                                const double2 *__restrict__ nrm2, double2 *__restrict__ out) {
+                                const double2 *__restrict__ nrm2, double2 *__restrict__ out,
+                                const long long *__restrict__ off) {
   const int rhs = blockIdx.y;
   const double q = nrm2[rhs].x;
   const double s = q > 0.0 ? 1.0 / sqrt(q) : 0.0;
-  const long long base = (long long)rhs * N;
+  const long long base = off != nullptr ? off[rhs] : (long long)rhs * N;
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
        n += (long long)gridDim.x * blockDim.x)
     out[base + n] = make_double2(in[base + n].x * s, in[base + n].y * s);
@@ -346,12 +353,13 @@ static inline dim3 grid_rhs(long long N, int nrhs) {
 }
 
 cudaError_t launch_apply_A(cudaStream_t st, const Geom &g, const Tables &tb, int nrhs,
-                           const double2 *u, double2 *Au, int divide_by_J, const double2 *sub) {
+                           const double2 *u, double2 *Au, int divide_by_J, const double2 *sub,
+                           const long long *uoff, const long long *aoff) {
   const unsigned grid = grid_for(g.Nglob * (long long)nrhs);
   if (g.dim == 2)
-    k_apply_A<2><<<grid, 256, 0, st>>>(g, tb, nrhs, u, Au, divide_by_J, sub);
+    k_apply_A<2><<<grid, 256, 0, st>>>(g, tb, nrhs, u, Au, divide_by_J, sub, uoff, aoff);
   else
-    k_apply_A<3><<<grid, 256, 0, st>>>(g, tb, nrhs, u, Au, divide_by_J, sub);
+    k_apply_A<3><<<grid, 256, 0, st>>>(g, tb, nrhs, u, Au, divide_by_J, sub, uoff, aoff);
   return cudaGetLastError();
 }
 
@@ -363,14 +371,15 @@ cudaError_t launch_scale_J(cudaStream_t st, const Geom &g, const Tables &tb, int
 
 cudaError_t launch_dots(cudaStream_t st, long long N, int nrhs, int nv, const double2 *V,
                         long long vsv, long long vsr, const double2 *w, long long wsr,
-                        double2 *partial, double2 *out, int nblk) {
+                        double2 *partial, double2 *out, int nblk, const long long *voff,
+                        const long long *woff) {
   dim3 grid(nblk, nrhs);
   for (int i0 = 0; i0 < nv; i0 += 4) {
     switch (std::min(4, nv - i0)) {
-      case 1: k_dots<1><<<grid, kDotThreads, 0, st>>>(N, nv, i0, V, vsv, vsr, w, wsr, partial); break;
-      case 2: k_dots<2><<<grid, kDotThreads, 0, st>>>(N, nv, i0, V, vsv, vsr, w, wsr, partial); break;
-      case 3: k_dots<3><<<grid, kDotThreads, 0, st>>>(N, nv, i0, V, vsv, vsr, w, wsr, partial); break;
-      default: k_dots<4><<<grid, kDotThreads, 0, st>>>(N, nv, i0, V, vsv, vsr, w, wsr, partial); break;
+      case 1: k_dots<1><<<grid, kDotThreads, 0, st>>>(N, nv, i0, V, vsv, vsr, w, wsr, partial, voff, woff); break;
+      case 2: k_dots<2><<<grid, kDotThreads, 0, st>>>(N, nv, i0, V, vsv, vsr, w, wsr, partial, voff, woff); break;
+      case 3: k_dots<3><<<grid, kDotThreads, 0, st>>>(N, nv, i0, V, vsv, vsr, w, wsr, partial, voff, woff); break;
+      default: k_dots<4><<<grid, kDotThreads, 0, st>>>(N, nv, i0, V, vsv, vsr, w, wsr, partial, voff, woff); break;
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -382,7 +391,8 @@ cudaError_t launch_dots(cudaStream_t st, long long N, int nrhs, int nv, const do
 cudaError_t launch_combination(cudaStream_t st, long long N, int nrhs, int nv, const double2 *V,
                                long long vsv, long long vsr, const double2 *coef, int cstride,
                                double sign, double2 *w, long long wsr, bool overwrite,
-                               double2 *partial, double2 *nrm2, int nblk, const double *cscale) {
+                               double2 *partial, double2 *nrm2, int nblk, const double *cscale,
+                               const long long *voff, const long long *woff) {
   const dim3 grid = nrm2 != nullptr ? dim3((unsigned)nblk, (unsigned)nrhs) : grid_rhs(N, nrhs);
   // groups of at most kCombMaxNv vectors; the norm comes with the last group
   for (int i0 = 0; i0 < nv || i0 == 0; i0 += kCombMaxNv) {
@@ -391,7 +401,7 @@ cudaError_t launch_combination(cudaStream_t st, long long N, int nrhs, int nv, c
     k_combination<<<grid, 256, 0, st>>>(N, std::max(cnt, 0), V + i0 * vsv, vsv, vsr, coef + i0,
                                         cstride, sign, cscale != nullptr ? cscale + i0 : nullptr,
                                         w, wsr, overwrite && i0 == 0 ? 1 : 0,
-                                        nrm2 != nullptr && last ? partial : nullptr);
+                                        nrm2 != nullptr && last ? partial : nullptr, voff, woff);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || last) break;
   }
@@ -405,12 +415,12 @@ cudaError_t launch_sub_combination(cudaStream_t st, long long N, int nrhs, int n
                                    const double2 *coef, double2 *w, long long wsr, double sign,
                                    int cstride) {
   return launch_combination(st, N, nrhs, nv, V, vsv, vsr, coef, cstride, sign, w, wsr, false,
-                            nullptr, nullptr, 0);
+                            nullptr, nullptr, 0, nullptr, nullptr, nullptr);
 }
 
 cudaError_t launch_scale_by_norm(cudaStream_t st, long long N, int nrhs, const double2 *in,
-                                const double2 *nrm2, double2 *out) {
-  k_scale_by_norm<<<grid_rhs(N, nrhs), 256, 0, st>>>(N, in, nrm2, out);
+                                const double2 *nrm2, double2 *out, const long long *off) {
+  k_scale_by_norm<<<grid_rhs(N, nrhs), 256, 0, st>>>(N, in, nrm2, out, off);
   return cudaGetLastError();
 }
 
