@@ -1748,43 +1748,78 @@ int server_nblk(const dds_server *srv) {
 }
 
 // x = sum_i Z_i y_i from the slot's Hessenberg system, then the true residual
-dds_status server_finalize(dds_server *srv, int s) {
+// Finish slots `fin`: x = sum_i y_i Z_i from the slot's Hessenberg system, then the true
+// residual ||A x - b|| / ||b||; batched over the slots with the same basis length (offset tables
+// address their vectors), one readback for all.
+dds_status server_finalize(dds_server *srv, const std::vector<int> &fin) {
+  if (fin.empty()) return DDS_OK;
   dds_ctx *ctx = srv->ctx;
-  auto &sl = srv->slots[s];
-  const int m = srv->maxit, kr = sl.kused;
-  auto Hat = [&](int i, int jj) -> cd & { return sl.H[(size_t)i * m + jj]; };
-  std::vector<cd> y(kr, cd(0, 0));
-  for (int i = kr - 1; i >= 0; --i) {
-    cd t = sl.g[i];
-    for (int q = i + 1; q < kr; ++q) t -= Hat(i, q) * y[q];
-    y[i] = t / Hat(i, i);
-  }
   cudaStream_t st = ctx->stream;
   const long long N = srv->N;
-  SCK(cudaMemsetAsync(srv->Us(s), 0, N * sizeof(double2), st));
-  if (kr > 0) {
-    std::vector<double2> yc(kr);
-    for (int i = 0; i < kr; ++i) yc[i] = make_double2(y[i].real(), y[i].imag());
-    SCK(cudaMemcpyAsync(srv->coef.p, yc.data(), kr * sizeof(double2), cudaMemcpyHostToDevice, st));
-    ++ctx->launches;
-    SCK(launch_sub_combination(st, N, 1, kr, srv->Zs(s, 0), N, 0, srv->coef.as<double2>(),
-                               srv->Us(s), 0, 1.0, kr));
+  const int m = srv->maxit;
+  const long long vslot = (long long)(m + 1) * N, zslot = (long long)m * N;
+  std::map<int, std::vector<int>> groups;   // basis length -> slots
+  for (int s : fin) groups[srv->slots[s].kused].push_back(s);
+  double2 *hb = srv->hb.as<double2>();
+  long long *doff = srv->offs.as<long long>();
+  double2 *coef = srv->coef.as<double2>();
+  std::vector<std::pair<int, long long>> where;   // (slot, norm index in hb)
+  long long used = 0;
+  for (auto &grp : groups) {
+    const int kr = grp.first, kg = (int)grp.second.size();
+    std::vector<double2> yc((size_t)kg * std::max(kr, 1), make_double2(0.0, 0.0));
+    std::vector<long long> off(3 * (size_t)srv->S);
+    for (int i = 0; i < kg; ++i) {
+      const int s = grp.second[i];
+      auto &sl = srv->slots[s];
+      auto Hat = [&](int a, int b) -> cd & { return sl.H[(size_t)a * m + b]; };
+      std::vector<cd> y(kr, cd(0, 0));
+      for (int a = kr - 1; a >= 0; --a) {
+        cd t = sl.g[a];
+        for (int q = a + 1; q < kr; ++q) t -= Hat(a, q) * y[q];
+        y[a] = t / Hat(a, a);
+      }
+      for (int a = 0; a < kr; ++a) yc[(size_t)i * kr + a] = make_double2(y[a].real(), y[a].imag());
+      off[i] = (long long)s * zslot;                // Z_0
+      off[srv->S + i] = (long long)s * N;           // U (solution) and B (source): slot s
+      off[2 * srv->S + i] = (long long)s * vslot;   // residual in V_0 (no longer needed)
+      where.emplace_back(s, used + i);
+    }
+    const long long *zo = doff, *uo = doff + srv->S, *wo = doff + 2 * srv->S;
+    SCK(cudaMemcpyAsync(doff, off.data(), 3 * srv->S * sizeof(long long), cudaMemcpyHostToDevice, st));
+    double2 *U = srv->U.as<double2>(), *Vb = srv->V.as<double2>();
+    if (kr > 0) {
+      // coefficients after the unit entries of the residual update: [kg ones][kg * kr y]
+      std::vector<double2> cbuf((size_t)kg + yc.size());
+      for (int i = 0; i < kg; ++i) cbuf[i] = make_double2(1.0, 0.0);
+      std::copy(yc.begin(), yc.end(), cbuf.begin() + kg);
+      SCK(cudaMemcpyAsync(coef, cbuf.data(), cbuf.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
+      ctx->launches += 1;
+      SCK(launch_combination(st, N, kg, kr, srv->Z.as<double2>(), N, 0, coef + kg, kr, 1.0, U, 0,
+                             true, nullptr, nullptr, 0, nullptr, zo, uo));
+    } else {
+      const std::vector<double2> ones((size_t)kg, make_double2(1.0, 0.0));
+      SCK(cudaMemcpyAsync(coef, ones.data(), kg * sizeof(double2), cudaMemcpyHostToDevice, st));
+      for (int i = 0; i < kg; ++i)
+        SCK(cudaMemsetAsync(srv->Us(grp.second[i]), 0, N * sizeof(double2), st));
+    }
+    // residual W = A x - b and its squared norm in the same update pass
+    ctx->launches += 3;
+    SCK(launch_apply_A(st, ctx->g, ctx->tb, kg, U, Vb, 0, nullptr, uo, wo));
+    SCK(launch_combination(st, N, kg, 1, srv->B.as<double2>(), 0, 0, coef, 1, -1.0, Vb, 0, false,
+                           srv->part.as<double2>(), hb + used, server_nblk(srv), nullptr, uo, wo));
+    used += kg;
+    // the next group's tables and coefficients are copied in stream order, after these kernels
   }
-  // residual: W = A x - b in the slot's last basis vector (no longer needed)
-  double2 *W = srv->Vs(s, 0);
-  ctx->launches += 4;
-  SCK(launch_apply_A(st, ctx->g, ctx->tb, 1, srv->Us(s), W, 0));
-  const double2 one = make_double2(1.0, 0.0);
-  SCK(cudaMemcpyAsync(srv->coef.p, &one, sizeof(double2), cudaMemcpyHostToDevice, st));
-  SCK(launch_sub_combination(st, N, 1, 1, srv->Bs(s), 0, 0, srv->coef.as<double2>(), W, 0, -1.0, 1));
-  SCK(launch_dots(st, N, 1, 1, W, 0, 0, W, 0, srv->part.as<double2>(), srv->Hd(s),
-                  server_nblk(srv)));
-  double2 r2;
-  SCK(cudaMemcpyAsync(&r2, srv->Hd(s), sizeof(double2), cudaMemcpyDeviceToHost, st));
+  std::vector<double2> r2((size_t)used);
+  SCK(cudaMemcpyAsync(r2.data(), hb, (size_t)used * sizeof(double2), cudaMemcpyDeviceToHost, st));
   SCK(cudaStreamSynchronize(st));
-  sl.relres = sl.beta > 0 ? std::sqrt(std::max(r2.x, 0.0)) / sl.beta : 0.0;
-  sl.state = 2;
-  srv->finished.push_back(s);
+  for (auto &w : where) {
+    auto &sl = srv->slots[w.first];
+    sl.relres = sl.beta > 0 ? std::sqrt(std::max(r2[w.second].x, 0.0)) / sl.beta : 0.0;
+    sl.state = 2;
+    srv->finished.push_back(w.first);
+  }
   return DDS_OK;
 }
 
@@ -1819,16 +1854,18 @@ dds_status server_admit(dds_server *srv) {
   }
   if (admitted.empty()) return DDS_OK;
   SCK(cudaStreamSynchronize(st));
+  std::vector<int> zero;
   for (int s : admitted) {
     auto &sl = srv->slots[s];
     sl.beta = std::sqrt(std::max(b2[s].x, 0.0));
     sl.g[0] = sl.beta;
     if (sl.beta == 0.0) {   // zero source: the solution is zero
       sl.kused = 0;
-      dds_status r = server_finalize(srv, s);
-      if (r != DDS_OK) return r;
+      zero.push_back(s);
     }
   }
+  dds_status rz = server_finalize(srv, zero);
+  if (rz != DDS_OK) return rz;
   return DDS_OK;
 }
 
@@ -1899,6 +1936,7 @@ dds_status server_step(dds_server *srv, int *active_out, int *queued_out) {
     SCK(cudaMemcpyAsync(hh.data(), hb, (size_t)used * sizeof(double2), cudaMemcpyDeviceToHost, st));
     SCK(cudaStreamSynchronize(st));
     const int m = srv->maxit;
+    std::vector<int> fin;   // slots that finish this step
     for (int i = 0; i < k; ++i) {
       const int s = act[i];
       auto &sl = srv->slots[s];
@@ -1927,11 +1965,10 @@ dds_status server_step(dds_server *srv, int *active_out, int *queued_out) {
       sl.j = j + 1;
       sl.kused = j + 1;
       const double res = std::abs(sl.g[j + 1]) / sl.beta;
-      if (res < srv->tol || hn == 0.0 || sl.j >= m) {
-        r = server_finalize(srv, s);
-        if (r != DDS_OK) return r;
-      }
+      if (res < srv->tol || hn == 0.0 || sl.j >= m) fin.push_back(s);
     }
+    r = server_finalize(srv, fin);
+    if (r != DDS_OK) return r;
   }
   r = check_errflag(ctx);
   if (r != DDS_OK) return r;
@@ -1966,7 +2003,7 @@ dds_status dds_server_create(dds_ctx *ctx, int max_slots, double tol, int maxit,
             srv->hdev.ensure(S * (2 * maxit + 3) * sizeof(double2)) == cudaSuccess &&
             srv->part.ensure(S * (maxit + 2) * (srv->N / dots_chunk() + 2) * sizeof(double2)) ==
                 cudaSuccess &&
-            srv->coef.ensure((size_t)(maxit + 2) * sizeof(double2)) == cudaSuccess &&
+            srv->coef.ensure(S * (maxit + 2) * sizeof(double2)) == cudaSuccess &&
             srv->offs.ensure(3 * S * sizeof(long long)) == cudaSuccess &&
             srv->hb.ensure(S * (2 * maxit + 3) * sizeof(double2)) == cudaSuccess;
   if (!ok) {
