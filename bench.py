@@ -149,6 +149,21 @@ def oracle_solve_sample(wl, rhs_index: int, workers: int, tol: float):
     return time.perf_counter() - t0, it, hist[-1]
 
 
+def cpu_baseline_sample(wl, tol, budget_s: float = 10.0):
+    """The CPU oracle on right-hand sides of the workload, one after another, until about
+    budget_s seconds of work (at least one solve)."""
+    workers = os.cpu_count() or 1
+    total, done, its = 0.0, 0, []
+    while done < wl.f.shape[0] and (done == 0 or total < budget_s):
+        dt, it_o, _ = oracle_solve_sample(wl, done, workers, tol)
+        total += dt
+        done += 1
+        its.append(it_o)
+    return {"value": done / total, "unit": "RHS/s", "cores": workers, "kind": "oracle",
+            "sample": f"FGMRES solves (tol {tol:g}, {min(its)}-{max(its)} iterations) of "
+                      f"right-hand sides 0..{done - 1} of the same workload, {total:.1f} s"}
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -354,17 +369,7 @@ def run_gpu(args):
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        workers = os.cpu_count() or 1
-        # right-hand sides of the same workload one after another until ~10 s of CPU work
-        total, done, its = 0.0, 0, []
-        while done < wl.f.shape[0] and (done == 0 or total < 10.0):
-            dt, it_o, _ = oracle_solve_sample(wl, done, workers, args.tol)
-            total += dt
-            done += 1
-            its.append(it_o)
-        cpu = {"value": done / total, "unit": "RHS/s", "cores": workers, "kind": "oracle",
-               "sample": f"FGMRES solves (tol {args.tol:g}, {min(its)}-{max(its)} iterations) of "
-                         f"right-hand sides 0..{done - 1} of the same workload, {total:.1f} s"}
+        cpu = cpu_baseline_sample(wl, args.tol)
 
     lat = sorted(step_ms)
 
