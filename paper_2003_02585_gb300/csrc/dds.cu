@@ -658,11 +658,11 @@ dds_status run_ddm(dds_ctx *ctx, const double2 *b, int nrhs, double2 *u, int rou
     LAUNCHK(DDS_K_SUBST, subst_any<R>(ctx, all.npanels, pans + all.pan_off, cols, sinv, cpl, work, all.pc, nzf));
     LAUNCHK(DDS_K_EXTRACT, launch_extract<R>(st, g, all.ncols, cols + all.col_off, work, u, 0, rawf,
                              (C *)nullptr, route, 0, nrhs));
-    // sweeps: every step of every sweep, traces of the step set through the trace map, in one
-    // cooperative launch with a grid barrier between steps
+    // sweeps: every trace solve of every sweep through the trace map, in one cooperative launch
+    // over the dataflow levels (host-built item lists, a counter wait between levels)
     auto tti = cp->trace_steps.find(rounds);   // built by prepare_ddm
     if (tti == cp->trace_steps.end() || tti->second.n < 0) {
-      ctx->err = "trace-step table missing";
+      ctx->err = "trace item table missing";
       return DDS_EINVAL;
     }
     const CallPlan::TraceTable &tt = tti->second;

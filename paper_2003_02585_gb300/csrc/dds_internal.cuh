@@ -294,12 +294,6 @@ cudaError_t launch_combination(cudaStream_t st, long long N, int nrhs, int nv, c
                                double2 *partial, double2 *nrm2, int nblk,
                                const double *cscale = nullptr, const long long *voff = nullptr,
                                const long long *woff = nullptr);
-cudaError_t launch_sub_combination(cudaStream_t st, long long N, int nrhs, int nv, const double2 *V,
-                                   long long v_stride_vec, long long v_stride_rhs,
-                                   const double2 *coef, double2 *w, long long w_stride_rhs,
-                                   double sign, int coef_stride);
-cudaError_t launch_scale_vec(cudaStream_t st, long long N, int nrhs, const double2 *in,
-                             const double *inv_scale, double2 *out);
 cudaError_t launch_scale_by_norm(cudaStream_t st, long long N, int nrhs, const double2 *in,
                                 const double2 *nrm2, double2 *out, const long long *off = nullptr);
 int dots_chunk();

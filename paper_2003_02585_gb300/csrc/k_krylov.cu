@@ -316,17 +316,6 @@ __global__ void __launch_bounds__(256) k_combination(long long N, int nv,
   }
 }
 
-// out[rhs] = in[rhs] * inv_scale[rhs]                            (grid.y = rhs)
-__global__ void k_scale_vec(long long N, const double2 *__restrict__ in,
-                            const double *__restrict__ inv_scale, double2 *__restrict__ out) {
-  const int rhs = blockIdx.y;
-  const double s = inv_scale[rhs];
-  const long long base = (long long)rhs * N;
-  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
-       n += (long long)gridDim.x * blockDim.x)
-    out[base + n] = make_double2(in[base + n].x * s, in[base + n].y * s);
-}
-
 // out[rhs] = in[rhs] / sqrt(Re nrm2[rhs]) (0 where the norm vanishes)   (grid.y = rhs)
 __global__ void k_scale_by_norm(long long N, const double2 *__restrict__ in,
                                 const double2 *__restrict__ nrm2, double2 *__restrict__ out,
@@ -410,23 +399,9 @@ cudaError_t launch_combination(cudaStream_t st, long long N, int nrhs, int nv, c
   return cudaGetLastError();
 }
 
-cudaError_t launch_sub_combination(cudaStream_t st, long long N, int nrhs, int nv,
-                                   const double2 *V, long long vsv, long long vsr,
-                                   const double2 *coef, double2 *w, long long wsr, double sign,
-                                   int cstride) {
-  return launch_combination(st, N, nrhs, nv, V, vsv, vsr, coef, cstride, sign, w, wsr, false,
-                            nullptr, nullptr, 0, nullptr, nullptr, nullptr);
-}
-
 cudaError_t launch_scale_by_norm(cudaStream_t st, long long N, int nrhs, const double2 *in,
                                 const double2 *nrm2, double2 *out, const long long *off) {
   k_scale_by_norm<<<grid_rhs(N, nrhs), 256, 0, st>>>(N, in, nrm2, out, off);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_scale_vec(cudaStream_t st, long long N, int nrhs, const double2 *in,
-                             const double *inv_scale, double2 *out) {
-  k_scale_vec<<<grid_rhs(N, nrhs), 256, 0, st>>>(N, in, inv_scale, out);
   return cudaGetLastError();
 }
 
