@@ -113,13 +113,21 @@ def _dist():
 
 
 def _reduce_max(value: float, world: int):
+    """Max over ranks (the slowest replica sets the whole job's time)."""
     if world == 1:
         return value
     import torch
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_rate(world: int, rhs_per_rank: int, steps: int, max_seconds: float):
+    """Replicas: every rank solves rhs_per_rank right-hand sides per step; the job's rate is all
+    ranks' right-hand sides over the slowest rank's time."""
+    return world * rhs_per_rank * steps / max_seconds if max_seconds > 0 else None
 
 
 def _barrier(world: int):
@@ -320,7 +328,7 @@ def run_gpu(args):
     clocks = clk.summary()
     launches = ctx.launches() - launches0
     total_ms = _reduce_max(sum(step_ms), world)
-    value = world * R * args.steps / (total_ms / 1e3)
+    value = whole_job_rate(world, R, args.steps, total_ms / 1e3)
     u_mixed = u
 
     # accuracy against the plain FP64 GPU solve, and that solve's own throughput
@@ -348,7 +356,7 @@ def run_gpu(args):
         if st not in (0, 4):
             raise RuntimeError(f"dds_solve from host buffers failed: {st}")
     e2e_total = _reduce_max(sum(e2e_s), world) if e2e_s else 0.0
-    e2e_value = world * R * len(e2e_s) / e2e_total if e2e_total > 0 else None
+    e2e_value = whole_job_rate(world, R, len(e2e_s), e2e_total)
 
     # roofline of the dominant kernel family, timed with CUDA events on the library's stream
     ctx.profile(True)
