@@ -48,3 +48,19 @@ def test_section51_mesh_source_and_medium():
     ramp = c[(x2 >= 0.65) & (x2 <= 0.66), 0]
     assert ramp.size > 0 and np.all(np.diff(ramp) < 0)
     assert np.all(c == c[:, :1])   # layered along x2 only
+
+
+def test_gaussian_patch_equals_the_full_field():
+    """The serving client evaluates sources on their compact support only
+    (synth.gaussian_source_patch); placed into a zero field it must equal gaussian_source."""
+    from paper_2003_02585_gb300 import synth
+    rng = np.random.default_rng(0)
+    for n in ((256, 256), (100, 60), (24, 40, 16)):
+        h = 1.0 / n[0]
+        for _ in range(4):
+            c = rng.uniform(0.0, 1.0, len(n)) * np.array(n) * h
+            full = synth.gaussian_source(n, h, c, 2 * h)
+            sl, vals = synth.gaussian_source_patch(n, h, c, 2 * h)
+            placed = np.zeros_like(full)
+            placed[sl] = vals
+            assert np.array_equal(placed, full)
