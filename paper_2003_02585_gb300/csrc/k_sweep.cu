@@ -256,15 +256,17 @@ long long gmap_elems(const Geom &g, int nfac) { return gmap_index(g, nfac, 0, 0,
 // one 64-row tile, one panel of up to 8 columns and one segment of at most kTraceSeg consecutive
 // inputs of one receiving side.  A CTA (256 threads) runs an item as
 //   map slice (n inputs x 64 rows) -> shared memory by one bulk copy on an mbarrier,
-//   inputs (n x 8 columns) -> shared memory from L2 (ld.global.cg: written by earlier levels),
+//   inputs (n x 8 columns) -> one of two shared-memory buffers by cp.async (slots written by
+//   earlier levels; the next item's inputs land in the other buffer during this item's FMAs),
 //   four K-groups of 64 threads; thread (row pair rp, column group cg) of a group accumulates
-//   rows 2 rp, 2 rp + 1 x columns 4 cg .. 4 cg + 3 over its quarter of the inputs,
-//   the four partial tiles meet in shared memory; every thread then owns one (column, row pair)
+//   rows 2 rp, 2 rp + 1 x columns 4 cg .. 4 cg + 3 over its quarter of the inputs (a tile with
+//   at most 32 live rows: eight K-groups over 16 row pairs), on packed two-lane FMAs,
+//   the partial tiles meet in shared memory; every thread then owns one (column, row pair)
 //   and adds it into the receiver's slot with one vector reduction (segments of one output meet
 //   there; the slot accumulates with += in any case).
-// The next item of the CTA is staged while the current one finishes: its descriptor and panel
-// are fetched during the FMAs, its map-slice copy issued as soon as the slice buffer is free and
-// its inputs loaded while the partial tiles are reduced.
+// Item records carry their columns' slot offsets precomputed; warp 0 fetches a record one item
+// ahead of writing its descriptors, and the next item's map-slice copy is issued as soon as the
+// slice buffer is free.
 constexpr int kTraceSeg = 104;
 
 template <typename C> __device__ inline void atomic_cadd(C *dst, C v);
