@@ -1154,7 +1154,8 @@ struct Busy {
 };
 
 // ------------------------------------------------------------------------------------------
-// FGMRES (right preconditioned, x0 = 0, classical Gram-Schmidt twice, Givens rotations)
+// FGMRES (right preconditioned, x0 = 0, classical Gram-Schmidt with reorthogonalisation where the
+// tolerance needs it, Givens rotations, unnormalised basis with host scales)
 // The basis lives in two contiguous device buffers V[maxit+1][nrhs][N], Z[maxit][nrhs][N];
 // Gram-Schmidt coefficients stay on the device between the dot and update kernels, and the
 // host reads them once per iteration for the Hessenberg / Givens bookkeeping.
