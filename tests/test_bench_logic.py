@@ -1,0 +1,48 @@
+"""Host-side arithmetic of bench.py's JSON line, on synthetic kernel statistics: the roofline
+entries (achieved = algorithmic work / event-timed device time, frac = achieved / peak, the
+family with the larger device time as the line's roofline) and the whole-job rate of replicas."""
+
+import os
+import sys
+
+import pytest
+
+pytest.importorskip("torch")
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+import bench  # noqa: E402
+
+
+class _Args:
+    precision = "mixed"
+    workload = "const2d_640"
+
+
+def test_roofline_entries_and_main_family():
+    # two DDM applications profiled: substitutions 2.9 ms over 4 launches, trace 2.75 ms over 2
+    stats = {"subst": (4, 2.9), "trace_step": (2, 2.75), "assemble": (4, 0.36), "extract": (4, 0.14),
+             "krylov": (10, 3.0)}
+    work = (18.4e9 * 2, 11.3e9)          # per DDM application: 2 substitution launches, 1 trace
+    geo = {"plan": 2, "nrhs": 16, "nsub": 64, "T": 832, "Nglob": 664 * 664, "Nloc": 104 * 104,
+           "sweeps": 8}
+    main, entries = bench.roofline_entry(stats, work, 2, _Args(), geo)
+    by = {e["kernel"].split(" ")[0]: e for e in entries}
+    sub = by["k_subst_tc<tf32>"]
+    assert sub["bound"] == "tensor" and sub["unit"] == "TFLOP/s"
+    assert sub["achieved"] == pytest.approx(18.4e9 * 2 * 2 / 2.9e-3 / 1e12)
+    assert sub["frac"] == pytest.approx(sub["achieved"] / sub["peak"])
+    assert sub["avg_launch_ms"] == pytest.approx(2.9 / 4)
+    assert sub["traffic"] == bench.SUBST_TRAFFIC[("mixed", "const2d_640")]
+    tr = by["k_trace_sweeps<float>"]
+    assert tr["bound"] == "alu"
+    assert tr["achieved"] == pytest.approx(11.3e9 * 2 / 2.75e-3 / 1e12)
+    asm = by["k_assemble"]
+    assert asm["bound"] == "hbm" and asm["unit"] == "GB/s"
+    assert asm["achieved"] == pytest.approx(asm["bytes_per_ddm"] * 2 / 0.36e-3 / 1e9)
+    # the family with the larger device time carries the line
+    assert main["kernel"] == sub["kernel"] and "family_share" in main
+
+
+def test_whole_job_rate_of_replicas():
+    assert bench.whole_job_rate(1, 16, 5, 0.025) == pytest.approx(3200.0)
+    assert bench.whole_job_rate(4, 16, 5, 0.025) == pytest.approx(4 * 3200.0)
+    assert bench.whole_job_rate(2, 16, 5, 0.0) is None
