@@ -126,7 +126,8 @@ dds_status dds_apply(dds_ctx *ctx, const void *u, int nrhs, void *Au);
 /* dds_local_solve -- one block-tridiagonal subdomain solve A_R x = b (the local problem
  * P_{Omega_ij, kappa_ij} of Algorithm 2.1), for nrhs right-hand sides b laid out
  * [rhs][x3][x2][x1] over the extended subdomain grid (M per axis), interleaved complex double.
- * sub is the subdomain's linear index (x1 fastest).  Runs in the context's precision. */
+ * sub is the subdomain's linear index (x1 fastest).  Runs in the context's precision.
+ * DDS_ETIMEOUT if a bounded device-side wait in the substitutions gave up. */
 dds_status dds_local_solve(dds_ctx *ctx, int sub, const void *b, int nrhs, void *x);
 
 /* dds_local_solve_noalloc -- dds_local_solve for callers that must not have this library
@@ -144,7 +145,9 @@ dds_status dds_local_solve(dds_ctx *ctx, int sub, const void *b, int nrhs, void 
  * cudaMalloc / cudaFree.  The first call on a device looks up the array's device address (once
  * per device, with that device current); make that first call before any stream capture.
  * Every call on a device shares the one array and leaves its contents behind: calls that
- * overlap on the GPU (other contexts or streams on the same device) race on it. */
+ * overlap on the GPU (other contexts or streams on the same device) race on it.  The call
+ * waits for its stream before it returns; DDS_ETIMEOUT if a bounded device-side wait in the
+ * substitutions gave up (x is then not valid). */
 dds_status dds_local_solve_noalloc(dds_ctx *ctx, int sub, const void *b, int nrhs, void *x);
 
 /* ---- continuous-batching server (serving several requests against one set-up context) ------

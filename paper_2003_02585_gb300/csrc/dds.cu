@@ -1535,6 +1535,10 @@ dds_status dds_local_solve(dds_ctx *ctx, int sub, const void *b, int nrhs, void 
                                 ctx->sinv64.as<double2>(), ctx->cpl64.as<double2>(), ctx->work.as<double2>(), pc));
     LAUNCH(launch_copy_local_back<double>(st, n, ctx->work.as<double2>(), xd));
   }
+  // a bounded wait that gave up inside the substitutions leaves x wrong: report it here (and
+  // clear the flag) instead of passing it on to the next call
+  r = check_errflag(ctx);
+  if (r != DDS_OK) return r;
   return finish_out(ctx, x, bytes, xh);
 }
 
@@ -2178,6 +2182,6 @@ extern "C" dds_status dds_local_solve_noalloc(dds_ctx *ctx, int sub, const void 
                                               ctx->cpl64.as<double2>(), w, pc));
     LAUNCH(launch_copy_local_back<double>(st, n, w, xd));
   }
-  CK(cudaStreamSynchronize(st));
-  return DDS_OK;
+  // synchronises the stream; DDS_ETIMEOUT (flag cleared) if a bounded wait gave up
+  return check_errflag(ctx);
 }

@@ -113,6 +113,47 @@ def _is_torch(x):
         return False
 
 
+def local_field_count(b, M, dim):
+    """Number of right-hand sides in a local field array of shape M[::-1] or (nrhs,) + M[::-1]
+    (complex128, contiguous); raises TypeError / ValueError otherwise."""
+    if _is_torch(b):
+        import torch
+        if b.dtype != torch.complex128:
+            raise TypeError(f"local fields must be complex128, got {b.dtype}")
+        if not b.is_contiguous():
+            raise ValueError("local fields must be contiguous")
+    else:
+        if np.asarray(b).dtype != np.complex128:
+            raise TypeError(f"local fields must be complex128, got {np.asarray(b).dtype}")
+    shape = tuple(b.shape)
+    loc = tuple(M[::-1])
+    if shape == loc:
+        return 1
+    if len(shape) == dim + 1 and shape[1:] == loc and shape[0] >= 1:
+        return int(shape[0])
+    raise ValueError(f"local field shape must be {loc} or (nrhs,) + {loc}, got {shape}")
+
+
+def check_noalloc_pair(b, out, M, dim, device_index):
+    """Checks of dds_local_solve_noalloc's arguments made before any pointer is handed over:
+    the library reads and writes nrhs * prod(M) * 16 bytes at both addresses, so b and out must
+    be complex128 CUDA tensors on the context's device, contiguous, of one local-field shape.
+    Returns nrhs."""
+    if not (_is_torch(b) and _is_torch(out)):
+        raise TypeError("b and out must be torch CUDA tensors (device memory)")
+    if not (b.is_cuda and out.is_cuda):
+        raise TypeError("b and out must be CUDA tensors")
+    for name, t in (("b", b), ("out", out)):
+        if device_index is not None and t.device.index != device_index:
+            raise ValueError(f"{name} is on cuda:{t.device.index}, the context on "
+                             f"cuda:{device_index}")
+    nrhs = local_field_count(b, M, dim)
+    local_field_count(out, M, dim)
+    if tuple(out.shape) != tuple(b.shape):
+        raise ValueError(f"out has shape {tuple(out.shape)}, b {tuple(b.shape)}")
+    return nrhs
+
+
 class Context:
     """One set-up problem (dds_setup); owns the device factors and buffers."""
 
@@ -150,6 +191,13 @@ class Context:
         info = self.info()
         self.G = tuple(info["G"][:dim])
         self.M = tuple(info["M"][:dim])
+        self.device_index = None
+        try:
+            import torch
+            if torch.cuda.is_available():
+                self.device_index = torch.cuda.current_device()
+        except ImportError:  # pragma: no cover
+            pass
 
     # -- helpers -----------------------------------------------------------------------------
     def _check(self, st):
@@ -221,11 +269,9 @@ class Context:
 
     def local_solve(self, sub, b):
         """Block-tridiagonal local solve on subdomain `sub` (dds_local_solve)."""
-        if _is_torch(b):
-            nrhs = 1 if b.ndim == self.dim else int(b.shape[0])
-        else:
+        if not _is_torch(b):
             b = np.ascontiguousarray(b, dtype=np.complex128)
-            nrhs = 1 if b.ndim == self.dim else int(b.shape[0])
+        nrhs = local_field_count(b, self.M, self.dim)
         x = self._like(b, tuple(b.shape))
         self._bind_stream(b, x)
         self._check(self._lib.dds_local_solve(self._h, int(sub), self._ptr(b), nrhs, self._ptr(x)))
@@ -233,8 +279,9 @@ class Context:
 
     def local_solve_noalloc(self, sub, b, out):
         """Local solve whose scratch is the library's fixed device array (no allocation in
-        the call): b and out must be preallocated CUDA tensors."""
-        nrhs = 1 if b.ndim == self.dim else int(b.shape[0])
+        the call): b and out must be preallocated complex128 CUDA tensors of one shape,
+        M[::-1] or (nrhs,) + M[::-1], on the context's device."""
+        nrhs = check_noalloc_pair(b, out, self.M, self.dim, self.device_index)
         self._bind_stream(b, out)
         self._check(self._lib.dds_local_solve_noalloc(self._h, int(sub), self._ptr(b), nrhs,
                                                       self._ptr(out)))

@@ -9,7 +9,8 @@ finite-difference one.  The continuous solution is not available here (absolute 
 pinned), so the rates are measured from successive meshes: e_h = ||u_h - R u_{h/2}|| with R the
 average over the four fine cells of a coarse cell; for a second-order scheme
 e_h / e_{h/2} -> 4.  The fields are the GPU's FGMRES solutions to 1e-10 (DDM preconditioner, two
-rounds), far below the discretisation error.  At the coarsest mesh the direct DDM (two rounds,
+rounds), far below the discretisation error; on the 270^2 and 540^2 meshes they are compared with
+the oracle's global solve of the same discrete problem.  At the coarsest mesh the direct DDM (two rounds,
 FP64, no Krylov) is compared with the same field: its own error must sit well below the
 discretisation error, which is the paper's claim for this medium.
 """
@@ -21,12 +22,15 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
+from oracle.discretize import Problem, extend_interior, rhs_from_source
+from oracle.linsolve import global_solve
 from paper_2003_02585_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
 DEV = "cuda:0"
 TOTALS = (270, 540, 1080)
+ORACLE_TOTALS = (270, 540)
 
 
 @pytest.fixture(scope="module")
@@ -47,6 +51,12 @@ def fields():
         u, it, rel = ctx.solve(fe, tol=1e-10, maxit=30, rounds=2)
         assert np.all(np.asarray(rel) < 1e-10)
         entry = {"u": ctx.interior(u.cpu().numpy()), "h": h}
+        if total in ORACLE_TOTALS:
+            # the oracle's global solve of the same discrete problem (banded LU at 270^2, SuperLU
+            # above), no domain decomposition
+            prob = Problem(n, h, synth.CONV_KAPPA_DOWN, c, (4, 4), pml, 30.0)
+            ug = global_solve(prob, rhs_from_source(prob, extend_interior(prob, f)))
+            entry["oracle"] = ctx.interior(ug)
         if total == TOTALS[0]:
             ctx64 = dds.Context(n, h, synth.CONV_KAPPA_DOWN, c, (4, 4), pml, 30.0, precision="fp64")
             ud = ctx64.sweep(torch.from_numpy(ctx64.extend(f)).to(DEV), 2).cpu().numpy()
@@ -91,6 +101,17 @@ def test_second_order_rates_in_l2_and_h1(fields):
     # one source (column 0) and four symmetric sources (column 1) against the printed rates
     assert np.all(np.abs(rate_l2 - want[:, 0]) < 0.2), (rate_l2, want)
     assert np.all(np.abs(rate_h1 - want[:, 1]) < 0.3), (rate_h1, want)
+
+
+def test_fields_match_the_oracle_global_solve(fields):
+    """The fields behind the rates are the discrete solutions: on the 270^2 and 540^2 meshes
+    every field (one source, four sources) equals the oracle's global solve of the same PML
+    problem to relative L2 1e-6."""
+    for total in ORACLE_TOTALS:
+        u, ug = fields[total]["u"], fields[total]["oracle"]
+        for r in range(u.shape[0]):
+            err = np.linalg.norm(u[r] - ug[r]) / np.linalg.norm(ug[r])
+            assert err < 1e-6, (total, r, err)
 
 
 def test_direct_ddm_error_is_below_the_discretisation_error(fields):

@@ -76,6 +76,17 @@ def test_layer2d_1024_full_size_matches_oracle():
     _check(wl, prob, u, rel, sample=(5,))
 
 
+def test_table5_2x2_mixed_fgmres_matches_global_solve():
+    """Table 5's smallest workload (Section 5.2, Eq. 5.4): 600^2 interior, 2x2 subdomains of
+    300^2 with a 30-point PML (lines of 360 nodes: the stage-parallel tensor-core substitutions),
+    four approximated delta sources in one right-hand side, omega / 2 pi = 65.9, mixed sweeps with
+    FP64 FGMRES to 1e-6: the field against the oracle's global solve of the whole PML problem."""
+    wl, prob, u, it, rel = _solve_workload("table5_2")
+    assert prob.M[0] == 360
+    _check(wl, prob, u, rel, sample=(0,))
+    assert it <= 4, it     # the paper needs 3 iterations on this workload
+
+
 def test_const2d_128_direct_solver_one_round():
     """The 128^2 / 2x2 case: the DDM as a direct solver (one round, FP64) against the oracle's
     DDM and, Theorem 3.3, within PML level of the global solve."""

@@ -147,21 +147,46 @@ def test_ddm_mixed_matches_oracle(plan, precision):
 
 @pytest.mark.parametrize("precision", ["mixed", "mixed_bf16"])
 @pytest.mark.parametrize("nrhs", [20, 40])
-def test_tensor_core_wide_panels_match_fp64_sweep(nrhs, precision):
+def test_tensor_core_wide_panels_match_oracle(nrhs, precision):
     """64 subdomains x 20 (40) right-hand sides put 1280 (2560) columns into one substitution
     launch, so the tensor-core kernel runs panels of 16 (32) columns; the mixed DDM must agree
-    with the FP64 GPU DDM (itself pinned to the oracle above) column by column."""
+    with the oracle's DDM (Algorithm 2.1, banded-LU local solves) right-hand side by right-hand
+    side."""
     n = (128, 128)
     rng = np.random.default_rng(7)
     centres = [tuple(x) for x in rng.uniform(0.1, 0.9, size=(nrhs, 2))]
     prob, f = _case(n, (8, 8), 4, 2 * np.pi * 5, c=_medium("layer", n), centres=centres)
-    ref = _ctx(prob, "fp64", "trace")
-    fe = ref.extend(f)
-    u64 = ref.sweep(_on_dev(fe)).cpu().numpy()
+    b = rhs_from_source(prob, extend_interior(prob, f))
+    ref = ddm_solve(prob, b, 1)
     ctx = _ctx(prob, precision, "trace")
-    got = ctx.sweep(_on_dev(fe)).cpu().numpy()
+    got = ctx.sweep(_on_dev(ctx.extend(f))).cpu().numpy()
     for r in range(nrhs):
-        assert _rel(got[r], u64[r]) < SINGLE_TOL[precision]
+        assert _rel(got[r], ref[r]) < SINGLE_TOL[precision], r
+
+
+@pytest.mark.parametrize("precision", ["mixed", "mixed_bf16"])
+def test_mixed_wide_lines_2d_match_oracle(precision):
+    """2D lines of 136 nodes (> 128: the stage-parallel tensor-core substitutions, direct plan):
+    the raw mixed DDM against the oracle's DDM, and mixed FGMRES against the oracle's global
+    solve."""
+    n = (240, 240)
+    prob, f = _case(n, (2, 2), 8, 2 * np.pi * 6, c=_medium("layer", n),
+                    centres=[(0.4, 0.3), (0.7, 0.8)])
+    assert prob.M[0] == 136
+    bb = rhs_from_source(prob, extend_interior(prob, f))
+    ref = ddm_solve(prob, bb, 1)
+    ctx = _ctx(prob, precision)
+    assert ctx.info()["plan"] == 1   # the automatic plan is the direct one for wide lines
+    fe = _on_dev(ctx.extend(f))
+    got = ctx.sweep(fe).cpu().numpy()
+    for r in range(2):
+        assert _rel(got[r], ref[r]) < SINGLE_TOL[precision], r
+    u, it, rel = ctx.solve(fe, tol=1e-9, maxit=30)
+    ug = global_solve(prob, bb)
+    u = u.cpu().numpy()
+    assert np.all(rel < 1e-9), rel
+    for r in range(2):
+        assert _rel(u[r], ug[r]) < 1e-6, r
 
 
 def test_ddm_host_buffers_equal_device_buffers():

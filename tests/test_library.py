@@ -42,3 +42,33 @@ def test_binding_rejects_missing_library(tmp_path):
     with pytest.raises(RuntimeError):
         dds.load(str(tmp_path / "nope.so")) if dds._lib is None else (_ for _ in ()).throw(
             RuntimeError("already loaded"))
+
+
+def test_local_solve_arguments_are_checked_before_the_call():
+    """The binding refuses local-solve buffers whose dtype, shape or memory kind would make the
+    library read or write past them (it touches nrhs * prod(M) * 16 bytes at each address)."""
+    import numpy as np
+    torch = pytest.importorskip("torch")
+    from paper_2003_02585_gb300 import dds
+    M, dim = (30, 28), 2
+    ok = torch.zeros((3, 28, 30), dtype=torch.complex128)
+    assert dds.local_field_count(ok, M, dim) == 3
+    assert dds.local_field_count(ok[0], M, dim) == 1
+    assert dds.local_field_count(np.zeros((28, 30), np.complex128), M, dim) == 1
+    with pytest.raises(TypeError):
+        dds.local_field_count(ok.to(torch.complex64), M, dim)
+    with pytest.raises(TypeError):
+        dds.local_field_count(np.zeros((28, 30), np.complex64), M, dim)
+    with pytest.raises(ValueError):
+        dds.local_field_count(torch.zeros((3, 30, 28), dtype=torch.complex128), M, dim)
+    with pytest.raises(ValueError):
+        dds.local_field_count(torch.zeros((3, 28, 60), dtype=torch.complex128)[:, :, ::2],
+                              M, dim)
+    with pytest.raises(ValueError):
+        dds.local_field_count(torch.zeros((0, 28, 30), dtype=torch.complex128), M, dim)
+    # allocation-free entry point: device memory only, and out must match b
+    with pytest.raises(TypeError):
+        dds.check_noalloc_pair(ok, ok.clone(), M, dim, 0)
+    with pytest.raises(TypeError):
+        dds.check_noalloc_pair(np.zeros((28, 30), np.complex128),
+                               np.zeros((28, 30), np.complex128), M, dim, 0)
