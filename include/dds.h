@@ -110,6 +110,16 @@ dds_status dds_setup(const dds_problem *prob, dds_ctx **out);
  * media). */
 dds_status dds_sweep(dds_ctx *ctx, const void *f, int nrhs, void *u, int rounds);
 
+/* dds_sweep_strip -- the one-dimensional sweeping DDM of Section 3.2 on a strip partition
+ * (exactly one axis a with N_a > 1, e.g. 1 x N2): nsweeps sweeps along axis a, forward (+)
+ * first, then alternating, with the trace routing of Rules 2.4/2.5 (4.1/4.2) over that list and
+ * u_DDM = sum of the sweeps' local solutions on owned nodes.  nsweeps = 2 is the forward and
+ * backward sweep (the same field as dds_sweep with one round on the strip, whose other two
+ * sweeps are empty); nsweeps = 3 adds the extra forward sweep of Theorem 3.6, which makes the
+ * result exact (up to PML reflection) in two-layer media with an interface across the strip.
+ * 1 <= nsweeps <= 64; DDS_EINVAL on a partition cut along more than one axis. */
+dds_status dds_sweep_strip(dds_ctx *ctx, const void *f, int nrhs, void *u, int nsweeps);
+
 /* dds_solve -- solve the discrete PML problem for nrhs sources with right-preconditioned
  * flexible GMRES, one DDM application (`rounds` rounds) per iteration as the preconditioner
  * (Section 5.2), FP64 residuals and orthogonalisation.  Stops when every RHS has relative

@@ -135,6 +135,26 @@ def side_vector(side, dim):
     return tuple(v)
 
 
+def strip_sweeps(parts, nsweeps: int):
+    """Sweep list of the one-dimensional sweeping DDM for a strip partition (Section 3.2): only
+    one axis a has N_a > 1, and the sweeps run along it alternately forward (+) and backward
+    (-), starting forward.  nsweeps = 2 is the forward/backward pair, the degenerate form of
+    Algorithm 2.1 on a strip; nsweeps = 3 adds the extra forward sweep of Theorem 3.6.  The
+    other components of every direction are +1 (no neighbours lie along them)."""
+    axes = [a for a, Na in enumerate(parts) if Na > 1]
+    if len(axes) > 1:
+        raise ValueError("strip sweeps need a partition with one axis of more than 1 part")
+    if nsweeps < 1:
+        raise ValueError("nsweeps must be >= 1")
+    a = axes[0] if axes else len(parts) - 1
+    out = []
+    for k in range(nsweeps):
+        v = [1] * len(parts)
+        v[a] = 1 if k % 2 == 0 else -1
+        out.append(tuple(v))
+    return out
+
+
 def route_table(dim: int, rounds: int = 1):
     """route[l][side] over all 2^n * rounds sweeps (None = dropped), generated from the Rules."""
     dirs = sweep_directions(dim)
@@ -218,8 +238,13 @@ def neighbour(sub, side, parts):
 
 
 def ddm_solve(prob: Problem, b_ext, rounds: int = 1, local: LocalProblems | None = None,
-              workers: int = 1, record: list | None = None):
+              workers: int = 1, record: list | None = None, sweeps=None):
     """Run Algorithm 2.1 (2D) / 4.1 (3D) with `rounds` rounds of 2^n sweeps.
+
+    sweeps  optional explicit list of sweep directions replacing the `rounds` rounds of Eq. 2.9
+            / 4.2 (e.g. strip_sweeps(parts, 3), the one-dimensional sweeping DDM of Section 3.2
+            with its extra forward sweep); steps, routing (Rules 2.4/2.5, 4.1/4.2 over this
+            list) and accumulation are unchanged.
 
     b_ext   J-scaled right-hand side(s) on the global extended grid, shape (*G[::-1]) or
             (R, *G[::-1]) (for a physical source f, b = J f = f in the box).
@@ -236,8 +261,12 @@ def ddm_solve(prob: Problem, b_ext, rounds: int = 1, local: LocalProblems | None
         b = b[None]
     R = b.shape[0]
     n = prob.dim
-    dirs = sweep_directions(n)
-    L = len(dirs) * rounds
+    if sweeps is None:
+        dirs = sweep_directions(n)
+        L = len(dirs) * rounds
+    else:
+        dirs = [tuple(d) for d in sweeps]
+        L = len(dirs)
     if local is None:
         local = LocalProblems(prob)
     u = np.zeros_like(b)

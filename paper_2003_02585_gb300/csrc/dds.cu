@@ -56,6 +56,8 @@ struct StepPlan {            // launch lists of one (direction, step) or one pha
 
 // right-hand sides per call: the batched FP64 kernels put the RHS on gridDim.y
 constexpr int kMaxRhs = 65535;
+// sweeps of one strip-DDM call (dds_sweep_strip)
+constexpr int kMaxStripSweeps = 64;
 
 struct CallPlan {            // all launch lists for one nrhs
   int nrhs = 0;
@@ -250,9 +252,38 @@ bool barred(const int *D, const int *dgen, const int *duse, int dim) {
   return false;
 }
 
-std::vector<int> build_route(int dim, int rounds) {
+// Sweep program of one DDM application, as indices into sweep_dirs(dim).  prog >= 1: `prog`
+// rounds of the 2^n diagonal sweeps in the order of Eq. 2.9 / 4.2.  prog <= -1: the
+// one-dimensional sweeping DDM of Section 3.2 on a strip partition (one axis a with N_a > 1):
+// -prog sweeps along a, forward (+) first, then alternating; every other component is +1 (no
+// neighbour lies along it).  Two strip sweeps are Algorithm 2.1 / 4.1 on the strip with its
+// empty sweeps left out; the third is the extra forward sweep of Theorem 3.6.
+std::vector<int> sweep_program(const Geom &g, int prog) {
+  std::vector<int> seq;
+  const int nd = 1 << g.dim;
+  if (prog >= 1) {
+    for (int l = 0; l < nd * prog; ++l) seq.push_back(l % nd);
+    return seq;
+  }
+  int a = g.dim - 1;
+  for (int b = 0; b < g.dim; ++b)
+    if (g.parts[b] > 1) a = b;
+  for (int k = 0; k < -prog; ++k) seq.push_back((k & 1) ? (1 << a) : 0);
+  return seq;
+}
+
+// a strip partition: at most one axis cut into more than one part
+bool is_strip(const Geom &g) {
+  int cut = 0;
+  for (int b = 0; b < g.dim; ++b) cut += g.parts[b] > 1;
+  return cut <= 1;
+}
+
+std::vector<int> build_route(const Geom &g, int prog) {
+  const int dim = g.dim;
   const auto dirs = sweep_dirs(dim);
-  const int nd = (int)dirs.size(), L = nd * rounds;
+  const std::vector<int> seq = sweep_program(g, prog);
+  const int L = (int)seq.size();
   std::vector<int> route(L * 6, -1);
   for (int l = 0; l < L; ++l) {
     for (int d = 0; d < 2 * dim; ++d) {
@@ -260,8 +291,8 @@ std::vector<int> build_route(int dim, int rounds) {
       D[d >> 1] = (d & 1) ? -1 : 1;
       for (int lp = l; lp < L; ++lp) {
         // Rule 2.4 / 4.1 and Rule 2.5 / 4.2: smallest usable sweep
-        if (!similar(D, dirs[lp % nd].data(), dim)) continue;
-        if (lp > l && barred(D, dirs[l % nd].data(), dirs[lp % nd].data(), dim)) continue;
+        if (!similar(D, dirs[seq[lp]].data(), dim)) continue;
+        if (lp > l && barred(D, dirs[seq[l]].data(), dirs[seq[lp]].data(), dim)) continue;
         route[l * 6 + d] = lp;
         break;
       }
@@ -405,9 +436,9 @@ CallPlan *get_plan(dds_ctx *ctx, int nrhs) {
 
 dds_status set_route(dds_ctx *ctx, int rounds) {
   if (ctx->route_rounds == rounds) return DDS_OK;
-  const std::vector<int> r = build_route(ctx->g.dim, rounds);
+  const std::vector<int> r = build_route(ctx->g, rounds);
   CK(upload(ctx->route_dev, r, ctx->stream));
-  const int L = ctx->ndirs * rounds, ns = 2 * ctx->g.dim;
+  const int L = (int)r.size() / 6, ns = 2 * ctx->g.dim;
   ctx->in_mask.assign(L, 0);
   ctx->out_mask.assign(L, 0);
   for (int l = 0; l < L; ++l)
@@ -481,8 +512,9 @@ int build_trace_schedule(dds_ctx *ctx, int nrhs, int rounds, std::vector<TraceIt
                          std::vector<int> &lev_off) {
   std::vector<TracePanel> tp;
   const Geom &g = ctx->g;
-  const int L = ctx->ndirs * rounds, ns = g.nsub;
-  const std::vector<int> route = build_route(g.dim, rounds);
+  const std::vector<int> seq = sweep_program(g, rounds);
+  const int L = (int)seq.size(), ns = g.nsub;
+  const std::vector<int> route = build_route(g, rounds);
   std::vector<std::vector<int>> prod((size_t)L * ns);
   for (int lq = 0; lq < L; ++lq)
     for (int y = 0; y < ns; ++y)
@@ -493,7 +525,7 @@ int build_trace_schedule(dds_ctx *ctx, int nrhs, int rounds, std::vector<TraceIt
   std::vector<int> depth((size_t)L * ns, -1);
   int nlev = 0;
   for (int l = 0; l < L; ++l) {
-    const int dir = l % ctx->ndirs;
+    const int dir = seq[l];
     for (int s = 0; s < ctx->nsteps; ++s)
       for (int x : ctx->step_subs[dir][s]) {
         int dmax = -1;
@@ -554,7 +586,7 @@ dds_status prepare_ddm(dds_ctx *ctx, int nrhs, int rounds, bool *grown) {
   if (rs != DDS_OK) return rs;
   CallPlan *cp = get_plan(ctx, nrhs);
   if (!cp) { ctx->err = "failed to upload launch lists"; return DDS_ENOMEM; }
-  const int L = ctx->ndirs * rounds;
+  const int L = (int)sweep_program(g, rounds).size();
   const long long slot = (long long)nrhs * g.nsub * g.T;
   const bool trace_plan = ctx->plan == DDS_PLAN_TRACE;
   long long work_cols = (long long)g.nsub * nrhs;
@@ -625,7 +657,8 @@ dds_status run_ddm(dds_ctx *ctx, const double2 *b, int nrhs, double2 *u, int rou
   const C *sinv = ctx->single ? (const C *)ctx->sinv32.p : (const C *)ctx->sinv64.p;
   const C *cpl = ctx->single ? (const C *)ctx->cpl32.p : (const C *)ctx->cpl64.p;
   const C *gmap = ctx->single ? (const C *)ctx->gmap32.p : (const C *)ctx->gmap64.p;
-  const int L = ctx->ndirs * rounds;
+  const std::vector<int> seq = sweep_program(g, rounds);
+  const int L = (int)seq.size();
   const long long slot = (long long)nrhs * g.nsub * g.T;
   const bool trace_plan = ctx->plan == DDS_PLAN_TRACE;
   CK(cudaMemsetAsync(ctx->gtr.p, 0, L * slot * sizeof(C), st));
@@ -638,7 +671,7 @@ dds_status run_ddm(dds_ctx *ctx, const double2 *b, int nrhs, double2 *u, int rou
   if (!trace_plan) {
     CK(cudaMemsetAsync(u, 0, (size_t)nrhs * g.Nglob * sizeof(double2), st));
     for (int l = 0; l < L; ++l) {
-      const int dir = l % ctx->ndirs;
+      const int dir = seq[l];
       for (int s = 0; s < ctx->nsteps; ++s) {
         const StepPlan &sp = cp->steps[dir * ctx->nsteps + s];
         if (sp.ncols == 0) continue;
@@ -1412,12 +1445,9 @@ dds_status dds_setup(const dds_problem *prob, dds_ctx **out) {
   return DDS_OK;
 }
 
-dds_status dds_sweep(dds_ctx *ctx, const void *f, int nrhs, void *u, int rounds) {
-  if (!ctx) return DDS_EINVAL;
-  Busy busy(ctx);
-  if (!busy.ok) return DDS_EBUSY;
-  ctx->err.clear();
-  if (!f || !u || nrhs <= 0 || nrhs > kMaxRhs || rounds < 1) { ctx->err = "invalid argument"; return DDS_EINVAL; }
+// the DDM as a direct solver with sweep program `prog` (sweep_program): J-scaling of f, one
+// DDM application, the error flag and the copy back to a host u
+static dds_status sweep_impl(dds_ctx *ctx, const void *f, int nrhs, void *u, int prog) {
   const size_t bytes = (size_t)nrhs * ctx->g.Nglob * sizeof(double2);
   const double2 *fd;
   double2 *ud;
@@ -1428,11 +1458,36 @@ dds_status dds_sweep(dds_ctx *ctx, const void *f, int nrhs, void *u, int rounds)
   if (r != DDS_OK) return r;
   CK(ctx->bbuf.ensure(bytes));
   LAUNCHK(DDS_K_KRYLOV, launch_scale_J(ctx->stream, ctx->g, ctx->tb, nrhs, fd, ctx->bbuf.as<double2>()));
-  r = ddm(ctx, ctx->bbuf.as<double2>(), nrhs, ud, rounds);
+  r = ddm(ctx, ctx->bbuf.as<double2>(), nrhs, ud, prog);
   if (r != DDS_OK) return r;
   r = check_errflag(ctx);
   if (r != DDS_OK) return r;
   return finish_out(ctx, u, bytes, uh);
+}
+
+dds_status dds_sweep(dds_ctx *ctx, const void *f, int nrhs, void *u, int rounds) {
+  if (!ctx) return DDS_EINVAL;
+  Busy busy(ctx);
+  if (!busy.ok) return DDS_EBUSY;
+  ctx->err.clear();
+  if (!f || !u || nrhs <= 0 || nrhs > kMaxRhs || rounds < 1) { ctx->err = "invalid argument"; return DDS_EINVAL; }
+  return sweep_impl(ctx, f, nrhs, u, rounds);
+}
+
+dds_status dds_sweep_strip(dds_ctx *ctx, const void *f, int nrhs, void *u, int nsweeps) {
+  if (!ctx) return DDS_EINVAL;
+  Busy busy(ctx);
+  if (!busy.ok) return DDS_EBUSY;
+  ctx->err.clear();
+  if (!f || !u || nrhs <= 0 || nrhs > kMaxRhs || nsweeps < 1 || nsweeps > kMaxStripSweeps) {
+    ctx->err = "invalid argument";
+    return DDS_EINVAL;
+  }
+  if (!is_strip(ctx->g)) {
+    ctx->err = "dds_sweep_strip needs a strip partition (one axis with more than one part)";
+    return DDS_EINVAL;
+  }
+  return sweep_impl(ctx, f, nrhs, u, -nsweeps);
 }
 
 dds_status dds_solve(dds_ctx *ctx, const void *f, int nrhs, void *u, double tol, int maxit,
@@ -1649,8 +1704,8 @@ dds_status dds_work_per_ddm(dds_ctx *ctx, int nrhs, int rounds, double *subst_fl
   const Geom &g = ctx->g;
   dds_status r = set_route(ctx, rounds);
   if (r != DDS_OK) return r;
-  const std::vector<int> route = build_route(g.dim, rounds);
-  const int L = ctx->ndirs * rounds;
+  const std::vector<int> route = build_route(g, rounds);
+  const int L = (int)route.size() / 6;
   const double per_solve = 16.0 * g.Ml * (double)g.Mb * g.Mb;
   // substitutions: trace plan = own-source solves + final solves of every (sub, RHS);
   // direct plan = one solve per (sub, RHS) per sweep

@@ -22,7 +22,7 @@ STATUS = {0: "DDS_OK", 1: "DDS_EINVAL", 2: "DDS_ENOMEM", 3: "DDS_ECUDA", 4: "DDS
 PRECISION = {"fp64": 0, "mixed": 1, "mixed_bf16": 2, "mixed_fp32": 3}
 PLAN = {"auto": 0, "direct": 1, "trace": 2}
 
-EXPORTS = ["dds_setup", "dds_sweep", "dds_solve", "dds_apply", "dds_local_solve",
+EXPORTS = ["dds_setup", "dds_sweep", "dds_sweep_strip", "dds_solve", "dds_apply", "dds_local_solve",
            "dds_set_stream", "dds_get_info", "dds_kernel_launches", "dds_last_error",
            "dds_destroy", "dds_profile", "dds_profile_read", "dds_local_solve_noalloc",
            "dds_server_create", "dds_server_submit", "dds_server_step", "dds_server_poll",
@@ -65,6 +65,7 @@ def load(path: str = LIB_PATH):
     vp = ctypes.c_void_p
     lib.dds_setup.argtypes = [ctypes.POINTER(_Problem), ctypes.POINTER(vp)]
     lib.dds_sweep.argtypes = [vp, vp, ctypes.c_int, vp, ctypes.c_int]
+    lib.dds_sweep_strip.argtypes = [vp, vp, ctypes.c_int, vp, ctypes.c_int]
     lib.dds_solve.argtypes = [vp, vp, ctypes.c_int, vp, ctypes.c_double, ctypes.c_int,
                               ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                               ctypes.POINTER(ctypes.c_double)]
@@ -96,7 +97,7 @@ def load(path: str = LIB_PATH):
     lib.dds_profile.argtypes = [vp, ctypes.c_int]
     lib.dds_profile_read.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
                                      ctypes.POINTER(ctypes.c_double)]
-    for name in ["dds_setup", "dds_sweep", "dds_solve", "dds_apply", "dds_local_solve",
+    for name in ["dds_setup", "dds_sweep", "dds_sweep_strip", "dds_solve", "dds_apply", "dds_local_solve",
                  "dds_set_stream", "dds_get_info", "dds_profile", "dds_profile_read",
                  "dds_local_solve_noalloc", "dds_server_create", "dds_server_submit",
                  "dds_server_step", "dds_server_poll"]:
@@ -244,6 +245,16 @@ class Context:
         u = self._like(f, tuple(f.shape))
         self._bind_stream(f, u)
         self._check(self._lib.dds_sweep(self._h, self._ptr(f), nrhs, self._ptr(u), int(rounds)))
+        return u
+
+    def sweep_strip(self, f, nsweeps=3):
+        """One-dimensional sweeping DDM of Section 3.2 on a strip partition with nsweeps
+        alternating sweeps (dds_sweep_strip)."""
+        f, nrhs = self._fields(f)
+        u = self._like(f, tuple(f.shape))
+        self._bind_stream(f, u)
+        self._check(self._lib.dds_sweep_strip(self._h, self._ptr(f), nrhs, self._ptr(u),
+                                              int(nsweeps)))
         return u
 
     def solve(self, f, tol=1e-6, maxit=50, rounds=1):

@@ -189,6 +189,42 @@ def test_mixed_wide_lines_2d_match_oracle(precision):
         assert _rel(u[r], ug[r]) < 1e-6, r
 
 
+STRIP_CASES = [
+    # (n, parts, P, interface, centre)
+    ((64, 64), (1, 4), 10, 0.3, (0.5, 0.875)),     # Theorem 3.6: interface below the source
+    ((48, 48), (3, 1), 8, 0.4, (0.7, 0.45)),       # strip along x1
+    ((12, 12, 18), (1, 1, 3), 3, 0.4, (0.5, 0.5, 0.8)),
+]
+
+
+@pytest.mark.parametrize("nsweeps", [2, 3])
+@pytest.mark.parametrize("plan", ["direct", "trace"])
+@pytest.mark.parametrize("case", STRIP_CASES, ids=lambda c: "x".join(map(str, c[1])))
+def test_strip_sweeps_match_oracle(case, plan, nsweeps):
+    """dds_sweep_strip (the one-dimensional sweeping DDM of Section 3.2, with the extra forward
+    sweep of Theorem 3.6 at nsweeps = 3) against the oracle's strip sweeps: FP64 to 1e-10, the
+    3xTF32 tensor-core path to the single-precision tolerance."""
+    from oracle.sweep import strip_sweeps
+    n, parts, P, interface, centre = case
+    h = 1.0 / n[0]
+    c = synth.medium_two_layer(n, h, interface=interface, axis=len(n) - 1)
+    prob, f = _case(n, parts, P, 2 * np.pi * 3, c=c, centres=[centre])
+    b = rhs_from_source(prob, extend_interior(prob, f))
+    ref = ddm_solve(prob, b, sweeps=strip_sweeps(parts, nsweeps))
+    for precision, tol in (("fp64", 1e-10), ("mixed", SINGLE_TOL["mixed"])):
+        ctx = _ctx(prob, precision, plan)
+        got = ctx.sweep_strip(_on_dev(ctx.extend(f)), nsweeps).cpu().numpy()
+        assert _rel(got[0], ref[0]) < tol, precision
+
+
+def test_strip_sweeps_reject_a_checkerboard():
+    dds = _dds()
+    prob, f = _case((32, 32), (2, 2), 4, 2 * np.pi * 2)
+    ctx = _ctx(prob)
+    with pytest.raises(dds.DDSError):
+        ctx.sweep_strip(_on_dev(ctx.extend(f)), 3)
+
+
 def test_ddm_host_buffers_equal_device_buffers():
     prob, f = _case((48, 48), (2, 2), 8, 2 * np.pi * 3)
     ctx = _ctx(prob)

@@ -18,7 +18,7 @@ from oracle.fgmres import fgmres
 from oracle.linsolve import global_solve
 from oracle.sweep import (LocalProblems, _coupling, _line_slice, ddm_solve, num_steps, route,
                           route_table, side_vector, similar_direction, step_index, step_set,
-                          sweep_directions)
+                          strip_sweeps, sweep_directions)
 from paper_2003_02585_gb300 import synth
 
 
@@ -291,3 +291,63 @@ def test_fgmres_two_layer_and_exact_preconditioner():
     p1 = _problem((32, 32), (1, 1), 8, 4 * np.pi)
     _, it1, hist1, _ = _fgmres_case(p1, (0.5, 0.5))
     assert it1 == 1 and hist1[-1] < 1e-12
+
+
+# ------------------------------------------------------------------ strip partitions ----------
+
+def _strip_case(n, parts, P, interface, centre):
+    h = 1.0 / n[0]
+    c = (synth.medium_constant(n) if interface is None
+         else synth.medium_two_layer(n, h, interface=interface))
+    prob = _problem(n, parts, P, 2 * np.pi * 4, c=c)
+    b = _rhs(prob, [centre])[0]
+    return prob, b, global_solve(prob, b)
+
+
+def test_strip_sweep_list_alternates_along_the_cut_axis():
+    """Section 3.2: forward, backward, forward ... along the one cut axis."""
+    assert strip_sweeps((1, 4), 3) == [(1, 1), (1, -1), (1, 1)]
+    assert strip_sweeps((4, 1), 2) == [(1, 1), (-1, 1)]
+    assert strip_sweeps((1, 1, 3), 3) == [(1, 1, 1), (1, 1, -1), (1, 1, 1)]
+    with pytest.raises(ValueError):
+        strip_sweeps((2, 2), 3)
+
+
+@pytest.mark.parametrize("parts", [(1, 3), (3, 1)])
+def test_strip_two_sweeps_are_algorithm_2_1_on_the_strip(parts):
+    """The one-dimensional sweeping DDM is the degenerate form of Algorithm 2.1 on a 1 x N (or
+    N x 1) partition (Section 3.2): its forward/backward pair gives exactly the field of one round
+    of the four diagonal sweeps, two of which receive nothing."""
+    prob, b, _ = _strip_case((48, 48), parts, 8, 0.4, (0.45, 0.6))
+    loc = LocalProblems(prob)
+    two = ddm_solve(prob, b, local=loc, sweeps=strip_sweeps(parts, 2))
+    diag = ddm_solve(prob, b, 1, loc)
+    assert np.array_equal(two, diag)
+
+
+def test_strip_lemma_3_4_two_sweeps_suffice_below_the_interface():
+    """Lemma 3.4 (1 x 2, horizontal interface above the subdomain interface, source in the lower
+    subdomain): forward + backward already give the PML solution (up to PML reflection); one
+    sweep alone does not."""
+    prob, b, ug = _strip_case((48, 48), (1, 2), 10, 0.7, (0.5, 0.25))
+    loc = LocalProblems(prob)
+    gaps = [_rel(ddm_solve(prob, b, local=loc, sweeps=strip_sweeps((1, 2), k)), ug)
+            for k in (1, 2)]
+    assert gaps[0] > 1e-2 and gaps[1] < 3e-4, gaps
+
+
+@pytest.mark.parametrize("n,parts,centre", [((48, 48), (1, 2), (0.5, 0.75)),
+                                           ((64, 64), (1, 4), (0.5, 0.875))])
+def test_strip_extra_forward_sweep_theorem_3_6(n, parts, centre):
+    """Lemma 3.5 / Theorem 3.6: with the interface below the source's subdomain the reflection
+    back into the upper subdomains needs a third (forward) sweep.  Two sweeps leave an O(1e-1)
+    gap to the global PML solve; three sweeps reach PML-reflection level, and that gap shrinks
+    as the PML thickens."""
+    gaps = {}
+    for P in (10, 16):
+        prob, b, ug = _strip_case(n, parts, P, 0.3, centre)
+        loc = LocalProblems(prob)
+        gaps[P] = [_rel(ddm_solve(prob, b, local=loc, sweeps=strip_sweeps(parts, k)), ug)
+                   for k in (2, 3)]
+    assert gaps[10][0] > 3e-2 and gaps[16][0] > 3e-2, gaps
+    assert gaps[10][1] < 2e-4 and gaps[16][1] < 0.7 * gaps[10][1], gaps
