@@ -482,6 +482,8 @@ def run_gpu(args):
                 "Nglob": int(np.prod(inf["G"][:len(wl.n)])),
                 "Nloc": int(np.prod(inf["M"][:len(wl.n)])),
                 "Mb": int(np.prod(inf["M"][:len(wl.n) - 1])),
+                "trace_kernel": inf.get("trace_kernel", 1),
+                "subst_kernel": inf.get("subst_kernel", 2),
                 "sweeps": (2 ** len(wl.n)) * wl.rounds}
     roofline, roofline_kernels = (roofline_entry(stats, work, ddm_apps, args, geometry)
                                   if args.profile_steps > 0 else (None, []))
@@ -549,6 +551,7 @@ SPLIT_KIND = {"mixed": "tf32", "mixed_bf16": "bf16", "mixed_fp32": "fp32"}
 # configuration (cold, serialised replay: written data that stays in L2 is not counted)
 SUBST_TRAFFIC = {("mixed", "const2d_640"): 48.68e6 + 0.99e6}
 TRACE_TRAFFIC = {("mixed", "const2d_640"): 40.26e6 + 0.08e6}
+TRACE_TC_TRAFFIC = {}
 
 
 def roofline_entry(stats, work, ddm_apps, args, geometry=None):
@@ -597,13 +600,27 @@ def roofline_entry(stats, work, ddm_apps, args, geometry=None):
     n_t, ms_t = stats["trace_step"]
     if n_t > 0 and ms_t > 0 and work[1] > 0:
         achieved = work[1] * ddm_apps / (ms_t / 1e3) / 1e12
-        entries.append({"kernel": "k_trace_sweeps<float> (every trace step of a DDM application, "
-                                  "one cooperative launch)", "bound": "alu",
-                        "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
-                        "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                        "frac": achieved / fp32_peak,
-                        "traffic": TRACE_TRAFFIC.get((args.precision, args.workload)),
-                        "launches": n_t, "avg_launch_ms": ms_t / n_t, "device_ms": ms_t})
+        tc = (geometry or {}).get("trace_kernel", 1) == 0 and kind != "fp32"
+        if tc:
+            bf16 = peaks["bf16_tflops"]
+            peak = (bf16 * (1.1 / 2.25) if kind == "tf32" else bf16) / 3.0
+            e = {"kernel": f"k_trace_tc<{kind}> (every trace solve of a DDM application as "
+                           f"3x{kind.upper()} split-product GEMMs on tcgen05, one cooperative "
+                           f"launch)", "bound": "tensor",
+                 "peak_source": f"{src} bf16 burst {bf16:.0f} TF/s"
+                                + (" x 1.1/2.25 (nominal TF32:BF16)" if kind == "tf32" else "")
+                                + " / 3 split products",
+                 "traffic": TRACE_TC_TRAFFIC.get((args.precision, args.workload))}
+        else:
+            peak = fp32_peak
+            e = {"kernel": "k_trace_sweeps<float> (every trace step of a DDM application, "
+                           "one cooperative launch, FP32 CUDA cores)", "bound": "alu",
+                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                 "traffic": TRACE_TRAFFIC.get((args.precision, args.workload))}
+        e.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                  "frac": achieved / peak, "launches": n_t, "avg_launch_ms": ms_t / n_t,
+                  "device_ms": ms_t})
+        entries.append(e)
     # HBM-side kernels of the trace plan, from their algorithmic bytes per DDM application:
     #   assembly (two launches): every local right-hand side written once, the source read once
     #   over the owned ranges (which tile the global grid), and the final launch reads the trace

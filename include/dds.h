@@ -93,6 +93,11 @@ typedef struct {
   int plan;               /* plan in use                                                      */
   long long factor_bytes; /* device bytes held by factors (+ trace maps)                      */
   double setup_seconds;   /* wall time of dds_setup                                           */
+  int trace_kernel;       /* trace solves: 0 = tensor cores (k_trace_tc), 1 / 2 = CUDA cores   */
+                          /* with that many CTAs per SM (k_trace_sweeps), -1 = direct plan     */
+  int subst_kernel;       /* substitutions: 0 = FP64 CUDA cores, 1 = FP32 CUDA cores,          */
+                          /* 2 = tensor cores (lines <= 128 nodes), 3 = stage-parallel tensor  */
+                          /* cores (wider blocks)                                              */
 } dds_info_t;
 
 /* dds_setup -- discretise, deduplicate and factor every extended subdomain (Section 2.3,
@@ -199,13 +204,15 @@ long long dds_kernel_launches(const dds_ctx *ctx);
 /* dds_autotune -- time the tunable launch shapes of one DDM application on this context's
  * geometry for nrhs right-hand sides and `rounds` rounds, and keep the fastest:
  *   the tensor-core substitution panel width (8, 16 or 32 columns per CTA or CTA pair;
- *   mixed modes with tensor-core substitutions), and the CTAs per SM of the cooperative trace
- *   launch (1 or 2; trace plan).
+ *   mixed modes with tensor-core substitutions), and the trace-solve kernel of the trace plan:
+ *   the CUDA-core cooperative launch with 1 or 2 CTAs per SM, or (0) the tensor-core launch
+ *   (split products of the context's piece type; mixed modes with tensor-core pieces).
  * Each candidate is captured once and then timed over three DDM applications with CUDA events
  * on the context's stream, with synthetic nonzero right-hand sides in scratch the call allocates
- * and frees.  table (row-major [n][3]: panel width (0 = automatic), CTAs per SM, ms per DDM
- * application) receives at most max_entries rows; *n_entries is the number of candidates timed;
- * best[0], best[1] the chosen panel width and CTAs per SM.  Cached plans and graphs are dropped.
+ * and frees.  table (row-major [n][3]: panel width (0 = automatic), trace kernel (CTAs per SM
+ * of the CUDA-core launch, 0 = tensor cores), ms per DDM application) receives at most
+ * max_entries rows; *n_entries is the number of candidates timed; best[0], best[1] the chosen
+ * panel width and trace kernel.  Cached plans and graphs are dropped.
  * Not part of the paper: it picks block and panel tile shapes by measurement. */
 dds_status dds_autotune(dds_ctx *ctx, int nrhs, int rounds, int max_entries, int *n_entries,
                         double *table, int *best);
@@ -220,6 +227,22 @@ dds_status dds_autotune(dds_ctx *ctx, int nrhs, int rounds, int max_entries, int
  * Used to turn kernel times into achieved rates.  DDS_EINVAL on bad arguments. */
 dds_status dds_work_per_ddm(dds_ctx *ctx, int nrhs, int rounds, double *subst_flops,
                             double *trace_flops);
+
+/* dds_set_zero_skip -- zero-work skipping (Algorithm 2.1: a subdomain whose assembled right-hand
+ * side f_ij is zero is not solved, u_ij = 0).  On (enable = 1, the default), after each batched
+ * assembly the (subdomain, RHS) local problems whose right-hand side is exactly zero are dropped
+ * from the substitution launch on the device (their solution is the zero already in place); the
+ * result is the same as with skipping off (bit-identical in DDS_FP64).  Off (0) solves every
+ * local problem, e.g. to compare.  Drops cached CUDA graphs when it changes the setting. */
+dds_status dds_set_zero_skip(dds_ctx *ctx, int enable);
+
+/* dds_local_solve_counts -- (subdomain, RHS) local problems whose substitutions ran (*solved)
+ * and that were assembled (*assembled) in the DDM applications of dds_sweep, dds_sweep_strip,
+ * dds_solve and the server since the context was set up or last reset; with zero-work skipping
+ * off both count only the compacted launches (0).  reset != 0 zeroes the counts after reading.
+ * Synchronises the context's stream. */
+dds_status dds_local_solve_counts(dds_ctx *ctx, long long *solved, long long *assembled,
+                                  int reset);
 
 /* Kernel families timed by the profiler (dds_profile_read). */
 typedef enum {

@@ -52,6 +52,7 @@ struct DBuf {
 struct StepPlan {            // launch lists of one (direction, step) or one phase
   int col_off = 0, ncols = 0;
   int pan_off = 0, npanels = 0, pc = 1;
+  int grp_off = 0, ngrp = 0;   // factor groups of the panels (zero-work skipping)
 };
 
 // right-hand sides per call: the batched FP64 kernels put the RHS on gridDim.y
@@ -65,7 +66,15 @@ struct CallPlan {            // all launch lists for one nrhs
   std::vector<StepPlan> tsteps;  // [dir][step] for the trace plan (trace-step panels)
   StepPlan all;                  // every (sub, rhs) column (trace plan phases, local solves)
   DBuf cols, panels, tpanels;
-  struct TraceTable { int n = -1, nlev = 0; DBuf buf, cols, levs; };   // items, level offsets
+  // zero-work skipping: factor groups of every substitution launch, and the packed column and
+  // panel lists that k_compact_panels writes (same index space as cols / panels)
+  DBuf groups, dcols, dpans;
+  struct TraceTable {
+    int n = -1, nlev = 0;
+    DBuf buf, cols, levs;            // k_trace_sweeps: items, their columns, level offsets
+    int tn = -1, tnlev = 0;
+    DBuf tunits, tcols, tlevs;       // k_trace_tc: units, their columns, level offsets
+  };
   std::map<int, TraceTable> trace_steps;   // rounds -> item lists of the cooperative launch
 };
 
@@ -94,10 +103,15 @@ struct dds_ctx {
   DBuf sinv64, sinv32, cpl64, cpl32, coef64, coef32, k2glob, gmap64, gmap32, status;
   DBuf tctiles;  // block inverses split into tensor-core pieces (layout of k_subst_tc.cu)
   DBuf bigtiles, bigB, bigacc;   // blocks wider than 128 nodes: tiles, B pieces, accumulator
+  DBuf tttiles;          // the trace map split into tensor-core pieces (k_trace_tc.cu)
+  bool trace_tc_avail = false;  // tttiles exist
+  bool trace_tc = false; // trace solves on the tensor cores (k_trace_tc) or CUDA cores
   bool big_tc = false;
   DBuf errflag;  // set by kernels whose bounded waits gave up
   DBuf gbar;     // step counters of the cooperative trace-sweep launch
   DBuf nzflag;   // per work slot: the assembled right-hand side has a nonzero entry
+  bool zero_skip = true;   // drop the substitutions of zero right-hand sides (Algorithm 2.1)
+  DBuf solve_stats;        // [0] local solves run, [1] local solves assembled (u64)
   DBuf an_glob[3], iah_glob[3];
   DBuf stc0, stcp[3];  // global stencil (centre, coupling to +e_a)
   Tables tb{};
@@ -376,6 +390,7 @@ CallPlan *get_plan(dds_ctx *ctx, int nrhs) {
   const int maxpc = max_pc_for(ctx, elem);
   std::vector<Col> cols;
   std::vector<Panel> panels;
+  std::vector<int4> groups;
   // every (sub, rhs), subs grouped by factor
   std::vector<int> order(g.nsub);
   for (int s = 0; s < g.nsub; ++s) order[s] = s;
@@ -405,6 +420,17 @@ CallPlan *get_plan(dds_ctx *ctx, int nrhs) {
     sp.pan_off = (int)panels.size();
     add_panels(cols, sp.col_off, sp.col_off + sp.ncols, ctx->fac_of_sub, sp.pc, panels);
     sp.npanels = (int)panels.size() - sp.pan_off;
+    if (!trace) {
+      // runs of panels sharing a factor: the units of zero-work compaction
+      sp.grp_off = (int)groups.size();
+      for (int q = sp.pan_off; q < sp.pan_off + sp.npanels;) {
+        int e = q;
+        while (e < sp.pan_off + sp.npanels && panels[e].factor == panels[q].factor) ++e;
+        groups.push_back(make_int4(panels[q].col0, panels[e - 1].col0 + panels[e - 1].ncol, q, e));
+        q = e;
+      }
+      sp.ngrp = (int)groups.size() - sp.grp_off;
+    }
     return sp;
   };
   cp->all = emit(order, maxpc, false);
@@ -415,6 +441,9 @@ CallPlan *get_plan(dds_ctx *ctx, int nrhs) {
     for (int s = 0; s < ctx->nsteps; ++s) cp->tsteps.push_back(emit(ctx->step_subs[dir][s], tmax, true));
   if (upload(cp->cols, cols, ctx->stream) != cudaSuccess) return nullptr;
   if (upload(cp->panels, panels, ctx->stream) != cudaSuccess) return nullptr;
+  if (upload(cp->groups, groups, ctx->stream) != cudaSuccess) return nullptr;
+  if (cp->dcols.ensure(cols.size() * sizeof(Col)) != cudaSuccess) return nullptr;
+  if (cp->dpans.ensure(panels.size() * sizeof(Panel)) != cudaSuccess) return nullptr;
   // trace-step panels with their columns inline (panels wider than 8 columns keep the first 8,
   // and only trace-step panels, which have at most 8, are read through this table)
   std::vector<TracePanel> tp(panels.size());
@@ -508,9 +537,7 @@ dds_status check_errflag(dds_ctx *ctx) {
 // those producers (0 without any), computed in sweep and step order.  Per level and sweep one
 // entry holds that sweep's subdomains of the level, as panels of 8 (subdomain, RHS) columns of
 // one factor.  Returns the number of levels.
-int build_trace_schedule(dds_ctx *ctx, int nrhs, int rounds, std::vector<TraceItem> &items,
-                         std::vector<int> &lev_off) {
-  std::vector<TracePanel> tp;
+std::vector<int> trace_depths(const dds_ctx *ctx, int rounds, int *nlev_out) {
   const Geom &g = ctx->g;
   const std::vector<int> seq = sweep_program(g, rounds);
   const int L = (int)seq.size(), ns = g.nsub;
@@ -534,6 +561,18 @@ int build_trace_schedule(dds_ctx *ctx, int nrhs, int rounds, std::vector<TraceIt
         nlev = std::max(nlev, dmax + 2);
       }
   }
+  *nlev_out = nlev;
+  return depth;
+}
+
+int build_trace_schedule(dds_ctx *ctx, int nrhs, int rounds, std::vector<TraceItem> &items,
+                         std::vector<int> &lev_off) {
+  std::vector<TracePanel> tp;
+  const Geom &g = ctx->g;
+  const int L = (int)sweep_program(g, rounds).size(), ns = g.nsub;
+  const std::vector<int> route = build_route(g, rounds);
+  int nlev = 0;
+  const std::vector<int> depth = trace_depths(ctx, rounds, &nlev);
   for (int v = 0; v < nlev; ++v) {
     const size_t first = items.size();
     lev_off.push_back((int)first);
@@ -577,6 +616,86 @@ int build_trace_schedule(dds_ctx *ctx, int nrhs, int rounds, std::vector<TraceIt
   return nlev;
 }
 
+// Work units of the tensor-core trace launch (k_trace_tc.cu), on the same dataflow levels.  Per
+// level and sweep, the level's subdomains (by factor) times every RHS are cut into column tiles
+// of at most 32 columns of one factor; a tile yields one unit per 128-row tile of the stacked
+// output rows that holds a routed side with a neighbour of some column.  The unit multiplies the
+// inputs of the sides that receive in this sweep and have a neighbour of some column (kmask);
+// in the first sweep it also adds the raw own-source lines (a unit without inputs then only does
+// that).  Returns the number of levels.
+int build_tc_trace_schedule(dds_ctx *ctx, int nrhs, int rounds, std::vector<int4> &units,
+                            std::vector<int> &ucols, std::vector<int> &lev_off) {
+  const Geom &g = ctx->g;
+  const int L = (int)sweep_program(g, rounds).size(), ns = g.nsub;
+  const std::vector<int> route = build_route(g, rounds);
+  int nlev = 0;
+  const std::vector<int> depth = trace_depths(ctx, rounds, &nlev);
+  constexpr int kCols = 32;
+  const int RT = (g.T + 127) / 128;
+  for (int v = 0; v < nlev; ++v) {
+    lev_off.push_back((int)units.size());
+    for (int l = 0; l < L; ++l) {
+      std::vector<int> subs;
+      for (int x = 0; x < ns; ++x)
+        if (depth[(size_t)l * ns + x] == v) subs.push_back(x);
+      if (subs.empty()) continue;
+      std::stable_sort(subs.begin(), subs.end(),
+                       [&](int a, int b) { return ctx->fac_of_sub[a] < ctx->fac_of_sub[b]; });
+      std::vector<int> tile;   // (rhs * nsub + sub) of the current column tile
+      int fac = -1;
+      auto flush = [&]() {
+        if (tile.empty()) return;
+        int nb = 0;   // sides with a neighbour for some column
+        for (int c : tile)
+          for (int d = 0; d < g.nsides; ++d)
+            if (sub_neighbour(g, c % ns, d) >= 0) nb |= 1 << d;
+        int outs = 0;
+        for (int d = 0; d < g.nsides; ++d)
+          if (((nb >> d) & 1) && route[l * 6 + d] >= 0) outs |= 1 << d;
+        const int kmask = ctx->in_mask[l] & nb;
+        const int raw = l == 0 ? 1 : 0;
+        if (outs != 0 && (kmask != 0 || raw)) {
+          const int col0 = (int)ucols.size();
+          ucols.insert(ucols.end(), tile.begin(), tile.end());
+          for (int rt = 0; rt < RT; ++rt) {
+            bool need = false;
+            for (int d = 0; d < g.nsides; ++d)
+              if (((outs >> d) & 1) && g.toff[d] < 128 * (rt + 1) &&
+                  g.toff[d] + 2 * g.Lt[d] > 128 * rt)
+                need = true;
+            if (!need) continue;
+            units.push_back(make_int4(fac | ((int)tile.size() << 24), l | (rt << 16), col0,
+                                      kmask | (raw << 8)));
+          }
+        }
+        tile.clear();
+      };
+      for (int x : subs) {
+        if (ctx->fac_of_sub[x] != fac) {
+          flush();
+          fac = ctx->fac_of_sub[x];
+        }
+        for (int r = 0; r < nrhs; ++r) {
+          if ((int)tile.size() == kCols) flush();
+          tile.push_back(r * ns + x);
+        }
+      }
+      flush();
+    }
+    // heaviest units first (K-steps of the received sides), so that the snake deal balances
+    auto cost = [&](const int4 &u) {
+      int k = 0;
+      for (int d = 0; d < g.nsides; ++d)
+        if ((u.w >> d) & 1) k += 2 * g.Lt[d];
+      return k;
+    };
+    std::stable_sort(units.begin() + lev_off.back(), units.end(),
+                     [&](const int4 &a, const int4 &b) { return cost(a) > cost(b); });
+  }
+  lev_off.push_back((int)units.size());
+  return nlev;
+}
+
 // workspaces of one DDM application; *grown is set if any buffer moved (cached graphs go stale)
 template <typename R>
 dds_status prepare_ddm(dds_ctx *ctx, int nrhs, int rounds, bool *grown) {
@@ -617,6 +736,18 @@ dds_status prepare_ddm(dds_ctx *ctx, int nrhs, int rounds, bool *grown) {
       tt.n = (int)items.size();
       void *gb0 = ctx->gbar.p;
       CK(ctx->gbar.ensure(trace_counter_bytes(std::max(tt.nlev, 1))));
+      if (gb0 != ctx->gbar.p) *grown = true;
+    }
+    if (ctx->trace_tc && tt.tn < 0) {
+      std::vector<int4> units;
+      std::vector<int> ucols, lev;
+      tt.tnlev = build_tc_trace_schedule(ctx, nrhs, rounds, units, ucols, lev);
+      CK(upload(tt.tunits, units, ctx->stream));
+      CK(upload(tt.tcols, ucols, ctx->stream));
+      CK(upload(tt.tlevs, lev, ctx->stream));
+      tt.tn = (int)units.size();
+      void *gb0 = ctx->gbar.p;
+      CK(ctx->gbar.ensure(trace_counter_bytes(std::max(std::max(tt.nlev, tt.tnlev), 1))));
       if (gb0 != ctx->gbar.p) *grown = true;
     }
   }
@@ -668,6 +799,18 @@ dds_status run_ddm(dds_ctx *ctx, const double2 *b, int nrhs, double2 *u, int rou
   int *nzf = ctx->nzflag.as<int>();   // per work slot: nonzero right-hand side
   const Panel *pans = cp->panels.as<Panel>();
   const int *route = ctx->route_dev.as<int>();
+  // the panels of one substitution launch: with zero-work skipping, the columns whose assembled
+  // right-hand side is nonzero, packed by k_compact_panels after the assembly
+  const Panel *dpans = cp->dpans.as<Panel>();
+  const Col *dcols = cp->dcols.as<Col>();
+  auto skip = [&](const StepPlan &sp) -> cudaError_t {
+    return launch_compact_panels(st, sp.ngrp, cp->groups.as<int4>() + sp.grp_off, pans, cols,
+                                 nzf, cp->dcols.as<Col>(), cp->dpans.as<Panel>(), sp.pc,
+                                 ctx->solve_stats.as<unsigned long long>());
+  };
+  const bool zs = ctx->zero_skip;
+  const Panel *spans = zs ? dpans : pans;
+  const Col *scols = zs ? dcols : cols;
   if (!trace_plan) {
     CK(cudaMemsetAsync(u, 0, (size_t)nrhs * g.Nglob * sizeof(double2), st));
     for (int l = 0; l < L; ++l) {
@@ -677,7 +820,8 @@ dds_status run_ddm(dds_ctx *ctx, const double2 *b, int nrhs, double2 *u, int rou
         if (sp.ncols == 0) continue;
         LAUNCHK(DDS_K_ASSEMBLE, launch_assemble<R>(st, g, ctx->tb, sp.ncols, cols + sp.col_off, work, b, nullptr,
                                   l == 0, gtr + l * slot, (long long)g.nsub * g.T, g.T, 1, 0, nzf));
-        LAUNCHK(DDS_K_SUBST, subst_any<R>(ctx, sp.npanels, pans + sp.pan_off, cols, sinv, cpl, work, sp.pc, nzf));
+        if (zs) LAUNCH(skip(sp));
+        LAUNCHK(DDS_K_SUBST, subst_any<R>(ctx, sp.npanels, spans + sp.pan_off, scols, sinv, cpl, work, sp.pc, nzf));
         LAUNCHK(DDS_K_EXTRACT, launch_extract<R>(st, g, sp.ncols, cols + sp.col_off, work, u, 1, nullptr, gtr,
                                  route, l, nrhs));
       }
@@ -688,7 +832,8 @@ dds_status run_ddm(dds_ctx *ctx, const double2 *b, int nrhs, double2 *u, int rou
     // own sources: x_f = A_R^{-1} b_own; keep its raw trace lines
     LAUNCHK(DDS_K_ASSEMBLE, launch_assemble<R>(st, g, ctx->tb, all.ncols, cols + all.col_off, work, b, nullptr, 1,
                               (const C *)nullptr, 0, 0, 1, 0, nzf));
-    LAUNCHK(DDS_K_SUBST, subst_any<R>(ctx, all.npanels, pans + all.pan_off, cols, sinv, cpl, work, all.pc, nzf));
+    if (zs) LAUNCH(skip(all));
+    LAUNCHK(DDS_K_SUBST, subst_any<R>(ctx, all.npanels, spans + all.pan_off, scols, sinv, cpl, work, all.pc, nzf));
     LAUNCHK(DDS_K_EXTRACT, launch_extract<R>(st, g, all.ncols, cols + all.col_off, work, u, 0, rawf,
                              (C *)nullptr, route, 0, nrhs));
     // sweeps: every trace solve of every sweep through the trace map, in one cooperative launch
@@ -699,14 +844,29 @@ dds_status run_ddm(dds_ctx *ctx, const double2 *b, int nrhs, double2 *u, int rou
       return DDS_EINVAL;
     }
     const CallPlan::TraceTable &tt = tti->second;
-    LAUNCHK(DDS_K_TRACE_STEP, launch_trace_sweeps<R>(st, g, tt.buf.as<int4>(), tt.cols.as<int2>(),
-                                                     tt.n, tt.levs.as<int>(), tt.nlev, gmap, gtr,
-                                                     rawf, nrhs, ctx->gbar.as<unsigned>(),
-                                                     ctx->errflag.as<int>(), ctx->trace_per_sm));
+    if constexpr (sizeof(R) == 4) {
+      if (ctx->trace_tc) {
+        if (tt.tn < 0) {
+          ctx->err = "tensor-core trace schedule missing";
+          return DDS_EINVAL;
+        }
+        LAUNCHK(DDS_K_TRACE_STEP,
+                launch_trace_tc(st, g, ctx->split, tt.tunits.as<int4>(), tt.tcols.as<int>(), tt.tn,
+                                tt.tlevs.as<int>(), tt.tnlev, ctx->tttiles.as<unsigned char>(),
+                                route, (float2 *)gtr, (const float2 *)rawf, nrhs,
+                                ctx->gbar.as<unsigned>(), ctx->errflag.as<int>()));
+      }
+    }
+    if (!(sizeof(R) == 4 && ctx->trace_tc))
+      LAUNCHK(DDS_K_TRACE_STEP, launch_trace_sweeps<R>(st, g, tt.buf.as<int4>(), tt.cols.as<int2>(),
+                                                       tt.n, tt.levs.as<int>(), tt.nlev, gmap, gtr,
+                                                       rawf, nrhs, ctx->gbar.as<unsigned>(),
+                                                       ctx->errflag.as<int>(), ctx->trace_per_sm));
     // own nodes: u = A_R^{-1}(b_own + potentials of all traces received in every sweep)
     LAUNCHK(DDS_K_ASSEMBLE, launch_assemble<R>(st, g, ctx->tb, all.ncols, cols + all.col_off, work, b, nullptr, 1,
                               gtr, (long long)g.nsub * g.T, g.T, L, slot, nzf));
-    LAUNCHK(DDS_K_SUBST, subst_any<R>(ctx, all.npanels, pans + all.pan_off, cols, sinv, cpl, work, all.pc, nzf));
+    if (zs) LAUNCH(skip(all));
+    LAUNCHK(DDS_K_SUBST, subst_any<R>(ctx, all.npanels, spans + all.pan_off, scols, sinv, cpl, work, all.pc, nzf));
     LAUNCHK(DDS_K_EXTRACT, launch_extract<R>(st, g, all.ncols, cols + all.col_off, work, u, 2, (C *)nullptr,
                              (C *)nullptr, route, 0, nrhs));
   }
@@ -1078,6 +1238,8 @@ dds_status setup_impl(dds_ctx *ctx, const dds_problem *p) {
   CK(cudaMemsetAsync(ctx->status.p, 0, sizeof(int), st));
   CK(ctx->errflag.ensure(sizeof(int)));
   CK(cudaMemsetAsync(ctx->errflag.p, 0, sizeof(int), st));
+  CK(ctx->solve_stats.ensure(2 * sizeof(unsigned long long)));
+  CK(cudaMemsetAsync(ctx->solve_stats.p, 0, 2 * sizeof(unsigned long long), st));
 
   CK(cudaMemsetAsync(ctx->sinv64.p, 0, sinv_elems * sizeof(double2), st));
   CK(cudaMemsetAsync(ctx->sinv32.p, 0, sinv_elems * sizeof(float2), st));
@@ -1142,6 +1304,15 @@ dds_status setup_impl(dds_ctx *ctx, const dds_problem *p) {
     ctx->big_tc = true;
   } else {
     ctx->split = -1;   // FP32 CUDA-core substitutions
+  }
+  if (ctx->plan == DDS_PLAN_TRACE && ctx->single && ctx->split >= 0 &&
+      tt_shape(g, ctx->split, nullptr)) {
+    // trace solves on the tensor cores with the substitutions' piece type
+    CK(ctx->tttiles.ensure((size_t)tt_tiles_bytes(g, ctx->split, ctx->nfac)));
+    LAUNCH(launch_split_trace(st, g, ctx->split, ctx->nfac, ctx->gmap64.as<double2>(),
+                              ctx->tttiles.as<unsigned char>()));
+    CK(cudaStreamSynchronize(st));
+    ctx->trace_tc_avail = ctx->trace_tc = true;
   }
   if (ctx->single) ctx->sinv64.release(), ctx->gmap64.release();
   ctx->setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -1616,8 +1787,10 @@ dds_status dds_get_info(const dds_ctx *ctx, dds_info_t *info) {
   info->trace_len = ctx->g.T;
   info->plan = ctx->plan;
   info->factor_bytes = (long long)(ctx->sinv64.n + ctx->sinv32.n + ctx->gmap64.n + ctx->gmap32.n +
-                                   ctx->tctiles.n);
+                                   ctx->tctiles.n + ctx->bigtiles.n + ctx->tttiles.n);
   info->setup_seconds = ctx->setup_seconds;
+  info->trace_kernel = ctx->plan != DDS_PLAN_TRACE ? -1 : (ctx->single && ctx->trace_tc ? 0 : ctx->trace_per_sm);
+  info->subst_kernel = !ctx->single ? 0 : (ctx->split < 0 ? 1 : (ctx->big_tc ? 3 : 2));
   return DDS_OK;
 }
 
@@ -1637,8 +1810,12 @@ dds_status dds_autotune(dds_ctx *ctx, int nrhs, int rounds, int max_entries, int
     for (int pc : {8, 16, 32})
       if (subst_tc_ok(g, ctx->split, pc, ctx->tc_m > 0)) pcs.push_back(pc);
   }
-  std::vector<int> pers = {ctx->trace_per_sm};
-  if (ctx->plan == DDS_PLAN_TRACE) pers = {1, 2};
+  // trace kernel: 1 or 2 = CUDA-core kernel with that many CTAs per SM, 0 = tensor-core kernel
+  std::vector<int> pers = {ctx->trace_tc ? 0 : ctx->trace_per_sm};
+  if (ctx->plan == DDS_PLAN_TRACE) {
+    pers = {1, 2};
+    if (ctx->trace_tc_avail) pers.push_back(0);
+  }
   // synthetic right-hand sides, nonzero everywhere so that no local solve is skipped as zero
   // work (every byte 0x3F: each double is a finite ~5e-4)
   DBuf bb, uu;
@@ -1652,13 +1829,14 @@ dds_status dds_autotune(dds_ctx *ctx, int nrhs, int rounds, int max_entries, int
   const bool prof = ctx->profiling;
   ctx->profiling = false;
   double best_ms = 1e300;
-  int best_pc = ctx->tune_pc, best_per = ctx->trace_per_sm;
+  int best_pc = ctx->tune_pc, best_per = ctx->trace_tc ? 0 : ctx->trace_per_sm;
   int n = 0;
   dds_status r = DDS_OK;
   for (int pc : pcs)
     for (int per : pers) {
       ctx->tune_pc = pc;
-      ctx->trace_per_sm = per;
+      ctx->trace_tc = per == 0;
+      if (per > 0) ctx->trace_per_sm = per;
       ctx->clear_graphs();
       ctx->plans.clear();
       r = ddm(ctx, bb.as<double2>(), nrhs, uu.as<double2>(), rounds);   // build + capture
@@ -1685,7 +1863,8 @@ dds_status dds_autotune(dds_ctx *ctx, int nrhs, int rounds, int max_entries, int
   cudaEventDestroy(e1);
   ctx->profiling = prof;
   ctx->tune_pc = best_pc;
-  ctx->trace_per_sm = best_per;
+  ctx->trace_tc = best_per == 0;
+  if (best_per > 0) ctx->trace_per_sm = best_per;
   ctx->clear_graphs();
   ctx->plans.clear();
   if (r != DDS_OK) return r;
@@ -1748,6 +1927,36 @@ dds_status dds_profile_read(dds_ctx *ctx, int kind, long long *launches, double 
   CK(prof_fold(ctx));
   if (launches) *launches = ctx->prof_count[kind];
   if (ms) *ms = ctx->prof_ms[kind];
+  return DDS_OK;
+}
+
+dds_status dds_set_zero_skip(dds_ctx *ctx, int enable) {
+  if (!ctx) return DDS_EINVAL;
+  Busy busy(ctx);
+  if (!busy.ok) return DDS_EBUSY;
+  ctx->err.clear();
+  if ((enable != 0) != ctx->zero_skip) {
+    ctx->zero_skip = enable != 0;
+    ctx->clear_graphs();   // the captured launch sequences differ
+  }
+  return DDS_OK;
+}
+
+dds_status dds_local_solve_counts(dds_ctx *ctx, long long *solved, long long *assembled,
+                                  int reset) {
+  if (!ctx) return DDS_EINVAL;
+  Busy busy(ctx);
+  if (!busy.ok) return DDS_EBUSY;
+  ctx->err.clear();
+  unsigned long long h[2] = {0, 0};
+  CK(cudaMemcpyAsync(h, ctx->solve_stats.p, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (solved) *solved = (long long)h[0];
+  if (assembled) *assembled = (long long)h[1];
+  if (reset) {
+    CK(cudaMemsetAsync(ctx->solve_stats.p, 0, sizeof(h), ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
   return DDS_OK;
 }
 

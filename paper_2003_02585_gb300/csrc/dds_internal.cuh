@@ -117,6 +117,40 @@ __host__ __device__ inline void own_range(const Geom &g, const int k[3], int a, 
 }
 
 // ------------------------------------------------------------------------------------------
+// the FP64 / FP32 trace map (trace plan): per factor [output side d][row tile of 64][input
+// k = 0..T)[64 rows], rows past 2 Lt_d zero, so the rows of one tile for a run of consecutive
+// inputs are one contiguous slice
+// ------------------------------------------------------------------------------------------
+constexpr int kTraceRows = 64;
+
+__host__ __device__ inline int trace_tiles(const Geom &g, int d) {
+  return (2 * g.Lt[d] + kTraceRows - 1) / kTraceRows;
+}
+__host__ __device__ inline int trace_max_tiles(const Geom &g) {
+  int m = 0;
+  for (int d = 0; d < g.nsides; ++d) m = trace_tiles(g, d) > m ? trace_tiles(g, d) : m;
+  return m;
+}
+// element offset of (factor f, side d, tile tl, input k, row r) in the tiled trace map
+__host__ __device__ inline long long gmap_index(const Geom &g, int f, int d, int tl, long long k,
+                                                int r) {
+  const long long per_tile = (long long)g.T * kTraceRows;
+  const long long per_side = per_tile * trace_max_tiles(g);
+  const long long per_fac = per_side * g.nsides;
+  return f * per_fac + d * per_side + tl * per_tile + k * kTraceRows + r;
+}
+
+// Level completion counters of the cooperative trace launches: eight words per dataflow level
+// (arrivals spread over them by CTA index), zeroed before every launch
+constexpr int kStepCounters = 8;
+
+__device__ inline unsigned ld_acquire_gpu(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// ------------------------------------------------------------------------------------------
 // work descriptors
 // ------------------------------------------------------------------------------------------
 struct Col { int sub; int rhs; int slot; int pad; };     // one (subdomain, RHS) local problem
@@ -178,6 +212,14 @@ cudaError_t launch_assemble(cudaStream_t st, const Geom &g, const Tables &tb, in
                             long long trace_sub_stride, int nslots, long long slot_stride,
                             int *nzflag = nullptr);
 
+// zero-work skipping: pack the columns with a nonzero right-hand side (nz[slot]) of each
+// group (int4: column range [x, y), panel range [z, w), one factor) into dcols / dpans (same
+// index space as cols / panels; surplus panels get ncol = 0); stats[0] += live columns,
+// stats[1] += columns
+cudaError_t launch_compact_panels(cudaStream_t st, int ngroups, const int4 *groups,
+                                  const Panel *pans, const Col *cols, const int *nz, Col *dcols,
+                                  Panel *dpans, int pc, unsigned long long *stats);
+
 template <typename R>
 cudaError_t launch_subst(cudaStream_t st, const Geom &g, int npanels, const Panel *panels,
                          const Col *cols, const typename Cx<R>::T *sinv,
@@ -213,6 +255,25 @@ long long tc_tiles_bytes(const Geom &g, int kind, int nfac);
 cudaError_t launch_split_tc(cudaStream_t st, const Geom &g, int kind, int nfac,
                             const double2 *sinv64, const double2 *tw64, int m,
                             unsigned char *tiles);
+
+// tensor-core trace solves (k_trace_tc.cu): split-map shape, its set-up and the cooperative
+// launch over the dataflow levels (units: int4 headers, ucols: RHS * nsub + subdomain words)
+struct TtShape {
+  int kind, EK, KE;      // piece type, elements per 16 bytes, elements per K-step
+  int RT;                // 128-row tiles of the stacked output rows
+  int KP;                // stacked inputs, each side padded to a multiple of 16
+  int kpo[6], kpn[6];    // offset / padded count of side d's inputs
+  long long rt_bytes, fac_bytes;
+  size_t smem;
+};
+bool tt_shape(const Geom &g, int kind, TtShape *s);
+long long tt_tiles_bytes(const Geom &g, int kind, int nfac);
+cudaError_t launch_split_trace(cudaStream_t st, const Geom &g, int kind, int nfac,
+                               const double2 *gmap64, unsigned char *tiles);
+cudaError_t launch_trace_tc(cudaStream_t st, const Geom &g, int kind, const int4 *units,
+                            const int *ucols, int nunits, const int *lev_off, int nlevels,
+                            const unsigned char *tiles, const int *route, float2 *gtr,
+                            const float2 *rawf, int nrhs, unsigned *gbar, int *err);
 
 template <typename R>
 cudaError_t launch_extract(cudaStream_t st, const Geom &g, int ncols, const Col *cols,

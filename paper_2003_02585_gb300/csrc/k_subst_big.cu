@@ -170,6 +170,7 @@ __global__ void __launch_bounds__(192, 1)
   const int ks = (unit / a.RT) % ((a.KT + a.KTU - 1) / a.KTU);
   const int pn = unit / (a.RT * ((a.KT + a.KTU - 1) / a.KTU));
   const Panel p = panels[pn];
+  if (p.ncol == 0) return;   // an empty panel of a compacted list: its B and acc stay zero
   const int t0 = ks * a.KTU, nt = min(a.KTU, a.KT - t0);
   const uint32_t a_step = 16384u, b_step = 128u * PC;
   const uint32_t slot_bytes = (a_step + b_step) * a.KS;

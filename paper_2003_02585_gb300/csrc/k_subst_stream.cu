@@ -28,6 +28,7 @@ __global__ void __launch_bounds__(256, 1) k_subst_stream(Geom g, const Panel *__
   float2 *red = vbuf + 2 * Mb * PC;                       // [Mb][PC]
   uint64_t *bars = reinterpret_cast<uint64_t *>(red + Mb * PC);
   const Panel p = panels[blockIdx.x];
+  if (p.ncol == 0) return;   // an empty panel of a compacted list (zero-work skipping)
   const float2 *Sf = sinv + (long long)p.factor * Ml * St;
   const float2 *cf = cpl + (long long)p.factor * Ml * (long long)Mb;
   const int tid = threadIdx.x;

@@ -252,6 +252,8 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1)
   float2 *xch = reinterpret_cast<float2 *>(sB + (size_t)(a.Kp / (KIND == 0 ? 4 : 8)) * a.LB);
   const Panel p = panels[TW ? blockIdx.x / 2 : blockIdx.x];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // an empty panel of a compacted list (zero-work skipping); both CTAs of a cluster leave
+  if (p.ncol == 0) return;
   if (nz != nullptr) {
     // zero-work skipping: the solve of a zero right-hand side is zero, which work already holds
     // (both CTAs of a cluster see the same columns and leave together)

@@ -102,6 +102,7 @@ __global__ void __launch_bounds__(128) k_subst(Geom g, const Panel *__restrict__
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *v = reinterpret_cast<C *>(smem_raw);  // [Mb][PC]
   const Panel p = panels[blockIdx.x];
+  if (p.ncol == 0) return;   // an empty panel of a compacted list (zero-work skipping)
   const int Mb = g.Mb, Ml = g.Ml;
   const C *Sf = sinv + (long long)p.factor * Ml * g.St;
   const C *cf = cpl + (long long)p.factor * Ml * (long long)Mb;
@@ -232,24 +233,6 @@ __global__ void k_extract(Geom g, const Col *__restrict__ cols,
 // Gmap layout per factor: [output side d][row tile of 64][input k = 0..T)[64 rows], rows past
 // 2 Lt_d zero, so the rows of one tile for a run of consecutive inputs are one contiguous slice.
 // ------------------------------------------------------------------------------------------
-constexpr int kTraceRows = 64;
-
-__host__ __device__ inline int trace_tiles(const Geom &g, int d) {
-  return (2 * g.Lt[d] + kTraceRows - 1) / kTraceRows;
-}
-__host__ __device__ inline int trace_max_tiles(const Geom &g) {
-  int m = 0;
-  for (int d = 0; d < g.nsides; ++d) m = trace_tiles(g, d) > m ? trace_tiles(g, d) : m;
-  return m;
-}
-// element offset of (factor f, side d, tile tl, input k, row r) in the tiled trace map
-__host__ __device__ inline long long gmap_index(const Geom &g, int f, int d, int tl, long long k,
-                                                int r) {
-  const long long per_tile = (long long)g.T * kTraceRows;
-  const long long per_side = per_tile * trace_max_tiles(g);
-  const long long per_fac = per_side * g.nsides;
-  return f * per_fac + d * per_side + tl * per_tile + k * kTraceRows + r;
-}
 long long gmap_elems(const Geom &g, int nfac) { return gmap_index(g, nfac, 0, 0, 0, 0); }
 
 // Work items of the cooperative trace launch (built on the host, TraceItem): one output side,
@@ -285,13 +268,6 @@ template <> __device__ inline void atomic_cadd<double2>(double2 *dst, double2 v)
 // without items never wait.  The counters are zeroed before every launch.  The wait is bounded:
 // on a timeout the CTA records code 4 and goes on (results wrong, launch ends, the host reports
 // DDS_ETIMEOUT).
-constexpr int kStepCounters = 8;
-
-__device__ inline unsigned ld_acquire_gpu(const unsigned *p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
 __device__ inline void step_arrive(unsigned *cnt, int s) {
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -605,6 +581,69 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
     }
   }
   // every staged item is consumed in its level, so no copy is in flight here
+}
+
+// ------------------------------------------------------------------------------------------
+// Zero-work skipping (Algorithm 2.1: "if f_ij != 0 solve, else u_ij = 0").  A local problem
+// whose assembled right-hand side is exactly zero has the zero solution, which its work slot
+// already holds, so its substitutions are dropped.  One CTA per group of consecutive panels
+// that share a factor (gr = column range [x, y), panel range [z, w)): the group's columns with
+// a nonzero right-hand side (nz[slot], written by k_assemble) are packed, in their order, into
+// dcols[x ...]; the group's panels become ceil(live / pc) panels of up to pc packed columns
+// followed by empty ones (ncol = 0, which every substitution kernel leaves at once).
+// stats[0] += live columns, stats[1] += columns.
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024)
+    k_compact_panels(const int4 *__restrict__ groups, const Panel *__restrict__ pans,
+                     const Col *__restrict__ cols, const int *__restrict__ nz,
+                     Col *__restrict__ dcols, Panel *__restrict__ dpans, int pc,
+                     unsigned long long *__restrict__ stats) {
+  __shared__ int wsum[32];
+  const int4 gr = groups[blockIdx.x];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  int carry = 0;   // live columns packed so far (the same in every thread)
+  for (int base = gr.x; base < gr.y; base += blockDim.x) {
+    const int i = base + tid;
+    const bool live = i < gr.y && nz[cols[i].slot] != 0;
+    const unsigned m = __ballot_sync(0xffffffffu, live);
+    if (lane == 0) wsum[warp] = __popc(m);
+    __syncthreads();
+    if (warp == 0) {
+      int v = lane < nw ? wsum[lane] : 0;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+      }
+      wsum[lane] = v;   // inclusive over warps
+    }
+    __syncthreads();
+    const int before = warp > 0 ? wsum[warp - 1] : 0;
+    if (live) dcols[gr.x + carry + before + __popc(m & ((1u << lane) - 1u))] = cols[i];
+    carry += wsum[nw - 1];
+    __syncthreads();   // wsum is rewritten in the next chunk
+  }
+  const int n = carry, factor = pans[gr.z].factor;
+  const int need = (n + pc - 1) / pc;
+  for (int q = tid; q < gr.w - gr.z; q += blockDim.x) {
+    Panel p;
+    p.factor = factor;
+    p.pad = 0;
+    p.col0 = q < need ? gr.x + q * pc : gr.x;
+    p.ncol = q < need ? min(pc, n - q * pc) : 0;
+    dpans[gr.z + q] = p;
+  }
+  if (tid == 0) {
+    atomicAdd(stats, (unsigned long long)n);
+    atomicAdd(stats + 1, (unsigned long long)(gr.y - gr.x));
+  }
+}
+
+cudaError_t launch_compact_panels(cudaStream_t st, int ngroups, const int4 *groups,
+                                  const Panel *pans, const Col *cols, const int *nz, Col *dcols,
+                                  Panel *dpans, int pc, unsigned long long *stats) {
+  if (ngroups <= 0) return cudaSuccess;
+  k_compact_panels<<<ngroups, 1024, 0, st>>>(groups, pans, cols, nz, dcols, dpans, pc, stats);
+  return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------------------------------

@@ -1,0 +1,555 @@
+// Trace transfer on the 5th-generation tensor cores (tcgen05): every trace solve of one DDM
+// application of the trace-operator plan as complex split-product GEMMs.
+//
+// The trace solve of (sweep l, subdomain X) maps the traces X received in slot l to the traces it
+// sends (Lemma 2.2 in discrete form, the back-trace correction folded into the map):
+//   out[R] = sum_k Map_f[R][k] in_l,X[k]   (+ the raw own-source lines in the first sweep),
+// R over the stacked output rows of every side (side d at toff_d .. toff_d + 2 Lt_d), k over the
+// inputs of the sides that receive in sweep l.  Row R of side d is added to the slot
+// route[l][d] of the neighbour across d, at its side d ^ 1.  All (l, X, RHS) columns of one
+// dataflow level that share a factor and a sweep share the map, so a level is a GEMM
+//   (128-row tile of Map_f) x (K = received inputs) x (32 columns)
+// per work unit, run with the split products of k_subst_tc.cu (pieces a = a0 + a1, b = b0 + b1,
+// a b ~ a0 b0 + a0 b1 + a1 b0, TF32 or BF16 pieces, FP32 accumulation in tensor memory) and the
+// real-ified complex form: B = [b0_re | b0_im | b1_re | b1_im] (4 x 32 rows of the K-major B
+// operand), D1 = A0_re B + A1_re B[:64], D2 = A0_im B + A1_im B[:64].
+//
+// One CTA per SM, cooperative launch over the dataflow levels (the schedule and level counters
+// of k_trace_sweeps).  Warp roles:
+//   warps 0-3   epilogue: TMEM lane quarter = warp; row R of the tile per thread; forms the
+//               complex outputs of the 32 columns and adds them into the receivers' slots with
+//               vector reductions; arrives on the level counter after its level's units;
+//   warps 4-7   B producers: after the level barrier, load the unit's inputs from the trace
+//               slots (L1 bypassed: other CTAs wrote them), split them into pieces and store
+//               them in the canonical K-major layout of the ring slot;
+//   warp 8      A producer: streams the pre-split map tiles through the two-slot ring with bulk
+//               copies completed on the slot's mbarrier (independent of the levels, so it runs
+//               ahead);
+//   warp 9      MMA issuer (one thread) and owner of the tensor memory: two accumulator pairs,
+//               so that the epilogue of one unit runs under the MMAs of the next.
+// Every wait is bounded; on a timeout the CTA records an error code, stops issuing work, lets its
+// copies and MMAs drain, frees its tensor memory and leaves (the host reports DDS_ETIMEOUT).
+#include "async_copy.cuh"
+#include "dds_internal.cuh"
+#include "umma.cuh"
+
+namespace dds {
+
+namespace {
+
+constexpr int kTtCols = 32;        // complex columns per unit
+constexpr int kTtKS = 4;           // K-steps per ring chunk
+constexpr int kTtSlots = 2;        // ring slots
+constexpr int kTtStep = 16384;     // bytes of one K-step of an A tile (4 comps x 2 x 128 x 16)
+constexpr int kTtLB = 4 * kTtCols * 16 + 16;   // bytes per 16-byte K group of B (+16: banks)
+constexpr int kTtBStep = 2 * kTtLB;            // bytes of one K-step of B
+constexpr int kTtSlotBytes = kTtKS * (kTtStep + kTtBStep);
+constexpr int kTtThreads = 320;
+constexpr int kTtTmemCols = 512;   // two accumulator pairs of 8 x 32 FP32 columns
+
+}  // namespace
+
+// Split-map layout, per factor: [row tile rt][K-step t][comp][g][row m < 128][16 bytes]; comp
+// 0/1 = pieces 0/1 of the real part, 2/3 of the imaginary part; g = which 16-byte core-matrix
+// column of the K-step (the canonical K-major no-swizzle layout, as k_subst_tc.cu).  Inputs are
+// stacked by side with side d at kpo[d], its 2 Lt_d values padded to a multiple of 16.
+bool tt_shape(const Geom &g, int kind, TtShape *s) {
+  TtShape t{};
+  t.kind = kind;
+  t.EK = kind == 0 ? 4 : 8;
+  t.KE = 2 * t.EK;
+  t.RT = (g.T + 127) / 128;
+  int off = 0;
+  for (int d = 0; d < 6; ++d) {
+    t.kpo[d] = off;
+    t.kpn[d] = d < g.nsides ? (2 * g.Lt[d] + 15) / 16 * 16 : 0;
+    off += t.kpn[d];
+  }
+  t.KP = off;
+  t.rt_bytes = (long long)(t.KP / t.KE) * kTtStep;
+  t.fac_bytes = (long long)t.RT * t.rt_bytes;
+  t.smem = (size_t)kTtSlots * kTtSlotBytes + 1024;
+  if (t.smem > 227 * 1024) return false;
+  if (s) *s = t;
+  return true;
+}
+
+long long tt_tiles_bytes(const Geom &g, int kind, int nfac) {
+  TtShape t;
+  if (!tt_shape(g, kind, &t)) return 0;
+  return (long long)nfac * t.fac_bytes;
+}
+
+template <int KIND>
+__global__ void k_split_trace(const double2 *__restrict__ gmap, unsigned char *__restrict__ out,
+                              Geom g, TtShape t, int nfac) {
+  constexpr int EK = KIND == 0 ? 4 : 8, ES = 16 / EK;
+  const long long rows = (long long)t.RT * 128;
+  const long long total = (long long)nfac * rows * t.KP;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int R = (int)(i % rows);
+    const int kp = (int)((i / rows) % t.KP);
+    const int f = (int)(i / (rows * t.KP));
+    // output side / row of R, input side / index of kp
+    double2 a = make_double2(0.0, 0.0);
+    int dout = -1, din = -1;
+    for (int d = 0; d < g.nsides; ++d) {
+      if (R >= g.toff[d] && R < g.toff[d] + 2 * g.Lt[d]) dout = d;
+      if (kp >= t.kpo[d] && kp < t.kpo[d] + t.kpn[d]) din = d;
+    }
+    if (dout >= 0 && din >= 0 && kp - t.kpo[din] < 2 * g.Lt[din]) {
+      const int ro = R - g.toff[dout];
+      const long long k = g.toff[din] + (kp - t.kpo[din]);
+      a = gmap[gmap_index(g, f, dout, ro / kTraceRows, k, ro % kTraceRows)];
+    }
+    const int rt = R / 128, m = R % 128;
+    const int ts = kp / t.KE, gg = (kp / EK) & 1;
+    unsigned char *base = out + (long long)f * t.fac_bytes + (long long)rt * t.rt_bytes +
+                          (long long)ts * kTtStep + (long long)gg * 128 * 16 + m * 16 + (kp % EK) * ES;
+    const double parts[2] = {a.x, a.y};
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const double x = parts[e];
+      unsigned char *p0 = base + (long long)(2 * e + 0) * 2 * 128 * 16;
+      unsigned char *p1 = base + (long long)(2 * e + 1) * 2 * 128 * 16;
+      if (KIND == 0) {
+        const float x0 = umma::tf32_rna((float)x);
+        const float x1 = umma::tf32_rna((float)(x - (double)x0));
+        *reinterpret_cast<float *>(p0) = x0;
+        *reinterpret_cast<float *>(p1) = x1;
+      } else {
+        const unsigned short b0 = umma::bf16_rn_bits((float)x);
+        const unsigned short b1 = umma::bf16_rn_bits((float)(x - (double)umma::bf16_to_float(b0)));
+        *reinterpret_cast<unsigned short *>(p0) = b0;
+        *reinterpret_cast<unsigned short *>(p1) = b1;
+      }
+    }
+  }
+}
+
+cudaError_t launch_split_trace(cudaStream_t st, const Geom &g, int kind, int nfac,
+                               const double2 *gmap64, unsigned char *tiles) {
+  TtShape t;
+  if (!tt_shape(g, kind, &t)) return cudaErrorInvalidValue;
+  const long long total = (long long)nfac * t.RT * 128 * t.KP;
+  const int blocks = (int)std::min<long long>((total + 255) / 256, 152LL * 16);
+  if (kind == 0)
+    k_split_trace<0><<<blocks, 256, 0, st>>>(gmap64, tiles, g, t, nfac);
+  else
+    k_split_trace<1><<<blocks, 256, 0, st>>>(gmap64, tiles, g, t, nfac);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Work units (host-built): hdr = (factor | columns << 24, sweep | row tile << 16, first column
+// word, input sides mask | raw << 8); column words = RHS * nsub + subdomain.
+
+struct TtUnit {
+  int factor, ncol, l, rt, col0, kmask, raw;
+};
+__device__ inline TtUnit tt_unit(const int4 *units, int idx) {
+  const int4 h = __ldg(units + idx);
+  TtUnit u;
+  u.factor = h.x & 0xFFFFFF;
+  u.ncol = (h.x >> 24) & 0xFF;
+  u.l = h.y & 0xFFFF;
+  u.rt = (h.y >> 16) & 0xFFFF;
+  u.col0 = h.z;
+  u.kmask = h.w & 0xFF;
+  u.raw = (h.w >> 8) & 1;
+  return u;
+}
+
+// chunks of a unit: per input side in the mask, its K-steps in runs of at most kTtKS
+__device__ inline int tt_nchunks(const TtShape &t, int kmask) {
+  int n = 0;
+  for (int d = 0; d < 6; ++d)
+    if ((kmask >> d) & 1) n += (t.kpn[d] / t.KE + kTtKS - 1) / kTtKS;
+  return n;
+}
+// chunk c of a unit: input side, first K-step within the side, K-steps
+__device__ inline void tt_chunk(const TtShape &t, int kmask, int c, int &d, int &t0, int &nks) {
+  for (d = 0; d < 6; ++d) {
+    if (!((kmask >> d) & 1)) continue;
+    const int ns = t.kpn[d] / t.KE, nc = (ns + kTtKS - 1) / kTtKS;
+    if (c < nc) {
+      t0 = c * kTtKS;
+      nks = min(kTtKS, ns - t0);
+      return;
+    }
+    c -= nc;
+  }
+  d = 0;
+  t0 = 0;
+  nks = 0;
+}
+
+// the pieces of v written as B rows c (real) and 32 + c (imaginary) of piece 0, and the same
+// rows + 64 of piece 1, at K position k of the chunk
+template <int KIND>
+__device__ __forceinline__ void tt_put_b(unsigned char *sB, int k, int c, float2 v) {
+  constexpr int EK = KIND == 0 ? 4 : 8, ES = 16 / EK;
+  const int off = (k / EK) * kTtLB + (k % EK) * ES;
+  const int n[4] = {c, kTtCols + c, 2 * kTtCols + c, 3 * kTtCols + c};
+  if (KIND == 0) {
+    float w[4];
+    w[0] = __uint_as_float((__float_as_uint(v.x) + 0x1000u) & 0xFFFFE000u);
+    w[1] = __uint_as_float((__float_as_uint(v.y) + 0x1000u) & 0xFFFFE000u);
+    const float rx = v.x - w[0], ry = v.y - w[1];
+    w[2] = __uint_as_float((__float_as_uint(rx) + 0x1000u) & 0xFFFFE000u);
+    w[3] = __uint_as_float((__float_as_uint(ry) + 0x1000u) & 0xFFFFE000u);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      *reinterpret_cast<float *>(sB + off + (n[i] >> 3) * 128 + (n[i] & 7) * 16) = w[i];
+  } else {
+    unsigned short b[4];
+    b[0] = (unsigned short)((__float_as_uint(v.x) + 0x8000u) >> 16);
+    b[1] = (unsigned short)((__float_as_uint(v.y) + 0x8000u) >> 16);
+    b[2] = (unsigned short)((__float_as_uint(v.x - umma::bf16_to_float(b[0])) + 0x8000u) >> 16);
+    b[3] = (unsigned short)((__float_as_uint(v.y - umma::bf16_to_float(b[1])) + 0x8000u) >> 16);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      *reinterpret_cast<unsigned short *>(sB + off + (n[i] >> 3) * 128 + (n[i] & 7) * 16) = b[i];
+  }
+}
+
+__device__ inline void named_sync(int id, int threads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kTtThreads, 1)
+    k_trace_tc(Geom g, TtShape t, const int4 *__restrict__ units, const int *__restrict__ ucols,
+               const int *__restrict__ lev_off, int nlev, const unsigned char *__restrict__ tiles,
+               const int *__restrict__ route, float2 *__restrict__ gtr,
+               const float2 *__restrict__ rawf, int nrhs, unsigned *cnt, int *__restrict__ err) {
+  constexpr uint32_t kIdN4 = KIND == 0 ? umma::idesc_tf32(128, 4 * kTtCols)
+                                       : umma::idesc_bf16(128, 4 * kTtCols);
+  constexpr uint32_t kIdN2 = KIND == 0 ? umma::idesc_tf32(128, 2 * kTtCols)
+                                       : umma::idesc_bf16(128, 2 * kTtCols);
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // full[s]: A bytes + one arrival per B-producer warp; empty[s]: MMA commit; accf[b]: MMA
+  // commit; acce[b]: one arrival per epilogue warp; drain: final MMA commit
+  __shared__ uint64_t full[kTtSlots], empty[kTtSlots], accf[2], acce[2], drain;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int G = (int)gridDim.x, b = (int)blockIdx.x;
+  auto pos = [&](int r) { return r * G + ((r & 1) ? G - 1 - b : b); };
+  auto aborted = [&]() { return *reinterpret_cast<volatile int *>(&abort_flag) != 0; };
+  auto fail = [&](int code) {
+    atomicExch(err, code);
+    *reinterpret_cast<volatile int *>(&abort_flag) = 1;
+  };
+  auto slotA = [&](int s) { return smem_raw + (size_t)s * kTtSlotBytes; };
+  auto slotB = [&](int s) { return smem_raw + (size_t)s * kTtSlotBytes + kTtKS * kTtStep; };
+  const long long slot_stride = (long long)nrhs * g.nsub * g.T;
+
+  if (tid == 0) {
+    for (int s = 0; s < kTtSlots; ++s) {
+      mbar_init(&full[s], 1 + 4);
+      mbar_init(&empty[s], 1);
+    }
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(&accf[q], 1);
+      mbar_init(&acce[q], 4);
+    }
+    mbar_init(&drain, 1);
+    abort_flag = 0;
+    mbar_init_fence();
+  }
+  if (warp == 9) {
+    umma::tmem_alloc(&tmem_base, kTtTmemCols);
+    umma::tmem_relinquish();
+  }
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  const uint32_t tmem = tmem_base;
+
+  if (warp == 8) {
+    // ---------------- A producer: the map tiles of every unit's chunks, in unit order
+    if (lane == 0) {
+      int ci = 0;                 // chunks issued
+      int last[kTtSlots];
+      for (int s = 0; s < kTtSlots; ++s) last[s] = -1;
+      for (int v = 0; v < nlev && !aborted(); ++v) {
+        const int base = __ldg(lev_off + v), Nv = __ldg(lev_off + v + 1) - base;
+        for (int r = 0; pos(r) < Nv && !aborted(); ++r) {
+          const TtUnit u = tt_unit(units, base + pos(r));
+          const int nch = tt_nchunks(t, u.kmask);
+          for (int c = 0; c < nch; ++c, ++ci) {
+            const int s = ci % kTtSlots;
+            if (ci >= kTtSlots && !mbar_wait(&empty[s], ((ci / kTtSlots) - 1) & 1)) {
+              fail(21);
+              break;
+            }
+            if (aborted()) break;
+            int d, t0, nks;
+            tt_chunk(t, u.kmask, c, d, t0, nks);
+            const uint32_t bytes = (uint32_t)nks * kTtStep;
+            const unsigned char *src = tiles + (long long)u.factor * t.fac_bytes +
+                                       (long long)u.rt * t.rt_bytes +
+                                       (long long)(t.kpo[d] / t.KE + t0) * kTtStep;
+            mbar_arrive_expect_tx(&full[s], bytes);
+            bulk_g2s(slotA(s), src, bytes, &full[s]);
+            last[s] = ci;
+          }
+        }
+      }
+      // no copy may still be landing when the CTA leaves
+      for (int s = 0; s < kTtSlots; ++s)
+        if (last[s] >= 0 && !mbar_wait(&full[s], (last[s] / kTtSlots) & 1)) atomicExch(err, 22);
+    }
+  } else if (warp == 9) {
+    // ---------------- MMA issuer
+    if (lane == 0) {
+      const uint32_t lbo_a = 128u * 16u;
+      const uint64_t dA = (uint64_t)kTtStep >> 4;        // one K-step of A (16-byte units)
+      const uint64_t dC = (uint64_t)(2 * 128 * 16) >> 4; // one component of A
+      const uint64_t dB = (uint64_t)kTtBStep >> 4;       // one K-step of B
+      int ci = 0, mi = 0;   // chunks consumed, MMA units issued
+      for (int v = 0; v < nlev && !aborted(); ++v) {
+        const int base = __ldg(lev_off + v), Nv = __ldg(lev_off + v + 1) - base;
+        for (int r = 0; pos(r) < Nv && !aborted(); ++r) {
+          const TtUnit u = tt_unit(units, base + pos(r));
+          const int nch = tt_nchunks(t, u.kmask);
+          if (nch == 0) continue;
+          const int q = mi & 1;
+          if (mi >= 2 && !mbar_wait(&acce[q], ((mi >> 1) - 1) & 1)) { fail(23); break; }
+          umma::fence_after_sync();
+          const uint32_t d1 = tmem + (uint32_t)q * (8 * kTtCols), d2 = d1 + 4 * kTtCols;
+          bool ok = true;
+          for (int c = 0; c < nch; ++c, ++ci) {
+            const int s = ci % kTtSlots;
+            if (!mbar_wait(&full[s], (ci / kTtSlots) & 1)) { fail(24); ok = false; break; }
+            if (aborted()) { ok = false; break; }
+            umma::fence_after_sync();
+            int d, t0, nks;
+            tt_chunk(t, u.kmask, c, d, t0, nks);
+            uint64_t ad = umma::smem_desc(umma::saddr(slotA(s)), lbo_a, 128);
+            uint64_t bd = umma::smem_desc(umma::saddr(slotB(s)), (uint32_t)kTtLB, 128);
+            for (int k = 0; k < nks; ++k) {
+              const uint32_t acc = (c > 0 || k > 0) ? 1u : 0u;
+              if (KIND == 0) {
+                umma::mma_tf32(d1, ad, bd, kIdN4, acc);
+                umma::mma_tf32(d1, ad + dC, bd, kIdN2, 1);
+                umma::mma_tf32(d2, ad + 2 * dC, bd, kIdN4, acc);
+                umma::mma_tf32(d2, ad + 3 * dC, bd, kIdN2, 1);
+              } else {
+                umma::mma_bf16(d1, ad, bd, kIdN4, acc);
+                umma::mma_bf16(d1, ad + dC, bd, kIdN2, 1);
+                umma::mma_bf16(d2, ad + 2 * dC, bd, kIdN4, acc);
+                umma::mma_bf16(d2, ad + 3 * dC, bd, kIdN2, 1);
+              }
+              ad += dA;
+              bd += dB;
+            }
+            umma::mma_commit(&empty[s]);   // the slot is free once these MMAs have read it
+          }
+          if (!ok) break;
+          umma::mma_commit(&accf[q]);
+          ++mi;
+        }
+      }
+      umma::mma_commit(&drain);
+      if (!mbar_wait(&drain, 0)) atomicExch(err, 25);
+    }
+  } else if (warp >= 4) {
+    // ---------------- B producers: inputs of every unit's chunks, split into pieces
+    const int pt = tid - 128;   // 0..127
+    int ci = 0;
+    for (int v = 0; v < nlev; ++v) {
+      const int base = __ldg(lev_off + v), Nv = __ldg(lev_off + v + 1) - base;
+      if (pos(0) >= Nv) continue;
+      if (v > 0) {
+        // the level barrier: every CTA has finished (and published) level v - 1
+        if (warp == 4) {
+          uint32_t spins = 0;
+          for (;;) {
+            unsigned x = lane < kStepCounters ? ld_acquire_gpu(cnt + (v - 1) * kStepCounters + lane) : 0u;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            if (x >= (unsigned)G) break;
+            int stop = 0;
+            if (lane == 0)
+              stop = (++spins > (1u << 20)) || *reinterpret_cast<volatile int *>(err) != 0;
+            stop = __shfl_sync(0xffffffffu, stop, 0);
+            if (stop) {
+              if (lane == 0) { atomicExch(err, 4); *reinterpret_cast<volatile int *>(&abort_flag) = 1; }
+              break;
+            }
+            __nanosleep(64);
+          }
+        }
+        named_sync(2, 128);
+      }
+      for (int r = 0; pos(r) < Nv; ++r) {
+        const TtUnit u = tt_unit(units, base + pos(r));
+        const int nch = tt_nchunks(t, u.kmask);
+        for (int c = 0; c < nch; ++c, ++ci) {
+          const int s = ci % kTtSlots;
+          if (ci >= kTtSlots && !aborted()) {
+            // (after an abort no wait is made: the MMAs may have stopped consuming)
+            int okw = 1;
+            if (lane == 0) okw = mbar_wait(&empty[s], ((ci / kTtSlots) - 1) & 1) ? 1 : 0;
+            okw = __shfl_sync(0xffffffffu, okw, 0);
+            if (!okw && lane == 0) fail(26);
+          }
+          int d, t0, nks;
+          tt_chunk(t, u.kmask, c, d, t0, nks);
+          if (!aborted()) {
+            unsigned char *sB = slotB(s);
+            const int nk = nks * t.KE;                 // K values of the chunk
+            const int k0 = t0 * t.KE;                  // first K value within the side
+            const int lim = 2 * g.Lt[d];
+            for (int idx = pt; idx < kTtCols * nk; idx += 128) {
+              const int c2 = idx / nk, kk = idx - c2 * nk;
+              float2 val = make_float2(0.f, 0.f);
+              if (c2 < u.ncol && k0 + kk < lim) {
+                const int col = __ldg(ucols + u.col0 + c2);
+                val = __ldcg(gtr + (long long)u.l * slot_stride + (long long)col * g.T +
+                             g.toff[d] + k0 + kk);
+              }
+              tt_put_b<KIND>(sB, kk, c2, val);
+            }
+          }
+          fence_proxy_async();   // the generic writes of B before the MMAs' async reads
+          umma::fence_before_sync();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&full[s]);
+        }
+      }
+    }
+  } else {
+    // ---------------- epilogue: row R of the unit's tile, every column
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    int mi = 0;
+    for (int v = 0; v < nlev; ++v) {
+      const int base = __ldg(lev_off + v), Nv = __ldg(lev_off + v + 1) - base;
+      for (int r = 0; pos(r) < Nv; ++r) {
+        const TtUnit u = tt_unit(units, base + pos(r));
+        const int nch = tt_nchunks(t, u.kmask);
+        const int R = u.rt * 128 + warp * 32 + lane;
+        int dout = -1, ro = 0, dst_off = 0;
+#pragma unroll
+        for (int d = 0; d < 6; ++d)
+          if (d < g.nsides && R >= g.toff[d] && R < g.toff[d] + 2 * g.Lt[d]) {
+            dout = d;
+            ro = R - g.toff[d];
+            dst_off = g.toff[d ^ 1] + ro;   // the same row of the receiver's side d ^ 1
+          }
+        const int lp = dout >= 0 ? __ldg(route + u.l * 6 + dout) : -1;
+        float2 out[kTtCols];
+#pragma unroll
+        for (int c = 0; c < kTtCols; ++c) out[c] = make_float2(0.f, 0.f);
+        if (nch > 0) {
+          const int q = mi & 1;
+          int ok = 1;
+          if (lane == 0) ok = (!aborted() && mbar_wait(&accf[q], (mi >> 1) & 1)) ? 1 : 0;
+          ok = __shfl_sync(0xffffffffu, ok, 0);
+          if (!ok && lane == 0 && !aborted()) fail(27);
+          if (ok) {
+            umma::fence_after_sync();
+            const uint32_t d1 = tmem + lane_base + (uint32_t)q * (8 * kTtCols);
+            const uint32_t d2 = d1 + 4 * kTtCols;
+#pragma unroll
+            for (int cg = 0; cg < kTtCols; cg += 8) {
+              float x[8][8];
+              umma::tmem_ld8(d1 + cg, x[0]);                   // A_re b0_re (+ A_re1 b0_re)
+              umma::tmem_ld8(d1 + kTtCols + cg, x[1]);         // A_re b0_im
+              umma::tmem_ld8(d1 + 2 * kTtCols + cg, x[2]);     // A_re0 b1_re
+              umma::tmem_ld8(d1 + 3 * kTtCols + cg, x[3]);     // A_re0 b1_im
+              umma::tmem_ld8(d2 + cg, x[4]);                   // A_im b0_re
+              umma::tmem_ld8(d2 + kTtCols + cg, x[5]);
+              umma::tmem_ld8(d2 + 2 * kTtCols + cg, x[6]);
+              umma::tmem_ld8(d2 + 3 * kTtCols + cg, x[7]);
+              umma::tmem_wait_ld();
+#pragma unroll
+              for (int i = 0; i < 8; ++i) {
+                const float p_re = x[0][i] + x[2][i], p_im = x[1][i] + x[3][i];
+                const float q_re = x[4][i] + x[6][i], q_im = x[5][i] + x[7][i];
+                out[cg + i] = make_float2(p_re - q_im, p_im + q_re);
+              }
+            }
+          }
+          umma::fence_before_sync();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&acce[q]);
+          ++mi;
+        }
+        if (dout >= 0 && lp >= 0 && !aborted()) {
+          float2 *slot = gtr + (long long)lp * slot_stride + dst_off;
+#pragma unroll
+          for (int c = 0; c < kTtCols; ++c) {
+            if (c < u.ncol) {
+              const int col = __ldg(ucols + u.col0 + c);
+              const int X = col % g.nsub, rhs = col - X;   // rhs * nsub
+              const int Y = sub_neighbour(g, X, dout);
+              if (Y >= 0) {
+                float2 val = out[c];
+                if (u.raw) {
+                  const float2 w = __ldg(rawf + (long long)col * g.T + R);
+                  val = make_float2(val.x + w.x, val.y + w.y);
+                }
+                red_add_f2(slot + (long long)(rhs + Y) * g.T, val);
+              }
+            }
+          }
+        }
+      }
+      // level v done on this CTA: publish (every CTA arrives, with or without units)
+      named_sync(1, 128);
+      if (tid == 0) {
+        __threadfence();
+        atomicAdd(cnt + v * kStepCounters + (b % kStepCounters), 1u);
+      }
+    }
+  }
+  umma::fence_before_sync();
+  __syncthreads();
+  if (warp == 9) {
+    umma::fence_after_sync();
+    umma::tmem_dealloc(tmem, kTtTmemCols);
+  }
+}
+
+cudaError_t launch_trace_tc(cudaStream_t st, const Geom &g, int kind, const int4 *units,
+                            const int *ucols, int nunits, const int *lev_off, int nlevels,
+                            const unsigned char *tiles, const int *route, float2 *gtr,
+                            const float2 *rawf, int nrhs, unsigned *gbar, int *err) {
+  if (nunits <= 0 || nlevels <= 0) return cudaSuccess;
+  TtShape t;
+  if (!tt_shape(g, kind, &t)) return cudaErrorInvalidValue;
+  static bool done0[64] = {false}, done1[64] = {false};
+  cudaError_t e = kind == 0 ? smem_limit_once(k_trace_tc<0>, done0)
+                            : smem_limit_once(k_trace_tc<1>, done1);
+  if (e != cudaSuccess) return e;
+  int dev = 0, nsm = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  e = kind == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_tc<0>, kTtThreads, t.smem)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_tc<1>, kTtThreads, t.smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  e = cudaMemsetAsync(gbar, 0, (size_t)nlevels * kStepCounters * sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)nsm);   // one CTA per SM: it owns the whole tensor memory
+  cfg.blockDim = dim3(kTtThreads);
+  cfg.dynamicSmemBytes = t.smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (kind == 0)
+    return cudaLaunchKernelEx(&cfg, k_trace_tc<0>, g, t, units, ucols, lev_off, nlevels, tiles,
+                              route, gtr, rawf, nrhs, gbar, err);
+  return cudaLaunchKernelEx(&cfg, k_trace_tc<1>, g, t, units, ucols, lev_off, nlevels, tiles,
+                            route, gtr, rawf, nrhs, gbar, err);
+}
+
+}  // namespace dds

@@ -26,7 +26,8 @@ EXPORTS = ["dds_setup", "dds_sweep", "dds_sweep_strip", "dds_solve", "dds_apply"
            "dds_set_stream", "dds_get_info", "dds_kernel_launches", "dds_last_error",
            "dds_destroy", "dds_profile", "dds_profile_read", "dds_local_solve_noalloc",
            "dds_server_create", "dds_server_submit", "dds_server_step", "dds_server_poll",
-           "dds_server_destroy", "dds_work_per_ddm", "dds_autotune"]
+           "dds_server_destroy", "dds_work_per_ddm", "dds_autotune", "dds_set_zero_skip",
+           "dds_local_solve_counts"]
 KERNEL_KINDS = {"assemble": 0, "subst": 1, "extract": 2, "trace_step": 3, "krylov": 4,
                 "other": 5}
 
@@ -48,7 +49,8 @@ class _Problem(ctypes.Structure):
 class _Info(ctypes.Structure):
     _fields_ = [("G", ctypes.c_int * 3), ("M", ctypes.c_int * 3), ("n_sub", ctypes.c_int),
                 ("n_factors", ctypes.c_int), ("trace_len", ctypes.c_int), ("plan", ctypes.c_int),
-                ("factor_bytes", ctypes.c_longlong), ("setup_seconds", ctypes.c_double)]
+                ("factor_bytes", ctypes.c_longlong), ("setup_seconds", ctypes.c_double),
+                ("trace_kernel", ctypes.c_int), ("subst_kernel", ctypes.c_int)]
 
 
 _lib = None
@@ -95,12 +97,16 @@ def load(path: str = LIB_PATH):
     lib.dds_server_destroy.argtypes = [vp]
     lib.dds_server_destroy.restype = None
     lib.dds_profile.argtypes = [vp, ctypes.c_int]
+    lib.dds_set_zero_skip.argtypes = [vp, ctypes.c_int]
+    lib.dds_local_solve_counts.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong),
+                                           ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
     lib.dds_profile_read.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
                                      ctypes.POINTER(ctypes.c_double)]
     for name in ["dds_setup", "dds_sweep", "dds_sweep_strip", "dds_solve", "dds_apply", "dds_local_solve",
                  "dds_set_stream", "dds_get_info", "dds_profile", "dds_profile_read",
                  "dds_local_solve_noalloc", "dds_server_create", "dds_server_submit",
-                 "dds_server_step", "dds_server_poll"]:
+                 "dds_server_step", "dds_server_poll", "dds_set_zero_skip",
+                 "dds_local_solve_counts"]:
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -303,14 +309,16 @@ class Context:
         self._check(self._lib.dds_get_info(self._h, ctypes.byref(inf)))
         return {"G": list(inf.G), "M": list(inf.M), "n_sub": inf.n_sub,
                 "n_factors": inf.n_factors, "trace_len": inf.trace_len, "plan": inf.plan,
-                "factor_bytes": inf.factor_bytes, "setup_seconds": inf.setup_seconds}
+                "factor_bytes": inf.factor_bytes, "setup_seconds": inf.setup_seconds,
+                "trace_kernel": inf.trace_kernel, "subst_kernel": inf.subst_kernel}
 
     def launches(self):
         return int(self._lib.dds_kernel_launches(self._h))
 
     def autotune(self, nrhs, rounds=1):
         """Time the tunable launch shapes (dds_autotune) and keep the fastest; returns
-        {"panel_width", "trace_ctas_per_sm", "table": [(width, ctas, ms per DDM application)]}."""
+        {"panel_width", "trace_ctas_per_sm", "table": [(width, ctas, ms per DDM application)]};
+        trace_ctas_per_sm = 0 is the tensor-core trace kernel."""
         n = ctypes.c_int(0)
         table = (ctypes.c_double * (3 * 16))()
         best = (ctypes.c_int * 2)()
@@ -341,6 +349,19 @@ class Context:
             self._check(self._lib.dds_profile_read(self._h, k, ctypes.byref(n), ctypes.byref(ms)))
             out[name] = (int(n.value), float(ms.value))
         return out
+
+    def set_zero_skip(self, enable=True):
+        """Zero-work skipping of local problems with a zero right-hand side (dds_set_zero_skip)."""
+        self._check(self._lib.dds_set_zero_skip(self._h, 1 if enable else 0))
+
+    def local_solve_counts(self, reset=False):
+        """(local problems solved, local problems assembled) in compacted substitution launches
+        since set-up or the last reset (dds_local_solve_counts)."""
+        a = ctypes.c_longlong(0)
+        b = ctypes.c_longlong(0)
+        self._check(self._lib.dds_local_solve_counts(self._h, ctypes.byref(a), ctypes.byref(b),
+                                                     1 if reset else 0))
+        return int(a.value), int(b.value)
 
     def set_stream(self, stream_handle):
         self._check(self._lib.dds_set_stream(self._h, ctypes.c_void_p(stream_handle)))

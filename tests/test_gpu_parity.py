@@ -146,6 +146,24 @@ def test_ddm_mixed_matches_oracle(plan, precision):
 
 
 @pytest.mark.parametrize("precision", ["mixed", "mixed_bf16"])
+@pytest.mark.parametrize("case", [DDM_CASES[1], DDM_CASES[2], DDM_CASES[5], DDM_CASES[6]],
+                         ids=lambda c: "x".join(map(str, c[0])) + f"-{c[1]}-r{c[6]}")
+def test_tensor_core_trace_solves_match_oracle(case, precision):
+    """The trace solves of the trace plan on the tensor cores (k_trace_tc: the map as 128-row
+    tiles of split pieces, 32-column tiles of (subdomain, RHS), FP32 accumulation in TMEM) on
+    ragged geometry: sides of 60 and 64 inputs (padded to 16), 2D and 3D, two rounds, a halo;
+    the raw DDM against the oracle's DDM."""
+    n, parts, P, kappa, med, centres, rounds, H = case
+    prob, f = _case(n, parts, P, kappa, c=_medium(med, n), centres=centres, H=H)
+    b = rhs_from_source(prob, extend_interior(prob, f))
+    ref = ddm_solve(prob, b, rounds)
+    ctx = _ctx(prob, precision, "trace")
+    got = ctx.sweep(_on_dev(ctx.extend(f)), rounds).cpu().numpy()
+    for r in range(len(centres)):
+        assert _rel(got[r], ref[r]) < SINGLE_TOL[precision], r
+
+
+@pytest.mark.parametrize("precision", ["mixed", "mixed_bf16"])
 @pytest.mark.parametrize("nrhs", [20, 40])
 def test_tensor_core_wide_panels_match_oracle(nrhs, precision):
     """64 subdomains x 20 (40) right-hand sides put 1280 (2560) columns into one substitution
@@ -223,6 +241,58 @@ def test_strip_sweeps_reject_a_checkerboard():
     ctx = _ctx(prob)
     with pytest.raises(dds.DDSError):
         ctx.sweep_strip(_on_dev(ctx.extend(f)), 3)
+
+
+ZERO_SKIP_CASES = [
+    # (n, parts, P, centres, plan): sources that leave most own-source solves zero
+    ((128, 128), (8, 8), 4, [(0.2, 0.3), (0.7, 0.6), (0.5, 0.85)], "trace"),
+    ((128, 128), (8, 8), 4, [(0.2, 0.3), (0.7, 0.6), (0.5, 0.85)], "direct"),
+    ((240, 240), (2, 2), 8, [(0.3, 0.3)], "direct"),                   # 136-node lines
+    ((24, 24, 24), (2, 2, 2), 4, [(0.3, 0.3, 0.3)], "direct"),         # 400-node planes
+]
+
+
+@pytest.mark.parametrize("case", ZERO_SKIP_CASES,
+                         ids=lambda c: "x".join(map(str, c[1])) + "-" + c[4] + f"-{c[0][0]}")
+def test_zero_work_skipping_drops_zero_solves_and_keeps_the_field(case):
+    """Algorithm 2.1's 'if f_ij != 0 solve, else u_ij = 0': with skipping on, the local problems
+    whose assembled right-hand side is zero are not solved (fewer solves counted), and the field
+    is bit-identical in FP64 to the one with skipping off (direct plan; the trace plan's atomic
+    slot accumulation has no fixed order, so there to rounding); the mixed path agrees with its
+    unskipped self to single-precision rounding and with the oracle's DDM (which skips the same
+    solves)."""
+    n, parts, P, centres, plan = case
+    prob, f = _case(n, parts, P, 2 * np.pi * 4, c=_medium("layer", n), centres=centres)
+    b = rhs_from_source(prob, extend_interior(prob, f))
+    record = []
+    ref = ddm_solve(prob, b, 1, record=record)
+    oracle_solved = sum(1 for rec in record if rec["solved"])
+    for precision in ("fp64", "mixed"):
+        ctx = _ctx(prob, precision, plan)
+        fe = _on_dev(ctx.extend(f))
+        ctx.local_solve_counts(reset=True)
+        on = ctx.sweep(fe).cpu().numpy()
+        solved, assembled = ctx.local_solve_counts(reset=True)
+        ctx.set_zero_skip(False)
+        off = ctx.sweep(fe).cpu().numpy()
+        assert ctx.local_solve_counts() == (0, 0)
+        assert 0 < solved < assembled, (solved, assembled)
+        if precision == "fp64" and plan == "trace":
+            # the trace slots are accumulated with atomics in no fixed order: rounding only
+            for r in range(len(centres)):
+                assert _rel(on[r], off[r]) < 1e-13
+        elif precision == "fp64":
+            assert np.array_equal(on, off)
+            if len(centres) == 1:
+                # one assembled local problem per (sweep, subdomain): the skipped ones are
+                # exactly those the oracle finds zero
+                assert assembled == len(record) and solved == oracle_solved, \
+                    (assembled, len(record), solved, oracle_solved)
+        else:
+            for r in range(len(centres)):
+                assert _rel(on[r], off[r]) < 1e-6
+        for r in range(len(centres)):
+            assert _rel(on[r], ref[r]) < (1e-10 if precision == "fp64" else SINGLE_TOL["mixed"])
 
 
 def test_ddm_host_buffers_equal_device_buffers():
@@ -344,7 +414,8 @@ def test_autotune_picks_a_valid_shape_and_keeps_results():
     fe = _on_dev(ctx.extend(f))
     before = ctx.sweep(fe, 2).cpu().numpy()
     t = ctx.autotune(3, 2)
-    assert t["panel_width"] in (8, 16, 32) and t["trace_ctas_per_sm"] in (1, 2)
+    assert t["panel_width"] in (8, 16, 32) and t["trace_ctas_per_sm"] in (0, 1, 2)
+    assert {row[1] for row in t["table"]} == {0, 1, 2}   # CUDA-core 1/SM, 2/SM, tensor cores
     assert len(t["table"]) >= 2 and all(row[2] > 0 for row in t["table"])
     after = ctx.sweep(fe, 2).cpu().numpy()
     for r in range(3):
