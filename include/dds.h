@@ -93,6 +93,7 @@ typedef struct {
   int plan;               /* plan in use                                                      */
   long long factor_bytes; /* device bytes held by factors (+ trace maps)                      */
   double setup_seconds;   /* wall time of dds_setup                                           */
+  long long device_bytes; /* device memory the context holds now (dds_set_memory_budget)       */
   int trace_kernel;       /* trace solves: 0 = tensor cores (k_trace_tc), 1 / 2 = CUDA cores   */
                           /* with that many CTAs per SM (k_trace_sweeps), -1 = direct plan     */
   int subst_kernel;       /* substitutions: 0 = FP64 CUDA cores, 1 = FP32 CUDA cores,          */
@@ -112,7 +113,11 @@ dds_status dds_setup(const dds_problem *prob, dds_ctx **out);
  * dds_sweep -- the DDM as a direct solver: `rounds` rounds of the 2^n diagonal sweeps of
  * Algorithm 2.1 / 4.1 on the sources f (nrhs fields on the global extended grid), writing
  * u_DDM (Algorithm 2.1, last line) to u.  rounds >= 1 (Theorem 3.10 needs 2 in two-layer
- * media). */
+ * media).
+ *
+ * Right-hand sides are independent: one whose source holds a NaN or infinite entry gets a NaN
+ * field (dds_sweep, dds_sweep_strip) or a NaN field and relative residual (dds_solve, which then
+ * returns DDS_ENOCONV); the other right-hand sides of the batch are computed as without it. */
 dds_status dds_sweep(dds_ctx *ctx, const void *f, int nrhs, void *u, int rounds);
 
 /* dds_sweep_strip -- the one-dimensional sweeping DDM of Section 3.2 on a strip partition
@@ -203,16 +208,17 @@ long long dds_kernel_launches(const dds_ctx *ctx);
 
 /* dds_autotune -- time the tunable launch shapes of one DDM application on this context's
  * geometry for nrhs right-hand sides and `rounds` rounds, and keep the fastest:
- *   the tensor-core substitution panel width (8, 16 or 32 columns per CTA or CTA pair;
+ *   the tensor-core substitution panel width (8, 16 or 32 columns) and panels per CTA or CTA
+ *   pair (1, or 2 for widths up to 16: one panel's epilogue runs under the other's MMAs;
  *   mixed modes with tensor-core substitutions), and the trace-solve kernel of the trace plan:
  *   the CUDA-core cooperative launch with 1 or 2 CTAs per SM, or (0) the tensor-core launch
  *   (split products of the context's piece type; mixed modes with tensor-core pieces).
  * Each candidate is captured once and then timed over three DDM applications with CUDA events
  * on the context's stream, with synthetic nonzero right-hand sides in scratch the call allocates
- * and frees.  table (row-major [n][3]: panel width (0 = automatic), trace kernel (CTAs per SM
- * of the CUDA-core launch, 0 = tensor cores), ms per DDM application) receives at most
- * max_entries rows; *n_entries is the number of candidates timed; best[0], best[1] the chosen
- * panel width and trace kernel.  Cached plans and graphs are dropped.
+ * and frees.  table (row-major [n][4]: panel width (0 = automatic), panels per CTA, trace
+ * kernel (CTAs per SM of the CUDA-core launch, 0 = tensor cores), ms per DDM application)
+ * receives at most max_entries rows; *n_entries is the number of candidates timed; best[0],
+ * best[1], best[2] (three ints) the chosen panel width, trace kernel and panels per CTA.  Cached plans and graphs are dropped.
  * Not part of the paper: it picks block and panel tile shapes by measurement. */
 dds_status dds_autotune(dds_ctx *ctx, int nrhs, int rounds, int max_entries, int *n_entries,
                         double *table, int *best);
@@ -227,6 +233,22 @@ dds_status dds_autotune(dds_ctx *ctx, int nrhs, int rounds, int max_entries, int
  * Used to turn kernel times into achieved rates.  DDS_EINVAL on bad arguments. */
 dds_status dds_work_per_ddm(dds_ctx *ctx, int nrhs, int rounds, double *subst_flops,
                             double *trace_flops);
+
+/* dds_set_memory_budget -- cap the device memory this context may hold: its factors and trace
+ * maps, work buffers, launch tables, staging buffers and the slots of its servers.  A call whose
+ * allocations would take the total above `bytes` returns DDS_ENOMEM (with the sizes in
+ * dds_last_error) and leaves the context usable for smaller calls; buffers already held stay.
+ * 0 removes the cap.  *in_use (may be NULL) receives the bytes held now.  A real cudaMalloc
+ * failure returns DDS_ENOMEM the same way.  Not part of the paper: admission control for a
+ * device shared by several contexts or servers. */
+dds_status dds_set_memory_budget(dds_ctx *ctx, long long bytes, long long *in_use);
+
+/* dds_set_wait_limit -- polls a level-completion wait of the cooperative trace launches makes
+ * before it gives up (the launch then ends with wrong results and the call returns
+ * DDS_ETIMEOUT); 0 restores the default (2^20 polls, about 0.1 s).  A diagnostic control: a
+ * small limit makes those waits run out on purpose (no GPU fault, the context stays usable),
+ * which is how the timeout path is tested.  Drops cached CUDA graphs. */
+dds_status dds_set_wait_limit(dds_ctx *ctx, long long polls);
 
 /* dds_set_zero_skip -- zero-work skipping (Algorithm 2.1: a subdomain whose assembled right-hand
  * side f_ij is zero is not solved, u_ij = 0).  On (enable = 1, the default), after each batched

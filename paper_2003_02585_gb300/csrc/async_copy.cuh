@@ -80,6 +80,10 @@ __device__ inline void cp_async16(void *dst, const void *src, uint32_t src_bytes
 }
 __device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ inline void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+// wait until at most N of this thread's committed cp.async groups are still pending
+template <int N> __device__ inline void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 // ---- reductions into global memory without a returned value (fire and forget)
 __device__ inline void red_add_f4(float4 *p, float4 v) {

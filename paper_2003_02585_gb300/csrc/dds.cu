@@ -17,6 +17,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/dds.h"
 #include "dds_internal.cuh"
 
@@ -25,28 +27,58 @@ using cd = std::complex<double>;
 
 namespace {
 
+// Device bytes held on behalf of one context and its cap (0 = none).  Allocations made while a
+// context's call runs (inside its Busy guard, or its set-up) count against that context.
+struct MemAcct {
+  size_t used = 0, budget = 0;
+};
+thread_local MemAcct *tl_acct = nullptr;
+
 struct DBuf {
   void *p = nullptr;
   size_t n = 0;
+  MemAcct *acct = nullptr;   // the context charged for these bytes
   DBuf() = default;
   DBuf(const DBuf &) = delete;
   DBuf &operator=(const DBuf &) = delete;
   ~DBuf() { release(); }
   void release() {
-    if (p) cudaFree(p);
+    if (p) {
+      cudaFree(p);
+      if (acct) acct->used -= n;
+    }
     p = nullptr;
     n = 0;
+    acct = nullptr;
   }
   cudaError_t ensure(size_t bytes) {
     if (bytes <= n && p) return cudaSuccess;
     release();
     if (bytes == 0) bytes = 16;
+    MemAcct *a = tl_acct;
+    if (a && a->budget && a->used + bytes > a->budget) return cudaErrorMemoryAllocation;
     cudaError_t e = cudaMalloc(&p, bytes);
-    if (e == cudaSuccess) n = bytes;
-    else p = nullptr;
+    if (e == cudaSuccess) {
+      n = bytes;
+      acct = a;
+      if (a) a->used += bytes;
+    } else {
+      p = nullptr;
+      cudaGetLastError();   // a failed allocation must not surface at a later launch check
+    }
     return e;
   }
   template <class T> T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+// NVTX range over a scope (host side): the API calls, each DDM application, each FGMRES
+// iteration and, outside graph capture, each sweep step, so that a timeline tool shows the
+// method's structure.  Without a tool attached the calls do nothing.
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
 };
 
 struct StepPlan {            // launch lists of one (direction, step) or one phase
@@ -72,8 +104,9 @@ struct CallPlan {            // all launch lists for one nrhs
   struct TraceTable {
     int n = -1, nlev = 0;
     DBuf buf, cols, levs;            // k_trace_sweeps: items, their columns, level offsets
-    int tn = -1, tnlev = 0;
+    int tn = -1, tnlev = 0, tslots = 0;
     DBuf tunits, tcols, tlevs;       // k_trace_tc: units, their columns, level offsets
+    DBuf tneed, tready;              // k_trace_tc: publications expected / made per slot
   };
   std::map<int, TraceTable> trace_steps;   // rounds -> item lists of the cooperative launch
 };
@@ -81,6 +114,7 @@ struct CallPlan {            // all launch lists for one nrhs
 }  // namespace
 
 struct dds_ctx {
+  MemAcct acct;   // first member: destroyed after every buffer that reports to it
   std::mutex mu;
   std::string err;
   Geom g{};
@@ -89,6 +123,7 @@ struct dds_ctx {
   int split = -1;        // tensor-core substitution pieces: 0 = TF32, 1 = BF16, -1 = none
   int tc_m = 0;          // middle block of the two-sided tensor-core chain (0: one-sided)
   int tune_pc = 0;       // tensor-core panel width chosen by dds_autotune (0: automatic)
+  int tune_np = 1;       // tensor-core panels per CTA (or CTA pair) chosen by dds_autotune
   int trace_per_sm = 2;  // CTAs per SM of the cooperative trace launch
   double h = 0, omega = 0, S = 0;
   int P = 0, power = 2, H = 0;
@@ -110,7 +145,9 @@ struct dds_ctx {
   DBuf errflag;  // set by kernels whose bounded waits gave up
   DBuf gbar;     // step counters of the cooperative trace-sweep launch
   DBuf nzflag;   // per work slot: the assembled right-hand side has a nonzero entry
+  DBuf badrhs;   // per RHS of a DDM application: its source has a NaN or infinite entry
   bool zero_skip = true;   // drop the substitutions of zero right-hand sides (Algorithm 2.1)
+  unsigned wait_limit = 1u << 20;   // polls of a level-completion wait before it gives up
   DBuf solve_stats;        // [0] local solves run, [1] local solves assembled (u64)
   DBuf an_glob[3], iah_glob[3];
   DBuf stc0, stcp[3];  // global stencil (centre, coupling to +e_a)
@@ -166,7 +203,7 @@ namespace {
     cudaError_t e_ = (call);                                                     \
     if (e_ != cudaSuccess) {                                                     \
       ctx->err = std::string(#call) + ": " + cudaGetErrorString(e_);             \
-      return DDS_ECUDA;                                                          \
+      return e_ == cudaErrorMemoryAllocation ? DDS_ENOMEM : DDS_ECUDA;           \
     }                                                                            \
   } while (0)
 
@@ -505,10 +542,12 @@ cudaError_t subst_any(dds_ctx *ctx, int npan, const Panel *pans, const Col *cols
                               ctx->bigacc.as<float2>(), ctx->bigB.as<unsigned char>(),
                               ctx->errflag.as<int>(), &ctx->launches);
     }
-    if (ctx->split >= 0 && subst_tc_ok(ctx->g, ctx->split, pc, ctx->tc_m > 0))
+    if (ctx->split >= 0 && subst_tc_ok(ctx->g, ctx->split, pc, ctx->tc_m > 0)) {
+      const int np = subst_tc_ok(ctx->g, ctx->split, pc, ctx->tc_m > 0, ctx->tune_np) ? ctx->tune_np : 1;
       return launch_subst_tc(ctx->stream, ctx->g, ctx->split, npan, pans, cols,
                              ctx->tctiles.as<unsigned char>(), cpl, work, pc,
-                             ctx->errflag.as<int>(), ctx->tc_m, nz);
+                             ctx->errflag.as<int>(), ctx->tc_m, nz, np);
+    }
     if (subst_stream_ok(ctx->g, pc))
       return launch_subst_stream(ctx->stream, ctx->g, npan, pans, cols, sinv, cpl, work, pc,
                                  ctx->errflag.as<int>());
@@ -622,9 +661,11 @@ int build_trace_schedule(dds_ctx *ctx, int nrhs, int rounds, std::vector<TraceIt
 // output rows that holds a routed side with a neighbour of some column.  The unit multiplies the
 // inputs of the sides that receive in this sweep and have a neighbour of some column (kmask);
 // in the first sweep it also adds the raw own-source lines (a unit without inputs then only does
-// that).  Returns the number of levels.
+// that).  need[] receives, per slot, the publications its trace solve waits for.  Returns the
+// number of levels.
 int build_tc_trace_schedule(dds_ctx *ctx, int nrhs, int rounds, std::vector<int4> &units,
-                            std::vector<int> &ucols, std::vector<int> &lev_off) {
+                            std::vector<int> &ucols, std::vector<int> &lev_off,
+                            std::vector<unsigned> &need) {
   const Geom &g = ctx->g;
   const int L = (int)sweep_program(g, rounds).size(), ns = g.nsub;
   const std::vector<int> route = build_route(g, rounds);
@@ -632,6 +673,22 @@ int build_tc_trace_schedule(dds_ctx *ctx, int nrhs, int rounds, std::vector<int4
   const std::vector<int> depth = trace_depths(ctx, rounds, &nlev);
   constexpr int kCols = 32;
   const int RT = (g.T + 127) / 128;
+  need.assign((size_t)L * ns, 0u);
+  // the publications a unit makes (k_trace_tc's epilogue counts the same): per subdomain of its
+  // tile and per side whose rows lie in its row tile, routed and with a neighbour
+  auto publish = [&](int l, int rt, const std::vector<int> &tile) {
+    int prevX = -1;
+    for (int col : tile) {
+      const int X = col % ns;
+      if (X == prevX) continue;
+      prevX = X;
+      for (int d = 0; d < g.nsides; ++d) {
+        if (g.toff[d] >= 128 * (rt + 1) || g.toff[d] + 2 * g.Lt[d] <= 128 * rt) continue;
+        const int lq = route[l * 6 + d], Y = sub_neighbour(g, X, d);
+        if (lq >= 0 && Y >= 0) ++need[(size_t)lq * ns + Y];
+      }
+    }
+  };
   for (int v = 0; v < nlev; ++v) {
     lev_off.push_back((int)units.size());
     for (int l = 0; l < L; ++l) {
@@ -664,8 +721,11 @@ int build_tc_trace_schedule(dds_ctx *ctx, int nrhs, int rounds, std::vector<int4
                   g.toff[d] + 2 * g.Lt[d] > 128 * rt)
                 need = true;
             if (!need) continue;
+            // one unit multiplies the inputs of every received side into one accumulator, so
+            // each output is added into its receiver once
             units.push_back(make_int4(fac | ((int)tile.size() << 24), l | (rt << 16), col0,
                                       kmask | (raw << 8)));
+            publish(l, rt, tile);
           }
         }
         tile.clear();
@@ -741,14 +801,15 @@ dds_status prepare_ddm(dds_ctx *ctx, int nrhs, int rounds, bool *grown) {
     if (ctx->trace_tc && tt.tn < 0) {
       std::vector<int4> units;
       std::vector<int> ucols, lev;
-      tt.tnlev = build_tc_trace_schedule(ctx, nrhs, rounds, units, ucols, lev);
+      std::vector<unsigned> need;
+      tt.tnlev = build_tc_trace_schedule(ctx, nrhs, rounds, units, ucols, lev, need);
       CK(upload(tt.tunits, units, ctx->stream));
       CK(upload(tt.tcols, ucols, ctx->stream));
       CK(upload(tt.tlevs, lev, ctx->stream));
+      CK(upload(tt.tneed, need, ctx->stream));
+      CK(tt.tready.ensure(need.size() * sizeof(unsigned)));
+      tt.tslots = (int)need.size();
       tt.tn = (int)units.size();
-      void *gb0 = ctx->gbar.p;
-      CK(ctx->gbar.ensure(trace_counter_bytes(std::max(std::max(tt.nlev, tt.tnlev), 1))));
-      if (gb0 != ctx->gbar.p) *grown = true;
     }
   }
   if (ctx->big_tc && ctx->single) {
@@ -770,6 +831,9 @@ dds_status prepare_ddm(dds_ctx *ctx, int nrhs, int rounds, bool *grown) {
   }
   void *w0 = ctx->work.p, *g0 = ctx->gtr.p, *r0 = ctx->rawf.p, *z0 = ctx->nzflag.p;
   CK(ctx->nzflag.ensure(work_cols * sizeof(int)));
+  void *bad0 = ctx->badrhs.p;
+  CK(ctx->badrhs.ensure((size_t)nrhs * sizeof(int)));
+  *grown = *grown || bad0 != ctx->badrhs.p;
   *grown = *grown || z0 != ctx->nzflag.p;
   CK(ctx->work.ensure(work_cols * g.Nloc * sizeof(C)));
   CK(ctx->gtr.ensure(L * slot * sizeof(C)));
@@ -797,6 +861,8 @@ dds_status run_ddm(dds_ctx *ctx, const double2 *b, int nrhs, double2 *u, int rou
   C *gtr = ctx->gtr.as<C>();
   const Col *cols = cp->cols.as<Col>();
   int *nzf = ctx->nzflag.as<int>();   // per work slot: nonzero right-hand side
+  int *badf = ctx->badrhs.as<int>();  // per RHS: non-finite source entry
+  CK(cudaMemsetAsync(badf, 0, (size_t)nrhs * sizeof(int), st));
   const Panel *pans = cp->panels.as<Panel>();
   const int *route = ctx->route_dev.as<int>();
   // the panels of one substitution launch: with zero-work skipping, the columns whose assembled
@@ -813,17 +879,24 @@ dds_status run_ddm(dds_ctx *ctx, const double2 *b, int nrhs, double2 *u, int rou
   const Col *scols = zs ? dcols : cols;
   if (!trace_plan) {
     CK(cudaMemsetAsync(u, 0, (size_t)nrhs * g.Nglob * sizeof(double2), st));
+    // not while a graph is captured (capture runs on gstream)
+    const bool annotate = !(ctx->gstream && ctx->stream == ctx->gstream);
     for (int l = 0; l < L; ++l) {
       const int dir = seq[l];
       for (int s = 0; s < ctx->nsteps; ++s) {
         const StepPlan &sp = cp->steps[dir * ctx->nsteps + s];
         if (sp.ncols == 0) continue;
+        char label[48];
+        if (annotate) std::snprintf(label, sizeof label, "sweep %d step %d", l + 1, s + 1);
+        if (annotate) nvtxRangePushA(label);
         LAUNCHK(DDS_K_ASSEMBLE, launch_assemble<R>(st, g, ctx->tb, sp.ncols, cols + sp.col_off, work, b, nullptr,
-                                  l == 0, gtr + l * slot, (long long)g.nsub * g.T, g.T, 1, 0, nzf));
+                                  l == 0, gtr + l * slot, (long long)g.nsub * g.T, g.T, 1, 0, nzf,
+                                  l == 0 ? badf : nullptr));
         if (zs) LAUNCH(skip(sp));
         LAUNCHK(DDS_K_SUBST, subst_any<R>(ctx, sp.npanels, spans + sp.pan_off, scols, sinv, cpl, work, sp.pc, nzf));
         LAUNCHK(DDS_K_EXTRACT, launch_extract<R>(st, g, sp.ncols, cols + sp.col_off, work, u, 1, nullptr, gtr,
                                  route, l, nrhs));
+        if (annotate) nvtxRangePop();
       }
     }
   } else {
@@ -831,7 +904,7 @@ dds_status run_ddm(dds_ctx *ctx, const double2 *b, int nrhs, double2 *u, int rou
     const StepPlan &all = cp->all;
     // own sources: x_f = A_R^{-1} b_own; keep its raw trace lines
     LAUNCHK(DDS_K_ASSEMBLE, launch_assemble<R>(st, g, ctx->tb, all.ncols, cols + all.col_off, work, b, nullptr, 1,
-                              (const C *)nullptr, 0, 0, 1, 0, nzf));
+                              (const C *)nullptr, 0, 0, 1, 0, nzf, badf));
     if (zs) LAUNCH(skip(all));
     LAUNCHK(DDS_K_SUBST, subst_any<R>(ctx, all.npanels, spans + all.pan_off, scols, sinv, cpl, work, all.pc, nzf));
     LAUNCHK(DDS_K_EXTRACT, launch_extract<R>(st, g, all.ncols, cols + all.col_off, work, u, 0, rawf,
@@ -854,14 +927,16 @@ dds_status run_ddm(dds_ctx *ctx, const double2 *b, int nrhs, double2 *u, int rou
                 launch_trace_tc(st, g, ctx->split, tt.tunits.as<int4>(), tt.tcols.as<int>(), tt.tn,
                                 tt.tlevs.as<int>(), tt.tnlev, ctx->tttiles.as<unsigned char>(),
                                 route, (float2 *)gtr, (const float2 *)rawf, nrhs,
-                                ctx->gbar.as<unsigned>(), ctx->errflag.as<int>()));
+                                tt.tready.as<unsigned>(), tt.tneed.as<unsigned>(), tt.tslots,
+                                ctx->errflag.as<int>(), ctx->wait_limit));
       }
     }
     if (!(sizeof(R) == 4 && ctx->trace_tc))
       LAUNCHK(DDS_K_TRACE_STEP, launch_trace_sweeps<R>(st, g, tt.buf.as<int4>(), tt.cols.as<int2>(),
                                                        tt.n, tt.levs.as<int>(), tt.nlev, gmap, gtr,
                                                        rawf, nrhs, ctx->gbar.as<unsigned>(),
-                                                       ctx->errflag.as<int>(), ctx->trace_per_sm));
+                                                       ctx->errflag.as<int>(), ctx->trace_per_sm,
+                                                       ctx->wait_limit));
     // own nodes: u = A_R^{-1}(b_own + potentials of all traces received in every sweep)
     LAUNCHK(DDS_K_ASSEMBLE, launch_assemble<R>(st, g, ctx->tb, all.ncols, cols + all.col_off, work, b, nullptr, 1,
                               gtr, (long long)g.nsub * g.T, g.T, L, slot, nzf));
@@ -882,10 +957,15 @@ dds_status enqueue_ddm(dds_ctx *ctx, const double2 *b, int nrhs, double2 *u, int
 // captured once into a CUDA graph per (b, u, nrhs, rounds) and replayed on an internal stream
 // ordered after and before the caller's stream by events.
 dds_status ddm(dds_ctx *ctx, const double2 *b, int nrhs, double2 *u, int rounds) {
+  NvtxRange range("DDM application");
   bool grown = false;
   dds_status r = ctx->single ? prepare_ddm<float>(ctx, nrhs, rounds, &grown)
                                              : prepare_ddm<double>(ctx, nrhs, rounds, &grown);
-  if (r != DDS_OK) return r;
+  if (r != DDS_OK) {
+    // a failed allocation may have released a buffer that cached graphs still name
+    ctx->clear_graphs();
+    return r;
+  }
   if (grown) ctx->clear_graphs();
   if (!ctx->use_graphs || ctx->profiling) {
     r = enqueue_ddm(ctx, b, nrhs, u, rounds);
@@ -1353,8 +1433,16 @@ dds_status finish_out(dds_ctx *ctx, void *ptr, size_t bytes, bool host) {
 struct Busy {
   dds_ctx *c;
   bool ok;
-  explicit Busy(dds_ctx *cc) : c(cc), ok(cc->mu.try_lock()) {}
-  ~Busy() { if (ok) c->mu.unlock(); }
+  MemAcct *prev;
+  explicit Busy(dds_ctx *cc) : c(cc), ok(cc->mu.try_lock()), prev(tl_acct) {
+    if (ok) tl_acct = &cc->acct;   // this call's allocations count against its context
+  }
+  ~Busy() {
+    if (ok) {
+      tl_acct = prev;
+      c->mu.unlock();
+    }
+  }
 };
 
 // ------------------------------------------------------------------------------------------
@@ -1400,6 +1488,10 @@ dds_status fgmres(dds_ctx *ctx, const double2 *f, int nrhs, double2 *x, double t
   CK(cudaStreamSynchronize(st));
   std::vector<double> beta(nrhs);
   for (int r = 0; r < nrhs; ++r) beta[r] = std::sqrt(std::max(hh[r].x, 0.0));
+  // a right-hand side with a NaN or infinite entry has a non-finite norm: it is not iterated,
+  // its field is set to NaN and its relative residual reported as NaN (the others go on)
+  std::vector<char> bad(nrhs, 0);
+  for (int r = 0; r < nrhs; ++r) bad[r] = !std::isfinite(hh[r].x);
   std::vector<double> sc((size_t)nrhs * (maxit + 1), 0.0);   // s_i per RHS
   for (int r = 0; r < nrhs; ++r) sc[(size_t)r * (maxit + 1)] = beta[r];
   auto inv2 = [](double v) {   // 1 / v^2, 0 for a vanished vector
@@ -1414,11 +1506,14 @@ dds_status fgmres(dds_ctx *ctx, const double2 *f, int nrhs, double2 *x, double t
   std::vector<char> done(nrhs, 0);
   for (int r = 0; r < nrhs; ++r) {
     gg[(size_t)r * (m + 1)] = beta[r];
-    if (beta[r] == 0) done[r] = 1;
+    if (beta[r] == 0 || bad[r]) done[r] = 1;
   }
   auto Hat = [&](int r, int i, int j) -> cd & { return H[((size_t)r * (m + 1) + i) * m + j]; };
   int k = 0;
   for (int j = 0; j < m; ++j) {
+    char label[32];
+    std::snprintf(label, sizeof label, "FGMRES iteration %d", j + 1);
+    NvtxRange it_range(label);
     double2 *Vj = V + j * vs, *Zj = Z + j * vs, *W = V + (j + 1) * vs;
     dds_status rs = ddm(ctx, Vj, nrhs, Zj, rounds);
     if (rs != DDS_OK) return rs;
@@ -1567,6 +1662,8 @@ dds_status fgmres(dds_ctx *ctx, const double2 *f, int nrhs, double2 *x, double t
   } else {
     CK(cudaMemsetAsync(x, 0, vbytes, st));
   }
+  for (int r = 0; r < nrhs; ++r)
+    if (bad[r]) CK(cudaMemsetAsync(x + (size_t)r * N, 0xFF, (size_t)N * sizeof(double2), st));
   if (x_host != nullptr) {
     // x is final: its copy to the host overlaps the true-residual computation below
     if (!ctx->out_stream) CK(cudaStreamCreateWithFlags(&ctx->out_stream, cudaStreamNonBlocking));
@@ -1584,7 +1681,7 @@ dds_status fgmres(dds_ctx *ctx, const double2 *f, int nrhs, double2 *x, double t
   relres.assign(nrhs, 0.0);
   bool ok = true;
   for (int r = 0; r < nrhs; ++r) {
-    relres[r] = beta[r] > 0 ? std::sqrt(std::max(hh[r].x, 0.0)) / beta[r] : 0.0;
+    relres[r] = bad[r] ? std::nan("") : (beta[r] > 0 ? std::sqrt(std::max(hh[r].x, 0.0)) / beta[r] : 0.0);
     if (!(relres[r] < tol)) ok = false;
   }
   return ok ? DDS_OK : DDS_ENOCONV;
@@ -1607,7 +1704,11 @@ dds_status dds_setup(const dds_problem *prob, dds_ctx **out) {
     return v;
   }
   ctx->stream = nullptr;
+  NvtxRange range("dds_setup");
+  MemAcct *prev = tl_acct;
+  tl_acct = &ctx->acct;   // set-up allocations count against the new context
   dds_status r = setup_impl(ctx.get(), prob);
+  tl_acct = prev;
   if (r != DDS_OK) {
     std::fprintf(stderr, "dds_setup: %s\n", ctx->err.c_str());
     return r;
@@ -1619,6 +1720,7 @@ dds_status dds_setup(const dds_problem *prob, dds_ctx **out) {
 // the DDM as a direct solver with sweep program `prog` (sweep_program): J-scaling of f, one
 // DDM application, the error flag and the copy back to a host u
 static dds_status sweep_impl(dds_ctx *ctx, const void *f, int nrhs, void *u, int prog) {
+  NvtxRange range(prog > 0 ? "dds_sweep" : "dds_sweep_strip");
   const size_t bytes = (size_t)nrhs * ctx->g.Nglob * sizeof(double2);
   const double2 *fd;
   double2 *ud;
@@ -1631,8 +1733,17 @@ static dds_status sweep_impl(dds_ctx *ctx, const void *f, int nrhs, void *u, int
   LAUNCHK(DDS_K_KRYLOV, launch_scale_J(ctx->stream, ctx->g, ctx->tb, nrhs, fd, ctx->bbuf.as<double2>()));
   r = ddm(ctx, ctx->bbuf.as<double2>(), nrhs, ud, prog);
   if (r != DDS_OK) return r;
-  r = check_errflag(ctx);
+  r = check_errflag(ctx);   // (synchronises the stream)
   if (r != DDS_OK) return r;
+  // a right-hand side whose source has a NaN or infinite entry gets a NaN field: the local
+  // solves of the single-precision modes need not carry a NaN through (the tensor-core split
+  // products do not), and a finite field would hide the bad input
+  std::vector<int> badh(nrhs, 0);
+  CK(cudaMemcpyAsync(badh.data(), ctx->badrhs.p, nrhs * sizeof(int), cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int q = 0; q < nrhs; ++q)
+    if (badh[q]) CK(cudaMemsetAsync(ud + (size_t)q * ctx->g.Nglob, 0xFF, ctx->g.Nglob * sizeof(double2), ctx->stream));
   return finish_out(ctx, u, bytes, uh);
 }
 
@@ -1671,6 +1782,7 @@ dds_status dds_solve(dds_ctx *ctx, const void *f, int nrhs, void *u, double tol,
     ctx->err = "invalid argument";
     return DDS_EINVAL;
   }
+  NvtxRange range("dds_solve");
   const size_t bytes = (size_t)nrhs * ctx->g.Nglob * sizeof(double2);
   const double2 *fd;
   double2 *ud;
@@ -1789,6 +1901,7 @@ dds_status dds_get_info(const dds_ctx *ctx, dds_info_t *info) {
   info->factor_bytes = (long long)(ctx->sinv64.n + ctx->sinv32.n + ctx->gmap64.n + ctx->gmap32.n +
                                    ctx->tctiles.n + ctx->bigtiles.n + ctx->tttiles.n);
   info->setup_seconds = ctx->setup_seconds;
+  info->device_bytes = (long long)ctx->acct.used;
   info->trace_kernel = ctx->plan != DDS_PLAN_TRACE ? -1 : (ctx->single && ctx->trace_tc ? 0 : ctx->trace_per_sm);
   info->subst_kernel = !ctx->single ? 0 : (ctx->split < 0 ? 1 : (ctx->big_tc ? 3 : 2));
   return DDS_OK;
@@ -1804,11 +1917,13 @@ dds_status dds_autotune(dds_ctx *ctx, int nrhs, int rounds, int max_entries, int
   if (!busy.ok) return DDS_EBUSY;
   ctx->err.clear();
   const Geom &g = ctx->g;
-  std::vector<int> pcs = {0};
+  // substitution shapes (panel width, panels per CTA); 0 = automatic (non-tensor-core paths)
+  std::vector<std::array<int, 2>> pcs = {{0, 1}};
   if (ctx->single && ctx->split >= 0) {
     pcs.clear();
-    for (int pc : {8, 16, 32})
-      if (subst_tc_ok(g, ctx->split, pc, ctx->tc_m > 0)) pcs.push_back(pc);
+    for (int np : {1, 2})
+      for (int pc : {8, 16, 32})
+        if (subst_tc_ok(g, ctx->split, pc, ctx->tc_m > 0, np)) pcs.push_back({pc, np});
   }
   // trace kernel: 1 or 2 = CUDA-core kernel with that many CTAs per SM, 0 = tensor-core kernel
   std::vector<int> pers = {ctx->trace_tc ? 0 : ctx->trace_per_sm};
@@ -1829,12 +1944,14 @@ dds_status dds_autotune(dds_ctx *ctx, int nrhs, int rounds, int max_entries, int
   const bool prof = ctx->profiling;
   ctx->profiling = false;
   double best_ms = 1e300;
-  int best_pc = ctx->tune_pc, best_per = ctx->trace_tc ? 0 : ctx->trace_per_sm;
+  int best_pc = ctx->tune_pc, best_np = ctx->tune_np, best_per = ctx->trace_tc ? 0 : ctx->trace_per_sm;
   int n = 0;
   dds_status r = DDS_OK;
-  for (int pc : pcs)
+  for (const auto &shape : pcs)
     for (int per : pers) {
+      const int pc = shape[0];
       ctx->tune_pc = pc;
+      ctx->tune_np = shape[1];
       ctx->trace_tc = per == 0;
       if (per > 0) ctx->trace_per_sm = per;
       ctx->clear_graphs();
@@ -1852,17 +1969,24 @@ dds_status dds_autotune(dds_ctx *ctx, int nrhs, int rounds, int max_entries, int
       cudaEventElapsedTime(&ms, e0, e1);
       const double per_app = ms / reps;
       if (n < max_entries) {
-        table[3 * n + 0] = pc;
-        table[3 * n + 1] = per;
-        table[3 * n + 2] = per_app;
+        table[4 * n + 0] = pc;
+        table[4 * n + 1] = shape[1];
+        table[4 * n + 2] = per;
+        table[4 * n + 3] = per_app;
       }
       ++n;
-      if (per_app < best_ms) { best_ms = per_app; best_pc = pc; best_per = per; }
+      if (per_app < best_ms) {
+        best_ms = per_app;
+        best_pc = pc;
+        best_np = shape[1];
+        best_per = per;
+      }
     }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   ctx->profiling = prof;
   ctx->tune_pc = best_pc;
+  ctx->tune_np = best_np;
   ctx->trace_tc = best_per == 0;
   if (best_per > 0) ctx->trace_per_sm = best_per;
   ctx->clear_graphs();
@@ -1872,6 +1996,7 @@ dds_status dds_autotune(dds_ctx *ctx, int nrhs, int rounds, int max_entries, int
   *n_entries = n;
   best[0] = best_pc;
   best[1] = best_per;
+  best[2] = best_np;
   return check_errflag(ctx);
 }
 
@@ -1927,6 +2052,26 @@ dds_status dds_profile_read(dds_ctx *ctx, int kind, long long *launches, double 
   CK(prof_fold(ctx));
   if (launches) *launches = ctx->prof_count[kind];
   if (ms) *ms = ctx->prof_ms[kind];
+  return DDS_OK;
+}
+
+dds_status dds_set_memory_budget(dds_ctx *ctx, long long bytes, long long *in_use) {
+  if (!ctx || bytes < 0) return DDS_EINVAL;
+  Busy busy(ctx);
+  if (!busy.ok) return DDS_EBUSY;
+  ctx->err.clear();
+  ctx->acct.budget = (size_t)bytes;
+  if (in_use) *in_use = (long long)ctx->acct.used;
+  return DDS_OK;
+}
+
+dds_status dds_set_wait_limit(dds_ctx *ctx, long long polls) {
+  if (!ctx || polls < 0 || polls > 0xFFFFFFFFLL) return DDS_EINVAL;
+  Busy busy(ctx);
+  if (!busy.ok) return DDS_EBUSY;
+  ctx->err.clear();
+  ctx->wait_limit = polls == 0 ? (1u << 20) : (unsigned)polls;
+  ctx->clear_graphs();   // the limit is a launch argument of the captured launches
   return DDS_OK;
 }
 

@@ -210,7 +210,7 @@ cudaError_t launch_assemble(cudaStream_t st, const Geom &g, const Tables &tb, in
                             const double2 *unused, int with_source,
                             const typename Cx<R>::T *traces, long long trace_rhs_stride,
                             long long trace_sub_stride, int nslots, long long slot_stride,
-                            int *nzflag = nullptr);
+                            int *nzflag = nullptr, int *badrhs = nullptr);
 
 // zero-work skipping: pack the columns with a nonzero right-hand side (nz[slot]) of each
 // group (int4: column range [x, y), panel range [z, w), one factor) into dcols / dpans (same
@@ -241,14 +241,16 @@ cudaError_t launch_subst_big(cudaStream_t st, const Geom &g, int kind, int npane
                              const float2 *cpl, float2 *work, int pc, int ksplit, float2 *acc,
                              unsigned char *B, int *err, long long *launches);
 
-// m > 0: two-sided chain split at block m, one 2-CTA cluster per panel; m = 0: one-sided
+// m > 0: two-sided chain split at block m, one 2-CTA cluster per np panels; m = 0: one-sided
 // nz (optional): per work slot, nonzero if the column's right-hand side has a nonzero entry;
-// CTAs whose columns are all zero leave at once (their solution is the zero already in work)
+// panels whose columns are all zero are dropped (their solution is the zero already in work)
+// np: panels per CTA (or CTA pair), 1, or 2 for pc <= 16 (one panel's epilogue under the
+// other's MMAs)
 cudaError_t launch_subst_tc(cudaStream_t st, const Geom &g, int kind, int npanels,
                             const Panel *panels, const Col *cols, const unsigned char *tiles,
                             const float2 *cpl, float2 *work, int pc, int *err, int m,
-                            const int *nz = nullptr);
-bool subst_tc_ok(const Geom &g, int kind, int pc, bool twisted);
+                            const int *nz = nullptr, int np = 1);
+bool subst_tc_ok(const Geom &g, int kind, int pc, bool twisted, int np = 1);
 int tc_middle_block(const Geom &g);   // m of the two-sided chain (0: too few blocks)
 long long tc_tiles_bytes(const Geom &g, int kind, int nfac);
 // tiles j < m from sinv64, j >= m from tw64 (m = 0 or tw64 null: all from sinv64)
@@ -273,7 +275,8 @@ cudaError_t launch_split_trace(cudaStream_t st, const Geom &g, int kind, int nfa
 cudaError_t launch_trace_tc(cudaStream_t st, const Geom &g, int kind, const int4 *units,
                             const int *ucols, int nunits, const int *lev_off, int nlevels,
                             const unsigned char *tiles, const int *route, float2 *gtr,
-                            const float2 *rawf, int nrhs, unsigned *gbar, int *err);
+                            const float2 *rawf, int nrhs, unsigned *ready, const unsigned *need,
+                            int nslots, int *err, unsigned wait_limit);
 
 template <typename R>
 cudaError_t launch_extract(cudaStream_t st, const Geom &g, int ncols, const Col *cols,
@@ -312,7 +315,7 @@ cudaError_t launch_trace_sweeps(cudaStream_t st, const Geom &g, const int4 *hdr,
                                 int nitems, const int *lev_off, int nlevels,
                                 const typename Cx<R>::T *gmap, typename Cx<R>::T *g_traces,
                                 const typename Cx<R>::T *rawf, int nrhs, unsigned *gbar, int *err,
-                                int ctas_per_sm);
+                                int ctas_per_sm, unsigned wait_limit);
 
 template <typename R>
 cudaError_t launch_unit_traces(cudaStream_t st, const Geom &g, const Tables &tb, int k0, int nk,

@@ -55,7 +55,7 @@ struct TcShape {
 
 static size_t tc_static_smem() { return 1024; }
 
-bool tc_shape(const Geom &g, int kind, int pc, TcShape *s, bool twisted = false) {
+bool tc_shape(const Geom &g, int kind, int pc, TcShape *s, bool twisted = false, int np = 1) {
   TcShape t;
   t.kind = kind;
   t.EK = kind == 0 ? 4 : 8;
@@ -63,11 +63,12 @@ bool tc_shape(const Geom &g, int kind, int pc, TcShape *s, bool twisted = false)
   t.Kp = (g.Mb + 2 * t.EK - 1) / (2 * t.EK) * (2 * t.EK);
   if (t.Mp > 128 || t.Kp > 128) return false;
   if (pc != 8 && pc != 16 && pc != 32) return false;
+  if (np != 1 && !(np == 2 && pc <= 16)) return false;
   t.ks = t.Kp / (2 * t.EK);
   t.LB = 4 * pc * 16 + 16;
   t.tile_bytes = (long long)t.ks * 128 * t.Mp;
-  // B operand, plus the exchange buffer [128 rows][pc] of the two-sided chain
-  const size_t bbytes = (size_t)(t.Kp / t.EK) * t.LB + (twisted ? (size_t)128 * pc * 8 : 0);
+  // B operand, plus the exchange buffer [128 rows][pc] of the two-sided chain, per panel
+  const size_t bbytes = (size_t)np * ((size_t)(t.Kp / t.EK) * t.LB + (twisted ? (size_t)128 * pc * 8 : 0));
   const size_t budget = 227 * 1024 - tc_static_smem();
   for (int nch = 1; nch <= t.ks; ++nch) {
     const int KS = (t.ks + nch - 1) / nch;
@@ -222,45 +223,66 @@ __device__ inline int tc_nstages(int role, int m, int Ml) {
   return role == 0 ? 2 * m + 1 : 2 * (Ml - 1 - m) + 1;
 }
 
-template <int PC, int KIND, int NG, bool TW>
+// NP panels per CTA (1 or 2): each panel has its own tensor-memory accumulator pair, B operand,
+// exchange buffer and barriers; the MMA issuer and the epilogue take the panels in turn at every
+// stage, so the epilogue of one panel runs while the other panel's MMAs do.
+template <int PC, int KIND, int NG, bool TW, int NP>
 __global__ void __launch_bounds__(32 * (4 * NG + 2), 1)
-    k_subst_tc(Geom g, TcArgs a, const Panel *__restrict__ panels, const Col *__restrict__ cols,
-               const unsigned char *__restrict__ tiles, const float2 *__restrict__ cpl,
-               float2 *__restrict__ work, int *__restrict__ err, int m,
-               const int *__restrict__ nz) {
+    k_subst_tc(Geom g, TcArgs a, const Panel *__restrict__ panels, int npanels,
+               const Col *__restrict__ cols, const unsigned char *__restrict__ tiles,
+               const float2 *__restrict__ cpl, float2 *__restrict__ work, int *__restrict__ err,
+               int m, const int *__restrict__ nz) {
   constexpr int H = PC / NG;            // columns per epilogue thread
   constexpr int NEPI = 128 * NG;        // epilogue threads
-  constexpr int NCOL = 8 * PC;          // TMEM columns: D1 [0, 4PC), D2 [4PC, 8PC)
-  constexpr int NALLOC = NCOL <= 32 ? 32 : (NCOL <= 64 ? 64 : (NCOL <= 128 ? 128 : 256));
+  constexpr int NCOL = 8 * PC;          // TMEM columns per panel: D1 [0, 4PC), D2 [4PC, 8PC)
+  constexpr int NALL = NP * NCOL;
+  constexpr int NALLOC = NALL <= 32 ? 32 : (NALL <= 64 ? 64 : (NALL <= 128 ? 128 : (NALL <= 256 ? 256 : 512)));
   constexpr uint32_t kIdN4 = KIND == 0 ? umma::idesc_tf32(128, 4 * PC) : umma::idesc_bf16(128, 4 * PC);
   constexpr uint32_t kIdN2 = KIND == 0 ? umma::idesc_tf32(128, 2 * PC) : umma::idesc_bf16(128, 2 * PC);
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  __shared__ uint64_t bars[8];   // full[2], empty[2], dready, bready, drain, xbar
+  // full[2], empty[2], drain, then per panel: dready, bready, xbar
+  __shared__ uint64_t bars[5 + 3 * NP];
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
-  uint64_t *full = bars, *empty = bars + 2, *dready = bars + 4, *bready = bars + 5,
-           *drain = bars + 6, *xbar = bars + 7;
+  uint64_t *full = bars, *empty = bars + 2, *drain = bars + 4;
+  uint64_t *dready = bars + 5, *bready = bars + 5 + NP, *xbar = bars + 5 + 2 * NP;
 
   const int Mb = g.Mb, Ml = g.Ml;
   const int role = TW ? (int)cluster_ctarank() : 0;
   const int nst = tc_nstages(role, m, Ml);
   const int nfwd = role == 0 ? m : Ml - 1 - m;   // forward stages before the middle block
   const long long chunk_bytes = (long long)a.KS * 128 * a.Mp;
+  const size_t bbytes = (size_t)(a.Kp / (KIND == 0 ? 4 : 8)) * a.LB;
   unsigned char *ring = smem_raw;
-  unsigned char *sB = smem_raw + 2 * chunk_bytes;
-  // exchange buffer of the two-sided chain: the peer's coupling term, [row][PC]
-  float2 *xch = reinterpret_cast<float2 *>(sB + (size_t)(a.Kp / (KIND == 0 ? 4 : 8)) * a.LB);
-  const Panel p = panels[TW ? blockIdx.x / 2 : blockIdx.x];
+  auto sBp = [&](int h) { return smem_raw + 2 * chunk_bytes + (size_t)h * bbytes; };
+  // exchange buffers of the two-sided chain: the peer's coupling terms, [panel][row][PC]
+  float2 *xch0 = reinterpret_cast<float2 *>(smem_raw + 2 * chunk_bytes + (size_t)NP * bbytes);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  // an empty panel of a compacted list (zero-work skipping); both CTAs of a cluster leave
-  if (p.ncol == 0) return;
-  if (nz != nullptr) {
-    // zero-work skipping: the solve of a zero right-hand side is zero, which work already holds
-    // (both CTAs of a cluster see the same columns and leave together)
-    int any = 0;
-    for (int c = 0; c < p.ncol; ++c) any |= nz[cols[p.col0 + c].slot];
-    if (!any) return;
+  // this CTA's panels: NP consecutive entries of the list, of which the empty ones (a compacted
+  // list's spares, or, with nz, panels whose columns all have zero right-hand sides: their solution
+  // is the zero already in work) are dropped; both CTAs of a cluster see the same and agree
+  Panel P[NP];
+  int np_act = 0;
+  {
+    const int pair = TW ? blockIdx.x / 2 : blockIdx.x;
+#pragma unroll
+    for (int h = 0; h < NP; ++h) {
+      const int idx = pair * NP + h;
+      if (idx >= npanels) continue;
+      const Panel p = panels[idx];
+      if (p.ncol == 0) continue;
+      if (nz != nullptr) {
+        int any = 0;
+        for (int c = 0; c < p.ncol; ++c) any |= nz[cols[p.col0 + c].slot];
+        if (!any) continue;
+      }
+#pragma unroll
+      for (int k = 0; k < NP; ++k)
+        if (k == np_act) P[k] = p;
+      ++np_act;
+    }
   }
+  if (np_act == 0) return;
   auto aborted = [&]() { return *reinterpret_cast<volatile int *>(&abort_flag) != 0; };
   auto fail = [&](int code) {
     atomicExch(err, code);
@@ -272,10 +294,13 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1)
     mbar_init(&full[1], 1);
     mbar_init(&empty[0], 1);
     mbar_init(&empty[1], 1);
-    mbar_init(dready, 1);
-    mbar_init(bready, NEPI / 32);   // one arrival per epilogue warp
     mbar_init(drain, 1);
-    mbar_init(xbar, NEPI);          // one remote arrival per epilogue thread of the peer
+#pragma unroll
+    for (int h = 0; h < NP; ++h) {
+      mbar_init(&dready[h], 1);
+      mbar_init(&bready[h], NEPI / 32);   // one arrival per epilogue warp
+      mbar_init(&xbar[h], NEPI);          // one remote arrival per epilogue thread of the peer
+    }
     abort_flag = 0;
     mbar_init_fence();
   }
@@ -290,19 +315,23 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1)
   const uint32_t tmem = tmem_base;
 
   if (warp == 4 * NG) {
-    // ---------------- producer: the tiles of this CTA's stages through the two-slot ring
+    // ---------------- producer: the tiles of every (stage, panel) through the two-slot ring
     if (lane == 0) {
       int last0 = -1, last1 = -1;
-      const int nchunks = nst * a.nch;
+      const int nchunks = nst * np_act * a.nch;
       for (int i = 0; i < nchunks; ++i) {
         const int s = i & 1;
         if (i >= 2 && !mbar_wait(&empty[s], ((i >> 1) - 1) & 1)) { fail(11); break; }
         if (aborted()) break;
-        const int q = i / a.nch, c = i % a.nch;
+        const int q = i / (np_act * a.nch), h = (i / a.nch) % np_act, c = i % a.nch;
         const int nks = min(a.KS, a.ks - c * a.KS);
         const uint32_t bytes = (uint32_t)nks * 128u * (uint32_t)a.Mp;
         const int j = tc_stage(role, q, m, Ml).j;
-        const unsigned char *src = tiles + ((long long)p.factor * Ml + j) * a.tile_bytes +
+        int fac = P[0].factor;
+#pragma unroll
+        for (int k = 1; k < NP; ++k)
+          if (h == k) fac = P[k].factor;
+        const unsigned char *src = tiles + ((long long)fac * Ml + j) * a.tile_bytes +
                                    (long long)c * a.KS * 128 * a.Mp;
         mbar_arrive_expect_tx(&full[s], bytes);
         bulk_g2s(ring + s * chunk_bytes, src, bytes, &full[s]);
@@ -313,164 +342,183 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1)
       if (last1 >= 0 && !mbar_wait(&full[1], (last1 >> 1) & 1)) atomicExch(err, 12);
     }
   } else if (warp == 4 * NG + 1) {
-    // ---------------- MMA issuer
+    // ---------------- MMA issuer: at every stage, each panel in turn once its B operand is in
     if (lane == 0) {
       const uint32_t lbo_a = (uint32_t)a.Mp * 16u;
       const uint64_t dA = (uint64_t)8 * a.Mp;              // one K-step of A, in 16-byte units
       const uint64_t dC = (uint64_t)2 * a.Mp;              // one component of A
       const uint64_t dB = (uint64_t)(2 * a.LB) >> 4;       // one K-step of B
-      const uint64_t b0 = umma::smem_desc(umma::saddr(sB), (uint32_t)a.LB, 128);
-      const uint32_t d1 = tmem, d2 = tmem + 4 * PC;
-      for (int q = 0; q < nst; ++q) {
-        if (!mbar_wait(bready, q & 1)) { fail(13); break; }
-        if (aborted()) break;
-        umma::fence_after_sync();
-        bool ok = true;
-        for (int c = 0; c < a.nch; ++c) {
-          const int i = q * a.nch + c, s = i & 1;
-          if (!mbar_wait(&full[s], (i >> 1) & 1)) { fail(14); ok = false; break; }
+      int i = 0;                                           // ring chunks consumed
+      bool ok = true;
+      for (int q = 0; q < nst && ok; ++q) {
+        for (int h = 0; h < np_act && ok; ++h) {
+          if (!mbar_wait(&bready[h], q & 1)) { fail(13); ok = false; break; }
+          if (aborted()) { ok = false; break; }
           umma::fence_after_sync();
-          const int nks = min(a.KS, a.ks - c * a.KS);
-          uint64_t ad = umma::smem_desc(umma::saddr(ring + s * chunk_bytes), lbo_a, 128);
-          uint64_t bd = b0 + (uint64_t)(c * a.KS) * dB;
-          for (int t = 0; t < nks; ++t) {
-            const uint32_t acc = (c > 0 || t > 0) ? 1u : 0u;
-            if (KIND == 0) {
-              umma::mma_tf32(d1, ad, bd, kIdN4, acc);
-              umma::mma_tf32(d1, ad + dC, bd, kIdN2, 1);
-              umma::mma_tf32(d2, ad + 2 * dC, bd, kIdN4, acc);
-              umma::mma_tf32(d2, ad + 3 * dC, bd, kIdN2, 1);
-            } else {
-              umma::mma_bf16(d1, ad, bd, kIdN4, acc);
-              umma::mma_bf16(d1, ad + dC, bd, kIdN2, 1);
-              umma::mma_bf16(d2, ad + 2 * dC, bd, kIdN4, acc);
-              umma::mma_bf16(d2, ad + 3 * dC, bd, kIdN2, 1);
+          const uint64_t b0 = umma::smem_desc(umma::saddr(sBp(h)), (uint32_t)a.LB, 128);
+          const uint32_t d1 = tmem + (uint32_t)h * NCOL, d2 = d1 + 4 * PC;
+          for (int c = 0; c < a.nch; ++c, ++i) {
+            const int s = i & 1;
+            if (!mbar_wait(&full[s], (i >> 1) & 1)) { fail(14); ok = false; break; }
+            umma::fence_after_sync();
+            const int nks = min(a.KS, a.ks - c * a.KS);
+            uint64_t ad = umma::smem_desc(umma::saddr(ring + s * chunk_bytes), lbo_a, 128);
+            uint64_t bd = b0 + (uint64_t)(c * a.KS) * dB;
+            for (int t = 0; t < nks; ++t) {
+              const uint32_t acc = (c > 0 || t > 0) ? 1u : 0u;
+              if (KIND == 0) {
+                umma::mma_tf32(d1, ad, bd, kIdN4, acc);
+                umma::mma_tf32(d1, ad + dC, bd, kIdN2, 1);
+                umma::mma_tf32(d2, ad + 2 * dC, bd, kIdN4, acc);
+                umma::mma_tf32(d2, ad + 3 * dC, bd, kIdN2, 1);
+              } else {
+                umma::mma_bf16(d1, ad, bd, kIdN4, acc);
+                umma::mma_bf16(d1, ad + dC, bd, kIdN2, 1);
+                umma::mma_bf16(d2, ad + 2 * dC, bd, kIdN4, acc);
+                umma::mma_bf16(d2, ad + 3 * dC, bd, kIdN2, 1);
+              }
+              ad += dA;
+              bd += dB;
             }
-            ad += dA;
-            bd += dB;
+            umma::mma_commit(&empty[s]);   // the slot is free once these MMAs have read it
           }
-          umma::mma_commit(&empty[s]);   // the slot is free once these MMAs have read it
+          if (!ok) break;
+          umma::mma_commit(&dready[h]);
         }
-        if (!ok) break;
-        umma::mma_commit(dready);
       }
       umma::mma_commit(drain);
       if (!mbar_wait(drain, 0)) atomicExch(err, 15);
     }
   } else {
-    // ---------------- epilogue: row r of the block, columns grp*H .. grp*H + H - 1
+    // ---------------- epilogue: row r of the block, columns grp*H .. grp*H + H - 1, each panel
     const int r = tid & 127, grp = tid >> 7;
     const bool row = r < Mb, krow = r < a.Kp;
-    const float2 *cf = cpl + (long long)p.factor * Ml * (long long)Mb;
-    float2 *xs[H];
+    float2 *xs[NP][H];
+    const float2 *cf[NP];
 #pragma unroll
-    for (int h = 0; h < H; ++h) {
-      const int c = grp * H + h;
-      xs[h] = c < p.ncol ? work + (long long)cols[p.col0 + c].slot * g.Nloc : nullptr;
+    for (int h = 0; h < NP; ++h) {
+      const Panel &p = P[h];
+      const bool act = h < np_act;
+      cf[h] = cpl + (long long)(act ? p.factor : 0) * Ml * (long long)Mb;
+#pragma unroll
+      for (int k = 0; k < H; ++k) {
+        const int c = grp * H + k;
+        xs[h][k] = (act && c < p.ncol) ? work + (long long)cols[p.col0 + c].slot * g.Nloc : nullptr;
+      }
     }
-    // B operand of the first stage: the right-hand side of its block
+    // B operand of the first stage of every panel: the right-hand side of its block
     {
       const int j = tc_stage(role, 0, m, Ml).j;
-      if (krow) {
 #pragma unroll
-        for (int h = 0; h < H; ++h) {
-          const float2 v = (row && xs[h]) ? xs[h][(long long)j * Mb + r] : make_float2(0.f, 0.f);
-          put_b<KIND, PC>(sB, a.LB, r, grp * 2 * H + h, grp * 2 * H + H + h, v);
+      for (int h = 0; h < NP; ++h) {
+        if (h >= np_act) break;
+        if (krow) {
+#pragma unroll
+          for (int k = 0; k < H; ++k) {
+            const float2 v = (row && xs[h][k]) ? xs[h][k][(long long)j * Mb + r] : make_float2(0.f, 0.f);
+            put_b<KIND, PC>(sBp(h), a.LB, r, grp * 2 * H + k, grp * 2 * H + H + k, v);
+          }
         }
-      }
-    }
-    fence_proxy_async();
-    umma::fence_before_sync();
-    __syncwarp();
-    if (lane == 0) mbar_arrive(bready);
-    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
-    for (int q = 0; q < nst; ++q) {
-      const TcStage st = tc_stage(role, q, m, Ml);
-      const bool exch = TW && st.kind == 0 && q == nfwd - 1;   // last forward stage
-      // epilogue operands, loaded before the accumulator is ready: the right-hand side of the
-      // next block (forward), this block's forward result (backward), the coupling to the next
-      float2 pre[H];
-      float2 cn = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int h = 0; h < H; ++h) pre[h] = make_float2(0.f, 0.f);
-      if (row) {
-        const int jp = st.kind == 0 ? st.jn : (st.kind == 2 ? st.j : -1);
-        if (jp >= 0) {
-#pragma unroll
-          for (int h = 0; h < H; ++h)
-            if (xs[h]) pre[h] = xs[h][(long long)jp * Mb + r];
-        }
-        if (st.jn >= 0) cn = cf[(long long)min(st.j, st.jn) * Mb + r];
-      }
-      // one lane per warp polls the accumulator barrier; the warp follows it
-      int ok = 1;
-      if (lane == 0) ok = mbar_wait(dready, q & 1) ? 1 : 0;
-      ok = __shfl_sync(0xffffffffu, ok, 0);
-      if (!ok) { if (lane == 0) fail(16); break; }
-      if (aborted()) break;
-      umma::fence_after_sync();
-      // accumulator runs of this column group: D1 piece 0, D1 piece 1, D2 piece 0, D2 piece 1
-      float d[4][2 * H];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const uint32_t col = (uint32_t)((u >> 1) * 4 * PC + (u & 1) * 2 * PC + grp * 2 * H);
-#pragma unroll
-        for (int c8 = 0; c8 < 2 * H; c8 += 8) umma::tmem_ld8(tmem + lane_base + col + c8, &d[u][c8]);
-      }
-      umma::tmem_wait_ld();
-      const bool more = q + 1 < nst;
-      float2 xo[H], vv[H];
-#pragma unroll
-      for (int h = 0; h < H; ++h) {
-        const float p_re = d[0][h] + d[1][h], p_im = d[0][H + h] + d[1][H + h];
-        const float q_re = d[2][h] + d[3][h], q_im = d[2][H + h] + d[3][H + h];
-        const float2 acc = make_float2(p_re - q_im, p_im + q_re);
-        if (st.kind == 2) {
-          xo[h] = csub(pre[h], acc);            // x_j = y_j - S_j^{-1} C x_next
-          vv[h] = cmul(cn, xo[h]);
-        } else if (st.kind == 1) {
-          xo[h] = acc;                          // middle block: x_m
-          vv[h] = cmul(cn, acc);
-        } else {
-          xo[h] = acc;                          // forward: y_j (or z_j)
-          vv[h] = exch ? cmul(cn, acc) : csub(pre[h], cmul(cn, acc));
-        }
-        if (!row) vv[h] = make_float2(0.f, 0.f);
-      }
-      if (exch) {
-        // the coupling term C y of this half goes to the peer; the peer's comes back
-        const uint32_t peer = (uint32_t)(role ^ 1);
-        if (row) {
-#pragma unroll
-          for (int h = 0; h < H; ++h)
-            st_cluster_f2(cluster_map(xch + r * PC + grp * H + h, peer), vv[h]);
-        }
-        // every thread releases its own remote writes and acquires the peer's
-        mbar_arrive_remote(cluster_map(xbar, peer));
-        const int okx = __all_sync(0xffffffffu, mbar_wait_cluster(xbar, 0) ? 1 : 0);
-        if (!okx) { if (lane == 0) fail(17); break; }
-#pragma unroll
-        for (int h = 0; h < H; ++h) {
-          const float2 other = row ? xch[r * PC + grp * H + h] : make_float2(0.f, 0.f);
-          vv[h] = row ? csub(csub(pre[h], vv[h]), other) : make_float2(0.f, 0.f);
-        }
-      }
-      if (more && krow) {
-#pragma unroll
-        for (int h = 0; h < H; ++h)
-          put_b<KIND, PC>(sB, a.LB, r, grp * 2 * H + h, grp * 2 * H + H + h, vv[h]);
-      }
-      if (more) {
         fence_proxy_async();
         umma::fence_before_sync();
         __syncwarp();
-        if (lane == 0) mbar_arrive(bready);
+        if (lane == 0) mbar_arrive(&bready[h]);
       }
-      // x_j leaves for global memory while the next stage's MMAs run (the middle block once)
-      const bool store = !(TW && st.kind == 1 && role == 1);
+    }
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+    bool stop = false;
+    for (int q = 0; q < nst && !stop; ++q) {
+      const TcStage st = tc_stage(role, q, m, Ml);
+      const bool exch = TW && st.kind == 0 && q == nfwd - 1;   // last forward stage
+      const bool more = q + 1 < nst;
 #pragma unroll
-      for (int h = 0; h < H; ++h)
-        if (store && row && xs[h]) xs[h][(long long)st.j * Mb + r] = xo[h];
+      for (int h = 0; h < NP; ++h) {
+        if (h >= np_act || stop) break;
+        // epilogue operands, loaded before the accumulator is ready: the right-hand side of the
+        // next block (forward), this block's forward result (backward), the coupling to the next
+        float2 pre[H];
+        float2 cn = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < H; ++k) pre[k] = make_float2(0.f, 0.f);
+        if (row) {
+          const int jp = st.kind == 0 ? st.jn : (st.kind == 2 ? st.j : -1);
+          if (jp >= 0) {
+#pragma unroll
+            for (int k = 0; k < H; ++k)
+              if (xs[h][k]) pre[k] = xs[h][k][(long long)jp * Mb + r];
+          }
+          if (st.jn >= 0) cn = cf[h][(long long)min(st.j, st.jn) * Mb + r];
+        }
+        // one lane per warp polls the accumulator barrier; the warp follows it
+        int ok = 1;
+        if (lane == 0) ok = mbar_wait(&dready[h], q & 1) ? 1 : 0;
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) { if (lane == 0) fail(16); stop = true; break; }
+        if (aborted()) { stop = true; break; }
+        umma::fence_after_sync();
+        // accumulator runs of this column group: D1 piece 0, D1 piece 1, D2 piece 0, D2 piece 1
+        float d[4][2 * H];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const uint32_t col = (uint32_t)(h * NCOL + (u >> 1) * 4 * PC + (u & 1) * 2 * PC + grp * 2 * H);
+#pragma unroll
+          for (int c8 = 0; c8 < 2 * H; c8 += 8) umma::tmem_ld8(tmem + lane_base + col + c8, &d[u][c8]);
+        }
+        umma::tmem_wait_ld();
+        float2 xo[H], vv[H];
+#pragma unroll
+        for (int k = 0; k < H; ++k) {
+          const float p_re = d[0][k] + d[1][k], p_im = d[0][H + k] + d[1][H + k];
+          const float q_re = d[2][k] + d[3][k], q_im = d[2][H + k] + d[3][H + k];
+          const float2 acc = make_float2(p_re - q_im, p_im + q_re);
+          if (st.kind == 2) {
+            xo[k] = csub(pre[k], acc);            // x_j = y_j - S_j^{-1} C x_next
+            vv[k] = cmul(cn, xo[k]);
+          } else if (st.kind == 1) {
+            xo[k] = acc;                          // middle block: x_m
+            vv[k] = cmul(cn, acc);
+          } else {
+            xo[k] = acc;                          // forward: y_j (or z_j)
+            vv[k] = exch ? cmul(cn, acc) : csub(pre[k], cmul(cn, acc));
+          }
+          if (!row) vv[k] = make_float2(0.f, 0.f);
+        }
+        if (exch) {
+          // the coupling term C y of this half goes to the peer; the peer's comes back
+          float2 *xch = xch0 + (size_t)h * 128 * PC;
+          const uint32_t peer = (uint32_t)(role ^ 1);
+          if (row) {
+#pragma unroll
+            for (int k = 0; k < H; ++k)
+              st_cluster_f2(cluster_map(xch + r * PC + grp * H + k, peer), vv[k]);
+          }
+          // every thread releases its own remote writes and acquires the peer's
+          mbar_arrive_remote(cluster_map(&xbar[h], peer));
+          const int okx = __all_sync(0xffffffffu, mbar_wait_cluster(&xbar[h], 0) ? 1 : 0);
+          if (!okx) { if (lane == 0) fail(17); stop = true; break; }
+#pragma unroll
+          for (int k = 0; k < H; ++k) {
+            const float2 other = row ? xch[r * PC + grp * H + k] : make_float2(0.f, 0.f);
+            vv[k] = row ? csub(csub(pre[k], vv[k]), other) : make_float2(0.f, 0.f);
+          }
+        }
+        if (more && krow) {
+#pragma unroll
+          for (int k = 0; k < H; ++k)
+            put_b<KIND, PC>(sBp(h), a.LB, r, grp * 2 * H + k, grp * 2 * H + H + k, vv[k]);
+        }
+        if (more) {
+          fence_proxy_async();
+          umma::fence_before_sync();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&bready[h]);
+        }
+        // x_j leaves for global memory while the next MMAs run (the middle block once)
+        const bool store = !(TW && st.kind == 1 && role == 1);
+#pragma unroll
+        for (int k = 0; k < H; ++k)
+          if (store && row && xs[h][k]) xs[h][k][(long long)st.j * Mb + r] = xo[k];
+      }
     }
   }
   umma::fence_before_sync();
@@ -482,40 +530,48 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1)
   if (TW) cluster_sync_all();   // no CTA leaves while its peer may still touch its memory
 }
 
-template <int PC, int KIND, bool TW>
+template <int PC, int KIND, bool TW, int NP>
 static cudaError_t tc_launch(cudaStream_t st, const Geom &g, const TcShape &t, int npanels,
                              const Panel *panels, const Col *cols, const unsigned char *tiles,
                              const float2 *cpl, float2 *work, int *err, int m, const int *nz) {
   constexpr int NG = 2;   // two epilogue column groups (measured faster than four at 16 columns)
   static bool done[64] = {false};
-  cudaError_t e = smem_limit_once(k_subst_tc<PC, KIND, NG, TW>, done);
+  cudaError_t e = smem_limit_once(k_subst_tc<PC, KIND, NG, TW, NP>, done);
   if (e != cudaSuccess) return e;
   TcArgs a{t.Mp, t.Kp, t.ks, t.KS, t.nch, t.LB, t.tile_bytes};
+  const int groups = (npanels + NP - 1) / NP;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(TW ? 2 * npanels : npanels));
+  cfg.gridDim = dim3((unsigned)(TW ? 2 * groups : groups));
   cfg.blockDim = dim3(32 * (4 * NG + 2));
   cfg.dynamicSmemBytes = t.smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = TW ? 2 : 1;
+  attr[0].val.clusterDim.x = 2;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = TW ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, k_subst_tc<PC, KIND, NG, TW>, g, a, panels, cols, tiles, cpl,
-                            work, err, TW ? m : g.Ml - 1, nz);
+  return cudaLaunchKernelEx(&cfg, k_subst_tc<PC, KIND, NG, TW, NP>, g, a, panels, npanels, cols,
+                            tiles, cpl, work, err, TW ? m : g.Ml - 1, nz);
 }
 
 template <int KIND, bool TW>
 static cudaError_t tc_dispatch(cudaStream_t st, const Geom &g, const TcShape &t, int npanels,
                                const Panel *panels, const Col *cols, const unsigned char *tiles,
                                const float2 *cpl, float2 *work, int pc, int *err, int m,
-                               const int *nz) {
+                               const int *nz, int np) {
+  if (np == 2) {
+    switch (pc) {
+      case 8: return tc_launch<8, KIND, TW, 2>(st, g, t, npanels, panels, cols, tiles, cpl, work, err, m, nz);
+      case 16: return tc_launch<16, KIND, TW, 2>(st, g, t, npanels, panels, cols, tiles, cpl, work, err, m, nz);
+    }
+    return cudaErrorInvalidValue;
+  }
   switch (pc) {
-    case 8: return tc_launch<8, KIND, TW>(st, g, t, npanels, panels, cols, tiles, cpl, work, err, m, nz);
-    case 16: return tc_launch<16, KIND, TW>(st, g, t, npanels, panels, cols, tiles, cpl, work, err, m, nz);
-    case 32: return tc_launch<32, KIND, TW>(st, g, t, npanels, panels, cols, tiles, cpl, work, err, m, nz);
+    case 8: return tc_launch<8, KIND, TW, 1>(st, g, t, npanels, panels, cols, tiles, cpl, work, err, m, nz);
+    case 16: return tc_launch<16, KIND, TW, 1>(st, g, t, npanels, panels, cols, tiles, cpl, work, err, m, nz);
+    case 32: return tc_launch<32, KIND, TW, 1>(st, g, t, npanels, panels, cols, tiles, cpl, work, err, m, nz);
   }
   return cudaErrorInvalidValue;
 }
@@ -523,20 +579,20 @@ static cudaError_t tc_dispatch(cudaStream_t st, const Geom &g, const TcShape &t,
 cudaError_t launch_subst_tc(cudaStream_t st, const Geom &g, int kind, int npanels,
                             const Panel *panels, const Col *cols, const unsigned char *tiles,
                             const float2 *cpl, float2 *work, int pc, int *err, int m,
-                            const int *nz) {
+                            const int *nz, int np) {
   if (npanels <= 0) return cudaSuccess;
   const bool tw = m > 0;
   TcShape t;
-  if (!tc_shape(g, kind, pc, &t, tw)) return cudaErrorInvalidValue;
+  if (!tc_shape(g, kind, pc, &t, tw, np)) return cudaErrorInvalidValue;
   if (kind == 0)
-    return tw ? tc_dispatch<0, true>(st, g, t, npanels, panels, cols, tiles, cpl, work, pc, err, m, nz)
-              : tc_dispatch<0, false>(st, g, t, npanels, panels, cols, tiles, cpl, work, pc, err, m, nz);
-  return tw ? tc_dispatch<1, true>(st, g, t, npanels, panels, cols, tiles, cpl, work, pc, err, m, nz)
-            : tc_dispatch<1, false>(st, g, t, npanels, panels, cols, tiles, cpl, work, pc, err, m, nz);
+    return tw ? tc_dispatch<0, true>(st, g, t, npanels, panels, cols, tiles, cpl, work, pc, err, m, nz, np)
+              : tc_dispatch<0, false>(st, g, t, npanels, panels, cols, tiles, cpl, work, pc, err, m, nz, np);
+  return tw ? tc_dispatch<1, true>(st, g, t, npanels, panels, cols, tiles, cpl, work, pc, err, m, nz, np)
+            : tc_dispatch<1, false>(st, g, t, npanels, panels, cols, tiles, cpl, work, pc, err, m, nz, np);
 }
 
-bool subst_tc_ok(const Geom &g, int kind, int pc, bool twisted) {
-  return tc_shape(g, kind, pc, nullptr, twisted);
+bool subst_tc_ok(const Geom &g, int kind, int pc, bool twisted, int np) {
+  return tc_shape(g, kind, pc, nullptr, twisted, np);
 }
 
 int tc_middle_block(const Geom &g) { return g.Ml >= 4 ? (g.Ml - 1) / 2 : 0; }

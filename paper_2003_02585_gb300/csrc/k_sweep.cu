@@ -20,10 +20,12 @@ __global__ void k_assemble(Geom g, Tables tb, const Col *__restrict__ cols,
                            typename Cx<R>::T *__restrict__ work, const double2 *__restrict__ b,
                            int with_source, const typename Cx<R>::T *__restrict__ traces,
                            long long trs_rhs, long long trs_sub, int nslots,
-                           long long slot_stride, int *__restrict__ nzflag) {
+                           long long slot_stride, int *__restrict__ nzflag,
+                           int *__restrict__ badrhs) {
   using C = typename Cx<R>::T;
   const Col c = cols[blockIdx.x];
   bool nz = false;   // any nonzero entry written (the local solve of a zero source is zero)
+  bool bad = false;  // a NaN or infinite source entry (its RHS is reported as NaN)
   C *x = work + (long long)c.slot * g.Nloc;
   int k[3];
   sub_index(g, c.sub, k);
@@ -48,8 +50,10 @@ __global__ void k_assemble(Geom g, Tables tb, const Col *__restrict__ cols,
         const int i0 = e % M0, r = e / M0, i1 = r % M1, i2 = r / M1;
         if (e < nloc && i0 >= lo[0] && i0 < hi[0] && i1 >= lo[1] && i1 < hi[1] &&
             (g.dim < 3 || (i2 >= lo[2] && i2 < hi[2]))) {
-          v[u] = to_c(bb[i0 + G0 * i1 + G01 * i2], C());
+          const double2 s = bb[i0 + G0 * i1 + G01 * i2];
+          v[u] = to_c(s, C());
           nz = nz || v[u].x != 0 || v[u].y != 0;
+          bad = bad || !isfinite(s.x) || !isfinite(s.y);
         }
       }
 #pragma unroll
@@ -83,6 +87,10 @@ __global__ void k_assemble(Geom g, Tables tb, const Col *__restrict__ cols,
   if (nzflag != nullptr) {
     const int any = __syncthreads_or(nz);
     if (threadIdx.x == 0) nzflag[c.slot] = any;
+  }
+  if (badrhs != nullptr) {
+    const int anybad = __syncthreads_or(bad);
+    if (threadIdx.x == 0 && anybad) atomicOr(badrhs + c.rhs, 1);
   }
 }
 
@@ -275,7 +283,7 @@ __device__ inline void step_arrive(unsigned *cnt, int s) {
     atomicAdd(cnt + s * kStepCounters + (blockIdx.x % kStepCounters), 1u);
   }
 }
-__device__ inline void step_wait(const unsigned *cnt, int s, int *err) {
+__device__ inline void step_wait(const unsigned *cnt, int s, int *err, unsigned limit) {
   if (threadIdx.x < 32) {
     // warp 0 polls the eight counters; the full-warp sum keeps every lane's exit decision
     // identical.  Once any wait has given up (err set) no later wait spins.
@@ -287,7 +295,7 @@ __device__ inline void step_wait(const unsigned *cnt, int s, int *err) {
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
       if (v >= gridDim.x) break;
       int stop = 0;
-      if (lane == 0) stop = (++spins > (1u << 20)) || *reinterpret_cast<volatile int *>(err) != 0;
+      if (lane == 0) stop = (++spins > limit) || *reinterpret_cast<volatile int *>(err) != 0;
       stop = __shfl_sync(0xffffffffu, stop, 0);
       if (stop) {
         if (lane == 0) atomicExch(err, 4);
@@ -466,7 +474,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
                    const int *__restrict__ lev_off, int nlev,
                    const typename Cx<R>::T *__restrict__ gmap, typename Cx<R>::T *__restrict__ gtr,
                    const typename Cx<R>::T *__restrict__ rawf, int nrhs, unsigned *cnt,
-                   int *__restrict__ err) {
+                   int *__restrict__ err, unsigned wait_limit) {
   using C = typename Cx<R>::T;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   C *Gs = reinterpret_cast<C *>(smem_raw);            // map slice [k][64 rows]
@@ -509,7 +517,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
       if (h1) trace_describe(g, p1, its[(s + 1) % 3], slot_stride);
     }
     __syncthreads();
-    if (v > 0) step_wait(cnt, v - 1, err);
+    if (v > 0) step_wait(cnt, v - 1, err, wait_limit);
     trace_gather<C>(its[s], gtr, vin2 + vb * 8 * kTraceSeg);
     cp_async_wait_all();
     for (int r = 0; pos(r) < Nv; ++r) {
@@ -733,10 +741,10 @@ cudaError_t launch_assemble(cudaStream_t st, const Geom &g, const Tables &tb, in
                             const Col *cols, typename Cx<R>::T *work, const double2 *b,
                             const double2 *, int with_source, const typename Cx<R>::T *traces,
                             long long trs_rhs, long long trs_sub, int nslots,
-                            long long slot_stride, int *nzflag) {
+                            long long slot_stride, int *nzflag, int *badrhs) {
   if (ncols <= 0) return cudaSuccess;
   k_assemble<R><<<ncols, 256, 0, st>>>(g, tb, cols, work, b, with_source, traces, trs_rhs,
-                                       trs_sub, nslots, slot_stride, nzflag);
+                                       trs_sub, nslots, slot_stride, nzflag, badrhs);
   return cudaGetLastError();
 }
 
@@ -783,7 +791,7 @@ cudaError_t launch_trace_sweeps(cudaStream_t st, const Geom &g, const int4 *hdr,
                                 int nitems, const int *lev_off, int nlevels,
                                 const typename Cx<R>::T *gmap, typename Cx<R>::T *gtr,
                                 const typename Cx<R>::T *rawf, int nrhs, unsigned *gbar, int *err,
-                                int ctas_per_sm) {
+                                int ctas_per_sm, unsigned wait_limit) {
   if (nitems <= 0 || nlevels <= 0) return cudaSuccess;
   const size_t smem = trace_smem_bytes(sizeof(typename Cx<R>::T), nlevels);
   static bool done[64] = {false};
@@ -809,7 +817,7 @@ cudaError_t launch_trace_sweeps(cudaStream_t st, const Geom &g, const int4 *hdr,
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, k_trace_sweeps<R>, g, hdr, cols, lev_off, nlevels, gmap, gtr,
-                            rawf, nrhs, gbar, err);
+                            rawf, nrhs, gbar, err, wait_limit);
 }
 
 size_t trace_counter_bytes(int nlevels) { return (size_t)nlevels * kStepCounters * sizeof(unsigned); }
@@ -906,7 +914,7 @@ cudaError_t launch_copy_local_back(cudaStream_t st, long long n, const typename 
   template cudaError_t launch_assemble<R>(cudaStream_t, const Geom &, const Tables &, int,     \
                                           const Col *, Cx<R>::T *, const double2 *,           \
                                           const double2 *, int, const Cx<R>::T *, long long,   \
-                                          long long, int, long long, int *);                    \
+                                          long long, int, long long, int *, int *);             \
   template cudaError_t launch_subst<R>(cudaStream_t, const Geom &, int, const Panel *,         \
                                        const Col *, const Cx<R>::T *, const Cx<R>::T *,        \
                                        Cx<R>::T *, int);                                        \
@@ -916,7 +924,7 @@ cudaError_t launch_copy_local_back(cudaStream_t st, long long n, const typename 
   template cudaError_t launch_trace_sweeps<R>(cudaStream_t, const Geom &, const int4 *,         \
                                               const int2 *, int, const int *, int,              \
                                               const Cx<R>::T *, Cx<R>::T *, const Cx<R>::T *,  \
-                                              int, unsigned *, int *, int);                     \
+                                              int, unsigned *, int *, int, unsigned);           \
   template cudaError_t launch_unit_traces<R>(cudaStream_t, const Geom &, const Tables &, int,  \
                                              int, Cx<R>::T *);                                  \
   template cudaError_t launch_raw_lines<R>(cudaStream_t, const Geom &, int, const Cx<R>::T *,  \

@@ -14,16 +14,18 @@
 // real-ified complex form: B = [b0_re | b0_im | b1_re | b1_im] (4 x 32 rows of the K-major B
 // operand), D1 = A0_re B + A1_re B[:64], D2 = A0_im B + A1_im B[:64].
 //
-// One CTA per SM, cooperative launch over the dataflow levels (the schedule and level counters
-// of k_trace_sweeps).  Warp roles:
+// One CTA per SM, cooperative launch; each CTA takes its units of every dataflow level (the
+// schedule of k_trace_sweeps) in level order, with no barrier between levels: a unit waits only
+// until the trace solves routed into its own slots have published (per-slot counters against
+// host-computed totals), so the levels overlap.  Warp roles:
 //   warps 0-3   epilogue: TMEM lane quarter = warp; row R of the tile per thread; forms the
 //               complex outputs of the 32 columns and adds them into the receivers' slots with
-//               vector reductions; arrives on the level counter after its level's units;
-//   warps 4-7   B producers: after the level barrier, load the unit's inputs from the trace
-//               slots (L1 bypassed: other CTAs wrote them), split them into pieces and store
-//               them in the canonical K-major layout of the ring slot;
-//   warp 8      A producer: streams the pre-split map tiles through the two-slot ring with bulk
-//               copies completed on the slot's mbarrier (independent of the levels, so it runs
+//               vector reductions; then publishes the unit on the receivers' counters;
+//   warps 4-7   B producers: once the unit's slots are complete, copy its inputs from the trace
+//               slots (cp.async, L1 bypassed: other CTAs wrote them) a few chunks ahead, split
+//               them into pieces and store them in the canonical K-major layout of the ring slot;
+//   warp 8      A producer: streams the pre-split map tiles through the four-slot ring with bulk
+//               copies completed on the slot's mbarrier (it depends on no trace, so it runs
 //               ahead);
 //   warp 9      MMA issuer (one thread) and owner of the tensor memory: two accumulator pairs,
 //               so that the epilogue of one unit runs under the MMAs of the next.
@@ -44,7 +46,15 @@ constexpr int kTtStep = 16384;     // bytes of one K-step of an A tile (4 comps 
 constexpr int kTtLB = 4 * kTtCols * 16 + 16;   // bytes per 16-byte K group of B (+16: banks)
 constexpr int kTtBStep = 2 * kTtLB;            // bytes of one K-step of B
 constexpr int kTtSlotBytes = kTtKS * (kTtStep + kTtBStep);
-constexpr int kTtThreads = 320;
+// raw inputs of a chunk (32 columns x up to 4 K-steps of 16 BF16 values, 8 bytes each), staged by
+// cp.async a few chunks ahead of their split into the B operand
+constexpr int kTtRawSlots = 3;
+constexpr int kTtRawBytes = kTtCols * kTtKS * 16 * 8;
+constexpr int kTtAhead = kTtRawSlots - 1;   // chunks in flight ahead of the one being split
+constexpr int kTtBWarps = 8;       // B-producer warps
+constexpr int kTtBThreads = 32 * kTtBWarps;
+constexpr int kTtAWarp = 4 + kTtBWarps, kTtMmaWarp = kTtAWarp + 1;
+constexpr int kTtThreads = 32 * (kTtMmaWarp + 1);
 constexpr int kTtTmemCols = 512;   // two accumulator pairs of 8 x 32 FP32 columns
 
 }  // namespace
@@ -68,7 +78,7 @@ bool tt_shape(const Geom &g, int kind, TtShape *s) {
   t.KP = off;
   t.rt_bytes = (long long)(t.KP / t.KE) * kTtStep;
   t.fac_bytes = (long long)t.RT * t.rt_bytes;
-  t.smem = (size_t)kTtSlots * kTtSlotBytes + 1024;
+  t.smem = (size_t)kTtSlots * kTtSlotBytes + (size_t)kTtRawSlots * kTtRawBytes + 1024;
   if (t.smem > 227 * 1024) return false;
   if (s) *s = t;
   return true;
@@ -223,7 +233,8 @@ __global__ void __launch_bounds__(kTtThreads, 1)
     k_trace_tc(Geom g, TtShape t, const int4 *__restrict__ units, const int *__restrict__ ucols,
                const int *__restrict__ lev_off, int nlev, const unsigned char *__restrict__ tiles,
                const int *__restrict__ route, float2 *__restrict__ gtr,
-               const float2 *__restrict__ rawf, int nrhs, unsigned *cnt, int *__restrict__ err) {
+               const float2 *__restrict__ rawf, int nrhs, unsigned *ready,
+               const unsigned *__restrict__ need, int *__restrict__ err, unsigned wait_limit) {
   constexpr uint32_t kIdN4 = KIND == 0 ? umma::idesc_tf32(128, 4 * kTtCols)
                                        : umma::idesc_bf16(128, 4 * kTtCols);
   constexpr uint32_t kIdN2 = KIND == 0 ? umma::idesc_tf32(128, 2 * kTtCols)
@@ -234,6 +245,7 @@ __global__ void __launch_bounds__(kTtThreads, 1)
   __shared__ uint64_t full[kTtSlots], empty[kTtSlots], accf[2], acce[2], drain;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
+  __shared__ int ready_flag[2];   // B producers: the last input check (alternating)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int G = (int)gridDim.x, b = (int)blockIdx.x;
   auto pos = [&](int r) { return r * G + ((r & 1) ? G - 1 - b : b); };
@@ -244,11 +256,14 @@ __global__ void __launch_bounds__(kTtThreads, 1)
   };
   auto slotA = [&](int s) { return smem_raw + (size_t)s * kTtSlotBytes; };
   auto slotB = [&](int s) { return smem_raw + (size_t)s * kTtSlotBytes + kTtKS * kTtStep; };
+  auto slotR = [&](int s) {
+    return smem_raw + (size_t)kTtSlots * kTtSlotBytes + (size_t)s * kTtRawBytes;
+  };
   const long long slot_stride = (long long)nrhs * g.nsub * g.T;
 
   if (tid == 0) {
     for (int s = 0; s < kTtSlots; ++s) {
-      mbar_init(&full[s], 1 + 4);
+      mbar_init(&full[s], 1 + kTtBWarps);
       mbar_init(&empty[s], 1);
     }
     for (int q = 0; q < 2; ++q) {
@@ -259,7 +274,7 @@ __global__ void __launch_bounds__(kTtThreads, 1)
     abort_flag = 0;
     mbar_init_fence();
   }
-  if (warp == 9) {
+  if (warp == kTtMmaWarp) {
     umma::tmem_alloc(&tmem_base, kTtTmemCols);
     umma::tmem_relinquish();
   }
@@ -268,7 +283,7 @@ __global__ void __launch_bounds__(kTtThreads, 1)
   umma::fence_after_sync();
   const uint32_t tmem = tmem_base;
 
-  if (warp == 8) {
+  if (warp == kTtAWarp) {
     // ---------------- A producer: the map tiles of every unit's chunks, in unit order
     if (lane == 0) {
       int ci = 0;                 // chunks issued
@@ -302,7 +317,7 @@ __global__ void __launch_bounds__(kTtThreads, 1)
       for (int s = 0; s < kTtSlots; ++s)
         if (last[s] >= 0 && !mbar_wait(&full[s], (last[s] / kTtSlots) & 1)) atomicExch(err, 22);
     }
-  } else if (warp == 9) {
+  } else if (warp == kTtMmaWarp) {
     // ---------------- MMA issuer
     if (lane == 0) {
       const uint32_t lbo_a = 128u * 16u;
@@ -358,70 +373,152 @@ __global__ void __launch_bounds__(kTtThreads, 1)
     }
   } else if (warp >= 4) {
     // ---------------- B producers: inputs of every unit's chunks, split into pieces
-    const int pt = tid - 128;   // 0..127
-    int ci = 0;
-    for (int v = 0; v < nlev; ++v) {
-      const int base = __ldg(lev_off + v), Nv = __ldg(lev_off + v + 1) - base;
-      if (pos(0) >= Nv) continue;
-      if (v > 0) {
-        // the level barrier: every CTA has finished (and published) level v - 1
-        if (warp == 4) {
+    // Dataflow instead of level barriers: before the first copy of a unit's inputs, warp 4
+    // waits until every trace solve routed into the unit's slots (l, X) has published
+    // (ready[l nsub + X] == need[l nsub + X]).  Each chunk's raw inputs are copied into a
+    // staging slot by cp.async (L1 bypassed: other CTAs wrote them) kTtAhead chunks before they
+    // are split into the ring slot, across unit and level boundaries.  Thread pt owns the pairs
+    // of consecutive inputs p = pt + 128 i of every chunk (column p / (nk / 2), inputs
+    // 2 (p % (nk / 2)) and the next), copies them and splits them itself, so no barrier is
+    // needed between the copy and the split.
+    const int pt = tid - 128;   // 0 .. kTtBThreads - 1
+    struct Cur {
+      int v, base, Nv, r, c, nch;
+      TtUnit u;
+    };
+    auto seek = [&](Cur &k, bool next) {
+      if (next) ++k.c;
+      for (;;) {
+        if (k.v >= nlev) return false;
+        if (pos(k.r) >= k.Nv) {
+          if (++k.v >= nlev) return false;
+          k.base = __ldg(lev_off + k.v);
+          k.Nv = __ldg(lev_off + k.v + 1) - k.base;
+          k.r = 0;
+          k.c = 0;
+          continue;
+        }
+        if (k.c == 0) {
+          k.u = tt_unit(units, k.base + pos(k.r));
+          k.nch = tt_nchunks(t, k.u.kmask);
+        }
+        if (k.c < k.nch) return true;
+        ++k.r;
+        k.c = 0;
+      }
+    };
+    // are the unit's inputs complete (every producer routed into its slots has published)?  One
+    // thread polls, `block` = until they are (bounded) or once; the answer goes to all 128
+    // producer threads through a shared flag (two, alternating, so that a reader of one check
+    // never races the next write)
+    int check_no = 0;
+    auto inputs_ready = [&](const TtUnit &u, bool block) {
+      const int fl = check_no++ & 1;
+      if (warp == 4 && lane == 0) {
+        int ok = 1;
+        int prevX = -1;
+        for (int c = 0; c < u.ncol && ok; ++c) {
+          const int X = __ldg(ucols + u.col0 + c) % g.nsub;
+          if (X == prevX) continue;
+          prevX = X;
+          const long long sl = (long long)u.l * g.nsub + X;
+          const unsigned want = __ldg(need + sl);
           uint32_t spins = 0;
-          for (;;) {
-            unsigned x = lane < kStepCounters ? ld_acquire_gpu(cnt + (v - 1) * kStepCounters + lane) : 0u;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-            if (x >= (unsigned)G) break;
-            int stop = 0;
-            if (lane == 0)
-              stop = (++spins > (1u << 20)) || *reinterpret_cast<volatile int *>(err) != 0;
-            stop = __shfl_sync(0xffffffffu, stop, 0);
-            if (stop) {
-              if (lane == 0) { atomicExch(err, 4); *reinterpret_cast<volatile int *>(&abort_flag) = 1; }
-              break;
+          while (ld_acquire_gpu(ready + sl) < want) {
+            if (!block) { ok = 0; break; }
+            if (++spins > wait_limit || *reinterpret_cast<volatile int *>(err) != 0) {
+              atomicExch(err, 4);
+              *reinterpret_cast<volatile int *>(&abort_flag) = 1;
+              break;   // go on (results are wrong, the host reports DDS_ETIMEOUT)
             }
-            __nanosleep(64);
+            __nanosleep(32);
           }
         }
-        named_sync(2, 128);
+        ready_flag[fl] = ok;
       }
-      for (int r = 0; pos(r) < Nv; ++r) {
-        const TtUnit u = tt_unit(units, base + pos(r));
-        const int nch = tt_nchunks(t, u.kmask);
-        for (int c = 0; c < nch; ++c, ++ci) {
-          const int s = ci % kTtSlots;
-          if (ci >= kTtSlots && !aborted()) {
-            // (after an abort no wait is made: the MMAs may have stopped consuming)
-            int okw = 1;
-            if (lane == 0) okw = mbar_wait(&empty[s], ((ci / kTtSlots) - 1) & 1) ? 1 : 0;
-            okw = __shfl_sync(0xffffffffu, okw, 0);
-            if (!okw && lane == 0) fail(26);
-          }
-          int d, t0, nks;
-          tt_chunk(t, u.kmask, c, d, t0, nks);
-          if (!aborted()) {
-            unsigned char *sB = slotB(s);
-            const int nk = nks * t.KE;                 // K values of the chunk
-            const int k0 = t0 * t.KE;                  // first K value within the side
-            const int lim = 2 * g.Lt[d];
-            for (int idx = pt; idx < kTtCols * nk; idx += 128) {
-              const int c2 = idx / nk, kk = idx - c2 * nk;
-              float2 val = make_float2(0.f, 0.f);
-              if (c2 < u.ncol && k0 + kk < lim) {
-                const int col = __ldg(ucols + u.col0 + c2);
-                val = __ldcg(gtr + (long long)u.l * slot_stride + (long long)col * g.T +
-                             g.toff[d] + k0 + kk);
-              }
-              tt_put_b<KIND>(sB, kk, c2, val);
-            }
-          }
-          fence_proxy_async();   // the generic writes of B before the MMAs' async reads
-          umma::fence_before_sync();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&full[s]);
-        }
+      named_sync(2, kTtBThreads);
+      return ready_flag[fl] != 0;
+    };
+    auto stage = [&](const Cur &k, int slot) {
+      const TtUnit &u = k.u;
+      int d, t0, nks;
+      tt_chunk(t, u.kmask, k.c, d, t0, nks);
+      const int half = nks * t.KE / 2;            // input pairs per column
+      const int k0 = t0 * t.KE, lim = 2 * g.Lt[d];
+      const float2 *src0 = gtr + (long long)u.l * slot_stride + g.toff[d] + k0;
+      unsigned char *raw = slotR(slot);
+      for (int q = pt; q < kTtCols * half; q += kTtBThreads) {
+        const int c2 = q / half, kk = 2 * (q - c2 * half);
+        const bool live = c2 < u.ncol && k0 + kk < lim;
+        const int col = live ? __ldg(ucols + u.col0 + c2) : 0;
+        cp_async16(raw + q * 16, live ? (const void *)(src0 + (long long)col * g.T + kk)
+                                      : (const void *)gtr, live ? 16u : 0u);
       }
+    };
+    Cur P{}, S{};
+    if (nlev > 0) {
+      P.base = S.base = __ldg(lev_off);
+      P.Nv = S.Nv = __ldg(lev_off + 1) - P.base;
     }
+    bool havep = nlev > 0 && seek(P, false);
+    bool haves = nlev > 0 && seek(S, false);
+    // The copy cursor P stages chunks up to kTtAhead ahead of the split cursor S.  It enters a new
+    // unit only once that unit's inputs are complete, without waiting, except when S needs the
+    // chunk now (then nothing earlier is pending in these threads, so the wait cannot hold up the
+    // trace solves it waits for).  Each iteration commits one cp.async group; gsl[slot] is the
+    // group that staged the chunk held in a staging slot.
+    int staged = 0, groups = 0;
+    int gsl[kTtRawSlots];
+#pragma unroll
+    for (int i = 0; i < kTtRawSlots; ++i) gsl[i] = 0;
+    for (int ci = 0; haves; ++ci) {
+      while (havep && staged < ci + kTtRawSlots) {   // the slot's previous chunk is split
+        if (P.c == 0 && !inputs_ready(P.u, staged == ci)) break;
+        const int rs = staged % kTtRawSlots;
+        stage(P, rs);
+        gsl[rs] = groups;
+        ++staged;
+        havep = seek(P, true);
+      }
+      cp_async_commit();
+      ++groups;
+      // this thread's copies of chunk ci have landed: at most (groups committed after its
+      // group) groups may still be pending
+      switch (groups - 1 - gsl[ci % kTtRawSlots]) {
+        case 0: cp_async_wait_group<0>(); break;
+        case 1: cp_async_wait_group<1>(); break;
+        case 2: cp_async_wait_group<2>(); break;
+        case 3: cp_async_wait_group<3>(); break;
+        default: cp_async_wait_group<4>(); break;
+      }
+      const int s = ci % kTtSlots;
+      if (ci >= kTtSlots && !aborted()) {
+        // (after an abort no wait is made: the MMAs may have stopped consuming)
+        int okw = 1;
+        if (lane == 0) okw = mbar_wait(&empty[s], ((ci / kTtSlots) - 1) & 1) ? 1 : 0;
+        okw = __shfl_sync(0xffffffffu, okw, 0);
+        if (!okw && lane == 0) fail(26);
+      }
+      if (!aborted()) {
+        int d, t0, nks;
+        tt_chunk(t, S.u.kmask, S.c, d, t0, nks);
+        const int half = nks * t.KE / 2;
+        const unsigned char *raw = slotR(ci % kTtRawSlots);
+        unsigned char *sB = slotB(s);
+        for (int q = pt; q < kTtCols * half; q += kTtBThreads) {
+          const int c2 = q / half, kk = 2 * (q - c2 * half);
+          const float4 w = *reinterpret_cast<const float4 *>(raw + q * 16);
+          tt_put_b<KIND>(sB, kk, c2, make_float2(w.x, w.y));
+          tt_put_b<KIND>(sB, kk + 1, c2, make_float2(w.z, w.w));
+        }
+      }
+      fence_proxy_async();   // the generic writes of B before the MMAs' async reads
+      umma::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&full[s]);
+      haves = seek(S, true);
+    }
+    cp_async_wait_all();   // nothing stays in flight
   } else {
     // ---------------- epilogue: row R of the unit's tile, every column
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
@@ -479,37 +576,64 @@ __global__ void __launch_bounds__(kTtThreads, 1)
           if (lane == 0) mbar_arrive(&acce[q]);
           ++mi;
         }
-        if (dout >= 0 && lp >= 0 && !aborted()) {
-          float2 *slot = gtr + (long long)lp * slot_stride + dst_off;
+        // the raw own-source lines of this row (first sweep), then rows in pairs: lanes 2j and
+        // 2j + 1 hold rows R and R + 1 of one side (sides have an even number of rows from an
+        // even offset), so each exchanges one value per column pair with its partner and adds
+        // two rows of one column with one 16-byte vector reduction
+        const bool live = dout >= 0 && lp >= 0 && !aborted();
+        if (u.raw && dout >= 0) {
 #pragma unroll
           for (int c = 0; c < kTtCols; ++c) {
             if (c < u.ncol) {
-              const int col = __ldg(ucols + u.col0 + c);
-              const int X = col % g.nsub, rhs = col - X;   // rhs * nsub
-              const int Y = sub_neighbour(g, X, dout);
-              if (Y >= 0) {
-                float2 val = out[c];
-                if (u.raw) {
-                  const float2 w = __ldg(rawf + (long long)col * g.T + R);
-                  val = make_float2(val.x + w.x, val.y + w.y);
-                }
-                red_add_f2(slot + (long long)(rhs + Y) * g.T, val);
-              }
+              const float2 w = __ldg(rawf + (long long)__ldg(ucols + u.col0 + c) * g.T + R);
+              out[c] = make_float2(out[c].x + w.x, out[c].y + w.y);
             }
           }
         }
-      }
-      // level v done on this CTA: publish (every CTA arrives, with or without units)
-      named_sync(1, 128);
-      if (tid == 0) {
+        const bool odd = lane & 1;
+        float2 *slot = gtr + (long long)(lp >= 0 ? lp : 0) * slot_stride + dst_off - (odd ? 1 : 0);
+#pragma unroll
+        for (int c = 0; c < kTtCols; c += 2) {
+          const float2 mine = odd ? out[c + 1] : out[c];
+          const float2 send = odd ? out[c] : out[c + 1];
+          const float2 got = make_float2(__shfl_xor_sync(0xffffffffu, send.x, 1),
+                                         __shfl_xor_sync(0xffffffffu, send.y, 1));
+          const int cc = c + (odd ? 1 : 0);
+          if (live && cc < u.ncol) {
+            const int col = __ldg(ucols + u.col0 + cc);
+            const int X = col % g.nsub, rhs = col - X;   // rhs * nsub
+            const int Y = sub_neighbour(g, X, dout);
+            if (Y >= 0) {
+              const float4 v = odd ? make_float4(got.x, got.y, mine.x, mine.y)
+                                   : make_float4(mine.x, mine.y, got.x, got.y);
+              red_add_f4(reinterpret_cast<float4 *>(slot + (long long)(rhs + Y) * g.T), v);
+            }
+          }
+        }
+        // each thread's reductions are performed before the unit is published
         __threadfence();
-        atomicAdd(cnt + v * kStepCounters + (b % kStepCounters), 1u);
+        // publish the unit: one count per (receiving slot, subdomain of the tile, side whose
+        // rows lie in this row tile), as the host counted them into need[]
+        named_sync(1, 128);
+        if (tid == 0) {
+          int prevX = -1;
+          for (int c = 0; c < u.ncol; ++c) {
+            const int X = __ldg(ucols + u.col0 + c) % g.nsub;
+            if (X == prevX) continue;
+            prevX = X;
+            for (int d = 0; d < g.nsides; ++d) {
+              if (g.toff[d] >= 128 * (u.rt + 1) || g.toff[d] + 2 * g.Lt[d] <= 128 * u.rt) continue;
+              const int lq = __ldg(route + u.l * 6 + d), Y = sub_neighbour(g, X, d);
+              if (lq >= 0 && Y >= 0) atomicAdd(ready + (long long)lq * g.nsub + Y, 1u);
+            }
+          }
+        }
       }
     }
   }
   umma::fence_before_sync();
   __syncthreads();
-  if (warp == 9) {
+  if (warp == kTtMmaWarp) {
     umma::fence_after_sync();
     umma::tmem_dealloc(tmem, kTtTmemCols);
   }
@@ -518,7 +642,8 @@ __global__ void __launch_bounds__(kTtThreads, 1)
 cudaError_t launch_trace_tc(cudaStream_t st, const Geom &g, int kind, const int4 *units,
                             const int *ucols, int nunits, const int *lev_off, int nlevels,
                             const unsigned char *tiles, const int *route, float2 *gtr,
-                            const float2 *rawf, int nrhs, unsigned *gbar, int *err) {
+                            const float2 *rawf, int nrhs, unsigned *ready, const unsigned *need,
+                            int nslots, int *err, unsigned wait_limit) {
   if (nunits <= 0 || nlevels <= 0) return cudaSuccess;
   TtShape t;
   if (!tt_shape(g, kind, &t)) return cudaErrorInvalidValue;
@@ -533,7 +658,7 @@ cudaError_t launch_trace_tc(cudaStream_t st, const Geom &g, int kind, const int4
                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_tc<1>, kTtThreads, t.smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  e = cudaMemsetAsync(gbar, 0, (size_t)nlevels * kStepCounters * sizeof(unsigned), st);
+  e = cudaMemsetAsync(ready, 0, (size_t)nslots * sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)nsm);   // one CTA per SM: it owns the whole tensor memory
@@ -547,9 +672,9 @@ cudaError_t launch_trace_tc(cudaStream_t st, const Geom &g, int kind, const int4
   cfg.numAttrs = 1;
   if (kind == 0)
     return cudaLaunchKernelEx(&cfg, k_trace_tc<0>, g, t, units, ucols, lev_off, nlevels, tiles,
-                              route, gtr, rawf, nrhs, gbar, err);
+                              route, gtr, rawf, nrhs, ready, need, err, wait_limit);
   return cudaLaunchKernelEx(&cfg, k_trace_tc<1>, g, t, units, ucols, lev_off, nlevels, tiles,
-                            route, gtr, rawf, nrhs, gbar, err);
+                            route, gtr, rawf, nrhs, ready, need, err, wait_limit);
 }
 
 }  // namespace dds

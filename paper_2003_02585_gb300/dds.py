@@ -27,7 +27,7 @@ EXPORTS = ["dds_setup", "dds_sweep", "dds_sweep_strip", "dds_solve", "dds_apply"
            "dds_destroy", "dds_profile", "dds_profile_read", "dds_local_solve_noalloc",
            "dds_server_create", "dds_server_submit", "dds_server_step", "dds_server_poll",
            "dds_server_destroy", "dds_work_per_ddm", "dds_autotune", "dds_set_zero_skip",
-           "dds_local_solve_counts"]
+           "dds_local_solve_counts", "dds_set_memory_budget", "dds_set_wait_limit"]
 KERNEL_KINDS = {"assemble": 0, "subst": 1, "extract": 2, "trace_step": 3, "krylov": 4,
                 "other": 5}
 
@@ -50,7 +50,8 @@ class _Info(ctypes.Structure):
     _fields_ = [("G", ctypes.c_int * 3), ("M", ctypes.c_int * 3), ("n_sub", ctypes.c_int),
                 ("n_factors", ctypes.c_int), ("trace_len", ctypes.c_int), ("plan", ctypes.c_int),
                 ("factor_bytes", ctypes.c_longlong), ("setup_seconds", ctypes.c_double),
-                ("trace_kernel", ctypes.c_int), ("subst_kernel", ctypes.c_int)]
+                ("device_bytes", ctypes.c_longlong), ("trace_kernel", ctypes.c_int),
+                ("subst_kernel", ctypes.c_int)]
 
 
 _lib = None
@@ -98,6 +99,8 @@ def load(path: str = LIB_PATH):
     lib.dds_server_destroy.restype = None
     lib.dds_profile.argtypes = [vp, ctypes.c_int]
     lib.dds_set_zero_skip.argtypes = [vp, ctypes.c_int]
+    lib.dds_set_memory_budget.argtypes = [vp, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)]
+    lib.dds_set_wait_limit.argtypes = [vp, ctypes.c_longlong]
     lib.dds_local_solve_counts.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong),
                                            ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
     lib.dds_profile_read.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
@@ -106,7 +109,7 @@ def load(path: str = LIB_PATH):
                  "dds_set_stream", "dds_get_info", "dds_profile", "dds_profile_read",
                  "dds_local_solve_noalloc", "dds_server_create", "dds_server_submit",
                  "dds_server_step", "dds_server_poll", "dds_set_zero_skip",
-                 "dds_local_solve_counts"]:
+                 "dds_local_solve_counts", "dds_set_memory_budget", "dds_set_wait_limit"]:
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -310,23 +313,27 @@ class Context:
         return {"G": list(inf.G), "M": list(inf.M), "n_sub": inf.n_sub,
                 "n_factors": inf.n_factors, "trace_len": inf.trace_len, "plan": inf.plan,
                 "factor_bytes": inf.factor_bytes, "setup_seconds": inf.setup_seconds,
-                "trace_kernel": inf.trace_kernel, "subst_kernel": inf.subst_kernel}
+                "trace_kernel": inf.trace_kernel, "subst_kernel": inf.subst_kernel,
+                "device_bytes": inf.device_bytes}
 
     def launches(self):
         return int(self._lib.dds_kernel_launches(self._h))
 
     def autotune(self, nrhs, rounds=1):
         """Time the tunable launch shapes (dds_autotune) and keep the fastest; returns
-        {"panel_width", "trace_ctas_per_sm", "table": [(width, ctas, ms per DDM application)]};
+        {"panel_width", "trace_ctas_per_sm", "panels_per_cta",
+         "table": [(width, panels per CTA, trace CTAs per SM, ms per DDM application)]};
         trace_ctas_per_sm = 0 is the tensor-core trace kernel."""
         n = ctypes.c_int(0)
-        table = (ctypes.c_double * (3 * 16))()
-        best = (ctypes.c_int * 2)()
-        self._check(self._lib.dds_autotune(self._h, int(nrhs), int(rounds), 16, ctypes.byref(n),
+        cap = 32
+        table = (ctypes.c_double * (4 * cap))()
+        best = (ctypes.c_int * 3)()
+        self._check(self._lib.dds_autotune(self._h, int(nrhs), int(rounds), cap, ctypes.byref(n),
                                            table, best))
-        rows = [(int(table[3 * i]), int(table[3 * i + 1]), float(table[3 * i + 2]))
-                for i in range(min(n.value, 16))]
-        return {"panel_width": int(best[0]), "trace_ctas_per_sm": int(best[1]), "table": rows}
+        rows = [(int(table[4 * i]), int(table[4 * i + 1]), int(table[4 * i + 2]),
+                 float(table[4 * i + 3])) for i in range(min(n.value, cap))]
+        return {"panel_width": int(best[0]), "trace_ctas_per_sm": int(best[1]),
+                "panels_per_cta": int(best[2]), "table": rows}
 
     def work_per_ddm(self, nrhs, rounds=1):
         """(substitution flops, trace-map flops) of one DDM application (dds_work_per_ddm)."""
@@ -349,6 +356,16 @@ class Context:
             self._check(self._lib.dds_profile_read(self._h, k, ctypes.byref(n), ctypes.byref(ms)))
             out[name] = (int(n.value), float(ms.value))
         return out
+
+    def set_memory_budget(self, nbytes):
+        """Cap the device memory of this context (dds_set_memory_budget); returns bytes held."""
+        used = ctypes.c_longlong(0)
+        self._check(self._lib.dds_set_memory_budget(self._h, int(nbytes), ctypes.byref(used)))
+        return int(used.value)
+
+    def set_wait_limit(self, polls=0):
+        """Polls of a level-completion wait before it gives up (dds_set_wait_limit; 0 = default)."""
+        self._check(self._lib.dds_set_wait_limit(self._h, int(polls)))
 
     def set_zero_skip(self, enable=True):
         """Zero-work skipping of local problems with a zero right-hand side (dds_set_zero_skip)."""

@@ -415,8 +415,10 @@ def test_autotune_picks_a_valid_shape_and_keeps_results():
     before = ctx.sweep(fe, 2).cpu().numpy()
     t = ctx.autotune(3, 2)
     assert t["panel_width"] in (8, 16, 32) and t["trace_ctas_per_sm"] in (0, 1, 2)
-    assert {row[1] for row in t["table"]} == {0, 1, 2}   # CUDA-core 1/SM, 2/SM, tensor cores
-    assert len(t["table"]) >= 2 and all(row[2] > 0 for row in t["table"])
+    assert t["panels_per_cta"] in (1, 2)
+    assert {row[2] for row in t["table"]} == {0, 1, 2}   # CUDA-core 1/SM, 2/SM, tensor cores
+    assert {row[1] for row in t["table"]} == {1, 2}      # one or two panels per CTA
+    assert len(t["table"]) >= 2 and all(row[3] > 0 for row in t["table"])
     after = ctx.sweep(fe, 2).cpu().numpy()
     for r in range(3):
         assert _rel(after[r], before[r]) < 1e-5
