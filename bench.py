@@ -269,7 +269,8 @@ def fp64_check(args, wl, R, f_dev, u_mixed, stream, flush):
     err = [float(torch.linalg.vector_norm(u_mixed[r] - u64[r]) / torch.linalg.vector_norm(u64[r]))
            for r in range(R)]
     steps = args.steps if args.fp64_steps is None else args.fp64_steps
-    for _ in range(args.warmup if steps > 0 else 0):
+    fp64_warm = args.warmup if args.fp64_warmup is None else args.fp64_warmup
+    for _ in range(fp64_warm if steps > 0 else 0):
         ctx64.solve(f_dev, tol=args.tol, maxit=args.maxit, rounds=wl.rounds)
     torch.cuda.synchronize()
     fp64_ms, its = [], []
@@ -364,6 +365,10 @@ def short_measure(args, name, stream, flush):
     out = {"workload": workload_desc(name), "name": name, "value": R * len(ms) / (sum(ms) / 1e3),
            "unit": "RHS/s", "ms_per_step": sum(ms) / len(ms), "steps": len(ms),
            "fgmres_iterations": sorted(set(its)), "setup_seconds": ctx.info()["setup_seconds"]}
+    if name.startswith("table5_"):
+        N = int(name.split("_")[1])
+        out["paper"] = {"fgmres_iterations": TABLE5_PAPER[N][0], "solve_s": TABLE5_PAPER[N][1],
+                        "hardware": "the paper's CPU cluster, one core per subdomain"}
     ctx.close()
     if len(wl.n) == 2 and not args.no_fp64:
         c64 = dds.Context(wl.n, wl.h, wl.omega, wl.c, wl.parts, wl.pml_cells, wl.pml_strength,
@@ -395,15 +400,22 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     lbuild.build()
-    wl = synth.workload(args.workload)
+    wl = synth.workload(args.workload, args.nrhs)
     if args.rounds is not None:
         wl.rounds = args.rounds
     R = wl.f.shape[0]
 
     ctx = dds.Context(wl.n, wl.h, wl.omega, wl.c, wl.parts, wl.pml_cells, wl.pml_strength,
                       precision=args.precision, plan=args.plan)
-    # launch shapes picked by measurement on this workload (set-up work, outside the timing)
-    tuned = ctx.autotune(R, wl.rounds) if not args.no_autotune else None
+    # launch shapes picked by measurement on this workload (set-up work, outside the timing), or
+    # pinned by --shape (panel width, panels per CTA, trace kernel)
+    tuned = None
+    if args.shape:
+        pw, npc, tk = (int(v) for v in args.shape.split(","))
+        ctx.set_launch_shape(pw, npc, tk)
+        tuned = {"panel_width": pw, "panels_per_cta": npc, "trace_ctas_per_sm": tk, "table": []}
+    elif not args.no_autotune:
+        tuned = ctx.autotune(R, wl.rounds)
     info = ctx.info()
     f_host = ctx.extend(wl.f)
     f_dev = torch.from_numpy(f_host).to(dev)
@@ -498,7 +510,7 @@ def run_gpu(args):
         return lat[min(len(lat) - 1, int(math.ceil(p / 100.0 * len(lat))) - 1)]
 
     also = []
-    for name in [w for w in args.also.split(",") if w and w != args.workload]:
+    for name in [w for w in args.also.split(",") if w and w != "none" and w != args.workload]:
         also.append(short_measure(args, name, stream, flush))
 
     # the long, descriptive keys first; the headline evidence (roofline, accuracy, FP64
@@ -529,7 +541,8 @@ def run_gpu(args):
         "accuracy": {"max_rel_l2_vs_fp64_gpu": max(err), "fp64_reference_tol": 1e-10,
                      "fgmres_iterations": sorted(set(iters_seen))},
         "fp64_comparator": {"value": fp64_value, "unit": "RHS/s", "steps": len(fp64_ms),
-                            "warmup": args.warmup if fp64_ms else 0, "spread": fp64_spread,
+                            "warmup": (args.warmup if args.fp64_warmup is None else args.fp64_warmup)
+                                      if fp64_ms else 0, "spread": fp64_spread,
                             "fgmres_iterations": fp64_its,
                             "what": "same plan, factors and batching in FP64 (plain FP64 GPU "
                                     "sweep + FP64 FGMRES), same timing protocol"},
@@ -758,14 +771,24 @@ def main():
                     help="partitions N of the Table 5 series (--workload table5)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch shapes instead of timing the candidates")
+    ap.add_argument("--shape", default=None,
+                    help="pin the launch shapes instead of autotuning: 'panel width,panels per "
+                         "CTA,trace kernel' (trace kernel 0 = tensor cores, 1/2 = CUDA cores)")
     ap.add_argument("--variants", default="mixed_bf16,mixed_fp32",
                     help="other sweep variants timed the same way and reported beside the line")
     ap.add_argument("--rounds", type=int, default=None,
                     help="DDM rounds per preconditioner application (default: the workload's)")
     ap.add_argument("--fp64-steps", type=int, default=None,
                     help="timed steps of the FP64 comparator (default: --steps)")
-    ap.add_argument("--also", default="const2d_640",
-                    help="other workloads measured briefly and reported beside the headline")
+    ap.add_argument("--fp64-warmup", type=int, default=None,
+                    help="warm-up solves of the FP64 comparator (default: --warmup; its solve to "
+                         "1e-10 for the accuracy check precedes them)")
+    ap.add_argument("--nrhs", type=int, default=None,
+                    help="right-hand sides of the workload (default: its own count; smaller "
+                         "counts make the small cases the profiler captures)")
+    ap.add_argument("--also", default="const2d_640,table5_2,table5_4",
+                    help="other workloads measured briefly and reported beside the headline "
+                         "('none' for none)")
     ap.add_argument("--also-steps", type=int, default=5)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--profile-steps", type=int, default=2)

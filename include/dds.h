@@ -176,12 +176,19 @@ dds_status dds_local_solve_noalloc(dds_ctx *ctx, int sub, const void *b, int nrh
  * slots, applies ONE batched DDM application (`rounds` rounds) to the current Krylov vector of
  * every active slot, completes that iteration's FP64 Arnoldi step per slot, and retires slots
  * whose relative residual is below tol (or that reached maxit).  Requests submitted while others
- * are in flight therefore join at the next iteration.  Slot memory ((2 maxit + 3) fields per
- * slot) is allocated by dds_server_create; max_slots is the admission limit. */
+ * are in flight therefore join at the next iteration.  Slot memory ((2 maxit + 5) fields per
+ * slot, and the slot's columns of the batched DDM's work buffers) is allocated by
+ * dds_server_create, which admits by device memory: it takes as many slots as fit in the room
+ * the context's budget leaves (dds_set_memory_budget; without a budget, 90% of the device's
+ * free memory), at most max_slots, and returns DDS_ENOMEM if not even one fits.  The slot
+ * count is the admission limit (dds_server_slots).  Destroy a server before its context. */
 typedef struct dds_server dds_server;
 
 dds_status dds_server_create(dds_ctx *ctx, int max_slots, double tol, int maxit, int rounds,
                              dds_server **out);
+
+/* slots of a server (its admission limit) */
+int dds_server_slots(const dds_server *srv);
 
 /* queue one source field f (global extended grid, complex double, host or device); tag is
  * returned with its solution.  The field is copied before the call returns. */
@@ -222,6 +229,14 @@ long long dds_kernel_launches(const dds_ctx *ctx);
  * Not part of the paper: it picks block and panel tile shapes by measurement. */
 dds_status dds_autotune(dds_ctx *ctx, int nrhs, int rounds, int max_entries, int *n_entries,
                         double *table, int *best);
+
+/* dds_set_launch_shape -- set the tunable launch shapes directly (the values dds_autotune
+ * chooses, so that a measured choice can be pinned): panel_width 8, 16 or 32 (0 = automatic)
+ * and panels_per_cta 1 or 2 of the tensor-core substitutions, trace_kernel 0 (tensor cores) or
+ * 1 / 2 (CUDA cores, CTAs per SM).  DDS_EINVAL for a shape this context cannot run.  Drops cached
+ * plans and graphs. */
+dds_status dds_set_launch_shape(dds_ctx *ctx, int panel_width, int panels_per_cta,
+                                int trace_kernel);
 
 /* dds_work_per_ddm -- algorithmic floating-point work of one DDM application (Algorithm 2.1 /
  * 4.1, `rounds` rounds of 2^n sweeps) for nrhs right-hand sides, computed on the host:

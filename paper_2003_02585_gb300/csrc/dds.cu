@@ -5,6 +5,7 @@
 // line-block coefficients, routing, step schedules) and drives the launches.
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <complex>
@@ -30,7 +31,8 @@ namespace {
 // Device bytes held on behalf of one context and its cap (0 = none).  Allocations made while a
 // context's call runs (inside its Busy guard, or its set-up) count against that context.
 struct MemAcct {
-  size_t used = 0, budget = 0;
+  std::atomic<size_t> used{0};   // (a server may release its slots from another thread)
+  size_t budget = 0;
 };
 thread_local MemAcct *tl_acct = nullptr;
 
@@ -2055,6 +2057,36 @@ dds_status dds_profile_read(dds_ctx *ctx, int kind, long long *launches, double 
   return DDS_OK;
 }
 
+dds_status dds_set_launch_shape(dds_ctx *ctx, int panel_width, int panels_per_cta,
+                                int trace_kernel) {
+  if (!ctx) return DDS_EINVAL;
+  Busy busy(ctx);
+  if (!busy.ok) return DDS_EBUSY;
+  ctx->err.clear();
+  const Geom &g = ctx->g;
+  const bool tc = ctx->single && ctx->split >= 0;
+  if (panel_width != 0 && !(tc && subst_tc_ok(g, ctx->split, panel_width, ctx->tc_m > 0,
+                                               panels_per_cta))) {
+    ctx->err = "dds_set_launch_shape: panel width / panels per CTA not available here";
+    return DDS_EINVAL;
+  }
+  if (panel_width == 0 && panels_per_cta != 1) {
+    ctx->err = "dds_set_launch_shape: panels per CTA needs an explicit panel width";
+    return DDS_EINVAL;
+  }
+  if (trace_kernel < 0 || trace_kernel > 2 || (trace_kernel == 0 && !ctx->trace_tc_avail)) {
+    ctx->err = "dds_set_launch_shape: trace kernel not available here";
+    return DDS_EINVAL;
+  }
+  ctx->tune_pc = panel_width;
+  ctx->tune_np = panels_per_cta;
+  ctx->trace_tc = trace_kernel == 0;
+  if (trace_kernel > 0) ctx->trace_per_sm = trace_kernel;
+  ctx->clear_graphs();
+  ctx->plans.clear();
+  return DDS_OK;
+}
+
 dds_status dds_set_memory_budget(dds_ctx *ctx, long long bytes, long long *in_use) {
   if (!ctx || bytes < 0) return DDS_EINVAL;
   Busy busy(ctx);
@@ -2397,19 +2429,53 @@ dds_status server_step(dds_server *srv, int *active_out, int *queued_out) {
 
 extern "C" {
 
+// device bytes one server slot needs: its Krylov basis and batch fields, its share of the
+// Arnoldi scratch, and its columns in the DDM work buffers of a batched application
+static size_t server_slot_bytes(const dds_ctx *ctx, int maxit, int rounds) {
+  const Geom &g = ctx->g;
+  const size_t fb = (size_t)g.Nglob * sizeof(double2);
+  const size_t elem = ctx->single ? sizeof(float2) : sizeof(double2);
+  const size_t L = sweep_program(g, rounds).size();
+  size_t b = fb * ((size_t)(maxit + 1) + (size_t)maxit + 4);
+  b += (size_t)(2 * (2 * maxit + 3) + (maxit + 2)) * sizeof(double2) + 3 * sizeof(long long);
+  b += (size_t)(maxit + 2) * ((size_t)g.Nglob / dots_chunk() + 2) * sizeof(double2);
+  b += (size_t)g.nsub * ((size_t)g.Nloc * elem + (L + 1) * (size_t)g.T * elem + 2 * sizeof(int));
+  return b;
+}
+
 dds_status dds_server_create(dds_ctx *ctx, int max_slots, double tol, int maxit, int rounds,
                              dds_server **out) {
   if (!ctx || !out || max_slots < 1 || maxit < 1 || rounds < 1 || !(tol > 0)) return DDS_EINVAL;
+  Busy busy(ctx);   // the slots' memory counts against the context (dds_set_memory_budget)
+  if (!busy.ok) return DDS_EBUSY;
+  ctx->err.clear();
+  // admission by device memory: as many slots as the context's budget (or, without one, 90% of
+  // the device's free memory) leaves room for, up to max_slots
+  const size_t per_slot = server_slot_bytes(ctx, maxit, rounds);
+  size_t room = 0;
+  if (ctx->acct.budget) {
+    room = ctx->acct.budget > ctx->acct.used ? ctx->acct.budget - ctx->acct.used : 0;
+  } else {
+    size_t fr = 0, tot = 0;
+    CK(cudaMemGetInfo(&fr, &tot));
+    room = fr / 10 * 9;
+  }
+  const long long fit = (long long)(room / per_slot);
+  if (fit < 1) {
+    ctx->err = "dds_server_create: one slot needs " + std::to_string(per_slot) +
+               " device bytes, " + std::to_string(room) + " are available";
+    return DDS_ENOMEM;
+  }
   std::unique_ptr<dds_server> srv(new (std::nothrow) dds_server());
   if (!srv) return DDS_ENOMEM;
   srv->ctx = ctx;
-  srv->S = max_slots;
+  srv->S = (int)std::min<long long>(max_slots, fit);
   srv->maxit = maxit;
   srv->rounds = rounds;
   srv->tol = tol;
   srv->N = ctx->g.Nglob;
   const size_t fb = (size_t)srv->N * sizeof(double2);
-  const size_t S = (size_t)max_slots;
+  const size_t S = (size_t)srv->S;
   bool ok = srv->V.ensure(S * (maxit + 1) * fb) == cudaSuccess &&
             srv->Z.ensure(S * maxit * fb) == cudaSuccess &&
             srv->B.ensure(S * fb) == cudaSuccess && srv->U.ensure(S * fb) == cudaSuccess &&
@@ -2422,14 +2488,16 @@ dds_status dds_server_create(dds_ctx *ctx, int max_slots, double tol, int maxit,
             srv->hb.ensure(S * (2 * maxit + 3) * sizeof(double2)) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
-    ctx->err = "dds_server_create: device memory for " + std::to_string(max_slots) +
+    ctx->err = "dds_server_create: device memory for " + std::to_string(srv->S) +
                " slots is not available";
     return DDS_ENOMEM;
   }
-  srv->slots.resize(max_slots);
+  srv->slots.resize(srv->S);
   *out = srv.release();
   return DDS_OK;
 }
+
+int dds_server_slots(const dds_server *srv) { return srv ? srv->S : 0; }
 
 dds_status dds_server_submit(dds_server *srv, const void *f, long long tag) {
   if (!srv || !f) return DDS_EINVAL;

@@ -513,7 +513,6 @@ __global__ void __launch_bounds__(kTtThreads, 1)
         }
       }
       fence_proxy_async();   // the generic writes of B before the MMAs' async reads
-      umma::fence_before_sync();
       __syncwarp();
       if (lane == 0) mbar_arrive(&full[s]);
       haves = seek(S, true);

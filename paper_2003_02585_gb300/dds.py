@@ -27,7 +27,8 @@ EXPORTS = ["dds_setup", "dds_sweep", "dds_sweep_strip", "dds_solve", "dds_apply"
            "dds_destroy", "dds_profile", "dds_profile_read", "dds_local_solve_noalloc",
            "dds_server_create", "dds_server_submit", "dds_server_step", "dds_server_poll",
            "dds_server_destroy", "dds_work_per_ddm", "dds_autotune", "dds_set_zero_skip",
-           "dds_local_solve_counts", "dds_set_memory_budget", "dds_set_wait_limit"]
+           "dds_local_solve_counts", "dds_set_memory_budget", "dds_set_wait_limit",
+           "dds_server_slots", "dds_set_launch_shape"]
 KERNEL_KINDS = {"assemble": 0, "subst": 1, "extract": 2, "trace_step": 3, "krylov": 4,
                 "other": 5}
 
@@ -96,11 +97,15 @@ def load(path: str = LIB_PATH):
     lib.dds_server_poll.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), vp,
                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
     lib.dds_server_destroy.argtypes = [vp]
+    lib.dds_server_slots.argtypes = [vp]
+    lib.dds_server_slots.restype = ctypes.c_int
     lib.dds_server_destroy.restype = None
     lib.dds_profile.argtypes = [vp, ctypes.c_int]
     lib.dds_set_zero_skip.argtypes = [vp, ctypes.c_int]
     lib.dds_set_memory_budget.argtypes = [vp, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)]
     lib.dds_set_wait_limit.argtypes = [vp, ctypes.c_longlong]
+    lib.dds_set_launch_shape.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.dds_set_launch_shape.restype = ctypes.c_int
     lib.dds_local_solve_counts.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong),
                                            ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
     lib.dds_profile_read.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
@@ -363,6 +368,11 @@ class Context:
         self._check(self._lib.dds_set_memory_budget(self._h, int(nbytes), ctypes.byref(used)))
         return int(used.value)
 
+    def set_launch_shape(self, panel_width=0, panels_per_cta=1, trace_kernel=2):
+        """Pin the launch shapes dds_autotune would choose (dds_set_launch_shape)."""
+        self._check(self._lib.dds_set_launch_shape(self._h, int(panel_width), int(panels_per_cta),
+                                                   int(trace_kernel)))
+
     def set_wait_limit(self, polls=0):
         """Polls of a level-completion wait before it gives up (dds_set_wait_limit; 0 = default)."""
         self._check(self._lib.dds_set_wait_limit(self._h, int(polls)))
@@ -426,6 +436,7 @@ class Server:
             raise DDSError(st, self._lib.dds_last_error(ctx._h).decode())
         self._h = h
         self.G = ctx.G
+        self.slots = int(self._lib.dds_server_slots(h))   # admitted by device memory
 
     def submit(self, f, tag: int):
         f, _ = self.ctx._fields(f)

@@ -1,7 +1,8 @@
 """Serving loop: Poisson request streams over several cached media, continuous batching.
 
-Each medium has one set-up Context (its cached factorisation) and one dds_server whose slot
-count is the admission limit derived from a device-memory budget.  A request carries 1..32
+Each medium has one set-up Context (its cached factorisation) and one dds_server; the library
+admits by device memory: the context's budget (dds_set_memory_budget) caps what it holds, and the
+server's slot count (its admission limit) is what fits in the rest.  A request carries 1..32
 point sources (right-hand sides); each right-hand side becomes one server submission, and the
 request completes when all of them have.  One worker thread per medium steps its server (the
 C calls release the GIL), so the media's batched iterations overlap on the GPU; inside a
@@ -44,14 +45,6 @@ def serving_media(seed: int = 5):
     ]
 
 
-def slots_for_budget(ctx: dds.Context, budget_bytes: float, maxit: int, cap: int = 64) -> int:
-    """Admission limit: slots whose Krylov storage ((2 maxit + 4) fields each, plus the batch
-    buffers of the DDM) fits the device-memory budget."""
-    field = 16.0 * float(np.prod(ctx.G))
-    per_slot = field * (2 * maxit + 6)
-    return int(max(1, min(cap, budget_bytes // per_slot)))
-
-
 @dataclasses.dataclass
 class Request:
     rid: int
@@ -83,8 +76,11 @@ class MediumWorker(threading.Thread):
         self.medium = medium
         self.ctx = dds.Context(medium.n, 1.0 / medium.n[0], medium.omega, medium.c, medium.parts,
                                medium.pml_cells, 30.0, precision="mixed")
-        self.slots = slots_for_budget(self.ctx, budget_bytes, maxit)
-        self.server = dds.Server(self.ctx, self.slots, tol, maxit, rounds)
+        # admission by device memory inside the library: the context's budget caps everything
+        # it holds, and the server takes the slots that fit in what is left (at most 64)
+        self.ctx.set_memory_budget(int(budget_bytes))
+        self.server = dds.Server(self.ctx, 64, tol, maxit, rounds)
+        self.slots = self.server.slots
         self.inbox = []
         self.lock = threading.Lock()
         self.pending = {}

@@ -422,3 +422,23 @@ def test_autotune_picks_a_valid_shape_and_keeps_results():
     after = ctx.sweep(fe, 2).cpu().numpy()
     for r in range(3):
         assert _rel(after[r], before[r]) < 1e-5
+
+
+def test_pinned_launch_shape_keeps_results():
+    """dds_set_launch_shape pins each shape dds_autotune could choose; every pinned shape gives
+    the oracle's DDM output to single-precision rounding, and a shape the context cannot run is
+    rejected with DDS_EINVAL."""
+    n = (128, 128)
+    prob, f = _case(n, (8, 8), 4, 2 * np.pi * 5, c=_medium("layer", n),
+                    centres=[(0.2, 0.3), (0.7, 0.6)])
+    ctx = _ctx(prob, "mixed", "trace")
+    fe = _on_dev(ctx.extend(f))
+    want = ddm_solve(prob, rhs_from_source(prob, extend_interior(prob, f)), 2)
+    for shape in ((8, 1, 1), (16, 2, 2), (32, 1, 0), (0, 1, 2)):
+        ctx.set_launch_shape(*shape)
+        got = ctx.sweep(fe, 2).cpu().numpy()
+        for r in range(2):
+            assert _rel(got[r], want[r]) < 1e-4, shape
+    for bad in ((12, 1, 1), (0, 2, 1), (16, 1, 3)):
+        with pytest.raises(_dds().DDSError):
+            ctx.set_launch_shape(*bad)

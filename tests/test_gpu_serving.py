@@ -75,3 +75,32 @@ def test_server_result_alone_equals_result_in_the_mix():
         assert got[k][2] < 1e-9
         assert _rel(got[k][0], ug[k]) < 1e-6
     assert _rel(got[0][0], u_alone) < 1e-6
+
+
+def test_server_admits_by_device_memory():
+    """dds_server_create takes as many slots as the context's budget leaves room for (at most
+    max_slots): a larger budget admits more slots, a budget with no room for one slot is
+    DDS_ENOMEM, and the slots a server holds count against the budget."""
+    from paper_2003_02585_gb300 import dds
+    n = (96, 96)
+    h = 1.0 / 96
+    ctx = dds.Context(n, h, 2 * np.pi * 6, synth.medium_constant(n), (3, 3), 10, 30.0,
+                      precision="mixed")
+    held = ctx.info()["device_bytes"]
+    field = 16 * int(np.prod(ctx.G))
+    per_slot_floor = field * (2 * 20 + 5)          # the basis and batch fields alone
+    ctx.set_memory_budget(held + 3 * per_slot_floor)
+    s_small = dds.Server(ctx, 64, 1e-6, 20, 1)
+    assert 1 <= s_small.slots <= 3
+    assert ctx.info()["device_bytes"] <= held + 3 * per_slot_floor
+    s_small.close()
+    ctx.set_memory_budget(held + 12 * per_slot_floor)
+    s_big = dds.Server(ctx, 64, 1e-6, 20, 1)
+    assert s_small.slots < s_big.slots <= 12
+    s_big.close()
+    ctx.set_memory_budget(held + per_slot_floor // 4)
+    with pytest.raises(dds.DDSError) as e:
+        dds.Server(ctx, 64, 1e-6, 20, 1)
+    assert e.value.status == 2                     # DDS_ENOMEM
+    ctx.set_memory_budget(0)
+    assert dds.Server(ctx, 5, 1e-6, 20, 1).slots == 5
