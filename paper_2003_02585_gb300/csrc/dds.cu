@@ -107,7 +107,9 @@ struct CallPlan {            // all launch lists for one nrhs
     int n = -1, nlev = 0;
     DBuf buf, cols, levs;            // k_trace_sweeps: items, their columns, level offsets
     int tn = -1, tnlev = 0, tslots = 0;
-    DBuf tunits, tcols, tlevs;       // k_trace_tc: units, their columns, level offsets
+    DBuf tunits, tcols;              // k_trace_tc: units, their columns
+    DBuf tuoff, tcunits, tcoff, tchunks;   // k_trace_tc: per-CTA unit and chunk streams
+    int tG = 0;                      // k_trace_tc: CTAs the streams were dealt to
     DBuf tneed, tready;              // k_trace_tc: publications expected / made per slot
   };
   std::map<int, TraceTable> trace_steps;   // rounds -> item lists of the cooperative launch
@@ -805,9 +807,23 @@ dds_status prepare_ddm(dds_ctx *ctx, int nrhs, int rounds, bool *grown) {
       std::vector<int> ucols, lev;
       std::vector<unsigned> need;
       tt.tnlev = build_tc_trace_schedule(ctx, nrhs, rounds, units, ucols, lev, need);
+      int dev = 0, nsm = 0;
+      CK(cudaGetDevice(&dev));
+      CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+      std::vector<int> uoff, coff;
+      std::vector<int2> cunits;
+      std::vector<int4> chunks;
+      if (!build_tt_streams(g, ctx->split, nsm, units, lev, uoff, cunits, coff, chunks)) {
+        ctx->err = "tensor-core trace streams cannot be built for this geometry";
+        return DDS_EINVAL;
+      }
       CK(upload(tt.tunits, units, ctx->stream));
       CK(upload(tt.tcols, ucols, ctx->stream));
-      CK(upload(tt.tlevs, lev, ctx->stream));
+      CK(upload(tt.tuoff, uoff, ctx->stream));
+      CK(upload(tt.tcunits, cunits, ctx->stream));
+      CK(upload(tt.tcoff, coff, ctx->stream));
+      CK(upload(tt.tchunks, chunks, ctx->stream));
+      tt.tG = nsm;
       CK(upload(tt.tneed, need, ctx->stream));
       CK(tt.tready.ensure(need.size() * sizeof(unsigned)));
       tt.tslots = (int)need.size();
@@ -926,8 +942,10 @@ dds_status run_ddm(dds_ctx *ctx, const double2 *b, int nrhs, double2 *u, int rou
           return DDS_EINVAL;
         }
         LAUNCHK(DDS_K_TRACE_STEP,
-                launch_trace_tc(st, g, ctx->split, tt.tunits.as<int4>(), tt.tcols.as<int>(), tt.tn,
-                                tt.tlevs.as<int>(), tt.tnlev, ctx->tttiles.as<unsigned char>(),
+                launch_trace_tc(st, g, ctx->split, tt.tunits.as<int4>(), tt.tcols.as<int>(),
+                                tt.tuoff.as<int>(), tt.tcunits.as<int2>(), tt.tcoff.as<int>(),
+                                tt.tchunks.as<int4>(), tt.tn, tt.tG,
+                                ctx->tttiles.as<unsigned char>(),
                                 route, (float2 *)gtr, (const float2 *)rawf, nrhs,
                                 tt.tready.as<unsigned>(), tt.tneed.as<unsigned>(), tt.tslots,
                                 ctx->errflag.as<int>(), ctx->wait_limit));

@@ -272,8 +272,15 @@ bool tt_shape(const Geom &g, int kind, TtShape *s);
 long long tt_tiles_bytes(const Geom &g, int kind, int nfac);
 cudaError_t launch_split_trace(cudaStream_t st, const Geom &g, int kind, int nfac,
                                const double2 *gmap64, unsigned char *tiles);
+bool build_tt_streams(const Geom &g, int kind, int G, const std::vector<int4> &units,
+                      const std::vector<int> &lev_off, std::vector<int> &uoff,
+                      std::vector<int2> &cunits, std::vector<int> &coff,
+                      std::vector<int4> &chunks);
+// G must be the CTA count the streams were built for (the device's SM count); nunits = units in
+// all streams
 cudaError_t launch_trace_tc(cudaStream_t st, const Geom &g, int kind, const int4 *units,
-                            const int *ucols, int nunits, const int *lev_off, int nlevels,
+                            const int *ucols, const int *uoff, const int2 *cunits,
+                            const int *coff, const int4 *chunks, int nunits, int G,
                             const unsigned char *tiles, const int *route, float2 *gtr,
                             const float2 *rawf, int nrhs, unsigned *ready, const unsigned *need,
                             int nslots, int *err, unsigned wait_limit);

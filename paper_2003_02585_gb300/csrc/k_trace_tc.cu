@@ -14,23 +14,27 @@
 // real-ified complex form: B = [b0_re | b0_im | b1_re | b1_im] (4 x 32 rows of the K-major B
 // operand), D1 = A0_re B + A1_re B[:64], D2 = A0_im B + A1_im B[:64].
 //
-// One CTA per SM, cooperative launch; each CTA takes its units of every dataflow level (the
-// schedule of k_trace_sweeps) in level order, with no barrier between levels: a unit waits only
+// One CTA per SM, cooperative launch.  The host deals the units of every dataflow level (the
+// schedule of k_trace_sweeps) over the CTAs and gives each CTA its units and their chunks
+// (runs of at most four K-steps of one input side) as flat streams in run order, so that no
+// role walks a schedule on the device.  There is no barrier between levels: a unit waits only
 // until the trace solves routed into its own slots have published (per-slot counters against
 // host-computed totals), so the levels overlap.  Warp roles:
 //   warps 0-3   epilogue: TMEM lane quarter = warp; row R of the tile per thread; forms the
 //               complex outputs of the 32 columns and adds them into the receivers' slots with
 //               vector reductions; then publishes the unit on the receivers' counters;
-//   warps 4-7   B producers: once the unit's slots are complete, copy its inputs from the trace
+//   warps 4-11  B producers: once the unit's slots are complete, copy its inputs from the trace
 //               slots (cp.async, L1 bypassed: other CTAs wrote them) a few chunks ahead, split
 //               them into pieces and store them in the canonical K-major layout of the ring slot;
-//   warp 8      A producer: streams the pre-split map tiles through the four-slot ring with bulk
+//   warp 12     A producer: streams the pre-split map tiles through the two-slot ring with bulk
 //               copies completed on the slot's mbarrier (it depends on no trace, so it runs
 //               ahead);
-//   warp 9      MMA issuer (one thread) and owner of the tensor memory: two accumulator pairs,
+//   warp 13     MMA issuer (one thread) and owner of the tensor memory: two accumulator pairs,
 //               so that the epilogue of one unit runs under the MMAs of the next.
 // Every wait is bounded; on a timeout the CTA records an error code, stops issuing work, lets its
 // copies and MMAs drain, frees its tensor memory and leaves (the host reports DDS_ETIMEOUT).
+#include <algorithm>
+
 #include "async_copy.cuh"
 #include "dds_internal.cuh"
 #include "umma.cuh"
@@ -46,11 +50,11 @@ constexpr int kTtStep = 16384;     // bytes of one K-step of an A tile (4 comps 
 constexpr int kTtLB = 4 * kTtCols * 16 + 16;   // bytes per 16-byte K group of B (+16: banks)
 constexpr int kTtBStep = 2 * kTtLB;            // bytes of one K-step of B
 constexpr int kTtSlotBytes = kTtKS * (kTtStep + kTtBStep);
-// raw inputs of a chunk (32 columns x up to 4 K-steps of 16 BF16 values, 8 bytes each), staged by
-// cp.async a few chunks ahead of their split into the B operand
-constexpr int kTtRawSlots = 3;
-constexpr int kTtRawBytes = kTtCols * kTtKS * 16 * 8;
-constexpr int kTtAhead = kTtRawSlots - 1;   // chunks in flight ahead of the one being split
+// raw inputs of a chunk (32 columns x up to 4 K-steps of 8 TF32 or 16 BF16 values, 8 bytes
+// each), staged by cp.async a few chunks ahead of their split into the B operand: six staging
+// slots of 8 KB (TF32) or three of 16 KB (BF16) in the same 48 KB
+constexpr int kTtRawTotal = 3 * kTtCols * kTtKS * 16 * 8;
+template <int KIND> __host__ __device__ constexpr int tt_raw_slots() { return KIND == 0 ? 6 : 3; }
 constexpr int kTtBWarps = 8;       // B-producer warps
 constexpr int kTtBThreads = 32 * kTtBWarps;
 constexpr int kTtAWarp = 4 + kTtBWarps, kTtMmaWarp = kTtAWarp + 1;
@@ -78,7 +82,7 @@ bool tt_shape(const Geom &g, int kind, TtShape *s) {
   t.KP = off;
   t.rt_bytes = (long long)(t.KP / t.KE) * kTtStep;
   t.fac_bytes = (long long)t.RT * t.rt_bytes;
-  t.smem = (size_t)kTtSlots * kTtSlotBytes + (size_t)kTtRawSlots * kTtRawBytes + 1024;
+  t.smem = (size_t)kTtSlots * kTtSlotBytes + (size_t)kTtRawTotal + 1024;
   if (t.smem > 227 * 1024) return false;
   if (s) *s = t;
   return true;
@@ -88,6 +92,59 @@ long long tt_tiles_bytes(const Geom &g, int kind, int nfac) {
   TtShape t;
   if (!tt_shape(g, kind, &t)) return 0;
   return (long long)nfac * t.fac_bytes;
+}
+
+// The work of each CTA of a G-CTA launch, in the order it runs it: the units of every dataflow
+// level dealt in a snake (unit j of a level goes to CTA j % G on even rounds j / G and to
+// CTA G - 1 - j % G on odd ones), heaviest first as the host sorted them; and the chunks of those
+// units, one descriptor each:
+//   x = unit index | (1 << 30 on the unit's first chunk)
+//   y = global K-step of the chunk's map tile (factor, row tile and input side folded in)
+//   z = offset of the chunk's first input within a trace slot column (toff[d] + k0)
+//   w = K-steps of the chunk | (inputs that exist, the rest being padding) << 8
+// Units (x = unit index, y = its chunks) and chunks are stored CTA by CTA with offsets.
+bool build_tt_streams(const Geom &g, int kind, int G, const std::vector<int4> &units,
+                      const std::vector<int> &lev_off, std::vector<int> &uoff,
+                      std::vector<int2> &cunits, std::vector<int> &coff,
+                      std::vector<int4> &chunks) {
+  TtShape t;
+  if (!tt_shape(g, kind, &t) || G <= 0 || units.size() >= (1u << 30)) return false;
+  const int nlev = (int)lev_off.size() - 1;
+  std::vector<std::vector<int>> per(G);
+  for (int v = 0; v < nlev; ++v)
+    for (int j = lev_off[v]; j < lev_off[v + 1]; ++j) {
+      const int r = (j - lev_off[v]) / G, w = (j - lev_off[v]) % G;
+      per[(r & 1) ? G - 1 - w : w].push_back(j);
+    }
+  const long long steps = t.KP / t.KE;   // K-steps of one row tile of one factor
+  uoff.assign(1, 0);
+  coff.assign(1, 0);
+  cunits.clear();
+  chunks.clear();
+  for (int b = 0; b < G; ++b) {
+    for (int j : per[b]) {
+      const int4 h = units[j];
+      const int fac = h.x & 0xFFFFFF, rt = (h.y >> 16) & 0xFFFF, kmask = h.w & 0xFF;
+      int nch = 0;
+      for (int d = 0; d < g.nsides; ++d) {
+        if (!((kmask >> d) & 1)) continue;
+        const int ns = t.kpn[d] / t.KE;
+        for (int t0 = 0; t0 < ns; t0 += kTtKS) {
+          const int nks = std::min(kTtKS, ns - t0), k0 = t0 * t.KE;
+          const int live = std::min(nks * t.KE, 2 * g.Lt[d] - k0);
+          const long long a = ((long long)fac * t.RT + rt) * steps + t.kpo[d] / t.KE + t0;
+          if (a > INT32_MAX || live <= 0) return false;
+          chunks.push_back(make_int4(j | (nch == 0 ? 1 << 30 : 0), (int)a, g.toff[d] + k0,
+                                     nks | (live << 8)));
+          ++nch;
+        }
+      }
+      cunits.push_back(make_int2(j, nch));
+    }
+    uoff.push_back((int)cunits.size());
+    coff.push_back((int)chunks.size());
+  }
+  return true;
 }
 
 template <int KIND>
@@ -171,30 +228,6 @@ __device__ inline TtUnit tt_unit(const int4 *units, int idx) {
   return u;
 }
 
-// chunks of a unit: per input side in the mask, its K-steps in runs of at most kTtKS
-__device__ inline int tt_nchunks(const TtShape &t, int kmask) {
-  int n = 0;
-  for (int d = 0; d < 6; ++d)
-    if ((kmask >> d) & 1) n += (t.kpn[d] / t.KE + kTtKS - 1) / kTtKS;
-  return n;
-}
-// chunk c of a unit: input side, first K-step within the side, K-steps
-__device__ inline void tt_chunk(const TtShape &t, int kmask, int c, int &d, int &t0, int &nks) {
-  for (d = 0; d < 6; ++d) {
-    if (!((kmask >> d) & 1)) continue;
-    const int ns = t.kpn[d] / t.KE, nc = (ns + kTtKS - 1) / kTtKS;
-    if (c < nc) {
-      t0 = c * kTtKS;
-      nks = min(kTtKS, ns - t0);
-      return;
-    }
-    c -= nc;
-  }
-  d = 0;
-  t0 = 0;
-  nks = 0;
-}
-
 // the pieces of v written as B rows c (real) and 32 + c (imaginary) of piece 0, and the same
 // rows + 64 of piece 1, at K position k of the chunk
 template <int KIND>
@@ -230,15 +263,19 @@ __device__ inline void named_sync(int id, int threads) {
 
 template <int KIND>
 __global__ void __launch_bounds__(kTtThreads, 1)
-    k_trace_tc(Geom g, TtShape t, const int4 *__restrict__ units, const int *__restrict__ ucols,
-               const int *__restrict__ lev_off, int nlev, const unsigned char *__restrict__ tiles,
-               const int *__restrict__ route, float2 *__restrict__ gtr,
-               const float2 *__restrict__ rawf, int nrhs, unsigned *ready,
-               const unsigned *__restrict__ need, int *__restrict__ err, unsigned wait_limit) {
+    k_trace_tc(Geom g, const int4 *__restrict__ units, const int *__restrict__ ucols,
+               const int *__restrict__ uoff, const int2 *__restrict__ cunits,
+               const int *__restrict__ coff, const int4 *__restrict__ chunks,
+               const unsigned char *__restrict__ tiles, const int *__restrict__ route,
+               float2 *__restrict__ gtr, const float2 *__restrict__ rawf, int nrhs,
+               unsigned *ready, const unsigned *__restrict__ need, int *__restrict__ err,
+               unsigned wait_limit) {
   constexpr uint32_t kIdN4 = KIND == 0 ? umma::idesc_tf32(128, 4 * kTtCols)
                                        : umma::idesc_bf16(128, 4 * kTtCols);
   constexpr uint32_t kIdN2 = KIND == 0 ? umma::idesc_tf32(128, 2 * kTtCols)
                                        : umma::idesc_bf16(128, 2 * kTtCols);
+  constexpr int kRawSlots = tt_raw_slots<KIND>();
+  constexpr int kRawBytes = kTtRawTotal / kRawSlots;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // full[s]: A bytes + one arrival per B-producer warp; empty[s]: MMA commit; accf[b]: MMA
   // commit; acce[b]: one arrival per epilogue warp; drain: final MMA commit
@@ -246,9 +283,12 @@ __global__ void __launch_bounds__(kTtThreads, 1)
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   __shared__ int ready_flag[2];   // B producers: the last input check (alternating)
+  __shared__ int pcol[2][kTtCols];   // B producers: column words of the unit being staged
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int G = (int)gridDim.x, b = (int)blockIdx.x;
-  auto pos = [&](int r) { return r * G + ((r & 1) ? G - 1 - b : b); };
+  const int b = (int)blockIdx.x;
+  // this CTA's units and chunks (host-built streams)
+  const int u_beg = __ldg(uoff + b), u_end = __ldg(uoff + b + 1);
+  const int c_beg = __ldg(coff + b), c_end = __ldg(coff + b + 1);
   auto aborted = [&]() { return *reinterpret_cast<volatile int *>(&abort_flag) != 0; };
   auto fail = [&](int code) {
     atomicExch(err, code);
@@ -257,7 +297,7 @@ __global__ void __launch_bounds__(kTtThreads, 1)
   auto slotA = [&](int s) { return smem_raw + (size_t)s * kTtSlotBytes; };
   auto slotB = [&](int s) { return smem_raw + (size_t)s * kTtSlotBytes + kTtKS * kTtStep; };
   auto slotR = [&](int s) {
-    return smem_raw + (size_t)kTtSlots * kTtSlotBytes + (size_t)s * kTtRawBytes;
+    return smem_raw + (size_t)kTtSlots * kTtSlotBytes + (size_t)s * kRawBytes;
   };
   const long long slot_stride = (long long)nrhs * g.nsub * g.T;
 
@@ -284,38 +324,26 @@ __global__ void __launch_bounds__(kTtThreads, 1)
   const uint32_t tmem = tmem_base;
 
   if (warp == kTtAWarp) {
-    // ---------------- A producer: the map tiles of every unit's chunks, in unit order
+    // ---------------- A producer: the map tiles of this CTA's chunks, in order
     if (lane == 0) {
-      int ci = 0;                 // chunks issued
-      int last[kTtSlots];
-      for (int s = 0; s < kTtSlots; ++s) last[s] = -1;
-      for (int v = 0; v < nlev && !aborted(); ++v) {
-        const int base = __ldg(lev_off + v), Nv = __ldg(lev_off + v + 1) - base;
-        for (int r = 0; pos(r) < Nv && !aborted(); ++r) {
-          const TtUnit u = tt_unit(units, base + pos(r));
-          const int nch = tt_nchunks(t, u.kmask);
-          for (int c = 0; c < nch; ++c, ++ci) {
-            const int s = ci % kTtSlots;
-            if (ci >= kTtSlots && !mbar_wait(&empty[s], ((ci / kTtSlots) - 1) & 1)) {
-              fail(21);
-              break;
-            }
-            if (aborted()) break;
-            int d, t0, nks;
-            tt_chunk(t, u.kmask, c, d, t0, nks);
-            const uint32_t bytes = (uint32_t)nks * kTtStep;
-            const unsigned char *src = tiles + (long long)u.factor * t.fac_bytes +
-                                       (long long)u.rt * t.rt_bytes +
-                                       (long long)(t.kpo[d] / t.KE + t0) * kTtStep;
-            mbar_arrive_expect_tx(&full[s], bytes);
-            bulk_g2s(slotA(s), src, bytes, &full[s]);
-            last[s] = ci;
-          }
+      int ci = 0;   // chunks issued
+      for (int j = c_beg; j < c_end && !aborted(); ++j, ++ci) {
+        const int4 dsc = __ldg(chunks + j);
+        const int s = ci % kTtSlots;
+        if (ci >= kTtSlots && !mbar_wait(&empty[s], ((ci / kTtSlots) - 1) & 1)) {
+          fail(21);
+          break;
         }
+        if (aborted()) break;
+        const uint32_t bytes = (uint32_t)(dsc.w & 0xFF) * kTtStep;
+        mbar_arrive_expect_tx(&full[s], bytes);
+        bulk_g2s(slotA(s), tiles + (long long)dsc.y * kTtStep, bytes, &full[s]);
       }
-      // no copy may still be landing when the CTA leaves
-      for (int s = 0; s < kTtSlots; ++s)
-        if (last[s] >= 0 && !mbar_wait(&full[s], (last[s] / kTtSlots) & 1)) atomicExch(err, 22);
+      // no copy may still be landing when the CTA leaves: wait for the last chunk of each slot
+      for (int s = 0; s < kTtSlots && s < ci; ++s) {
+        const int last = s + (ci - 1 - s) / kTtSlots * kTtSlots;
+        if (!mbar_wait(&full[s], (last / kTtSlots) & 1)) atomicExch(err, 22);
+      }
     }
   } else if (warp == kTtMmaWarp) {
     // ---------------- MMA issuer
@@ -325,11 +353,9 @@ __global__ void __launch_bounds__(kTtThreads, 1)
       const uint64_t dC = (uint64_t)(2 * 128 * 16) >> 4; // one component of A
       const uint64_t dB = (uint64_t)kTtBStep >> 4;       // one K-step of B
       int ci = 0, mi = 0;   // chunks consumed, MMA units issued
-      for (int v = 0; v < nlev && !aborted(); ++v) {
-        const int base = __ldg(lev_off + v), Nv = __ldg(lev_off + v + 1) - base;
-        for (int r = 0; pos(r) < Nv && !aborted(); ++r) {
-          const TtUnit u = tt_unit(units, base + pos(r));
-          const int nch = tt_nchunks(t, u.kmask);
+      for (int ui = u_beg; ui < u_end && !aborted(); ++ui) {
+        {
+          const int nch = __ldg(cunits + ui).y;
           if (nch == 0) continue;
           const int q = mi & 1;
           if (mi >= 2 && !mbar_wait(&acce[q], ((mi >> 1) - 1) & 1)) { fail(23); break; }
@@ -338,11 +364,10 @@ __global__ void __launch_bounds__(kTtThreads, 1)
           bool ok = true;
           for (int c = 0; c < nch; ++c, ++ci) {
             const int s = ci % kTtSlots;
+            const int nks = __ldg(&chunks[c_beg + ci].w) & 0xFF;
             if (!mbar_wait(&full[s], (ci / kTtSlots) & 1)) { fail(24); ok = false; break; }
             if (aborted()) { ok = false; break; }
             umma::fence_after_sync();
-            int d, t0, nks;
-            tt_chunk(t, u.kmask, c, d, t0, nks);
             uint64_t ad = umma::smem_desc(umma::saddr(slotA(s)), lbo_a, 128);
             uint64_t bd = umma::smem_desc(umma::saddr(slotB(s)), (uint32_t)kTtLB, 128);
             for (int k = 0; k < nks; ++k) {
@@ -372,56 +397,32 @@ __global__ void __launch_bounds__(kTtThreads, 1)
       if (!mbar_wait(&drain, 0)) atomicExch(err, 25);
     }
   } else if (warp >= 4) {
-    // ---------------- B producers: inputs of every unit's chunks, split into pieces
+    // ---------------- B producers: inputs of this CTA's chunks, split into pieces
     // Dataflow instead of level barriers: before the first copy of a unit's inputs, warp 4
     // waits until every trace solve routed into the unit's slots (l, X) has published
     // (ready[l nsub + X] == need[l nsub + X]).  Each chunk's raw inputs are copied into a
-    // staging slot by cp.async (L1 bypassed: other CTAs wrote them) kTtAhead chunks before they
+    // staging slot by cp.async (L1 bypassed: other CTAs wrote them) several chunks before they
     // are split into the ring slot, across unit and level boundaries.  Thread pt owns the pairs
-    // of consecutive inputs p = pt + 128 i of every chunk (column p / (nk / 2), inputs
-    // 2 (p % (nk / 2)) and the next), copies them and splits them itself, so no barrier is
-    // needed between the copy and the split.
+    // of consecutive inputs p = pt + 256 i of every chunk (column p / kPairs, inputs
+    // 2 (p % kPairs) and the next), copies them and splits them itself, so no barrier is
+    // needed between the copy and the split.  The unit's column words sit in a shared table
+    // (two, by unit parity), written by the readiness check, so that no copy waits on a load.
+    constexpr int kPairs = kTtKS * (KIND == 0 ? 8 : 16) / 2;   // input pairs per column
     const int pt = tid - 128;   // 0 .. kTtBThreads - 1
-    struct Cur {
-      int v, base, Nv, r, c, nch;
-      TtUnit u;
-    };
-    auto seek = [&](Cur &k, bool next) {
-      if (next) ++k.c;
-      for (;;) {
-        if (k.v >= nlev) return false;
-        if (pos(k.r) >= k.Nv) {
-          if (++k.v >= nlev) return false;
-          k.base = __ldg(lev_off + k.v);
-          k.Nv = __ldg(lev_off + k.v + 1) - k.base;
-          k.r = 0;
-          k.c = 0;
-          continue;
-        }
-        if (k.c == 0) {
-          k.u = tt_unit(units, k.base + pos(k.r));
-          k.nch = tt_nchunks(t, k.u.kmask);
-        }
-        if (k.c < k.nch) return true;
-        ++k.r;
-        k.c = 0;
-      }
-    };
-    // are the unit's inputs complete (every producer routed into its slots has published)?  One
-    // thread polls, `block` = until they are (bounded) or once; the answer goes to all 128
+    // are the unit's inputs complete (every producer routed into its slots has published)?  Lane
+    // c of warp 4 polls the slot of column c (all columns at once), `block` = until it is complete
+    // (bounded) or once, and puts the column word into table `tab`; the answer goes to all
     // producer threads through a shared flag (two, alternating, so that a reader of one check
-    // never races the next write)
+    // never races the next write).  The table of unit n is written only after every producer
+    // thread has passed the check of unit n - 1, so after its copies of unit n - 2.
     int check_no = 0;
-    auto inputs_ready = [&](const TtUnit &u, bool block) {
+    auto inputs_ready = [&](const TtUnit &u, int tab, bool block) {
       const int fl = check_no++ & 1;
-      if (warp == 4 && lane == 0) {
-        int ok = 1;
-        int prevX = -1;
-        for (int c = 0; c < u.ncol && ok; ++c) {
-          const int X = __ldg(ucols + u.col0 + c) % g.nsub;
-          if (X == prevX) continue;
-          prevX = X;
-          const long long sl = (long long)u.l * g.nsub + X;
+      if (warp == 4) {
+        int ok = 1, col = -1;
+        if (lane < u.ncol) {
+          col = __ldg(ucols + u.col0 + lane);
+          const long long sl = (long long)u.l * g.nsub + col % g.nsub;
           const unsigned want = __ldg(need + sl);
           uint32_t spins = 0;
           while (ld_acquire_gpu(ready + sl) < want) {
@@ -434,62 +435,61 @@ __global__ void __launch_bounds__(kTtThreads, 1)
             __nanosleep(32);
           }
         }
-        ready_flag[fl] = ok;
+        pcol[tab][lane] = col;
+        ok = __all_sync(0xffffffffu, ok);
+        if (lane == 0) ready_flag[fl] = ok;
       }
       named_sync(2, kTtBThreads);
       return ready_flag[fl] != 0;
     };
-    auto stage = [&](const Cur &k, int slot) {
-      const TtUnit &u = k.u;
-      int d, t0, nks;
-      tt_chunk(t, u.kmask, k.c, d, t0, nks);
-      const int half = nks * t.KE / 2;            // input pairs per column
-      const int k0 = t0 * t.KE, lim = 2 * g.Lt[d];
-      const float2 *src0 = gtr + (long long)u.l * slot_stride + g.toff[d] + k0;
+    // copy the raw inputs of chunk `dsc` of unit `u` (column table `tab`) into staging slot `slot`
+    auto stage = [&](const int4 &dsc, const TtUnit &u, int tab, int slot) {
+      const int live = dsc.w >> 8;
+      const float2 *src0 = gtr + (long long)u.l * slot_stride + dsc.z;
       unsigned char *raw = slotR(slot);
-      for (int q = pt; q < kTtCols * half; q += kTtBThreads) {
-        const int c2 = q / half, kk = 2 * (q - c2 * half);
-        const bool live = c2 < u.ncol && k0 + kk < lim;
-        const int col = live ? __ldg(ucols + u.col0 + c2) : 0;
-        cp_async16(raw + q * 16, live ? (const void *)(src0 + (long long)col * g.T + kk)
-                                      : (const void *)gtr, live ? 16u : 0u);
+      const int *cols = pcol[tab];
+#pragma unroll
+      for (int i = 0; i < kTtCols * kPairs / kTtBThreads; ++i) {
+        const int q = pt + i * kTtBThreads;
+        const int c2 = q / kPairs, kk = 2 * (q % kPairs);
+        const bool on = c2 < u.ncol && kk < live;
+        const int col = on ? cols[c2] : 0;
+        cp_async16(raw + q * 16, on ? (const void *)(src0 + (long long)col * g.T + kk)
+                                    : (const void *)gtr, on ? 16u : 0u);
       }
     };
-    Cur P{}, S{};
-    if (nlev > 0) {
-      P.base = S.base = __ldg(lev_off);
-      P.Nv = S.Nv = __ldg(lev_off + 1) - P.base;
-    }
-    bool havep = nlev > 0 && seek(P, false);
-    bool haves = nlev > 0 && seek(S, false);
-    // The copy cursor P stages chunks up to kTtAhead ahead of the split cursor S.  It enters a new
-    // unit only once that unit's inputs are complete, without waiting, except when S needs the
-    // chunk now (then nothing earlier is pending in these threads, so the wait cannot hold up the
-    // trace solves it waits for).  Each iteration commits one cp.async group; gsl[slot] is the
-    // group that staged the chunk held in a staging slot.
-    int staged = 0, groups = 0;
-    int gsl[kTtRawSlots];
-#pragma unroll
-    for (int i = 0; i < kTtRawSlots; ++i) gsl[i] = 0;
-    for (int ci = 0; haves; ++ci) {
-      while (havep && staged < ci + kTtRawSlots) {   // the slot's previous chunk is split
-        if (P.c == 0 && !inputs_ready(P.u, staged == ci)) break;
-        const int rs = staged % kTtRawSlots;
-        stage(P, rs);
-        gsl[rs] = groups;
+    // Chunk jp (stream position) is the next to stage, chunk c_beg + ci the next to split.  The
+    // copy side stages up to the staging slots ahead.  It enters a new unit only once that unit's
+    // inputs are complete, without waiting, except when the split needs the chunk now (then
+    // nothing earlier is pending in these threads, so the wait cannot hold up the trace solves it
+    // waits for).  Each staged chunk is one cp.async group, so chunk ci has landed once at most
+    // staged - 1 - ci groups are pending.
+    const int nchunks = c_end - c_beg;
+    int staged = 0, un = -1, hdr_at = -1;   // chunks staged, ordinal of the staging unit
+    int4 dP = nchunks > 0 ? __ldg(chunks + c_beg) : make_int4(0, 0, 0, 0);
+    TtUnit uP{};
+    for (int ci = 0; ci < nchunks; ++ci) {
+      while (staged < nchunks && staged < ci + kRawSlots) {   // the slot's chunk is split
+        if ((dP.x >> 30) & 1) {   // first chunk of a unit
+          if (hdr_at != staged) {
+            uP = tt_unit(units, dP.x & 0x3FFFFFFF);
+            hdr_at = staged;
+          }
+          if (!inputs_ready(uP, (un + 1) & 1, staged == ci)) break;
+          ++un;
+        }
+        stage(dP, uP, un & 1, staged % kRawSlots);
+        cp_async_commit();
         ++staged;
-        havep = seek(P, true);
+        if (staged < nchunks) dP = __ldg(chunks + c_beg + staged);
       }
-      cp_async_commit();
-      ++groups;
-      // this thread's copies of chunk ci have landed: at most (groups committed after its
-      // group) groups may still be pending
-      switch (groups - 1 - gsl[ci % kTtRawSlots]) {
+      switch (staged - 1 - ci) {
         case 0: cp_async_wait_group<0>(); break;
         case 1: cp_async_wait_group<1>(); break;
         case 2: cp_async_wait_group<2>(); break;
         case 3: cp_async_wait_group<3>(); break;
-        default: cp_async_wait_group<4>(); break;
+        case 4: cp_async_wait_group<4>(); break;
+        default: cp_async_wait_group<5>(); break;
       }
       const int s = ci % kTtSlots;
       if (ci >= kTtSlots && !aborted()) {
@@ -500,13 +500,13 @@ __global__ void __launch_bounds__(kTtThreads, 1)
         if (!okw && lane == 0) fail(26);
       }
       if (!aborted()) {
-        int d, t0, nks;
-        tt_chunk(t, S.u.kmask, S.c, d, t0, nks);
-        const int half = nks * t.KE / 2;
-        const unsigned char *raw = slotR(ci % kTtRawSlots);
+        // every K-step of the ring slot is written; the MMAs read only the chunk's own
+        const unsigned char *raw = slotR(ci % kRawSlots);
         unsigned char *sB = slotB(s);
-        for (int q = pt; q < kTtCols * half; q += kTtBThreads) {
-          const int c2 = q / half, kk = 2 * (q - c2 * half);
+#pragma unroll
+        for (int i = 0; i < kTtCols * kPairs / kTtBThreads; ++i) {
+          const int q = pt + i * kTtBThreads;
+          const int c2 = q / kPairs, kk = 2 * (q % kPairs);
           const float4 w = *reinterpret_cast<const float4 *>(raw + q * 16);
           tt_put_b<KIND>(sB, kk, c2, make_float2(w.x, w.y));
           tt_put_b<KIND>(sB, kk + 1, c2, make_float2(w.z, w.w));
@@ -515,18 +515,17 @@ __global__ void __launch_bounds__(kTtThreads, 1)
       fence_proxy_async();   // the generic writes of B before the MMAs' async reads
       __syncwarp();
       if (lane == 0) mbar_arrive(&full[s]);
-      haves = seek(S, true);
     }
     cp_async_wait_all();   // nothing stays in flight
   } else {
     // ---------------- epilogue: row R of the unit's tile, every column
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
     int mi = 0;
-    for (int v = 0; v < nlev; ++v) {
-      const int base = __ldg(lev_off + v), Nv = __ldg(lev_off + v + 1) - base;
-      for (int r = 0; pos(r) < Nv; ++r) {
-        const TtUnit u = tt_unit(units, base + pos(r));
-        const int nch = tt_nchunks(t, u.kmask);
+    for (int ui = u_beg; ui < u_end; ++ui) {
+      {
+        const int2 cu = __ldg(cunits + ui);
+        const TtUnit u = tt_unit(units, cu.x);
+        const int nch = cu.y;
         const int R = u.rt * 128 + warp * 32 + lane;
         int dout = -1, ro = 0, dst_off = 0;
 #pragma unroll
@@ -537,6 +536,8 @@ __global__ void __launch_bounds__(kTtThreads, 1)
             dst_off = g.toff[d ^ 1] + ro;   // the same row of the receiver's side d ^ 1
           }
         const int lp = dout >= 0 ? __ldg(route + u.l * 6 + dout) : -1;
+        // lane c holds the column word of column c (loaded before the accumulator wait)
+        const int mycol = lane < u.ncol ? __ldg(ucols + u.col0 + lane) : -1;
         float2 out[kTtCols];
 #pragma unroll
         for (int c = 0; c < kTtCols; ++c) out[c] = make_float2(0.f, 0.f);
@@ -580,11 +581,12 @@ __global__ void __launch_bounds__(kTtThreads, 1)
         // even offset), so each exchanges one value per column pair with its partner and adds
         // two rows of one column with one 16-byte vector reduction
         const bool live = dout >= 0 && lp >= 0 && !aborted();
-        if (u.raw && dout >= 0) {
+        if (u.raw) {
 #pragma unroll
           for (int c = 0; c < kTtCols; ++c) {
-            if (c < u.ncol) {
-              const float2 w = __ldg(rawf + (long long)__ldg(ucols + u.col0 + c) * g.T + R);
+            const int col = __shfl_sync(0xffffffffu, mycol, c);
+            if (c < u.ncol && dout >= 0) {
+              const float2 w = __ldg(rawf + (long long)col * g.T + R);
               out[c] = make_float2(out[c].x + w.x, out[c].y + w.y);
             }
           }
@@ -598,8 +600,8 @@ __global__ void __launch_bounds__(kTtThreads, 1)
           const float2 got = make_float2(__shfl_xor_sync(0xffffffffu, send.x, 1),
                                          __shfl_xor_sync(0xffffffffu, send.y, 1));
           const int cc = c + (odd ? 1 : 0);
+          const int col = __shfl_sync(0xffffffffu, mycol, cc);
           if (live && cc < u.ncol) {
-            const int col = __ldg(ucols + u.col0 + cc);
             const int X = col % g.nsub, rhs = col - X;   // rhs * nsub
             const int Y = sub_neighbour(g, X, dout);
             if (Y >= 0) {
@@ -612,14 +614,13 @@ __global__ void __launch_bounds__(kTtThreads, 1)
         // each thread's reductions are performed before the unit is published
         __threadfence();
         // publish the unit: one count per (receiving slot, subdomain of the tile, side whose
-        // rows lie in this row tile), as the host counted them into need[]
+        // rows lie in this row tile), as the host counted them into need[]; lane c of warp 0
+        // takes column c when its subdomain differs from column c - 1's
         named_sync(1, 128);
-        if (tid == 0) {
-          int prevX = -1;
-          for (int c = 0; c < u.ncol; ++c) {
-            const int X = __ldg(ucols + u.col0 + c) % g.nsub;
-            if (X == prevX) continue;
-            prevX = X;
+        if (warp == 0) {
+          const int X = mycol >= 0 ? mycol % g.nsub : -1;
+          const int Xp = __shfl_up_sync(0xffffffffu, X, 1);
+          if (X >= 0 && (lane == 0 || X != Xp)) {
             for (int d = 0; d < g.nsides; ++d) {
               if (g.toff[d] >= 128 * (u.rt + 1) || g.toff[d] + 2 * g.Lt[d] <= 128 * u.rt) continue;
               const int lq = __ldg(route + u.l * 6 + d), Y = sub_neighbour(g, X, d);
@@ -639,11 +640,12 @@ __global__ void __launch_bounds__(kTtThreads, 1)
 }
 
 cudaError_t launch_trace_tc(cudaStream_t st, const Geom &g, int kind, const int4 *units,
-                            const int *ucols, int nunits, const int *lev_off, int nlevels,
+                            const int *ucols, const int *uoff, const int2 *cunits,
+                            const int *coff, const int4 *chunks, int nunits, int G,
                             const unsigned char *tiles, const int *route, float2 *gtr,
                             const float2 *rawf, int nrhs, unsigned *ready, const unsigned *need,
                             int nslots, int *err, unsigned wait_limit) {
-  if (nunits <= 0 || nlevels <= 0) return cudaSuccess;
+  if (nunits <= 0) return cudaSuccess;
   TtShape t;
   if (!tt_shape(g, kind, &t)) return cudaErrorInvalidValue;
   static bool done0[64] = {false}, done1[64] = {false};
@@ -653,6 +655,8 @@ cudaError_t launch_trace_tc(cudaStream_t st, const Geom &g, int kind, const int4
   int dev = 0, nsm = 0, per_sm = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  // one CTA per SM (it owns the whole tensor memory), all resident: the streams were dealt for G
+  if (G != nsm) return cudaErrorInvalidConfiguration;
   e = kind == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_tc<0>, kTtThreads, t.smem)
                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_tc<1>, kTtThreads, t.smem);
   if (e != cudaSuccess) return e;
@@ -660,7 +664,7 @@ cudaError_t launch_trace_tc(cudaStream_t st, const Geom &g, int kind, const int4
   e = cudaMemsetAsync(ready, 0, (size_t)nslots * sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)nsm);   // one CTA per SM: it owns the whole tensor memory
+  cfg.gridDim = dim3((unsigned)G);
   cfg.blockDim = dim3(kTtThreads);
   cfg.dynamicSmemBytes = t.smem;
   cfg.stream = st;
@@ -670,10 +674,10 @@ cudaError_t launch_trace_tc(cudaStream_t st, const Geom &g, int kind, const int4
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   if (kind == 0)
-    return cudaLaunchKernelEx(&cfg, k_trace_tc<0>, g, t, units, ucols, lev_off, nlevels, tiles,
-                              route, gtr, rawf, nrhs, ready, need, err, wait_limit);
-  return cudaLaunchKernelEx(&cfg, k_trace_tc<1>, g, t, units, ucols, lev_off, nlevels, tiles,
-                            route, gtr, rawf, nrhs, ready, need, err, wait_limit);
+    return cudaLaunchKernelEx(&cfg, k_trace_tc<0>, g, units, ucols, uoff, cunits, coff, chunks,
+                              tiles, route, gtr, rawf, nrhs, ready, need, err, wait_limit);
+  return cudaLaunchKernelEx(&cfg, k_trace_tc<1>, g, units, ucols, uoff, cunits, coff, chunks,
+                            tiles, route, gtr, rawf, nrhs, ready, need, err, wait_limit);
 }
 
 }  // namespace dds
