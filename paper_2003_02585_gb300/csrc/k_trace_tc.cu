@@ -45,16 +45,13 @@ namespace {
 
 constexpr int kTtCols = 32;        // complex columns per unit
 constexpr int kTtKS = 4;           // K-steps per ring chunk
-constexpr int kTtSlots = 2;        // ring slots
+constexpr int kTtSlots = 2;        // B ring slots (one chunk each)
+constexpr int kTtASlots = 3;       // A ring slots (one chunk each)
 constexpr int kTtStep = 16384;     // bytes of one K-step of an A tile (4 comps x 2 x 128 x 16)
 constexpr int kTtLB = 4 * kTtCols * 16 + 16;   // bytes per 16-byte K group of B (+16: banks)
 constexpr int kTtBStep = 2 * kTtLB;            // bytes of one K-step of B
-constexpr int kTtSlotBytes = kTtKS * (kTtStep + kTtBStep);
-// raw inputs of a chunk (32 columns x up to 4 K-steps of 8 TF32 or 16 BF16 values, 8 bytes
-// each), staged by cp.async a few chunks ahead of their split into the B operand: six staging
-// slots of 8 KB (TF32) or three of 16 KB (BF16) in the same 48 KB
-constexpr int kTtRawTotal = 3 * kTtCols * kTtKS * 16 * 8;
-template <int KIND> __host__ __device__ constexpr int tt_raw_slots() { return KIND == 0 ? 6 : 3; }
+constexpr int kTtASlotBytes = kTtKS * kTtStep;
+constexpr int kTtBSlotBytes = kTtKS * kTtBStep;
 constexpr int kTtBWarps = 8;       // B-producer warps
 constexpr int kTtBThreads = 32 * kTtBWarps;
 constexpr int kTtAWarp = 4 + kTtBWarps, kTtMmaWarp = kTtAWarp + 1;
@@ -82,7 +79,7 @@ bool tt_shape(const Geom &g, int kind, TtShape *s) {
   t.KP = off;
   t.rt_bytes = (long long)(t.KP / t.KE) * kTtStep;
   t.fac_bytes = (long long)t.RT * t.rt_bytes;
-  t.smem = (size_t)kTtSlots * kTtSlotBytes + (size_t)kTtRawTotal + 1024;
+  t.smem = (size_t)kTtASlots * kTtASlotBytes + (size_t)kTtSlots * kTtBSlotBytes + 1024;
   if (t.smem > 227 * 1024) return false;
   if (s) *s = t;
   return true;
@@ -274,12 +271,12 @@ __global__ void __launch_bounds__(kTtThreads, 1)
                                        : umma::idesc_bf16(128, 4 * kTtCols);
   constexpr uint32_t kIdN2 = KIND == 0 ? umma::idesc_tf32(128, 2 * kTtCols)
                                        : umma::idesc_bf16(128, 2 * kTtCols);
-  constexpr int kRawSlots = tt_raw_slots<KIND>();
-  constexpr int kRawBytes = kTtRawTotal / kRawSlots;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  // full[s]: A bytes + one arrival per B-producer warp; empty[s]: MMA commit; accf[b]: MMA
+  // fullA[a]: A bytes; emptyA[a]: MMA commit; full[s]: one arrival per B-producer warp;
+  // empty[s]: MMA commit; accf[b]: MMA
   // commit; acce[b]: one arrival per epilogue warp; drain: final MMA commit
-  __shared__ uint64_t full[kTtSlots], empty[kTtSlots], accf[2], acce[2], drain;
+  __shared__ uint64_t fullA[kTtASlots], emptyA[kTtASlots], full[kTtSlots], empty[kTtSlots];
+  __shared__ uint64_t accf[2], acce[2], drain;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   __shared__ int ready_flag[2];   // B producers: the last input check (alternating)
@@ -294,16 +291,19 @@ __global__ void __launch_bounds__(kTtThreads, 1)
     atomicExch(err, code);
     *reinterpret_cast<volatile int *>(&abort_flag) = 1;
   };
-  auto slotA = [&](int s) { return smem_raw + (size_t)s * kTtSlotBytes; };
-  auto slotB = [&](int s) { return smem_raw + (size_t)s * kTtSlotBytes + kTtKS * kTtStep; };
-  auto slotR = [&](int s) {
-    return smem_raw + (size_t)kTtSlots * kTtSlotBytes + (size_t)s * kRawBytes;
+  auto slotA = [&](int a) { return smem_raw + (size_t)a * kTtASlotBytes; };
+  auto slotB = [&](int s) {
+    return smem_raw + (size_t)kTtASlots * kTtASlotBytes + (size_t)s * kTtBSlotBytes;
   };
   const long long slot_stride = (long long)nrhs * g.nsub * g.T;
 
   if (tid == 0) {
+    for (int a = 0; a < kTtASlots; ++a) {
+      mbar_init(&fullA[a], 1);
+      mbar_init(&emptyA[a], 1);
+    }
     for (int s = 0; s < kTtSlots; ++s) {
-      mbar_init(&full[s], 1 + kTtBWarps);
+      mbar_init(&full[s], kTtBWarps);
       mbar_init(&empty[s], 1);
     }
     for (int q = 0; q < 2; ++q) {
@@ -329,20 +329,20 @@ __global__ void __launch_bounds__(kTtThreads, 1)
       int ci = 0;   // chunks issued
       for (int j = c_beg; j < c_end && !aborted(); ++j, ++ci) {
         const int4 dsc = __ldg(chunks + j);
-        const int s = ci % kTtSlots;
-        if (ci >= kTtSlots && !mbar_wait(&empty[s], ((ci / kTtSlots) - 1) & 1)) {
+        const int a = ci % kTtASlots;
+        if (ci >= kTtASlots && !mbar_wait(&emptyA[a], ((ci / kTtASlots) - 1) & 1)) {
           fail(21);
           break;
         }
         if (aborted()) break;
         const uint32_t bytes = (uint32_t)(dsc.w & 0xFF) * kTtStep;
-        mbar_arrive_expect_tx(&full[s], bytes);
-        bulk_g2s(slotA(s), tiles + (long long)dsc.y * kTtStep, bytes, &full[s]);
+        mbar_arrive_expect_tx(&fullA[a], bytes);
+        bulk_g2s(slotA(a), tiles + (long long)dsc.y * kTtStep, bytes, &fullA[a]);
       }
       // no copy may still be landing when the CTA leaves: wait for the last chunk of each slot
-      for (int s = 0; s < kTtSlots && s < ci; ++s) {
-        const int last = s + (ci - 1 - s) / kTtSlots * kTtSlots;
-        if (!mbar_wait(&full[s], (last / kTtSlots) & 1)) atomicExch(err, 22);
+      for (int a = 0; a < kTtASlots && a < ci; ++a) {
+        const int last = a + (ci - 1 - a) / kTtASlots * kTtASlots;
+        if (!mbar_wait(&fullA[a], (last / kTtASlots) & 1)) atomicExch(err, 22);
       }
     }
   } else if (warp == kTtMmaWarp) {
@@ -363,12 +363,17 @@ __global__ void __launch_bounds__(kTtThreads, 1)
           const uint32_t d1 = tmem + (uint32_t)q * (8 * kTtCols), d2 = d1 + 4 * kTtCols;
           bool ok = true;
           for (int c = 0; c < nch; ++c, ++ci) {
-            const int s = ci % kTtSlots;
+            const int s = ci % kTtSlots, a = ci % kTtASlots;
             const int nks = __ldg(&chunks[c_beg + ci].w) & 0xFF;
-            if (!mbar_wait(&full[s], (ci / kTtSlots) & 1)) { fail(24); ok = false; break; }
+            if (!mbar_wait(&full[s], (ci / kTtSlots) & 1) ||
+                !mbar_wait(&fullA[a], (ci / kTtASlots) & 1)) {
+              fail(24);
+              ok = false;
+              break;
+            }
             if (aborted()) { ok = false; break; }
             umma::fence_after_sync();
-            uint64_t ad = umma::smem_desc(umma::saddr(slotA(s)), lbo_a, 128);
+            uint64_t ad = umma::smem_desc(umma::saddr(slotA(a)), lbo_a, 128);
             uint64_t bd = umma::smem_desc(umma::saddr(slotB(s)), (uint32_t)kTtLB, 128);
             for (int k = 0; k < nks; ++k) {
               const uint32_t acc = (c > 0 || k > 0) ? 1u : 0u;
@@ -386,7 +391,8 @@ __global__ void __launch_bounds__(kTtThreads, 1)
               ad += dA;
               bd += dB;
             }
-            umma::mma_commit(&empty[s]);   // the slot is free once these MMAs have read it
+            umma::mma_commit(&empty[s]);   // the slots are free once these MMAs have read them
+            umma::mma_commit(&emptyA[a]);
           }
           if (!ok) break;
           umma::mma_commit(&accf[q]);
@@ -398,23 +404,23 @@ __global__ void __launch_bounds__(kTtThreads, 1)
     }
   } else if (warp >= 4) {
     // ---------------- B producers: inputs of this CTA's chunks, split into pieces
-    // Dataflow instead of level barriers: before the first copy of a unit's inputs, warp 4
+    // Dataflow instead of level barriers: before the first load of a unit's inputs, warp 4
     // waits until every trace solve routed into the unit's slots (l, X) has published
-    // (ready[l nsub + X] == need[l nsub + X]).  Each chunk's raw inputs are copied into a
-    // staging slot by cp.async (L1 bypassed: other CTAs wrote them) several chunks before they
-    // are split into the ring slot, across unit and level boundaries.  Thread pt owns the pairs
-    // of consecutive inputs p = pt + 256 i of every chunk (column p / kPairs, inputs
-    // 2 (p % kPairs) and the next), copies them and splits them itself, so no barrier is
-    // needed between the copy and the split.  The unit's column words sit in a shared table
-    // (two, by unit parity), written by the readiness check, so that no copy waits on a load.
+    // (ready[l nsub + X] == need[l nsub + X]).  Thread pt owns the pairs of consecutive inputs
+    // p = pt + 256 i of every chunk (column p / kPairs, inputs 2 (p % kPairs) and the next): it
+    // loads them from the trace slots into registers (L2 only: other CTAs wrote them) two chunks
+    // ahead of their split, across unit and level boundaries, and splits them itself into the
+    // ring slot, so the inputs never pass through shared memory.  The unit's column words sit in a
+    // shared table (two, by unit parity), written by the readiness check.
     constexpr int kPairs = kTtKS * (KIND == 0 ? 8 : 16) / 2;   // input pairs per column
+    constexpr int kPer = kTtCols * kPairs / kTtBThreads;        // pairs per thread and chunk
     const int pt = tid - 128;   // 0 .. kTtBThreads - 1
     // are the unit's inputs complete (every producer routed into its slots has published)?  Lane
     // c of warp 4 polls the slot of column c (all columns at once), `block` = until it is complete
     // (bounded) or once, and puts the column word into table `tab`; the answer goes to all
     // producer threads through a shared flag (two, alternating, so that a reader of one check
     // never races the next write).  The table of unit n is written only after every producer
-    // thread has passed the check of unit n - 1, so after its copies of unit n - 2.
+    // thread has passed the check of unit n - 1, so after its loads of unit n - 2.
     int check_no = 0;
     auto inputs_ready = [&](const TtUnit &u, int tab, bool block) {
       const int fl = check_no++ & 1;
@@ -442,34 +448,33 @@ __global__ void __launch_bounds__(kTtThreads, 1)
       named_sync(2, kTtBThreads);
       return ready_flag[fl] != 0;
     };
-    // copy the raw inputs of chunk `dsc` of unit `u` (column table `tab`) into staging slot `slot`
-    auto stage = [&](const int4 &dsc, const TtUnit &u, int tab, int slot) {
+    // load this thread's pairs of chunk `dsc` of unit `u` (column table `tab`); zeros where the
+    // column or the input does not exist
+    auto load = [&](float4 (&rb)[kPer], const int4 &dsc, const TtUnit &u, int tab) {
       const int live = dsc.w >> 8;
       const float2 *src0 = gtr + (long long)u.l * slot_stride + dsc.z;
-      unsigned char *raw = slotR(slot);
       const int *cols = pcol[tab];
 #pragma unroll
-      for (int i = 0; i < kTtCols * kPairs / kTtBThreads; ++i) {
+      for (int i = 0; i < kPer; ++i) {
         const int q = pt + i * kTtBThreads;
         const int c2 = q / kPairs, kk = 2 * (q % kPairs);
-        const bool on = c2 < u.ncol && kk < live;
-        const int col = on ? cols[c2] : 0;
-        cp_async16(raw + q * 16, on ? (const void *)(src0 + (long long)col * g.T + kk)
-                                    : (const void *)gtr, on ? 16u : 0u);
+        rb[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (c2 < u.ncol && kk < live)
+          rb[i] = __ldcg(reinterpret_cast<const float4 *>(src0 + (long long)cols[c2] * g.T + kk));
       }
     };
-    // Chunk jp (stream position) is the next to stage, chunk c_beg + ci the next to split.  The
-    // copy side stages up to the staging slots ahead.  It enters a new unit only once that unit's
-    // inputs are complete, without waiting, except when the split needs the chunk now (then
-    // nothing earlier is pending in these threads, so the wait cannot hold up the trace solves it
-    // waits for).  Each staged chunk is one cp.async group, so chunk ci has landed once at most
-    // staged - 1 - ci groups are pending.
+    // Chunk `staged` is the next to load (into register buffer staged % 3), chunk ci the next to
+    // split.  Loads run up to two chunks ahead.  A unit is entered only once its inputs are
+    // complete, without waiting, except when its chunk is the one to split now (then nothing
+    // earlier is pending in these threads, so the wait cannot hold up the trace solves it waits
+    // for).
     const int nchunks = c_end - c_beg;
-    int staged = 0, un = -1, hdr_at = -1;   // chunks staged, ordinal of the staging unit
+    int staged = 0, un = -1, hdr_at = -1;   // chunks loaded, ordinal of the loading unit
     int4 dP = nchunks > 0 ? __ldg(chunks + c_beg) : make_int4(0, 0, 0, 0);
     TtUnit uP{};
-    for (int ci = 0; ci < nchunks; ++ci) {
-      while (staged < nchunks && staged < ci + kRawSlots) {   // the slot's chunk is split
+    float4 rb0[kPer], rb1[kPer], rb2[kPer];
+    auto fill = [&](int ci) {
+      while (staged < nchunks && staged <= ci + 2) {
         if ((dP.x >> 30) & 1) {   // first chunk of a unit
           if (hdr_at != staged) {
             uP = tt_unit(units, dP.x & 0x3FFFFFFF);
@@ -478,19 +483,18 @@ __global__ void __launch_bounds__(kTtThreads, 1)
           if (!inputs_ready(uP, (un + 1) & 1, staged == ci)) break;
           ++un;
         }
-        stage(dP, uP, un & 1, staged % kRawSlots);
-        cp_async_commit();
+        switch (staged % 3) {
+          case 0: load(rb0, dP, uP, un & 1); break;
+          case 1: load(rb1, dP, uP, un & 1); break;
+          default: load(rb2, dP, uP, un & 1); break;
+        }
         ++staged;
         if (staged < nchunks) dP = __ldg(chunks + c_beg + staged);
       }
-      switch (staged - 1 - ci) {
-        case 0: cp_async_wait_group<0>(); break;
-        case 1: cp_async_wait_group<1>(); break;
-        case 2: cp_async_wait_group<2>(); break;
-        case 3: cp_async_wait_group<3>(); break;
-        case 4: cp_async_wait_group<4>(); break;
-        default: cp_async_wait_group<5>(); break;
-      }
+    };
+    // split chunk ci (held in rb) into B ring slot ci % 2; every K-step of the slot is written,
+    // the MMAs read only the chunk's own
+    auto split = [&](const float4 (&rb)[kPer], int ci) {
       const int s = ci % kTtSlots;
       if (ci >= kTtSlots && !aborted()) {
         // (after an abort no wait is made: the MMAs may have stopped consuming)
@@ -500,23 +504,31 @@ __global__ void __launch_bounds__(kTtThreads, 1)
         if (!okw && lane == 0) fail(26);
       }
       if (!aborted()) {
-        // every K-step of the ring slot is written; the MMAs read only the chunk's own
-        const unsigned char *raw = slotR(ci % kRawSlots);
         unsigned char *sB = slotB(s);
 #pragma unroll
-        for (int i = 0; i < kTtCols * kPairs / kTtBThreads; ++i) {
+        for (int i = 0; i < kPer; ++i) {
           const int q = pt + i * kTtBThreads;
           const int c2 = q / kPairs, kk = 2 * (q % kPairs);
-          const float4 w = *reinterpret_cast<const float4 *>(raw + q * 16);
-          tt_put_b<KIND>(sB, kk, c2, make_float2(w.x, w.y));
-          tt_put_b<KIND>(sB, kk + 1, c2, make_float2(w.z, w.w));
+          tt_put_b<KIND>(sB, kk, c2, make_float2(rb[i].x, rb[i].y));
+          tt_put_b<KIND>(sB, kk + 1, c2, make_float2(rb[i].z, rb[i].w));
         }
       }
       fence_proxy_async();   // the generic writes of B before the MMAs' async reads
       __syncwarp();
       if (lane == 0) mbar_arrive(&full[s]);
+    };
+    for (int ci = 0; ci < nchunks; ci += 3) {
+      fill(ci);
+      split(rb0, ci);
+      if (ci + 1 < nchunks) {
+        fill(ci + 1);
+        split(rb1, ci + 1);
+      }
+      if (ci + 2 < nchunks) {
+        fill(ci + 2);
+        split(rb2, ci + 2);
+      }
     }
-    cp_async_wait_all();   // nothing stays in flight
   } else {
     // ---------------- epilogue: row R of the unit's tile, every column
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
