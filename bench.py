@@ -496,7 +496,9 @@ def run_gpu(args):
                 "Mb": int(np.prod(inf["M"][:len(wl.n) - 1])),
                 "trace_kernel": inf.get("trace_kernel", 1),
                 "subst_kernel": inf.get("subst_kernel", 2),
-                "sweeps": (2 ** len(wl.n)) * wl.rounds}
+                "sweeps": (2 ** len(wl.n)) * wl.rounds,
+                "panel_width": (tuned or {}).get("panel_width"),
+                "panels_per_cta": (tuned or {}).get("panels_per_cta")}
     roofline, roofline_kernels = (roofline_entry(stats, work, ddm_apps, args, geometry)
                                   if args.profile_steps > 0 else (None, []))
 
@@ -561,10 +563,16 @@ DTYPE = {"mixed": "c64 sweeps (3xTF32 tensor-core substitutions) + c128 FGMRES",
 SPLIT_KIND = {"mixed": "tf32", "mixed_bf16": "bf16", "mixed_fp32": "fp32"}
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the substitution and
 # trace kernels, from one ncu capture of each kernel as it stands, on the same workload and launch
-# configuration (cold, serialised replay: written data that stays in L2 is not counted)
-SUBST_TRAFFIC = {("mixed", "const2d_640"): 48.68e6 + 0.99e6}
+# shape (panel width, panels per CTA; cold, serialised replay: written data that stays in L2 is
+# not counted).  The substitution figure is the mean over the launches of one solve (the first
+# own-source launch skips most local problems as zero).  HBM_TRAFFIC: the same counters per DDM
+# application for the assembly and extraction families.
+SUBST_TRAFFIC = {("mixed", "const2d_640", 16, 1): 48.68e6 + 0.99e6,
+                 ("mixed", "layer2d_1024", 16, 2): (40.0e6 + 5 * 3176.5e6) / 6}
 TRACE_TRAFFIC = {("mixed", "const2d_640"): 40.26e6 + 0.08e6}
-TRACE_TC_TRAFFIC = {}
+TRACE_TC_TRAFFIC = {("mixed", "layer2d_1024"): 691.0e6 + 503.3e6}
+HBM_TRAFFIC = {("mixed", "layer2d_1024"): {"assemble": 1125.1e6 + 1115.0e6 + 1924.7e6 + 1255.4e6,
+                                           "extract": 403.0e6 + 76.8e6 + 695.8e6 + 1135.2e6}}
 
 
 def roofline_entry(stats, work, ddm_apps, args, geometry=None):
@@ -581,6 +589,7 @@ def roofline_entry(stats, work, ddm_apps, args, geometry=None):
     device time is the line's roofline; all are listed.
     """
     peaks, src = _peaks()
+    geo = geometry or {}
     fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
     kind = SPLIT_KIND.get(args.precision, "fp32")
     entries = []
@@ -607,7 +616,8 @@ def roofline_entry(stats, work, ddm_apps, args, geometry=None):
             e = {"kernel": "k_subst_stream<float> (block forward+back substitution)", "bound": "alu",
                  "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
         e.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                  "traffic": SUBST_TRAFFIC.get((args.precision, args.workload)),
+                  "traffic": SUBST_TRAFFIC.get((args.precision, args.workload,
+                                                geo.get("panel_width"), geo.get("panels_per_cta"))),
                   "launches": n_s, "avg_launch_ms": ms_s / n_s, "device_ms": ms_s})
         entries.append(e)
     n_t, ms_t = stats["trace_step"]
@@ -639,7 +649,6 @@ def roofline_entry(stats, work, ddm_apps, args, geometry=None):
     #   over the owned ranges (which tile the global grid), and the final launch reads the trace
     #   slots of every sweep;  extraction (two launches): the raw trace lines read and written,
     #   then the owned nodes read locally and written to the global field (FP64).
-    geo = geometry or {}
     if geo.get("plan") == 2 and geo.get("Nloc"):   # DDS_PLAN_TRACE
         hbm = peaks.get("hbm_gbs", 6800.0)
         el = 16 if args.precision == "fp64" else 8
@@ -652,14 +661,17 @@ def roofline_entry(stats, work, ddm_apps, args, geometry=None):
             "extract": ("k_extract (trace lines, owned nodes to the global field)",
                         2 * cols * T * el + R * Ng * (el + 16)),
         }
+        measured = HBM_TRAFFIC.get((args.precision, args.workload), {})
         for key, (name, nbytes) in fam.items():
             n_k, ms_k = stats.get(key, (0, 0.0))
             if n_k > 0 and ms_k > 0:
                 achieved = nbytes * ddm_apps / (ms_k / 1e3) / 1e9
+                # per launch (two launches per DDM application), like the algorithmic bytes
+                traffic = measured[key] / 2 if key in measured else None
                 entries.append({"kernel": name, "bound": "hbm",
                                 "peak_source": f"{src} hbm_gbs", "achieved": achieved,
                                 "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                                "traffic": None, "bytes_per_ddm": nbytes,
+                                "traffic": traffic, "bytes_per_launch": nbytes / 2,
                                 "launches": n_k, "avg_launch_ms": ms_k / n_k, "device_ms": ms_k})
     if not entries:
         return None, []

@@ -23,7 +23,7 @@ def test_roofline_entries_and_main_family():
              "krylov": (10, 3.0)}
     work = (18.4e9 * 2, 11.3e9)          # per DDM application: 2 substitution launches, 1 trace
     geo = {"plan": 2, "nrhs": 16, "nsub": 64, "T": 832, "Nglob": 664 * 664, "Nloc": 104 * 104,
-           "sweeps": 8}
+           "sweeps": 8, "panel_width": 16, "panels_per_cta": 1}
     main, entries = bench.roofline_entry(stats, work, 2, _Args(), geo)
     by = {e["kernel"].split(" ")[0]: e for e in entries}
     sub = by["k_subst_tc<tf32>"]
@@ -31,13 +31,16 @@ def test_roofline_entries_and_main_family():
     assert sub["achieved"] == pytest.approx(18.4e9 * 2 * 2 / 2.9e-3 / 1e12)
     assert sub["frac"] == pytest.approx(sub["achieved"] / sub["peak"])
     assert sub["avg_launch_ms"] == pytest.approx(2.9 / 4)
-    assert sub["traffic"] == bench.SUBST_TRAFFIC[("mixed", "const2d_640")]
+    # the measured DRAM bytes belong to the launch shape they were taken with
+    assert sub["traffic"] == bench.SUBST_TRAFFIC[("mixed", "const2d_640", 16, 1)]
     tr = by["k_trace_sweeps<float>"]
     assert tr["bound"] == "alu"
     assert tr["achieved"] == pytest.approx(11.3e9 * 2 / 2.75e-3 / 1e12)
     asm = by["k_assemble"]
     assert asm["bound"] == "hbm" and asm["unit"] == "GB/s"
-    assert asm["achieved"] == pytest.approx(asm["bytes_per_ddm"] * 2 / 0.36e-3 / 1e9)
+    assert asm["achieved"] == pytest.approx(asm["bytes_per_launch"] * 2 * 2 / 0.36e-3 / 1e9)
+    # no DRAM counters were taken for this workload's HBM kernels
+    assert asm["traffic"] is None
     # the family with the larger device time carries the line
     assert main["kernel"] == sub["kernel"] and "family_share" in main
 
@@ -46,3 +49,23 @@ def test_whole_job_rate_of_replicas():
     assert bench.whole_job_rate(1, 16, 5, 0.025) == pytest.approx(3200.0)
     assert bench.whole_job_rate(4, 16, 5, 0.025) == pytest.approx(4 * 3200.0)
     assert bench.whole_job_rate(2, 16, 5, 0.0) is None
+
+
+def test_roofline_traffic_follows_the_launch_shape():
+    """DRAM bytes are attached only to the workload and launch shape they were counted on."""
+    stats = {"subst": (6, 16.0), "trace_step": (3, 9.3), "assemble": (6, 4.6), "extract": (6, 1.8)}
+    work = (2 * 178.6e9, 202e9)
+    geo = {"plan": 2, "nrhs": 64, "nsub": 256, "T": 704, "Nglob": 1048 * 1048, "Nloc": 88 * 88,
+           "sweeps": 8, "trace_kernel": 0, "panel_width": 16, "panels_per_cta": 2}
+
+    class A(_Args):
+        workload = "layer2d_1024"
+
+    _, entries = bench.roofline_entry(stats, work, 3, A(), geo)
+    by = {e["kernel"].split(" ")[0]: e for e in entries}
+    assert by["k_subst_tc<tf32>"]["traffic"] == bench.SUBST_TRAFFIC[("mixed", "layer2d_1024", 16, 2)]
+    assert by["k_trace_tc<tf32>"]["traffic"] == bench.TRACE_TC_TRAFFIC[("mixed", "layer2d_1024")]
+    assert by["k_assemble"]["traffic"] == bench.HBM_TRAFFIC[("mixed", "layer2d_1024")]["assemble"] / 2
+    _, entries = bench.roofline_entry(stats, work, 3, A(), dict(geo, panel_width=32, panels_per_cta=1))
+    by = {e["kernel"].split(" ")[0]: e for e in entries}
+    assert by["k_subst_tc<tf32>"]["traffic"] is None
