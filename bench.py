@@ -482,13 +482,19 @@ def run_gpu(args):
 
     # roofline of the dominant kernel family, timed with CUDA events on the library's stream
     ctx.profile(True)
+    ctx.local_solve_counts(reset=True)
     ddm_apps = 0
     for _ in range(args.profile_steps):
         _, it_p, _ = ctx.solve(f_dev, tol=args.tol, maxit=args.maxit, rounds=wl.rounds)
         ddm_apps += it_p
     stats = ctx.kernel_stats()
     ctx.profile(False)
-    work = ctx.work_per_ddm(R, wl.rounds)
+    # zero-work skipping leaves some local problems unsolved: the substitutions are credited only
+    # with the ones they ran
+    solved, assembled = ctx.local_solve_counts(reset=True)
+    work = list(ctx.work_per_ddm(R, wl.rounds))
+    if assembled > 0:
+        work[0] *= solved / assembled
     inf = ctx.info()
     geometry = {"plan": inf["plan"], "nrhs": R, "nsub": inf["n_sub"], "T": inf["trace_len"],
                 "Nglob": int(np.prod(inf["G"][:len(wl.n)])),
@@ -499,7 +505,10 @@ def run_gpu(args):
                 "sweeps": (2 ** len(wl.n)) * wl.rounds,
                 "panel_width": (tuned or {}).get("panel_width"),
                 "panels_per_cta": (tuned or {}).get("panels_per_cta")}
-    roofline, roofline_kernels = (roofline_entry(stats, work, ddm_apps, args, geometry)
+    # the dense MMA rate of the piece type on this GPU, next to the recipe's peak (set-up work)
+    kind = SPLIT_KIND.get(args.precision, "fp32")
+    mma_rate = dds.tensor_rate(kind) if kind in ("tf32", "bf16") and args.profile_steps > 0 else None
+    roofline, roofline_kernels = (roofline_entry(stats, work, ddm_apps, args, geometry, mma_rate)
                                   if args.profile_steps > 0 else (None, []))
 
     cpu = None
@@ -575,7 +584,7 @@ HBM_TRAFFIC = {("mixed", "layer2d_1024"): {"assemble": 1125.1e6 + 1115.0e6 + 192
                                            "extract": 403.0e6 + 76.8e6 + 695.8e6 + 1135.2e6}}
 
 
-def roofline_entry(stats, work, ddm_apps, args, geometry=None):
+def roofline_entry(stats, work, ddm_apps, args, geometry=None, mma_rate=None):
     """Rooflines of the two sweep kernel families from their event-timed totals.
 
     work = (substitution flops, trace-map flops) of one DDM application (dds_work_per_ddm:
@@ -586,13 +595,22 @@ def roofline_entry(stats, work, ddm_apps, args, geometry=None):
     measured BF16 rate x 1.1/2.25, the nominal TF32:BF16 ratio); FP32 CUDA-core kernels take
     152 SMs x 128 lanes x 2 flop x 2070 MHz.  The tensor peaks are the measured burst rate: each
     launch is timed alone, within solves of milliseconds.  The entry of the family with the larger
-    device time is the line's roofline; all are listed.
+    device time is the line's roofline; all are listed.  mma_rate: the dense rate of the piece type
+    measured on this GPU by dds_tensor_rate (TF/s of pieces); a tensor entry then also gives its
+    fraction of that rate / 3 (`frac_of_mma_rate`).
     """
     peaks, src = _peaks()
     geo = geometry or {}
     fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
     kind = SPLIT_KIND.get(args.precision, "fp32")
     entries = []
+
+    def with_rate(e):
+        if mma_rate and e.get("bound") == "tensor":
+            e["mma_rate_peak"] = mma_rate / 3.0
+            e["frac_of_mma_rate"] = e["achieved"] / (mma_rate / 3.0)
+        return e
+
     n_s, ms_s = stats["subst"]
     if n_s > 0 and ms_s > 0 and work[0] > 0:
         achieved = work[0] * ddm_apps / (ms_s / 1e3) / 1e12
@@ -619,7 +637,7 @@ def roofline_entry(stats, work, ddm_apps, args, geometry=None):
                   "traffic": SUBST_TRAFFIC.get((args.precision, args.workload,
                                                 geo.get("panel_width"), geo.get("panels_per_cta"))),
                   "launches": n_s, "avg_launch_ms": ms_s / n_s, "device_ms": ms_s})
-        entries.append(e)
+        entries.append(with_rate(e))
     n_t, ms_t = stats["trace_step"]
     if n_t > 0 and ms_t > 0 and work[1] > 0:
         achieved = work[1] * ddm_apps / (ms_t / 1e3) / 1e12
@@ -643,7 +661,7 @@ def roofline_entry(stats, work, ddm_apps, args, geometry=None):
         e.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                   "frac": achieved / peak, "launches": n_t, "avg_launch_ms": ms_t / n_t,
                   "device_ms": ms_t})
-        entries.append(e)
+        entries.append(with_rate(e))
     # HBM-side kernels of the trace plan, from their algorithmic bytes per DDM application:
     #   assembly (two launches): every local right-hand side written once, the source read once
     #   over the owned ranges (which tile the global grid), and the final launch reads the trace

@@ -238,6 +238,15 @@ dds_status dds_autotune(dds_ctx *ctx, int nrhs, int rounds, int max_entries, int
 dds_status dds_set_launch_shape(dds_ctx *ctx, int panel_width, int panels_per_cta,
                                 int trace_kernel);
 
+/* dds_tensor_rate -- measured dense tensor-core rate of the current device for a split-product
+ * piece type: kind 0 = TF32 (tcgen05 kind::tf32), 1 = BF16 (kind::f16), in TFLOP/s of the
+ * pieces (a 3x split product delivers a third of it in useful flops).  Every SM issues
+ * back-to-back M = 128, N = 256 MMAs from shared memory into tensor memory for about a
+ * millisecond, as the substitution and trace kernels do.  Needs no context; runs on its own
+ * stream and synchronises it.  DDS_EINVAL for another kind, DDS_ETIMEOUT if the completion wait
+ * gave up, DDS_ECUDA on a CUDA error. */
+dds_status dds_tensor_rate(int kind, double *tflops);
+
 /* dds_work_per_ddm -- algorithmic floating-point work of one DDM application (Algorithm 2.1 /
  * 4.1, `rounds` rounds of 2^n sweeps) for nrhs right-hand sides, computed on the host:
  *   *subst_flops  block forward + back substitutions, 16 Ml Mb^2 real flops per local solve

@@ -19,7 +19,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libdds.so")
 SOURCES = ["dds.cu", "k_sweep.cu", "k_factor.cu", "k_krylov.cu", "k_subst_stream.cu",
-           "k_subst_tc.cu", "k_subst_big.cu", "k_trace_tc.cu"]
+           "k_subst_tc.cu", "k_subst_big.cu", "k_trace_tc.cu", "k_rate.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -2020,6 +2020,27 @@ dds_status dds_autotune(dds_ctx *ctx, int nrhs, int rounds, int max_entries, int
   return check_errflag(ctx);
 }
 
+dds_status dds_tensor_rate(int kind, double *tflops) {
+  if (!tflops || (kind != 0 && kind != 1)) return DDS_EINVAL;
+  *tflops = 0.0;
+  int *err = nullptr;
+  if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return DDS_ENOMEM;
+  }
+  int herr = 0;
+  double flops = 0.0;
+  float ms = 0.f;
+  cudaError_t e = cudaMemset(err, 0, sizeof(int));
+  if (e == cudaSuccess) e = measure_mma_rate(kind, 16384, err, &flops, &ms);
+  if (e == cudaSuccess) e = cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(err);
+  if (e != cudaSuccess) return DDS_ECUDA;
+  if (herr != 0) return DDS_ETIMEOUT;
+  if (ms > 0.f) *tflops = flops / (ms * 1e-3) / 1e12;
+  return DDS_OK;
+}
+
 dds_status dds_work_per_ddm(dds_ctx *ctx, int nrhs, int rounds, double *subst_flops,
                             double *trace_flops) {
   if (!ctx || nrhs <= 0 || rounds < 1 || !subst_flops || !trace_flops) return DDS_EINVAL;

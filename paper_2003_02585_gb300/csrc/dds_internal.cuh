@@ -268,6 +268,9 @@ struct TtShape {
   long long rt_bytes, fac_bytes;
   size_t smem;
 };
+// dense MMA rate (M = 128, N = 256) of piece type `kind` on every SM: flops and time of `iters`
+// MMAs per SM (k_rate.cu)
+cudaError_t measure_mma_rate(int kind, int iters, int *err, double *flops, float *ms);
 bool tt_shape(const Geom &g, int kind, TtShape *s);
 long long tt_tiles_bytes(const Geom &g, int kind, int nfac);
 cudaError_t launch_split_trace(cudaStream_t st, const Geom &g, int kind, int nfac,

@@ -283,6 +283,10 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1)
     }
   }
   if (np_act == 0) return;
+  // two panels of one factor read the same tile at every stage: it is streamed once and both
+  // panels' MMAs read it (half the L2 traffic of the tiles, which paces the chain)
+  const bool shared = NP == 2 && np_act == 2 && P[0].factor == P[NP - 1].factor;
+  const int streams = shared ? 1 : np_act;   // tile streams per stage
   auto aborted = [&]() { return *reinterpret_cast<volatile int *>(&abort_flag) != 0; };
   auto fail = [&](int code) {
     atomicExch(err, code);
@@ -315,15 +319,15 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1)
   const uint32_t tmem = tmem_base;
 
   if (warp == 4 * NG) {
-    // ---------------- producer: the tiles of every (stage, panel) through the two-slot ring
+    // ---------------- producer: the tiles of every (stage, stream) through the two-slot ring
     if (lane == 0) {
       int last0 = -1, last1 = -1;
-      const int nchunks = nst * np_act * a.nch;
+      const int nchunks = nst * streams * a.nch;
       for (int i = 0; i < nchunks; ++i) {
         const int s = i & 1;
         if (i >= 2 && !mbar_wait(&empty[s], ((i >> 1) - 1) & 1)) { fail(11); break; }
         if (aborted()) break;
-        const int q = i / (np_act * a.nch), h = (i / a.nch) % np_act, c = i % a.nch;
+        const int q = i / (streams * a.nch), h = (i / a.nch) % streams, c = i % a.nch;
         const int nks = min(a.KS, a.ks - c * a.KS);
         const uint32_t bytes = (uint32_t)nks * 128u * (uint32_t)a.Mp;
         const int j = tc_stage(role, q, m, Ml).j;
@@ -350,36 +354,63 @@ __global__ void __launch_bounds__(32 * (4 * NG + 2), 1)
       const uint64_t dB = (uint64_t)(2 * a.LB) >> 4;       // one K-step of B
       int i = 0;                                           // ring chunks consumed
       bool ok = true;
+      // the MMAs of panel h on ring slot s, chunk c of the stage
+      auto issue = [&](int h, int s, int c) {
+        const uint64_t b0 = umma::smem_desc(umma::saddr(sBp(h)), (uint32_t)a.LB, 128);
+        const uint32_t d1 = tmem + (uint32_t)h * NCOL, d2 = d1 + 4 * PC;
+        const int nks = min(a.KS, a.ks - c * a.KS);
+        uint64_t ad = umma::smem_desc(umma::saddr(ring + s * chunk_bytes), lbo_a, 128);
+        uint64_t bd = b0 + (uint64_t)(c * a.KS) * dB;
+        for (int t = 0; t < nks; ++t) {
+          const uint32_t acc = (c > 0 || t > 0) ? 1u : 0u;
+          if (KIND == 0) {
+            umma::mma_tf32(d1, ad, bd, kIdN4, acc);
+            umma::mma_tf32(d1, ad + dC, bd, kIdN2, 1);
+            umma::mma_tf32(d2, ad + 2 * dC, bd, kIdN4, acc);
+            umma::mma_tf32(d2, ad + 3 * dC, bd, kIdN2, 1);
+          } else {
+            umma::mma_bf16(d1, ad, bd, kIdN4, acc);
+            umma::mma_bf16(d1, ad + dC, bd, kIdN2, 1);
+            umma::mma_bf16(d2, ad + 2 * dC, bd, kIdN4, acc);
+            umma::mma_bf16(d2, ad + 3 * dC, bd, kIdN2, 1);
+          }
+          ad += dA;
+          bd += dB;
+        }
+      };
       for (int q = 0; q < nst && ok; ++q) {
-        for (int h = 0; h < np_act && ok; ++h) {
-          if (!mbar_wait(&bready[h], q & 1)) { fail(13); ok = false; break; }
+        if (shared) {
+          // one tile stream for both panels: panel 0's MMAs, then panel 1's, on every chunk.
+          // Panel 1's operand is waited for only before its first MMA, and panel 0's accumulator
+          // is released right after its last, so each panel's epilogue overlaps the other's MMAs.
+          if (!mbar_wait(&bready[0], q & 1)) { fail(13); ok = false; break; }
           if (aborted()) { ok = false; break; }
-          umma::fence_after_sync();
-          const uint64_t b0 = umma::smem_desc(umma::saddr(sBp(h)), (uint32_t)a.LB, 128);
-          const uint32_t d1 = tmem + (uint32_t)h * NCOL, d2 = d1 + 4 * PC;
           for (int c = 0; c < a.nch; ++c, ++i) {
             const int s = i & 1;
             if (!mbar_wait(&full[s], (i >> 1) & 1)) { fail(14); ok = false; break; }
             umma::fence_after_sync();
-            const int nks = min(a.KS, a.ks - c * a.KS);
-            uint64_t ad = umma::smem_desc(umma::saddr(ring + s * chunk_bytes), lbo_a, 128);
-            uint64_t bd = b0 + (uint64_t)(c * a.KS) * dB;
-            for (int t = 0; t < nks; ++t) {
-              const uint32_t acc = (c > 0 || t > 0) ? 1u : 0u;
-              if (KIND == 0) {
-                umma::mma_tf32(d1, ad, bd, kIdN4, acc);
-                umma::mma_tf32(d1, ad + dC, bd, kIdN2, 1);
-                umma::mma_tf32(d2, ad + 2 * dC, bd, kIdN4, acc);
-                umma::mma_tf32(d2, ad + 3 * dC, bd, kIdN2, 1);
-              } else {
-                umma::mma_bf16(d1, ad, bd, kIdN4, acc);
-                umma::mma_bf16(d1, ad + dC, bd, kIdN2, 1);
-                umma::mma_bf16(d2, ad + 2 * dC, bd, kIdN4, acc);
-                umma::mma_bf16(d2, ad + 3 * dC, bd, kIdN2, 1);
-              }
-              ad += dA;
-              bd += dB;
+            issue(0, s, c);
+            if (c == a.nch - 1) umma::mma_commit(&dready[0]);
+            if (c == 0) {
+              if (!mbar_wait(&bready[1], q & 1)) { fail(13); ok = false; break; }
+              umma::fence_after_sync();
             }
+            issue(1, s, c);
+            umma::mma_commit(&empty[s]);   // the slot is free once these MMAs have read it
+          }
+          if (!ok) break;
+          umma::mma_commit(&dready[1]);
+          continue;
+        }
+        for (int h = 0; h < np_act && ok; ++h) {
+          if (!mbar_wait(&bready[h], q & 1)) { fail(13); ok = false; break; }
+          if (aborted()) { ok = false; break; }
+          umma::fence_after_sync();
+          for (int c = 0; c < a.nch; ++c, ++i) {
+            const int s = i & 1;
+            if (!mbar_wait(&full[s], (i >> 1) & 1)) { fail(14); ok = false; break; }
+            umma::fence_after_sync();
+            issue(h, s, c);
             umma::mma_commit(&empty[s]);   // the slot is free once these MMAs have read it
           }
           if (!ok) break;

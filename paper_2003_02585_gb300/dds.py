@@ -28,7 +28,8 @@ EXPORTS = ["dds_setup", "dds_sweep", "dds_sweep_strip", "dds_solve", "dds_apply"
            "dds_server_create", "dds_server_submit", "dds_server_step", "dds_server_poll",
            "dds_server_destroy", "dds_work_per_ddm", "dds_autotune", "dds_set_zero_skip",
            "dds_local_solve_counts", "dds_set_memory_budget", "dds_set_wait_limit",
-           "dds_server_slots", "dds_set_launch_shape"]
+           "dds_server_slots", "dds_set_launch_shape",
+           "dds_tensor_rate"]
 KERNEL_KINDS = {"assemble": 0, "subst": 1, "extract": 2, "trace_step": 3, "krylov": 4,
                 "other": 5}
 
@@ -106,6 +107,8 @@ def load(path: str = LIB_PATH):
     lib.dds_set_wait_limit.argtypes = [vp, ctypes.c_longlong]
     lib.dds_set_launch_shape.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     lib.dds_set_launch_shape.restype = ctypes.c_int
+    lib.dds_tensor_rate.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    lib.dds_tensor_rate.restype = ctypes.c_int
     lib.dds_local_solve_counts.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong),
                                            ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
     lib.dds_profile_read.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
@@ -167,6 +170,17 @@ def check_noalloc_pair(b, out, M, dim, device_index):
     if tuple(out.shape) != tuple(b.shape):
         raise ValueError(f"out has shape {tuple(out.shape)}, b {tuple(b.shape)}")
     return nrhs
+
+
+def tensor_rate(kind="tf32"):
+    """Measured dense tensor-core rate (TFLOP/s of pieces) of the current device for the TF32 or
+    BF16 split-product pieces (dds_tensor_rate)."""
+    lib = load()
+    v = ctypes.c_double(0.0)
+    st = lib.dds_tensor_rate({"tf32": 0, "bf16": 1}[kind], ctypes.byref(v))
+    if st != 0:
+        raise DDSError(f"dds_tensor_rate failed with status {st}")
+    return v.value
 
 
 class Context:

@@ -69,3 +69,18 @@ def test_roofline_traffic_follows_the_launch_shape():
     _, entries = bench.roofline_entry(stats, work, 3, A(), dict(geo, panel_width=32, panels_per_cta=1))
     by = {e["kernel"].split(" ")[0]: e for e in entries}
     assert by["k_subst_tc<tf32>"]["traffic"] is None
+
+
+def test_tensor_entries_report_the_measured_mma_rate():
+    """With the measured dense rate of the piece type, each tensor entry also gives its fraction of
+    a third of it (three split products per useful product); other entries are unchanged."""
+    stats = {"subst": (6, 16.0), "trace_step": (3, 9.3), "assemble": (6, 4.6), "extract": (6, 1.8)}
+    work = (2 * 178.6e9, 202e9)
+    geo = {"plan": 2, "nrhs": 64, "nsub": 256, "T": 704, "Nglob": 1048 * 1048, "Nloc": 88 * 88,
+           "sweeps": 8, "trace_kernel": 0, "panel_width": 16, "panels_per_cta": 2}
+    _, entries = bench.roofline_entry(stats, work, 3, _Args(), geo, mma_rate=1209.0)
+    by = {e["kernel"].split(" ")[0]: e for e in entries}
+    for k in ("k_subst_tc<tf32>", "k_trace_tc<tf32>"):
+        assert by[k]["mma_rate_peak"] == pytest.approx(403.0)
+        assert by[k]["frac_of_mma_rate"] == pytest.approx(by[k]["achieved"] / 403.0)
+    assert "frac_of_mma_rate" not in by["k_assemble"]
