@@ -577,7 +577,7 @@ SPLIT_KIND = {"mixed": "tf32", "mixed_bf16": "bf16", "mixed_fp32": "fp32"}
 # own-source launch skips most local problems as zero).  HBM_TRAFFIC: the same counters per DDM
 # application for the assembly and extraction families.
 SUBST_TRAFFIC = {("mixed", "const2d_640", 16, 1): 48.68e6 + 0.99e6,
-                 ("mixed", "layer2d_1024", 16, 2): (40.0e6 + 5 * 3176.5e6) / 6}
+                 ("mixed", "layer2d_1024", 16, 2): 16326.6e6 / 6}
 TRACE_TRAFFIC = {("mixed", "const2d_640"): 40.26e6 + 0.08e6}
 TRACE_TC_TRAFFIC = {("mixed", "layer2d_1024"): 691.0e6 + 503.3e6}
 HBM_TRAFFIC = {("mixed", "layer2d_1024"): {"assemble": 1125.1e6 + 1115.0e6 + 1924.7e6 + 1255.4e6,
