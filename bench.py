@@ -39,7 +39,7 @@ WORKLOAD = "layer2d_1024"
 WORKLOADS = {
     "layer2d_1024": ("2D two-layer medium (c=1 for y<0.37, c=1.5 above; interface not aligned to "
                      "subdomain boundaries), k=2*pi*50, 1024x1024 grid, 16x16 subdomains (64x64 + "
-                     "12-cell PML), 64 RHS seeded Gaussian point sources (width 2h), DDM (2 rounds) "
+                     "12-cell PML), 64 RHS seeded Gaussian point sources (width 2h), DDM (3 rounds) "
                      "as FGMRES preconditioner, tol 1e-6, complex64 sweeps / FP64 factorisation "
                      "and FGMRES"),
     "const2d_640": ("2D constant medium c=1, k=2*pi*40, 640x640 interior grid, 8x8 subdomains "
@@ -577,11 +577,10 @@ SPLIT_KIND = {"mixed": "tf32", "mixed_bf16": "bf16", "mixed_fp32": "fp32"}
 # own-source launch skips most local problems as zero).  HBM_TRAFFIC: the same counters per DDM
 # application for the assembly and extraction families.
 SUBST_TRAFFIC = {("mixed", "const2d_640", 16, 1): 48.68e6 + 0.99e6,
-                 ("mixed", "layer2d_1024", 16, 2): 16326.6e6 / 6}
+                 ("mixed", "layer2d_1024", 16, 2): 9808.2e6 / 4}
 TRACE_TRAFFIC = {("mixed", "const2d_640"): 40.26e6 + 0.08e6}
-TRACE_TC_TRAFFIC = {("mixed", "layer2d_1024"): 691.0e6 + 503.3e6}
-HBM_TRAFFIC = {("mixed", "layer2d_1024"): {"assemble": 1125.1e6 + 1115.0e6 + 1924.7e6 + 1255.4e6,
-                                           "extract": 403.0e6 + 76.8e6 + 695.8e6 + 1135.2e6}}
+TRACE_TC_TRAFFIC = {("mixed", "layer2d_1024"): 1030.9e6 + 822.7e6}
+HBM_TRAFFIC = {("mixed", "layer2d_1024"): {"assemble": 11619.9e6 / 2, "extract": 4621.4e6 / 2}}
 
 
 def roofline_entry(stats, work, ddm_apps, args, geometry=None, mma_rate=None):
