@@ -4,7 +4,8 @@
 //   backward x_{Ml-1} = y_{Ml-1}, x_j = y_j - S_j^{-1} (C_j x_{j+1})
 // Each of the 2 Ml - 1 stages is one GEMM over all columns of the launch, S_j^{-1} V (Mb x Mb
 // times Mb x columns), spread over the whole GPU:
-//   k_big_mma  one CTA per unit (128-row tile of S_j^{-1}, panel of PC columns, K segment):
+//   k_big_mma  one CTA per unit (128-row tile of S_j^{-1}, panel of PC columns, K segment; the
+//              panels of one tile segment adjacent in the grid, so they share its reads in L2):
 //              the unit's pre-split A tiles and the matching B pieces stream through a two-slot
 //              shared-memory ring (bulk copies on mbarriers); four tcgen05.mma per K-step into
 //              two TMEM accumulators (split products, as in k_subst_tc.cu); the unit's partial
@@ -165,10 +166,13 @@ __global__ void __launch_bounds__(192, 1)
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   uint64_t *full = bars, *empty = bars + 2, *dready = bars + 4, *drain = bars + 5;
+  // the panel index varies fastest: the CTAs that read the same (row tile, K segment) of S_j^{-1}
+  // run side by side, so that the tile comes from HBM once and from L2 for the other panels
   const int unit = blockIdx.x;
-  const int rt = unit % a.RT;
-  const int ks = (unit / a.RT) % ((a.KT + a.KTU - 1) / a.KTU);
-  const int pn = unit / (a.RT * ((a.KT + a.KTU - 1) / a.KTU));
+  const int npan = (int)(gridDim.x / (a.RT * ((a.KT + a.KTU - 1) / a.KTU)));
+  const int pn = unit % npan;
+  const int rt = (unit / npan) % a.RT;
+  const int ks = unit / (npan * a.RT);
   const Panel p = panels[pn];
   if (p.ncol == 0) return;   // an empty panel of a compacted list: its B and acc stay zero
   const int t0 = ks * a.KTU, nt = min(a.KTU, a.KT - t0);
