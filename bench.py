@@ -773,7 +773,8 @@ def run_serving(args):
         "config": {"workload": "serving: Poisson requests (1-32 sources) over 256^2 constant, "
                                "512^2 two-layer and 1024^2 random media, continuous batching",
                    "requests": len(reqs), "arrival_rate_per_s": args.serve_rate,
-                   "slots": out["slots"], "budget_gb": args.serve_budget_gb,
+                   "slots": out["slots"], "launch_shapes": out["launch_shapes"],
+                   "budget_gb": args.serve_budget_gb,
                    "maxit": args.serve_maxit},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
         "setup_seconds": out["setup_s"], "max_relres": out["max_relres"],
@@ -825,7 +826,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-rate", type=float, default=10.0, help="requests per second")
-    ap.add_argument("--serve-budget-gb", type=float, default=120.0)
+    ap.add_argument("--serve-budget-gb", type=float, default=180.0)
     ap.add_argument("--serve-maxit", type=int, default=16,
                     help="FGMRES iterations a serving slot is sized for (slot memory grows with it)")
     args = ap.parse_args()

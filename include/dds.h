@@ -191,7 +191,10 @@ dds_status dds_server_create(dds_ctx *ctx, int max_slots, double tol, int maxit,
 int dds_server_slots(const dds_server *srv);
 
 /* queue one source field f (global extended grid, complex double, host or device); tag is
- * returned with its solution.  The field is copied before the call returns. */
+ * returned with its solution.  The field is copied before the call returns: into device memory
+ * while the context's budget (dds_set_memory_budget) has room for it beyond the eighth the
+ * server keeps free for its steps, otherwise (or when the device has no room) into host memory,
+ * from which admission copies it to its slot.  DDS_ENOMEM only if neither has room. */
 dds_status dds_server_submit(dds_server *srv, const void *f, long long tag);
 
 /* one batched iteration; *active = slots in flight after it, *queued = requests still waiting */
@@ -201,6 +204,9 @@ dds_status dds_server_step(dds_server *srv, int *active, int *queued);
  * final true relative residual.  Returns DDS_EBUSY (and touches nothing) when none is ready. */
 dds_status dds_server_poll(dds_server *srv, long long *tag, void *u, int *iters, double *relres);
 
+/* free the server.  The server may outlive its context: dds_destroy releases the device memory
+ * of every server made on the context and leaves them orphaned; every later call on an orphaned
+ * server but this one returns DDS_EINVAL. */
 void dds_server_destroy(dds_server *srv);
 
 /* dds_set_stream -- run all later work of ctx on the given cudaStream_t (NULL = the context's
@@ -312,7 +318,9 @@ dds_status dds_profile_read(dds_ctx *ctx, int kind, long long *launches, double 
 /* dds_last_error -- message of the last failed call on ctx (empty string if none). */
 const char *dds_last_error(const dds_ctx *ctx);
 
-/* dds_destroy -- free every device and host resource of ctx (NULL is ignored). */
+/* dds_destroy -- free every device and host resource of ctx (NULL is ignored), including the
+ * device memory of the servers made on it, which stay allocated as orphans until
+ * dds_server_destroy. */
 void dds_destroy(dds_ctx *ctx);
 
 #ifdef __cplusplus

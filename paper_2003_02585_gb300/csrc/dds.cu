@@ -11,6 +11,7 @@
 #include <complex>
 #include <cstdio>
 #include <cstring>
+#include <new>
 #include <deque>
 #include <map>
 #include <memory>
@@ -117,6 +118,9 @@ struct CallPlan {            // all launch lists for one nrhs
 
 }  // namespace
 
+// releases a server's device memory and detaches it from its context (defined with the server)
+void server_orphan(dds_server *srv);
+
 struct dds_ctx {
   MemAcct acct;   // first member: destroyed after every buffer that reports to it
   std::mutex mu;
@@ -165,6 +169,9 @@ struct dds_ctx {
   DBuf work, gtr, acc, rawf, bbuf, stage_in, stage_out, dots_part, dots_out, coefbuf, scalebuf;
   DBuf Vbig, Zbig;   // Krylov bases
   // CUDA graphs of whole DDM applications, keyed by (b, u, nrhs, rounds); captured on gstream
+  // servers made on this context: destroying the context first releases their device memory
+  // (while its accounting still exists) and leaves them orphaned
+  std::vector<dds_server *> servers;
   struct GraphEntry { cudaGraphExec_t exec = nullptr; long long nodes = 0; };
   std::map<std::array<long long, 4>, GraphEntry> graphs;
   cudaStream_t gstream = nullptr;
@@ -2182,6 +2189,7 @@ void dds_destroy(dds_ctx *ctx) {
   if (!ctx) return;
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   else cudaDeviceSynchronize();
+  for (dds_server *srv : ctx->servers) server_orphan(srv);
   delete ctx;
 }
 
@@ -2193,6 +2201,7 @@ void dds_destroy(dds_ctx *ctx) {
 struct dds_server {
   dds_ctx *ctx = nullptr;
   int S = 0, maxit = 0, rounds = 1;
+  size_t reserve = 0;   // budget bytes kept free for what a step allocates besides the slots
   double tol = 1e-6;
   long long N = 0;
   DBuf V, Z, B, U, bin, bout, hdev, part, coef;
@@ -2205,7 +2214,14 @@ struct dds_server {
     std::vector<cd> H, cs, sn, g;
   };
   std::vector<Slot> slots;
-  std::deque<std::pair<long long, std::unique_ptr<DBuf>>> queue;
+  // a submitted source waiting for a slot: in a device buffer, or, when the context's budget has
+  // no room for one more, in host memory (copied to the device at admission)
+  struct Queued {
+    long long tag;
+    std::unique_ptr<DBuf> buf;
+    std::vector<double2> host;
+  };
+  std::deque<Queued> queue;
   // spent queue buffers, reused by later submissions (no cudaMalloc / cudaFree per request,
   // both of which synchronise the whole device); reuse is ordered by the context's stream
   std::vector<std::unique_ptr<DBuf>> pool;
@@ -2308,6 +2324,23 @@ dds_status server_finalize(dds_server *srv, const std::vector<int> &fin) {
   return DDS_OK;
 }
 
+}  // namespace
+
+void server_orphan(dds_server *srv) {
+  if (!srv) return;
+  srv->queue.clear();
+  srv->pool.clear();
+  srv->finished.clear();
+  srv->slots.clear();
+  for (DBuf *b : {&srv->V, &srv->Z, &srv->B, &srv->U, &srv->bin, &srv->bout, &srv->hdev,
+                  &srv->part, &srv->coef, &srv->offs, &srv->hb})
+    b->release();
+  srv->S = 0;
+  srv->ctx = nullptr;
+}
+
+namespace {
+
 dds_status server_admit(dds_server *srv) {
   dds_ctx *ctx = srv->ctx;
   cudaStream_t st = ctx->stream;
@@ -2315,6 +2348,7 @@ dds_status server_admit(dds_server *srv) {
   // every admission of this step is launched first; their norms come back in one read
   std::vector<int> admitted;
   std::vector<double2> b2(srv->S);
+  std::vector<std::vector<double2>> kept;
   for (int s = 0; s < srv->S && !srv->queue.empty(); ++s) {
     auto &sl = srv->slots[s];
     if (sl.state != 0) continue;
@@ -2322,15 +2356,27 @@ dds_status server_admit(dds_server *srv) {
     srv->queue.pop_front();
     sl = dds_server::Slot();
     sl.state = 1;
-    sl.tag = req.first;
+    sl.tag = req.tag;
     const int m = srv->maxit;
     sl.H.assign((size_t)(m + 1) * m, cd(0, 0));
     sl.cs.assign(m, cd(0, 0));
     sl.sn.assign(m, cd(0, 0));
     sl.g.assign(m + 1, cd(0, 0));
     ctx->launches += 3;
-    SCK(launch_scale_J(st, ctx->g, ctx->tb, 1, req.second->as<double2>(), srv->Bs(s)));
-    srv->pool.push_back(std::move(req.second));   // later copies into it follow on the stream
+    const double2 *src = nullptr;
+    if (req.buf) {
+      src = req.buf->as<double2>();
+    } else {
+      // a source queued in host memory goes through this slot's part of the DDM input buffer
+      // (rewritten later in the step, on the same stream)
+      double2 *stage = srv->bin.as<double2>() + (long long)s * N;
+      SCK(cudaMemcpyAsync(stage, req.host.data(), (size_t)N * sizeof(double2),
+                          cudaMemcpyHostToDevice, st));
+      src = stage;
+      kept.push_back(std::move(req.host));   // alive until the synchronisation below
+    }
+    SCK(launch_scale_J(st, ctx->g, ctx->tb, 1, src, srv->Bs(s)));
+    if (req.buf) srv->pool.push_back(std::move(req.buf));   // later copies into it follow on the stream
     SCK(launch_dots(st, N, 1, 1, srv->Bs(s), 0, 0, srv->Bs(s), 0, srv->part.as<double2>(),
                     srv->Hd(s), server_nblk(srv)));
     SCK(launch_scale_by_norm(st, N, 1, srv->Bs(s), srv->Hd(s), srv->Vs(s, 0)));
@@ -2488,8 +2534,8 @@ dds_status dds_server_create(dds_ctx *ctx, int max_slots, double tol, int maxit,
   Busy busy(ctx);   // the slots' memory counts against the context (dds_set_memory_budget)
   if (!busy.ok) return DDS_EBUSY;
   ctx->err.clear();
-  // admission by device memory: as many slots as the context's budget (or, without one, 90% of
-  // the device's free memory) leaves room for, up to max_slots
+  // admission by device memory: as many slots as seven eighths of what the context's budget (or,
+  // without one, 90% of the device's free memory) leaves room for, up to max_slots
   const size_t per_slot = server_slot_bytes(ctx, maxit, rounds);
   size_t room = 0;
   if (ctx->acct.budget) {
@@ -2499,6 +2545,10 @@ dds_status dds_server_create(dds_ctx *ctx, int max_slots, double tol, int maxit,
     CK(cudaMemGetInfo(&fr, &tot));
     room = fr / 10 * 9;
   }
+  // an eighth of the room stays free for what a step allocates besides the slots: the DDM plan
+  // of each batch size (trace schedules, tables) and the growth of shared work buffers
+  const size_t reserve = room / 8;
+  room -= reserve;
   const long long fit = (long long)(room / per_slot);
   if (fit < 1) {
     ctx->err = "dds_server_create: one slot needs " + std::to_string(per_slot) +
@@ -2509,6 +2559,7 @@ dds_status dds_server_create(dds_ctx *ctx, int max_slots, double tol, int maxit,
   if (!srv) return DDS_ENOMEM;
   srv->ctx = ctx;
   srv->S = (int)std::min<long long>(max_slots, fit);
+  srv->reserve = ctx->acct.budget ? reserve : 0;
   srv->maxit = maxit;
   srv->rounds = rounds;
   srv->tol = tol;
@@ -2532,6 +2583,7 @@ dds_status dds_server_create(dds_ctx *ctx, int max_slots, double tol, int maxit,
     return DDS_ENOMEM;
   }
   srv->slots.resize(srv->S);
+  ctx->servers.push_back(srv.get());
   *out = srv.release();
   return DDS_OK;
 }
@@ -2539,10 +2591,12 @@ dds_status dds_server_create(dds_ctx *ctx, int max_slots, double tol, int maxit,
 int dds_server_slots(const dds_server *srv) { return srv ? srv->S : 0; }
 
 dds_status dds_server_submit(dds_server *srv, const void *f, long long tag) {
-  if (!srv || !f) return DDS_EINVAL;
+  if (!srv || !f || !srv->ctx) return DDS_EINVAL;
   dds_ctx *ctx = srv->ctx;
   Busy busy(ctx);
   if (!busy.ok) return DDS_EBUSY;
+  // waiting sources take device copies while the budget has room beyond the reserve a step
+  // needs; the rest wait in host memory
   std::unique_ptr<DBuf> buf;
   if (!srv->pool.empty()) {
     buf = std::move(srv->pool.back());
@@ -2551,16 +2605,39 @@ dds_status dds_server_submit(dds_server *srv, const void *f, long long tag) {
     buf = std::make_unique<DBuf>();
   }
   const size_t fb = (size_t)srv->N * sizeof(double2);
-  CK(buf->ensure(fb));
-  CK(cudaMemcpyAsync(buf->p, f, fb, is_device_ptr(f) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                     ctx->stream));
+  dds_server::Queued q{tag, nullptr, {}};
+  const bool room = buf->p || !ctx->acct.budget ||
+                    ctx->acct.used + fb + srv->reserve <= ctx->acct.budget;
+  const cudaError_t e = room ? buf->ensure(fb) : cudaErrorMemoryAllocation;
+  if (e != cudaSuccess && buf->p) srv->pool.push_back(std::move(buf));   // kept for later
+  if (e == cudaSuccess) {
+    CK(cudaMemcpyAsync(buf->p, f, fb, is_device_ptr(f) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                       ctx->stream));
+    q.buf = std::move(buf);
+  } else if (e == cudaErrorMemoryAllocation) {
+    // no device room for one more waiting source (the budget, or the device itself): it waits
+    // in host memory instead
+    cudaGetLastError();
+    try {
+      q.host.resize((size_t)srv->N);
+    } catch (const std::bad_alloc &) {
+      ctx->err = "dds_server_submit: no device or host memory for the source";
+      return DDS_ENOMEM;
+    }
+    if (is_device_ptr(f))
+      CK(cudaMemcpyAsync(q.host.data(), f, fb, cudaMemcpyDeviceToHost, ctx->stream));
+    else
+      std::memcpy(q.host.data(), f, fb);
+  } else {
+    CK(e);
+  }
   CK(cudaStreamSynchronize(ctx->stream));
-  srv->queue.emplace_back(tag, std::move(buf));
+  srv->queue.push_back(std::move(q));
   return DDS_OK;
 }
 
 dds_status dds_server_step(dds_server *srv, int *active, int *queued) {
-  if (!srv) return DDS_EINVAL;
+  if (!srv || !srv->ctx) return DDS_EINVAL;
   Busy busy(srv->ctx);
   if (!busy.ok) return DDS_EBUSY;
   srv->ctx->err.clear();
@@ -2568,7 +2645,7 @@ dds_status dds_server_step(dds_server *srv, int *active, int *queued) {
 }
 
 dds_status dds_server_poll(dds_server *srv, long long *tag, void *u, int *iters, double *relres) {
-  if (!srv || !u) return DDS_EINVAL;
+  if (!srv || !u || !srv->ctx) return DDS_EINVAL;
   dds_ctx *ctx = srv->ctx;
   Busy busy(ctx);
   if (!busy.ok) return DDS_EBUSY;
@@ -2589,7 +2666,11 @@ dds_status dds_server_poll(dds_server *srv, long long *tag, void *u, int *iters,
 
 void dds_server_destroy(dds_server *srv) {
   if (!srv) return;
-  if (srv->ctx && srv->ctx->stream) cudaStreamSynchronize(srv->ctx->stream);
+  if (dds_ctx *ctx = srv->ctx) {   // (an orphaned server's context is gone already)
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    auto &v = ctx->servers;
+    v.erase(std::remove(v.begin(), v.end(), srv), v.end());
+  }
   delete srv;
 }
 

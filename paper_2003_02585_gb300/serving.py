@@ -76,6 +76,9 @@ class MediumWorker(threading.Thread):
         self.medium = medium
         self.ctx = dds.Context(medium.n, 1.0 / medium.n[0], medium.omega, medium.c, medium.parts,
                                medium.pml_cells, 30.0, precision="mixed")
+        # launch shapes picked by measurement for a typical batch (set-up work, before the budget
+        # applies: the tuner's scratch is its own)
+        self.tuned = self.ctx.autotune(32, rounds)
         # admission by device memory inside the library: the context's budget caps everything
         # it holds, and the server takes the slots that fit in what is left (at most 64)
         self.ctx.set_memory_budget(int(budget_bytes))
@@ -89,6 +92,15 @@ class MediumWorker(threading.Thread):
         self.steps = 0
         self.rhs_done = 0
         self.error = None
+
+    def close(self):
+        """Destroy the server, then its context (after the worker has stopped)."""
+        if self.server is not None:
+            self.server.close()
+            self.server = None
+        if self.ctx is not None:
+            self.ctx.close()
+            self.ctx = None
 
     def put(self, req: Request):
         with self.lock:
@@ -159,15 +171,22 @@ def run(requests, media=None, budget_bytes=40e9, tol=1e-6, maxit=30, rounds=2):
         workers[req.medium].put(req)
     for w in workers:
         w.stop = True
+    # every worker leaves the library before an error surfaces (a worker whose peer failed
+    # still finishes its own requests), and the servers go before their contexts
     for w in workers:
         w.join()
-        if w.error is not None:
-            raise w.error
+    errors = [w.error for w in workers if w.error is not None]
+    for w in workers:
+        w.close()
+    if errors:
+        raise errors[0]
     wall = time.perf_counter() - t0
     lat = np.array([r.completion - r.arrival for r in requests])
     return {"latency_s": lat, "wall_s": wall, "setup_s": setup,
             "rhs": int(sum(len(r.centres) for r in requests)),
             "slots": [w.slots for w in workers], "steps": [w.steps for w in workers],
+            "launch_shapes": [{k: w.tuned[k] for k in ("panel_width", "panels_per_cta",
+                                                        "trace_ctas_per_sm")} for w in workers],
             "max_relres": float(max(max(r.relres) for r in requests)),
             "max_iters": [max([max(r.iters) for r in requests if r.medium == i and r.iters] or [0])
                           for i in range(len(media))],

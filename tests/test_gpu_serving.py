@@ -104,3 +104,88 @@ def test_server_admits_by_device_memory():
     assert e.value.status == 2                     # DDS_ENOMEM
     ctx.set_memory_budget(0)
     assert dds.Server(ctx, 5, 1e-6, 20, 1).slots == 5
+
+
+def test_budgeted_server_steps_batches_of_every_size():
+    """A server created under a tight budget still has room, at every step, for what a step
+    allocates besides its slots (the DDM plan of each new batch size): requests arriving one, two
+    and three at a time all finish without DDS_ENOMEM, each to the tolerance."""
+    from paper_2003_02585_gb300 import dds
+    n = (96, 96)
+    h = 1.0 / 96
+    ctx = dds.Context(n, h, 2 * np.pi * 6, synth.medium_two_layer(n, h), (3, 3), 10, 30.0,
+                      precision="mixed", plan="trace")
+    held = ctx.info()["device_bytes"]
+    field = 16 * int(np.prod(ctx.G))
+    ctx.set_memory_budget(held + 8 * field * (2 * 12 + 5))
+    srv = dds.Server(ctx, 64, 1e-6, 12, 2)
+    assert srv.slots >= 3
+    rng = np.random.default_rng(7)
+    tag = 0
+    done = []
+    for burst in (1, 2, 3, srv.slots, 1):
+        for _ in range(burst):
+            f = synth.gaussian_sources(n, h, [tuple(rng.uniform(0.2, 0.8, size=2))], 2 * h)
+            srv.submit(ctx.extend(f), tag)
+            tag += 1
+        for _ in range(200):
+            active, queued = srv.step()
+            while (r := srv.poll()) is not None:
+                done.append(r)
+            if active == 0 and queued == 0:
+                break
+    assert len(done) == tag
+    assert max(r[3] for r in done) <= 1e-6
+    srv.close()
+
+
+def test_sources_waiting_beyond_the_budget_queue_in_host_memory():
+    """More sources than the budget holds device copies for are all accepted (the overflow waits
+    in host memory) and all solved, each to the tolerance."""
+    from paper_2003_02585_gb300 import dds
+    n = (96, 96)
+    h = 1.0 / 96
+    ctx = dds.Context(n, h, 2 * np.pi * 6, synth.medium_constant(n), (3, 3), 10, 30.0,
+                      precision="mixed")
+    held = ctx.info()["device_bytes"]
+    field = 16 * int(np.prod(ctx.G))
+    floor = field * (2 * 12 + 5)                  # one slot's basis and batch fields
+    budget = held + (5 * floor) // 2              # two slots at most, and about ten spare fields
+    ctx.set_memory_budget(budget)
+    srv = dds.Server(ctx, 2, 1e-6, 12, 1)
+    rng = np.random.default_rng(11)
+    nreq = 40                                     # far more waiting fields than the budget's room
+    for tag in range(nreq):
+        f = synth.gaussian_sources(n, h, [tuple(rng.uniform(0.2, 0.8, size=2))], 2 * h)
+        srv.submit(ctx.extend(f), tag)
+    assert ctx.info()["device_bytes"] <= budget
+    done = []
+    for _ in range(2000):
+        active, queued = srv.step()
+        while (r := srv.poll()) is not None:
+            done.append(r)
+        if active == 0 and queued == 0:
+            break
+    assert sorted(r[0] for r in done) == list(range(nreq))
+    assert max(r[3] for r in done) <= 1e-6
+    srv.close()
+
+
+def test_context_destroyed_before_its_server():
+    """A server may outlive its context (garbage collection can finalise them in any order): the
+    context's destruction releases the server's device memory, later calls on the server are
+    rejected with DDS_EINVAL, and destroying the server afterwards is safe."""
+    from paper_2003_02585_gb300 import dds
+    n = (48, 48)
+    h = 1.0 / 48
+    ctx = dds.Context(n, h, 2 * np.pi * 3, synth.medium_constant(n), (2, 2), 6, 30.0,
+                      precision="mixed")
+    srv = dds.Server(ctx, 4, 1e-6, 10, 1)
+    f = synth.gaussian_sources(n, h, [(0.4, 0.6)], 2 * h)
+    srv.submit(ctx.extend(f), 1)
+    srv.step()
+    ctx.close()
+    with pytest.raises(dds.DDSError) as e:
+        srv.step()
+    assert e.value.status == 1                     # DDS_EINVAL
+    srv.close()
