@@ -6,7 +6,7 @@ L2 is asserted (observed ~1e-13).  Single-precision modes: substitutions and tra
 (unit roundoff 6e-8; 3xTF32 split products ~1e-6 and 3xBF16 ~4e-6 per block product on the
 tensor cores, amplified by the local solve's conditioning); the raw DDM output is checked to
 1e-4 relative (1e-3 for 3xBF16), and after FP64 FGMRES refinement the field must match the oracle's
-global solve to 1e-6 (the BASELINE accuracy target).
+global solve to 1e-6 (the accuracy target of the mixed mode).
 """
 
 import numpy as np
