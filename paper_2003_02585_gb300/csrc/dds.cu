@@ -2417,6 +2417,13 @@ dds_status server_step(dds_server *srv, int *active_out, int *queued_out) {
                           srv->Vs(act[i], srv->slots[act[i]].j), N * sizeof(double2),
                           cudaMemcpyDeviceToDevice, st));
     r = ddm(ctx, srv->bin.as<double2>(), k, srv->bout.as<double2>(), srv->rounds);
+    if (r == DDS_ENOMEM && !srv->pool.empty()) {
+      // idle queue buffers give their memory back to the step, which is tried once more
+      SCK(cudaStreamSynchronize(st));
+      srv->pool.clear();
+      ctx->err.clear();
+      r = ddm(ctx, srv->bin.as<double2>(), k, srv->bout.as<double2>(), srv->rounds);
+    }
     if (r != DDS_OK) return r;
     const int nblk = server_nblk(srv);
     const long long vslot = (long long)(srv->maxit + 1) * N, zslot = (long long)srv->maxit * N;
