@@ -770,7 +770,7 @@ def run_serving(args):
     media = serving.serving_media()
     reqs = serving.poisson_requests(rng, args.serve_requests, args.serve_rate, len(media))
     out = serving.run(reqs, media, budget_bytes=args.serve_budget_gb * 1e9, tol=args.tol,
-                      maxit=args.serve_maxit, rounds=args.rounds or 2)
+                      maxit=args.serve_maxit, rounds=args.rounds or 3)
     lat = np.sort(out["latency_s"]) * 1e3
     line = {
         "metric": METRIC, "value": out["rhs"] / out["wall_s"], "unit": "RHS/s", "n_gpus": 1,

@@ -152,7 +152,7 @@ class MediumWorker(threading.Thread):
             self.error = e
 
 
-def run(requests, media=None, budget_bytes=40e9, tol=1e-6, maxit=30, rounds=2):
+def run(requests, media=None, budget_bytes=40e9, tol=1e-6, maxit=30, rounds=3):
     """Serve `requests` (arrival times in seconds from the start) in real time.  Returns per-
     request latencies (s), wall time, RHS count and worker statistics."""
     media = serving_media() if media is None else media
