@@ -451,20 +451,8 @@ def run_gpu(args):
     value = whole_job_rate(world, R, args.steps, total_ms / 1e3)
     u_mixed = u
 
-    # accuracy against the plain FP64 GPU solve, and that solve's own throughput
-    if args.no_fp64:
-        err, fp64_ms, fp64_value, u64, fp64_spread, fp64_its = [float("nan")], [], None, None, \
-            None, []
-    else:
-        err, fp64_ms, fp64_value, u64, fp64_spread, fp64_its = fp64_check(
-            args, wl, R, f_dev, u_mixed, stream, flush)
-    # the other single-precision sweep variants, timed the same way
-    variants = [time_variant(args, wl, R, f_dev, stream, flush, p, u64)
-                for p in args.variants.split(",")
-                if p and p != "none" and p != args.precision]
-    del u64
-
-    # end to end through the C ABI with host (pinned) buffers
+    # end to end through the C ABI with host (pinned) buffers, right after the device-timed steps
+    # (before the comparator and variant contexts come and go)
     f_pin = torch.from_numpy(f_host).pin_memory()
     u_pin = torch.empty_like(f_pin).pin_memory()
     fn = f_pin.numpy()
@@ -486,6 +474,19 @@ def run_gpu(args):
             raise RuntimeError(f"dds_solve from host buffers failed: {st}")
     e2e_total = _reduce_max(sum(e2e_s), world) if e2e_s else 0.0
     e2e_value = whole_job_rate(world, R, len(e2e_s), e2e_total)
+
+    # accuracy against the plain FP64 GPU solve, and that solve's own throughput
+    if args.no_fp64:
+        err, fp64_ms, fp64_value, u64, fp64_spread, fp64_its = [float("nan")], [], None, None, \
+            None, []
+    else:
+        err, fp64_ms, fp64_value, u64, fp64_spread, fp64_its = fp64_check(
+            args, wl, R, f_dev, u_mixed, stream, flush)
+    # the other single-precision sweep variants, timed the same way
+    variants = [time_variant(args, wl, R, f_dev, stream, flush, p, u64)
+                for p in args.variants.split(",")
+                if p and p != "none" and p != args.precision]
+    del u64
 
     # roofline of the dominant kernel family, timed with CUDA events on the library's stream
     ctx.profile(True)
