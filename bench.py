@@ -584,8 +584,7 @@ SPLIT_KIND = {"mixed": "tf32", "mixed_bf16": "bf16", "mixed_fp32": "fp32"}
 # not counted).  The substitution figure is the mean over the launches of one solve (the first
 # own-source launch skips most local problems as zero).  HBM_TRAFFIC: the same counters per DDM
 # application for the assembly and extraction families.
-SUBST_TRAFFIC = {("mixed", "const2d_640", 16, 1): 48.68e6 + 0.99e6,
-                 ("mixed", "layer2d_1024", 16, 2): 9808.2e6 / 4}
+SUBST_TRAFFIC = {("mixed", "layer2d_1024", 16, 2): 9808.2e6 / 4}
 TRACE_TRAFFIC = {("mixed", "const2d_640"): 40.26e6 + 0.08e6}
 TRACE_TC_TRAFFIC = {("mixed", "layer2d_1024"): 1030.9e6 + 822.7e6}
 HBM_TRAFFIC = {("mixed", "layer2d_1024"): {"assemble": 11619.9e6 / 2, "extract": 4621.4e6 / 2}}

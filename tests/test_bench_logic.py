@@ -31,8 +31,8 @@ def test_roofline_entries_and_main_family():
     assert sub["achieved"] == pytest.approx(18.4e9 * 2 * 2 / 2.9e-3 / 1e12)
     assert sub["frac"] == pytest.approx(sub["achieved"] / sub["peak"])
     assert sub["avg_launch_ms"] == pytest.approx(2.9 / 4)
-    # the measured DRAM bytes belong to the launch shape they were taken with
-    assert sub["traffic"] == bench.SUBST_TRAFFIC[("mixed", "const2d_640", 16, 1)]
+    # no counters of the substitution kernel as it stands were taken on this workload
+    assert sub["traffic"] is None
     tr = by["k_trace_sweeps<float>"]
     assert tr["bound"] == "alu"
     assert tr["achieved"] == pytest.approx(11.3e9 * 2 / 2.75e-3 / 1e12)
